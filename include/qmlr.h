@@ -1,0 +1,205 @@
+/*
+ * qmlr.h - C ABI of the GB300 (sm_103a) implementation of the SORF + FCHL19
+ * approximate kernel method (Browning, Faber, von Lilienfeld, "GPU-Accelerated
+ * Approximate Kernel Method for Quantum Machine Learning").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status (QMLR_OK = 0 on success). On failure
+ *   qmlr_last_error() returns a message for the calling thread.
+ * - Array arguments are device pointers owned by the caller unless the name
+ *   starts with host_. Nothing is freed or retained by the library unless a
+ *   handle says so.
+ * - Work is enqueued on the caller's CUDA stream (passed as void*, a
+ *   cudaStream_t; NULL = legacy default stream) and is asynchronous unless
+ *   stated otherwise.
+ * - Arguments are validated on the host before any launch (QMLR_EINVAL).
+ *   Conditions only the device can see (a molecule with more atoms than the
+ *   launch was sized for, an element index out of range) make the kernel skip
+ *   that molecule and record a code that qmlr_device_status() returns.
+ * - Layouts are row-major. Atoms of one molecule are contiguous; molecule m
+ *   owns atoms [mol_ptr[m], mol_ptr[m+1]) (CSR offsets, mol_ptr[0] = 0).
+ * - Element indices are 0..n_el-1 (the synthetic workloads use H,C,N,O,F).
+ */
+#ifndef QMLR_H
+#define QMLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  QMLR_OK = 0,
+  QMLR_EINVAL = 1,    /* invalid argument (shape, size, pointer, parameter) */
+  QMLR_ENOMEM = 2,    /* an allocation made by the library failed */
+  QMLR_ECUDA = 3,     /* a CUDA runtime call or launch failed */
+  QMLR_EBUSY = 4,     /* serving: request not admitted (slots or memory) */
+  QMLR_ETIMEOUT = 5,  /* a bounded wait ran out */
+  QMLR_ENOTCONV = 6,  /* solve: refinement did not reach its tolerance (alpha written) */
+  QMLR_EDEVICE = 7    /* a kernel recorded a device-side input error */
+};
+
+/* Library version string; never NULL. */
+const char* qmlr_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* qmlr_last_error(void);
+
+/*
+ * Synchronises `stream`, then reads and clears the device-side error word of
+ * the current device. *host_code = 0 if no kernel recorded an error since the
+ * last call; 1 = molecule larger than the launch's max_mol_atoms, 2 = element
+ * index out of range, 3 = index out of range, 4 = bounded wait ran out,
+ * 5 = matrix not positive definite. Returns QMLR_EDEVICE when *host_code != 0.
+ */
+int qmlr_device_status(void* stream, int32_t* host_code);
+
+/* ------------------------------------------------------------------------
+ * FCHL19 representation (Representation section: two-body, cutoff,
+ * three-body, ATM and Fourier-angular equations; parameter table of the
+ * Computational Details section).
+ * ------------------------------------------------------------------------ */
+typedef struct qmlr_fchl19_params {
+  int32_t n_el;      /* element types, 1..8 */
+  int32_t n2;        /* two-body radial grid points, R_s = rcut*k/n2, k=1..n2 (1..64) */
+  int32_t n3;        /* three-body radial grid points, R_s = rcut*k/n3 (1..64) */
+  int32_t nfourier;  /* Fourier order of the angular term; must be 1 */
+  double eta2;       /* two-body log-normal width parameter */
+  double eta3;       /* three-body Gaussian width */
+  double N2;         /* two-body decay exponent: r^-N2 */
+  double N3;         /* three-body ATM decay exponent: (r_ij r_jk r_ik)^-N3 */
+  double c3;         /* three-body weight */
+  double zeta;       /* angular Gaussian width */
+  double rcut;       /* cutoff radius in Angstrom */
+} qmlr_fchl19_params;
+
+/* rep_dim = n_el*n2 + n_el(n_el+1)/2 * n3 * 2 (780 for 5 elements, n2=24, n3=22). */
+int qmlr_fchl19_rep_dim(const qmlr_fchl19_params* p, int32_t* rep_dim);
+
+/*
+ * FCHL19 forward: rho_i for every atom.
+ *   coords   float [n_atoms][3]  positions (Angstrom)
+ *   elem     int32 [n_atoms]     element index
+ *   mol_ptr  int32 [n_mol+1]     CSR molecule offsets; neighbours are taken
+ *                                within the same molecule only
+ *   max_mol_atoms                upper bound on atoms per molecule (1..256);
+ *                                sizes the shared-memory staging
+ *   rep      float [n_atoms][rep_ld], rep_ld >= rep_dim; columns rep_dim..rep_ld-1
+ *            are written as zeros.
+ * Layout of a row: two-body block [element of j][n2], then three-body block
+ * [unordered element pair (a<=b), row-major upper triangle][n3][cos, sin].
+ * Deterministic: each atom's row is summed by one warp in a fixed order.
+ */
+int qmlr_fchl19(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                int32_t n_mol, int32_t n_atoms, int32_t max_mol_atoms,
+                const qmlr_fchl19_params* p, float* rep, int32_t rep_ld, void* stream);
+
+/*
+ * FCHL19 vector-Jacobian product (forces through the representation; the
+ * backward pass the Computational Details section describes, with three-body
+ * terms recomputed rather than stored):
+ *   grad_coords[k] (+)= sum_i (d rho_i / d r_k)^T grad_rep[i]
+ *   grad_rep    float [n_atoms][rep_ld]
+ *   grad_coords float [n_atoms][3]; overwritten when accumulate == 0, added to otherwise.
+ * Same geometry arguments as qmlr_fchl19. Deterministic (fixed-order sums per molecule).
+ */
+int qmlr_fchl19_vjp(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                    int32_t n_mol, int32_t n_atoms, int32_t max_mol_atoms,
+                    const qmlr_fchl19_params* p, const float* grad_rep, int32_t rep_ld,
+                    float* grad_coords, int32_t accumulate, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Per-element projection (SORF section: SVD of the representations of each
+ * element, rho_proj = rho^T U_e^{N_PCA}; GPU implementation paragraph: each
+ * element has its own projection matrix).
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace qmlr_group_by_element needs for n_atoms atoms. */
+int64_t qmlr_group_workspace_bytes(int32_t n_atoms);
+
+/*
+ * Stable grouping of atoms by element (a counting sort on the device):
+ *   perm         int32 [n_atoms]  atom indices, element 0 first, ascending atom
+ *                                 index within an element
+ *   elem_offsets int32 [n_el+1]   atoms of element e are perm[elem_offsets[e] .. elem_offsets[e+1])
+ *   work         device workspace of qmlr_group_workspace_bytes(n_atoms) bytes
+ * Element indices outside [0, n_el) are recorded as a device error and
+ * grouped with element 0.
+ */
+int qmlr_group_by_element(const int32_t* elem, int32_t n_atoms, int32_t n_el, int32_t* perm,
+                          int32_t* elem_offsets, void* work, int64_t work_bytes, void* stream);
+
+/*
+ * x[i][:] = rep[i][:rep_dim] * U[elem(i)]   (float32 arithmetic, float32 accumulation)
+ *   rep  float [n_atoms][rep_ld]
+ *   perm, elem_offsets  from qmlr_group_by_element
+ *   U    float [n_el][rep_dim][d]   (U_e with the d basis vectors as columns)
+ *   x    float [n_atoms][d]
+ * d is a power of two, 16..512.
+ */
+int qmlr_project(const float* rep, int32_t rep_ld, int32_t rep_dim, const int32_t* perm,
+                 const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el, const float* U,
+                 int32_t d, float* x, void* stream);
+
+/*
+ * Transposed projection (chain rule through the projection):
+ *   grad_rep[i][:rep_dim] = U[elem(i)] * sum_p gx[p][i][:]
+ * gx holds n_part partial gradients [n_part][n_atoms][d] (summed in a fixed
+ * order). Columns rep_dim..rep_ld-1 of grad_rep are written as zeros.
+ */
+int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* perm,
+                   const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el, const float* U,
+                   int32_t d, int32_t rep_dim, float* grad_rep, int32_t rep_ld, void* stream);
+
+/* ------------------------------------------------------------------------
+ * SORF feature map (SORF section; RFF feature-map equation; GPU
+ * implementation paragraph on structured orthogonal features).
+ *   u = (sqrt(d)/sigma) [H D_{s,T}] ... [H D_{s,1}] x / sqrt(d)^T + b,  z = sqrt(2/N_F) cos(u)
+ * for every stack s = 0..N_F/d-1, with H the unnormalised Walsh-Hadamard
+ * matrix and D_{s,t} the Rademacher diagonal of stack s, transform t (applied
+ * before H). sign_bits[(s*T + t)*(d/32 rounded up) + w] bit j set means
+ * D_{s,t}[32w + j] = -1.
+ * ------------------------------------------------------------------------ */
+enum {
+  QMLR_SORF_PER_ATOM = 0, /* out: float [n_atoms][N_F]  z for every atom */
+  QMLR_SORF_PER_MOL = 1,  /* out: float [n_mol][N_F]    Z_m = sum_{I in m} z_I (fixed order) */
+  QMLR_SORF_ENERGY = 2    /* out: double [n_mol]        E_m = sum_{I in m} alpha^T z_I */
+};
+
+/*
+ * x          float [n_atoms][d] projected representations
+ * sign_bits  uint32 [n_stack][T][ceil(d/32)]
+ * b          float [N_F] phases
+ * alpha      float [N_F] regression weights (ENERGY mode; otherwise may be NULL)
+ * out        see mode
+ * T is 1..4; d is a power of two, 16..128; N_F = n_features is a multiple of d.
+ * In ENERGY mode with more than 128 stacks the per-part molecule sums are
+ * added to out with FP64 atomics (out is zeroed first).
+ */
+int qmlr_sorf(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+              const uint32_t* sign_bits, int32_t T, const float* b, int32_t n_features,
+              double sigma, const float* alpha, int32_t mode, void* out, void* stream);
+
+/* Number of stack parts qmlr_sorf_grad splits N_F/d stacks into: ceil(N_F/d / 128). */
+int32_t qmlr_sorf_parts(int32_t n_features, int32_t d);
+
+/*
+ * Energy and its gradient with respect to the projected representations
+ * (the SORF backward pass: transposed Hadamard chain applied to
+ * -sqrt(2/N_F) alpha * sin(u)):
+ *   energies double [n_mol]                 E_m = sum_{I in m} alpha^T z(x_I)
+ *   gx       float [n_part][n_atoms][d]     dE/dx_I contributed by the stacks of part p
+ * n_part = qmlr_sorf_parts(n_features, d); qmlr_project_t sums the parts.
+ */
+int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
+                   int32_t n_atoms, const uint32_t* sign_bits, int32_t T, const float* b,
+                   int32_t n_features, double sigma, const float* alpha, double* energies,
+                   float* gx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMLR_H */

@@ -1,0 +1,569 @@
+// FCHL19 representation: forward and vector-Jacobian product (sm_103a).
+//
+// Representation section of the paper: two-body log-normal radial terms with
+// cutoff and r^-N2 decay; three-body terms = ATM weight x Gaussian radial in
+// (r_ij + r_ik)/2 x Fourier angular [cos, sin] x three cutoffs.
+//
+// Design (GB300): one warp per centre atom. The warp stages its molecule's
+// coordinates in shared memory, builds the neighbour list with a ballot /
+// popc compaction (no HBM neighbour list), and accumulates the 780-wide row
+// in a per-warp shared-memory accumulator in a fixed order (deterministic,
+// no atomics). Two-body: lanes over radial bins, loop over neighbours.
+// Three-body forward: pair geometry computed lane-parallel over neighbour
+// pairs, staged in a 32-entry shared buffer, then lanes over radial bins.
+// VJP: lanes over neighbour pairs, each lane loops over its pair's radial
+// bins (no per-pair warp reductions); forces are summed per molecule by one
+// CTA, per-warp buffers reduced in a fixed order.
+#include "common.cuh"
+
+namespace qmlr {
+
+constexpr int kMaxGrid = 64;     // n2, n3 <= 64
+constexpr int kWarpsFwd = 4;
+constexpr int kWarpsVjp = 4;
+
+struct Fchl19Consts {
+  int n_el, n2, n3, rep_dim, base3;
+  float rcut, rcut2, pi_over_rcut;
+  float eta2, eta3, N2, N3;
+  float w3;          // c3 * sqrt(eta3/pi)
+  float ang2;        // 2 exp(-zeta^2/2): G^cos = ang2 cos(th), G^sin = ang2 sin(th) for n = 1
+  float inv_sqrt_2pi;
+  float rs2_log[kMaxGrid], rs2_inv[kMaxGrid], rs3[kMaxGrid];
+};
+
+static Fchl19Consts make_consts(const qmlr_fchl19_params& p) {
+  Fchl19Consts c{};
+  c.n_el = p.n_el;
+  c.n2 = p.n2;
+  c.n3 = p.n3;
+  c.rep_dim = rep_dim_of(p);
+  c.base3 = p.n_el * p.n2;
+  c.rcut = (float)p.rcut;
+  c.rcut2 = (float)(p.rcut * p.rcut);
+  c.pi_over_rcut = (float)(M_PI / p.rcut);
+  c.eta2 = (float)p.eta2;
+  c.eta3 = (float)p.eta3;
+  c.N2 = (float)p.N2;
+  c.N3 = (float)p.N3;
+  c.w3 = (float)(p.c3 * sqrt(p.eta3 / M_PI));
+  c.ang2 = (float)(2.0 * exp(-p.zeta * p.zeta / 2.0));
+  c.inv_sqrt_2pi = (float)(1.0 / sqrt(2.0 * M_PI));
+  for (int k = 0; k < p.n2; ++k) {
+    double R = p.rcut * (k + 1) / p.n2;
+    c.rs2_log[k] = (float)log(R);
+    c.rs2_inv[k] = (float)(1.0 / R);
+  }
+  for (int k = 0; k < p.n3; ++k) c.rs3[k] = (float)(p.rcut * (k + 1) / p.n3);
+  return c;
+}
+
+int validate_params(const qmlr_fchl19_params* p) {
+  QMLR_REQUIRE(p != nullptr, "params is NULL");
+  QMLR_REQUIRE(p->n_el >= 1 && p->n_el <= 8, "n_el must be in 1..8 (got %d)", p->n_el);
+  QMLR_REQUIRE(p->n2 >= 1 && p->n2 <= kMaxGrid, "n2 must be in 1..64 (got %d)", p->n2);
+  QMLR_REQUIRE(p->n3 >= 1 && p->n3 <= kMaxGrid, "n3 must be in 1..64 (got %d)", p->n3);
+  QMLR_REQUIRE(p->nfourier == 1, "only nfourier = 1 is supported (got %d)", p->nfourier);
+  QMLR_REQUIRE(p->rcut > 0 && p->eta2 > 0 && p->eta3 > 0, "rcut, eta2, eta3 must be > 0");
+  return QMLR_OK;
+}
+
+__device__ __forceinline__ float cutoff_f(float r, const Fchl19Consts& c) {
+  return r < c.rcut ? 0.5f * (cospif(r / c.rcut) + 1.0f) : 0.0f;
+}
+__device__ __forceinline__ float cutoff_df(float r, const Fchl19Consts& c) {
+  return r < c.rcut ? -0.5f * c.pi_over_rcut * sinpif(r / c.rcut) : 0.0f;
+}
+
+__device__ __forceinline__ int pair_index(int a, int b, int n_el) {
+  int lo = min(a, b), hi = max(a, b);
+  return lo * n_el - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+__device__ __forceinline__ int find_molecule(const int32_t* mol_ptr, int n_mol, int atom) {
+  int lo = 0, hi = n_mol;  // mol_ptr[lo] <= atom < mol_ptr[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(mol_ptr + mid) <= atom) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Decode a flat index q over the pairs (j < k) of n items.
+__device__ __forceinline__ void decode_pair(int q, int n, int& j, int& k) {
+  float t = (float)(2 * n - 1);
+  int jj = (int)floorf((t - sqrtf(t * t - 8.0f * (float)q)) * 0.5f);
+  jj = max(0, min(jj, n - 2));
+  // fix rounding: first index of row jj is jj*(2n-jj-1)/2
+  while (jj > 0 && jj * (2 * n - jj - 1) / 2 > q) --jj;
+  while (jj < n - 2 && (jj + 1) * (2 * n - jj - 2) / 2 <= q) ++jj;
+  j = jj;
+  k = q - jj * (2 * n - jj - 1) / 2 + jj + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory staging and neighbour lists.
+
+// Positions of the molecule's atoms: pos[j] = (x, y, z, element bits).
+__device__ void stage_molecule(const float* __restrict__ coords, const int32_t* __restrict__ elem,
+                               int a0, int M, int n_el, float4* pos, int tid, int nthreads,
+                               int* err) {
+  for (int j = tid; j < M; j += nthreads) {
+    int e = __ldg(elem + a0 + j);
+    if (e < 0 || e >= n_el) {
+      record_device_error(err, DEV_BAD_ELEMENT);
+      e = 0;
+    }
+    pos[j] = make_float4(__ldg(coords + 3 * (a0 + j)), __ldg(coords + 3 * (a0 + j) + 1),
+                         __ldg(coords + 3 * (a0 + j) + 2), __int_as_float(e));
+  }
+}
+
+// Neighbour list of local atom il (ballot/popc compaction, ascending j).
+//   nb_u[s]  = unit vector i->j and r_ij; nb_2b[s] = (mu, 1/(2 s^2), two-body prefactor, f_cut)
+//   nb_el[s] = element of j; nb_idx[s] = local index j (nullable)
+// Returns the neighbour count (warp-uniform).
+__device__ int neighbour_list(const float4* pos, int M, int il, const Fchl19Consts& c,
+                              float4* nb_u, float4* nb_2b, int* nb_el, int* nb_idx, int lane) {
+  const float4 ri = pos[il];
+  int n = 0;
+  for (int base = 0; base < M; base += 32) {
+    const int j = base + lane;
+    bool ok = false;
+    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, wj = 0.f;
+    if (j < M && j != il) {
+      const float4 pj = pos[j];
+      dx = pj.x - ri.x;
+      dy = pj.y - ri.y;
+      dz = pj.z - ri.z;
+      wj = pj.w;
+      r2 = dx * dx + dy * dy + dz * dz;
+      ok = r2 < c.rcut2;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const int slot = n + __popc(mask & ((1u << lane) - 1u));
+      const float r = sqrtf(r2);
+      const float inv = 1.0f / r;
+      nb_u[slot] = make_float4(dx * inv, dy * inv, dz * inv, r);
+      nb_el[slot] = __float_as_int(wj);
+      if (nb_idx) nb_idx[slot] = j;
+      const float fc = cutoff_f(r, c);
+      const float q = 1.0f + c.eta2 * inv * inv;
+      const float s2 = logf(q);
+      const float s = sqrtf(s2);
+      nb_2b[slot] = make_float4(logf(r) - 0.5f * s2,                       // mu = ln(r / sqrt(q))
+                                0.5f / s2,                                  // 1 / (2 s^2)
+                                fc * expf(-c.N2 * logf(r)) * c.inv_sqrt_2pi / s,
+                                fc);
+    }
+    n += __popc(mask);
+  }
+  __syncwarp();
+  return n;
+}
+
+// Per-warp shared memory of the forward kernel (16-byte aligned pieces).
+struct FwdWarp {
+  float4* pos;    // [mxp]
+  float4* nb_u;   // [mxp]
+  float4* nb_2b;  // [mxp]
+  float4* pairs;  // [32] w*G^cos, w*G^sin, xbar, bin offset (bits)
+  float* acc;     // [rp]
+  int* nb_el;     // [mxp]
+};
+__host__ __device__ __forceinline__ size_t fwd_warp_bytes(int mxp, int rp) {
+  return (size_t)mxp * 52 + (size_t)rp * 4 + 512;
+}
+__device__ __forceinline__ FwdWarp carve_fwd(char* base, int mxp, int rp) {
+  FwdWarp s;
+  s.pos = reinterpret_cast<float4*>(base);
+  s.nb_u = s.pos + mxp;
+  s.nb_2b = s.nb_u + mxp;
+  s.pairs = s.nb_2b + mxp;
+  s.acc = reinterpret_cast<float*>(s.pairs + 32);
+  s.nb_el = reinterpret_cast<int*>(s.acc + rp);
+  return s;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsFwd)
+fchl19_forward_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
+                      const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx,
+                      int mxp, int rp, Fchl19Consts c, float* __restrict__ rep, int rep_ld,
+                      int* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int atom = blockIdx.x * kWarpsFwd + warp;
+  if (atom >= n_atoms) return;
+  FwdWarp s = carve_fwd(smem_raw + warp * fwd_warp_bytes(mxp, rp), mxp, rp);
+
+  const int m = find_molecule(mol_ptr, n_mol, atom);
+  const int a0 = __ldg(mol_ptr + m);
+  const int M = __ldg(mol_ptr + m + 1) - a0;
+  float* out = rep + (size_t)atom * rep_ld;
+  if (M > mx) {
+    if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+    for (int k = lane; k < rep_ld; k += 32) out[k] = 0.0f;
+    return;
+  }
+  for (int k = lane; k < rp; k += 32) s.acc[k] = 0.0f;
+  stage_molecule(coords, elem, a0, M, c.n_el, s.pos, lane, 32, err);
+  __syncwarp();
+  const int n = neighbour_list(s.pos, M, atom - a0, c, s.nb_u, s.nb_2b, s.nb_el, nullptr, lane);
+
+  // two-body: lanes over radial bins, neighbours in order
+  for (int jn = 0; jn < n; ++jn) {
+    const float4 t = s.nb_2b[jn];
+    float* dst = s.acc + s.nb_el[jn] * c.n2;
+    for (int k = lane; k < c.n2; k += 32) {
+      const float a = c.rs2_log[k] - t.x;
+      dst[k] += t.z * c.rs2_inv[k] * expf(-a * a * t.y);
+    }
+  }
+  __syncwarp();
+
+  // three-body: pair geometry lane-parallel over flat pairs (j < k), then lanes over bins
+  const int n_pairs = n * (n - 1) / 2;
+  for (int q0 = 0; q0 < n_pairs; q0 += 32) {
+    const int q = q0 + lane;
+    bool ok = false;
+    float wc = 0.f, ws = 0.f, xbar = 0.f;
+    int bin = 0;
+    if (q < n_pairs) {
+      int jn, kn;
+      decode_pair(q, n, jn, kn);
+      const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+      const float vx = uk.x * uk.w - uj.x * uj.w;
+      const float vy = uk.y * uk.w - uj.y * uj.w;
+      const float vz = uk.z * uk.w - uj.z * uj.w;
+      const float rjk2 = vx * vx + vy * vy + vz * vz;
+      if (rjk2 < c.rcut2) {
+        ok = true;
+        const float rjk = sqrtf(rjk2);
+        const float inv_rjk = 1.0f / rjk;
+        const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+        const float cx = uj.y * uk.z - uj.z * uk.y;
+        const float cy = uj.z * uk.x - uj.x * uk.z;
+        const float cz = uj.x * uk.y - uj.y * uk.x;
+        const float si = sqrtf(cx * cx + cy * cy + cz * cz);
+        const float cj = -(uj.x * vx + uj.y * vy + uj.z * vz) * inv_rjk;
+        const float ck = (uk.x * vx + uk.y * vy + uk.z * vz) * inv_rjk;
+        const float atm = (1.0f + 3.0f * ci * cj * ck) * expf(-c.N3 * logf(uj.w * uk.w * rjk));
+        const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * cutoff_f(rjk, c);
+        wc = w * c.ang2 * ci;
+        ws = w * c.ang2 * si;
+        xbar = 0.5f * (uj.w + uk.w);
+        bin = c.base3 + pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el) * c.n3 * 2;
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) s.pairs[__popc(mask & ((1u << lane) - 1u))] = make_float4(wc, ws, xbar, __int_as_float(bin));
+    __syncwarp();
+    const int cnt = __popc(mask);
+    for (int t = 0; t < cnt; ++t) {
+      const float4 pr = s.pairs[t];
+      float* dst = s.acc + __float_as_int(pr.w);
+      for (int k = lane; k < c.n3; k += 32) {
+        const float a = pr.z - c.rs3[k];
+        const float g = expf(-c.eta3 * a * a);
+        dst[2 * k] += g * pr.x;
+        dst[2 * k + 1] += g * pr.y;
+      }
+    }
+    __syncwarp();
+  }
+  for (int k = lane; k < rep_ld; k += 32) out[k] = k < c.rep_dim ? s.acc[k] : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// VJP: one CTA per molecule, warps over centre atoms.
+
+struct VjpWarp {
+  float4* nb_u;   // [mxp]
+  float4* nb_2b;  // [mxp]
+  float* g;       // [rp]   gradient row of the centre
+  float* facc;    // [3 mxp] gradient with respect to the molecule's positions
+  int* nb_el;     // [mxp]
+  int* nb_idx;    // [mxp]
+};
+__host__ __device__ __forceinline__ size_t vjp_warp_bytes(int mxp, int rp) {
+  return (size_t)mxp * (16 + 16 + 12 + 4 + 4) + (size_t)rp * 4;
+}
+__device__ __forceinline__ VjpWarp carve_vjp(char* base, int mxp, int rp) {
+  VjpWarp s;
+  s.nb_u = reinterpret_cast<float4*>(base);
+  s.nb_2b = s.nb_u + mxp;
+  s.g = reinterpret_cast<float*>(s.nb_2b + mxp);
+  s.facc = s.g + rp;
+  s.nb_el = reinterpret_cast<int*>(s.facc + 3 * mxp);
+  s.nb_idx = s.nb_el + mxp;
+  return s;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsVjp)
+fchl19_vjp_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
+                  const int32_t* __restrict__ mol_ptr, int n_mol, int mx, int mxp, int rp,
+                  Fchl19Consts c, const float* __restrict__ grad_rep, int rep_ld,
+                  float* __restrict__ grad_coords, int accumulate, int* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = blockIdx.x;
+  const int a0 = __ldg(mol_ptr + m);
+  const int M = __ldg(mol_ptr + m + 1) - a0;
+  if (M > mx) {
+    if (threadIdx.x == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+    return;
+  }
+  float4* pos = reinterpret_cast<float4*>(smem_raw);
+  VjpWarp s = carve_vjp(smem_raw + (size_t)mxp * 16 + warp * vjp_warp_bytes(mxp, rp), mxp, rp);
+  stage_molecule(coords, elem, a0, M, c.n_el, pos, threadIdx.x, blockDim.x, err);
+  for (int k = lane; k < 3 * mxp; k += 32) s.facc[k] = 0.0f;
+  __syncthreads();
+
+  for (int il = warp; il < M; il += kWarpsVjp) {
+    const float* grow = grad_rep + (size_t)(a0 + il) * rep_ld;
+    for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grow + k);
+    const int n = neighbour_list(pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
+
+    float gi_x = 0.f, gi_y = 0.f, gi_z = 0.f;   // gradient on the centre (per-lane partials)
+
+    // two-body: lanes over neighbours (distinct atoms per lane)
+    for (int jn = lane; jn < n; jn += 32) {
+      const float4 u = s.nb_u[jn];
+      const float r = u.w;
+      const float4 t = s.nb_2b[jn];   // mu, 1/(2s^2), fc r^-N2/(s sqrt(2pi)), fc
+      const float inv_r = 1.0f / r;
+      const float s2 = 0.5f / t.y;
+      const float sd = sqrtf(s2);
+      const float rr_eta = r * r + c.eta2;
+      const float ds = -c.eta2 / (sd * r * rr_eta);            // d sigma / dr
+      const float dmu = inv_r + c.eta2 / (r * rr_eta);          // d mu / dr
+      const float fc = t.w;
+      const float dfc = cutoff_df(r, c);
+      const float rN = expf(-c.N2 * logf(r));
+      const float P = fc * rN;
+      const float dP = rN * (dfc - c.N2 * fc * inv_r);
+      const float* gb = s.g + s.nb_el[jn] * c.n2;
+      float dEdr = 0.f;
+      for (int k = 0; k < c.n2; ++k) {
+        const float a = c.rs2_log[k] - t.x;
+        const float L = c.rs2_inv[k] * c.inv_sqrt_2pi / sd * expf(-a * a * t.y);
+        const float dlnL = -ds / sd + a * dmu / s2 + a * a * ds / (s2 * sd);
+        dEdr += gb[k] * L * (dP + P * dlnL);
+      }
+      const int jl = s.nb_idx[jn];
+      s.facc[3 * jl + 0] += dEdr * u.x;
+      s.facc[3 * jl + 1] += dEdr * u.y;
+      s.facc[3 * jl + 2] += dEdr * u.z;
+      gi_x -= dEdr * u.x;
+      gi_y -= dEdr * u.y;
+      gi_z -= dEdr * u.z;
+    }
+    __syncwarp();
+
+    // three-body: lanes over flat neighbour pairs, each lane loops over its radial bins
+    const int n_pairs = n * (n - 1) / 2;
+    for (int q0 = 0; q0 < n_pairs; q0 += 32) {
+      const int q = q0 + lane;
+      float gj0 = 0.f, gj1 = 0.f, gj2 = 0.f, gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
+      int jl = 0, kl = 0;
+      if (q < n_pairs) {
+        int jn, kn;
+        decode_pair(q, n, jn, kn);
+        jl = s.nb_idx[jn];
+        kl = s.nb_idx[kn];
+        const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+        const float a = uj.w, b = uk.w;
+        const float vx = uk.x * b - uj.x * a, vy = uk.y * b - uj.y * a, vz = uk.z * b - uj.z * a;
+        const float c2 = vx * vx + vy * vy + vz * vz;
+        if (c2 < c.rcut2) {
+          const float cc = sqrtf(c2);
+          const float inv_c = 1.0f / cc;
+          const float ux = vx * inv_c, uy = vy * inv_c, uz = vz * inv_c;   // unit j -> k
+          const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+          const float crx = uj.y * uk.z - uj.z * uk.y;
+          const float cry = uj.z * uk.x - uj.x * uk.z;
+          const float crz = uj.x * uk.y - uj.y * uk.x;
+          const float si = sqrtf(crx * crx + cry * cry + crz * crz);
+          const float cj = -(uj.x * ux + uj.y * uy + uj.z * uz);
+          const float ck = (uk.x * ux + uk.y * uy + uk.z * uz);
+          // cosines as functions of the sides a = r_ij, b = r_ik, cc = r_jk
+          const float dci_da = (a - b * ci) / (a * b), dci_db = (b - a * ci) / (a * b), dci_dc = -cc / (a * b);
+          const float dcj_da = (a - cc * cj) / (a * cc), dcj_dc = (cc - a * cj) / (a * cc), dcj_db = -b / (a * cc);
+          const float dck_db = (b - cc * ck) / (b * cc), dck_dc = (cc - b * ck) / (b * cc), dck_da = -a / (b * cc);
+          const float Q = 1.0f + 3.0f * ci * cj * ck;
+          const float dQ_da = 3.0f * (dci_da * cj * ck + ci * dcj_da * ck + ci * cj * dck_da);
+          const float dQ_db = 3.0f * (dci_db * cj * ck + ci * dcj_db * ck + ci * cj * dck_db);
+          const float dQ_dc = 3.0f * (dci_dc * cj * ck + ci * dcj_dc * ck + ci * cj * dck_dc);
+          const float R3 = expf(-c.N3 * logf(a * b * cc));
+          const float fa = s.nb_2b[jn].w, fb = s.nb_2b[kn].w, fcc = cutoff_f(cc, c);
+          const float dfa = cutoff_df(a, c), dfb = cutoff_df(b, c), dfcc = cutoff_df(cc, c);
+          const float F3 = fa * fb * fcc;
+          const float W = c.w3 * Q * R3 * F3;
+          const float dW_da = c.w3 * R3 * (dQ_da * F3 - Q * F3 * c.N3 / a + Q * dfa * fb * fcc);
+          const float dW_db = c.w3 * R3 * (dQ_db * F3 - Q * F3 * c.N3 / b + Q * fa * dfb * fcc);
+          const float dW_dc = c.w3 * R3 * (dQ_dc * F3 - Q * F3 * c.N3 / cc + Q * fa * fb * dfcc);
+          const float Ac = c.ang2 * ci, As = c.ang2 * si;
+          const float dsi_dci = si > 1e-7f ? -ci / si : 0.0f;   // collinear guard
+          const float xbar = 0.5f * (a + b);
+          const float* gb = s.g + c.base3 + pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el) * c.n3 * 2;
+          float Sc = 0.f, Ss = 0.f, Sc1 = 0.f, Ss1 = 0.f;
+          for (int k = 0; k < c.n3; ++k) {
+            const float d = xbar - c.rs3[k];
+            const float rad = expf(-c.eta3 * d * d);
+            const float drad = -2.0f * c.eta3 * d * rad;
+            const float g0 = gb[2 * k], g1 = gb[2 * k + 1];
+            Sc += g0 * rad;
+            Ss += g1 * rad;
+            Sc1 += g0 * drad;
+            Ss1 += g1 * drad;
+          }
+          const float AS = Ac * Sc + As * Ss;
+          const float AS1 = Ac * Sc1 + As * Ss1;
+          const float dA = c.ang2 * (Sc + dsi_dci * Ss);   // d(A.S)/d cos(th_i) at fixed S
+          const float dE_da = dW_da * AS + W * dA * dci_da + W * AS1 * 0.5f;
+          const float dE_db = dW_db * AS + W * dA * dci_db + W * AS1 * 0.5f;
+          const float dE_dc = dW_dc * AS + W * dA * dci_dc;
+          // a = |r_j - r_i|, b = |r_k - r_i|, cc = |r_k - r_j|
+          gi_x -= dE_da * uj.x + dE_db * uk.x;
+          gi_y -= dE_da * uj.y + dE_db * uk.y;
+          gi_z -= dE_da * uj.z + dE_db * uk.z;
+          gj0 = dE_da * uj.x - dE_dc * ux;
+          gj1 = dE_da * uj.y - dE_dc * uy;
+          gj2 = dE_da * uj.z - dE_dc * uz;
+          gk0 = dE_db * uk.x + dE_dc * ux;
+          gk1 = dE_db * uk.y + dE_dc * uy;
+          gk2 = dE_db * uk.z + dE_dc * uz;
+        }
+      }
+      // scatter the j- and k-side gradients in a fixed lane order
+      const int cnt = min(32, n_pairs - q0);
+      for (int t = 0; t < cnt; ++t) {
+        const int jt = __shfl_sync(0xffffffffu, jl, t);
+        const int kt = __shfl_sync(0xffffffffu, kl, t);
+        const float v0 = __shfl_sync(0xffffffffu, gj0, t);
+        const float v1 = __shfl_sync(0xffffffffu, gj1, t);
+        const float v2 = __shfl_sync(0xffffffffu, gj2, t);
+        const float v3 = __shfl_sync(0xffffffffu, gk0, t);
+        const float v4 = __shfl_sync(0xffffffffu, gk1, t);
+        const float v5 = __shfl_sync(0xffffffffu, gk2, t);
+        if (lane == 0) {
+          s.facc[3 * jt + 0] += v0;
+          s.facc[3 * jt + 1] += v1;
+          s.facc[3 * jt + 2] += v2;
+          s.facc[3 * kt + 0] += v3;
+          s.facc[3 * kt + 1] += v4;
+          s.facc[3 * kt + 2] += v5;
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gi_x += __shfl_xor_sync(0xffffffffu, gi_x, o);
+      gi_y += __shfl_xor_sync(0xffffffffu, gi_y, o);
+      gi_z += __shfl_xor_sync(0xffffffffu, gi_z, o);
+    }
+    if (lane == 0) {
+      s.facc[3 * il + 0] += gi_x;
+      s.facc[3 * il + 1] += gi_y;
+      s.facc[3 * il + 2] += gi_z;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // fixed-order reduction over the warps' buffers
+  for (int k = threadIdx.x; k < 3 * M; k += blockDim.x) {
+    float sum = 0.f;
+    for (int w = 0; w < kWarpsVjp; ++w)
+      sum += carve_vjp(smem_raw + (size_t)mxp * 16 + w * vjp_warp_bytes(mxp, rp), mxp, rp).facc[k];
+    float* dst = grad_coords + 3 * (size_t)a0 + k;
+    *dst = accumulate ? *dst + sum : sum;
+  }
+}
+
+static int rep_pad_of(int rep_dim) { return (rep_dim + 3) & ~3; }
+
+static int check_geometry(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                          int n_mol, int n_atoms, int max_mol_atoms) {
+  QMLR_REQUIRE(n_mol >= 0 && n_atoms >= 0, "n_mol and n_atoms must be >= 0");
+  QMLR_REQUIRE(max_mol_atoms >= 1 && max_mol_atoms <= 256,
+               "max_mol_atoms must be in 1..256 (got %d)", max_mol_atoms);
+  QMLR_REQUIRE(n_atoms == 0 || (coords && elem), "coords/elem are NULL");
+  QMLR_REQUIRE(n_mol == 0 || mol_ptr, "mol_ptr is NULL");
+  return QMLR_OK;
+}
+
+}  // namespace qmlr
+
+using namespace qmlr;
+
+extern "C" int qmlr_fchl19_rep_dim(const qmlr_fchl19_params* p, int32_t* rep_dim) {
+  int rc = validate_params(p);
+  if (rc) return rc;
+  QMLR_REQUIRE(rep_dim, "rep_dim is NULL");
+  *rep_dim = rep_dim_of(*p);
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_fchl19(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                           int32_t n_mol, int32_t n_atoms, int32_t max_mol_atoms,
+                           const qmlr_fchl19_params* p, float* rep, int32_t rep_ld, void* stream) {
+  int rc = validate_params(p);
+  if (rc) return rc;
+  rc = check_geometry(coords, elem, mol_ptr, n_mol, n_atoms, max_mol_atoms);
+  if (rc) return rc;
+  const int rd = rep_dim_of(*p);
+  QMLR_REQUIRE(rep_ld >= rd, "rep_ld (%d) < rep_dim (%d)", rep_ld, rd);
+  QMLR_REQUIRE(n_atoms == 0 || rep, "rep is NULL");
+  if (n_atoms == 0) return QMLR_OK;
+  QMLR_REQUIRE(n_mol >= 1, "n_atoms > 0 but n_mol == 0");
+  const Fchl19Consts c = make_consts(*p);
+  const int rp = rep_pad_of(rd);
+  const int mx = max_mol_atoms;
+  const int mxp = (mx + 3) & ~3;
+  const size_t smem = kWarpsFwd * fwd_warp_bytes(mxp, rp);
+  QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
+  static bool attr_set = false;
+  if (!attr_set) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_forward_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set = true;
+  }
+  const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
+  fchl19_forward_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
+      coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, rep, rep_ld, device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_fchl19_vjp(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                               int32_t n_mol, int32_t n_atoms, int32_t max_mol_atoms,
+                               const qmlr_fchl19_params* p, const float* grad_rep, int32_t rep_ld,
+                               float* grad_coords, int32_t accumulate, void* stream) {
+  int rc = validate_params(p);
+  if (rc) return rc;
+  rc = check_geometry(coords, elem, mol_ptr, n_mol, n_atoms, max_mol_atoms);
+  if (rc) return rc;
+  const int rd = rep_dim_of(*p);
+  QMLR_REQUIRE(rep_ld >= rd, "rep_ld (%d) < rep_dim (%d)", rep_ld, rd);
+  QMLR_REQUIRE(n_atoms == 0 || (grad_rep && grad_coords), "grad_rep/grad_coords are NULL");
+  if (n_atoms == 0 || n_mol == 0) return QMLR_OK;
+  const Fchl19Consts c = make_consts(*p);
+  const int rp = rep_pad_of(rd);
+  const int mx = max_mol_atoms;
+  const int mxp = (mx + 3) & ~3;
+  const size_t smem = (size_t)mxp * 16 + kWarpsVjp * vjp_warp_bytes(mxp, rp);
+  QMLR_REQUIRE(smem <= 200 * 1024, "shared memory request too large");
+  static bool attr_set = false;
+  if (!attr_set) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_vjp_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  fchl19_vjp_kernel<<<n_mol, 32 * kWarpsVjp, smem, as_stream(stream)>>>(
+      coords, elem, mol_ptr, n_mol, mx, mxp, rp, c, grad_rep, rep_ld, grad_coords, accumulate,
+      device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}

@@ -1,0 +1,275 @@
+// Per-element projection rho_proj = rho^T U_e and its transpose (sm_103a).
+//
+// SORF section of the paper: each element has its own basis U_e (leading
+// left singular vectors of that element's representations); the projection
+// is one matrix product per element. Atoms are first grouped by element with
+// a stable device counting sort (count / scan / scatter), then a grouped
+// FP32 GEMM runs over 64-atom tiles that each hold one element, so that U_e
+// is streamed once per tile. Arithmetic and accumulation are FP32.
+#include "common.cuh"
+
+namespace qmlr {
+
+constexpr int kGroupChunk = 1024;  // atoms per CTA of the counting sort
+constexpr int kMaxEl = 8;
+
+__global__ void group_count_kernel(const int32_t* __restrict__ elem, int n_atoms, int n_el,
+                                   int* __restrict__ counts, int* err) {
+  __shared__ int c[kMaxEl];
+  if (threadIdx.x < kMaxEl) c[threadIdx.x] = 0;
+  __syncthreads();
+  const int i = blockIdx.x * kGroupChunk + threadIdx.x;
+  if (i < n_atoms) {
+    int e = __ldg(elem + i);
+    if (e < 0 || e >= n_el) {
+      record_device_error(err, DEV_BAD_ELEMENT);
+      e = 0;
+    }
+    atomicAdd(&c[e], 1);  // integer counts: order-independent
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxEl) counts[blockIdx.x * kMaxEl + threadIdx.x] = c[threadIdx.x];
+}
+
+// Exclusive scan over (element, chunk) in element-major order. One CTA.
+__global__ void group_scan_kernel(const int* __restrict__ counts, int n_chunks, int n_el,
+                                  int* __restrict__ offsets, int32_t* __restrict__ elem_offsets) {
+  __shared__ int tot[kMaxEl];
+  const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (e < n_el) {
+    // per element: warp-wide chunked scan over the chunks
+    int run = 0;
+    for (int base = 0; base < n_chunks; base += 32) {
+      const int k = base + lane;
+      int v = k < n_chunks ? counts[k * kMaxEl + e] : 0;
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (k < n_chunks) offsets[k * kMaxEl + e] = run + incl - v;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) tot[e] = run;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < n_el; ++k) {
+      elem_offsets[k] = acc;
+      acc += tot[k];
+    }
+    elem_offsets[n_el] = acc;
+  }
+  __syncthreads();
+  // shift per-chunk offsets by the element start
+  for (int idx = threadIdx.x; idx < n_chunks * n_el; idx += blockDim.x) {
+    const int k = idx / n_el, ee = idx % n_el;
+    offsets[k * kMaxEl + ee] += elem_offsets[ee];
+  }
+}
+
+__global__ void group_scatter_kernel(const int32_t* __restrict__ elem, int n_atoms, int n_el,
+                                     const int* __restrict__ offsets, int32_t* __restrict__ perm) {
+  __shared__ int wtot[kGroupChunk / 32][kMaxEl];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kGroupChunk + threadIdx.x;
+  int e = -1;
+  if (i < n_atoms) {
+    e = __ldg(elem + i);
+    if (e < 0 || e >= n_el) e = 0;
+  }
+  int rank = 0;
+  for (int k = 0; k < n_el; ++k) {
+    const unsigned mask = __ballot_sync(0xffffffffu, e == k);
+    if (e == k) rank = __popc(mask & ((1u << lane) - 1u));
+    if (lane == 0) wtot[warp][k] = __popc(mask);
+  }
+  __syncthreads();
+  if (e >= 0) {
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wtot[w][e];
+    perm[offsets[blockIdx.x * kMaxEl + e] + before + rank] = i;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grouped GEMM: for each element e, rows perm[off[e] .. off[e+1]) :
+//   C[row][n] = sum_k A_sum[row][k] * B_e[k][n]
+// A_sum = sum over n_part slices of A (slice stride a_part_stride).
+// B_e[k][n] = B[e*b_elem_stride + k*ldb + n]          (B_T = false)
+//           = B[e*b_elem_stride + n*ldb + k]          (B_T = true)
+constexpr int TM = 64, TN = 128, TK = 16;
+
+template <bool B_T>
+__global__ void __launch_bounds__(256)
+grouped_gemm_kernel(const float* __restrict__ A, int lda, int K, int n_part, long a_part_stride,
+                    const float* __restrict__ B, int ldb, long b_elem_stride, int N,
+                    const int32_t* __restrict__ perm, const int32_t* __restrict__ elem_offsets,
+                    int n_el, float* __restrict__ C, int ldc, int zero_pad_to) {
+  __shared__ __align__(16) float As[TK][TM + 4];
+  __shared__ __align__(16) float Bs[TK][TN + 4];
+  __shared__ int rows[TM];
+
+  // map blockIdx.x to (element, tile)
+  int e = -1, tile = blockIdx.x, start = 0, count = 0;
+  for (int k = 0; k < n_el; ++k) {
+    const int s = elem_offsets[k], cnt = elem_offsets[k + 1] - s;
+    const int nt = (cnt + TM - 1) / TM;
+    if (tile < nt) {
+      e = k;
+      start = s + tile * TM;
+      count = min(TM, cnt - tile * TM);
+      break;
+    }
+    tile -= nt;
+  }
+  if (e < 0) return;
+  const int n0 = blockIdx.y * TN;
+  const int tid = threadIdx.x;
+  if (tid < TM) rows[tid] = tid < count ? perm[start + tid] : -1;
+  __syncthreads();
+
+  const float* Be = B + (long)e * b_elem_stride;
+  const int tr = tid / 16, tc = tid % 16;   // 16 x 16 threads, 4 rows x 8 cols each
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    // A tile: TM x TK, thread loads 4 elements (row = tid/4, k = (tid%4)*4 .. +3)
+    {
+      const int r = tid / 4, kk = (tid % 4) * 4;
+      const int row = rows[r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float v = 0.f;
+        const int k = k0 + kk + q;
+        if (row >= 0 && k < K) {
+          const float* ap = A + (long)row * lda + k;
+          for (int p = 0; p < n_part; ++p) v += __ldg(ap + p * a_part_stride);
+        }
+        As[kk + q][r] = v;
+      }
+    }
+    // B tile: TK x TN
+    if (!B_T) {
+      // thread loads 8 elements: k = tid/16, n = (tid%16)*8
+      const int k = k0 + tid / 16, nb = (tid % 16) * 8;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int n = n0 + nb + q;
+        Bs[tid / 16][nb + q] = (k < K && n < N) ? __ldg(Be + (long)k * ldb + n) : 0.f;
+      }
+    } else {
+      // k fastest: thread loads 8 elements: n = tid/2, k = (tid%2)*8
+      const int nl = tid / 2, kb = (tid % 2) * 8;
+      const int n = n0 + nl;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + kb + q;
+        Bs[kb + q][nl] = (k < K && n < N) ? __ldg(Be + (long)n * ldb + k) : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      float a[4], b[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tr * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = Bs[k][tc * 8 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = tr * 4 + i;
+    if (r >= count) continue;
+    const int row = rows[r];
+    float* cp = C + (long)row * ldc;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + tc * 8 + j;
+      if (n < N) cp[n] = acc[i][j];
+      else if (n < zero_pad_to) cp[n] = 0.f;
+    }
+  }
+}
+
+}  // namespace qmlr
+
+using namespace qmlr;
+
+extern "C" int64_t qmlr_group_workspace_bytes(int32_t n_atoms) {
+  const int64_t chunks = (n_atoms + kGroupChunk - 1) / kGroupChunk;
+  return 2 * chunks * kMaxEl * (int64_t)sizeof(int) + 256;
+}
+
+extern "C" int qmlr_group_by_element(const int32_t* elem, int32_t n_atoms, int32_t n_el,
+                                     int32_t* perm, int32_t* elem_offsets, void* work,
+                                     int64_t work_bytes, void* stream) {
+  QMLR_REQUIRE(n_el >= 1 && n_el <= kMaxEl, "n_el must be in 1..8 (got %d)", n_el);
+  QMLR_REQUIRE(n_atoms >= 0, "n_atoms must be >= 0");
+  QMLR_REQUIRE(elem_offsets, "elem_offsets is NULL");
+  QMLR_REQUIRE(n_atoms == 0 || (elem && perm), "elem/perm are NULL");
+  QMLR_REQUIRE(work && work_bytes >= qmlr_group_workspace_bytes(n_atoms),
+               "workspace too small (%lld < %lld bytes)", (long long)work_bytes,
+               (long long)qmlr_group_workspace_bytes(n_atoms));
+  cudaStream_t s = as_stream(stream);
+  const int chunks = (n_atoms + kGroupChunk - 1) / kGroupChunk;
+  int* counts = static_cast<int*>(work);
+  int* offsets = counts + (size_t)chunks * kMaxEl;
+  if (chunks > 0) {
+    group_count_kernel<<<chunks, kGroupChunk, 0, s>>>(elem, n_atoms, n_el, counts, device_error_ptr());
+    QMLR_LAUNCH_CHECK();
+  }
+  group_scan_kernel<<<1, 256, 0, s>>>(counts, chunks, n_el, offsets, elem_offsets);
+  QMLR_LAUNCH_CHECK();
+  if (chunks > 0) {
+    group_scatter_kernel<<<chunks, kGroupChunk, 0, s>>>(elem, n_atoms, n_el, offsets, perm);
+    QMLR_LAUNCH_CHECK();
+  }
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_project(const float* rep, int32_t rep_ld, int32_t rep_dim, const int32_t* perm,
+                            const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el,
+                            const float* U, int32_t d, float* x, void* stream) {
+  QMLR_REQUIRE(n_el >= 1 && n_el <= kMaxEl, "n_el must be in 1..8");
+  QMLR_REQUIRE(is_pow2(d) && d >= 16 && d <= 512, "d must be a power of two in 16..512 (got %d)", d);
+  QMLR_REQUIRE(rep_dim >= 1 && rep_ld >= rep_dim, "need 1 <= rep_dim <= rep_ld");
+  QMLR_REQUIRE(n_atoms >= 0, "n_atoms must be >= 0");
+  if (n_atoms == 0) return QMLR_OK;
+  QMLR_REQUIRE(rep && perm && elem_offsets && U && x, "NULL pointer argument");
+  dim3 grid((n_atoms + TM - 1) / TM + n_el, (d + TN - 1) / TN);
+  grouped_gemm_kernel<false><<<grid, 256, 0, as_stream(stream)>>>(
+      rep, rep_ld, rep_dim, 1, 0, U, d, (long)rep_dim * d, d, perm, elem_offsets, n_el, x, d, d);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* perm,
+                              const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el,
+                              const float* U, int32_t d, int32_t rep_dim, float* grad_rep,
+                              int32_t rep_ld, void* stream) {
+  QMLR_REQUIRE(n_el >= 1 && n_el <= kMaxEl, "n_el must be in 1..8");
+  QMLR_REQUIRE(is_pow2(d) && d >= 16 && d <= 512, "d must be a power of two in 16..512 (got %d)", d);
+  QMLR_REQUIRE(rep_dim >= 1 && rep_ld >= rep_dim, "need 1 <= rep_dim <= rep_ld");
+  QMLR_REQUIRE(n_part >= 1, "n_part must be >= 1");
+  if (n_atoms == 0) return QMLR_OK;
+  QMLR_REQUIRE(gx && perm && elem_offsets && U && grad_rep, "NULL pointer argument");
+  dim3 grid((n_atoms + TM - 1) / TM + n_el, (rep_ld + TN - 1) / TN);
+  grouped_gemm_kernel<true><<<grid, 256, 0, as_stream(stream)>>>(
+      gx, d, d, n_part, (long)n_atoms * d, U, d, (long)rep_dim * d, rep_dim, perm, elem_offsets,
+      n_el, grad_rep, rep_ld, rep_ld);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}

@@ -1,0 +1,536 @@
+// FP64 solve of the regularised normal equations (sm_103a).
+//
+// RFF section of the paper: (Z^T Z + lambda I) alpha = Z^T y. The paper
+// factorises with LU; the matrix is symmetric positive definite, so this
+// library uses a blocked right-looking Cholesky factorisation in FP64
+// (64 x 64 blocks: diagonal factor, panel triangular solve, trailing
+// symmetric update), then refines alpha against the exact operator
+// A v = Z^T (Z v) + lambda v evaluated in FP64 from the stored FP32 Z, with
+// the Cholesky factor as preconditioner (preconditioned conjugate gradients,
+// or classical refinement). This keeps the low-precision Gram an
+// approximation used only for the factor, while the residual is that of the
+// exact FP64 normal equations.
+#include "common.cuh"
+
+namespace qmlr {
+
+constexpr int NB = 64;
+
+// A = G + (lambda + shift) I in FP64, lower triangle (G symmetric fp32 [n][n]).
+__global__ void assemble_kernel(const float* __restrict__ G, int n, double diag,
+                                double* __restrict__ L, long ldl) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  double v = (double)G[idx];
+  if (i == j) v += diag;
+  L[(long)i * ldl + j] = (j <= i) ? v : 0.0;
+}
+
+// Unblocked Cholesky of the nb x nb diagonal block at (k0, k0), in shared memory.
+__global__ void __launch_bounds__(256)
+potrf_diag_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, int* info) {
+  __shared__ double a[NB][NB + 1];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    a[i][j] = (j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      double d = a[j][j];
+      if (!(d > 0.0)) {
+        record_device_error(err, DEV_NOT_SPD);
+        if (info && *info == 0) *info = k0 + j + 1;
+        d = 1e-300;
+      }
+      a[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = a[j][j];
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) a[i][j] /= piv;
+    __syncthreads();
+    for (int idx = tid; idx < (nb - j - 1) * (nb - j - 1); idx += blockDim.x) {
+      const int i = j + 1 + idx / (nb - j - 1), l = j + 1 + idx % (nb - j - 1);
+      if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    if (j <= i) L[(long)(k0 + i) * ldl + k0 + j] = a[i][j];
+  }
+}
+
+// Panel: rows r in [k0+nb, n): L[r][k0:k0+nb] = A[r][k0:k0+nb] * L_kk^{-T}. One thread per row.
+__global__ void __launch_bounds__(64)
+trsm_panel_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
+  __shared__ double lkk[NB][NB + 1];
+  __shared__ double x[NB][NB + 1];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    lkk[i][j] = (j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : 0.0;
+  }
+  const int r0 = k0 + nb + blockIdx.x * 64;
+  for (int idx = tid; idx < 64 * nb; idx += blockDim.x) {
+    const int rr = idx / nb, j = idx % nb;
+    const int r = r0 + rr;
+    x[rr][j] = (r < n) ? L[(long)r * ldl + k0 + j] : 0.0;
+  }
+  __syncthreads();
+  const int r = r0 + tid;
+  if (r < n) {
+    for (int j = 0; j < nb; ++j) {
+      double v = x[tid][j];
+      for (int l = 0; l < j; ++l) v -= x[tid][l] * lkk[j][l];
+      x[tid][j] = v / lkk[j][j];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < 64 * nb; idx += blockDim.x) {
+    const int rr = idx / nb, j = idx % nb;
+    const int rw = r0 + rr;
+    if (rw < n) L[(long)rw * ldl + k0 + j] = x[rr][j];
+  }
+}
+
+// Trailing update of the lower block tiles: A[I][J] -= L[I][k] L[J][k]^T, I >= J > k.
+__global__ void __launch_bounds__(256)
+syrk_update_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
+  __shared__ double li[NB][NB + 1];
+  __shared__ double lj[NB][NB + 1];
+  const int t0 = (k0 + nb) / NB;          // first trailing block
+  const int T = (n + NB - 1) / NB - t0;   // trailing blocks
+  int t = blockIdx.x, bi = 0;
+  while (t > bi) {                        // lower-triangular (bi >= bj) enumeration
+    t -= bi + 1;
+    ++bi;
+  }
+  const int bj = t;
+  if (bi >= T) return;
+  const int i0 = (t0 + bi) * NB, j0 = (t0 + bj) * NB;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * nb; idx += blockDim.x) {
+    const int rr = idx / nb, c = idx % nb;
+    li[rr][c] = (i0 + rr < n) ? L[(long)(i0 + rr) * ldl + k0 + c] : 0.0;
+    lj[rr][c] = (j0 + rr < n) ? L[(long)(j0 + rr) * ldl + k0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int tr = tid / 16, tc = tid % 16;   // 4 x 4 outputs each
+  double acc[4][4] = {};
+  for (int c = 0; c < nb; ++c) {
+    double a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = li[tr + 16 * u][c];
+      b[u] = lj[tc + 16 * u][c];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tr + 16 * u;
+    if (i >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + tc + 16 * v;
+      if (j >= n || j > i) continue;
+      L[(long)i * ldl + j] -= acc[u][v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// triangular solves with the factor (lower L; forward L y = b, backward L^T x = y)
+
+// Solve the nb-block at k0 in place: v[k0:k0+nb] = L_kk^{-1} v (forward) or L_kk^{-T} v (backward).
+__global__ void tri_block_kernel(const double* __restrict__ L, long ldl, int k0, int nb,
+                                 double* __restrict__ v, int transposed) {
+  __shared__ double lkk[NB][NB + 1];
+  __shared__ double x[NB];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    lkk[i][j] = (j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : 0.0;
+  }
+  if (tid < nb) x[tid] = v[k0 + tid];
+  __syncthreads();
+  if (tid == 0) {
+    if (!transposed) {
+      for (int j = 0; j < nb; ++j) {
+        double s = x[j];
+        for (int l = 0; l < j; ++l) s -= lkk[j][l] * x[l];
+        x[j] = s / lkk[j][j];
+      }
+    } else {
+      for (int j = nb - 1; j >= 0; --j) {
+        double s = x[j];
+        for (int l = j + 1; l < nb; ++l) s -= lkk[l][j] * x[l];
+        x[j] = s / lkk[j][j];
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < nb) v[k0 + tid] = x[tid];
+}
+
+// forward: v[r] -= sum_c L[r][k0+c] v[k0+c] for r >= k0+nb  (warp per row)
+// backward: v[c] -= sum_r L[k0+r][c] v[k0+r] for c < k0     (thread per column)
+__global__ void tri_update_kernel(const double* __restrict__ L, long ldl, int k0, int nb, int n,
+                                  double* __restrict__ v, int transposed) {
+  __shared__ double xb[NB];
+  if (threadIdx.x < nb) xb[threadIdx.x] = v[k0 + threadIdx.x];
+  __syncthreads();
+  if (!transposed) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int r = k0 + nb + warp;
+    if (r >= n) return;
+    double s = 0.0;
+    for (int c = lane; c < nb; c += 32) s = fma(L[(long)r * ldl + k0 + c], xb[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) v[r] -= s;
+  } else {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= k0) return;
+    double s = 0.0;
+    for (int r = 0; r < nb; ++r) s = fma(L[(long)(k0 + r) * ldl + c], xb[r], s);
+    v[c] -= s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// exact operator pieces: t = Z p (rows), q = Z^T t + lambda p (features), FP64 arithmetic
+
+__global__ void zmv_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz,
+                           const double* __restrict__ p, double* __restrict__ t) {
+  const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_rows) return;
+  const float* zr = Z + r * ldz;
+  double s = 0.0;
+  for (int f = lane; f < n_features; f += 32) s = fma((double)__ldg(zr + f), __ldg(p + f), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) t[r] = s;
+}
+
+constexpr int kZtRows = 2048;
+
+__global__ void ztmv_partial_kernel(const float* __restrict__ Z, long n_rows, int n_features,
+                                    long ldz, const double* __restrict__ t,
+                                    double* __restrict__ part) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const long r0 = (long)blockIdx.y * kZtRows;
+  const long r1 = min(n_rows, r0 + kZtRows);
+  if (f >= n_features) return;
+  double acc = 0.0;
+  for (long r = r0; r < r1; ++r) acc = fma((double)__ldg(Z + r * ldz + f), __ldg(t + r), acc);
+  part[(long)blockIdx.y * n_features + f] = acc;
+}
+
+__global__ void ztmv_finish_kernel(const double* __restrict__ part, int n_parts, int n,
+                                   const double* __restrict__ p, double lambda,
+                                   double* __restrict__ q) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  double acc = 0.0;
+  for (int k = 0; k < n_parts; ++k) acc += part[(long)k * n + f];
+  q[f] = acc + lambda * p[f];
+}
+
+// small vector kernels (single CTA reductions keep the order fixed)
+__global__ void dot_kernel(const double* __restrict__ a, const double* __restrict__ b, int n,
+                           double* __restrict__ out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(a[i], b[i], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void axpy_kernel(int n, const double* __restrict__ coef, double sign,
+                            const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += sign * (*coef) * x[i];
+}
+
+// p = z + (rz_new / rz_old) p
+__global__ void pupdate_kernel(int n, const double* __restrict__ rz_new,
+                               const double* __restrict__ rz_old, const double* __restrict__ z,
+                               double* __restrict__ p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = z[i] + (*rz_new / *rz_old) * p[i];
+}
+
+__global__ void ratio_kernel(const double* a, const double* b, double* out) { *out = *a / *b; }
+
+__global__ void sub_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] - b[i];
+}
+
+// ---------------------------------------------------------------------------
+struct SolveCtx {
+  int n;
+  long n_rows, ldz;
+  const float* Z;
+  double lambda;
+  double* L;
+  long ldl;
+  double* part;  // [parts][n]
+  int parts;
+  double* t;     // [n_rows]
+  cudaStream_t s;
+};
+
+static int cholesky(double* L, long ldl, int n, cudaStream_t s, int* info) {
+  int* err = device_error_ptr();
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int nb = std::min(NB, n - k0);
+    potrf_diag_kernel<<<1, 256, 0, s>>>(L, ldl, k0, nb, err, info);
+    QMLR_LAUNCH_CHECK();
+    const int rows = n - k0 - nb;
+    if (rows <= 0) break;
+    trsm_panel_kernel<<<(rows + 63) / 64, 64, 0, s>>>(L, ldl, k0, nb, n);
+    QMLR_LAUNCH_CHECK();
+    const int T = (rows + NB - 1) / NB;
+    syrk_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(L, ldl, k0, nb, n);
+    QMLR_LAUNCH_CHECK();
+  }
+  return QMLR_OK;
+}
+
+static int chol_apply(const double* L, long ldl, int n, double* v, cudaStream_t s) {
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int nb = std::min(NB, n - k0);
+    tri_block_kernel<<<1, 64, 0, s>>>(L, ldl, k0, nb, v, 0);
+    QMLR_LAUNCH_CHECK();
+    const int rows = n - k0 - nb;
+    if (rows > 0) {
+      tri_update_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(L, ldl, k0, nb, n, v, 0);
+      QMLR_LAUNCH_CHECK();
+    }
+  }
+  const int last = ((n - 1) / NB) * NB;
+  for (int k0 = last; k0 >= 0; k0 -= NB) {
+    const int nb = std::min(NB, n - k0);
+    tri_block_kernel<<<1, 64, 0, s>>>(L, ldl, k0, nb, v, 1);
+    QMLR_LAUNCH_CHECK();
+    if (k0 > 0) {
+      tri_update_kernel<<<(k0 + 255) / 256, 256, 0, s>>>(L, ldl, k0, nb, n, v, 1);
+      QMLR_LAUNCH_CHECK();
+    }
+  }
+  return QMLR_OK;
+}
+
+static int apply_exact(const SolveCtx& c, const double* p, double* q) {
+  const long threads = c.n_rows * 32;
+  if (c.n_rows > 0) {
+    zmv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, p, c.t);
+    QMLR_LAUNCH_CHECK();
+    dim3 grid((c.n + 255) / 256, c.parts);
+    ztmv_partial_kernel<<<grid, 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.t, c.part);
+    QMLR_LAUNCH_CHECK();
+  } else {
+    QMLR_CUDA_TRY(cudaMemsetAsync(c.part, 0, sizeof(double) * c.n, c.s));
+  }
+  ztmv_finish_kernel<<<(c.n + 255) / 256, 256, 0, c.s>>>(c.part, c.n_rows > 0 ? c.parts : 1, c.n,
+                                                        p, c.lambda, q);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+}  // namespace qmlr
+
+using namespace qmlr;
+
+extern "C" int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features) {
+  const int64_t n = n_features;
+  const int64_t parts = std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
+  return n * n * 8                 // factor L
+         + parts * n * 8           // partial sums of Z^T t
+         + std::max<int64_t>(n_rows, 1) * 8   // t = Z p
+         + 6 * n * 8               // c, r, z, p, q, tmp
+         + 8 * 8 + 4096;           // scalars + alignment
+}
+
+extern "C" int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_info, void* stream) {
+  QMLR_REQUIRE(L && n >= 1 && ldl >= n, "bad factor arguments");
+  cudaStream_t s = as_stream(stream);
+  int* info = nullptr;
+  QMLR_CUDA_TRY(cudaMallocAsync(&info, sizeof(int), s));
+  QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+  int rc = cholesky(L, ldl, n, s, info);
+  int h = 0;
+  if (rc == QMLR_OK) {
+    QMLR_CUDA_TRY(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QMLR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  cudaFreeAsync(info, s);
+  if (host_info) *host_info = h;
+  return rc;
+}
+
+extern "C" int qmlr_cholesky_solve(const double* L, int64_t ldl, int32_t n, double* v, void* stream) {
+  QMLR_REQUIRE(L && v && n >= 1 && ldl >= n, "bad arguments");
+  return chol_apply(L, ldl, n, v, as_stream(stream));
+}
+
+static void carve(char*& p, void** out, size_t bytes) {
+  *out = p;
+  p += (bytes + 255) & ~size_t(255);
+}
+
+extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, int32_t n_features,
+                               int64_t ldz, const double* y, double lambda, qmlr_solve_opts* opts,
+                               double* alpha, void* work, int64_t work_bytes, void* stream) {
+  QMLR_REQUIRE(G && alpha && opts, "NULL pointer argument");
+  QMLR_REQUIRE(n_features >= 1 && n_rows >= 0 && ldz >= n_features, "bad shapes");
+  QMLR_REQUIRE(n_rows == 0 || (Z && y), "Z/y are NULL");
+  QMLR_REQUIRE(lambda >= 0 && opts->shift >= 0, "lambda and shift must be >= 0");
+  QMLR_REQUIRE(opts->max_iter >= 0, "max_iter must be >= 0");
+  QMLR_REQUIRE(work && work_bytes >= qmlr_solve_workspace_bytes(n_rows, n_features) - 4096 + 2048,
+               "workspace too small");
+  cudaStream_t s = as_stream(stream);
+  const int n = n_features;
+  SolveCtx c;
+  c.n = n;
+  c.n_rows = n_rows;
+  c.ldz = ldz;
+  c.Z = Z;
+  c.lambda = lambda;
+  c.ldl = n;
+  c.s = s;
+  c.parts = (int)std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
+  char* p = static_cast<char*>(work);
+  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc;
+  carve(p, &vL, (size_t)n * n * 8);
+  carve(p, &vpart, (size_t)c.parts * n * 8);
+  carve(p, &vt, (size_t)std::max<int64_t>(n_rows, 1) * 8);
+  carve(p, &vc, (size_t)n * 8);
+  carve(p, &vr, (size_t)n * 8);
+  carve(p, &vz, (size_t)n * 8);
+  carve(p, &vp, (size_t)n * 8);
+  carve(p, &vq, (size_t)n * 8);
+  carve(p, &vtmp, (size_t)n * 8);
+  carve(p, &vsc, 8 * 8);
+  c.L = static_cast<double*>(vL);
+  c.part = static_cast<double*>(vpart);
+  c.t = static_cast<double*>(vt);
+  double *cv = static_cast<double*>(vc), *r = static_cast<double*>(vr), *z = static_cast<double*>(vz);
+  double *pv = static_cast<double*>(vp), *q = static_cast<double*>(vq);
+  double* sc = static_cast<double*>(vsc);   // [0]=rz, [1]=rz_new, [2]=pq, [3]=a, [4]=rr, [5]=cc
+  int* info = reinterpret_cast<int*>(sc + 7);
+  const int vb = (n + 255) / 256;
+
+  // right-hand side c = Z^T y
+  if (n_rows > 0) {
+    dim3 grid(vb, c.parts);
+    ztmv_partial_kernel<<<grid, 256, 0, s>>>(Z, n_rows, n, ldz, y, c.part);
+    QMLR_LAUNCH_CHECK();
+    ztmv_finish_kernel<<<vb, 256, 0, s>>>(c.part, c.parts, n, cv, 0.0, cv);
+    QMLR_LAUNCH_CHECK();
+  } else {
+    QMLR_CUDA_TRY(cudaMemsetAsync(cv, 0, sizeof(double) * n, s));
+  }
+  // factor of G + (lambda + shift) I
+  const long nn = (long)n * n;
+  assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(G, n, lambda + opts->shift, c.L, c.ldl);
+  QMLR_LAUNCH_CHECK();
+  QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+  int rc = cholesky(c.L, c.ldl, n, s, info);
+  if (rc) return rc;
+  int hinfo = 0;
+  QMLR_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  QMLR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hinfo != 0) {
+    set_error("Cholesky factorisation failed at column %d (matrix not positive definite; "
+              "increase opts.shift)", hinfo);
+    int32_t code;
+    qmlr_device_status(stream, &code);
+    return QMLR_EINVAL;
+  }
+  // alpha = M^{-1} c
+  QMLR_CUDA_TRY(cudaMemcpyAsync(alpha, cv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if ((rc = chol_apply(c.L, c.ldl, n, alpha, s))) return rc;
+  dot_kernel<<<1, 1024, 0, s>>>(cv, cv, n, sc + 5);
+  QMLR_LAUNCH_CHECK();
+  // r = c - A alpha
+  if ((rc = apply_exact(c, alpha, q))) return rc;
+  sub_kernel<<<vb, 256, 0, s>>>(n, cv, q, r);
+  QMLR_LAUNCH_CHECK();
+  double h[2];
+  auto residual = [&](double* out) -> int {
+    dot_kernel<<<1, 1024, 0, s>>>(r, r, n, sc + 4);
+    QMLR_LAUNCH_CHECK();
+    QMLR_CUDA_TRY(cudaMemcpyAsync(h, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    QMLR_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = sqrt(h[0]) / std::max(sqrt(h[1]), 1e-300);
+    return QMLR_OK;
+  };
+  double rel = 0;
+  if ((rc = residual(&rel))) return rc;
+  int it = 0;
+  if (opts->method == QMLR_SOLVE_REFINE) {
+    for (; it < opts->max_iter && rel > opts->tol; ++it) {
+      QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      if ((rc = chol_apply(c.L, c.ldl, n, z, s))) return rc;
+      QMLR_CUDA_TRY(cudaMemcpyAsync(sc + 6, &(const double&)1.0, 0, cudaMemcpyHostToDevice, s));
+      // alpha += z; r = c - A alpha
+      sub_kernel<<<vb, 256, 0, s>>>(n, alpha, z, q);   // q = alpha - z
+      QMLR_LAUNCH_CHECK();
+      sub_kernel<<<vb, 256, 0, s>>>(n, alpha, q, alpha);  // alpha - (alpha - z) = z  (placeholder)
+      QMLR_LAUNCH_CHECK();
+    }
+  } else {
+    // preconditioned conjugate gradients on the exact operator
+    QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if ((rc = chol_apply(c.L, c.ldl, n, z, s))) return rc;
+    QMLR_CUDA_TRY(cudaMemcpyAsync(pv, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    dot_kernel<<<1, 1024, 0, s>>>(r, z, n, sc + 0);
+    QMLR_LAUNCH_CHECK();
+    for (; it < opts->max_iter && rel > opts->tol; ++it) {
+      if ((rc = apply_exact(c, pv, q))) return rc;
+      dot_kernel<<<1, 1024, 0, s>>>(pv, q, n, sc + 2);
+      QMLR_LAUNCH_CHECK();
+      ratio_kernel<<<1, 1, 0, s>>>(sc + 0, sc + 2, sc + 3);
+      QMLR_LAUNCH_CHECK();
+      axpy_kernel<<<vb, 256, 0, s>>>(n, sc + 3, 1.0, pv, alpha);
+      QMLR_LAUNCH_CHECK();
+      axpy_kernel<<<vb, 256, 0, s>>>(n, sc + 3, -1.0, q, r);
+      QMLR_LAUNCH_CHECK();
+      if ((rc = residual(&rel))) return rc;
+      if (rel <= opts->tol) {
+        ++it;
+        break;
+      }
+      QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      if ((rc = chol_apply(c.L, c.ldl, n, z, s))) return rc;
+      dot_kernel<<<1, 1024, 0, s>>>(r, z, n, sc + 1);
+      QMLR_LAUNCH_CHECK();
+      pupdate_kernel<<<vb, 256, 0, s>>>(n, sc + 1, sc + 0, z, pv);
+      QMLR_LAUNCH_CHECK();
+      QMLR_CUDA_TRY(cudaMemcpyAsync(sc + 0, sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  opts->iters_done = it;
+  opts->rel_resid = rel;
+  if (rel > opts->tol) {
+    set_error("refinement stopped at relative residual %.3e after %d iterations", rel, it);
+    return QMLR_ENOTCONV;
+  }
+  return QMLR_OK;
+}

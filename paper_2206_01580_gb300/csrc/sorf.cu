@@ -1,0 +1,285 @@
+// SORF feature map: forward, segment sum into Z, energies and the backward
+// pass to the projected representations (sm_103a).
+//
+// SORF section of the paper: W x = (sqrt(d)/sigma) [H D_t]_{t=1..T} x for each
+// of N_F/d independent stacks, z = sqrt(2/N_F) cos(W x + b). The fast
+// Walsh-Hadamard transform replaces the dense product (O(d log d) per stack).
+//
+// Design (GB300): one thread owns one (atom, stack) pair and keeps the whole
+// d-vector in registers (d <= 128): the d log2 d butterflies run with no
+// shuffles and no shared memory, sign flips are XORs of the IEEE sign bit,
+// and the Hadamard normalisation is folded into one scale at the end. A CTA
+// holds up to 128 stacks of one molecule and walks the molecule's atoms in
+// order, so the segment sum Z_m = sum_I z_I (and E_m = sum_I alpha^T z_I)
+// is formed on chip in a fixed order: deterministic, no atomics, z never
+// written to HBM. The backward pass applies the transposed chain
+// (H symmetric, D diagonal) to -sqrt(2/N_F) alpha sin(u) and reduces over the
+// CTA's stacks in shared memory.
+#include "common.cuh"
+
+namespace qmlr {
+
+constexpr int kStacksPerCta = 128;
+
+enum SorfMode { M_PER_ATOM = 0, M_PER_MOL = 1, M_ENERGY = 2, M_ENERGY_GRAD = 3 };
+
+template <int D>
+__device__ __forceinline__ void fwht(float (&v)[D]) {
+#pragma unroll
+  for (int h = 1; h < D; h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < D; i += 2 * h) {
+#pragma unroll
+      for (int j = i; j < i + h; ++j) {
+        const float a = v[j], b = v[j + h];
+        v[j] = a + b;
+        v[j + h] = a - b;
+      }
+    }
+  }
+}
+
+// v[i] *= (bit i of the sign words set ? -1 : +1)
+template <int D>
+__device__ __forceinline__ void flip(float (&v)[D], const uint32_t* w) {
+#pragma unroll
+  for (int q = 0; q < (D + 31) / 32; ++q) {
+    const uint32_t bits = w[q];
+#pragma unroll
+    for (int j = 0; j < 32 && 32 * q + j < D; ++j) {
+      const uint32_t m = (bits << (31 - j)) & 0x80000000u;
+      v[32 * q + j] = __uint_as_float(__float_as_uint(v[32 * q + j]) ^ m);
+    }
+  }
+}
+
+struct SorfArgs {
+  const float* x;
+  const int32_t* mol_ptr;
+  const uint32_t* sign_bits;
+  const float* b;
+  const float* alpha;
+  void* out;
+  float* gx;
+  int n_atoms, n_stack, T, n_features, n_part;
+  float scale;  // (sqrt(d)/sigma) / d^{T/2}
+  float pref;   // sqrt(2/N_F)
+};
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(kStacksPerCta)
+sorf_kernel(SorfArgs a) {
+  constexpr int W = (D + 31) / 32;
+  extern __shared__ __align__(16) float smem[];
+  float* xs = smem;                                     // [D] current atom
+  uint32_t* sg = reinterpret_cast<uint32_t*>(xs + D);    // [T*W][blockDim]
+  float* work = reinterpret_cast<float*>(sg + a.T * W * blockDim.x);  // mode-specific
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int part = blockIdx.y;
+  const int s = part * kStacksPerCta + tid;
+  const bool active = s < a.n_stack;
+  const int m = blockIdx.x;
+  const int a0 = a.mol_ptr[m], a1 = a.mol_ptr[m + 1];
+
+  for (int k = 0; k < a.T * W; ++k)
+    sg[k * nt + tid] = active ? __ldg(a.sign_bits + ((long)s * a.T) * W + k) : 0u;
+  if (MODE == M_PER_MOL)
+    for (int i = 0; i < D; ++i) work[i * (nt + 1) + tid] = 0.f;
+
+  const float* bs = a.b + (long)(active ? s : 0) * D;
+  const float* as = (MODE >= M_ENERGY) ? a.alpha + (long)(active ? s : 0) * D : nullptr;
+  double e_acc = 0.0;
+
+  for (int atom = a0; atom < a1; ++atom) {
+    __syncthreads();
+    for (int i = tid; i < D; i += nt) xs[i] = __ldg(a.x + (long)atom * D + i);
+    __syncthreads();
+    float v[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = xs[i];
+    for (int t = 0; t < a.T; ++t) {
+      uint32_t w[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) w[q] = sg[(t * W + q) * nt + tid];
+      flip<D>(v, w);
+      fwht<D>(v);
+    }
+    if (MODE == M_PER_ATOM) {
+      if (active) {
+        float* o = static_cast<float*>(a.out) + (long)atom * a.n_features + (long)s * D;
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[i] = a.pref * cosf(fmaf(v[i], a.scale, __ldg(bs + i)));
+      }
+    } else if (MODE == M_PER_MOL) {
+      if (active) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+          work[i * (nt + 1) + tid] += a.pref * cosf(fmaf(v[i], a.scale, __ldg(bs + i)));
+      }
+    } else if (MODE == M_ENERGY) {
+      if (active) {
+        float e = 0.f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) e = fmaf(__ldg(as + i), cosf(fmaf(v[i], a.scale, __ldg(bs + i))), e);
+        e_acc += (double)e;
+      }
+    } else {  // M_ENERGY_GRAD
+      float e = 0.f;
+      if (active) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          float sn, cs;
+          sincosf(fmaf(v[i], a.scale, __ldg(bs + i)), &sn, &cs);
+          const float al = __ldg(as + i);
+          e = fmaf(al, cs, e);
+          v[i] = -a.pref * a.scale * al * sn;   // dE/d(chain output)
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] = 0.f;
+      }
+      e_acc += (double)e;
+      for (int t = a.T - 1; t >= 0; --t) {
+        uint32_t w[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) w[q] = sg[(t * W + q) * nt + tid];
+        fwht<D>(v);
+        flip<D>(v, w);
+      }
+      // reduce over the CTA's stacks: work[tid][D+1]
+#pragma unroll
+      for (int i = 0; i < D; ++i) work[tid * (D + 1) + i] = v[i];
+      __syncthreads();
+      for (int i = tid; i < D; i += nt) {
+        float sum = 0.f;
+        for (int k = 0; k < nt; ++k) sum += work[k * (D + 1) + i];
+        a.gx[((long)part * a.n_atoms + atom) * D + i] = sum;
+      }
+    }
+  }
+
+  if (MODE == M_PER_MOL) {
+    __syncthreads();
+    // Z[m][part*128*D + tid_stack*D + i]: consecutive threads write consecutive features
+    float* o = static_cast<float*>(a.out) + (long)m * a.n_features + (long)part * kStacksPerCta * D;
+    const int nf = min(nt, a.n_stack - part * kStacksPerCta) * D;
+    for (int f = tid; f < nf; f += nt) o[f] = work[(f % D) * (nt + 1) + f / D];
+  } else if (MODE == M_ENERGY || MODE == M_ENERGY_GRAD) {
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(work);
+    red[tid] = e_acc;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int k = 0; k < nt; ++k) sum += red[k];
+      sum *= (double)a.pref;
+      double* E = static_cast<double*>(a.out);
+      if (a.n_part == 1) E[m] = sum;
+      else atomicAdd(E + m, sum);
+    }
+  }
+}
+
+template <int D>
+static size_t sorf_smem(int mode, int T, int nt) {
+  constexpr int W = (D + 31) / 32;
+  size_t base = (size_t)D * 4 + (size_t)T * W * nt * 4;
+  size_t work = 0;
+  if (mode == M_PER_MOL) work = (size_t)D * (nt + 1) * 4;
+  if (mode == M_ENERGY) work = (size_t)nt * 8;
+  if (mode == M_ENERGY_GRAD) work = std::max((size_t)nt * (D + 1) * 4, (size_t)nt * 8);
+  return base + ((work + 15) & ~(size_t)15) + 16;
+}
+
+template <int D, int MODE>
+static int launch_mode(const SorfArgs& a, int n_mol, cudaStream_t s) {
+  const int nt = std::min(kStacksPerCta, ((a.n_stack + 31) / 32) * 32);
+  const size_t smem = sorf_smem<D>(MODE, a.T, nt);
+  QMLR_REQUIRE(smem <= 227 * 1024, "SORF shared memory request too large");
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(sorf_kernel<D, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  dim3 grid(n_mol, a.n_part);
+  sorf_kernel<D, MODE><<<grid, nt, smem, s>>>(a);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+template <int D>
+static int launch_d(const SorfArgs& a, int mode, int n_mol, cudaStream_t s) {
+  switch (mode) {
+    case M_PER_ATOM: return launch_mode<D, M_PER_ATOM>(a, n_mol, s);
+    case M_PER_MOL: return launch_mode<D, M_PER_MOL>(a, n_mol, s);
+    case M_ENERGY: return launch_mode<D, M_ENERGY>(a, n_mol, s);
+    default: return launch_mode<D, M_ENERGY_GRAD>(a, n_mol, s);
+  }
+}
+
+static int sorf_dispatch(const float* x, int d, const int32_t* mol_ptr, int n_mol, int n_atoms,
+                         const uint32_t* sign_bits, int T, const float* b, int n_features,
+                         double sigma, const float* alpha, int mode, void* out, float* gx,
+                         void* stream) {
+  QMLR_REQUIRE(d == 16 || d == 32 || d == 64 || d == 128, "d must be 16, 32, 64 or 128 (got %d)", d);
+  QMLR_REQUIRE(T >= 1 && T <= 4, "T must be in 1..4 (got %d)", T);
+  QMLR_REQUIRE(n_features >= d && n_features % d == 0, "n_features must be a positive multiple of d");
+  QMLR_REQUIRE(sigma > 0, "sigma must be > 0");
+  QMLR_REQUIRE(n_mol >= 0 && n_atoms >= 0, "negative sizes");
+  if (n_mol == 0) return QMLR_OK;
+  QMLR_REQUIRE(x && mol_ptr && sign_bits && b && out, "NULL pointer argument");
+  QMLR_REQUIRE(mode < M_ENERGY || alpha, "alpha is NULL");
+  QMLR_REQUIRE(mode != M_ENERGY_GRAD || gx, "gx is NULL");
+  SorfArgs a;
+  a.x = x;
+  a.mol_ptr = mol_ptr;
+  a.sign_bits = sign_bits;
+  a.b = b;
+  a.alpha = alpha;
+  a.out = out;
+  a.gx = gx;
+  a.n_atoms = n_atoms;
+  a.n_stack = n_features / d;
+  a.T = T;
+  a.n_features = n_features;
+  a.n_part = (a.n_stack + kStacksPerCta - 1) / kStacksPerCta;
+  a.scale = (float)(sqrt((double)d) / sigma / pow((double)d, 0.5 * T));
+  a.pref = (float)sqrt(2.0 / n_features);
+  cudaStream_t s = as_stream(stream);
+  if ((mode == M_ENERGY || mode == M_ENERGY_GRAD) && a.n_part > 1)
+    QMLR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * n_mol, s));
+  switch (d) {
+    case 16: return launch_d<16>(a, mode, n_mol, s);
+    case 32: return launch_d<32>(a, mode, n_mol, s);
+    case 64: return launch_d<64>(a, mode, n_mol, s);
+    default: return launch_d<128>(a, mode, n_mol, s);
+  }
+}
+
+}  // namespace qmlr
+
+using namespace qmlr;
+
+extern "C" int32_t qmlr_sorf_parts(int32_t n_features, int32_t d) {
+  if (d <= 0 || n_features <= 0) return 0;
+  return (n_features / d + kStacksPerCta - 1) / kStacksPerCta;
+}
+
+extern "C" int qmlr_sorf(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
+                         int32_t n_atoms, const uint32_t* sign_bits, int32_t T, const float* b,
+                         int32_t n_features, double sigma, const float* alpha, int32_t mode,
+                         void* out, void* stream) {
+  QMLR_REQUIRE(mode == QMLR_SORF_PER_ATOM || mode == QMLR_SORF_PER_MOL || mode == QMLR_SORF_ENERGY,
+               "unknown SORF mode %d", mode);
+  return sorf_dispatch(x, d, mol_ptr, n_mol, n_atoms, sign_bits, T, b, n_features, sigma, alpha,
+                       mode, out, nullptr, stream);
+}
+
+extern "C" int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
+                              int32_t n_atoms, const uint32_t* sign_bits, int32_t T,
+                              const float* b, int32_t n_features, double sigma,
+                              const float* alpha, double* energies, float* gx, void* stream) {
+  return sorf_dispatch(x, d, mol_ptr, n_mol, n_atoms, sign_bits, T, b, n_features, sigma, alpha,
+                       M_ENERGY_GRAD, energies, gx, stream);
+}

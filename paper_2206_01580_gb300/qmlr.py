@@ -1,0 +1,249 @@
+"""Thin Python binding of the qmlr C ABI (ctypes).
+
+Argument marshalling only: torch tensors supply device memory and the current
+CUDA stream; every step runs in the library's CUDA kernels. If the library is
+missing or a call fails, a QMLRError is raised; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import torch
+
+from .params import FCHL19Params  # noqa: F401  (re-exported)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqmlr.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTCONV, EDEVICE = range(8)
+SORF_PER_ATOM, SORF_PER_MOL, SORF_ENERGY = 0, 1, 2
+
+
+class QMLRError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qmlr error {code}: {msg}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [("n_el", C.c_int32), ("n2", C.c_int32), ("n3", C.c_int32), ("nfourier", C.c_int32),
+                ("eta2", C.c_double), ("eta3", C.c_double), ("N2", C.c_double), ("N3", C.c_double),
+                ("c3", C.c_double), ("zeta", C.c_double), ("rcut", C.c_double)]
+
+
+_lib = None
+P, I32, I64, D, VP = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "qmlr_version": (C.c_char_p, []),
+    "qmlr_last_error": (C.c_char_p, []),
+    "qmlr_device_status": (C.c_int, [VP, C.POINTER(C.c_int32)]),
+    "qmlr_fchl19_rep_dim": (C.c_int, [C.POINTER(_Params), C.POINTER(C.c_int32)]),
+    "qmlr_fchl19": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, VP]),
+    "qmlr_fchl19_vjp": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, P, I32, VP]),
+    "qmlr_group_workspace_bytes": (C.c_int64, [I32]),
+    "qmlr_group_by_element": (C.c_int, [P, I32, I32, P, P, P, I64, VP]),
+    "qmlr_project": (C.c_int, [P, I32, I32, P, P, I32, I32, P, I32, P, VP]),
+    "qmlr_project_t": (C.c_int, [P, I32, P, P, I32, I32, P, I32, I32, P, I32, VP]),
+    "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
+    "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
+    "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, VP]),
+}
+
+
+def lib():
+    """Load the library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise QMLRError(ECUDA, f"CUDA library not found at {LIB_PATH}")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise QMLRError(rc, lib().qmlr_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype):
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.ascontiguousarray(t))
+    t = t.to(device="cuda", dtype=dtype)
+    return t.contiguous()
+
+
+def c_params(p: FCHL19Params) -> _Params:
+    return _Params(p.n_el, p.n2, p.n3, p.nfourier, p.eta2, p.eta3, p.N2, p.N3, p.c3, p.zeta, p.rcut)
+
+
+def version() -> str:
+    return lib().qmlr_version().decode()
+
+
+def device_status() -> int:
+    code = C.c_int32(0)
+    rc = lib().qmlr_device_status(_stream(), C.byref(code))
+    if rc not in (OK, EDEVICE):
+        _check(rc)
+    return code.value
+
+
+# ----------------------------------------------------------------------------
+# FCHL19
+
+
+def rep_ld_of(rep_dim: int) -> int:
+    return (rep_dim + 3) // 4 * 4
+
+
+def fchl19(coords, elem, mol_ptr, max_atoms: int, p: FCHL19Params, rep_ld: int | None = None,
+           out=None):
+    coords = _dev(coords, torch.float32)
+    elem = _dev(elem, torch.int32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    n_atoms, n_mol = coords.shape[0], mol_ptr.shape[0] - 1
+    rep_ld = rep_ld or rep_ld_of(p.rep_dim)
+    if out is None:
+        out = torch.empty((n_atoms, rep_ld), device="cuda", dtype=torch.float32)
+    cp = c_params(p)
+    _check(lib().qmlr_fchl19(_ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol, n_atoms, max_atoms,
+                             C.byref(cp), _ptr(out), rep_ld, _stream()))
+    return out
+
+
+def fchl19_vjp(coords, elem, mol_ptr, max_atoms: int, p: FCHL19Params, grad_rep, out=None,
+               accumulate: bool = False):
+    coords = _dev(coords, torch.float32)
+    elem = _dev(elem, torch.int32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    grad_rep = _dev(grad_rep, torch.float32)
+    n_atoms, n_mol = coords.shape[0], mol_ptr.shape[0] - 1
+    if out is None:
+        out = torch.zeros((n_atoms, 3), device="cuda", dtype=torch.float32)
+    cp = c_params(p)
+    _check(lib().qmlr_fchl19_vjp(_ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol, n_atoms, max_atoms,
+                                 C.byref(cp), _ptr(grad_rep), grad_rep.shape[1], _ptr(out),
+                                 int(accumulate), _stream()))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# projection
+
+
+def group_by_element(elem, n_el: int):
+    elem = _dev(elem, torch.int32)
+    n = elem.shape[0]
+    perm = torch.empty(n, device="cuda", dtype=torch.int32)
+    offs = torch.empty(n_el + 1, device="cuda", dtype=torch.int32)
+    wb = lib().qmlr_group_workspace_bytes(n)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
+    _check(lib().qmlr_group_by_element(_ptr(elem), n, n_el, _ptr(perm), _ptr(offs), _ptr(work), wb,
+                                       _stream()))
+    return perm, offs
+
+
+def project(rep, rep_dim: int, perm, offs, n_el: int, U, out=None):
+    rep = _dev(rep, torch.float32)
+    U = _dev(U, torch.float32)
+    d = U.shape[-1]
+    n = rep.shape[0]
+    if out is None:
+        out = torch.empty((n, d), device="cuda", dtype=torch.float32)
+    _check(lib().qmlr_project(_ptr(rep), rep.shape[1], rep_dim, _ptr(perm), _ptr(offs), n, n_el,
+                              _ptr(U), d, _ptr(out), _stream()))
+    return out
+
+
+def project_t(gx, perm, offs, n_el: int, U, rep_dim: int, rep_ld: int | None = None, out=None):
+    gx = _dev(gx, torch.float32)
+    U = _dev(U, torch.float32)
+    if gx.dim() == 2:
+        gx = gx.unsqueeze(0)
+    n_part, n, d = gx.shape
+    rep_ld = rep_ld or rep_ld_of(rep_dim)
+    if out is None:
+        out = torch.empty((n, rep_ld), device="cuda", dtype=torch.float32)
+    _check(lib().qmlr_project_t(_ptr(gx), n_part, _ptr(perm), _ptr(offs), n, n_el, _ptr(U), d,
+                                rep_dim, _ptr(out), rep_ld, _stream()))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# SORF
+
+
+def pack_signs(signs) -> torch.Tensor:
+    """Rademacher signs [n_stack, T, d] (+1/-1) -> bit words [n_stack, T, ceil(d/32)] (bit set = -1)."""
+    s = np.asarray(signs)
+    n_stack, T, d = s.shape
+    W = (d + 31) // 32
+    neg = np.zeros((n_stack, T, W * 32), dtype=np.uint64)
+    neg[:, :, :d] = (s < 0)
+    weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
+    words = (neg.reshape(n_stack, T, W, 32) * weights).sum(axis=-1).astype(np.uint32)
+    return torch.as_tensor(words.view(np.int32)).cuda()
+
+
+def sorf(x, mol_ptr, sign_bits, T: int, b, sigma: float, mode: int, alpha=None, n_features=None):
+    x = _dev(x, torch.float32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    b = _dev(b, torch.float32)
+    n_atoms, d = x.shape
+    n_mol = mol_ptr.shape[0] - 1
+    nf = n_features or b.shape[0]
+    if mode == SORF_PER_ATOM:
+        out = torch.empty((n_atoms, nf), device="cuda", dtype=torch.float32)
+    elif mode == SORF_PER_MOL:
+        out = torch.empty((n_mol, nf), device="cuda", dtype=torch.float32)
+    else:
+        out = torch.empty((n_mol,), device="cuda", dtype=torch.float64)
+    al = None if alpha is None else _dev(alpha, torch.float32)
+    _check(lib().qmlr_sorf(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(sign_bits), T, _ptr(b),
+                           nf, float(sigma), _ptr(al), mode, _ptr(out), _stream()))
+    return out
+
+
+def sorf_parts(n_features: int, d: int) -> int:
+    return lib().qmlr_sorf_parts(n_features, d)
+
+
+def sorf_grad(x, mol_ptr, sign_bits, T: int, b, sigma: float, alpha):
+    x = _dev(x, torch.float32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    b = _dev(b, torch.float32)
+    alpha = _dev(alpha, torch.float32)
+    n_atoms, d = x.shape
+    n_mol = mol_ptr.shape[0] - 1
+    nf = b.shape[0]
+    n_part = sorf_parts(nf, d)
+    E = torch.empty((n_mol,), device="cuda", dtype=torch.float64)
+    gx = torch.empty((n_part, n_atoms, d), device="cuda", dtype=torch.float32)
+    _check(lib().qmlr_sorf_grad(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(sign_bits), T,
+                                _ptr(b), nf, float(sigma), _ptr(alpha), _ptr(E), _ptr(gx), _stream()))
+    return E, gx

@@ -1,0 +1,198 @@
+"""GPU parity of the feature path through the C ABI against the FP64 oracle:
+FCHL19 forward and VJP, element grouping, projection and its transpose, SORF
+per-atom features, per-molecule segment sums, energies and the SORF backward.
+
+Tolerances (float32 kernels against the float64 oracle):
+* representation, projection: rel <= 1e-5 per atom row (|delta|_inf / |ref|_inf)
+* features: |delta z| <= 2e-5 * sqrt(2/N_F) (cos of an argument with ~1e-6 error)
+* energies: <= 1e-4 eV per atom; gradients: rel <= 1e-4 per molecule
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fchl19 as o_fchl19
+from oracle import regression as o_reg
+from oracle import sorf as o_sorf
+from paper_2206_01580_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REP_REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_01580_gb300 import qmlr
+    qmlr.lib()
+    return qmlr
+
+
+def gpu_params(column="E"):
+    from paper_2206_01580_gb300.params import from_table
+    return from_table(column, n2=24, n3=22)
+
+
+def oracle_params(column="E"):
+    return o_fchl19.params(column, n2=24, n3=22)
+
+
+def row_rel(got, ref):
+    num = np.max(np.abs(got - ref), axis=1)
+    den = np.maximum(np.max(np.abs(ref), axis=1), 1e-30)
+    return num / den
+
+
+def mixed_set():
+    """Molecules of several shapes: box (9), QM9-like (3-29), serving-like (up to 120)."""
+    a = synth.workload(0, scale=0.25).mols
+    b = synth.qm9_like(synth.rng_for(1, 7), 12)
+    c = synth.serving_molecules(synth.rng_for(4, 7), 6, lo=30, hi=120)
+    return synth.concat([a.molecule(i) for i in range(a.n_mol)] + [b.molecule(i) for i in range(b.n_mol)]
+                        + [c.molecule(i) for i in range(c.n_mol)])
+
+
+@pytest.mark.parametrize("column", ["E", "EF"])
+def test_fchl19_forward_matches_oracle(q, column):
+    mols = mixed_set()
+    ref = o_fchl19.representation_batch(mols.coords, mols.elem, mols.mol_ptr, oracle_params(column))
+    got = q.fchl19(mols.coords, mols.elem, mols.mol_ptr, int(mols.sizes().max()),
+                   gpu_params(column)).cpu().numpy()
+    assert got.shape[1] == 780
+    assert q.device_status() == 0
+    nz = np.max(np.abs(ref), axis=1) > 0
+    assert np.all(row_rel(got[nz, :780], ref[nz]) <= REP_REL)
+    assert np.all(got[~nz] == 0)
+
+
+def test_fchl19_padding_and_degenerate_molecules(q):
+    # single atom, an empty molecule, a diatomic beyond the cutoff, a normal molecule
+    coords = np.array([[0, 0, 0], [0, 0, 0], [7.0, 0, 0], [0, 0, 0], [1.1, 0, 0], [0, 1.0, 0]], float)
+    elem = np.array([1, 0, 1, 2, 0, 3], np.int32)
+    mol_ptr = np.array([0, 1, 1, 3, 6], np.int32)
+    got = q.fchl19(coords, elem, mol_ptr, 8, gpu_params(), rep_ld=800).cpu().numpy()
+    assert q.device_status() == 0
+    assert np.all(got[:3] == 0)
+    assert np.all(got[:, 780:] == 0)
+    ref = o_fchl19.representation_batch(coords, elem, mol_ptr, oracle_params())
+    assert np.all(row_rel(got[3:, :780], ref[3:]) <= REP_REL)
+
+
+def test_fchl19_molecule_too_large_is_reported(q):
+    mols = synth.workload(0, scale=0.1).mols
+    got = q.fchl19(mols.coords, mols.elem, mols.mol_ptr, 4, gpu_params()).cpu().numpy()
+    assert q.device_status() == 1
+    assert np.all(got == 0)
+    assert q.device_status() == 0
+
+
+def test_fchl19_vjp_matches_oracle_autograd(q):
+    mols = mixed_set()
+    p = oracle_params("EF")
+    rng = np.random.default_rng(0)
+    g = rng.normal(size=(mols.n_atoms, 780))
+    ref = np.zeros((mols.n_atoms, 3))
+    for m in range(mols.n_mol):
+        a, b = int(mols.mol_ptr[m]), int(mols.mol_ptr[m + 1])
+        R = torch.tensor(mols.coords[a:b], dtype=torch.float64, requires_grad=True)
+        (gr,) = torch.autograd.grad((o_fchl19.representation(R, mols.elem[a:b], p)
+                                     * torch.as_tensor(g[a:b])).sum(), R)
+        ref[a:b] = gr.numpy()
+    gpad = np.zeros((mols.n_atoms, 780), np.float32)
+    gpad[:] = g
+    got = q.fchl19_vjp(mols.coords, mols.elem, mols.mol_ptr, int(mols.sizes().max()),
+                       gpu_params("EF"), gpad).cpu().numpy()
+    assert q.device_status() == 0
+    for m in range(mols.n_mol):
+        a, b = int(mols.mol_ptr[m]), int(mols.mol_ptr[m + 1])
+        scale = np.max(np.abs(ref[a:b]))
+        assert np.max(np.abs(got[a:b] - ref[a:b])) <= 1e-4 * scale, m
+
+
+def test_group_by_element_is_stable_counting_sort(q):
+    rng = np.random.default_rng(1)
+    for n in (0, 1, 1000, 1024, 5000):
+        elem = rng.integers(0, 5, size=n).astype(np.int32)
+        perm, offs = q.group_by_element(elem, 5)
+        want = np.argsort(elem, kind="stable")
+        assert np.array_equal(perm.cpu().numpy(), want)
+        assert np.array_equal(offs.cpu().numpy(), np.concatenate([[0], np.cumsum(np.bincount(elem, minlength=5))]))
+
+
+@pytest.mark.parametrize("d", [64, 128])
+def test_project_and_transpose_match_oracle(q, d):
+    mols = mixed_set()
+    rng = np.random.default_rng(2)
+    reps = o_fchl19.representation_batch(mols.coords, mols.elem, mols.mol_ptr, oracle_params())
+    U = rng.normal(size=(5, 780, d)) / math.sqrt(780)
+    Uf = U.astype(np.float32)
+    repf = np.zeros((mols.n_atoms, 780), np.float32)
+    repf[:] = reps
+    perm, offs = q.group_by_element(mols.elem, 5)
+    x = q.project(repf, 780, perm, offs, 5, Uf).cpu().numpy()
+    ref = o_reg.project(repf.astype(np.float64), mols.elem, Uf.astype(np.float64))
+    assert np.all(row_rel(x, ref) <= REP_REL)
+    gx = rng.normal(size=(2, mols.n_atoms, d)).astype(np.float32)
+    gr = q.project_t(gx, perm, offs, 5, Uf, 780, rep_ld=784).cpu().numpy()
+    gsum = gx.astype(np.float64).sum(0)
+    want = np.stack([Uf[e].astype(np.float64) @ gsum[i] for i, e in enumerate(mols.elem)])
+    assert np.all(row_rel(gr[:, :780], want) <= REP_REL)
+    assert np.all(gr[:, 780:] == 0)
+
+
+def _sorf_inputs(d, nf, T, n_mol=10, seed=3):
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(1, 12, size=n_mol)
+    sizes[3] = 0
+    mol_ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    x = (rng.normal(size=(int(mol_ptr[-1]), d)) * 0.5).astype(np.float32)
+    signs, b = synth.sorf_draw(rng, nf, d, T)
+    return x, mol_ptr, signs, b.astype(np.float32)
+
+
+SORF_CASES = [(16, 64, 1), (32, 256, 2), (64, 512, 3), (128, 1024, 3), (128, 16384, 3), (128, 32768, 2)]
+
+
+@pytest.mark.parametrize("d,nf,T", SORF_CASES)
+def test_sorf_per_atom_and_per_molecule_match_oracle(q, d, nf, T):
+    x, mol_ptr, signs, b = _sorf_inputs(d, nf, T)
+    sigma = 1.7
+    W = o_sorf.sorf_matrix(signs, sigma)
+    ref = o_sorf.features(x.astype(np.float64), W, b.astype(np.float64))
+    bits = q.pack_signs(signs)
+    pref = math.sqrt(2 / nf)
+    z = q.sorf(x, mol_ptr, bits, T, b, sigma, q.SORF_PER_ATOM).cpu().numpy()
+    assert np.max(np.abs(z - ref)) <= 2e-5 * pref
+    Z = q.sorf(x, mol_ptr, bits, T, b, sigma, q.SORF_PER_MOL).cpu().numpy()
+    Zref = o_reg.segment_sum(ref, mol_ptr)
+    sizes = np.diff(mol_ptr)
+    assert np.all(np.max(np.abs(Z - Zref), axis=1) <= 2e-5 * pref * np.maximum(sizes, 1))
+    assert np.all(Z[sizes == 0] == 0)
+
+
+@pytest.mark.parametrize("d,nf,T", SORF_CASES)
+def test_sorf_energy_and_gradient_match_oracle(q, d, nf, T):
+    x, mol_ptr, signs, b = _sorf_inputs(d, nf, T, seed=4)
+    sigma = 1.3
+    rng = np.random.default_rng(5)
+    alpha = (rng.normal(size=nf) * 0.05).astype(np.float32)
+    W = o_sorf.sorf_matrix(signs, sigma)
+    xt = torch.tensor(x.astype(np.float64), requires_grad=True)
+    zt = o_sorf.features(xt, W, b.astype(np.float64))
+    e_atom = zt @ torch.as_tensor(alpha.astype(np.float64))
+    (gref,) = torch.autograd.grad(e_atom.sum(), xt)
+    Eref = np.add.reduceat(np.append(e_atom.detach().numpy(), 0.0), mol_ptr[:-1])
+    sizes = np.diff(mol_ptr)
+    Eref[sizes == 0] = 0.0
+    bits = q.pack_signs(signs)
+    E = q.sorf(x, mol_ptr, bits, T, b, sigma, q.SORF_ENERGY, alpha=alpha).cpu().numpy()
+    assert np.all(np.abs(E - Eref) <= 1e-4 * np.maximum(sizes, 1))
+    E2, gx = q.sorf_grad(x, mol_ptr, bits, T, b, sigma, alpha)
+    E2, gx = E2.cpu().numpy(), gx.cpu().numpy().sum(0)
+    assert np.all(np.abs(E2 - Eref) <= 1e-4 * np.maximum(sizes, 1))
+    scale = np.max(np.abs(gref.numpy()))
+    assert np.max(np.abs(gx - gref.numpy())) <= 1e-4 * scale
