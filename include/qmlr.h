@@ -198,6 +198,84 @@ int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_
                    int32_t n_features, double sigma, const float* alpha, double* energies,
                    float* gx, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Regularised normal equations (RFF section: (Z^T Z + lambda I) alpha = Z^T E,
+ * energy and force rows stacked for energy+force training; the paper solves
+ * by LU in FP64 and builds Z^T Z in FP64 or FP32 with Kahan summation).
+ * ------------------------------------------------------------------------ */
+enum {
+  QMLR_GRAM_FP32 = 0,   /* plain FP32 SIMT product (comparison form) */
+  QMLR_GRAM_BF16X3 = 1  /* tensor cores: Z = H + L (bf16 hi/lo), H^T H + H^T L + L^T H, FP32 accumulate */
+};
+
+/*
+ * Split-precision Gram operand, transposed (feature-major, rows contiguous):
+ *   zt_hi[f][r] = bf16(Z[r][f]),  zt_lo[f][r] = bf16(Z[r][f] - zt_hi[f][r])
+ *   Z      float [n_rows][ldz]
+ *   zt_hi, zt_lo  bf16 bit patterns [n_features][k_pad]; k_pad >= n_rows, k_pad % 64 == 0;
+ *          rows n_rows..k_pad-1 are written as zeros.
+ */
+int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
+                      uint16_t* zt_hi, uint16_t* zt_lo, int64_t k_pad, void* stream);
+
+/*
+ * G = Z^T Z as a full symmetric float [n_features][n_features] matrix.
+ *   QMLR_GRAM_FP32:   reads Z [n_rows][ldz] (zt_* may be NULL)
+ *   QMLR_GRAM_BF16X3: reads zt_hi, zt_lo from qmlr_gram_operand (Z may be NULL);
+ *                     n_features % 128 == 0.
+ */
+int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
+              const uint16_t* zt_hi, const uint16_t* zt_lo, int64_t k_pad, float* G, void* stream);
+
+/* c = Z^T y in FP64 (y double [n_rows], c double [n_features]); fixed-order sums. */
+int64_t qmlr_zty_workspace_bytes(int64_t n_rows, int32_t n_features);
+int qmlr_zty(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz, const double* y,
+             double* c, void* work, int64_t work_bytes, void* stream);
+
+/*
+ * In-place FP64 Cholesky factorisation A = L L^T of the lower triangle of
+ * L (double [n][ldl], row-major); the strict upper triangle is not referenced.
+ * Synchronous. *host_info = 0 on success, else the 1-based column whose pivot
+ * was not positive (the factor is then not usable).
+ */
+int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_info, void* stream);
+
+/* v <- (L L^T)^{-1} v with the factor from qmlr_cholesky (forward, then backward substitution). */
+int qmlr_cholesky_solve(const double* L, int64_t ldl, int32_t n, double* v, void* stream);
+
+enum {
+  QMLR_SOLVE_PCG = 0,    /* conjugate gradients on the exact operator, Cholesky-preconditioned */
+  QMLR_SOLVE_REFINE = 1  /* classical iterative refinement with the Cholesky factor */
+};
+
+typedef struct qmlr_solve_opts {
+  int32_t method;      /* QMLR_SOLVE_PCG or QMLR_SOLVE_REFINE */
+  int32_t max_iter;    /* refinement iterations after the first solve (>= 0) */
+  double tol;          /* target ||c - A alpha|| / ||c|| */
+  double shift;        /* >= 0, added to the diagonal of the factorised matrix only */
+  int32_t iters_done;  /* out: refinement iterations run */
+  double rel_resid;    /* out: final ||c - A alpha|| / ||c|| with the exact operator */
+} qmlr_solve_opts;
+
+/* Device workspace bytes of qmlr_gram_solve. */
+int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features);
+
+/*
+ * Solve (Z^T Z + lambda I) alpha = Z^T y (synchronous; returns once alpha is final).
+ *   G      float [n_features]^2 symmetric Gram (any precision form of qmlr_gram)
+ *   Z      float [n_rows][ldz] the stored feature rows (the exact operator is
+ *          A v = Z^T (Z v) + lambda v, evaluated in FP64)
+ *   y      double [n_rows] targets
+ *   alpha  double [n_features] out
+ * Steps: c = Z^T y; FP64 Cholesky of G + (lambda + shift) I; alpha = factor
+ * solve of c; then up to max_iter refinement steps against the exact operator.
+ * QMLR_ENOTCONV: tolerance not reached (alpha and opts->rel_resid still written).
+ * QMLR_EINVAL with a message when the factorisation meets a non-positive pivot.
+ */
+int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, int32_t n_features,
+                    int64_t ldz, const double* y, double lambda, qmlr_solve_opts* opts,
+                    double* alpha, void* work, int64_t work_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -179,7 +179,8 @@ extern "C" int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int3
     QMLR_REQUIRE(n_features % 128 == 0, "BF16X3 Gram needs n_features % 128 == 0 (got %d)", n_features);
     return gram_bf16x3_tc(zt_hi, zt_lo, k_pad, n_features, G, s);
   }
-  QMLR_REQUIRE(false, "unknown Gram precision %d", precision);
+  set_error("unknown Gram precision %d", precision);
+  return QMLR_EINVAL;
 }
 
 extern "C" int64_t qmlr_zty_workspace_bytes(int64_t n_rows, int32_t n_features) {

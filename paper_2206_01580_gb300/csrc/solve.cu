@@ -66,8 +66,9 @@ potrf_diag_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, in
 // Panel: rows r in [k0+nb, n): L[r][k0:k0+nb] = A[r][k0:k0+nb] * L_kk^{-T}. One thread per row.
 __global__ void __launch_bounds__(64)
 trsm_panel_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
-  __shared__ double lkk[NB][NB + 1];
-  __shared__ double x[NB][NB + 1];
+  extern __shared__ double dsm[];
+  double (*lkk)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm);
+  double (*x)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm + NB * (NB + 1));
   const int tid = threadIdx.x;
   for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
     const int i = idx / nb, j = idx % nb;
@@ -99,8 +100,9 @@ trsm_panel_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
 // Trailing update of the lower block tiles: A[I][J] -= L[I][k] L[J][k]^T, I >= J > k.
 __global__ void __launch_bounds__(256)
 syrk_update_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
-  __shared__ double li[NB][NB + 1];
-  __shared__ double lj[NB][NB + 1];
+  extern __shared__ double dsm[];
+  double (*li)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm);
+  double (*lj)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm + NB * (NB + 1));
   const int t0 = (k0 + nb) / NB;          // first trailing block
   const int T = (n + NB - 1) / NB - t0;   // trailing blocks
   int t = blockIdx.x, bi = 0;
@@ -273,6 +275,11 @@ __global__ void pupdate_kernel(int n, const double* __restrict__ rz_new,
   if (i < n) p[i] = z[i] + (*rz_new / *rz_old) * p[i];
 }
 
+__global__ void add_kernel(int n, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+
 __global__ void ratio_kernel(const double* a, const double* b, double* out) { *out = *a / *b; }
 
 __global__ void sub_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
@@ -295,18 +302,28 @@ struct SolveCtx {
   cudaStream_t s;
 };
 
+constexpr size_t kPanelSmem = 2 * NB * (NB + 1) * sizeof(double);
+
 static int cholesky(double* L, long ldl, int n, cudaStream_t s, int* info) {
   int* err = device_error_ptr();
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPanelSmem));
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPanelSmem));
+    attr = true;
+  }
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int nb = std::min(NB, n - k0);
     potrf_diag_kernel<<<1, 256, 0, s>>>(L, ldl, k0, nb, err, info);
     QMLR_LAUNCH_CHECK();
     const int rows = n - k0 - nb;
     if (rows <= 0) break;
-    trsm_panel_kernel<<<(rows + 63) / 64, 64, 0, s>>>(L, ldl, k0, nb, n);
+    trsm_panel_kernel<<<(rows + 63) / 64, 64, kPanelSmem, s>>>(L, ldl, k0, nb, n);
     QMLR_LAUNCH_CHECK();
     const int T = (rows + NB - 1) / NB;
-    syrk_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(L, ldl, k0, nb, n);
+    syrk_update_kernel<<<T * (T + 1) / 2, 256, kPanelSmem, s>>>(L, ldl, k0, nb, n);
     QMLR_LAUNCH_CHECK();
   }
   return QMLR_OK;
@@ -402,8 +419,10 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   QMLR_REQUIRE(n_rows == 0 || (Z && y), "Z/y are NULL");
   QMLR_REQUIRE(lambda >= 0 && opts->shift >= 0, "lambda and shift must be >= 0");
   QMLR_REQUIRE(opts->max_iter >= 0, "max_iter must be >= 0");
-  QMLR_REQUIRE(work && work_bytes >= qmlr_solve_workspace_bytes(n_rows, n_features) - 4096 + 2048,
+  QMLR_REQUIRE(work && work_bytes >= qmlr_solve_workspace_bytes(n_rows, n_features),
                "workspace too small");
+  QMLR_REQUIRE(opts->method == QMLR_SOLVE_PCG || opts->method == QMLR_SOLVE_REFINE,
+               "unknown solve method %d", opts->method);
   cudaStream_t s = as_stream(stream);
   const int n = n_features;
   SolveCtx c;
@@ -485,15 +504,16 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   if ((rc = residual(&rel))) return rc;
   int it = 0;
   if (opts->method == QMLR_SOLVE_REFINE) {
+    // alpha += M^{-1} r ; r = c - A alpha
     for (; it < opts->max_iter && rel > opts->tol; ++it) {
       QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       if ((rc = chol_apply(c.L, c.ldl, n, z, s))) return rc;
-      QMLR_CUDA_TRY(cudaMemcpyAsync(sc + 6, &(const double&)1.0, 0, cudaMemcpyHostToDevice, s));
-      // alpha += z; r = c - A alpha
-      sub_kernel<<<vb, 256, 0, s>>>(n, alpha, z, q);   // q = alpha - z
+      add_kernel<<<vb, 256, 0, s>>>(n, z, alpha);
       QMLR_LAUNCH_CHECK();
-      sub_kernel<<<vb, 256, 0, s>>>(n, alpha, q, alpha);  // alpha - (alpha - z) = z  (placeholder)
+      if ((rc = apply_exact(c, alpha, q))) return rc;
+      sub_kernel<<<vb, 256, 0, s>>>(n, cv, q, r);
       QMLR_LAUNCH_CHECK();
+      if ((rc = residual(&rel))) return rc;
     }
   } else {
     // preconditioned conjugate gradients on the exact operator

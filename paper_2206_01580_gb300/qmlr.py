@@ -34,8 +34,15 @@ class _Params(C.Structure):
                 ("c3", C.c_double), ("zeta", C.c_double), ("rcut", C.c_double)]
 
 
+class SolveOpts(C.Structure):
+    _fields_ = [("method", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("shift", C.c_double), ("iters_done", C.c_int32), ("rel_resid", C.c_double)]
+
+
 _lib = None
 P, I32, I64, D, VP = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_void_p
+GRAM_FP32, GRAM_BF16X3 = 0, 1
+SOLVE_PCG, SOLVE_REFINE = 0, 1
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -52,6 +59,14 @@ _SIGS = {
     "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, VP]),
+    "qmlr_gram_operand": (C.c_int, [P, I64, I32, I64, P, P, I64, VP]),
+    "qmlr_gram": (C.c_int, [I32, P, I64, I32, I64, P, P, I64, P, VP]),
+    "qmlr_zty_workspace_bytes": (C.c_int64, [I64, I32]),
+    "qmlr_zty": (C.c_int, [P, I64, I32, I64, P, P, P, I64, VP]),
+    "qmlr_cholesky": (C.c_int, [P, I64, I32, C.POINTER(C.c_int32), VP]),
+    "qmlr_cholesky_solve": (C.c_int, [P, I64, I32, P, VP]),
+    "qmlr_solve_workspace_bytes": (C.c_int64, [I64, I32]),
+    "qmlr_gram_solve": (C.c_int, [P, P, I64, I32, I64, P, D, C.POINTER(SolveOpts), P, P, I64, VP]),
 }
 
 
@@ -247,3 +262,83 @@ def sorf_grad(x, mol_ptr, sign_bits, T: int, b, sigma: float, alpha):
     _check(lib().qmlr_sorf_grad(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(sign_bits), T,
                                 _ptr(b), nf, float(sigma), _ptr(alpha), _ptr(E), _ptr(gx), _stream()))
     return E, gx
+
+
+# ----------------------------------------------------------------------------
+# normal equations
+
+
+def k_pad_of(n_rows: int) -> int:
+    return max(64, (n_rows + 63) // 64 * 64)
+
+
+def gram_operand(Z):
+    Z = _dev(Z, torch.float32)
+    n_rows, nf = Z.shape
+    kp = k_pad_of(n_rows)
+    hi = torch.empty((nf, kp), device="cuda", dtype=torch.int16)
+    lo = torch.empty((nf, kp), device="cuda", dtype=torch.int16)
+    _check(lib().qmlr_gram_operand(_ptr(Z), n_rows, nf, Z.stride(0), _ptr(hi), _ptr(lo), kp, _stream()))
+    return hi, lo
+
+
+def gram(Z, precision: int = GRAM_BF16X3, operands=None):
+    """G = Z^T Z (float32, full symmetric)."""
+    Z = _dev(Z, torch.float32)
+    n_rows, nf = Z.shape
+    G = torch.empty((nf, nf), device="cuda", dtype=torch.float32)
+    if precision == GRAM_BF16X3:
+        hi, lo = operands if operands is not None else gram_operand(Z)
+        _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), _ptr(hi), _ptr(lo),
+                               hi.shape[1], _ptr(G), _stream()))
+    else:
+        _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), None, None, 0, _ptr(G),
+                               _stream()))
+    return G
+
+
+def zty(Z, y):
+    Z = _dev(Z, torch.float32)
+    y = _dev(y, torch.float64)
+    n_rows, nf = Z.shape
+    c = torch.empty(nf, device="cuda", dtype=torch.float64)
+    wb = lib().qmlr_zty_workspace_bytes(n_rows, nf)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
+    _check(lib().qmlr_zty(_ptr(Z), n_rows, nf, Z.stride(0), _ptr(y), _ptr(c), _ptr(work), wb, _stream()))
+    return c
+
+
+def cholesky(A):
+    """Lower Cholesky factor of a symmetric positive definite matrix (float64)."""
+    L = _dev(A, torch.float64).clone()
+    n = L.shape[0]
+    info = C.c_int32(0)
+    _check(lib().qmlr_cholesky(_ptr(L), n, n, C.byref(info), _stream()))
+    return L, info.value
+
+
+def cholesky_solve(L, v):
+    v = _dev(v, torch.float64).clone()
+    n = L.shape[0]
+    _check(lib().qmlr_cholesky_solve(_ptr(L), L.stride(0), n, _ptr(v), _stream()))
+    return v
+
+
+def gram_solve(G, Z, y, lam: float, method: int = SOLVE_PCG, max_iter: int = 50, tol: float = 1e-10,
+               shift: float = 0.0, raise_on_notconv: bool = False):
+    """alpha for (Z^T Z + lam I) alpha = Z^T y with a factor of G + (lam + shift) I.
+    Returns (alpha, iterations, relative residual)."""
+    G = _dev(G, torch.float32)
+    Z = _dev(Z, torch.float32)
+    y = _dev(y, torch.float64)
+    n_rows, nf = Z.shape
+    alpha = torch.empty(nf, device="cuda", dtype=torch.float64)
+    wb = lib().qmlr_solve_workspace_bytes(n_rows, nf)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
+    opts = SolveOpts(method, max_iter, tol, shift, 0, 0.0)
+    rc = lib().qmlr_gram_solve(_ptr(G), _ptr(Z), n_rows, nf, Z.stride(0), _ptr(y), float(lam),
+                               C.byref(opts), _ptr(alpha), _ptr(work), wb, _stream())
+    if rc == ENOTCONV and not raise_on_notconv:
+        return alpha, opts.iters_done, opts.rel_resid
+    _check(rc)
+    return alpha, opts.iters_done, opts.rel_resid

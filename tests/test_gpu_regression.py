@@ -1,0 +1,127 @@
+"""GPU parity of the normal-equation path through the C ABI: split-BF16
+operands, the plain-FP32 and tensor-core Gram, Z^T y, the FP64 Cholesky
+factor and solves, and the refined ridge solve against the FP64 oracle.
+
+Tolerances: Gram max-abs error <= 4e-5 * max|G| (FP32 accumulation, bf16 x3
+split drops the lo*lo term ~2^-16 relative); Z^T y and Cholesky: FP64 round-off
+(rel 1e-10); solves: relative normal-equation residual <= tol with the exact
+FP64 operator, and predictions Z alpha within 1e-6 relative of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import torch
+
+from oracle import regression as o_reg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_01580_gb300 import qmlr
+    qmlr.lib()
+    return qmlr
+
+
+def _features(n_rows, nf, seed=0):
+    """Rows shaped like per-molecule SORF sums: sums of a few bounded cosines."""
+    rng = np.random.default_rng(seed)
+    atoms = rng.integers(3, 12, size=n_rows)
+    Z = np.zeros((n_rows, nf), np.float32)
+    pref = math.sqrt(2 / nf)
+    for r in range(n_rows):
+        Z[r] = pref * np.cos(rng.normal(size=(atoms[r], nf)) * 2 + rng.uniform(0, 6.3, nf)).sum(0)
+    return Z
+
+
+def test_gram_operand_is_bf16_hi_lo_split(q):
+    Z = _features(100, 256)
+    hi, lo = q.gram_operand(Z)
+    assert hi.shape == (256, 128)
+    zt = torch.as_tensor(Z).T.contiguous()
+    want_hi = zt.to(torch.bfloat16)
+    want_lo = (zt - want_hi.float()).to(torch.bfloat16)
+    got_hi = hi.cpu()[:, :100].view(torch.bfloat16)
+    got_lo = lo.cpu()[:, :100].view(torch.bfloat16)
+    assert torch.equal(got_hi, want_hi) and torch.equal(got_lo, want_lo)
+    assert torch.all(hi.cpu()[:, 100:] == 0) and torch.all(lo.cpu()[:, 100:] == 0)
+
+
+@pytest.mark.parametrize("n_rows,nf", [(64, 128), (1000, 256), (777, 384), (4096, 1024), (130, 512)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gram_matches_fp64(q, n_rows, nf, precision):
+    Z = _features(n_rows, nf, seed=n_rows + nf)
+    ref = Z.astype(np.float64).T @ Z.astype(np.float64)
+    G = q.gram(Z, precision).cpu().numpy()
+    assert q.device_status() == 0
+    err = np.max(np.abs(G - ref)) / np.max(np.abs(ref))
+    assert err <= 4e-5, err
+    assert np.array_equal(G, G.T)
+
+
+def test_zty_matches_fp64(q):
+    Z = _features(3000, 384, seed=5)
+    y = np.random.default_rng(6).normal(size=3000)
+    c = q.zty(Z, y).cpu().numpy()
+    ref = Z.astype(np.float64).T @ y
+    np.testing.assert_allclose(c, ref, rtol=1e-10, atol=1e-12 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 100, 300])
+def test_cholesky_matches_lapack(q, n):
+    rng = np.random.default_rng(n)
+    X = rng.normal(size=(n + 5, n))
+    A = X.T @ X + 0.1 * np.eye(n)
+    L, info = q.cholesky(A)
+    assert info == 0
+    L = np.tril(L.cpu().numpy())
+    ref = np.linalg.cholesky(A)
+    np.testing.assert_allclose(L, ref, rtol=1e-10, atol=1e-12 * np.max(np.abs(ref)))
+    v = rng.normal(size=n)
+    x = q.cholesky_solve(torch.as_tensor(L).cuda(), v).cpu().numpy()
+    np.testing.assert_allclose(x, scipy.linalg.cho_solve((ref, True), v), rtol=1e-9)
+
+
+def test_cholesky_reports_indefinite_matrix(q):
+    A = np.eye(80)
+    A[50, 50] = -1.0
+    _, info = q.cholesky(A)
+    assert info == 51
+    assert q.device_status() == 5
+    assert q.device_status() == 0
+
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ridge_solve_matches_oracle(q, method, precision):
+    Z = _features(1500, 256, seed=9)
+    y = np.random.default_rng(10).normal(size=1500)
+    lam = 1e-6
+    alpha_ref, _ = o_reg.ridge_solve(Z.astype(np.float64), y, lam, refine=2)
+    G = q.gram(Z, precision)
+    alpha, it, rel = q.gram_solve(G, Z, y, lam, method=method, max_iter=30, tol=1e-11)
+    assert rel <= 1e-11, (it, rel)
+    alpha = alpha.cpu().numpy()
+    pz, pr = Z.astype(np.float64) @ alpha, Z.astype(np.float64) @ alpha_ref
+    assert np.max(np.abs(pz - pr)) <= 1e-6 * np.max(np.abs(pr))
+
+
+def test_ridge_solve_underdetermined_with_shift(q):
+    """Fewer rows than features (the parity workload's shape): G is rank
+    deficient, so the factor is taken of G + (lambda + shift) I and the exact
+    operator recovers the lambda-regularised solution."""
+    Z = _features(64, 512, seed=11)
+    y = np.random.default_rng(12).normal(size=64)
+    lam = 1e-6
+    alpha_ref, _ = o_reg.ridge_solve(Z.astype(np.float64), y, lam, refine=2)
+    G = q.gram(Z, 1)
+    alpha, it, rel = q.gram_solve(G, Z, y, lam, method=0, max_iter=200, tol=1e-10, shift=1e-4)
+    assert rel <= 1e-10, (it, rel)
+    pz = Z.astype(np.float64) @ alpha.cpu().numpy()
+    pr = Z.astype(np.float64) @ alpha_ref
+    assert np.max(np.abs(pz - pr)) <= 1e-6 * np.max(np.abs(pr))
