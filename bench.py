@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the SORF + FCHL19 hot path on GB300.
+
+One step = one pass of the whole path over the QM9-shaped workload
+(100 000 synthetic molecules, 3-29 atoms, ~1.77 M atoms, N_F = 16384):
+training (FCHL19 -> per-element projection -> SORF + segment sum -> split
+BF16 Gram on the tensor cores -> FP64 Cholesky + PCG on the exact operator)
+followed by energy + force prediction of the same molecules with the trained
+weights. The metric is microseconds per atom of that step (lower is better),
+with train seconds, prediction us/atom and the plain-FP32 comparison reported
+beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path is
+not sharded across GPUs here); rank 0 prints the line with max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "µs/atom E+F predict, train s at 16k feats, p50/p99 latency vs plain FP32 form"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="fraction of the 100k-molecule workload (1.0 for the reported line)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--pcg-iters", type=int, default=30)
+    ap.add_argument("--pcg-tol", type=float, default=1e-8)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) timing on a bounded sample: the reported CPU baseline
+
+def oracle_step_times(w, n_mol_sample: int, threads: int):
+    """Time the FP64 oracle's training + E+F prediction on a bounded sample of the
+    workload and extrapolate to the full workload: features and prediction scale
+    with atoms, the Gram with rows, the Cholesky solve is fixed (N_F^3)."""
+    import torch
+    torch.set_num_threads(threads)
+    from oracle import fchl19 as o_fchl19
+    from oracle import model as o_model
+    from oracle import regression as o_reg
+    mols = w.mols.subset(range(n_mol_sample))
+    p = o_fchl19.params(w.params_column, n2=w.n2, n3=w.n3)
+    t0 = time.perf_counter()
+    reps = o_fchl19.representation_batch(mols.coords, mols.elem, mols.mol_ptr, p)
+    U = o_reg.pca_bases(reps, mols.elem, 5, w.d)
+    m = o_model.sorf_model(p, U, w.signs, w.b, w.sigma)
+    t1 = time.perf_counter()
+    Z = o_model.feature_matrix(mols.coords, mols.elem, mols.mol_ptr, m)
+    t2 = time.perf_counter()
+    A, c = o_reg.normal_equations(Z, w.energies[:n_mol_sample], w.lam)
+    t3 = time.perf_counter()
+    alpha, _ = o_reg.cholesky_solve(A, c, refine=1)
+    t4 = time.perf_counter()
+    m.alpha = alpha
+    o_model.energies_forces(mols.coords, mols.elem, mols.mol_ptr, m)
+    t5 = time.perf_counter()
+    n_atoms_s = mols.n_atoms
+    full_atoms, full_rows = w.mols.n_atoms, w.mols.n_mol
+    feat = (t2 - t1) * full_atoms / n_atoms_s
+    gram = (t3 - t2) * full_rows / n_mol_sample
+    chol = t4 - t3
+    pred = (t5 - t4) * full_atoms / n_atoms_s
+    total = feat + gram + chol + pred
+    return {"total_s": total, "features_s": feat, "gram_s": gram, "solve_s": chol, "predict_s": pred,
+            "sample_molecules": n_mol_sample, "sample_atoms": n_atoms_s, "sample_wall_s": t5 - t0,
+            "train_s": feat + gram + chol, "predict_us_per_atom": pred / full_atoms * 1e6}
+
+
+# ----------------------------------------------------------------------------
+
+def build_workload(scale):
+    from paper_2206_01580_gb300 import synth
+    t = time.perf_counter()
+    w = synth.workload(1, scale=scale)
+    return w, time.perf_counter() - t
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores: each step is a bounded sample
+    (6 molecules) of the same workload, extrapolated to the whole workload."""
+    if rank != 0:
+        return
+    w, _ = build_workload(args.scale)
+    threads = os.cpu_count() or 1
+    times = []
+    for k in range(args.warmup + args.steps):
+        r = oracle_step_times(w, 6, threads)
+        if k >= args.warmup:
+            times.append(r)
+    total = statistics.mean(t["total_s"] for t in times)
+    val = total / w.mols.n_atoms * 1e6
+    line = {"metric": METRIC, "impl": "reference", "value": val, "unit": "us/atom",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
+                       "n_molecules": w.mols.n_mol, "n_atoms": w.mols.n_atoms, "n_features": w.n_features},
+            "train_s": statistics.mean(t["train_s"] for t in times),
+            "predict_us_per_atom": statistics.mean(t["predict_us_per_atom"] for t in times),
+            "cpu_baseline": {"value": val, "unit": "us/atom", "cores": threads, "kind": "oracle",
+                             "sample": f"6 molecules per step ({times[0]['sample_atoms']} atoms); features, "
+                                       "Gram rows and prediction extrapolated linearly to the workload; "
+                                       "full N_F^3 Cholesky"},
+            "e2e": {"value": val, "unit": "us/atom", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2206_01580_gb300 import pipeline, qmlr
+    from paper_2206_01580_gb300.params import from_table
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    w, gen_s = build_workload(args.scale)
+    mols = w.mols
+    n_atoms, n_mol = mols.n_atoms, mols.n_mol
+    p = from_table(w.params_column, n2=w.n2, n3=w.n3)
+    spec = pipeline.spec_from(p, w.d, w.signs, w.b, w.sigma)
+    batch = pipeline.Batch.from_host(mols.coords, mols.elem, mols.mol_ptr)
+    y = torch.as_tensor(w.energies).cuda()
+
+    # setup (untimed): PCA basis on the device, model handle for prediction
+    rep, perm, offs = pipeline.representations(batch, spec)
+    U = pipeline.fit_pca(rep, perm, offs, spec)
+    model = qmlr.Model(p, batch.max_atoms, U, w.signs, w.n_transform, w.b, w.sigma,
+                       np.zeros(w.n_features, np.float32))
+    model.reserve(n_atoms)
+    del rep, perm, offs
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+
+    def step(b: pipeline.Batch, yv, precision=qmlr.GRAM_BF16X6, timing=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        ev[0].record(stream)
+        rep, perm, offs = pipeline.representations(b, spec)
+        ev[1].record(stream)
+        x = qmlr.project(rep, p.rep_dim, perm, offs, p.n_el, U)
+        ev[2].record(stream)
+        Z = qmlr.sorf(x, b.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
+        ev[3].record(stream)
+        G = qmlr.gram(Z, precision)
+        ev[4].record(stream)
+        alpha, it, rel = qmlr.gram_solve(G, Z, yv, w.lam, method=qmlr.SOLVE_PCG,
+                                         max_iter=args.pcg_iters, tol=args.pcg_tol)
+        ev[5].record(stream)
+        model.set_alpha_device(alpha)
+        E, F = model.predict(b.coords, b.elem, b.mol_ptr)
+        ev[6].record(stream)
+        if timing is not None:
+            torch.cuda.synchronize()
+            so = qmlr.last_solve
+            timing.append({"fchl19": ev[0].elapsed_time(ev[1]), "project": ev[1].elapsed_time(ev[2]),
+                           "sorf_Z": ev[2].elapsed_time(ev[3]), "gram": ev[3].elapsed_time(ev[4]),
+                           "solve": ev[4].elapsed_time(ev[5]), "factor": so.factor_ms,
+                           "refine": so.refine_ms, "predict_ef": ev[5].elapsed_time(ev[6]),
+                           "total": ev[0].elapsed_time(ev[6]), "pcg_iters": it, "rel_resid": rel})
+        return alpha, E, F
+
+    for _ in range(args.warmup):
+        step(batch, y)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: device-resident inputs
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = qmlr.launch_count()
+    t_ev0 = torch.cuda.Event(enable_timing=True)
+    t_ev1 = torch.cuda.Event(enable_timing=True)
+    timing = []
+    t_ev0.record(stream)
+    for _ in range(args.steps):
+        alpha, E, F = step(batch, y, timing=timing)
+    t_ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = qmlr.launch_count() - launches0
+    clocks = sampler.stop()
+    ms = t_ev0.elapsed_time(t_ev1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    st = {k: statistics.median(t[k] for t in timing) for k in timing[0]}
+    mae = float(torch.mean(torch.abs(E - y)).item())
+
+    # ---------------- end to end: host buffers in, results out, copies timed
+    h_coords = torch.as_tensor(mols.coords.astype(np.float32)).pin_memory()
+    h_elem = torch.as_tensor(mols.elem.astype(np.int32)).pin_memory()
+    h_ptr = torch.as_tensor(mols.mol_ptr.astype(np.int32)).pin_memory()
+    h_y = torch.as_tensor(w.energies.astype(np.float64)).pin_memory()
+    out_alpha = torch.empty(w.n_features, dtype=torch.float64).pin_memory()
+    out_E = torch.empty(n_mol, dtype=torch.float64).pin_memory()
+    out_F = torch.empty((n_atoms, 3), dtype=torch.float32).pin_memory()
+    h2d = (h_coords.numel() * 4 + h_elem.numel() * 4 + h_ptr.numel() * 4 + h_y.numel() * 8)
+    d2h = out_alpha.numel() * 8 + out_E.numel() * 8 + out_F.numel() * 4
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        b2 = pipeline.Batch(h_coords.cuda(non_blocking=True), h_elem.cuda(non_blocking=True),
+                            h_ptr.cuda(non_blocking=True), batch.max_atoms)
+        y2 = h_y.cuda(non_blocking=True)
+        a2, E2, F2 = step(b2, y2)
+        out_alpha.copy_(a2, non_blocking=True)
+        out_E.copy_(E2, non_blocking=True)
+        out_F.copy_(F2, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    # ---------------- plain FP32 form (FP32 SIMT Gram, same solve), one step
+    plain = None
+    if not args.no_plain:
+        pt = []
+        _, Ep, _ = step(batch, y, precision=qmlr.GRAM_FP32, timing=pt)
+        plain = {"gram_ms": pt[0]["gram"], "train_s": (pt[0]["total"] - pt[0]["predict_ef"]) / 1e3,
+                 "step_ms": pt[0]["total"], "pcg_iters": pt[0]["pcg_iters"],
+                 "rel_resid": pt[0]["rel_resid"],
+                 "train_mae_eV": float(torch.mean(torch.abs(Ep - y)).item())}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dominant kernel
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    nf = w.n_features
+    rows = n_mol
+    chol_flops = nf ** 3 / 3.0
+    gram_flops = 3.0 * rows * nf * nf          # three bf16 products, symmetric half x 2 flop/MAC
+    fp64_peak = 1250.0                          # GFLOP/s nominal (FP64 units x clock, GB300)
+    stages = {k: st[k] for k in ("fchl19", "project", "sorf_Z", "gram", "factor", "refine", "predict_ef")}
+    dom = max(stages, key=stages.get)
+    if dom == "factor":
+        ach = chol_flops / (st["factor"] * 1e-3) / 1e12
+        roof = {"kernel": "fp64 blocked Cholesky (trailing update dominant)", "bound": "alu",
+                "achieved": ach, "peak": fp64_peak / 1e3, "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e3),
+                "traffic": None, "peak_source": "nominal FP64 rate of the profiling recipe (1.25 TFLOP/s)"}
+    elif dom == "gram":
+        pk = peaks.get("bf16_tflops_sustained", 1707.8)
+        ach = gram_flops / (st["gram"] * 1e-3) / 1e12
+        roof = {"kernel": "gram_bf16x3 (tcgen05)", "bound": "tensor", "achieved": ach, "peak": pk,
+                "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    line = {
+        "metric": METRIC, "value": ms * 1e3 / n_atoms, "unit": "us/atom", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 features, bf16x6 gram, f64 solve", "data": "synthetic",
+        "config": {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
+                   "n_molecules": n_mol, "n_atoms": n_atoms, "n_features": nf, "d": w.d,
+                   "n_transform": w.n_transform, "gram": "3-way bf16 split, 6 tcgen05 products, per-K-block FP32 Kahan promotion",
+                   "solve": "fp64 cholesky + pcg (exact fp64 operator)",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (rep 5.5 GB, Z 6.6 GB)"},
+        "train_s": (st["total"] - st["predict_ef"]) / 1e3,
+        "predict_us_per_atom": st["predict_ef"] * 1e3 / n_atoms,
+        "stages_ms": {k: round(v, 3) for k, v in st.items() if k not in ("pcg_iters", "rel_resid")},
+        "pcg": {"iters": st["pcg_iters"], "rel_resid": st["rel_resid"]},
+        "train_mae_eV": mae,
+        "roofline": roof,
+        "plain_fp32": plain,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_ms * 1e3 / n_atoms, "unit": "us/atom", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "workload_gen_s": gen_s,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        threads = os.cpu_count() or 1
+        cb = oracle_step_times(w, 6, threads)
+        line["cpu_baseline"] = {"value": cb["total_s"] / n_atoms * 1e6, "unit": "us/atom", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"{cb['sample_molecules']} molecules ({cb['sample_atoms']} atoms); "
+                                          "features, Gram rows and prediction extrapolated linearly to the "
+                                          "workload; full N_F^3 Cholesky",
+                                "train_s": cb["train_s"], "predict_us_per_atom": cb["predict_us_per_atom"]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

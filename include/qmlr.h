@@ -47,6 +47,9 @@ const char* qmlr_version(void);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* qmlr_last_error(void);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all threads). */
+int64_t qmlr_launch_count(void);
+
 /*
  * Synchronises `stream`, then reads and clears the device-side error word of
  * the current device. *host_code = 0 if no kernel recorded an error since the
@@ -204,28 +207,31 @@ int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_
  * by LU in FP64 and builds Z^T Z in FP64 or FP32 with Kahan summation).
  * ------------------------------------------------------------------------ */
 enum {
-  QMLR_GRAM_FP32 = 0,   /* plain FP32 SIMT product (comparison form) */
-  QMLR_GRAM_BF16X3 = 1  /* tensor cores: Z = H + L (bf16 hi/lo), H^T H + H^T L + L^T H, FP32 accumulate */
+  QMLR_GRAM_FP32 = 0,   /* plain FP32 SIMT product (comparison form, no compensation) */
+  QMLR_GRAM_BF16X3 = 1, /* tensor cores, 2-way BF16 split S0+S1: S0'S0 + S0'S1 + S1'S0 (~2^-16 rel.) */
+  QMLR_GRAM_BF16X6 = 2  /* tensor cores, 3-way BF16 split: the six products of order <= 2 (~2^-24 rel.) */
 };
 
 /*
  * Split-precision Gram operand, transposed (feature-major, rows contiguous):
- *   zt_hi[f][r] = bf16(Z[r][f]),  zt_lo[f][r] = bf16(Z[r][f] - zt_hi[f][r])
- *   Z      float [n_rows][ldz]
- *   zt_hi, zt_lo  bf16 bit patterns [n_features][k_pad]; k_pad >= n_rows, k_pad % 64 == 0;
- *          rows n_rows..k_pad-1 are written as zeros.
+ *   S0 = bf16(Z), S1 = bf16(Z - S0), S2 = bf16(Z - S0 - S1)   (round to nearest even)
+ *   zt[q][f][r] = S_q[r][f] for q < n_split (2 or 3); bf16 bit patterns,
+ *   [n_split][n_features][k_pad]; k_pad >= n_rows, k_pad % 64 == 0; rows
+ *   n_rows..k_pad-1 are written as zeros.
+ *   Z float [n_rows][ldz]
  */
 int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
-                      uint16_t* zt_hi, uint16_t* zt_lo, int64_t k_pad, void* stream);
+                      int32_t n_split, uint16_t* zt, int64_t k_pad, void* stream);
 
 /*
  * G = Z^T Z as a full symmetric float [n_features][n_features] matrix.
- *   QMLR_GRAM_FP32:   reads Z [n_rows][ldz] (zt_* may be NULL)
- *   QMLR_GRAM_BF16X3: reads zt_hi, zt_lo from qmlr_gram_operand (Z may be NULL);
- *                     n_features % 128 == 0.
+ *   QMLR_GRAM_FP32:   reads Z [n_rows][ldz] (zt may be NULL)
+ *   QMLR_GRAM_BF16X3: reads zt with n_split = 2; QMLR_GRAM_BF16X6: n_split = 3
+ *                     (Z may be NULL); n_features % 128 == 0.
+ * Deterministic: every element is summed in a fixed order.
  */
 int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
-              const uint16_t* zt_hi, const uint16_t* zt_lo, int64_t k_pad, float* G, void* stream);
+              const uint16_t* zt, int64_t k_pad, float* G, void* stream);
 
 /* c = Z^T y in FP64 (y double [n_rows], c double [n_features]); fixed-order sums. */
 int64_t qmlr_zty_workspace_bytes(int64_t n_rows, int32_t n_features);
@@ -252,9 +258,14 @@ typedef struct qmlr_solve_opts {
   int32_t method;      /* QMLR_SOLVE_PCG or QMLR_SOLVE_REFINE */
   int32_t max_iter;    /* refinement iterations after the first solve (>= 0) */
   double tol;          /* target ||c - A alpha|| / ||c|| */
-  double shift;        /* >= 0, added to the diagonal of the factorised matrix only */
+  double shift;        /* added to the diagonal of the factorised matrix only: >= 0 absolute,
+                          < 0 relative (|shift| * max_i G_ii); raised tenfold (up to 8 times)
+                          when a pivot is not positive */
   int32_t iters_done;  /* out: refinement iterations run */
   double rel_resid;    /* out: final ||c - A alpha|| / ||c|| with the exact operator */
+  double shift_used;   /* out: the shift of the factor that was used */
+  float factor_ms;     /* out: device time of assembly + Cholesky factorisation (CUDA events) */
+  float refine_ms;     /* out: device time of the first solve and the refinement */
 } qmlr_solve_opts;
 
 /* Device workspace bytes of qmlr_gram_solve. */
@@ -270,11 +281,69 @@ int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features);
  * Steps: c = Z^T y; FP64 Cholesky of G + (lambda + shift) I; alpha = factor
  * solve of c; then up to max_iter refinement steps against the exact operator.
  * QMLR_ENOTCONV: tolerance not reached (alpha and opts->rel_resid still written).
- * QMLR_EINVAL with a message when the factorisation meets a non-positive pivot.
+ * QMLR_EINVAL with a message when the factorisation still meets a non-positive
+ * pivot after the shift escalation.
  */
 int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, int32_t n_features,
                     int64_t ldz, const double* y, double lambda, qmlr_solve_opts* opts,
                     double* alpha, void* work, int64_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Per-element PCA basis (SORF section: U_e from the SVD of the element's
+ * representations; setup step, run once per model).
+ * ------------------------------------------------------------------------ */
+
+/* Device workspace bytes of qmlr_pca_fit. */
+int64_t qmlr_pca_workspace_bytes(int32_t rep_ld, int32_t d);
+
+/*
+ * U[e] (float [n_el][rep_dim][d]) = leading d eigenvectors of
+ * C_e = sum_i rho_i rho_i^T over the first max_per_element atoms of element e
+ * in perm order (perm, elem_offsets from qmlr_group_by_element), computed in
+ * FP64 by randomized subspace iteration + Rayleigh-Ritz + Jacobi. Columns are
+ * ordered by descending eigenvalue; each column's largest-magnitude entry is
+ * positive; columns with eigenvalue <= 1e-12 of the largest (and all columns
+ * of an element without atoms) are zero. Synchronous (reads elem_offsets).
+ * d <= 128.
+ */
+int qmlr_pca_fit(const float* rep, int32_t rep_ld, int32_t rep_dim, const int32_t* perm,
+                 const int32_t* elem_offsets, int32_t n_el, int32_t max_per_element, int32_t d,
+                 float* U, void* work, int64_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Trained model and energy + force prediction (atomic energy partition
+ * E = sum_I alpha^T z(rho_I), RFF section; forces by the SORF and FCHL19
+ * backward passes, Computational Details).
+ * ------------------------------------------------------------------------ */
+typedef struct qmlr_model qmlr_model;
+
+/*
+ * Copies the model to the current device. Host arrays (read once):
+ *   host_U         float [n_el][rep_dim][d]
+ *   host_sign_bits uint32 [N_F/d][T][ceil(d/32)]
+ *   host_b         float [N_F]
+ *   host_alpha     float [N_F]
+ * max_mol_atoms bounds the atoms per molecule of every later batch.
+ */
+int qmlr_model_create(const qmlr_fchl19_params* p, int32_t max_mol_atoms, const float* host_U,
+                      int32_t d, const uint32_t* host_sign_bits, int32_t T, const float* host_b,
+                      int32_t n_features, double sigma, const float* host_alpha, qmlr_model** out);
+int qmlr_model_destroy(qmlr_model* m);
+int qmlr_model_set_alpha(qmlr_model* m, const float* host_alpha);
+/* Replace alpha from a device FP64 vector [N_F] (e.g. the output of qmlr_gram_solve); asynchronous. */
+int qmlr_model_set_alpha_device(qmlr_model* m, const double* alpha, void* stream);
+
+/* Allocates (or grows) the model's prediction workspace for batches of up to max_atoms atoms. */
+int qmlr_model_reserve(qmlr_model* m, int32_t max_atoms);
+
+/*
+ * Energies (double [n_mol]) and forces F = -dE/dr (float [n_atoms][3];
+ * NULL = energies only) for a CSR batch of molecules; device inputs/outputs,
+ * asynchronous on `stream`, no allocation (n_atoms <= reserved capacity).
+ */
+int qmlr_predict_ef(qmlr_model* m, const float* coords, const int32_t* elem,
+                    const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms, double* energies,
+                    float* forces, void* stream);
 
 #ifdef __cplusplus
 }

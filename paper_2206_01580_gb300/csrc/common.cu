@@ -1,6 +1,8 @@
 // Error reporting and small runtime helpers of the qmlr library.
 #include "common.cuh"
 
+#include <atomic>
+
 namespace qmlr {
 
 static __device__ int g_device_error = 0;
@@ -18,6 +20,9 @@ int* device_error_ptr() {
 }
 
 static thread_local char t_last_error[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -52,3 +57,5 @@ extern "C" int qmlr_device_status(void* stream, int32_t* host_code) {
   }
   return QMLR_OK;
 }
+
+extern "C" int64_t qmlr_launch_count(void) { return qmlr::g_launches.load(); }

@@ -54,9 +54,14 @@ __device__ __forceinline__ void record_device_error(int* err, int code) {
     }                                                                           \
   } while (0)
 
-// Launch check: reports the launch error (if any) and returns QMLR_ECUDA.
+// Number of kernels the library has launched (qmlr_launch_count()).
+void count_launch();
+
+// Launch check: counts the launch, reports the launch error (if any) and
+// returns QMLR_ECUDA.
 #define QMLR_LAUNCH_CHECK()                                                     \
   do {                                                                          \
+    ::qmlr::count_launch();                                                     \
     cudaError_t _e = cudaGetLastError();                                        \
     if (_e != cudaSuccess) {                                                    \
       ::qmlr::set_error("kernel launch failed: %s (%s:%d)",                     \

@@ -8,10 +8,10 @@
 // Forms built here:
 // * QMLR_GRAM_FP32  - plain FP32 SIMT product (the comparison form; no
 //                     compensation), upper-triangle tiles mirrored.
-// * QMLR_GRAM_BF16X3 - split-precision tensor-core product (gram_tc.cu):
-//                     Z = H + L with H = bf16(Z), L = bf16(Z - H);
-//                     G ~= H^T H + H^T L + L^T H with FP32 accumulation in TMEM.
-// The operand kernel below writes H and L transposed (feature-major, rows
+// * QMLR_GRAM_BF16X3 / QMLR_GRAM_BF16X6 - split-precision tensor-core
+//                     products (gram_tc.cu) over a 2-way / 3-way BF16 split of
+//                     Z, FP32 accumulation in TMEM.
+// The operand kernel below writes the splits transposed (feature-major, rows
 // contiguous: the K-major layout the tensor-core kernel reads with TMA).
 #include "common.cuh"
 #include <cuda_bf16.h>
@@ -19,12 +19,13 @@
 namespace qmlr {
 
 // ---------------------------------------------------------------------------
-// split + transpose: Z [n_rows][ldz] fp32 -> Hᵀ, Lᵀ [n_features][k_pad] bf16
+// split + transpose: Z [n_rows][ldz] fp32 -> St[q] [n_features][k_pad] bf16, q < n_split:
+//   S0 = bf16(z), S1 = bf16(z - S0), S2 = bf16(z - S0 - S1)   (round to nearest even)
 constexpr int kTT = 32;
 
 __global__ void gram_operand_kernel(const float* __restrict__ Z, long n_rows, int n_features,
-                                    long ldz, __nv_bfloat16* __restrict__ hi,
-                                    __nv_bfloat16* __restrict__ lo, long k_pad) {
+                                    long ldz, int n_split, __nv_bfloat16* __restrict__ st,
+                                    long k_pad) {
   __shared__ float tile[kTT][kTT + 1];
   const long r0 = (long)blockIdx.x * kTT;
   const int f0 = blockIdx.y * kTT;
@@ -35,15 +36,17 @@ __global__ void gram_operand_kernel(const float* __restrict__ Z, long n_rows, in
     tile[j][tx] = (r < n_rows && f < n_features) ? __ldg(Z + r * ldz + f) : 0.f;
   }
   __syncthreads();
+  const long part = (long)n_features * k_pad;
   for (int j = ty; j < kTT; j += 8) {
     const int f = f0 + j;
     const long r = r0 + tx;
     if (f < n_features && r < k_pad) {
-      const float v = tile[tx][j];
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-      hi[(long)f * k_pad + r] = h;
-      lo[(long)f * k_pad + r] = l;
+      float v = tile[tx][j];
+      for (int q = 0; q < n_split; ++q) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        st[q * part + (long)f * k_pad + r] = h;
+        v -= __bfloat162float(h);
+      }
     }
   }
 }
@@ -140,30 +143,28 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int n_parts, i
   out[f] = acc;
 }
 
-int gram_bf16x3_tc(const uint16_t* zt_hi, const uint16_t* zt_lo, long k_pad, int n_features,
-                   float* G, cudaStream_t s);
+int gram_split_tc(int n_split, const uint16_t* zt, long k_pad, int n_features, float* G, cudaStream_t s);
 
 }  // namespace qmlr
 
 using namespace qmlr;
 
 extern "C" int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
-                                 uint16_t* zt_hi, uint16_t* zt_lo, int64_t k_pad, void* stream) {
+                                 int32_t n_split, uint16_t* zt, int64_t k_pad, void* stream) {
   QMLR_REQUIRE(n_rows >= 0 && n_features >= 1 && ldz >= n_features, "bad Z shape");
+  QMLR_REQUIRE(n_split == 2 || n_split == 3, "n_split must be 2 or 3 (got %d)", n_split);
   QMLR_REQUIRE(k_pad >= n_rows && k_pad % 64 == 0, "k_pad must be >= n_rows and a multiple of 64");
-  QMLR_REQUIRE(zt_hi && zt_lo && (n_rows == 0 || Z), "NULL pointer argument");
+  QMLR_REQUIRE(zt && (n_rows == 0 || Z), "NULL pointer argument");
   if (k_pad == 0) return QMLR_OK;
   dim3 grid((unsigned)((k_pad + kTT - 1) / kTT), (n_features + kTT - 1) / kTT);
   gram_operand_kernel<<<grid, dim3(32, 8), 0, as_stream(stream)>>>(
-      Z, n_rows, n_features, ldz, reinterpret_cast<__nv_bfloat16*>(zt_hi),
-      reinterpret_cast<__nv_bfloat16*>(zt_lo), k_pad);
+      Z, n_rows, n_features, ldz, n_split, reinterpret_cast<__nv_bfloat16*>(zt), k_pad);
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }
 
 extern "C" int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int32_t n_features,
-                         int64_t ldz, const uint16_t* zt_hi, const uint16_t* zt_lo, int64_t k_pad,
-                         float* G, void* stream) {
+                         int64_t ldz, const uint16_t* zt, int64_t k_pad, float* G, void* stream) {
   QMLR_REQUIRE(n_features >= 1 && G, "bad arguments");
   cudaStream_t s = as_stream(stream);
   if (precision == QMLR_GRAM_FP32) {
@@ -173,11 +174,11 @@ extern "C" int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int3
     QMLR_LAUNCH_CHECK();
     return QMLR_OK;
   }
-  if (precision == QMLR_GRAM_BF16X3) {
-    QMLR_REQUIRE(zt_hi && zt_lo, "split operands are NULL");
+  if (precision == QMLR_GRAM_BF16X3 || precision == QMLR_GRAM_BF16X6) {
+    QMLR_REQUIRE(zt, "split operand is NULL");
     QMLR_REQUIRE(k_pad % 64 == 0 && k_pad >= 0, "k_pad must be a multiple of 64");
-    QMLR_REQUIRE(n_features % 128 == 0, "BF16X3 Gram needs n_features % 128 == 0 (got %d)", n_features);
-    return gram_bf16x3_tc(zt_hi, zt_lo, k_pad, n_features, G, s);
+    QMLR_REQUIRE(n_features % 128 == 0, "tensor-core Gram needs n_features %% 128 == 0 (got %d)", n_features);
+    return gram_split_tc(precision == QMLR_GRAM_BF16X3 ? 2 : 3, zt, k_pad, n_features, G, s);
   }
   set_error("unknown Gram precision %d", precision);
   return QMLR_EINVAL;

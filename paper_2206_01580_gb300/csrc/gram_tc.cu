@@ -2,17 +2,23 @@
 //
 // The normal equations' Z^T Z (RFF section of the paper; "the dominant
 // term", built in FP32 with Kahan summation in the paper) is the one dense
-// contraction of the method, so it runs on the 5th-generation tensor cores:
-//   Z = H + L,  H = bf16(Z), L = bf16(Z - H)
-//   G ~= H^T H + H^T L + L^T H      (FP32 accumulation in tensor memory)
-// Operands are the transposed split matrices Zt_hi, Zt_lo [N_F][K] (rows of
-// Z contiguous: K-major), loaded by TMA into 128-byte-swizzled shared memory.
+// contraction of the method, so it runs on the 5th-generation tensor cores
+// with a split-precision BF16 representation of Z:
+//   2-way: Z = S0 + S1,       G ~= S0'S0 + S0'S1 + S1'S0                 (~2^-16 rel.)
+//   3-way: Z = S0 + S1 + S2,  G ~= S0'S0 + S0'S1 + S1'S0 + S0'S2 + S2'S0 + S1'S1
+//                                                                         (~2^-24 rel.)
+// with S0 = bf16(Z), S1 = bf16(Z - S0), S2 = bf16(Z - S0 - S1) and FP32
+// accumulation in tensor memory. Operands are the transposed splits
+// St [N_F][K] (rows of Z contiguous: K-major), loaded by TMA into
+// 128-byte-swizzled shared memory.
 //
-// One CTA computes a 128 x 256 tile of G (rows i0.., columns j0..) for the
-// upper triangle only: warp 0 lane 0 issues TMA copies into a 2-stage ring
-// (full/empty mbarriers), warp 1 lane 0 issues 3 x 4 tcgen05.mma per 64-deep
-// K block into one TMEM accumulator (256 columns), and all four warps drain
-// TMEM with tcgen05.ld and write G[i][j] and its mirror G[j][i] for j >= i.
+// One CTA computes a 128 x 128 tile of G for the upper triangle only: one
+// thread issues TMA copies into a ring of shared-memory stages (full/empty
+// mbarriers), one thread issues the split products (tcgen05.mma, 4 per 64-deep
+// K block each) into one of two TMEM accumulators, and eight warps promote
+// every K block's accumulator into FP32 Kahan sums in registers (the tensor
+// cores' accumulator adds truncate; promoting per K block keeps their error
+// to one block's worth), then write G[i][j] and its mirror G[j][i] for j >= i.
 // Every mbarrier wait is bounded by a clock budget: on expiry the CTA records
 // a device error, waits (bounded) for its own copies, frees TMEM and returns.
 #include "common.cuh"
@@ -25,14 +31,21 @@ namespace qmlr {
 namespace tc {
 
 constexpr int BM = 128;          // tile rows (features i)
-constexpr int BN = 256;          // tile columns (features j)
 constexpr int BK = 64;           // K block: 64 bf16 = 128 bytes (one swizzle row)
-constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;        // 16 KB per split part
-constexpr int B_BYTES = BN * BK * 2;        // 32 KB per split part
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB
-constexpr int TMEM_COLS = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int A_BYTES = BM * BK * 2;        // 16 KB per split part and 128 rows
+
+template <int S>
+struct Cfg {
+  static constexpr int BN = 128;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = S * A_BYTES + S * B_BYTES;   // 64 KB (2-way), 96 KB (3-way)
+  static constexpr int STAGES_N = S == 2 ? 3 : 2;
+  static constexpr int SMEM_BYTES = STAGES_N * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  // products (a-part, b-part) of the split expansion kept
+  static constexpr int NP = S == 2 ? 3 : 6;
+};
+__device__ __constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
+__device__ __constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -46,6 +59,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -122,24 +139,39 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-__global__ void __launch_bounds__(128, 1)
-gram_bf16x3_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-                   int n_features, int k_blocks, int tiles_j, float* __restrict__ G, int* err) {
+// Warp roles (576 threads): warps 0-15 drain the accumulators (warp w reads TMEM
+// lanes 32*(w%4).. and columns 32*(w/4)..), warp 16 lane 0 issues TMA, warp 17
+// lane 0 issues MMAs. Each 64-deep K block is accumulated into a fresh TMEM
+// accumulator (two, used alternately) and promoted into FP32 Kahan sums held
+// in the drain threads' registers, so that the tensor cores' accumulator adds
+// only ever sum one K block.
+constexpr int kDrainWarps = 16;
+constexpr int kDrainCols = 128 / (kDrainWarps / 4);   // columns per drain thread
+constexpr int kThreads = 32 * (kDrainWarps + 2);
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+                  const __grid_constant__ CUtensorMap map2, int n_features, int k_blocks, int tiles_j,
+                  float* __restrict__ G, int* err) {
+  using C = Cfg<S>;
+  constexpr int BN = C::BN, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES, NST = C::STAGES_N;
+  const CUtensorMap* maps[3] = {&map0, &map1, &map2};
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES);
+  uint64_t* empty = full + NST;
+  uint64_t* accf = empty + NST;        // [2] accumulator ready (MMA -> drain)
+  uint64_t* acce = accf + 2;           // [2] accumulator drained (drain -> MMA)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* never_abort = abort + 1;   // a flag nobody sets: waits bounded by the clock only
+  volatile int* never_abort = abort + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // tile (bi, bj): upper-triangle tiles of 128 x 256, enumerated row-major over bi
   int t = blockIdx.x, bi = 0;
   for (;;) {
-    const int first = (bi * BM) / BN;          // first column tile reaching the diagonal
+    const int first = (bi * BM) / BN;
     const int cnt = tiles_j - first;
     if (t < cnt) {
       t += first;
@@ -152,18 +184,21 @@ gram_bf16x3_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_cons
   const int i0 = bi * BM, j0 = bj * BN;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int q = 0; q < NST; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
     }
-    mbar_init(accum, 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], kDrainWarps);
+    }
     *abort = 0;
     *never_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS));
+                 "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -171,99 +206,133 @@ gram_bf16x3_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_cons
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
 
-  int last_round[STAGES];  // producer: round of the last TMA batch issued per stage (-1 = none)
+  int last_round[NST];
 #pragma unroll
-  for (int s = 0; s < STAGES; ++s) last_round[s] = -1;
-  if (warp == 0 && lane == 0) {
+  for (int q = 0; q < NST; ++q) last_round[q] = -1;
+
+  if (warp == kDrainWarps && lane == 0) {
     // ---------------- TMA producer
     for (int kb = 0; kb < k_blocks; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t round = kb / STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1, abort)) {
+      const int st = kb % NST;
+      const uint32_t round = kb / NST;
+      if (kb >= NST && !mbar_wait(&empty[st], (round - 1) & 1, abort)) {
         record_device_error(err, DEV_TIMEOUT);
         *abort = 1;
         break;
       }
-      uint8_t* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
+      uint8_t* sp = smem + st * STAGE_BYTES;
+      mbar_expect_tx(&full[st], STAGE_BYTES);
       const int k = kb * BK;
-      tma_load_2d(st, &map_hi, &full[s], k, i0);
-      tma_load_2d(st + A_BYTES, &map_lo, &full[s], k, i0);
-      tma_load_2d(st + 2 * A_BYTES, &map_hi, &full[s], k, j0);
-      tma_load_2d(st + 2 * A_BYTES + A_BYTES, &map_hi, &full[s], k, j0 + BM);
-      tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_lo, &full[s], k, j0);
-      tma_load_2d(st + 2 * A_BYTES + B_BYTES + A_BYTES, &map_lo, &full[s], k, j0 + BM);
-      last_round[s] = (int)round;
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        tma_load_2d(sp + q * A_BYTES, maps[q], &full[st], k, i0);
+#pragma unroll
+        for (int h = 0; h < BN / BM; ++h)
+          tma_load_2d(sp + S * A_BYTES + q * B_BYTES + h * A_BYTES, maps[q], &full[st], k, j0 + h * BM);
+      }
+      last_round[st] = (int)round;
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp == kDrainWarps + 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    int pa[C::NP], pb[C::NP];
+#pragma unroll
+    for (int q = 0; q < C::NP; ++q) {
+      pa[q] = kProdA[q];
+      pb[q] = kProdB[q];
+    }
     for (int kb = 0; kb < k_blocks; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t round = kb / STAGES;
-      if (!mbar_wait(&full[s], round & 1, abort)) {
+      const int st = kb % NST;
+      const uint32_t round = kb / NST;
+      const int buf = kb & 1;
+      const uint32_t use = kb >> 1;
+      if (!mbar_wait(&full[st], round & 1, abort) ||
+          (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1, abort))) {
         record_device_error(err, DEV_TIMEOUT);
         *abort = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint8_t* st = smem + s * STAGE_BYTES;
-      const uint8_t* a_hi = st;
-      const uint8_t* a_lo = st + A_BYTES;
-      const uint8_t* b_hi = st + 2 * A_BYTES;
-      const uint8_t* b_lo = st + 2 * A_BYTES + B_BYTES;
+      const uint8_t* sp = smem + st * STAGE_BYTES;
+      const uint32_t d = tmem + buf * BN;
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const int off = kk * 32;   // 16 bf16 along K inside the 128-byte swizzled row
-        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-        mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), idesc, acc0);
-        mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), idesc, 1u);
-        mma_bf16(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), idesc, 1u);
+#pragma unroll
+        for (int q = 0; q < C::NP; ++q) {
+          const uint8_t* a = sp + pa[q] * A_BYTES + off;
+          const uint8_t* b = sp + S * A_BYTES + pb[q] * B_BYTES + off;
+          mma_bf16(d, smem_desc(a), smem_desc(b), idesc, (kk > 0 || q > 0) ? 1u : 0u);
+        }
       }
-      mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
+      mma_commit(&empty[st]);   // frees the smem stage once these MMAs have read it
+      mma_commit(&accf[buf]);   // accumulator of this K block is ready
     }
-    mma_commit(accum);
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: TMEM -> registers -> G (upper triangle + mirror)
-  // The MMA thread always commits `accum` last, so this wait also covers an
-  // aborted main loop (it then only drains MMAs already issued).
-  bool ok = mbar_wait(accum, 0, never_abort);
-  if (!ok) {
-    record_device_error(err, DEV_TIMEOUT);
-    *abort = 1;
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  __syncthreads();
-  if (ok && !*abort) {
-    const int row = i0 + warp * 32 + lane;                 // TMEM lane = tile row
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + lane_base + c0, v);
-      if (row < n_features) {
+  } else if (warp < kDrainWarps) {
+    // ---------------- drain: promote each K block into FP32 Kahan sums
+    const int quarter = warp & 3, half = warp >> 2;
+    float sum[kDrainCols], cmp[kDrainCols];
+#pragma unroll
+    for (int k = 0; k < kDrainCols; ++k) {
+      sum[k] = 0.f;
+      cmp[k] = 0.f;
+    }
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    for (int kb = 0; kb < k_blocks; ++kb) {
+      const int buf = kb & 1;
+      const uint32_t use = kb >> 1;
+      const bool ok = mbar_wait(&accf[buf], use & 1, abort);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) {
+          record_device_error(err, DEV_TIMEOUT);
+          *abort = 1;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int c4 = 0; c4 < kDrainCols / 16; ++c4) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + buf * BN + half * kDrainCols + c4 * 16, v);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          const int col = j0 + c0 + k;
+          const int e = c4 * 16 + k;
+          const float y = v[k] - cmp[e];
+          const float tt = sum[e] + y;
+          cmp[e] = (tt - sum[e]) - y;
+          sum[e] = tt;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+    }
+    if (!*abort) {
+      const int row = i0 + quarter * 32 + lane;
+      if (row < n_features) {
+#pragma unroll
+        for (int k = 0; k < kDrainCols; ++k) {
+          const int col = j0 + half * kDrainCols + k;
           if (col >= row && col < n_features) {
-            G[(long)row * n_features + col] = v[k];
-            G[(long)col * n_features + row] = v[k];
+            G[(long)row * n_features + col] = sum[k];
+            G[(long)col * n_features + row] = sum[k];
           }
         }
       }
     }
   }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (*abort && warp == 0 && lane == 0) {
-    // bounded wait for the TMA copies this CTA issued, before the CTA exits
-    for (int s = 0; s < STAGES; ++s)
-      if (last_round[s] >= 0) mbar_wait(&full[s], (uint32_t)last_round[s] & 1, never_abort);
+  if (*abort) {
+    // drain whatever is still in flight before the CTA exits (bounded waits)
+    if (warp == kDrainWarps && lane == 0)
+      for (int q = 0; q < NST; ++q)
+        if (last_round[q] >= 0) mbar_wait(&full[q], (uint32_t)last_round[q] & 1, never_abort);
   }
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
   }
 }
 
@@ -295,34 +364,41 @@ static int make_map(CUtensorMap* map, const void* base, long k_pad, int n_featur
   return QMLR_OK;
 }
 
+template <int S>
+static int launch_split(const uint16_t* zt, long k_pad, int n_features, float* G, cudaStream_t s) {
+  using namespace tc;
+  using C = Cfg<S>;
+  CUtensorMap m[3];
+  for (int q = 0; q < 3; ++q) {
+    const uint16_t* part = zt + (size_t)std::min(q, S - 1) * n_features * k_pad;
+    int rc = make_map(&m[q], part, k_pad, n_features);
+    if (rc) return rc;
+  }
+  const int tiles_i = n_features / BM;
+  const int tiles_j = (n_features + C::BN - 1) / C::BN;
+  int n_tiles = 0;
+  for (int bi = 0; bi < tiles_i; ++bi) n_tiles += tiles_j - (bi * BM) / C::BN;
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(gram_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       C::SMEM_BYTES));
+    attr = true;
+  }
+  gram_split_kernel<S><<<n_tiles, kThreads, C::SMEM_BYTES, s>>>(m[0], m[1], m[2], n_features, (int)(k_pad / BK),
+                                                            tiles_j, G, device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
 }  // namespace tc
 
-int gram_bf16x3_tc(const uint16_t* zt_hi, const uint16_t* zt_lo, long k_pad, int n_features,
-                   float* G, cudaStream_t s) {
-  using namespace tc;
+int gram_split_tc(int n_split, const uint16_t* zt, long k_pad, int n_features, float* G, cudaStream_t s) {
   if (k_pad == 0) {
     QMLR_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n_features * n_features, s));
     return QMLR_OK;
   }
-  CUtensorMap mh, ml;
-  int rc = make_map(&mh, zt_hi, k_pad, n_features);
-  if (rc) return rc;
-  rc = make_map(&ml, zt_lo, k_pad, n_features);
-  if (rc) return rc;
-  const int tiles_i = n_features / BM;
-  const int tiles_j = (n_features + BN - 1) / BN;
-  int n_tiles = 0;
-  for (int bi = 0; bi < tiles_i; ++bi) n_tiles += tiles_j - (bi * BM) / BN;
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(gram_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SMEM_BYTES));
-    attr = true;
-  }
-  gram_bf16x3_kernel<<<n_tiles, 128, SMEM_BYTES, s>>>(mh, ml, n_features, (int)(k_pad / BK), tiles_j, G,
-                                                      device_error_ptr());
-  QMLR_LAUNCH_CHECK();
-  return QMLR_OK;
+  return n_split == 2 ? tc::launch_split<2>(zt, k_pad, n_features, G, s)
+                      : tc::launch_split<3>(zt, k_pad, n_features, G, s);
 }
 
 }  // namespace qmlr

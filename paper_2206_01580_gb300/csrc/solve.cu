@@ -149,61 +149,95 @@ syrk_update_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
 
 // ---------------------------------------------------------------------------
 // triangular solves with the factor (lower L; forward L y = b, backward L^T x = y)
+//
+// The inverses of the 64 x 64 diagonal blocks are formed once after the
+// factorisation; each block step of a solve is then one launch in which every
+// CTA forms x_k = L_kk^{-1} r_k (a small matrix-vector product) and applies it
+// to its share of the remaining rows (forward) or columns (backward).
 
-// Solve the nb-block at k0 in place: v[k0:k0+nb] = L_kk^{-1} v (forward) or L_kk^{-T} v (backward).
-__global__ void tri_block_kernel(const double* __restrict__ L, long ldl, int k0, int nb,
-                                 double* __restrict__ v, int transposed) {
+// Dinv[k] = L_kk^{-1} (lower triangular, 64 x 64, zero above the diagonal). One CTA per block.
+__global__ void __launch_bounds__(NB)
+diag_inverse_kernel(const double* __restrict__ L, long ldl, int n, double* __restrict__ Dinv) {
   __shared__ double lkk[NB][NB + 1];
-  __shared__ double x[NB];
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
-    const int i = idx / nb, j = idx % nb;
-    lkk[i][j] = (j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : 0.0;
-  }
-  if (tid < nb) x[tid] = v[k0 + tid];
-  __syncthreads();
-  if (tid == 0) {
-    if (!transposed) {
-      for (int j = 0; j < nb; ++j) {
-        double s = x[j];
-        for (int l = 0; l < j; ++l) s -= lkk[j][l] * x[l];
-        x[j] = s / lkk[j][j];
-      }
-    } else {
-      for (int j = nb - 1; j >= 0; --j) {
-        double s = x[j];
-        for (int l = j + 1; l < nb; ++l) s -= lkk[l][j] * x[l];
-        x[j] = s / lkk[j][j];
-      }
-    }
+  const int k0 = blockIdx.x * NB;
+  const int nb = min(NB, n - k0);
+  const int j = threadIdx.x;   // column of the inverse
+  for (int idx = j; idx < NB * NB; idx += NB) {
+    const int r = idx / NB, c = idx % NB;
+    lkk[r][c] = (r < nb && c <= r) ? L[(long)(k0 + r) * ldl + k0 + c] : (r == c ? 1.0 : 0.0);
   }
   __syncthreads();
-  if (tid < nb) v[k0 + tid] = x[tid];
+  double x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    double v = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+    for (int l = 0; l < i; ++l) v -= lkk[i][l] * x[l];
+    x[i] = v / lkk[i][i];
+  }
+  double* out = Dinv + (long)blockIdx.x * NB * NB;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) out[i * NB + j] = x[i];
 }
 
-// forward: v[r] -= sum_c L[r][k0+c] v[k0+c] for r >= k0+nb  (warp per row)
-// backward: v[c] -= sum_r L[k0+r][c] v[k0+r] for c < k0     (thread per column)
-__global__ void tri_update_kernel(const double* __restrict__ L, long ldl, int k0, int nb, int n,
-                                  double* __restrict__ v, int transposed) {
-  __shared__ double xb[NB];
-  if (threadIdx.x < nb) xb[threadIdx.x] = v[k0 + threadIdx.x];
+// forward step k: y_k = Dinv_k r_k; r[i] -= L[i][k0:k0+nb] y_k for rows i >= k0 + nb (warp per row)
+__global__ void __launch_bounds__(256)
+fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
+                int n, double* __restrict__ r, double* __restrict__ y) {
+  __shared__ double rk[NB], xk[NB];
+  const int tid = threadIdx.x;
+  if (tid < NB) rk[tid] = tid < nb ? r[k0 + tid] : 0.0;
   __syncthreads();
-  if (!transposed) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int r = k0 + nb + warp;
-    if (r >= n) return;
-    double s = 0.0;
-    for (int c = lane; c < nb; c += 32) s = fma(L[(long)r * ldl + k0 + c], xb[c], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) v[r] -= s;
-  } else {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= k0) return;
-    double s = 0.0;
-    for (int r = 0; r < nb; ++r) s = fma(L[(long)(k0 + r) * ldl + c], xb[r], s);
-    v[c] -= s;
+  if (tid < NB) {
+    const double* D = Dinv + (long)(k0 / NB) * NB * NB + tid * NB;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int l = 0; l < NB; l += 4) {
+      a0 = fma(D[l], rk[l], a0);
+      a1 = fma(D[l + 1], rk[l + 1], a1);
+      a2 = fma(D[l + 2], rk[l + 2], a2);
+      a3 = fma(D[l + 3], rk[l + 3], a3);
+    }
+    xk[tid] = (a0 + a1) + (a2 + a3);
+    if (blockIdx.x == 0 && tid < nb) y[k0 + tid] = xk[tid];
   }
+  __syncthreads();
+  const int warp = (blockIdx.x * blockDim.x + tid) >> 5, lane = tid & 31;
+  const int row = k0 + nb + warp;
+  if (row >= n) return;
+  const double* Lr = L + (long)row * ldl + k0;
+  double s = 0.0;
+  for (int c = lane; c < nb; c += 32) s = fma(Lr[c], xk[c], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) r[row] -= s;
+}
+
+// backward step k: x_k = Dinv_k^T y_k; y[c] -= sum_r L[k0+r][c] x_k[r] for columns c < k0
+__global__ void __launch_bounds__(256)
+bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
+                double* __restrict__ y, double* __restrict__ x) {
+  __shared__ double yk[NB], xk[NB];
+  const int tid = threadIdx.x;
+  if (tid < NB) yk[tid] = tid < nb ? y[k0 + tid] : 0.0;
+  __syncthreads();
+  if (tid < NB) {
+    const double* D = Dinv + (long)(k0 / NB) * NB * NB;   // x_t = sum_l Dinv[l][t] y_l
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int l = 0; l < NB; l += 4) {
+      a0 = fma(D[l * NB + tid], yk[l], a0);
+      a1 = fma(D[(l + 1) * NB + tid], yk[l + 1], a1);
+      a2 = fma(D[(l + 2) * NB + tid], yk[l + 2], a2);
+      a3 = fma(D[(l + 3) * NB + tid], yk[l + 3], a3);
+    }
+    xk[tid] = (a0 + a1) + (a2 + a3);
+    if (blockIdx.x == 0 && tid < nb) x[k0 + tid] = xk[tid];
+  }
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + tid;
+  if (c >= k0) return;
+  double s = 0.0;
+  for (int rr = 0; rr < nb; ++rr) s = fma(L[(long)(k0 + rr) * ldl + c], xk[rr], s);
+  y[c] -= s;
 }
 
 // ---------------------------------------------------------------------------
@@ -275,6 +309,19 @@ __global__ void pupdate_kernel(int n, const double* __restrict__ rz_new,
   if (i < n) p[i] = z[i] + (*rz_new / *rz_old) * p[i];
 }
 
+__global__ void maxdiag_kernel(const float* __restrict__ G, int n, double* out) {
+  __shared__ double red[1024];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, (double)G[(long)i * n + i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 __global__ void add_kernel(int n, const double* __restrict__ x, double* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += x[i];
@@ -329,27 +376,31 @@ static int cholesky(double* L, long ldl, int n, cudaStream_t s, int* info) {
   return QMLR_OK;
 }
 
-static int chol_apply(const double* L, long ldl, int n, double* v, cudaStream_t s) {
+// v <- (L L^T)^{-1} v; tmp is an n-vector of scratch.
+static int chol_apply(const double* L, long ldl, const double* Dinv, int n, double* v, double* tmp,
+                      cudaStream_t s) {
+  // forward: L tmp = v (v is consumed as the running residual)
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int nb = std::min(NB, n - k0);
-    tri_block_kernel<<<1, 64, 0, s>>>(L, ldl, k0, nb, v, 0);
+    const int rows = std::max(n - k0 - nb, 0);
+    const int grid = std::max((rows * 32 + 255) / 256, 1);
+    fwd_step_kernel<<<grid, 256, 0, s>>>(L, ldl, Dinv, k0, nb, n, v, tmp);
     QMLR_LAUNCH_CHECK();
-    const int rows = n - k0 - nb;
-    if (rows > 0) {
-      tri_update_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(L, ldl, k0, nb, n, v, 0);
-      QMLR_LAUNCH_CHECK();
-    }
   }
+  // backward: L^T v = tmp (tmp is consumed)
   const int last = ((n - 1) / NB) * NB;
   for (int k0 = last; k0 >= 0; k0 -= NB) {
     const int nb = std::min(NB, n - k0);
-    tri_block_kernel<<<1, 64, 0, s>>>(L, ldl, k0, nb, v, 1);
+    const int grid = std::max((k0 + 255) / 256, 1);
+    bwd_step_kernel<<<grid, 256, 0, s>>>(L, ldl, Dinv, k0, nb, tmp, v);
     QMLR_LAUNCH_CHECK();
-    if (k0 > 0) {
-      tri_update_kernel<<<(k0 + 255) / 256, 256, 0, s>>>(L, ldl, k0, nb, n, v, 1);
-      QMLR_LAUNCH_CHECK();
-    }
   }
+  return QMLR_OK;
+}
+
+static int diag_inverses(const double* L, long ldl, int n, double* Dinv, cudaStream_t s) {
+  diag_inverse_kernel<<<(n + NB - 1) / NB, NB, 0, s>>>(L, ldl, n, Dinv);
+  QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }
 
@@ -377,7 +428,10 @@ using namespace qmlr;
 extern "C" int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features) {
   const int64_t n = n_features;
   const int64_t parts = std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
+  const int64_t nblk = (n + NB - 1) / NB;
   return n * n * 8                 // factor L
+         + nblk * NB * NB * 8      // inverses of the diagonal blocks
+         + n * 8                   // triangular-solve scratch
          + parts * n * 8           // partial sums of Z^T t
          + std::max<int64_t>(n_rows, 1) * 8   // t = Z p
          + 6 * n * 8               // c, r, z, p, q, tmp
@@ -403,7 +457,14 @@ extern "C" int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_in
 
 extern "C" int qmlr_cholesky_solve(const double* L, int64_t ldl, int32_t n, double* v, void* stream) {
   QMLR_REQUIRE(L && v && n >= 1 && ldl >= n, "bad arguments");
-  return chol_apply(L, ldl, n, v, as_stream(stream));
+  cudaStream_t s = as_stream(stream);
+  const int nblk = (n + NB - 1) / NB;
+  double* buf = nullptr;
+  QMLR_CUDA_TRY(cudaMallocAsync(&buf, sizeof(double) * ((size_t)nblk * NB * NB + n), s));
+  int rc = diag_inverses(L, ldl, n, buf, s);
+  if (rc == QMLR_OK) rc = chol_apply(L, ldl, buf, n, v, buf + (size_t)nblk * NB * NB, s);
+  cudaFreeAsync(buf, s);
+  return rc;
 }
 
 static void carve(char*& p, void** out, size_t bytes) {
@@ -417,7 +478,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   QMLR_REQUIRE(G && alpha && opts, "NULL pointer argument");
   QMLR_REQUIRE(n_features >= 1 && n_rows >= 0 && ldz >= n_features, "bad shapes");
   QMLR_REQUIRE(n_rows == 0 || (Z && y), "Z/y are NULL");
-  QMLR_REQUIRE(lambda >= 0 && opts->shift >= 0, "lambda and shift must be >= 0");
+  QMLR_REQUIRE(lambda >= 0, "lambda must be >= 0");
   QMLR_REQUIRE(opts->max_iter >= 0, "max_iter must be >= 0");
   QMLR_REQUIRE(work && work_bytes >= qmlr_solve_workspace_bytes(n_rows, n_features),
                "workspace too small");
@@ -435,8 +496,11 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   c.s = s;
   c.parts = (int)std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
   char* p = static_cast<char*>(work);
-  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc;
+  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc, *vdinv, *vtri;
+  const int nblk = (n + NB - 1) / NB;
   carve(p, &vL, (size_t)n * n * 8);
+  carve(p, &vdinv, (size_t)nblk * NB * NB * 8);
+  carve(p, &vtri, (size_t)n * 8);
   carve(p, &vpart, (size_t)c.parts * n * 8);
   carve(p, &vt, (size_t)std::max<int64_t>(n_rows, 1) * 8);
   carve(p, &vc, (size_t)n * 8);
@@ -451,7 +515,9 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   c.t = static_cast<double*>(vt);
   double *cv = static_cast<double*>(vc), *r = static_cast<double*>(vr), *z = static_cast<double*>(vz);
   double *pv = static_cast<double*>(vp), *q = static_cast<double*>(vq);
-  double* sc = static_cast<double*>(vsc);   // [0]=rz, [1]=rz_new, [2]=pq, [3]=a, [4]=rr, [5]=cc
+  double* sc = static_cast<double*>(vsc);
+  double* Dinv = static_cast<double*>(vdinv);
+  double* tri = static_cast<double*>(vtri);   // [0]=rz, [1]=rz_new, [2]=pq, [3]=a, [4]=rr, [5]=cc
   int* info = reinterpret_cast<int*>(sc + 7);
   const int vb = (n + 255) / 256;
 
@@ -465,26 +531,57 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   } else {
     QMLR_CUDA_TRY(cudaMemsetAsync(cv, 0, sizeof(double) * n, s));
   }
-  // factor of G + (lambda + shift) I
-  const long nn = (long)n * n;
-  assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(G, n, lambda + opts->shift, c.L, c.ldl);
-  QMLR_LAUNCH_CHECK();
-  QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
-  int rc = cholesky(c.L, c.ldl, n, s, info);
-  if (rc) return rc;
-  int hinfo = 0;
-  QMLR_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
-  QMLR_CUDA_TRY(cudaStreamSynchronize(s));
-  if (hinfo != 0) {
-    set_error("Cholesky factorisation failed at column %d (matrix not positive definite; "
-              "increase opts.shift)", hinfo);
-    int32_t code;
-    qmlr_device_status(stream, &code);
-    return QMLR_EINVAL;
+  // factor of G + (lambda + shift) I; a negative opts->shift means |shift| * max_i G_ii.
+  // A non-positive pivot (the low-precision Gram can be slightly indefinite)
+  // raises the shift tenfold, up to 8 times.
+  double shift = opts->shift;
+  if (shift < 0) {
+    maxdiag_kernel<<<1, 1024, 0, s>>>(G, n, sc + 6);
+    QMLR_LAUNCH_CHECK();
+    double md = 0;
+    QMLR_CUDA_TRY(cudaMemcpyAsync(&md, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QMLR_CUDA_TRY(cudaStreamSynchronize(s));
+    shift = -shift * md;
   }
+  const long nn = (long)n * n;
+  int hinfo = 0;
+  cudaEvent_t ev[3];
+  for (int k = 0; k < 3; ++k) QMLR_CUDA_TRY(cudaEventCreate(&ev[k]));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int k = 0; k < 3; ++k) cudaEventDestroy(e[k]);
+    }
+  } ev_guard{ev};
+  QMLR_CUDA_TRY(cudaEventRecord(ev[0], s));
+  for (int attempt = 0;; ++attempt) {
+    assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(G, n, lambda + shift, c.L, c.ldl);
+    QMLR_LAUNCH_CHECK();
+    QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+    int rc = cholesky(c.L, c.ldl, n, s, info);
+    if (rc) return rc;
+    QMLR_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QMLR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hinfo == 0) break;
+    int32_t code;
+    qmlr_device_status(stream, &code);   // clear the recorded pivot failure
+    if (attempt == 8) {
+      set_error("Cholesky factorisation failed at column %d with shift %.3e "
+                "(matrix not positive definite)", hinfo, shift);
+      return QMLR_EINVAL;
+    }
+    shift = shift > 0 ? 10.0 * shift : 1e-12;
+  }
+  opts->shift_used = shift;
+  {
+    int rc0 = diag_inverses(c.L, c.ldl, n, Dinv, s);
+    if (rc0) return rc0;
+  }
+  QMLR_CUDA_TRY(cudaEventRecord(ev[1], s));
+  int rc = QMLR_OK;
   // alpha = M^{-1} c
   QMLR_CUDA_TRY(cudaMemcpyAsync(alpha, cv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  if ((rc = chol_apply(c.L, c.ldl, n, alpha, s))) return rc;
+  if ((rc = chol_apply(c.L, c.ldl, Dinv, n, alpha, tri, s))) return rc;
   dot_kernel<<<1, 1024, 0, s>>>(cv, cv, n, sc + 5);
   QMLR_LAUNCH_CHECK();
   // r = c - A alpha
@@ -507,7 +604,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
     // alpha += M^{-1} r ; r = c - A alpha
     for (; it < opts->max_iter && rel > opts->tol; ++it) {
       QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      if ((rc = chol_apply(c.L, c.ldl, n, z, s))) return rc;
+      if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s))) return rc;
       add_kernel<<<vb, 256, 0, s>>>(n, z, alpha);
       QMLR_LAUNCH_CHECK();
       if ((rc = apply_exact(c, alpha, q))) return rc;
@@ -518,7 +615,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   } else {
     // preconditioned conjugate gradients on the exact operator
     QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    if ((rc = chol_apply(c.L, c.ldl, n, z, s))) return rc;
+    if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s))) return rc;
     QMLR_CUDA_TRY(cudaMemcpyAsync(pv, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     dot_kernel<<<1, 1024, 0, s>>>(r, z, n, sc + 0);
     QMLR_LAUNCH_CHECK();
@@ -538,7 +635,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
         break;
       }
       QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      if ((rc = chol_apply(c.L, c.ldl, n, z, s))) return rc;
+      if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s))) return rc;
       dot_kernel<<<1, 1024, 0, s>>>(r, z, n, sc + 1);
       QMLR_LAUNCH_CHECK();
       pupdate_kernel<<<vb, 256, 0, s>>>(n, sc + 1, sc + 0, z, pv);
@@ -546,6 +643,10 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
       QMLR_CUDA_TRY(cudaMemcpyAsync(sc + 0, sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
   }
+  QMLR_CUDA_TRY(cudaEventRecord(ev[2], s));
+  QMLR_CUDA_TRY(cudaEventSynchronize(ev[2]));
+  cudaEventElapsedTime(&opts->factor_ms, ev[0], ev[1]);
+  cudaEventElapsedTime(&opts->refine_ms, ev[1], ev[2]);
   opts->iters_done = it;
   opts->rel_resid = rel;
   if (rel > opts->tol) {

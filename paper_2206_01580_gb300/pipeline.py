@@ -1,0 +1,96 @@
+"""Training and prediction pipelines over the qmlr C ABI.
+
+Each function only sequences library calls (FCHL19 -> projection -> SORF ->
+Gram -> solve); every arithmetic step runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import qmlr
+from .params import FCHL19Params
+
+
+@dataclass
+class Batch:
+    """A CSR batch of molecules resident on the device."""
+
+    coords: torch.Tensor   # float32 [n_atoms, 3]
+    elem: torch.Tensor     # int32 [n_atoms]
+    mol_ptr: torch.Tensor  # int32 [n_mol + 1]
+    max_atoms: int
+
+    @property
+    def n_atoms(self) -> int:
+        return self.coords.shape[0]
+
+    @property
+    def n_mol(self) -> int:
+        return self.mol_ptr.shape[0] - 1
+
+    @staticmethod
+    def from_host(coords, elem, mol_ptr) -> "Batch":
+        mol_ptr = np.asarray(mol_ptr)
+        return Batch(torch.as_tensor(np.asarray(coords, dtype=np.float32)).cuda(),
+                     torch.as_tensor(np.asarray(elem, dtype=np.int32)).cuda(),
+                     torch.as_tensor(mol_ptr.astype(np.int32)).cuda(),
+                     int(np.diff(mol_ptr).max()) if len(mol_ptr) > 1 else 1)
+
+
+@dataclass
+class FeatureSpec:
+    p: FCHL19Params
+    d: int
+    T: int
+    sign_bits: torch.Tensor   # packed Rademacher signs
+    b: torch.Tensor           # float32 [N_F]
+    sigma: float
+
+    @property
+    def n_features(self) -> int:
+        return self.b.shape[0]
+
+
+def spec_from(p: FCHL19Params, d: int, signs, b, sigma: float) -> FeatureSpec:
+    return FeatureSpec(p, d, signs.shape[1], qmlr.pack_signs(signs),
+                       torch.as_tensor(np.asarray(b, dtype=np.float32)).cuda(), float(sigma))
+
+
+def representations(batch: Batch, spec: FeatureSpec):
+    rep = qmlr.fchl19(batch.coords, batch.elem, batch.mol_ptr, batch.max_atoms, spec.p)
+    perm, offs = qmlr.group_by_element(batch.elem, spec.p.n_el)
+    return rep, perm, offs
+
+
+def fit_pca(rep, perm, offs, spec: FeatureSpec, max_per_element: int = 4096):
+    return qmlr.pca_fit(rep, spec.p.rep_dim, perm, offs, spec.p.n_el, spec.d, max_per_element)
+
+
+def feature_matrix(batch: Batch, spec: FeatureSpec, U, rep=None, perm=None, offs=None):
+    """Energy rows Z [n_mol, N_F] (float32) of the batch."""
+    if rep is None:
+        rep, perm, offs = representations(batch, spec)
+    x = qmlr.project(rep, spec.p.rep_dim, perm, offs, spec.p.n_el, U)
+    return qmlr.sorf(x, batch.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
+
+
+def solve(Z, y, lam: float, precision: int = qmlr.GRAM_BF16X6, method: int = qmlr.SOLVE_PCG,
+          max_iter: int = 50, tol: float = 1e-10, shift: float = -2.0 ** -14):
+    """alpha (float64) of (Z^T Z + lam I) alpha = Z^T y; returns (alpha, iterations, rel. residual)."""
+    G = qmlr.gram(Z, precision)
+    return qmlr.gram_solve(G, Z, y, lam, method=method, max_iter=max_iter, tol=tol, shift=shift)
+
+
+def train_energy(batch: Batch, energies, spec: FeatureSpec, lam: float, U=None,
+                 precision: int = qmlr.GRAM_BF16X6, **solve_kw):
+    """Energy-only training: returns (alpha, U, iterations, relative residual)."""
+    rep, perm, offs = representations(batch, spec)
+    if U is None:
+        U = fit_pca(rep, perm, offs, spec)
+    Z = feature_matrix(batch, spec, U, rep, perm, offs)
+    y = torch.as_tensor(np.asarray(energies, dtype=np.float64)).cuda()
+    alpha, it, rel = solve(Z, y, lam, precision, **solve_kw)
+    return alpha, U, it, rel

@@ -36,18 +36,20 @@ class _Params(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
-                ("shift", C.c_double), ("iters_done", C.c_int32), ("rel_resid", C.c_double)]
+                ("shift", C.c_double), ("iters_done", C.c_int32), ("rel_resid", C.c_double),
+                ("shift_used", C.c_double), ("factor_ms", C.c_float), ("refine_ms", C.c_float)]
 
 
 _lib = None
 P, I32, I64, D, VP = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_void_p
-GRAM_FP32, GRAM_BF16X3 = 0, 1
+GRAM_FP32, GRAM_BF16X3, GRAM_BF16X6 = 0, 1, 2
 SOLVE_PCG, SOLVE_REFINE = 0, 1
 
 # name -> (restype, argtypes)
 _SIGS = {
     "qmlr_version": (C.c_char_p, []),
     "qmlr_last_error": (C.c_char_p, []),
+    "qmlr_launch_count": (C.c_int64, []),
     "qmlr_device_status": (C.c_int, [VP, C.POINTER(C.c_int32)]),
     "qmlr_fchl19_rep_dim": (C.c_int, [C.POINTER(_Params), C.POINTER(C.c_int32)]),
     "qmlr_fchl19": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, VP]),
@@ -59,14 +61,23 @@ _SIGS = {
     "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, VP]),
-    "qmlr_gram_operand": (C.c_int, [P, I64, I32, I64, P, P, I64, VP]),
-    "qmlr_gram": (C.c_int, [I32, P, I64, I32, I64, P, P, I64, P, VP]),
+    "qmlr_gram_operand": (C.c_int, [P, I64, I32, I64, I32, P, I64, VP]),
+    "qmlr_gram": (C.c_int, [I32, P, I64, I32, I64, P, I64, P, VP]),
     "qmlr_zty_workspace_bytes": (C.c_int64, [I64, I32]),
     "qmlr_zty": (C.c_int, [P, I64, I32, I64, P, P, P, I64, VP]),
     "qmlr_cholesky": (C.c_int, [P, I64, I32, C.POINTER(C.c_int32), VP]),
     "qmlr_cholesky_solve": (C.c_int, [P, I64, I32, P, VP]),
     "qmlr_solve_workspace_bytes": (C.c_int64, [I64, I32]),
     "qmlr_gram_solve": (C.c_int, [P, P, I64, I32, I64, P, D, C.POINTER(SolveOpts), P, P, I64, VP]),
+    "qmlr_pca_workspace_bytes": (C.c_int64, [I32, I32]),
+    "qmlr_pca_fit": (C.c_int, [P, I32, I32, P, P, I32, I32, I32, P, P, I64, VP]),
+    "qmlr_model_create": (C.c_int, [C.POINTER(_Params), I32, P, I32, P, I32, P, I32, D, P,
+                                    C.POINTER(C.c_void_p)]),
+    "qmlr_model_destroy": (C.c_int, [VP]),
+    "qmlr_model_set_alpha": (C.c_int, [VP, P]),
+    "qmlr_model_set_alpha_device": (C.c_int, [VP, P, VP]),
+    "qmlr_model_reserve": (C.c_int, [VP, I32]),
+    "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
 }
 
 
@@ -272,28 +283,27 @@ def k_pad_of(n_rows: int) -> int:
     return max(64, (n_rows + 63) // 64 * 64)
 
 
-def gram_operand(Z):
+def gram_operand(Z, n_split: int = 2):
+    """Transposed split-BF16 operand [n_split, N_F, k_pad] (int16 holding bf16 bits)."""
     Z = _dev(Z, torch.float32)
     n_rows, nf = Z.shape
     kp = k_pad_of(n_rows)
-    hi = torch.empty((nf, kp), device="cuda", dtype=torch.int16)
-    lo = torch.empty((nf, kp), device="cuda", dtype=torch.int16)
-    _check(lib().qmlr_gram_operand(_ptr(Z), n_rows, nf, Z.stride(0), _ptr(hi), _ptr(lo), kp, _stream()))
-    return hi, lo
+    zt = torch.empty((n_split, nf, kp), device="cuda", dtype=torch.int16)
+    _check(lib().qmlr_gram_operand(_ptr(Z), n_rows, nf, Z.stride(0), n_split, _ptr(zt), kp, _stream()))
+    return zt
 
 
-def gram(Z, precision: int = GRAM_BF16X3, operands=None):
+def gram(Z, precision: int = GRAM_BF16X6, operand=None):
     """G = Z^T Z (float32, full symmetric)."""
     Z = _dev(Z, torch.float32)
     n_rows, nf = Z.shape
     G = torch.empty((nf, nf), device="cuda", dtype=torch.float32)
-    if precision == GRAM_BF16X3:
-        hi, lo = operands if operands is not None else gram_operand(Z)
-        _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), _ptr(hi), _ptr(lo),
-                               hi.shape[1], _ptr(G), _stream()))
+    if precision in (GRAM_BF16X3, GRAM_BF16X6):
+        zt = operand if operand is not None else gram_operand(Z, 2 if precision == GRAM_BF16X3 else 3)
+        _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), _ptr(zt), zt.shape[2],
+                               _ptr(G), _stream()))
     else:
-        _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), None, None, 0, _ptr(G),
-                               _stream()))
+        _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), None, 0, _ptr(G), _stream()))
     return G
 
 
@@ -325,9 +335,9 @@ def cholesky_solve(L, v):
 
 
 def gram_solve(G, Z, y, lam: float, method: int = SOLVE_PCG, max_iter: int = 50, tol: float = 1e-10,
-               shift: float = 0.0, raise_on_notconv: bool = False):
-    """alpha for (Z^T Z + lam I) alpha = Z^T y with a factor of G + (lam + shift) I.
-    Returns (alpha, iterations, relative residual)."""
+               shift: float = -2.0 ** -14, raise_on_notconv: bool = False):
+    """alpha for (Z^T Z + lam I) alpha = Z^T y with a factor of G + (lam + shift) I
+    (shift < 0: relative to max diag G). Returns (alpha, iterations, relative residual)."""
     G = _dev(G, torch.float32)
     Z = _dev(Z, torch.float32)
     y = _dev(y, torch.float64)
@@ -335,10 +345,97 @@ def gram_solve(G, Z, y, lam: float, method: int = SOLVE_PCG, max_iter: int = 50,
     alpha = torch.empty(nf, device="cuda", dtype=torch.float64)
     wb = lib().qmlr_solve_workspace_bytes(n_rows, nf)
     work = torch.empty(wb, device="cuda", dtype=torch.uint8)
-    opts = SolveOpts(method, max_iter, tol, shift, 0, 0.0)
+    opts = SolveOpts(method, max_iter, tol, shift, 0, 0.0, 0.0, 0.0, 0.0)
     rc = lib().qmlr_gram_solve(_ptr(G), _ptr(Z), n_rows, nf, Z.stride(0), _ptr(y), float(lam),
                                C.byref(opts), _ptr(alpha), _ptr(work), wb, _stream())
+    global last_solve
+    last_solve = opts
     if rc == ENOTCONV and not raise_on_notconv:
         return alpha, opts.iters_done, opts.rel_resid
     _check(rc)
     return alpha, opts.iters_done, opts.rel_resid
+
+
+last_solve = None
+
+
+def launch_count() -> int:
+    return lib().qmlr_launch_count()
+
+
+# ----------------------------------------------------------------------------
+# PCA fit and the model handle
+
+
+def pca_fit(rep, rep_dim: int, perm, offs, n_el: int, d: int, max_per_element: int = 4096):
+    rep = _dev(rep, torch.float32)
+    U = torch.empty((n_el, rep_dim, d), device="cuda", dtype=torch.float32)
+    wb = lib().qmlr_pca_workspace_bytes(rep.shape[1], d)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
+    _check(lib().qmlr_pca_fit(_ptr(rep), rep.shape[1], rep_dim, _ptr(perm), _ptr(offs), n_el,
+                              max_per_element, d, _ptr(U), _ptr(work), wb, _stream()))
+    return U
+
+
+class Model:
+    """Device-resident trained model (owns a qmlr_model handle)."""
+
+    def __init__(self, p: FCHL19Params, max_mol_atoms: int, U, signs, T: int, b, sigma: float,
+                 alpha):
+        U = np.ascontiguousarray(np.asarray(U.cpu() if isinstance(U, torch.Tensor) else U,
+                                            dtype=np.float32))
+        bits = pack_signs(signs).cpu().numpy().view(np.uint32) if not isinstance(signs, torch.Tensor) \
+            else signs.cpu().numpy().view(np.uint32)
+        bits = np.ascontiguousarray(bits)
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float32))
+        al = np.ascontiguousarray(np.asarray(alpha.cpu() if isinstance(alpha, torch.Tensor) else alpha,
+                                             dtype=np.float32))
+        self.p, self.d, self.T, self.n_features = p, U.shape[2], T, b.shape[0]
+        self.max_mol_atoms = max_mol_atoms
+        cp = c_params(p)
+        h = C.c_void_p()
+        _check(lib().qmlr_model_create(C.byref(cp), max_mol_atoms, U.ctypes.data, self.d,
+                                       bits.ctypes.data, T, b.ctypes.data, self.n_features,
+                                       float(sigma), al.ctypes.data, C.byref(h)))
+        self.handle = h
+        self.capacity = 0
+
+    def set_alpha(self, alpha):
+        al = np.ascontiguousarray(np.asarray(alpha.cpu() if isinstance(alpha, torch.Tensor) else alpha,
+                                             dtype=np.float32))
+        _check(lib().qmlr_model_set_alpha(self.handle, al.ctypes.data))
+
+    def set_alpha_device(self, alpha64: torch.Tensor):
+        _check(lib().qmlr_model_set_alpha_device(self.handle, _ptr(alpha64), _stream()))
+
+    def reserve(self, n_atoms: int):
+        if n_atoms > self.capacity:
+            _check(lib().qmlr_model_reserve(self.handle, n_atoms))
+            self.capacity = n_atoms
+
+    def predict(self, coords, elem, mol_ptr, forces: bool = True, out=None):
+        """Energies [n_mol] (float64) and forces [n_atoms, 3] (float32) on the device."""
+        coords = _dev(coords, torch.float32)
+        elem = _dev(elem, torch.int32)
+        mol_ptr = _dev(mol_ptr, torch.int32)
+        n_atoms, n_mol = coords.shape[0], mol_ptr.shape[0] - 1
+        self.reserve(n_atoms)
+        if out is None:
+            E = torch.empty(n_mol, device="cuda", dtype=torch.float64)
+            F = torch.empty((n_atoms, 3), device="cuda", dtype=torch.float32) if forces else None
+        else:
+            E, F = out
+        _check(lib().qmlr_predict_ef(self.handle, _ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol, n_atoms,
+                                     _ptr(E), _ptr(F), _stream()))
+        return E, F
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qmlr_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -503,6 +503,7 @@ class Workload:
     test: MoleculeSet | None = None
     test_energies: np.ndarray | None = None
     test_forces: np.ndarray | None = None
+    potential: PairPotential | None = None
 
 
 def workload(config: int, scale: float = 1.0, sigma: float | None = None) -> Workload:
@@ -516,7 +517,7 @@ def workload(config: int, scale: float = 1.0, sigma: float | None = None) -> Wor
         E = targets(pot, mols)
         signs, b = sorf_draw(rng, 512, 64, 3)
         return Workload("parity-64x9", mols, E, None, "E", 24, 22, 64, 512, 3,
-                        2.0 if sigma is None else sigma, 1e-6, signs, b)
+                        2.0 if sigma is None else sigma, 1e-6, signs, b, potential=pot)
     if config == 1:
         n_mol = max(1, int(round(100_000 * scale)))
         mols = qm9_like(rng, n_mol)
@@ -528,7 +529,7 @@ def workload(config: int, scale: float = 1.0, sigma: float | None = None) -> Wor
         E = targets(pot, mols)
         signs, b = sorf_draw(rng, 16384, 128, 3)
         return Workload("qm9-shaped-100k", mols, E, None, "E", 24, 22, 128, 16384, 3,
-                        2.0 if sigma is None else sigma, 1e-6, signs, b)
+                        2.0 if sigma is None else sigma, 1e-6, signs, b, potential=pot)
     if config in (2, 3):
         comp = ASPIRIN_LIKE if config == 2 else BPA3_LIKE
         n_train = 1000 if config == 2 else 500

@@ -2,8 +2,9 @@
 operands, the plain-FP32 and tensor-core Gram, Z^T y, the FP64 Cholesky
 factor and solves, and the refined ridge solve against the FP64 oracle.
 
-Tolerances: Gram max-abs error <= 4e-5 * max|G| (FP32 accumulation, bf16 x3
-split drops the lo*lo term ~2^-16 relative); Z^T y and Cholesky: FP64 round-off
+Tolerances: Gram max-abs error <= 4e-5 * max|G| for plain FP32 (accumulation)
+and the 2-way BF16 split (products ~2^-16 relative), <= 1e-5 for the 3-way
+split (~2^-24 products, FP32 accumulation); Z^T y and Cholesky: FP64 round-off
 (rel 1e-10); solves: relative normal-equation residual <= tol with the exact
 FP64 operator, and predictions Z alpha within 1e-6 relative of the oracle's.
 """
@@ -39,29 +40,44 @@ def _features(n_rows, nf, seed=0):
     return Z
 
 
-def test_gram_operand_is_bf16_hi_lo_split(q):
+@pytest.mark.parametrize("n_split", [2, 3])
+def test_gram_operand_is_bf16_split(q, n_split):
     Z = _features(100, 256)
-    hi, lo = q.gram_operand(Z)
-    assert hi.shape == (256, 128)
-    zt = torch.as_tensor(Z).T.contiguous()
-    want_hi = zt.to(torch.bfloat16)
-    want_lo = (zt - want_hi.float()).to(torch.bfloat16)
-    got_hi = hi.cpu()[:, :100].view(torch.bfloat16)
-    got_lo = lo.cpu()[:, :100].view(torch.bfloat16)
-    assert torch.equal(got_hi, want_hi) and torch.equal(got_lo, want_lo)
-    assert torch.all(hi.cpu()[:, 100:] == 0) and torch.all(lo.cpu()[:, 100:] == 0)
+    zt = q.gram_operand(Z, n_split).cpu()
+    assert zt.shape == (n_split, 256, 128)
+    rem = torch.as_tensor(Z).T.contiguous()
+    for k in range(n_split):
+        want = rem.to(torch.bfloat16)
+        assert torch.equal(zt[k, :, :100].view(torch.bfloat16), want)
+        assert torch.all(zt[k, :, 100:] == 0)
+        rem = rem - want.float()
+
+
+GRAM_TOL = {0: 4e-5, 1: 4e-5, 2: 1e-5}
 
 
 @pytest.mark.parametrize("n_rows,nf", [(64, 128), (1000, 256), (777, 384), (4096, 1024), (130, 512)])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_gram_matches_fp64(q, n_rows, nf, precision):
     Z = _features(n_rows, nf, seed=n_rows + nf)
     ref = Z.astype(np.float64).T @ Z.astype(np.float64)
     G = q.gram(Z, precision).cpu().numpy()
     assert q.device_status() == 0
     err = np.max(np.abs(G - ref)) / np.max(np.abs(ref))
-    assert err <= 4e-5, err
+    assert err <= GRAM_TOL[precision], err
     assert np.array_equal(G, G.T)
+
+
+def test_tensor_core_gram_is_unbiased_on_long_sums(q):
+    """Tensor-core accumulator adds truncate; the kernel promotes every 64-row K
+    block into FP32 Kahan sums, so the diagonal (sums of 6000 positive terms)
+    carries no systematic relative bias beyond FP32 rounding."""
+    Z = _features(6000, 256, seed=21)
+    ref = np.einsum("ij,ij->j", Z.astype(np.float64), Z.astype(np.float64))
+    for precision, tol in ((0, 1e-6), (2, 1e-6)):
+        G = q.gram(Z, precision).cpu().numpy()
+        bias = np.mean(np.diag(G) / ref - 1.0)
+        assert abs(bias) <= tol, (precision, bias)
 
 
 def test_zty_matches_fp64(q):
@@ -97,7 +113,7 @@ def test_cholesky_reports_indefinite_matrix(q):
 
 
 @pytest.mark.parametrize("method", [0, 1])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_ridge_solve_matches_oracle(q, method, precision):
     Z = _features(1500, 256, seed=9)
     y = np.random.default_rng(10).normal(size=1500)
@@ -119,7 +135,7 @@ def test_ridge_solve_underdetermined_with_shift(q):
     y = np.random.default_rng(12).normal(size=64)
     lam = 1e-6
     alpha_ref, _ = o_reg.ridge_solve(Z.astype(np.float64), y, lam, refine=2)
-    G = q.gram(Z, 1)
+    G = q.gram(Z, 2)
     alpha, it, rel = q.gram_solve(G, Z, y, lam, method=0, max_iter=200, tol=1e-10, shift=1e-4)
     assert rel <= 1e-10, (it, rel)
     pz = Z.astype(np.float64) @ alpha.cpu().numpy()
