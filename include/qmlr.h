@@ -135,6 +135,28 @@ int qmlr_group_by_element(const int32_t* elem, int32_t n_atoms, int32_t n_el, in
                           int32_t* elem_offsets, void* work, int64_t work_bytes, void* stream);
 
 /*
+ * Element grouping that allocates nothing (the paper has no counterpart: this
+ * is an integration convenience). Same result as qmlr_group_by_element, for
+ * callers that cannot allocate device memory when they need it: work being
+ * captured into a CUDA graph, a host framework that owns every device buffer
+ * through its own pool, or a latency-bound service that must not wait on the
+ * allocator. The counting sort's scratch is a fixed 256 KiB array inside the
+ * library (one per device that loads it, kept until the process exits), so
+ * n_atoms is limited to QMLR_GROUP_NOALLOC_MAX_ATOMS; larger inputs are
+ * rejected with QMLR_EINVAL before any launch.
+ *   - The first call on a device looks up that device's copy of the array
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (different streams, or different host threads on one device) race and
+ *     must be serialised by the caller. The array keeps the last call's
+ *     contents; every value a call reads is written by that call first.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+#define QMLR_GROUP_NOALLOC_MAX_ATOMS 4194304
+int qmlr_group_by_element_noalloc(const int32_t* elem, int32_t n_atoms, int32_t n_el,
+                                  int32_t* perm, int32_t* elem_offsets, void* stream);
+
+/*
  * x[i][:] = rep[i][:rep_dim] * U[elem(i)]   (float32 arithmetic, float32 accumulation)
  *   rep  float [n_atoms][rep_ld]
  *   perm, elem_offsets  from qmlr_group_by_element

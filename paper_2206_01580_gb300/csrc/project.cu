@@ -8,6 +8,8 @@
 // is streamed once per tile. Arithmetic and accumulation are FP32.
 #include "common.cuh"
 
+#include <mutex>
+
 namespace qmlr {
 
 constexpr int kGroupChunk = 1024;  // atoms per CTA of the counting sort
@@ -271,5 +273,73 @@ extern "C" int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* pe
       gx, d, d, n_part, (long)n_atoms * d, U, d, (long)rep_dim * d, rep_dim, perm, elem_offsets,
       n_el, grad_rep, rep_ld, rep_ld);
   QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Element grouping without any allocation (same kernels, fixed scratch).
+//
+// Some callers cannot allocate device memory at the moment they need the
+// grouping: a stream that is being captured into a CUDA graph, a host
+// framework that hands out all device memory from its own pool, or a
+// latency-critical service that must not block on the allocator. For them the
+// counting sort's per-chunk counts and offsets live in a file-scope device
+// array sized for QMLR_GROUP_NOALLOC_MAX_ATOMS atoms; every device that loads
+// the library holds it (256 KiB) until the process exits.
+namespace qmlr {
+
+constexpr int kNoAllocChunks = QMLR_GROUP_NOALLOC_MAX_ATOMS / kGroupChunk;
+static __device__ __align__(256) int g_group_scratch[2 * kNoAllocChunks * kMaxEl];
+
+// Device address of g_group_scratch on the current device. In host code the
+// symbol is only a host-side stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+static int* group_scratch_address() {
+  static std::mutex mu;
+  static int* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_group_scratch) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<int*>(p);
+  }
+  return addr[dev];
+}
+
+}  // namespace qmlr
+
+extern "C" int qmlr_group_by_element_noalloc(const int32_t* elem, int32_t n_atoms, int32_t n_el,
+                                             int32_t* perm, int32_t* elem_offsets, void* stream) {
+  QMLR_REQUIRE(n_el >= 1 && n_el <= kMaxEl, "n_el must be in 1..8 (got %d)", n_el);
+  QMLR_REQUIRE(n_atoms >= 0, "n_atoms must be >= 0");
+  QMLR_REQUIRE(n_atoms <= QMLR_GROUP_NOALLOC_MAX_ATOMS,
+               "n_atoms = %d exceeds the fixed scratch of the no-allocation grouping "
+               "(QMLR_GROUP_NOALLOC_MAX_ATOMS = %d); use qmlr_group_by_element with a workspace",
+               n_atoms, QMLR_GROUP_NOALLOC_MAX_ATOMS);
+  QMLR_REQUIRE(elem_offsets, "elem_offsets is NULL");
+  QMLR_REQUIRE(n_atoms == 0 || (elem && perm), "elem/perm are NULL");
+  int* scratch = group_scratch_address();
+  if (!scratch) {
+    set_error("cudaGetSymbolAddress of the grouping scratch failed on the current device");
+    return QMLR_ECUDA;
+  }
+  cudaStream_t s = as_stream(stream);
+  const int chunks = (n_atoms + kGroupChunk - 1) / kGroupChunk;
+  int* counts = scratch;
+  int* offsets = scratch + (size_t)kNoAllocChunks * kMaxEl;
+  // counts and offsets of every chunk used are written by the kernels below
+  // before they are read, so nothing left over from an earlier call is used.
+  if (chunks > 0) {
+    group_count_kernel<<<chunks, kGroupChunk, 0, s>>>(elem, n_atoms, n_el, counts, device_error_ptr());
+    QMLR_LAUNCH_CHECK();
+  }
+  group_scan_kernel<<<1, 256, 0, s>>>(counts, chunks, n_el, offsets, elem_offsets);
+  QMLR_LAUNCH_CHECK();
+  if (chunks > 0) {
+    group_scatter_kernel<<<chunks, kGroupChunk, 0, s>>>(elem, n_atoms, n_el, offsets, perm);
+    QMLR_LAUNCH_CHECK();
+  }
   return QMLR_OK;
 }

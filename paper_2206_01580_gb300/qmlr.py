@@ -56,6 +56,7 @@ _SIGS = {
     "qmlr_fchl19_vjp": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, P, I32, VP]),
     "qmlr_group_workspace_bytes": (C.c_int64, [I32]),
     "qmlr_group_by_element": (C.c_int, [P, I32, I32, P, P, P, I64, VP]),
+    "qmlr_group_by_element_noalloc": (C.c_int, [P, I32, I32, P, P, VP]),
     "qmlr_project": (C.c_int, [P, I32, I32, P, P, I32, I32, P, I32, P, VP]),
     "qmlr_project_t": (C.c_int, [P, I32, P, P, I32, I32, P, I32, I32, P, I32, VP]),
     "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
