@@ -113,6 +113,27 @@ int qmlr_fchl19_vjp(const float* coords, const int32_t* elem, const int32_t* mol
                     const qmlr_fchl19_params* p, const float* grad_rep, int32_t rep_ld,
                     float* grad_coords, int32_t accumulate, void* stream);
 
+/*
+ * Jacobian rows of FCHL19 (forward mode, for the force rows of energy+force
+ * training): jac_ptr int64 [n_mol+1] row offsets, jac_ptr[m] = sum_{m'<m} 3 M_{m'}^2,
+ * written by qmlr_jac_offsets (which also returns the total on the host,
+ * synchronously, when host_total is not NULL).
+ */
+int qmlr_jac_offsets(const int32_t* mol_ptr, int32_t n_mol, int64_t* jac_ptr, int64_t* host_total,
+                     void* stream);
+
+/*
+ * jac float [jac_ptr[n_mol]][rep_ld]: row jac_ptr[m] + (I*M + k)*3 + x holds
+ * d rho_{I} / d r_{k,x} for centre I and atom k of molecule m (local indices, M atoms):
+ * zero when k is beyond the cutoff of I; for k = I minus the sum over the
+ * neighbours (translation invariance). Three-body terms are recomputed.
+ * row_elem int32 [jac_ptr[n_mol]]: element of each row's centre (for the projection).
+ */
+int qmlr_fchl19_jac(const float* coords, const int32_t* elem, const int32_t* mol_ptr, int32_t n_mol,
+                    int32_t n_atoms, int32_t max_mol_atoms, const qmlr_fchl19_params* p,
+                    const int64_t* jac_ptr, float* jac, int32_t rep_ld, int32_t* row_elem,
+                    void* stream);
+
 /* ------------------------------------------------------------------------
  * Per-element projection (SORF section: SVD of the representations of each
  * element, rho_proj = rho^T U_e^{N_PCA}; GPU implementation paragraph: each
@@ -190,7 +211,9 @@ int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* perm,
 enum {
   QMLR_SORF_PER_ATOM = 0, /* out: float [n_atoms][N_F]  z for every atom */
   QMLR_SORF_PER_MOL = 1,  /* out: float [n_mol][N_F]    Z_m = sum_{I in m} z_I (fixed order) */
-  QMLR_SORF_ENERGY = 2    /* out: double [n_mol]        E_m = sum_{I in m} alpha^T z_I */
+  QMLR_SORF_ENERGY = 2,   /* out: double [n_mol]        E_m = sum_{I in m} alpha^T z_I */
+  QMLR_SORF_SIN_T = 4     /* out: float [n_atoms][d][N_F/d]  sqrt(2/N_F) sin(u) with the stack index
+                             fastest (feature f = s*d + i stored at [atom][i][s]); used by qmlr_force_rows */
 };
 
 /*
@@ -206,6 +229,22 @@ enum {
 int qmlr_sorf(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
               const uint32_t* sign_bits, int32_t T, const float* b, int32_t n_features,
               double sigma, const float* alpha, int32_t mode, void* out, void* stream);
+
+/*
+ * Force rows of the energy+force normal equations (RFF section: the
+ * derivative features dz/dr stacked under Z): for molecule m, atom k, axis x
+ *   rows[row0 + 3*(mol_ptr[m] + k) + x][f] = -dZ_m/dr_{k,x}[f]
+ *       = sum_{I in m} sqrt(2/N_F) sin(u_I[f]) (W t_{I,k,x})[f]
+ *   tangents float [n_jac_rows][d]: t_{I,k,x} = U_{e(I)}^T d rho_I/d r_{k,x} (qmlr_fchl19_jac
+ *            rows projected with qmlr_project), row jac_ptr[m] + (I*M + k)*3 + x
+ *   sin_t    float [n_atoms][d][N_F/d] from qmlr_sorf(..., QMLR_SORF_SIN_T)
+ *   rows     float, row stride ld >= N_F
+ * The sum over centres I runs in order (deterministic).
+ */
+int qmlr_force_rows(const float* tangents, int32_t d, const int64_t* jac_ptr, const int32_t* mol_ptr,
+                    int32_t n_mol, const float* sin_t, const uint32_t* sign_bits, int32_t T,
+                    int32_t n_features, double sigma, float* rows, int64_t ld, int64_t row0,
+                    void* stream);
 
 /* Number of stack parts qmlr_sorf_grad splits N_F/d stacks into: ceil(N_F/d / 128). */
 int32_t qmlr_sorf_parts(int32_t n_features, int32_t d);

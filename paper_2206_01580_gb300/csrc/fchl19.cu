@@ -482,6 +482,223 @@ fchl19_vjp_kernel(const float* __restrict__ coords, const int32_t* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Jacobian blocks (forward mode): for centre I and atom k of the same molecule,
+// the three rows d rho_I / d r_{k,x} (x = 0, 1, 2). Neighbour blocks are formed
+// from the two-body term of the pair (I, k) and every three-body term in which
+// k is one of the two neighbours (recomputed here); atoms beyond the cutoff
+// give zero rows; the centre's own block is minus the sum of its neighbours'
+// blocks (translation invariance), summed in neighbour order.
+//   row index = jac_ptr[m] + (I_local * M + k_local) * 3 + x
+
+struct JacWarp {
+  float4* pos;    // [mxp]
+  float4* nb_u;   // [mxp]
+  float4* nb_2b;  // [mxp]
+  float4* pairs;  // [32][4]: cA (cos, sin), hA (cos, sin) | cC (cos, sin), xbar, bin | uC, -
+  float* blk;     // [3][rp]
+  float* cblk;    // [3][rp]
+  int* nb_el;     // [mxp]
+  int* nb_idx;    // [mxp]
+};
+__host__ __device__ __forceinline__ size_t jac_warp_bytes(int mxp, int rp) {
+  return (size_t)mxp * 56 + (size_t)rp * 24 + 32 * 64;
+}
+__device__ __forceinline__ JacWarp carve_jac(char* base, int mxp, int rp) {
+  JacWarp s;
+  s.pos = reinterpret_cast<float4*>(base);
+  s.nb_u = s.pos + mxp;
+  s.nb_2b = s.nb_u + mxp;
+  s.pairs = s.nb_2b + mxp;
+  s.blk = reinterpret_cast<float*>(s.pairs + 32 * 4);
+  s.cblk = s.blk + 3 * rp;
+  s.nb_el = reinterpret_cast<int*>(s.cblk + 3 * rp);
+  s.nb_idx = s.nb_el + mxp;
+  return s;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsFwd)
+fchl19_jac_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
+                  const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp, int rp,
+                  Fchl19Consts c, const int64_t* __restrict__ jac_ptr, float* __restrict__ jac,
+                  int rep_ld, int32_t* __restrict__ row_elem, int* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int atom = blockIdx.x * kWarpsFwd + warp;
+  if (atom >= n_atoms) return;
+  JacWarp s = carve_jac(smem_raw + warp * jac_warp_bytes(mxp, rp), mxp, rp);
+  const int m = find_molecule(mol_ptr, n_mol, atom);
+  const int a0 = __ldg(mol_ptr + m);
+  const int M = __ldg(mol_ptr + m + 1) - a0;
+  const int il = atom - a0;
+  if (M > mx) {
+    if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+    return;
+  }
+  const long base_row = jac_ptr[m] + (long)il * M * 3;
+  const int ei = __ldg(elem + atom);
+  for (int r = lane; r < 3 * M; r += 32) row_elem[base_row + r] = (ei >= 0 && ei < c.n_el) ? ei : 0;
+  stage_molecule(coords, elem, a0, M, c.n_el, s.pos, lane, 32, err);
+  for (int k = lane; k < 3 * rp; k += 32) s.cblk[k] = 0.f;
+  __syncwarp();
+  const int n = neighbour_list(s.pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
+
+  int next_nb = 0;
+  for (int kl = 0; kl < M; ++kl) {
+    float* out = jac + (base_row + (long)kl * 3) * rep_ld;
+    if (kl == il) continue;                                   // written last
+    if (next_nb >= n || s.nb_idx[next_nb] != kl) {            // beyond the cutoff: zero rows
+      for (int q = lane; q < 3 * rep_ld; q += 32) out[q] = 0.f;
+      continue;
+    }
+    const int kn = next_nb++;
+    for (int q = lane; q < 3 * rp; q += 32) s.blk[q] = 0.f;
+    __syncwarp();
+    const float4 uA = s.nb_u[kn];
+    const float A = uA.w;
+    // two-body term of the pair (I, k): d G / d r_k = G'(A) uA
+    {
+      const float4 t = s.nb_2b[kn];
+      const float inv_r = 1.0f / A;
+      const float s2 = 0.5f / t.y;
+      const float sd = sqrtf(s2);
+      const float rr_eta = A * A + c.eta2;
+      const float ds = -c.eta2 / (sd * A * rr_eta);
+      const float dmu = inv_r + c.eta2 / (A * rr_eta);
+      const float fc = t.w;
+      const float dfc = cutoff_df(A, c);
+      const float rN = expf(-c.N2 * logf(A));
+      const float P = fc * rN;
+      const float dP = rN * (dfc - c.N2 * fc * inv_r);
+      const int b0 = s.nb_el[kn] * c.n2;
+      for (int q = lane; q < c.n2; q += 32) {
+        const float a = c.rs2_log[q] - t.x;
+        const float L = c.rs2_inv[q] * c.inv_sqrt_2pi / sd * expf(-a * a * t.y);
+        const float dlnL = -ds / sd + a * dmu / s2 + a * a * ds / (s2 * sd);
+        const float g = L * (dP + P * dlnL);
+        s.blk[0 * rp + b0 + q] += g * uA.x;
+        s.blk[1 * rp + b0 + q] += g * uA.y;
+        s.blk[2 * rp + b0 + q] += g * uA.z;
+      }
+    }
+    __syncwarp();
+    // three-body terms with k as one of the two neighbours, the other neighbour j
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      const int jn = j0 + lane;
+      bool ok = false;
+      float4 q0 = make_float4(0, 0, 0, 0), q1 = q0, q2 = q0;
+      if (jn < n && jn != kn) {
+        const float4 uB = s.nb_u[jn];
+        const float B = uB.w;
+        const float vx = uB.x * B - uA.x * A, vy = uB.y * B - uA.y * A, vz = uB.z * B - uA.z * A;
+        const float C2 = vx * vx + vy * vy + vz * vz;
+        if (C2 < c.rcut2) {
+          ok = true;
+          const float C = sqrtf(C2);
+          const float icc = 1.0f / C;
+          const float ux = vx * icc, uy = vy * icc, uz = vz * icc;   // unit k -> j
+          const float ci = uA.x * uB.x + uA.y * uB.y + uA.z * uB.z;
+          const float crx = uA.y * uB.z - uA.z * uB.y;
+          const float cry = uA.z * uB.x - uA.x * uB.z;
+          const float crz = uA.x * uB.y - uA.y * uB.x;
+          const float si = sqrtf(crx * crx + cry * cry + crz * crz);
+          const float ck = -(uA.x * ux + uA.y * uy + uA.z * uz);   // angle at k (first neighbour)
+          const float cj = (uB.x * ux + uB.y * uy + uB.z * uz);    // angle at j (second neighbour)
+          // sides: a = A (I-k), b = B (I-j), cc = C (k-j); "first" = k, "second" = j
+          const float a = A, b = B, cc = C;
+          const float dci_da = (a - b * ci) / (a * b), dci_dc = -cc / (a * b);
+          const float dcf_da = (a - cc * ck) / (a * cc), dcf_dc = (cc - a * ck) / (a * cc);
+          const float dcs_da = -a / (b * cc), dcs_dc = (cc - b * cj) / (b * cc);
+          const float Q = 1.0f + 3.0f * ci * ck * cj;
+          const float dQ_da = 3.0f * (dci_da * ck * cj + ci * dcf_da * cj + ci * ck * dcs_da);
+          const float dQ_dc = 3.0f * (dci_dc * ck * cj + ci * dcf_dc * cj + ci * ck * dcs_dc);
+          const float R3 = expf(-c.N3 * logf(a * b * cc));
+          const float fa = s.nb_2b[kn].w, fb = s.nb_2b[jn].w, fcc = cutoff_f(cc, c);
+          const float dfa = cutoff_df(a, c), dfcc = cutoff_df(cc, c);
+          const float F3 = fa * fb * fcc;
+          const float W = c.w3 * Q * R3 * F3;
+          const float dW_da = c.w3 * R3 * (dQ_da * F3 - Q * F3 * c.N3 / a + Q * dfa * fb * fcc);
+          const float dW_dc = c.w3 * R3 * (dQ_dc * F3 - Q * F3 * c.N3 / cc + Q * fa * fb * dfcc);
+          const float Ac = c.ang2 * ci, As = c.ang2 * si;
+          const float dAc = c.ang2, dAs = si > 1e-7f ? -c.ang2 * ci / si : 0.0f;
+          const int bin = c.base3 + pair_index(s.nb_el[kn], s.nb_el[jn], c.n_el) * c.n3 * 2;
+          q0 = make_float4(dW_da * Ac + W * dAc * dci_da, dW_da * As + W * dAs * dci_da, 0.5f * W * Ac,
+                           0.5f * W * As);
+          q1 = make_float4(dW_dc * Ac + W * dAc * dci_dc, dW_dc * As + W * dAs * dci_dc, 0.5f * (a + b),
+                           __int_as_float(bin));
+          q2 = make_float4(ux, uy, uz, 0.f);
+        }
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int slot = __popc(mask & ((1u << lane) - 1u));
+        s.pairs[4 * slot + 0] = q0;
+        s.pairs[4 * slot + 1] = q1;
+        s.pairs[4 * slot + 2] = q2;
+      }
+      __syncwarp();
+      const int cnt = __popc(mask);
+      for (int t = 0; t < cnt; ++t) {
+        const float4 p0 = s.pairs[4 * t], p1 = s.pairs[4 * t + 1], p2 = s.pairs[4 * t + 2];
+        const int bin = __float_as_int(p1.w);
+        for (int q = lane; q < c.n3; q += 32) {
+          const float d = p1.z - c.rs3[q];
+          const float rad = expf(-c.eta3 * d * d);
+          const float drad = -2.0f * c.eta3 * d * rad;
+          // d v / d r_k = dv/da * uA - dv/dc * uC   (C = |r_j - r_k|)
+          const float da_c = rad * p0.x + drad * p0.z, da_s = rad * p0.y + drad * p0.w;
+          const float dc_c = rad * p1.x, dc_s = rad * p1.y;
+          const int bc = bin + 2 * q;
+          s.blk[0 * rp + bc] += da_c * uA.x - dc_c * p2.x;
+          s.blk[1 * rp + bc] += da_c * uA.y - dc_c * p2.y;
+          s.blk[2 * rp + bc] += da_c * uA.z - dc_c * p2.z;
+          s.blk[0 * rp + bc + 1] += da_s * uA.x - dc_s * p2.x;
+          s.blk[1 * rp + bc + 1] += da_s * uA.y - dc_s * p2.y;
+          s.blk[2 * rp + bc + 1] += da_s * uA.z - dc_s * p2.z;
+        }
+      }
+      __syncwarp();
+    }
+    // write the block; accumulate minus it into the centre's block
+    for (int x = 0; x < 3; ++x)
+      for (int q = lane; q < rep_ld; q += 32) {
+        const float v = q < c.rep_dim ? s.blk[x * rp + q] : 0.f;
+        out[(long)x * rep_ld + q] = v;
+        if (q < c.rep_dim) s.cblk[x * rp + q] -= v;
+      }
+    __syncwarp();
+  }
+  float* outc = jac + (base_row + (long)il * 3) * rep_ld;
+  for (int x = 0; x < 3; ++x)
+    for (int q = lane; q < rep_ld; q += 32) outc[(long)x * rep_ld + q] = q < c.rep_dim ? s.cblk[x * rp + q] : 0.f;
+}
+
+// jac_ptr[m] = sum_{m' < m} 3 M_{m'}^2 (one CTA, sequential over chunks of 1024 molecules)
+__global__ void jac_offsets_kernel(const int32_t* __restrict__ mol_ptr, int n_mol, int64_t* __restrict__ out) {
+  __shared__ long long part[1024];
+  long long carry = 0;
+  for (int base = 0; base < n_mol; base += 1024) {
+    const int m = base + threadIdx.x;
+    long long v = 0;
+    if (m < n_mol) {
+      const long long M = mol_ptr[m + 1] - mol_ptr[m];
+      v = 3 * M * M;
+    }
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const long long t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (m < n_mol) out[m] = carry + part[threadIdx.x] - v;
+    carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n_mol] = carry;
+}
+
 static int rep_pad_of(int rep_dim) { return (rep_dim + 3) & ~3; }
 
 static int check_geometry(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
@@ -563,6 +780,53 @@ extern "C" int qmlr_fchl19_vjp(const float* coords, const int32_t* elem, const i
   }
   fchl19_vjp_kernel<<<n_mol, 32 * kWarpsVjp, smem, as_stream(stream)>>>(
       coords, elem, mol_ptr, n_mol, mx, mxp, rp, c, grad_rep, rep_ld, grad_coords, accumulate,
+      device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_jac_offsets(const int32_t* mol_ptr, int32_t n_mol, int64_t* jac_ptr, int64_t* host_total,
+                                void* stream) {
+  QMLR_REQUIRE(mol_ptr && jac_ptr && n_mol >= 0, "bad arguments");
+  cudaStream_t st = as_stream(stream);
+  jac_offsets_kernel<<<1, 1024, 0, st>>>(mol_ptr, n_mol, jac_ptr);
+  QMLR_LAUNCH_CHECK();
+  if (host_total) {
+    int64_t t = 0;
+    QMLR_CUDA_TRY(cudaMemcpyAsync(&t, jac_ptr + n_mol, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    QMLR_CUDA_TRY(cudaStreamSynchronize(st));
+    *host_total = t;
+  }
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_fchl19_jac(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                               int32_t n_mol, int32_t n_atoms, int32_t max_mol_atoms,
+                               const qmlr_fchl19_params* p, const int64_t* jac_ptr, float* jac,
+                               int32_t rep_ld, int32_t* row_elem, void* stream) {
+  int rc = validate_params(p);
+  if (rc) return rc;
+  rc = check_geometry(coords, elem, mol_ptr, n_mol, n_atoms, max_mol_atoms);
+  if (rc) return rc;
+  const int rd = rep_dim_of(*p);
+  QMLR_REQUIRE(rep_ld >= rd, "rep_ld (%d) < rep_dim (%d)", rep_ld, rd);
+  QMLR_REQUIRE(n_atoms == 0 || (jac_ptr && jac && row_elem), "NULL pointer argument");
+  if (n_atoms == 0) return QMLR_OK;
+  const Fchl19Consts c = make_consts(*p);
+  const int rp = rep_pad_of(rd);
+  const int mx = max_mol_atoms;
+  const int mxp = (mx + 3) & ~3;
+  const size_t smem = kWarpsFwd * jac_warp_bytes(mxp, rp);
+  QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
+  static bool attr_set = false;
+  if (!attr_set) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_jac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    attr_set = true;
+  }
+  const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
+  fchl19_jac_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
+      coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, jac_ptr, jac, rep_ld, row_elem,
       device_error_ptr());
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;

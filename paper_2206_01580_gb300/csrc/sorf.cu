@@ -21,7 +21,7 @@ namespace qmlr {
 
 constexpr int kStacksPerCta = 128;
 
-enum SorfMode { M_PER_ATOM = 0, M_PER_MOL = 1, M_ENERGY = 2, M_ENERGY_GRAD = 3 };
+enum SorfMode { M_PER_ATOM = 0, M_PER_MOL = 1, M_ENERGY = 2, M_ENERGY_GRAD = 3, M_SIN_T = 4 };
 
 template <int D>
 __device__ __forceinline__ void fwht(float (&v)[D]) {
@@ -87,7 +87,7 @@ sorf_kernel(SorfArgs a) {
     for (int i = 0; i < D; ++i) work[i * (nt + 1) + tid] = 0.f;
 
   const float* bs = a.b + (long)(active ? s : 0) * D;
-  const float* as = (MODE >= M_ENERGY) ? a.alpha + (long)(active ? s : 0) * D : nullptr;
+  const float* as = (MODE == M_ENERGY || MODE == M_ENERGY_GRAD) ? a.alpha + (long)(active ? s : 0) * D : nullptr;
   double e_acc = 0.0;
 
   for (int atom = a0; atom < a1; ++atom) {
@@ -104,7 +104,14 @@ sorf_kernel(SorfArgs a) {
       flip<D>(v, w);
       fwht<D>(v);
     }
-    if (MODE == M_PER_ATOM) {
+    if (MODE == M_SIN_T) {
+      // out[atom][i][s] = sqrt(2/N_F) sin(u_i): stacks contiguous (coalesced across the warp)
+      if (active) {
+        float* o = static_cast<float*>(a.out) + (long)atom * a.n_features + s;
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[(long)i * a.n_stack] = a.pref * sinf(fmaf(v[i], a.scale, __ldg(bs + i)));
+      }
+    } else if (MODE == M_PER_ATOM) {
       if (active) {
         float* o = static_cast<float*>(a.out) + (long)atom * a.n_features + (long)s * D;
 #pragma unroll
@@ -180,12 +187,77 @@ sorf_kernel(SorfArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Force rows of the energy+force normal equations (RFF section: derivative
+// features dz/dr stacked under the energy rows). For molecule m, atom k, axis x:
+//   row = -dZ_m/dr_{k,x} = sum_I sqrt(2/N_F) sin(u_I) (.) (W t_{I,k,x})
+// with t_{I,k,x} = U_{e(I)}^T d rho_I / d r_{k,x} the projected Jacobian row and W
+// the linear SORF map (sign flips, Hadamard chain, sqrt(d)/sigma scale). One
+// thread per stack holds the tangent's d-vector in registers; the sum over
+// centres I runs in order in a shared-memory accumulator.
+template <int D>
+__global__ void __launch_bounds__(kStacksPerCta)
+force_rows_kernel(const float* __restrict__ tang, const int64_t* __restrict__ jac_ptr,
+                  const int32_t* __restrict__ mol_ptr, const float* __restrict__ sin_t,
+                  const uint32_t* __restrict__ sign_bits, int T, int n_stack, int n_features, float scale,
+                  float* __restrict__ rows, long ld, long row0) {
+  constexpr int W = (D + 31) / 32;
+  constexpr int CH = 16;   // centres staged per round
+  extern __shared__ __align__(16) float smem[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int part = blockIdx.y;
+  const int sidx = part * kStacksPerCta + tid;
+  const bool active = sidx < n_stack;
+  const int m = blockIdx.x;
+  const int a0 = mol_ptr[m], M = mol_ptr[m + 1] - a0;
+  const long jb = jac_ptr[m];
+  uint32_t* sg = reinterpret_cast<uint32_t*>(smem);                 // [T*W][nt]
+  float* ts = reinterpret_cast<float*>(sg + T * W * nt);            // [CH][D] staged tangents
+  float* acc = ts + CH * D;                                         // [D][nt+1]
+  for (int k = 0; k < T * W; ++k) sg[k * nt + tid] = active ? __ldg(sign_bits + (long)sidx * T * W + k) : 0u;
+  for (int kx = 0; kx < 3 * M; ++kx) {
+    const int kl = kx / 3, x = kx % 3;
+    for (int i = 0; i < D; ++i) acc[i * (nt + 1) + tid] = 0.f;
+    for (int c0 = 0; c0 < M; c0 += CH) {
+      const int cn = min(CH, M - c0);
+      __syncthreads();
+      for (int q = tid; q < cn * D; q += nt) {
+        const int ci = q / D, i = q % D;
+        ts[q] = __ldg(tang + (jb + ((long)(c0 + ci) * M + kl) * 3 + x) * D + i);
+      }
+      __syncthreads();
+      for (int ci = 0; ci < cn; ++ci) {
+        float v[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] = ts[ci * D + i];
+        for (int t = 0; t < T; ++t) {
+          uint32_t w[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) w[q] = sg[(t * W + q) * nt + tid];
+          flip<D>(v, w);
+          fwht<D>(v);
+        }
+        if (active) {
+          const float* sp = sin_t + (long)(a0 + c0 + ci) * n_features + sidx;
+#pragma unroll
+          for (int i = 0; i < D; ++i) acc[i * (nt + 1) + tid] += __ldg(sp + (long)i * n_stack) * v[i] * scale;
+        }
+      }
+    }
+    __syncthreads();
+    float* o = rows + (row0 + (long)(a0 + kl) * 3 + x) * ld + (long)part * kStacksPerCta * D;
+    const int nf = min(nt, n_stack - part * kStacksPerCta) * D;
+    for (int f = tid; f < nf; f += nt) o[f] = acc[(f % D) * (nt + 1) + f / D];
+  }
+}
+
 template <int D>
 static size_t sorf_smem(int mode, int T, int nt) {
   constexpr int W = (D + 31) / 32;
   size_t base = (size_t)D * 4 + (size_t)T * W * nt * 4;
   size_t work = 0;
   if (mode == M_PER_MOL) work = (size_t)D * (nt + 1) * 4;
+  if (mode == M_SIN_T) work = 0;
   if (mode == M_ENERGY) work = (size_t)nt * 8;
   if (mode == M_ENERGY_GRAD) work = std::max((size_t)nt * (D + 1) * 4, (size_t)nt * 8);
   return base + ((work + 15) & ~(size_t)15) + 16;
@@ -214,6 +286,7 @@ static int launch_d(const SorfArgs& a, int mode, int n_mol, cudaStream_t s) {
     case M_PER_ATOM: return launch_mode<D, M_PER_ATOM>(a, n_mol, s);
     case M_PER_MOL: return launch_mode<D, M_PER_MOL>(a, n_mol, s);
     case M_ENERGY: return launch_mode<D, M_ENERGY>(a, n_mol, s);
+    case M_SIN_T: return launch_mode<D, M_SIN_T>(a, n_mol, s);
     default: return launch_mode<D, M_ENERGY_GRAD>(a, n_mol, s);
   }
 }
@@ -229,7 +302,7 @@ static int sorf_dispatch(const float* x, int d, const int32_t* mol_ptr, int n_mo
   QMLR_REQUIRE(n_mol >= 0 && n_atoms >= 0, "negative sizes");
   if (n_mol == 0) return QMLR_OK;
   QMLR_REQUIRE(x && mol_ptr && sign_bits && b && out, "NULL pointer argument");
-  QMLR_REQUIRE(mode < M_ENERGY || alpha, "alpha is NULL");
+  QMLR_REQUIRE((mode != M_ENERGY && mode != M_ENERGY_GRAD) || alpha, "alpha is NULL");
   QMLR_REQUIRE(mode != M_ENERGY_GRAD || gx, "gx is NULL");
   SorfArgs a;
   a.x = x;
@@ -270,10 +343,53 @@ extern "C" int qmlr_sorf(const float* x, int32_t d, const int32_t* mol_ptr, int3
                          int32_t n_atoms, const uint32_t* sign_bits, int32_t T, const float* b,
                          int32_t n_features, double sigma, const float* alpha, int32_t mode,
                          void* out, void* stream) {
-  QMLR_REQUIRE(mode == QMLR_SORF_PER_ATOM || mode == QMLR_SORF_PER_MOL || mode == QMLR_SORF_ENERGY,
+  QMLR_REQUIRE(mode == QMLR_SORF_PER_ATOM || mode == QMLR_SORF_PER_MOL || mode == QMLR_SORF_ENERGY ||
+                   mode == QMLR_SORF_SIN_T,
                "unknown SORF mode %d", mode);
   return sorf_dispatch(x, d, mol_ptr, n_mol, n_atoms, sign_bits, T, b, n_features, sigma, alpha,
                        mode, out, nullptr, stream);
+}
+
+template <int D>
+static int launch_force_rows(const float* tang, const int64_t* jac_ptr, const int32_t* mol_ptr, int n_mol,
+                             const float* sin_t, const uint32_t* sign_bits, int T, int n_features,
+                             float scale, float* rows, long ld, long row0, cudaStream_t s) {
+  constexpr int W = (D + 31) / 32;
+  const int n_stack = n_features / D;
+  const int nt = std::min(kStacksPerCta, ((n_stack + 31) / 32) * 32);
+  const size_t smem = (size_t)T * W * nt * 4 + 16 * D * 4 + (size_t)D * (nt + 1) * 4;
+  QMLR_REQUIRE(smem <= 227 * 1024, "force-row shared memory request too large");
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(force_rows_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    attr = true;
+  }
+  dim3 grid(n_mol, (n_stack + kStacksPerCta - 1) / kStacksPerCta);
+  force_rows_kernel<D><<<grid, nt, smem, s>>>(tang, jac_ptr, mol_ptr, sin_t, sign_bits, T, n_stack,
+                                              n_features, scale, rows, ld, row0);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_force_rows(const float* tangents, int32_t d, const int64_t* jac_ptr,
+                               const int32_t* mol_ptr, int32_t n_mol, const float* sin_t,
+                               const uint32_t* sign_bits, int32_t T, int32_t n_features, double sigma,
+                               float* rows, int64_t ld, int64_t row0, void* stream) {
+  QMLR_REQUIRE(d == 16 || d == 32 || d == 64 || d == 128, "d must be 16, 32, 64 or 128 (got %d)", d);
+  QMLR_REQUIRE(T >= 1 && T <= 4, "T must be in 1..4");
+  QMLR_REQUIRE(n_features >= d && n_features % d == 0, "n_features must be a positive multiple of d");
+  QMLR_REQUIRE(ld >= n_features && row0 >= 0 && sigma > 0, "bad row layout or sigma");
+  if (n_mol == 0) return QMLR_OK;
+  QMLR_REQUIRE(tangents && jac_ptr && mol_ptr && sin_t && sign_bits && rows, "NULL pointer argument");
+  const float scale = (float)(sqrt((double)d) / sigma / pow((double)d, 0.5 * T));
+  cudaStream_t s = as_stream(stream);
+  switch (d) {
+    case 16: return launch_force_rows<16>(tangents, jac_ptr, mol_ptr, n_mol, sin_t, sign_bits, T, n_features, scale, rows, ld, row0, s);
+    case 32: return launch_force_rows<32>(tangents, jac_ptr, mol_ptr, n_mol, sin_t, sign_bits, T, n_features, scale, rows, ld, row0, s);
+    case 64: return launch_force_rows<64>(tangents, jac_ptr, mol_ptr, n_mol, sin_t, sign_bits, T, n_features, scale, rows, ld, row0, s);
+    default: return launch_force_rows<128>(tangents, jac_ptr, mol_ptr, n_mol, sin_t, sign_bits, T, n_features, scale, rows, ld, row0, s);
+  }
 }
 
 extern "C" int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,

@@ -94,3 +94,36 @@ def train_energy(batch: Batch, energies, spec: FeatureSpec, lam: float, U=None,
     y = torch.as_tensor(np.asarray(energies, dtype=np.float64)).cuda()
     alpha, it, rel = solve(Z, y, lam, precision, **solve_kw)
     return alpha, U, it, rel
+
+
+def energy_force_rows(batch: Batch, spec: FeatureSpec, U):
+    """Rows of the energy+force normal equations: [Z; -dZ/dr] with Z [n_mol, N_F]
+    stacked over the force rows [3 n_atoms, N_F] (row 3k+x pairs with F[k, x])."""
+    rep, perm, offs = representations(batch, spec)
+    x = qmlr.project(rep, spec.p.rep_dim, perm, offs, spec.p.n_el, U)
+    n_mol, n_atoms = batch.n_mol, batch.n_atoms
+    rows = torch.empty((n_mol + 3 * n_atoms, spec.n_features), device="cuda", dtype=torch.float32)
+    rows[:n_mol] = qmlr.sorf(x, batch.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
+    sin_t = qmlr.sorf(x, batch.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_SIN_T)
+    del rep, x
+    jac_ptr, jac, row_elem = qmlr.fchl19_jacobian(batch.coords, batch.elem, batch.mol_ptr, batch.max_atoms, spec.p)
+    jperm, joffs = qmlr.group_by_element(row_elem, spec.p.n_el)
+    tangents = qmlr.project(jac, spec.p.rep_dim, jperm, joffs, spec.p.n_el, U)
+    del jac
+    qmlr.force_rows(tangents, jac_ptr, batch.mol_ptr, sin_t, spec.sign_bits, spec.T, spec.n_features,
+                    spec.sigma, out=rows, row0=n_mol)
+    return rows
+
+
+def train_energy_force(batch: Batch, energies, forces, spec: FeatureSpec, lam: float, U=None,
+                       precision: int = qmlr.GRAM_BF16X6, **solve_kw):
+    """Energy + force training: returns (alpha, U, iterations, relative residual)."""
+    if U is None:
+        rep, perm, offs = representations(batch, spec)
+        U = fit_pca(rep, perm, offs, spec)
+        del rep
+    rows = energy_force_rows(batch, spec, U)
+    y = torch.cat([torch.as_tensor(np.asarray(energies, dtype=np.float64)),
+                   torch.as_tensor(np.asarray(forces, dtype=np.float64)).reshape(-1)]).cuda()
+    alpha, it, rel = solve(rows, y, lam, precision, **solve_kw)
+    return alpha, U, it, rel

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libqmlr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTCONV, EDEVICE = range(8)
-SORF_PER_ATOM, SORF_PER_MOL, SORF_ENERGY = 0, 1, 2
+SORF_PER_ATOM, SORF_PER_MOL, SORF_ENERGY, SORF_SIN_T = 0, 1, 2, 4
 
 
 class QMLRError(RuntimeError):
@@ -54,6 +54,9 @@ _SIGS = {
     "qmlr_fchl19_rep_dim": (C.c_int, [C.POINTER(_Params), C.POINTER(C.c_int32)]),
     "qmlr_fchl19": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, VP]),
     "qmlr_fchl19_vjp": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, P, I32, VP]),
+    "qmlr_jac_offsets": (C.c_int, [P, I32, P, C.POINTER(C.c_int64), VP]),
+    "qmlr_fchl19_jac": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, P, I32, P, VP]),
+    "qmlr_force_rows": (C.c_int, [P, I32, P, P, I32, P, P, I32, I32, D, P, I64, I64, VP]),
     "qmlr_group_workspace_bytes": (C.c_int64, [I32]),
     "qmlr_group_by_element": (C.c_int, [P, I32, I32, P, P, P, I64, VP]),
     "qmlr_group_by_element_noalloc": (C.c_int, [P, I32, I32, P, P, VP]),
@@ -244,7 +247,7 @@ def sorf(x, mol_ptr, sign_bits, T: int, b, sigma: float, mode: int, alpha=None, 
     n_atoms, d = x.shape
     n_mol = mol_ptr.shape[0] - 1
     nf = n_features or b.shape[0]
-    if mode == SORF_PER_ATOM:
+    if mode in (SORF_PER_ATOM, SORF_SIN_T):
         out = torch.empty((n_atoms, nf), device="cuda", dtype=torch.float32)
     elif mode == SORF_PER_MOL:
         out = torch.empty((n_mol, nf), device="cuda", dtype=torch.float32)
@@ -440,3 +443,40 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# force rows for energy + force training
+
+
+def fchl19_jacobian(coords, elem, mol_ptr, max_atoms: int, p: FCHL19Params, rep_ld: int | None = None):
+    """(jac_ptr, jac [n_rows, rep_ld], row_elem) of FCHL19 Jacobian rows."""
+    coords = _dev(coords, torch.float32)
+    elem = _dev(elem, torch.int32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    n_atoms, n_mol = coords.shape[0], mol_ptr.shape[0] - 1
+    rep_ld = rep_ld or rep_ld_of(p.rep_dim)
+    jac_ptr = torch.empty(n_mol + 1, device="cuda", dtype=torch.int64)
+    total = C.c_int64(0)
+    _check(lib().qmlr_jac_offsets(_ptr(mol_ptr), n_mol, _ptr(jac_ptr), C.byref(total), _stream()))
+    jac = torch.empty((max(total.value, 1), rep_ld), device="cuda", dtype=torch.float32)
+    row_elem = torch.empty(max(total.value, 1), device="cuda", dtype=torch.int32)
+    cp = c_params(p)
+    _check(lib().qmlr_fchl19_jac(_ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol, n_atoms, max_atoms,
+                                 C.byref(cp), _ptr(jac_ptr), _ptr(jac), rep_ld, _ptr(row_elem), _stream()))
+    return jac_ptr, jac[:total.value], row_elem[:total.value]
+
+
+def force_rows(tangents, jac_ptr, mol_ptr, sin_t, sign_bits, T: int, n_features: int, sigma: float,
+               out=None, row0: int = 0):
+    """Force rows [3 n_atoms, N_F] (or written into `out` from row `row0`)."""
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    n_mol = mol_ptr.shape[0] - 1
+    n_atoms = sin_t.shape[0]
+    d = tangents.shape[1]
+    if out is None:
+        out = torch.empty((3 * n_atoms, n_features), device="cuda", dtype=torch.float32)
+    _check(lib().qmlr_force_rows(_ptr(tangents), d, _ptr(jac_ptr), _ptr(mol_ptr), n_mol, _ptr(sin_t),
+                                 _ptr(sign_bits), T, n_features, float(sigma), _ptr(out), out.stride(0),
+                                 row0, _stream()))
+    return out
