@@ -406,6 +406,61 @@ int qmlr_predict_ef(qmlr_model* m, const float* coords, const int32_t* elem,
                     const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms, double* energies,
                     float* forces, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching server for energy + force prediction (the timings
+ * section's observation that single configurations leave the GPU idle and
+ * batching cuts the cost per configuration). Host-side runtime in the library.
+ * ------------------------------------------------------------------------ */
+typedef struct qmlr_server qmlr_server;
+
+typedef struct qmlr_serve_config {
+  int32_t n_lanes;            /* batches in flight on the device (1..8), one CUDA stream each */
+  int32_t max_batch_atoms;    /* atoms per batch (>= the model's max_mol_atoms) */
+  int32_t max_batch_mols;     /* molecules per batch (real + padding) */
+  int32_t max_slots;          /* requests held (queued, running or not yet collected) */
+  int64_t max_inflight_atoms; /* atoms held */
+  int64_t mem_budget_bytes;   /* device memory the lanes may take (<= 0: no limit) */
+  int32_t use_graphs;         /* capture each (lane, batch-size bucket) prediction as a CUDA graph */
+} qmlr_serve_config;
+
+typedef struct qmlr_serve_report {
+  int64_t completed, rejected, batches;
+  double p50_us, p99_us, mean_us, max_us;  /* submit -> result ready latency */
+  double throughput_rps;                   /* completed requests per second (first submit -> last result) */
+  double us_per_atom;                      /* same span per predicted atom */
+  double mean_batch_atoms;
+} qmlr_serve_report;
+
+/*
+ * Starts a server for a model on the current device: allocates n_lanes
+ * workspaces and pinned staging buffers and a batcher thread. QMLR_EINVAL
+ * when the lanes do not fit mem_budget_bytes. The model must outlive the server.
+ */
+int qmlr_serve_create(qmlr_model* m, const qmlr_serve_config* cfg, qmlr_server** out);
+
+/*
+ * Admits one molecule (host coordinates float [n_atoms][3], elements int32
+ * [n_atoms]; copied before return). QMLR_EBUSY when the request or atom limit
+ * of held work would be exceeded (nothing is queued). Thread-safe.
+ */
+int qmlr_serve_submit(qmlr_server* s, const float* host_coords, const int32_t* host_elem,
+                      int32_t n_atoms, uint64_t* ticket);
+
+/*
+ * Waits up to timeout_us (bounded at 600 s) for a ticket's result and
+ * collects it: *host_E (double) and host_F float [n_atoms][3] (F = -dE/dr;
+ * either may be NULL). QMLR_ETIMEOUT if not ready (the ticket stays valid).
+ * A collected ticket is released. Thread-safe.
+ */
+int qmlr_serve_poll(qmlr_server* s, uint64_t ticket, double* host_E, float* host_F,
+                    int64_t timeout_us);
+
+int qmlr_serve_stats(qmlr_server* s, qmlr_serve_report* out);
+int qmlr_serve_reset_stats(qmlr_server* s);
+
+/* Finishes the batches in flight, stops the batcher and frees the server. */
+int qmlr_serve_destroy(qmlr_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,26 +11,7 @@
 //   -> transposed projection -> FCHL19 VJP -> F = -grad.
 #include "common.cuh"
 
-struct qmlr_model {
-  qmlr_fchl19_params p;
-  int max_mol_atoms;
-  int rep_dim, rep_ld, d, T, n_features, n_part;
-  double sigma;
-  float* U;          // [n_el][rep_dim][d]
-  uint32_t* signs;   // [n_stack][T][W]
-  float* b;          // [N_F]
-  float* alpha;      // [N_F]
-  // workspace
-  int cap_atoms = 0;
-  float* rep = nullptr;     // [cap][rep_ld]
-  float* x = nullptr;       // [cap][d]
-  float* gx = nullptr;      // [n_part][cap][d]
-  float* grep = nullptr;    // [cap][rep_ld]
-  int32_t* perm = nullptr;  // [cap]
-  int32_t* offs = nullptr;  // [n_el+1]
-  void* gwork = nullptr;
-  int64_t gwork_bytes = 0;
-};
+#include "model_internal.cuh"
 
 namespace qmlr {
 
@@ -39,17 +20,83 @@ __global__ void negate_kernel(float* v, long n) {
   if (i < n) v[i] = -v[i];
 }
 
-static void free_ws(qmlr_model* m) {
-  cudaFree(m->rep);
-  cudaFree(m->x);
-  cudaFree(m->gx);
-  cudaFree(m->grep);
-  cudaFree(m->perm);
-  cudaFree(m->gwork);
-  m->rep = m->x = m->gx = m->grep = nullptr;
-  m->perm = nullptr;
-  m->gwork = nullptr;
-  m->cap_atoms = 0;
+void PredictWorkspace::release() {
+  cudaFree(rep);
+  cudaFree(x);
+  cudaFree(gx);
+  cudaFree(grep);
+  cudaFree(perm);
+  cudaFree(offs);
+  cudaFree(gwork);
+  rep = x = gx = grep = nullptr;
+  perm = offs = nullptr;
+  gwork = nullptr;
+  cap_atoms = 0;
+}
+
+int PredictWorkspace::reserve(const qmlr_model* m, int max_atoms) {
+  if (max_atoms <= cap_atoms && offs) return QMLR_OK;
+  release();
+  const size_t n = (size_t)std::max(max_atoms, 1);
+  gwork_bytes = qmlr_group_workspace_bytes(max_atoms);
+  cudaError_t e = cudaMalloc(&rep, n * m->rep_ld * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&x, n * m->d * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&gx, (size_t)m->n_part * n * m->d * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&grep, n * m->rep_ld * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&perm, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&offs, 16 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&gwork, gwork_bytes);
+  if (e != cudaSuccess) {
+    release();
+    set_error("workspace allocation failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? QMLR_ENOMEM : QMLR_ECUDA;
+  }
+  cap_atoms = max_atoms;
+  return QMLR_OK;
+}
+
+size_t PredictWorkspace::bytes_per_atom(const qmlr_model* m) {
+  return (size_t)m->rep_ld * 8 + (size_t)m->d * 4 * (1 + m->n_part) + 4 + 64;
+}
+
+int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
+                  const int32_t* mol_ptr, int n_mol, int n_atoms, double* energies, float* forces,
+                  cudaStream_t s) {
+  QMLR_REQUIRE(n_atoms >= 0 && n_mol >= 0, "negative sizes");
+  QMLR_REQUIRE(n_atoms <= w.cap_atoms,
+               "batch of %d atoms exceeds the reserved capacity %d (call qmlr_model_reserve)", n_atoms,
+               w.cap_atoms);
+  QMLR_REQUIRE(energies || n_mol == 0, "energies is NULL");
+  if (n_mol == 0) return QMLR_OK;
+  void* stream = s;
+  int rc;
+  const int n_el = m->p.n_el;
+  if (n_atoms == 0) {
+    QMLR_CUDA_TRY(cudaMemsetAsync(energies, 0, sizeof(double) * n_mol, s));
+    return QMLR_OK;
+  }
+  if ((rc = qmlr_fchl19(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.rep, m->rep_ld, stream)))
+    return rc;
+  if ((rc = qmlr_group_by_element(elem, n_atoms, n_el, w.perm, w.offs, w.gwork, w.gwork_bytes, stream)))
+    return rc;
+  if ((rc = qmlr_project(w.rep, m->rep_ld, m->rep_dim, w.perm, w.offs, n_atoms, n_el, m->U, m->d, w.x, stream)))
+    return rc;
+  if (!forces) {
+    return qmlr_sorf(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->b, m->n_features, m->sigma,
+                     m->alpha, QMLR_SORF_ENERGY, energies, stream);
+  }
+  if ((rc = qmlr_sorf_grad(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->b, m->n_features, m->sigma,
+                           m->alpha, energies, w.gx, stream)))
+    return rc;
+  if ((rc = qmlr_project_t(w.gx, m->n_part, w.perm, w.offs, n_atoms, n_el, m->U, m->d, m->rep_dim, w.grep,
+                           m->rep_ld, stream)))
+    return rc;
+  if ((rc = qmlr_fchl19_vjp(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.grep, m->rep_ld,
+                            forces, 0, stream)))
+    return rc;
+  negate_kernel<<<(unsigned)((3L * n_atoms + 255) / 256), 256, 0, s>>>(forces, 3L * n_atoms);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
 }
 
 }  // namespace qmlr
@@ -86,7 +133,6 @@ extern "C" int qmlr_model_create(const qmlr_fchl19_params* p, int32_t max_mol_at
   if (e == cudaSuccess) e = cudaMalloc(&m->signs, nS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&m->b, (size_t)n_features * 4);
   if (e == cudaSuccess) e = cudaMalloc(&m->alpha, (size_t)n_features * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&m->offs, 16 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(m->U, host_U, nU * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->signs, host_sign_bits, nS * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->b, host_b, (size_t)n_features * 4, cudaMemcpyHostToDevice);
@@ -102,12 +148,11 @@ extern "C" int qmlr_model_create(const qmlr_fchl19_params* p, int32_t max_mol_at
 
 extern "C" int qmlr_model_destroy(qmlr_model* m) {
   if (!m) return QMLR_OK;
-  free_ws(m);
+  m->ws.release();
   cudaFree(m->U);
   cudaFree(m->signs);
   cudaFree(m->b);
   cudaFree(m->alpha);
-  cudaFree(m->offs);
   delete m;
   return QMLR_OK;
 }
@@ -135,63 +180,12 @@ extern "C" int qmlr_model_set_alpha_device(qmlr_model* m, const double* alpha, v
 
 extern "C" int qmlr_model_reserve(qmlr_model* m, int32_t max_atoms) {
   QMLR_REQUIRE(m && max_atoms >= 0, "bad arguments");
-  if (max_atoms <= m->cap_atoms) return QMLR_OK;
-  free_ws(m);
-  const size_t n = (size_t)max_atoms;
-  m->gwork_bytes = qmlr_group_workspace_bytes(max_atoms);
-  cudaError_t e = cudaMalloc(&m->rep, n * m->rep_ld * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&m->x, n * m->d * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&m->gx, (size_t)m->n_part * n * m->d * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&m->grep, n * m->rep_ld * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&m->perm, std::max<size_t>(n, 1) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&m->gwork, m->gwork_bytes);
-  if (e != cudaSuccess) {
-    free_ws(m);
-    set_error("workspace allocation failed: %s", cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? QMLR_ENOMEM : QMLR_ECUDA;
-  }
-  m->cap_atoms = max_atoms;
-  return QMLR_OK;
+  return m->ws.reserve(m, max_atoms);
 }
 
 extern "C" int qmlr_predict_ef(qmlr_model* m, const float* coords, const int32_t* elem,
                                const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
                                double* energies, float* forces, void* stream) {
   QMLR_REQUIRE(m, "model is NULL");
-  QMLR_REQUIRE(n_atoms >= 0 && n_mol >= 0, "negative sizes");
-  QMLR_REQUIRE(n_atoms <= m->cap_atoms,
-               "batch of %d atoms exceeds the reserved capacity %d (call qmlr_model_reserve)", n_atoms,
-               m->cap_atoms);
-  QMLR_REQUIRE(energies || n_mol == 0, "energies is NULL");
-  if (n_mol == 0) return QMLR_OK;
-  cudaStream_t s = as_stream(stream);
-  int rc;
-  const int n_el = m->p.n_el;
-  if (n_atoms == 0) {
-    QMLR_CUDA_TRY(cudaMemsetAsync(energies, 0, sizeof(double) * n_mol, s));
-    return QMLR_OK;
-  }
-  if ((rc = qmlr_fchl19(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, m->rep, m->rep_ld, stream)))
-    return rc;
-  if ((rc = qmlr_group_by_element(elem, n_atoms, n_el, m->perm, m->offs, m->gwork, m->gwork_bytes, stream)))
-    return rc;
-  if ((rc = qmlr_project(m->rep, m->rep_ld, m->rep_dim, m->perm, m->offs, n_atoms, n_el, m->U, m->d, m->x,
-                         stream)))
-    return rc;
-  if (!forces) {
-    return qmlr_sorf(m->x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->b, m->n_features, m->sigma,
-                     m->alpha, QMLR_SORF_ENERGY, energies, stream);
-  }
-  if ((rc = qmlr_sorf_grad(m->x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->b, m->n_features, m->sigma,
-                           m->alpha, energies, m->gx, stream)))
-    return rc;
-  if ((rc = qmlr_project_t(m->gx, m->n_part, m->perm, m->offs, n_atoms, n_el, m->U, m->d, m->rep_dim, m->grep,
-                           m->rep_ld, stream)))
-    return rc;
-  if ((rc = qmlr_fchl19_vjp(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, m->grep, m->rep_ld,
-                            forces, 0, stream)))
-    return rc;
-  negate_kernel<<<(unsigned)((3L * n_atoms + 255) / 256), 256, 0, s>>>(forces, 3L * n_atoms);
-  QMLR_LAUNCH_CHECK();
-  return QMLR_OK;
+  return predict_ef_ws(m, m->ws, coords, elem, mol_ptr, n_mol, n_atoms, energies, forces, as_stream(stream));
 }

@@ -1,0 +1,44 @@
+// Internal layout of the model handle (shared by model.cu and serve.cu).
+#pragma once
+
+#include "common.cuh"
+
+struct qmlr_model;
+
+namespace qmlr {
+
+// Device buffers of one prediction pass for batches of up to cap_atoms atoms.
+struct PredictWorkspace {
+  int cap_atoms = 0;
+  float* rep = nullptr;     // [cap][rep_ld]
+  float* x = nullptr;       // [cap][d]
+  float* gx = nullptr;      // [n_part][cap][d]
+  float* grep = nullptr;    // [cap][rep_ld]
+  int32_t* perm = nullptr;  // [cap]
+  int32_t* offs = nullptr;  // [n_el+1]
+  void* gwork = nullptr;
+  int64_t gwork_bytes = 0;
+
+  int reserve(const qmlr_model* m, int max_atoms);
+  void release();
+  static size_t bytes_per_atom(const qmlr_model* m);
+};
+
+// Energies and forces of a CSR batch with the given workspace (no allocation).
+int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
+                  const int32_t* mol_ptr, int n_mol, int n_atoms, double* energies, float* forces,
+                  cudaStream_t s);
+
+}  // namespace qmlr
+
+struct qmlr_model {
+  qmlr_fchl19_params p;
+  int max_mol_atoms;
+  int rep_dim, rep_ld, d, T, n_features, n_part;
+  double sigma;
+  float* U = nullptr;          // [n_el][rep_dim][d]
+  uint32_t* signs = nullptr;   // [n_stack][T][W]
+  float* b = nullptr;          // [N_F]
+  float* alpha = nullptr;      // [N_F]
+  qmlr::PredictWorkspace ws;   // workspace of qmlr_predict_ef
+};

@@ -34,6 +34,18 @@ class _Params(C.Structure):
                 ("c3", C.c_double), ("zeta", C.c_double), ("rcut", C.c_double)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("n_lanes", C.c_int32), ("max_batch_atoms", C.c_int32), ("max_batch_mols", C.c_int32),
+                ("max_slots", C.c_int32), ("max_inflight_atoms", C.c_int64), ("mem_budget_bytes", C.c_int64),
+                ("use_graphs", C.c_int32)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("rejected", C.c_int64), ("batches", C.c_int64),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double),
+                ("throughput_rps", C.c_double), ("us_per_atom", C.c_double), ("mean_batch_atoms", C.c_double)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("shift", C.c_double), ("iters_done", C.c_int32), ("rel_resid", C.c_double),
@@ -82,6 +94,12 @@ _SIGS = {
     "qmlr_model_set_alpha_device": (C.c_int, [VP, P, VP]),
     "qmlr_model_reserve": (C.c_int, [VP, I32]),
     "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
+    "qmlr_serve_create": (C.c_int, [VP, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]),
+    "qmlr_serve_submit": (C.c_int, [VP, P, P, I32, C.POINTER(C.c_uint64)]),
+    "qmlr_serve_poll": (C.c_int, [VP, C.c_uint64, P, P, I64]),
+    "qmlr_serve_stats": (C.c_int, [VP, C.POINTER(ServeStats)]),
+    "qmlr_serve_reset_stats": (C.c_int, [VP]),
+    "qmlr_serve_destroy": (C.c_int, [VP]),
 }
 
 
@@ -480,3 +498,62 @@ def force_rows(tangents, jac_ptr, mol_ptr, sin_t, sign_bits, T: int, n_features:
                                  _ptr(sign_bits), T, n_features, float(sigma), _ptr(out), out.stride(0),
                                  row0, _stream()))
     return out
+
+
+# ----------------------------------------------------------------------------
+# serving
+
+
+class Server:
+    """Continuous-batching prediction server around a Model (host arrays in and out)."""
+
+    def __init__(self, model: "Model", n_lanes: int = 2, max_batch_atoms: int = 16384,
+                 max_batch_mols: int = 1024, max_slots: int = 100000, max_inflight_atoms: int = 10_000_000,
+                 mem_budget_bytes: int = 0, use_graphs: bool = True):
+        self.model = model
+        cfg = ServeConfig(n_lanes, max_batch_atoms, max_batch_mols, max_slots, max_inflight_atoms,
+                          mem_budget_bytes, int(use_graphs))
+        h = C.c_void_p()
+        _check(lib().qmlr_serve_create(model.handle, C.byref(cfg), C.byref(h)))
+        self.handle = h
+
+    def submit(self, coords, elem) -> int:
+        """Ticket, or raises QMLRError (code EBUSY when not admitted)."""
+        c = np.ascontiguousarray(coords, dtype=np.float32)
+        e = np.ascontiguousarray(elem, dtype=np.int32)
+        t = C.c_uint64(0)
+        _check(lib().qmlr_serve_submit(self.handle, c.ctypes.data, e.ctypes.data, len(e), C.byref(t)))
+        return t.value
+
+    def try_submit(self, coords, elem):
+        c = np.ascontiguousarray(coords, dtype=np.float32)
+        e = np.ascontiguousarray(elem, dtype=np.int32)
+        t = C.c_uint64(0)
+        rc = lib().qmlr_serve_submit(self.handle, c.ctypes.data, e.ctypes.data, len(e), C.byref(t))
+        return rc, t.value
+
+    def poll(self, ticket: int, n_atoms: int, timeout_us: int = 10_000_000):
+        """(rc, E, F[n_atoms, 3])."""
+        E = C.c_double(0.0)
+        F = np.empty((n_atoms, 3), dtype=np.float32)
+        rc = lib().qmlr_serve_poll(self.handle, ticket, C.byref(E), F.ctypes.data, timeout_us)
+        return rc, E.value, F
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(lib().qmlr_serve_stats(self.handle, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def reset_stats(self):
+        _check(lib().qmlr_serve_reset_stats(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qmlr_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
