@@ -44,6 +44,8 @@ def parse():
                     help="fraction of the 100k-molecule workload (1.0 for the reported line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
     return ap.parse_args()
@@ -144,6 +146,82 @@ def oracle_step_times(w, n_mol_sample: int, threads: int):
 
 
 # ----------------------------------------------------------------------------
+# serving: Poisson request streams through the continuous-batching server
+
+def serving_phase(model_args, rates, seconds):
+    """p50/p99 latency, throughput and us/atom of the server under Poisson
+    arrivals of 5-200-atom molecules, and of one request at a time."""
+    import queue
+    from paper_2206_01580_gb300 import qmlr, synth
+    p, U, signs, T, b, sigma, alpha = model_args
+    pool = synth.serving_molecules(synth.rng_for(4), 2000)
+    mols = [(np.ascontiguousarray(c, dtype=np.float32), np.ascontiguousarray(e, dtype=np.int32))
+            for c, e in (pool.molecule(i) for i in range(pool.n_mol))]
+    model = qmlr.Model(p, 200, U, signs, T, b, sigma, alpha)
+    rng = np.random.default_rng(4)
+
+    def run_stream(srv, rate):
+        arrivals = synth.poisson_arrivals(rng, rate, seconds)
+        picks = rng.integers(0, len(mols), size=len(arrivals))
+        q = queue.Queue()
+
+        def collector():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                srv.poll(item[0], item[1])
+
+        th = threading.Thread(target=collector, daemon=True)
+        th.start()
+        srv.reset_stats()
+        rejected = 0
+        t0 = time.perf_counter()
+        for ta, k in zip(arrivals, picks):
+            while time.perf_counter() - t0 < ta:
+                pass
+            c, e = mols[k]
+            rc, t = srv.try_submit(c, e)
+            if rc == qmlr.EBUSY:
+                rejected += 1
+            else:
+                q.put((t, len(e)))
+        q.put(None)
+        th.join()
+        st = srv.stats()
+        return {"rate_rps": rate, "requests": len(arrivals), "rejected": rejected,
+                "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                "throughput_rps": st["throughput_rps"], "us_per_atom": st["us_per_atom"],
+                "mean_batch_atoms": st["mean_batch_atoms"]}
+
+    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=16384, max_batch_mols=1024, use_graphs=True)
+    # warm-up: every batch-size bucket once outside capture and once captured
+    for burst in (1, 2, 4, 8, 16, 32, 64, 128, 256, 320):
+        for _ in range(2):
+            ts = [(srv.submit(*mols[i % len(mols)]), len(mols[i % len(mols)][1])) for i in range(burst)]
+            for t, n in ts:
+                srv.poll(t, n)
+    out = {"streams": [run_stream(srv, r) for r in rates]}
+    srv.close()
+    # one request at a time, no batching, no graphs (the plain form)
+    one = qmlr.Server(model, n_lanes=1, max_batch_atoms=256, max_batch_mols=8, use_graphs=False)
+    for i in range(20):
+        t = one.submit(*mols[i])
+        one.poll(t, len(mols[i][1]))
+    one.reset_stats()
+    for i in range(300):
+        c, e = mols[(7 * i) % len(mols)]
+        t = one.submit(c, e)
+        one.poll(t, len(e))
+    st = one.stats()
+    out["one_at_a_time"] = {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                            "throughput_rps": st["throughput_rps"], "us_per_atom": st["us_per_atom"]}
+    one.close()
+    model.close()
+    out["molecules"] = "5-200 atoms, log-uniform (mean %.1f)" % pool.sizes().mean()
+    out["duration_s_per_rate"] = seconds
+    return out
+
 
 def build_workload(scale):
     from paper_2206_01580_gb300 import synth
@@ -364,6 +442,10 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": d2h},
         "workload_gen_s": gen_s,
     }
+    if not args.no_serve and world == 1:
+        alpha_host = alpha.float().cpu().numpy()
+        line["serving"] = serving_phase((p, U, w.signs, w.n_transform, w.b, w.sigma, alpha_host),
+                                        (1000, 5000, 20000), args.serve_seconds)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
         cb = oracle_step_times(w, 6, threads)
