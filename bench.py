@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-ef", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
@@ -162,39 +163,14 @@ def serving_phase(model_args, rates, seconds):
 
     def run_stream(srv, rate):
         arrivals = synth.poisson_arrivals(rng, rate, seconds)
-        picks = rng.integers(0, len(mols), size=len(arrivals))
-        q = queue.Queue()
-
-        def collector():
-            while True:
-                item = q.get()
-                if item is None:
-                    return
-                srv.poll(item[0], item[1])
-
-        th = threading.Thread(target=collector, daemon=True)
-        th.start()
-        srv.reset_stats()
-        rejected = 0
-        t0 = time.perf_counter()
-        for ta, k in zip(arrivals, picks):
-            while time.perf_counter() - t0 < ta:
-                pass
-            c, e = mols[k]
-            rc, t = srv.try_submit(c, e)
-            if rc == qmlr.EBUSY:
-                rejected += 1
-            else:
-                q.put((t, len(e)))
-        q.put(None)
-        th.join()
-        st = srv.stats()
-        return {"rate_rps": rate, "requests": len(arrivals), "rejected": rejected,
+        picks = rng.integers(0, pool.n_mol, size=len(arrivals))
+        st = srv.replay(pool.coords, pool.elem, pool.mol_ptr, arrivals, picks)
+        return {"rate_rps": rate, "requests": len(arrivals), "rejected": st["rejected"],
                 "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
                 "throughput_rps": st["throughput_rps"], "us_per_atom": st["us_per_atom"],
                 "mean_batch_atoms": st["mean_batch_atoms"]}
 
-    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=16384, max_batch_mols=1024, use_graphs=True)
+    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=16384, max_batch_mols=4096, use_graphs=True)
     # warm-up: every batch-size bucket once outside capture and once captured
     for burst in (1, 2, 4, 8, 16, 32, 64, 128, 256, 320):
         for _ in range(2):
@@ -204,10 +180,11 @@ def serving_phase(model_args, rates, seconds):
     out = {"streams": [run_stream(srv, r) for r in rates]}
     srv.close()
     # one request at a time, no batching, no graphs (the plain form)
-    one = qmlr.Server(model, n_lanes=1, max_batch_atoms=256, max_batch_mols=8, use_graphs=False)
+    one = qmlr.Server(model, n_lanes=1, max_batch_atoms=256, max_batch_mols=128, use_graphs=False)
     for i in range(20):
         t = one.submit(*mols[i])
         one.poll(t, len(mols[i][1]))
+    # one request at a time: each arrives after the previous result (closed loop, 300 requests)
     one.reset_stats()
     for i in range(300):
         c, e = mols[(7 * i) % len(mols)]
@@ -221,6 +198,55 @@ def serving_phase(model_args, rates, seconds):
     out["molecules"] = "5-200 atoms, log-uniform (mean %.1f)" % pool.sizes().mean()
     out["duration_s_per_rate"] = seconds
     return out
+
+
+# ----------------------------------------------------------------------------
+# energy + force training on the 3BPA-shaped workload
+
+def ef_training_phase(pcg_iters, pcg_tol):
+    """Train on 500 conformations with energy and force rows (41 000 x 16384),
+    then predict 2000 held-out conformations; stage times by CUDA events."""
+    import torch
+    from paper_2206_01580_gb300 import pipeline, qmlr, synth
+    from paper_2206_01580_gb300.params import from_table
+    w = synth.workload(3)
+    p = from_table(w.params_column, n2=w.n2, n3=w.n3)
+    spec = pipeline.spec_from(p, w.d, w.signs, w.b, w.sigma)
+    tr = pipeline.Batch.from_host(w.mols.coords, w.mols.elem, w.mols.mol_ptr)
+    rep, perm, offs = pipeline.representations(tr, spec)
+    U = pipeline.fit_pca(rep, perm, offs, spec)
+    del rep
+    y = torch.cat([torch.as_tensor(w.energies), torch.as_tensor(w.forces).reshape(-1)]).cuda()
+
+    def once():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        s = torch.cuda.current_stream()
+        ev[0].record(s)
+        rows = pipeline.energy_force_rows(tr, spec, U)
+        ev[1].record(s)
+        G = qmlr.gram(rows, qmlr.GRAM_BF16X6)
+        ev[2].record(s)
+        alpha, it, rel = qmlr.gram_solve(G, rows, y, w.lam, max_iter=pcg_iters, tol=pcg_tol)
+        ev[3].record(s)
+        torch.cuda.synchronize()
+        so = qmlr.last_solve
+        n_rows = rows.shape[0]
+        del rows, G
+        return alpha, {"rows_ms": ev[0].elapsed_time(ev[1]), "gram_ms": ev[1].elapsed_time(ev[2]),
+                       "solve_ms": ev[2].elapsed_time(ev[3]), "factor_ms": so.factor_ms,
+                       "refine_ms": so.refine_ms, "train_s": ev[0].elapsed_time(ev[3]) / 1e3,
+                       "pcg_iters": it, "rel_resid": rel, "n_rows": n_rows}
+
+    once()                     # warm-up
+    alpha, st = once()
+    model = qmlr.Model(p, 32, U, w.signs, w.n_transform, w.b, w.sigma, alpha.float().cpu().numpy())
+    E, F = model.predict(w.test.coords, w.test.elem, w.test.mol_ptr)
+    mae_e = float(np.mean(np.abs(E.cpu().numpy() - w.test_energies)))
+    mae_f = float(np.mean(np.abs(F.cpu().numpy() - w.test_forces)))
+    model.close()
+    st.update({"workload": "3bpa-shaped-500 (500 train / 2000 test conformations, 27 atoms, N_F = 16384)",
+               "test_mae_E_eV": mae_e, "test_mae_F_eV_per_A": mae_f})
+    return st
 
 
 def build_workload(scale):
@@ -442,6 +468,8 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": d2h},
         "workload_gen_s": gen_s,
     }
+    if not args.no_ef and world == 1:
+        line["ef_training"] = ef_training_phase(args.pcg_iters, args.pcg_tol)
     if not args.no_serve and world == 1:
         alpha_host = alpha.float().cpu().numpy()
         line["serving"] = serving_phase((p, U, w.signs, w.n_transform, w.b, w.sigma, alpha_host),

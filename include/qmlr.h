@@ -134,6 +134,20 @@ int qmlr_fchl19_jac(const float* coords, const int32_t* elem, const int32_t* mol
                     const int64_t* jac_ptr, float* jac, int32_t rep_ld, int32_t* row_elem,
                     void* stream);
 
+/*
+ * The same vector-Jacobian product with one warp per centre atom (the atoms
+ * of a molecule run in parallel; for small batches and large molecules):
+ *   pair_ptr   int64 [n_mol+1] from qmlr_jac_offsets (sum of 3 M^2)
+ *   contrib    float [pair_ptr[n_mol]] scratch: per-centre contributions
+ *   grad_coords[k] = scale * sum_i (d rho_i / d r_k)^T grad_rep[i]  (+ previous value if accumulate)
+ * The sum over centres runs in order (deterministic); scale = -1 gives forces.
+ */
+int qmlr_fchl19_vjp_atoms(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                          int32_t n_mol, int32_t n_atoms, int32_t max_mol_atoms,
+                          const qmlr_fchl19_params* p, const float* grad_rep, int32_t rep_ld,
+                          const int64_t* pair_ptr, float* contrib, float scale, float* grad_coords,
+                          int32_t accumulate, void* stream);
+
 /* ------------------------------------------------------------------------
  * Per-element projection (SORF section: SVD of the representations of each
  * element, rho_proj = rho^T U_e^{N_PCA}; GPU implementation paragraph: each
@@ -252,15 +266,18 @@ int32_t qmlr_sorf_parts(int32_t n_features, int32_t d);
 /*
  * Energy and its gradient with respect to the projected representations
  * (the SORF backward pass: transposed Hadamard chain applied to
- * -sqrt(2/N_F) alpha * sin(u)):
- *   energies double [n_mol]                 E_m = sum_{I in m} alpha^T z(x_I)
- *   gx       float [n_part][n_atoms][d]     dE/dx_I contributed by the stacks of part p
+ * -sqrt(2/N_F) alpha * sin(u)); one CTA per (atom, stack part), so the atoms
+ * of a molecule run in parallel:
+ *   atom_energy double [n_part][n_atoms]  per-atom partial energies (written; scratch)
+ *   energies    double [n_mol]            E_m = sum over atoms, then parts, in order
+ *   gx          float [n_part][n_atoms][d]  dE/dx_I from the stacks of part p, or NULL
+ *                                          (energies only)
  * n_part = qmlr_sorf_parts(n_features, d); qmlr_project_t sums the parts.
  */
 int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
                    int32_t n_atoms, const uint32_t* sign_bits, int32_t T, const float* b,
-                   int32_t n_features, double sigma, const float* alpha, double* energies,
-                   float* gx, void* stream);
+                   int32_t n_features, double sigma, const float* alpha, double* atom_energy,
+                   double* energies, float* gx, void* stream);
 
 /* ------------------------------------------------------------------------
  * Regularised normal equations (RFF section: (Z^T Z + lambda I) alpha = Z^T E,
@@ -457,6 +474,18 @@ int qmlr_serve_poll(qmlr_server* s, uint64_t ticket, double* host_E, float* host
 
 int qmlr_serve_stats(qmlr_server* s, qmlr_serve_report* out);
 int qmlr_serve_reset_stats(qmlr_server* s);
+
+/*
+ * Load driver: replays a request trace against the server from two host
+ * threads (one submits molecule pick[i] of the pool at arrival_us[i]
+ * microseconds after the start, spinning until then; one collects results in
+ * submission order), then returns the server's statistics for the run.
+ * Pool: host_coords float [pool atoms][3], host_elem int32, host_mol_ptr
+ * int32 [n_pool+1]. *rejected = requests refused by admission. Synchronous.
+ */
+int qmlr_serve_replay(qmlr_server* s, const float* host_coords, const int32_t* host_elem,
+                      const int32_t* host_mol_ptr, int32_t n_pool, const double* arrival_us,
+                      const int32_t* pick, int32_t n_req, int64_t* rejected, qmlr_serve_report* out);
 
 /* Finishes the batches in flight, stops the batcher and frees the server. */
 int qmlr_serve_destroy(qmlr_server* s);

@@ -300,6 +300,160 @@ __device__ __forceinline__ VjpWarp carve_vjp(char* base, int mxp, int rp) {
   return s;
 }
 
+// Adjoint of one centre: accumulates d(sum_b g_b rho_il,b)/d r_k into facc[3k..3k+2]
+// for every atom k of the molecule (the centre's own entry included). One warp.
+__device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts& c, const float* __restrict__ grow,
+                           VjpWarp& s, int lane) {
+  for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grow + k);
+  const int n = neighbour_list(pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
+
+  float gi_x = 0.f, gi_y = 0.f, gi_z = 0.f;   // gradient on the centre (per-lane partials)
+
+  // two-body: lanes over neighbours (distinct atoms per lane)
+  for (int jn = lane; jn < n; jn += 32) {
+    const float4 u = s.nb_u[jn];
+    const float r = u.w;
+    const float4 t = s.nb_2b[jn];   // mu, 1/(2s^2), fc r^-N2/(s sqrt(2pi)), fc
+    const float inv_r = 1.0f / r;
+    const float s2 = 0.5f / t.y;
+    const float sd = sqrtf(s2);
+    const float rr_eta = r * r + c.eta2;
+    const float ds = -c.eta2 / (sd * r * rr_eta);            // d sigma / dr
+    const float dmu = inv_r + c.eta2 / (r * rr_eta);          // d mu / dr
+    const float fc = t.w;
+    const float dfc = cutoff_df(r, c);
+    const float rN = expf(-c.N2 * logf(r));
+    const float P = fc * rN;
+    const float dP = rN * (dfc - c.N2 * fc * inv_r);
+    const float* gb = s.g + s.nb_el[jn] * c.n2;
+    float dEdr = 0.f;
+    for (int k = 0; k < c.n2; ++k) {
+      const float a = c.rs2_log[k] - t.x;
+      const float L = c.rs2_inv[k] * c.inv_sqrt_2pi / sd * expf(-a * a * t.y);
+      const float dlnL = -ds / sd + a * dmu / s2 + a * a * ds / (s2 * sd);
+      dEdr += gb[k] * L * (dP + P * dlnL);
+    }
+    const int jl = s.nb_idx[jn];
+    s.facc[3 * jl + 0] += dEdr * u.x;
+    s.facc[3 * jl + 1] += dEdr * u.y;
+    s.facc[3 * jl + 2] += dEdr * u.z;
+    gi_x -= dEdr * u.x;
+    gi_y -= dEdr * u.y;
+    gi_z -= dEdr * u.z;
+  }
+  __syncwarp();
+
+  // three-body: lanes over flat neighbour pairs, each lane loops over its radial bins
+  const int n_pairs = n * (n - 1) / 2;
+  for (int q0 = 0; q0 < n_pairs; q0 += 32) {
+    const int q = q0 + lane;
+    float gj0 = 0.f, gj1 = 0.f, gj2 = 0.f, gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
+    int jl = 0, kl = 0;
+    if (q < n_pairs) {
+      int jn, kn;
+      decode_pair(q, n, jn, kn);
+      jl = s.nb_idx[jn];
+      kl = s.nb_idx[kn];
+      const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+      const float a = uj.w, b = uk.w;
+      const float vx = uk.x * b - uj.x * a, vy = uk.y * b - uj.y * a, vz = uk.z * b - uj.z * a;
+      const float c2 = vx * vx + vy * vy + vz * vz;
+      if (c2 < c.rcut2) {
+        const float cc = sqrtf(c2);
+        const float inv_c = 1.0f / cc;
+        const float ux = vx * inv_c, uy = vy * inv_c, uz = vz * inv_c;   // unit j -> k
+        const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+        const float crx = uj.y * uk.z - uj.z * uk.y;
+        const float cry = uj.z * uk.x - uj.x * uk.z;
+        const float crz = uj.x * uk.y - uj.y * uk.x;
+        const float si = sqrtf(crx * crx + cry * cry + crz * crz);
+        const float cj = -(uj.x * ux + uj.y * uy + uj.z * uz);
+        const float ck = (uk.x * ux + uk.y * uy + uk.z * uz);
+        // cosines as functions of the sides a = r_ij, b = r_ik, cc = r_jk
+        const float dci_da = (a - b * ci) / (a * b), dci_db = (b - a * ci) / (a * b), dci_dc = -cc / (a * b);
+        const float dcj_da = (a - cc * cj) / (a * cc), dcj_dc = (cc - a * cj) / (a * cc), dcj_db = -b / (a * cc);
+        const float dck_db = (b - cc * ck) / (b * cc), dck_dc = (cc - b * ck) / (b * cc), dck_da = -a / (b * cc);
+        const float Q = 1.0f + 3.0f * ci * cj * ck;
+        const float dQ_da = 3.0f * (dci_da * cj * ck + ci * dcj_da * ck + ci * cj * dck_da);
+        const float dQ_db = 3.0f * (dci_db * cj * ck + ci * dcj_db * ck + ci * cj * dck_db);
+        const float dQ_dc = 3.0f * (dci_dc * cj * ck + ci * dcj_dc * ck + ci * cj * dck_dc);
+        const float R3 = expf(-c.N3 * logf(a * b * cc));
+        const float fa = s.nb_2b[jn].w, fb = s.nb_2b[kn].w, fcc = cutoff_f(cc, c);
+        const float dfa = cutoff_df(a, c), dfb = cutoff_df(b, c), dfcc = cutoff_df(cc, c);
+        const float F3 = fa * fb * fcc;
+        const float W = c.w3 * Q * R3 * F3;
+        const float dW_da = c.w3 * R3 * (dQ_da * F3 - Q * F3 * c.N3 / a + Q * dfa * fb * fcc);
+        const float dW_db = c.w3 * R3 * (dQ_db * F3 - Q * F3 * c.N3 / b + Q * fa * dfb * fcc);
+        const float dW_dc = c.w3 * R3 * (dQ_dc * F3 - Q * F3 * c.N3 / cc + Q * fa * fb * dfcc);
+        const float Ac = c.ang2 * ci, As = c.ang2 * si;
+        const float dsi_dci = si > 1e-7f ? -ci / si : 0.0f;   // collinear guard
+        const float xbar = 0.5f * (a + b);
+        const float* gb = s.g + c.base3 + pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el) * c.n3 * 2;
+        float Sc = 0.f, Ss = 0.f, Sc1 = 0.f, Ss1 = 0.f;
+        for (int k = 0; k < c.n3; ++k) {
+          const float d = xbar - c.rs3[k];
+          const float rad = expf(-c.eta3 * d * d);
+          const float drad = -2.0f * c.eta3 * d * rad;
+          const float g0 = gb[2 * k], g1 = gb[2 * k + 1];
+          Sc += g0 * rad;
+          Ss += g1 * rad;
+          Sc1 += g0 * drad;
+          Ss1 += g1 * drad;
+        }
+        const float AS = Ac * Sc + As * Ss;
+        const float AS1 = Ac * Sc1 + As * Ss1;
+        const float dA = c.ang2 * (Sc + dsi_dci * Ss);   // d(A.S)/d cos(th_i) at fixed S
+        const float dE_da = dW_da * AS + W * dA * dci_da + W * AS1 * 0.5f;
+        const float dE_db = dW_db * AS + W * dA * dci_db + W * AS1 * 0.5f;
+        const float dE_dc = dW_dc * AS + W * dA * dci_dc;
+        // a = |r_j - r_i|, b = |r_k - r_i|, cc = |r_k - r_j|
+        gi_x -= dE_da * uj.x + dE_db * uk.x;
+        gi_y -= dE_da * uj.y + dE_db * uk.y;
+        gi_z -= dE_da * uj.z + dE_db * uk.z;
+        gj0 = dE_da * uj.x - dE_dc * ux;
+        gj1 = dE_da * uj.y - dE_dc * uy;
+        gj2 = dE_da * uj.z - dE_dc * uz;
+        gk0 = dE_db * uk.x + dE_dc * ux;
+        gk1 = dE_db * uk.y + dE_dc * uy;
+        gk2 = dE_db * uk.z + dE_dc * uz;
+      }
+    }
+    // scatter the j- and k-side gradients in a fixed lane order
+    const int cnt = min(32, n_pairs - q0);
+    for (int t = 0; t < cnt; ++t) {
+      const int jt = __shfl_sync(0xffffffffu, jl, t);
+      const int kt = __shfl_sync(0xffffffffu, kl, t);
+      const float v0 = __shfl_sync(0xffffffffu, gj0, t);
+      const float v1 = __shfl_sync(0xffffffffu, gj1, t);
+      const float v2 = __shfl_sync(0xffffffffu, gj2, t);
+      const float v3 = __shfl_sync(0xffffffffu, gk0, t);
+      const float v4 = __shfl_sync(0xffffffffu, gk1, t);
+      const float v5 = __shfl_sync(0xffffffffu, gk2, t);
+      if (lane == 0) {
+        s.facc[3 * jt + 0] += v0;
+        s.facc[3 * jt + 1] += v1;
+        s.facc[3 * jt + 2] += v2;
+        s.facc[3 * kt + 0] += v3;
+        s.facc[3 * kt + 1] += v4;
+        s.facc[3 * kt + 2] += v5;
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gi_x += __shfl_xor_sync(0xffffffffu, gi_x, o);
+    gi_y += __shfl_xor_sync(0xffffffffu, gi_y, o);
+    gi_z += __shfl_xor_sync(0xffffffffu, gi_z, o);
+  }
+  if (lane == 0) {
+    s.facc[3 * il + 0] += gi_x;
+    s.facc[3 * il + 1] += gi_y;
+    s.facc[3 * il + 2] += gi_z;
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(32 * kWarpsVjp)
 fchl19_vjp_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
                   const int32_t* __restrict__ mol_ptr, int n_mol, int mx, int mxp, int rp,
@@ -321,155 +475,7 @@ fchl19_vjp_kernel(const float* __restrict__ coords, const int32_t* __restrict__ 
   __syncthreads();
 
   for (int il = warp; il < M; il += kWarpsVjp) {
-    const float* grow = grad_rep + (size_t)(a0 + il) * rep_ld;
-    for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grow + k);
-    const int n = neighbour_list(pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
-
-    float gi_x = 0.f, gi_y = 0.f, gi_z = 0.f;   // gradient on the centre (per-lane partials)
-
-    // two-body: lanes over neighbours (distinct atoms per lane)
-    for (int jn = lane; jn < n; jn += 32) {
-      const float4 u = s.nb_u[jn];
-      const float r = u.w;
-      const float4 t = s.nb_2b[jn];   // mu, 1/(2s^2), fc r^-N2/(s sqrt(2pi)), fc
-      const float inv_r = 1.0f / r;
-      const float s2 = 0.5f / t.y;
-      const float sd = sqrtf(s2);
-      const float rr_eta = r * r + c.eta2;
-      const float ds = -c.eta2 / (sd * r * rr_eta);            // d sigma / dr
-      const float dmu = inv_r + c.eta2 / (r * rr_eta);          // d mu / dr
-      const float fc = t.w;
-      const float dfc = cutoff_df(r, c);
-      const float rN = expf(-c.N2 * logf(r));
-      const float P = fc * rN;
-      const float dP = rN * (dfc - c.N2 * fc * inv_r);
-      const float* gb = s.g + s.nb_el[jn] * c.n2;
-      float dEdr = 0.f;
-      for (int k = 0; k < c.n2; ++k) {
-        const float a = c.rs2_log[k] - t.x;
-        const float L = c.rs2_inv[k] * c.inv_sqrt_2pi / sd * expf(-a * a * t.y);
-        const float dlnL = -ds / sd + a * dmu / s2 + a * a * ds / (s2 * sd);
-        dEdr += gb[k] * L * (dP + P * dlnL);
-      }
-      const int jl = s.nb_idx[jn];
-      s.facc[3 * jl + 0] += dEdr * u.x;
-      s.facc[3 * jl + 1] += dEdr * u.y;
-      s.facc[3 * jl + 2] += dEdr * u.z;
-      gi_x -= dEdr * u.x;
-      gi_y -= dEdr * u.y;
-      gi_z -= dEdr * u.z;
-    }
-    __syncwarp();
-
-    // three-body: lanes over flat neighbour pairs, each lane loops over its radial bins
-    const int n_pairs = n * (n - 1) / 2;
-    for (int q0 = 0; q0 < n_pairs; q0 += 32) {
-      const int q = q0 + lane;
-      float gj0 = 0.f, gj1 = 0.f, gj2 = 0.f, gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
-      int jl = 0, kl = 0;
-      if (q < n_pairs) {
-        int jn, kn;
-        decode_pair(q, n, jn, kn);
-        jl = s.nb_idx[jn];
-        kl = s.nb_idx[kn];
-        const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
-        const float a = uj.w, b = uk.w;
-        const float vx = uk.x * b - uj.x * a, vy = uk.y * b - uj.y * a, vz = uk.z * b - uj.z * a;
-        const float c2 = vx * vx + vy * vy + vz * vz;
-        if (c2 < c.rcut2) {
-          const float cc = sqrtf(c2);
-          const float inv_c = 1.0f / cc;
-          const float ux = vx * inv_c, uy = vy * inv_c, uz = vz * inv_c;   // unit j -> k
-          const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-          const float crx = uj.y * uk.z - uj.z * uk.y;
-          const float cry = uj.z * uk.x - uj.x * uk.z;
-          const float crz = uj.x * uk.y - uj.y * uk.x;
-          const float si = sqrtf(crx * crx + cry * cry + crz * crz);
-          const float cj = -(uj.x * ux + uj.y * uy + uj.z * uz);
-          const float ck = (uk.x * ux + uk.y * uy + uk.z * uz);
-          // cosines as functions of the sides a = r_ij, b = r_ik, cc = r_jk
-          const float dci_da = (a - b * ci) / (a * b), dci_db = (b - a * ci) / (a * b), dci_dc = -cc / (a * b);
-          const float dcj_da = (a - cc * cj) / (a * cc), dcj_dc = (cc - a * cj) / (a * cc), dcj_db = -b / (a * cc);
-          const float dck_db = (b - cc * ck) / (b * cc), dck_dc = (cc - b * ck) / (b * cc), dck_da = -a / (b * cc);
-          const float Q = 1.0f + 3.0f * ci * cj * ck;
-          const float dQ_da = 3.0f * (dci_da * cj * ck + ci * dcj_da * ck + ci * cj * dck_da);
-          const float dQ_db = 3.0f * (dci_db * cj * ck + ci * dcj_db * ck + ci * cj * dck_db);
-          const float dQ_dc = 3.0f * (dci_dc * cj * ck + ci * dcj_dc * ck + ci * cj * dck_dc);
-          const float R3 = expf(-c.N3 * logf(a * b * cc));
-          const float fa = s.nb_2b[jn].w, fb = s.nb_2b[kn].w, fcc = cutoff_f(cc, c);
-          const float dfa = cutoff_df(a, c), dfb = cutoff_df(b, c), dfcc = cutoff_df(cc, c);
-          const float F3 = fa * fb * fcc;
-          const float W = c.w3 * Q * R3 * F3;
-          const float dW_da = c.w3 * R3 * (dQ_da * F3 - Q * F3 * c.N3 / a + Q * dfa * fb * fcc);
-          const float dW_db = c.w3 * R3 * (dQ_db * F3 - Q * F3 * c.N3 / b + Q * fa * dfb * fcc);
-          const float dW_dc = c.w3 * R3 * (dQ_dc * F3 - Q * F3 * c.N3 / cc + Q * fa * fb * dfcc);
-          const float Ac = c.ang2 * ci, As = c.ang2 * si;
-          const float dsi_dci = si > 1e-7f ? -ci / si : 0.0f;   // collinear guard
-          const float xbar = 0.5f * (a + b);
-          const float* gb = s.g + c.base3 + pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el) * c.n3 * 2;
-          float Sc = 0.f, Ss = 0.f, Sc1 = 0.f, Ss1 = 0.f;
-          for (int k = 0; k < c.n3; ++k) {
-            const float d = xbar - c.rs3[k];
-            const float rad = expf(-c.eta3 * d * d);
-            const float drad = -2.0f * c.eta3 * d * rad;
-            const float g0 = gb[2 * k], g1 = gb[2 * k + 1];
-            Sc += g0 * rad;
-            Ss += g1 * rad;
-            Sc1 += g0 * drad;
-            Ss1 += g1 * drad;
-          }
-          const float AS = Ac * Sc + As * Ss;
-          const float AS1 = Ac * Sc1 + As * Ss1;
-          const float dA = c.ang2 * (Sc + dsi_dci * Ss);   // d(A.S)/d cos(th_i) at fixed S
-          const float dE_da = dW_da * AS + W * dA * dci_da + W * AS1 * 0.5f;
-          const float dE_db = dW_db * AS + W * dA * dci_db + W * AS1 * 0.5f;
-          const float dE_dc = dW_dc * AS + W * dA * dci_dc;
-          // a = |r_j - r_i|, b = |r_k - r_i|, cc = |r_k - r_j|
-          gi_x -= dE_da * uj.x + dE_db * uk.x;
-          gi_y -= dE_da * uj.y + dE_db * uk.y;
-          gi_z -= dE_da * uj.z + dE_db * uk.z;
-          gj0 = dE_da * uj.x - dE_dc * ux;
-          gj1 = dE_da * uj.y - dE_dc * uy;
-          gj2 = dE_da * uj.z - dE_dc * uz;
-          gk0 = dE_db * uk.x + dE_dc * ux;
-          gk1 = dE_db * uk.y + dE_dc * uy;
-          gk2 = dE_db * uk.z + dE_dc * uz;
-        }
-      }
-      // scatter the j- and k-side gradients in a fixed lane order
-      const int cnt = min(32, n_pairs - q0);
-      for (int t = 0; t < cnt; ++t) {
-        const int jt = __shfl_sync(0xffffffffu, jl, t);
-        const int kt = __shfl_sync(0xffffffffu, kl, t);
-        const float v0 = __shfl_sync(0xffffffffu, gj0, t);
-        const float v1 = __shfl_sync(0xffffffffu, gj1, t);
-        const float v2 = __shfl_sync(0xffffffffu, gj2, t);
-        const float v3 = __shfl_sync(0xffffffffu, gk0, t);
-        const float v4 = __shfl_sync(0xffffffffu, gk1, t);
-        const float v5 = __shfl_sync(0xffffffffu, gk2, t);
-        if (lane == 0) {
-          s.facc[3 * jt + 0] += v0;
-          s.facc[3 * jt + 1] += v1;
-          s.facc[3 * jt + 2] += v2;
-          s.facc[3 * kt + 0] += v3;
-          s.facc[3 * kt + 1] += v4;
-          s.facc[3 * kt + 2] += v5;
-        }
-      }
-      __syncwarp();
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      gi_x += __shfl_xor_sync(0xffffffffu, gi_x, o);
-      gi_y += __shfl_xor_sync(0xffffffffu, gi_y, o);
-      gi_z += __shfl_xor_sync(0xffffffffu, gi_z, o);
-    }
-    if (lane == 0) {
-      s.facc[3 * il + 0] += gi_x;
-      s.facc[3 * il + 1] += gi_y;
-      s.facc[3 * il + 2] += gi_z;
-    }
-    __syncwarp();
+    vjp_centre(pos, M, il, c, grad_rep + (size_t)(a0 + il) * rep_ld, s, lane);
   }
   __syncthreads();
   // fixed-order reduction over the warps' buffers
@@ -699,6 +705,58 @@ __global__ void jac_offsets_kernel(const int32_t* __restrict__ mol_ptr, int n_mo
   if (threadIdx.x == 0) out[n_mol] = carry;
 }
 
+// VJP with one warp per centre atom (the atoms of a molecule run in parallel):
+// each warp writes its centre's contributions to every atom of the molecule
+// into contrib[pair_ptr[m] + (I*M + k)*3 + x]; vjp_reduce_kernel then sums
+// them over the centres I in order.
+__global__ void __launch_bounds__(32 * kWarpsFwd)
+fchl19_vjp_centre_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
+                         const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp, int rp,
+                         Fchl19Consts c, const float* __restrict__ grad_rep, int rep_ld,
+                         const int64_t* __restrict__ pair_ptr, float* __restrict__ contrib, int* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int atom = blockIdx.x * kWarpsFwd + warp;
+  if (atom >= n_atoms) return;
+  char* base = smem_raw + warp * ((size_t)mxp * 16 + vjp_warp_bytes(mxp, rp));
+  float4* pos = reinterpret_cast<float4*>(base);
+  VjpWarp s = carve_vjp(base + (size_t)mxp * 16, mxp, rp);
+  const int m = find_molecule(mol_ptr, n_mol, atom);
+  const int a0 = __ldg(mol_ptr + m);
+  const int M = __ldg(mol_ptr + m + 1) - a0;
+  const int il = atom - a0;
+  if (M > mx) {
+    if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+    return;
+  }
+  stage_molecule(coords, elem, a0, M, c.n_el, pos, lane, 32, err);
+  for (int k = lane; k < 3 * M; k += 32) s.facc[k] = 0.0f;
+  __syncwarp();
+  vjp_centre(pos, M, il, c, grad_rep + (size_t)atom * rep_ld, s, lane);
+  __syncwarp();
+  float* out = contrib + pair_ptr[m] + (long)il * M * 3;
+  for (int k = lane; k < 3 * M; k += 32) out[k] = s.facc[k];
+}
+
+// grad[k][x] = scale * sum_{I = 0..M-1} contrib[pair_ptr[m] + (I*M + k_local)*3 + x] (+ grad if accumulate)
+__global__ void vjp_reduce_kernel(const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms,
+                                  const int64_t* __restrict__ pair_ptr, const float* __restrict__ contrib,
+                                  float scale, int accumulate, float* __restrict__ grad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n_atoms) return;
+  const int atom = t / 3, x = t % 3;
+  int lo = 0, hi = n_mol;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (mol_ptr[mid] <= atom) lo = mid; else hi = mid;
+  }
+  const int a0 = mol_ptr[lo], M = mol_ptr[lo + 1] - a0, kl = atom - a0;
+  const float* cp = contrib + pair_ptr[lo] + (long)kl * 3 + x;
+  float sum = 0.f;
+  for (int I = 0; I < M; ++I) sum += cp[(long)I * M * 3];
+  grad[t] = accumulate ? grad[t] + scale * sum : scale * sum;
+}
+
 static int rep_pad_of(int rep_dim) { return (rep_dim + 3) & ~3; }
 
 static int check_geometry(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
@@ -828,6 +886,42 @@ extern "C" int qmlr_fchl19_jac(const float* coords, const int32_t* elem, const i
   fchl19_jac_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
       coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, jac_ptr, jac, rep_ld, row_elem,
       device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_fchl19_vjp_atoms(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
+                                     int32_t n_mol, int32_t n_atoms, int32_t max_mol_atoms,
+                                     const qmlr_fchl19_params* p, const float* grad_rep, int32_t rep_ld,
+                                     const int64_t* pair_ptr, float* contrib, float scale,
+                                     float* grad_coords, int32_t accumulate, void* stream) {
+  int rc = validate_params(p);
+  if (rc) return rc;
+  rc = check_geometry(coords, elem, mol_ptr, n_mol, n_atoms, max_mol_atoms);
+  if (rc) return rc;
+  const int rd = rep_dim_of(*p);
+  QMLR_REQUIRE(rep_ld >= rd, "rep_ld (%d) < rep_dim (%d)", rep_ld, rd);
+  if (n_atoms == 0 || n_mol == 0) return QMLR_OK;
+  QMLR_REQUIRE(grad_rep && pair_ptr && contrib && grad_coords, "NULL pointer argument");
+  const Fchl19Consts c = make_consts(*p);
+  const int rp = rep_pad_of(rd);
+  const int mx = max_mol_atoms;
+  const int mxp = (mx + 3) & ~3;
+  const size_t smem = kWarpsFwd * ((size_t)mxp * 16 + vjp_warp_bytes(mxp, rp));
+  QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
+  static bool attr_set = false;
+  if (!attr_set) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_vjp_centre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    attr_set = true;
+  }
+  cudaStream_t st = as_stream(stream);
+  fchl19_vjp_centre_kernel<<<(n_atoms + kWarpsFwd - 1) / kWarpsFwd, 32 * kWarpsFwd, smem, st>>>(
+      coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, grad_rep, rep_ld, pair_ptr, contrib,
+      device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  vjp_reduce_kernel<<<(3 * n_atoms + 255) / 256, 256, 0, st>>>(mol_ptr, n_mol, n_atoms, pair_ptr, contrib, scale,
+                                                              accumulate, grad_coords);
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }

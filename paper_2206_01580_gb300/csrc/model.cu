@@ -7,20 +7,25 @@
 // and phases and alpha, plus a workspace sized by qmlr_model_reserve, so that
 // qmlr_predict_ef itself allocates nothing (it can be captured in a CUDA
 // graph). Pipeline per call, all on the caller's stream:
-//   FCHL19 -> group by element -> projection -> SORF energy + dE/dx
-//   -> transposed projection -> FCHL19 VJP -> F = -grad.
+//   FCHL19 -> group by element -> projection -> SORF energy + dE/dx (one CTA
+//   per atom) -> transposed projection -> FCHL19 VJP (one warp per centre,
+//   ordered reduction with scale -1, so F = -grad directly).
 #include "common.cuh"
 
 #include "model_internal.cuh"
 
+#include <vector>
+
 namespace qmlr {
 
-__global__ void negate_kernel(float* v, long n) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = -v[i];
-}
-
 void PredictWorkspace::release() {
+  cudaFree(atom_e);
+  cudaFree(pair_ptr);
+  cudaFree(contrib);
+  atom_e = nullptr;
+  pair_ptr = nullptr;
+  contrib = nullptr;
+  cap_mols = 0;
   cudaFree(rep);
   cudaFree(x);
   cudaFree(gx);
@@ -46,17 +51,22 @@ int PredictWorkspace::reserve(const qmlr_model* m, int max_atoms) {
   if (e == cudaSuccess) e = cudaMalloc(&perm, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&offs, 16 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&gwork, gwork_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&atom_e, (size_t)m->n_part * n * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&pair_ptr, (n + 4096 + 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&contrib, n * (size_t)m->max_mol_atoms * 3 * 4);
   if (e != cudaSuccess) {
     release();
     set_error("workspace allocation failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? QMLR_ENOMEM : QMLR_ECUDA;
   }
   cap_atoms = max_atoms;
+  cap_mols = max_atoms + 4096;
   return QMLR_OK;
 }
 
 size_t PredictWorkspace::bytes_per_atom(const qmlr_model* m) {
-  return (size_t)m->rep_ld * 8 + (size_t)m->d * 4 * (1 + m->n_part) + 4 + 64;
+  return (size_t)m->rep_ld * 8 + (size_t)m->d * 4 * (1 + m->n_part) + 4 + 64 + 8 * m->n_part + 8 +
+         (size_t)m->max_mol_atoms * 12;
 }
 
 int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
@@ -81,22 +91,18 @@ int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords,
     return rc;
   if ((rc = qmlr_project(w.rep, m->rep_ld, m->rep_dim, w.perm, w.offs, n_atoms, n_el, m->U, m->d, w.x, stream)))
     return rc;
-  if (!forces) {
-    return qmlr_sorf(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->b, m->n_features, m->sigma,
-                     m->alpha, QMLR_SORF_ENERGY, energies, stream);
-  }
-  if ((rc = qmlr_sorf_grad(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->b, m->n_features, m->sigma,
-                           m->alpha, energies, w.gx, stream)))
+  QMLR_REQUIRE(n_mol <= w.cap_mols, "batch of %d molecules exceeds the reserved capacity %d", n_mol, w.cap_mols);
+  if ((rc = sorf_energy_grad_model(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->bT, m->n_features,
+                                   m->sigma, m->alphaT, w.atom_e, energies, forces ? w.gx : nullptr, s)))
     return rc;
+  if (!forces) return QMLR_OK;
   if ((rc = qmlr_project_t(w.gx, m->n_part, w.perm, w.offs, n_atoms, n_el, m->U, m->d, m->rep_dim, w.grep,
                            m->rep_ld, stream)))
     return rc;
-  if ((rc = qmlr_fchl19_vjp(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.grep, m->rep_ld,
-                            forces, 0, stream)))
-    return rc;
-  negate_kernel<<<(unsigned)((3L * n_atoms + 255) / 256), 256, 0, s>>>(forces, 3L * n_atoms);
-  QMLR_LAUNCH_CHECK();
-  return QMLR_OK;
+  if ((rc = qmlr_jac_offsets(mol_ptr, n_mol, w.pair_ptr, nullptr, stream))) return rc;
+  // forces F = -dE/dr: scale -1 in the ordered reduction
+  return qmlr_fchl19_vjp_atoms(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.grep,
+                               m->rep_ld, w.pair_ptr, w.contrib, -1.0f, forces, 0, stream);
 }
 
 }  // namespace qmlr
@@ -137,6 +143,19 @@ extern "C" int qmlr_model_create(const qmlr_fchl19_params* p, int32_t max_mol_at
   if (e == cudaSuccess) e = cudaMemcpy(m->signs, host_sign_bits, nS * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->b, host_b, (size_t)n_features * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->alpha, host_alpha, (size_t)n_features * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&m->bT, (size_t)n_features * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&m->alphaT, (size_t)n_features * 4);
+  if (e == cudaSuccess) {
+    const int ns = n_features / d;
+    std::vector<float> t1((size_t)n_features), t2((size_t)n_features);
+    for (int st = 0; st < ns; ++st)
+      for (int i = 0; i < d; ++i) {
+        t1[(size_t)i * ns + st] = host_b[(size_t)st * d + i];
+        t2[(size_t)i * ns + st] = host_alpha[(size_t)st * d + i];
+      }
+    e = cudaMemcpy(m->bT, t1.data(), (size_t)n_features * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->alphaT, t2.data(), (size_t)n_features * 4, cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     set_error("model allocation/copy failed: %s", cudaGetErrorString(e));
     qmlr_model_destroy(m);
@@ -153,6 +172,8 @@ extern "C" int qmlr_model_destroy(qmlr_model* m) {
   cudaFree(m->signs);
   cudaFree(m->b);
   cudaFree(m->alpha);
+  cudaFree(m->bT);
+  cudaFree(m->alphaT);
   delete m;
   return QMLR_OK;
 }
@@ -160,20 +181,31 @@ extern "C" int qmlr_model_destroy(qmlr_model* m) {
 extern "C" int qmlr_model_set_alpha(qmlr_model* m, const float* host_alpha) {
   QMLR_REQUIRE(m && host_alpha, "NULL pointer argument");
   QMLR_CUDA_TRY(cudaMemcpy(m->alpha, host_alpha, (size_t)m->n_features * 4, cudaMemcpyHostToDevice));
+  const int ns = m->n_features / m->d;
+  std::vector<float> t((size_t)m->n_features);
+  for (int st = 0; st < ns; ++st)
+    for (int i = 0; i < m->d; ++i) t[(size_t)i * ns + st] = host_alpha[(size_t)st * m->d + i];
+  QMLR_CUDA_TRY(cudaMemcpy(m->alphaT, t.data(), (size_t)m->n_features * 4, cudaMemcpyHostToDevice));
   return QMLR_OK;
 }
 
 namespace qmlr {
-__global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int n) {
+// b[i] = float(a[i]); bT[(i % d) * n_stack + i / d] = float(a[i])  (natural and stack-minor copies)
+__global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, float* __restrict__ bT,
+                                  int n, int d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
+  if (i < n) {
+    const float v = (float)a[i];
+    b[i] = v;
+    bT[(long)(i % d) * (n / d) + i / d] = v;
+  }
 }
 }  // namespace qmlr
 
 extern "C" int qmlr_model_set_alpha_device(qmlr_model* m, const double* alpha, void* stream) {
   QMLR_REQUIRE(m && alpha, "NULL pointer argument");
-  f64_to_f32_kernel<<<(m->n_features + 255) / 256, 256, 0, as_stream(stream)>>>(alpha, m->alpha,
-                                                                                m->n_features);
+  f64_to_f32_kernel<<<(m->n_features + 255) / 256, 256, 0, as_stream(stream)>>>(alpha, m->alpha, m->alphaT,
+                                                                                m->n_features, m->d);
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }

@@ -18,11 +18,20 @@ struct PredictWorkspace {
   int32_t* offs = nullptr;  // [n_el+1]
   void* gwork = nullptr;
   int64_t gwork_bytes = 0;
+  double* atom_e = nullptr;   // [n_part][cap] per-atom energy partials
+  int64_t* pair_ptr = nullptr;// [cap_mols + 1] offsets of the per-centre force contributions
+  float* contrib = nullptr;   // [cap * max_mol_atoms * 3]
+  int cap_mols = 0;
 
   int reserve(const qmlr_model* m, int max_atoms);
   void release();
   static size_t bytes_per_atom(const qmlr_model* m);
 };
+
+// SORF energies (and gradients when gx != NULL) with stack-minor phases/weights.
+int sorf_energy_grad_model(const float* x, int d, const int32_t* mol_ptr, int n_mol, int n_atoms,
+                           const uint32_t* sign_bits, int T, const float* bT, int n_features, double sigma,
+                           const float* alphaT, double* atom_e, double* E, float* gx, cudaStream_t s);
 
 // Energies and forces of a CSR batch with the given workspace (no allocation).
 int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
@@ -40,5 +49,7 @@ struct qmlr_model {
   uint32_t* signs = nullptr;   // [n_stack][T][W]
   float* b = nullptr;          // [N_F]
   float* alpha = nullptr;      // [N_F]
+  float* bT = nullptr;         // [d][n_stack] stack-minor copy of b
+  float* alphaT = nullptr;     // [d][n_stack] stack-minor copy of alpha
   qmlr::PredictWorkspace ws;   // workspace of qmlr_predict_ef
 };

@@ -107,10 +107,10 @@ static void CUDART_CB lane_finished(void* p) {
   l->server->cv_work.notify_all();
 }
 
-// Batch-size buckets: 256 * 2^(q/4), rounded up to a multiple of 32, capped at max_batch_atoms.
+// Batch-size buckets: 64 * 2^(q/8), rounded up to a multiple of 32, capped at max_batch_atoms.
 static int bucket_for(int atoms, int cap) {
-  double b = 256.0;
-  while (b < atoms) b *= 1.189207115002721;   // 2^(1/4)
+  double b = 64.0;
+  while (b < atoms) b *= 1.0905077326652577;   // 2^(1/8)
   int v = ((int)std::ceil(b) + 31) & ~31;
   return std::min(std::max(v, 32), cap);
 }
@@ -179,11 +179,11 @@ static int dispatch(qmlr_server* S, Lane& L) {
     L.h_mol_ptr[++mm] = a;
     r->state = 1;
   }
-  // padding atoms: isolated (10 A apart, far from the molecules), in molecules of at most
-  // max_mol_atoms atoms
+  // padding atoms: isolated (10 A apart, far from the molecules), one per molecule so
+  // that no kernel walks a long padding molecule
   int k = 0;
   while (a < bucket) {
-    const int take = std::min(S->m->max_mol_atoms, bucket - a);
+    const int take = 1;
     for (int q = 0; q < take; ++q, ++k) {
       L.h_coords[3 * (size_t)(a + q) + 0] = 1.0e5f + 10.0f * (float)k;
       L.h_coords[3 * (size_t)(a + q) + 1] = 0.f;
@@ -290,9 +290,12 @@ extern "C" int qmlr_serve_create(qmlr_model* m, const qmlr_serve_config* cfg, qm
   QMLR_REQUIRE(cfg->max_batch_atoms >= m->max_mol_atoms,
                "max_batch_atoms (%d) must hold the largest molecule (%d)", cfg->max_batch_atoms,
                m->max_mol_atoms);
-  const int pad_reserve = (int)std::ceil(0.19 * cfg->max_batch_atoms / m->max_mol_atoms) + 1;
+  // padding is at most 9.1 % of a bucket (8 buckets per octave) plus rounding to 32
+  const int pad_reserve = (int)std::ceil(0.091 * cfg->max_batch_atoms) + 33;
   QMLR_REQUIRE(cfg->max_batch_mols >= pad_reserve + 1,
                "max_batch_mols must be >= %d (one molecule plus padding)", pad_reserve + 1);
+  QMLR_REQUIRE(cfg->max_batch_mols <= cfg->max_batch_atoms + 4096,
+               "max_batch_mols must be <= max_batch_atoms + 4096");
   QMLR_REQUIRE(cfg->max_slots >= 1 && cfg->max_inflight_atoms >= m->max_mol_atoms, "bad admission limits");
   const size_t per_atom = PredictWorkspace::bytes_per_atom(m) + 3 * 4 + 4 + 12;
   const int64_t need = (int64_t)cfg->n_lanes * ((int64_t)per_atom * cfg->max_batch_atoms +
@@ -445,5 +448,77 @@ extern "C" int qmlr_serve_destroy(qmlr_server* S) {
   if (S->worker.joinable()) S->worker.join();
   for (Lane* L : S->lanes) destroy_lane(L);
   delete S;
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_serve_replay(qmlr_server* S, const float* host_coords, const int32_t* host_elem,
+                                 const int32_t* host_mol_ptr, int32_t n_pool, const double* arrival_us,
+                                 const int32_t* pick, int32_t n_req, int64_t* rejected,
+                                 qmlr_serve_report* out) {
+  QMLR_REQUIRE(S && host_coords && host_elem && host_mol_ptr && arrival_us && pick && out, "NULL pointer argument");
+  QMLR_REQUIRE(n_pool >= 1 && n_req >= 0, "bad sizes");
+  for (int i = 0; i < n_req; ++i)
+    QMLR_REQUIRE(pick[i] >= 0 && pick[i] < n_pool, "pick[%d] = %d out of range", i, pick[i]);
+  int rc = qmlr_serve_reset_stats(S);
+  if (rc) return rc;
+  // collector: polls tickets in submission order
+  std::mutex qm;
+  std::condition_variable qcv;
+  std::deque<std::pair<uint64_t, int>> pending;
+  bool done_submitting = false;
+  int first_err = QMLR_OK;
+  std::thread collector([&]() {
+    std::vector<float> F;
+    for (;;) {
+      std::pair<uint64_t, int> item;
+      {
+        std::unique_lock<std::mutex> lk(qm);
+        qcv.wait(lk, [&] { return !pending.empty() || done_submitting; });
+        if (pending.empty()) return;
+        item = pending.front();
+        pending.pop_front();
+      }
+      F.resize(3 * (size_t)item.second);
+      double E;
+      const int r = qmlr_serve_poll(S, item.first, &E, F.data(), 60000000);
+      if (r != QMLR_OK && first_err == QMLR_OK) first_err = r;
+    }
+  });
+  int64_t rej = 0;
+  const double t0 = now_us();
+  for (int i = 0; i < n_req; ++i) {
+    while (now_us() - t0 < arrival_us[i]) {
+    }
+    const int k = pick[i];
+    const int a = host_mol_ptr[k], n = host_mol_ptr[k + 1] - a;
+    uint64_t t;
+    const int r = qmlr_serve_submit(S, host_coords + 3 * (size_t)a, host_elem + a, n, &t);
+    if (r == QMLR_EBUSY) {
+      ++rej;
+      continue;
+    }
+    if (r != QMLR_OK) {
+      if (first_err == QMLR_OK) first_err = r;
+      break;
+    }
+    {
+      std::lock_guard<std::mutex> lk(qm);
+      pending.emplace_back(t, n);
+    }
+    qcv.notify_one();
+  }
+  {
+    std::lock_guard<std::mutex> lk(qm);
+    done_submitting = true;
+  }
+  qcv.notify_one();
+  collector.join();
+  if (rejected) *rejected = rej;
+  rc = qmlr_serve_stats(S, out);
+  if (rc) return rc;
+  if (first_err) {
+    set_error("replay failed with status %d", first_err);
+    return first_err;
+  }
   return QMLR_OK;
 }

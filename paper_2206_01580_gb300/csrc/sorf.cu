@@ -53,6 +53,31 @@ __device__ __forceinline__ void flip(float (&v)[D], const uint32_t* w) {
   }
 }
 
+// sin and cos of an FP32 argument: Cody-Waite reduction by 2*pi with a
+// two-part constant (2*pi = 6.28125 + 1.9353071795864769e-3; 6.28125 has an
+// 8-bit significand so k * 6.28125 is exact for |k| < 2^16), then the
+// hardware approximations on [-pi, pi] (absolute error ~2^-21). The feature
+// arguments here stay well inside |u| < 2^16.
+__device__ __forceinline__ void fast_sincos(float u, float* sn, float* cs) {
+  const float k = rintf(u * 0.15915494309189535f);
+  float r = fmaf(-k, 6.28125f, u);
+  r = fmaf(-k, 1.9353071795864769e-3f, r);
+  *sn = __sinf(r);
+  *cs = __cosf(r);
+}
+__device__ __forceinline__ float fast_cos(float u) {
+  const float k = rintf(u * 0.15915494309189535f);
+  float r = fmaf(-k, 6.28125f, u);
+  r = fmaf(-k, 1.9353071795864769e-3f, r);
+  return __cosf(r);
+}
+__device__ __forceinline__ float fast_sin(float u) {
+  const float k = rintf(u * 0.15915494309189535f);
+  float r = fmaf(-k, 6.28125f, u);
+  r = fmaf(-k, 1.9353071795864769e-3f, r);
+  return __sinf(r);
+}
+
 struct SorfArgs {
   const float* x;
   const int32_t* mol_ptr;
@@ -64,6 +89,9 @@ struct SorfArgs {
   int n_atoms, n_stack, T, n_features, n_part;
   float scale;  // (sqrt(d)/sigma) / d^{T/2}
   float pref;   // sqrt(2/N_F)
+  // layout of b and alpha: element (stack s, index i) at s*sstr + i*istr
+  // (natural order: sstr = d, istr = 1; stack-minor: sstr = 1, istr = n_stack)
+  long sstr = 0, istr = 1;
 };
 
 template <int D, int MODE>
@@ -88,6 +116,7 @@ sorf_kernel(SorfArgs a) {
 
   const float* bs = a.b + (long)(active ? s : 0) * D;
   const float* as = (MODE == M_ENERGY || MODE == M_ENERGY_GRAD) ? a.alpha + (long)(active ? s : 0) * D : nullptr;
+  // (this kernel reads b and alpha in natural order)
   double e_acc = 0.0;
 
   for (int atom = a0; atom < a1; ++atom) {
@@ -109,25 +138,25 @@ sorf_kernel(SorfArgs a) {
       if (active) {
         float* o = static_cast<float*>(a.out) + (long)atom * a.n_features + s;
 #pragma unroll
-        for (int i = 0; i < D; ++i) o[(long)i * a.n_stack] = a.pref * sinf(fmaf(v[i], a.scale, __ldg(bs + i)));
+        for (int i = 0; i < D; ++i) o[(long)i * a.n_stack] = a.pref * fast_sin(fmaf(v[i], a.scale, __ldg(bs + i)));
       }
     } else if (MODE == M_PER_ATOM) {
       if (active) {
         float* o = static_cast<float*>(a.out) + (long)atom * a.n_features + (long)s * D;
 #pragma unroll
-        for (int i = 0; i < D; ++i) o[i] = a.pref * cosf(fmaf(v[i], a.scale, __ldg(bs + i)));
+        for (int i = 0; i < D; ++i) o[i] = a.pref * fast_cos(fmaf(v[i], a.scale, __ldg(bs + i)));
       }
     } else if (MODE == M_PER_MOL) {
       if (active) {
 #pragma unroll
         for (int i = 0; i < D; ++i)
-          work[i * (nt + 1) + tid] += a.pref * cosf(fmaf(v[i], a.scale, __ldg(bs + i)));
+          work[i * (nt + 1) + tid] += a.pref * fast_cos(fmaf(v[i], a.scale, __ldg(bs + i)));
       }
     } else if (MODE == M_ENERGY) {
       if (active) {
         float e = 0.f;
 #pragma unroll
-        for (int i = 0; i < D; ++i) e = fmaf(__ldg(as + i), cosf(fmaf(v[i], a.scale, __ldg(bs + i))), e);
+        for (int i = 0; i < D; ++i) e = fmaf(__ldg(as + i), fast_cos(fmaf(v[i], a.scale, __ldg(bs + i))), e);
         e_acc += (double)e;
       }
     } else {  // M_ENERGY_GRAD
@@ -136,7 +165,7 @@ sorf_kernel(SorfArgs a) {
 #pragma unroll
         for (int i = 0; i < D; ++i) {
           float sn, cs;
-          sincosf(fmaf(v[i], a.scale, __ldg(bs + i)), &sn, &cs);
+          fast_sincos(fmaf(v[i], a.scale, __ldg(bs + i)), &sn, &cs);
           const float al = __ldg(as + i);
           e = fmaf(al, cs, e);
           v[i] = -a.pref * a.scale * al * sn;   // dE/d(chain output)
@@ -249,6 +278,162 @@ force_rows_kernel(const float* __restrict__ tang, const int64_t* __restrict__ ja
     const int nf = min(nt, n_stack - part * kStacksPerCta) * D;
     for (int f = tid; f < nf; f += nt) o[f] = acc[(f % D) * (nt + 1) + f / D];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Energy (and gradient) with one CTA per (atom, stack part): atoms of one
+// molecule run in parallel. The atom's energy partial (FP64, reduced over the
+// CTA's stacks in a fixed order) goes to atom_e[part][atom]; molecule energies
+// are then summed over atoms and parts in order by segment_energy_kernel.
+template <int D, bool GRAD>
+__global__ void __launch_bounds__(kStacksPerCta)
+sorf_atom_kernel(SorfArgs a, double* __restrict__ atom_e) {
+  constexpr int W = (D + 31) / 32;
+  extern __shared__ __align__(16) float smem[];
+  float* xs = smem;                                           // [D]
+  double* red = reinterpret_cast<double*>(smem + D + 4);      // [nt]
+  uint32_t* sg = reinterpret_cast<uint32_t*>(red + kStacksPerCta);   // [T*W][nt]
+  float* work = reinterpret_cast<float*>(sg + 4 * W * kStacksPerCta);  // [nt][D+1] (gradient)
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int atom = blockIdx.x, part = blockIdx.y;
+  const int s = part * kStacksPerCta + tid;
+  const bool active = s < a.n_stack;
+  for (int i = tid; i < D; i += nt) xs[i] = __ldg(a.x + (long)atom * D + i);
+  for (int k = 0; k < a.T * W; ++k) sg[k * nt + tid] = active ? __ldg(a.sign_bits + (long)s * a.T * W + k) : 0u;
+  __syncthreads();
+  float v[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) v[i] = xs[i];
+  for (int t = 0; t < a.T; ++t) {
+    uint32_t w[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) w[q] = sg[(t * W + q) * nt + tid];
+    flip<D>(v, w);
+    fwht<D>(v);
+  }
+  const float* bs = a.b + (long)(active ? s : 0) * a.sstr;
+  const float* as = a.alpha + (long)(active ? s : 0) * a.sstr;
+  float e = 0.f;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float u = fmaf(v[i], a.scale, __ldg(bs + i * a.istr));
+      const float al = __ldg(as + i * a.istr);
+      if (GRAD) {
+        float sn, cs;
+        fast_sincos(u, &sn, &cs);
+        e = fmaf(al, cs, e);
+        v[i] = -a.pref * a.scale * al * sn;
+      } else {
+        e = fmaf(al, fast_cos(u), e);
+      }
+    }
+  } else if (GRAD) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = 0.f;
+  }
+  red[tid] = (double)e;
+  if (GRAD) {
+    for (int t = a.T - 1; t >= 0; --t) {
+      uint32_t w[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) w[q] = sg[(t * W + q) * nt + tid];
+      fwht<D>(v);
+      flip<D>(v, w);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) work[tid * (D + 1) + i] = v[i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int k = 0; k < nt; ++k) sum += red[k];
+    atom_e[(long)part * a.n_atoms + atom] = sum * (double)a.pref;
+  }
+  if (GRAD) {
+    for (int i = tid; i < D; i += nt) {
+      float sum = 0.f;
+      for (int k = 0; k < nt; ++k) sum += work[k * (D + 1) + i];
+      a.gx[((long)part * a.n_atoms + atom) * D + i] = sum;
+    }
+  }
+}
+
+// E[m] = sum over the molecule's atoms (in order) of sum over parts (in order).
+__global__ void segment_energy_kernel(const double* __restrict__ atom_e, int n_part, int n_atoms,
+                                      const int32_t* __restrict__ mol_ptr, int n_mol, double* __restrict__ E) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_mol) return;
+  double sum = 0.0;
+  for (int i = mol_ptr[m]; i < mol_ptr[m + 1]; ++i)
+    for (int p = 0; p < n_part; ++p) sum += atom_e[(long)p * n_atoms + i];
+  E[m] = sum;
+}
+
+template <int D, bool GRAD>
+static int launch_atoms(const SorfArgs& a, double* atom_e, int n_mol, double* E, cudaStream_t s) {
+  const int nt = std::min(kStacksPerCta, ((a.n_stack + 31) / 32) * 32);
+  constexpr int W = (D + 31) / 32;
+  const size_t smem = (size_t)(D + 4) * 4 + kStacksPerCta * 8 + (size_t)4 * W * kStacksPerCta * 4 +
+                      (GRAD ? (size_t)nt * (D + 1) * 4 : 0);
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(sorf_atom_kernel<D, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    attr = true;
+  }
+  if (a.n_atoms > 0) {
+    dim3 grid(a.n_atoms, a.n_part);
+    sorf_atom_kernel<D, GRAD><<<grid, nt, smem, s>>>(a, atom_e);
+    QMLR_LAUNCH_CHECK();
+  }
+  segment_energy_kernel<<<(n_mol + 255) / 256, 256, 0, s>>>(atom_e, a.n_part, a.n_atoms, a.mol_ptr, n_mol, E);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+// Energies and (optionally) gradients, atoms in parallel. Internal entry used
+// by qmlr_sorf_grad and the model's prediction (b/alpha layout from a.sstr/istr).
+int sorf_energy_atoms(const SorfArgs& a, int d, double* atom_e, int n_mol, double* E, bool grad,
+                      cudaStream_t s) {
+  switch (d) {
+    case 16: return grad ? launch_atoms<16, true>(a, atom_e, n_mol, E, s) : launch_atoms<16, false>(a, atom_e, n_mol, E, s);
+    case 32: return grad ? launch_atoms<32, true>(a, atom_e, n_mol, E, s) : launch_atoms<32, false>(a, atom_e, n_mol, E, s);
+    case 64: return grad ? launch_atoms<64, true>(a, atom_e, n_mol, E, s) : launch_atoms<64, false>(a, atom_e, n_mol, E, s);
+    default: return grad ? launch_atoms<128, true>(a, atom_e, n_mol, E, s) : launch_atoms<128, false>(a, atom_e, n_mol, E, s);
+  }
+}
+
+SorfArgs make_sorf_args(const float* x, int d, const int32_t* mol_ptr, int n_atoms, const uint32_t* sign_bits,
+                        int T, const float* b, int n_features, double sigma, const float* alpha, float* gx,
+                        bool stack_minor) {
+  SorfArgs a;
+  a.x = x;
+  a.mol_ptr = mol_ptr;
+  a.sign_bits = sign_bits;
+  a.b = b;
+  a.alpha = alpha;
+  a.out = nullptr;
+  a.gx = gx;
+  a.n_atoms = n_atoms;
+  a.n_stack = n_features / d;
+  a.T = T;
+  a.n_features = n_features;
+  a.n_part = (a.n_stack + kStacksPerCta - 1) / kStacksPerCta;
+  a.scale = (float)(sqrt((double)d) / sigma / pow((double)d, 0.5 * T));
+  a.pref = (float)sqrt(2.0 / n_features);
+  a.sstr = stack_minor ? 1 : d;
+  a.istr = stack_minor ? a.n_stack : 1;
+  return a;
+}
+
+// Energies and gradients for a model whose phases and weights are stored
+// stack-minor (element (s, i) at i * n_stack + s: coalesced across the warp).
+int sorf_energy_grad_model(const float* x, int d, const int32_t* mol_ptr, int n_mol, int n_atoms,
+                           const uint32_t* sign_bits, int T, const float* bT, int n_features, double sigma,
+                           const float* alphaT, double* atom_e, double* E, float* gx, cudaStream_t s) {
+  SorfArgs a = make_sorf_args(x, d, mol_ptr, n_atoms, sign_bits, T, bT, n_features, sigma, alphaT, gx, true);
+  return sorf_energy_atoms(a, d, atom_e, n_mol, E, gx != nullptr, s);
 }
 
 template <int D>
@@ -393,9 +578,17 @@ extern "C" int qmlr_force_rows(const float* tangents, int32_t d, const int64_t* 
 }
 
 extern "C" int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
-                              int32_t n_atoms, const uint32_t* sign_bits, int32_t T,
-                              const float* b, int32_t n_features, double sigma,
-                              const float* alpha, double* energies, float* gx, void* stream) {
-  return sorf_dispatch(x, d, mol_ptr, n_mol, n_atoms, sign_bits, T, b, n_features, sigma, alpha,
-                       M_ENERGY_GRAD, energies, gx, stream);
+                              int32_t n_atoms, const uint32_t* sign_bits, int32_t T, const float* b,
+                              int32_t n_features, double sigma, const float* alpha, double* atom_energy,
+                              double* energies, float* gx, void* stream) {
+  QMLR_REQUIRE(d == 16 || d == 32 || d == 64 || d == 128, "d must be 16, 32, 64 or 128 (got %d)", d);
+  QMLR_REQUIRE(T >= 1 && T <= 4, "T must be in 1..4 (got %d)", T);
+  QMLR_REQUIRE(n_features >= d && n_features % d == 0, "n_features must be a positive multiple of d");
+  QMLR_REQUIRE(sigma > 0, "sigma must be > 0");
+  QMLR_REQUIRE(n_mol >= 0 && n_atoms >= 0, "negative sizes");
+  if (n_mol == 0) return QMLR_OK;
+  QMLR_REQUIRE(mol_ptr && energies && atom_energy, "NULL pointer argument");
+  QMLR_REQUIRE(n_atoms == 0 || (x && sign_bits && b && alpha), "NULL pointer argument");
+  SorfArgs a = make_sorf_args(x, d, mol_ptr, n_atoms, sign_bits, T, b, n_features, sigma, alpha, gx, false);
+  return sorf_energy_atoms(a, d, atom_energy, n_mol, energies, gx != nullptr, as_stream(stream));
 }

@@ -67,6 +67,8 @@ _SIGS = {
     "qmlr_fchl19": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, VP]),
     "qmlr_fchl19_vjp": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, P, I32, VP]),
     "qmlr_jac_offsets": (C.c_int, [P, I32, P, C.POINTER(C.c_int64), VP]),
+    "qmlr_fchl19_vjp_atoms": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, I32, P, P, C.c_float,
+                                        P, I32, VP]),
     "qmlr_fchl19_jac": (C.c_int, [P, P, P, I32, I32, I32, C.POINTER(_Params), P, P, I32, P, VP]),
     "qmlr_force_rows": (C.c_int, [P, I32, P, P, I32, P, P, I32, I32, D, P, I64, I64, VP]),
     "qmlr_group_workspace_bytes": (C.c_int64, [I32]),
@@ -76,7 +78,7 @@ _SIGS = {
     "qmlr_project_t": (C.c_int, [P, I32, P, P, I32, I32, P, I32, I32, P, I32, VP]),
     "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
-    "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, VP]),
+    "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, VP]),
     "qmlr_gram_operand": (C.c_int, [P, I64, I32, I64, I32, P, I64, VP]),
     "qmlr_gram": (C.c_int, [I32, P, I64, I32, I64, P, I64, P, VP]),
     "qmlr_zty_workspace_bytes": (C.c_int64, [I64, I32]),
@@ -100,6 +102,7 @@ _SIGS = {
     "qmlr_serve_stats": (C.c_int, [VP, C.POINTER(ServeStats)]),
     "qmlr_serve_reset_stats": (C.c_int, [VP]),
     "qmlr_serve_destroy": (C.c_int, [VP]),
+    "qmlr_serve_replay": (C.c_int, [VP, P, P, P, I32, P, P, I32, C.POINTER(C.c_int64), C.POINTER(ServeStats)]),
 }
 
 
@@ -200,6 +203,25 @@ def fchl19_vjp(coords, elem, mol_ptr, max_atoms: int, p: FCHL19Params, grad_rep,
     return out
 
 
+def fchl19_vjp_atoms(coords, elem, mol_ptr, max_atoms: int, p: FCHL19Params, grad_rep, scale: float = 1.0):
+    """The VJP with one warp per centre (scratch sized from the molecule sizes)."""
+    coords = _dev(coords, torch.float32)
+    elem = _dev(elem, torch.int32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    grad_rep = _dev(grad_rep, torch.float32)
+    n_atoms, n_mol = coords.shape[0], mol_ptr.shape[0] - 1
+    pair_ptr = torch.empty(n_mol + 1, device="cuda", dtype=torch.int64)
+    total = C.c_int64(0)
+    _check(lib().qmlr_jac_offsets(_ptr(mol_ptr), n_mol, _ptr(pair_ptr), C.byref(total), _stream()))
+    contrib = torch.empty(max(total.value, 1), device="cuda", dtype=torch.float32)
+    out = torch.empty((n_atoms, 3), device="cuda", dtype=torch.float32)
+    cp = c_params(p)
+    _check(lib().qmlr_fchl19_vjp_atoms(_ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol, n_atoms, max_atoms,
+                                       C.byref(cp), _ptr(grad_rep), grad_rep.shape[1], _ptr(pair_ptr),
+                                       _ptr(contrib), scale, _ptr(out), 0, _stream()))
+    return out
+
+
 # ----------------------------------------------------------------------------
 # projection
 
@@ -292,8 +314,10 @@ def sorf_grad(x, mol_ptr, sign_bits, T: int, b, sigma: float, alpha):
     n_part = sorf_parts(nf, d)
     E = torch.empty((n_mol,), device="cuda", dtype=torch.float64)
     gx = torch.empty((n_part, n_atoms, d), device="cuda", dtype=torch.float32)
+    atom_e = torch.empty((n_part, max(n_atoms, 1)), device="cuda", dtype=torch.float64)
     _check(lib().qmlr_sorf_grad(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(sign_bits), T,
-                                _ptr(b), nf, float(sigma), _ptr(alpha), _ptr(E), _ptr(gx), _stream()))
+                                _ptr(b), nf, float(sigma), _ptr(alpha), _ptr(atom_e), _ptr(E), _ptr(gx),
+                                _stream()))
     return E, gx
 
 
@@ -546,6 +570,21 @@ class Server:
 
     def reset_stats(self):
         _check(lib().qmlr_serve_reset_stats(self.handle))
+
+    def replay(self, coords, elem, mol_ptr, arrival_s, pick) -> dict:
+        """Replay a request trace from native threads; returns the run's statistics."""
+        c = np.ascontiguousarray(coords, dtype=np.float32)
+        e = np.ascontiguousarray(elem, dtype=np.int32)
+        mp = np.ascontiguousarray(mol_ptr, dtype=np.int32)
+        at = np.ascontiguousarray(np.asarray(arrival_s, dtype=np.float64) * 1e6)
+        pk = np.ascontiguousarray(pick, dtype=np.int32)
+        rej = C.c_int64(0)
+        st = ServeStats()
+        _check(lib().qmlr_serve_replay(self.handle, c.ctypes.data, e.ctypes.data, mp.ctypes.data, len(mp) - 1,
+                                       at.ctypes.data, pk.ctypes.data, len(pk), C.byref(rej), C.byref(st)))
+        out = {k: getattr(st, k) for k, _ in ServeStats._fields_}
+        out["rejected"] = rej.value
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

@@ -107,10 +107,14 @@ def test_fchl19_vjp_matches_oracle_autograd(q):
     got = q.fchl19_vjp(mols.coords, mols.elem, mols.mol_ptr, int(mols.sizes().max()),
                        gpu_params("EF"), gpad).cpu().numpy()
     assert q.device_status() == 0
+    got2 = q.fchl19_vjp_atoms(mols.coords, mols.elem, mols.mol_ptr, int(mols.sizes().max()),
+                              gpu_params("EF"), gpad, scale=-1.0).cpu().numpy()
+    assert q.device_status() == 0
     for m in range(mols.n_mol):
         a, b = int(mols.mol_ptr[m]), int(mols.mol_ptr[m + 1])
         scale = np.max(np.abs(ref[a:b]))
         assert np.max(np.abs(got[a:b] - ref[a:b])) <= 1e-4 * scale, m
+        assert np.max(np.abs(-got2[a:b] - ref[a:b])) <= 1e-4 * scale, m
 
 
 def test_group_by_element_is_stable_counting_sort(q):

@@ -59,7 +59,7 @@ def _serve_all(srv, mols, alone: bool):
 @pytest.mark.parametrize("use_graphs", [True, False])
 def test_result_is_the_same_alone_and_in_the_mix(setup, use_graphs):
     qmlr, model, mols, _ = setup
-    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=2048, max_batch_mols=64, use_graphs=use_graphs)
+    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=2048, max_batch_mols=512, use_graphs=use_graphs)
     alone = _serve_all(srv, mols, alone=True)
     mixed = _serve_all(srv, mols, alone=False)
     mixed2 = _serve_all(srv, mols, alone=False)   # graphs replayed
@@ -80,7 +80,7 @@ def test_result_is_the_same_alone_and_in_the_mix(setup, use_graphs):
 
 def test_served_results_match_oracle(setup):
     qmlr, model, mols, (po, U, signs, b, alpha) = setup
-    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=2048, max_batch_mols=64)
+    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=2048, max_batch_mols=512)
     sub = mols.subset([0, 1, 2, 3])
     om = o_model.sorf_model(po, U.astype(np.float64), signs, b.astype(np.float64), 2.0, alpha.astype(np.float64))
     E_ref, F_ref = o_model.energies_forces(sub.coords, sub.elem, sub.mol_ptr, om)
@@ -95,7 +95,7 @@ def test_served_results_match_oracle(setup):
 
 def test_admission_limits_and_bounded_waits(setup):
     qmlr, model, mols, _ = setup
-    srv = qmlr.Server(model, n_lanes=1, max_batch_atoms=256, max_batch_mols=16, max_slots=4,
+    srv = qmlr.Server(model, n_lanes=1, max_batch_atoms=256, max_batch_mols=128, max_slots=4,
                       use_graphs=False)
     c, e = mols.molecule(0)
     tickets = [srv.submit(c, e) for _ in range(4)]
@@ -109,7 +109,7 @@ def test_admission_limits_and_bounded_waits(setup):
     assert srv.try_submit(big, np.zeros(201, np.int32))[0] == qmlr.EINVAL
     srv.close()
     # a bounded poll runs out while work is still queued, and the ticket stays valid
-    srv = qmlr.Server(model, n_lanes=1, max_batch_atoms=256, max_batch_mols=16, use_graphs=False)
+    srv = qmlr.Server(model, n_lanes=1, max_batch_atoms=256, max_batch_mols=128, use_graphs=False)
     bigm = [m for m in range(mols.n_mol) if mols.sizes()[m] > 150][:1]
     cb, eb = mols.molecule(bigm[0])
     ts = [srv.submit(cb, eb) for _ in range(40)]
