@@ -275,6 +275,123 @@ fchl19_forward_kernel(const float* __restrict__ coords, const int32_t* __restric
   for (int k = lane; k < rep_ld; k += 32) out[k] = k < c.rep_dim ? s.acc[k] : 0.0f;
 }
 
+// Register-accumulating forward for up to 5 elements (15 element pairs) and
+// radial grids of at most 32 points: lane k owns radial bin k of every element
+// (two-body) and of every element pair (three-body, cos and sin), so the
+// accumulation is a warp-uniform switch on the element or pair index into
+// registers instead of a shared-memory read-modify-write; the row is written
+// straight from registers at the end. Same order of summation as the
+// shared-memory kernel (neighbours, then pairs in the same order).
+#define QMLR_CASE2(E) case E: a2[E] += v; break;
+#define QMLR_CASE3(P) case P: ac[P] += g * pr.x; as[P] += g * pr.y; break;
+
+__global__ void __launch_bounds__(32 * kWarpsFwd)
+fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
+                          const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp, int rp,
+                          Fchl19Consts c, float* __restrict__ rep, int rep_ld, int* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int atom = blockIdx.x * kWarpsFwd + warp;
+  if (atom >= n_atoms) return;
+  FwdWarp s = carve_fwd(smem_raw + warp * fwd_warp_bytes(mxp, rp), mxp, rp);
+  const int m = find_molecule(mol_ptr, n_mol, atom);
+  const int a0 = __ldg(mol_ptr + m);
+  const int M = __ldg(mol_ptr + m + 1) - a0;
+  float* out = rep + (size_t)atom * rep_ld;
+  if (M > mx) {
+    if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+    for (int k = lane; k < rep_ld; k += 32) out[k] = 0.0f;
+    return;
+  }
+  stage_molecule(coords, elem, a0, M, c.n_el, s.pos, lane, 32, err);
+  __syncwarp();
+  const int n = neighbour_list(s.pos, M, atom - a0, c, s.nb_u, s.nb_2b, s.nb_el, nullptr, lane);
+
+  float a2[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  const bool has2 = lane < c.n2;
+  const float r2log = has2 ? c.rs2_log[lane] : 0.f, r2inv = has2 ? c.rs2_inv[lane] : 0.f;
+  for (int jn = 0; jn < n; ++jn) {
+    const float4 t = s.nb_2b[jn];
+    const float a = r2log - t.x;
+    const float v = t.z * r2inv * expf(-a * a * t.y);
+    switch (s.nb_el[jn]) { QMLR_CASE2(0) QMLR_CASE2(1) QMLR_CASE2(2) QMLR_CASE2(3) QMLR_CASE2(4) default: break; }
+  }
+
+  float ac[15], as[15];
+#pragma unroll
+  for (int q = 0; q < 15; ++q) {
+    ac[q] = 0.f;
+    as[q] = 0.f;
+  }
+  const bool has3 = lane < c.n3;
+  const float r3 = has3 ? c.rs3[lane] : 0.f;
+  const int n_pairs = n * (n - 1) / 2;
+  for (int q0 = 0; q0 < n_pairs; q0 += 32) {
+    const int q = q0 + lane;
+    bool ok = false;
+    float wc = 0.f, ws = 0.f, xbar = 0.f;
+    int pidx = 0;
+    if (q < n_pairs) {
+      int jn, kn;
+      decode_pair(q, n, jn, kn);
+      const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+      const float vx = uk.x * uk.w - uj.x * uj.w;
+      const float vy = uk.y * uk.w - uj.y * uj.w;
+      const float vz = uk.z * uk.w - uj.z * uj.w;
+      const float rjk2 = vx * vx + vy * vy + vz * vz;
+      if (rjk2 < c.rcut2) {
+        ok = true;
+        const float rjk = sqrtf(rjk2);
+        const float inv_rjk = 1.0f / rjk;
+        const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+        const float cx = uj.y * uk.z - uj.z * uk.y;
+        const float cy = uj.z * uk.x - uj.x * uk.z;
+        const float cz = uj.x * uk.y - uj.y * uk.x;
+        const float si = sqrtf(cx * cx + cy * cy + cz * cz);
+        const float cj = -(uj.x * vx + uj.y * vy + uj.z * vz) * inv_rjk;
+        const float ck = (uk.x * vx + uk.y * vy + uk.z * vz) * inv_rjk;
+        const float atm = (1.0f + 3.0f * ci * cj * ck) * expf(-c.N3 * logf(uj.w * uk.w * rjk));
+        const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * cutoff_f(rjk, c);
+        wc = w * c.ang2 * ci;
+        ws = w * c.ang2 * si;
+        xbar = 0.5f * (uj.w + uk.w);
+        pidx = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) s.pairs[__popc(mask & ((1u << lane) - 1u))] = make_float4(wc, ws, xbar, __int_as_float(pidx));
+    __syncwarp();
+    const int cnt = __popc(mask);
+    for (int t = 0; t < cnt; ++t) {
+      const float4 pr = s.pairs[t];
+      const float d = pr.z - r3;
+      const float g = expf(-c.eta3 * d * d);
+      switch (__float_as_int(pr.w)) {
+        QMLR_CASE3(0) QMLR_CASE3(1) QMLR_CASE3(2) QMLR_CASE3(3) QMLR_CASE3(4) QMLR_CASE3(5) QMLR_CASE3(6)
+        QMLR_CASE3(7) QMLR_CASE3(8) QMLR_CASE3(9) QMLR_CASE3(10) QMLR_CASE3(11) QMLR_CASE3(12) QMLR_CASE3(13)
+        QMLR_CASE3(14) default: break;
+      }
+    }
+    __syncwarp();
+  }
+  // write the row from registers; padding columns zero
+  if (has2)
+#pragma unroll
+    for (int e = 0; e < 5; ++e)
+      if (e < c.n_el) out[e * c.n2 + lane] = a2[e];
+  const int np = c.n_el * (c.n_el + 1) / 2;
+  if (has3)
+#pragma unroll
+    for (int q = 0; q < 15; ++q)
+      if (q < np) {
+        out[c.base3 + (q * c.n3 + lane) * 2] = ac[q];
+        out[c.base3 + (q * c.n3 + lane) * 2 + 1] = as[q];
+      }
+  for (int k = c.rep_dim + lane; k < rep_ld; k += 32) out[k] = 0.0f;
+}
+#undef QMLR_CASE2
+#undef QMLR_CASE3
+
 // ---------------------------------------------------------------------------
 // VJP: one CTA per molecule, warps over centre atoms.
 
@@ -803,11 +920,18 @@ extern "C" int qmlr_fchl19(const float* coords, const int32_t* elem, const int32
   if (!attr_set) {
     QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_forward_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_forward_reg_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr_set = true;
   }
   const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
-  fchl19_forward_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
-      coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, rep, rep_ld, device_error_ptr());
+  if (p->n_el <= 5 && p->n2 <= 32 && p->n3 <= 32) {
+    fchl19_forward_reg_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
+        coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, rep, rep_ld, device_error_ptr());
+  } else {
+    fchl19_forward_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
+        coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, rep, rep_ld, device_error_ptr());
+  }
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }

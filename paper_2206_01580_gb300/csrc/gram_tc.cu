@@ -146,6 +146,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // in the drain threads' registers, so that the tensor cores' accumulator adds
 // only ever sum one K block.
 constexpr int kDrainWarps = 16;
+constexpr int kGroupRows = 16;   // tile rows per rasterization panel
 constexpr int kDrainCols = 128 / (kDrainWarps / 4);   // columns per drain thread
 constexpr int kThreads = 32 * (kDrainWarps + 2);
 
@@ -169,18 +170,30 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  int t = blockIdx.x, bi = 0;
-  for (;;) {
-    const int first = (bi * BM) / BN;
-    const int cnt = tiles_j - first;
-    if (t < cnt) {
-      t += first;
-      break;
+  // Upper-triangle tiles in grouped order: panels of kGroupRows tile rows,
+  // each walked column by column, so the CTAs resident at one time share a
+  // few A and B panels (their K-block slices are then served from L2).
+  int t = blockIdx.x, bi = 0, bj = 0;
+  const int tiles_i = n_features / BM;
+  for (int r0 = 0; r0 < tiles_i; r0 += kGroupRows) {
+    const int r1 = min(r0 + kGroupRows, tiles_i);
+    int cnt = 0;
+    for (int c = r0; c < tiles_j; ++c) cnt += min(r1, c + 1) - r0;
+    if (t >= cnt) {
+      t -= cnt;
+      continue;
     }
-    t -= cnt;
-    ++bi;
+    for (int c = r0; c < tiles_j; ++c) {
+      const int h = min(r1, c + 1) - r0;
+      if (t < h) {
+        bi = r0 + t;
+        bj = c;
+        break;
+      }
+      t -= h;
+    }
+    break;
   }
-  const int bj = t;
   const int i0 = bi * BM, j0 = bj * BN;
 
   if (threadIdx.x == 0) {

@@ -120,3 +120,15 @@ def test_admission_limits_and_bounded_waits(setup):
     with pytest.raises(Exception):
         srv.submit(np.zeros((0, 3), np.float32), np.zeros(0, np.int32))
     srv.close()
+
+
+def test_trace_replay_completes_every_admitted_request(setup):
+    qmlr, model, mols, _ = setup
+    srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=2048, max_batch_mols=512)
+    rng = np.random.default_rng(5)
+    arrivals = synth.poisson_arrivals(rng, 2000.0, 0.2)
+    picks = rng.integers(0, mols.n_mol, size=len(arrivals))
+    st = srv.replay(mols.coords, mols.elem, mols.mol_ptr, arrivals, picks)
+    assert st["completed"] + st["rejected"] == len(arrivals)
+    assert st["completed"] > 0 and 0 < st["p50_us"] <= st["p99_us"]
+    srv.close()
