@@ -180,7 +180,27 @@ diag_inverse_kernel(const double* __restrict__ L, long ldl, int n, double* __res
   for (int i = 0; i < NB; ++i) out[i * NB + j] = x[i];
 }
 
-// forward step k: y_k = Dinv_k r_k; r[i] -= L[i][k0:k0+nb] y_k for rows i >= k0 + nb (warp per row)
+// x = Dinv_k^{(T)} v_k for one 64-block: 4 threads per output, 16 products each,
+// combined by shuffles (256 threads); result in xk (shared).
+__device__ __forceinline__ void block_matvec(const double* __restrict__ D, const double* vk, double* xk,
+                                             bool transposed) {
+  const int tid = threadIdx.x;
+  const int o = tid >> 2, part = tid & 3;
+  double acc = 0.0;
+  if (o < NB) {
+#pragma unroll
+    for (int l = part * 16; l < part * 16 + 16; ++l)
+      acc = fma(transposed ? D[l * NB + o] : D[o * NB + l], vk[l], acc);
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (o < NB && part == 0) xk[o] = acc;
+}
+
+constexpr int kTriCtas = 304;   // 2 CTAs per SM on 152 SMs
+
+// forward step k: y_k = Dinv_k r_k; r[i] -= L[i][k0:k0+nb] y_k for rows i >= k0 + nb
+// (warps grid-stride over rows, lanes over the 64 columns)
 __global__ void __launch_bounds__(256)
 fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
                 int n, double* __restrict__ r, double* __restrict__ y) {
@@ -188,31 +208,25 @@ fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict
   const int tid = threadIdx.x;
   if (tid < NB) rk[tid] = tid < nb ? r[k0 + tid] : 0.0;
   __syncthreads();
-  if (tid < NB) {
-    const double* D = Dinv + (long)(k0 / NB) * NB * NB + tid * NB;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int l = 0; l < NB; l += 4) {
-      a0 = fma(D[l], rk[l], a0);
-      a1 = fma(D[l + 1], rk[l + 1], a1);
-      a2 = fma(D[l + 2], rk[l + 2], a2);
-      a3 = fma(D[l + 3], rk[l + 3], a3);
-    }
-    xk[tid] = (a0 + a1) + (a2 + a3);
-    if (blockIdx.x == 0 && tid < nb) y[k0 + tid] = xk[tid];
-  }
+  block_matvec(Dinv + (long)(k0 / NB) * NB * NB, rk, xk, false);
   __syncthreads();
-  const int warp = (blockIdx.x * blockDim.x + tid) >> 5, lane = tid & 31;
-  const int row = k0 + nb + warp;
-  if (row >= n) return;
-  const double* Lr = L + (long)row * ldl + k0;
-  double s = 0.0;
-  for (int c = lane; c < nb; c += 32) s = fma(Lr[c], xk[c], s);
+  if (blockIdx.x == 0 && tid < nb) y[k0 + tid] = xk[tid];
+  const int lane = tid & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  const double x0 = lane < nb ? xk[lane] : 0.0, x1 = lane + 32 < nb ? xk[lane + 32] : 0.0;
+  for (int row = k0 + nb + blockIdx.x * (blockDim.x >> 5) + (tid >> 5); row < n; row += warps) {
+    const double* Lr = L + (long)row * ldl + k0;
+    double sum = 0.0;
+    if (lane < nb) sum = Lr[lane] * x0;
+    if (lane + 32 < nb) sum = fma(Lr[lane + 32], x1, sum);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) r[row] -= s;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) r[row] -= sum;
+  }
 }
 
 // backward step k: x_k = Dinv_k^T y_k; y[c] -= sum_r L[k0+r][c] x_k[r] for columns c < k0
+// (threads grid-stride over columns)
 __global__ void __launch_bounds__(256)
 bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
                 double* __restrict__ y, double* __restrict__ x) {
@@ -220,24 +234,21 @@ bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict
   const int tid = threadIdx.x;
   if (tid < NB) yk[tid] = tid < nb ? y[k0 + tid] : 0.0;
   __syncthreads();
-  if (tid < NB) {
-    const double* D = Dinv + (long)(k0 / NB) * NB * NB;   // x_t = sum_l Dinv[l][t] y_l
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int l = 0; l < NB; l += 4) {
-      a0 = fma(D[l * NB + tid], yk[l], a0);
-      a1 = fma(D[(l + 1) * NB + tid], yk[l + 1], a1);
-      a2 = fma(D[(l + 2) * NB + tid], yk[l + 2], a2);
-      a3 = fma(D[(l + 3) * NB + tid], yk[l + 3], a3);
-    }
-    xk[tid] = (a0 + a1) + (a2 + a3);
-    if (blockIdx.x == 0 && tid < nb) x[k0 + tid] = xk[tid];
-  }
+  block_matvec(Dinv + (long)(k0 / NB) * NB * NB, yk, xk, true);
   __syncthreads();
-  const int c = blockIdx.x * blockDim.x + tid;
-  if (c >= k0) return;
-  double s = 0.0;
-  for (int rr = 0; rr < nb; ++rr) s = fma(L[(long)(k0 + rr) * ldl + c], xk[rr], s);
-  y[c] -= s;
+  if (blockIdx.x == 0 && tid < nb) x[k0 + tid] = xk[tid];
+  for (int c = blockIdx.x * blockDim.x + tid; c < k0; c += gridDim.x * blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int rr = 0;
+    for (; rr + 4 <= nb; rr += 4) {
+      s0 = fma(L[(long)(k0 + rr) * ldl + c], xk[rr], s0);
+      s1 = fma(L[(long)(k0 + rr + 1) * ldl + c], xk[rr + 1], s1);
+      s2 = fma(L[(long)(k0 + rr + 2) * ldl + c], xk[rr + 2], s2);
+      s3 = fma(L[(long)(k0 + rr + 3) * ldl + c], xk[rr + 3], s3);
+    }
+    for (; rr < nb; ++rr) s0 = fma(L[(long)(k0 + rr) * ldl + c], xk[rr], s0);
+    y[c] -= (s0 + s1) + (s2 + s3);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -249,8 +260,16 @@ __global__ void zmv_kernel(const float* __restrict__ Z, long n_rows, int n_featu
   const int lane = threadIdx.x & 31;
   if (r >= n_rows) return;
   const float* zr = Z + r * ldz;
-  double s = 0.0;
-  for (int f = lane; f < n_features; f += 32) s = fma((double)__ldg(zr + f), __ldg(p + f), s);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int f = lane;
+  for (; f + 96 < n_features; f += 128) {
+    s0 = fma((double)__ldg(zr + f), __ldg(p + f), s0);
+    s1 = fma((double)__ldg(zr + f + 32), __ldg(p + f + 32), s1);
+    s2 = fma((double)__ldg(zr + f + 64), __ldg(p + f + 64), s2);
+    s3 = fma((double)__ldg(zr + f + 96), __ldg(p + f + 96), s3);
+  }
+  for (; f < n_features; f += 32) s0 = fma((double)__ldg(zr + f), __ldg(p + f), s0);
+  double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) t[r] = s;
@@ -265,9 +284,16 @@ __global__ void ztmv_partial_kernel(const float* __restrict__ Z, long n_rows, in
   const long r0 = (long)blockIdx.y * kZtRows;
   const long r1 = min(n_rows, r0 + kZtRows);
   if (f >= n_features) return;
-  double acc = 0.0;
-  for (long r = r0; r < r1; ++r) acc = fma((double)__ldg(Z + r * ldz + f), __ldg(t + r), acc);
-  part[(long)blockIdx.y * n_features + f] = acc;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  long r = r0;
+  for (; r + 4 <= r1; r += 4) {
+    a0 = fma((double)__ldg(Z + r * ldz + f), __ldg(t + r), a0);
+    a1 = fma((double)__ldg(Z + (r + 1) * ldz + f), __ldg(t + r + 1), a1);
+    a2 = fma((double)__ldg(Z + (r + 2) * ldz + f), __ldg(t + r + 2), a2);
+    a3 = fma((double)__ldg(Z + (r + 3) * ldz + f), __ldg(t + r + 3), a3);
+  }
+  for (; r < r1; ++r) a0 = fma((double)__ldg(Z + r * ldz + f), __ldg(t + r), a0);
+  part[(long)blockIdx.y * n_features + f] = (a0 + a1) + (a2 + a3);
 }
 
 __global__ void ztmv_finish_kernel(const double* __restrict__ part, int n_parts, int n,
@@ -383,7 +409,7 @@ static int chol_apply(const double* L, long ldl, const double* Dinv, int n, doub
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int nb = std::min(NB, n - k0);
     const int rows = std::max(n - k0 - nb, 0);
-    const int grid = std::max((rows * 32 + 255) / 256, 1);
+    const int grid = std::min(std::max((rows + 7) / 8, 1), kTriCtas);
     fwd_step_kernel<<<grid, 256, 0, s>>>(L, ldl, Dinv, k0, nb, n, v, tmp);
     QMLR_LAUNCH_CHECK();
   }
@@ -391,7 +417,7 @@ static int chol_apply(const double* L, long ldl, const double* Dinv, int n, doub
   const int last = ((n - 1) / NB) * NB;
   for (int k0 = last; k0 >= 0; k0 -= NB) {
     const int nb = std::min(NB, n - k0);
-    const int grid = std::max((k0 + 255) / 256, 1);
+    const int grid = std::min(std::max((k0 + 255) / 256, 1), kTriCtas);
     bwd_step_kernel<<<grid, 256, 0, s>>>(L, ldl, Dinv, k0, nb, tmp, v);
     QMLR_LAUNCH_CHECK();
   }
