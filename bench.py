@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
+    ap.add_argument("--factor", default="mixed", choices=["mixed", "fp64"],
+                    help="preconditioner factor: tensor-core trailing updates (mixed) or FP64 throughout")
     return ap.parse_args()
 
 
@@ -203,7 +205,7 @@ def serving_phase(model_args, rates, seconds):
 # ----------------------------------------------------------------------------
 # energy + force training on the 3BPA-shaped workload
 
-def ef_training_phase(pcg_iters, pcg_tol):
+def ef_training_phase(pcg_iters, pcg_tol, factor):
     """Train on 500 conformations with energy and force rows (41 000 x 16384),
     then predict 2000 held-out conformations; stage times by CUDA events."""
     import torch
@@ -226,7 +228,7 @@ def ef_training_phase(pcg_iters, pcg_tol):
         ev[1].record(s)
         G = qmlr.gram(rows, qmlr.GRAM_BF16X6)
         ev[2].record(s)
-        alpha, it, rel = qmlr.gram_solve(G, rows, y, w.lam, max_iter=pcg_iters, tol=pcg_tol)
+        alpha, it, rel = qmlr.gram_solve(G, rows, y, w.lam, max_iter=pcg_iters, tol=pcg_tol, factor=factor)
         ev[3].record(s)
         torch.cuda.synchronize()
         so = qmlr.last_solve
@@ -316,6 +318,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
+    factor = qmlr.FACTOR_MIXED if args.factor == "mixed" else qmlr.FACTOR_FP64
 
     def step(b: pipeline.Batch, yv, precision=qmlr.GRAM_BF16X6, timing=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
@@ -329,7 +332,7 @@ def run_ours(args, rank, world):
         G = qmlr.gram(Z, precision)
         ev[4].record(stream)
         alpha, it, rel = qmlr.gram_solve(G, Z, yv, w.lam, method=qmlr.SOLVE_PCG,
-                                         max_iter=args.pcg_iters, tol=args.pcg_tol)
+                                         max_iter=args.pcg_iters, tol=args.pcg_tol, factor=factor)
         ev[5].record(stream)
         model.set_alpha_device(alpha)
         E, F = model.predict(b.coords, b.elem, b.mol_ptr)
@@ -452,7 +455,8 @@ def run_ours(args, rank, world):
         "config": {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
                    "n_molecules": n_mol, "n_atoms": n_atoms, "n_features": nf, "d": w.d,
                    "n_transform": w.n_transform, "gram": "3-way bf16 split, 6 tcgen05 products, per-K-block FP32 Kahan promotion",
-                   "solve": "fp64 cholesky + pcg (exact fp64 operator)",
+                   "solve": ("mixed-precision cholesky (fp64 panels, tcgen05 trailing updates)"
+                             if args.factor == "mixed" else "fp64 cholesky") + " + pcg (exact fp64 operator)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (rep 5.5 GB, Z 6.6 GB)"},
         "train_s": (st["total"] - st["predict_ef"]) / 1e3,
@@ -469,7 +473,7 @@ def run_ours(args, rank, world):
         "workload_gen_s": gen_s,
     }
     if not args.no_ef and world == 1:
-        line["ef_training"] = ef_training_phase(args.pcg_iters, args.pcg_tol)
+        line["ef_training"] = ef_training_phase(args.pcg_iters, args.pcg_tol, factor)
     if not args.no_serve and world == 1:
         alpha_host = alpha.float().cpu().numpy()
         line["serving"] = serving_phase((p, U, w.signs, w.n_transform, w.b, w.sigma, alpha_host),

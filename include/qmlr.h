@@ -324,12 +324,33 @@ int qmlr_zty(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz, co
  */
 int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_info, void* stream);
 
-/* v <- (L L^T)^{-1} v with the factor from qmlr_cholesky (forward, then backward substitution). */
+/*
+ * Mixed-precision factor A ~= L L^T (same layout and info as qmlr_cholesky),
+ * meant as the preconditioner of an iteration on the exact operator (the
+ * ridge solve below). Right-looking in 256-column panels: each panel is
+ * factorised in FP64; the update of the remaining lower triangle by a panel
+ * runs on the tensor cores from the panel's 3-way BF16 split (products to
+ * ~2^-24 relative, FP32 sums over each 64-deep K block, subtracted from the
+ * FP64 matrix), so L L^T matches A to ~1e-7 of max|A| rather than to FP64
+ * round-off. work: device scratch of qmlr_cholesky_mixed_workspace_bytes(n)
+ * bytes, 256-byte aligned. Synchronous.
+ */
+int64_t qmlr_cholesky_mixed_workspace_bytes(int32_t n);
+int qmlr_cholesky_mixed(double* L, int64_t ldl, int32_t n, void* work, int64_t work_bytes,
+                        int32_t* host_info, void* stream);
+
+/* v <- (L L^T)^{-1} v with a factor from qmlr_cholesky or qmlr_cholesky_mixed
+   (forward, then backward substitution). */
 int qmlr_cholesky_solve(const double* L, int64_t ldl, int32_t n, double* v, void* stream);
 
 enum {
   QMLR_SOLVE_PCG = 0,    /* conjugate gradients on the exact operator, Cholesky-preconditioned */
   QMLR_SOLVE_REFINE = 1  /* classical iterative refinement with the Cholesky factor */
+};
+
+enum {
+  QMLR_FACTOR_FP64 = 0,  /* preconditioner factor: qmlr_cholesky (FP64 throughout) */
+  QMLR_FACTOR_MIXED = 1  /* preconditioner factor: qmlr_cholesky_mixed (tensor-core updates) */
 };
 
 typedef struct qmlr_solve_opts {
@@ -344,6 +365,7 @@ typedef struct qmlr_solve_opts {
   double shift_used;   /* out: the shift of the factor that was used */
   float factor_ms;     /* out: device time of assembly + Cholesky factorisation (CUDA events) */
   float refine_ms;     /* out: device time of the first solve and the refinement */
+  int32_t factor;      /* QMLR_FACTOR_FP64 or QMLR_FACTOR_MIXED */
 } qmlr_solve_opts;
 
 /* Device workspace bytes of qmlr_gram_solve. */
@@ -356,8 +378,9 @@ int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features);
  *          A v = Z^T (Z v) + lambda v, evaluated in FP64)
  *   y      double [n_rows] targets
  *   alpha  double [n_features] out
- * Steps: c = Z^T y; FP64 Cholesky of G + (lambda + shift) I; alpha = factor
- * solve of c; then up to max_iter refinement steps against the exact operator.
+ * Steps: c = Z^T y; Cholesky factor of G + (lambda + shift) I (FP64 or mixed
+ * precision, opts->factor); alpha = factor solve of c; then up to max_iter
+ * refinement steps against the exact operator, which alone sets the residual.
  * QMLR_ENOTCONV: tolerance not reached (alpha and opts->rel_resid still written).
  * QMLR_EINVAL with a message when the factorisation still meets a non-positive
  * pivot after the shift escalation.

@@ -268,14 +268,17 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint8_t* sp = smem + st * STAGE_BYTES;
       const uint32_t d = tmem + buf * BN;
+      // smallest split products first, S0'S0 last: every accumulator add
+      // truncates relative to the running sum, so the many small terms are
+      // added while that sum is still small (4 of the 4 * NP adds are large).
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const int off = kk * 32;   // 16 bf16 along K inside the 128-byte swizzled row
+      for (int q = C::NP - 1; q >= 0; --q) {
 #pragma unroll
-        for (int q = 0; q < C::NP; ++q) {
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const int off = kk * 32;   // 16 bf16 along K inside the 128-byte swizzled row
           const uint8_t* a = sp + pa[q] * A_BYTES + off;
           const uint8_t* b = sp + S * A_BYTES + pb[q] * B_BYTES + off;
-          mma_bf16(d, smem_desc(a), smem_desc(b), idesc, (kk > 0 || q > 0) ? 1u : 0u);
+          mma_bf16(d, smem_desc(a), smem_desc(b), idesc, (kk > 0 || q < C::NP - 1) ? 1u : 0u);
         }
       }
       mma_commit(&empty[st]);   // frees the smem stage once these MMAs have read it
@@ -349,6 +352,181 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
   }
 }
 
+// ---------------------------------------------------------------------------
+// Trailing update of the mixed-precision Cholesky factor on the tensor cores:
+//   A[i][j] -= sum_k P[i][k] P[j][k],  i >= j,  P = the factored 256-column
+// panel below its diagonal block (FP64), given as its 3-way BF16 split
+// [3][m][256] (K-major). Each CTA takes one 128 x 128 lower tile, runs the six
+// split products per 64-deep K block into TMEM, promotes every K block into
+// FP32 register sums (four blocks: K = 256), and subtracts the result from the
+// FP64 trailing matrix. The epilogue transposes each drain warp's 32 x 32 block
+// through its own slice of the (then idle) stage memory so that the FP64
+// read-modify-write runs along rows.
+constexpr int kPanelK = 256;
+
+__global__ void __launch_bounds__(kThreads, 1)
+syrk_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+               const __grid_constant__ CUtensorMap map2, int m, double* __restrict__ A, long lda, int* err) {
+  using C = Cfg<3>;
+  constexpr int BN = C::BN, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES, NST = C::STAGES_N;
+  constexpr int k_blocks = kPanelK / BK;
+  const CUtensorMap* maps[3] = {&map0, &map1, &map2};
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES);
+  uint64_t* empty = full + NST;
+  uint64_t* accf = empty + NST;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* never_abort = abort + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // lower-triangle tile (bi >= bj) of this CTA
+  const int t = blockIdx.x;
+  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while (bi * (bi + 1) / 2 > t) --bi;
+  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+  const int bj = t - bi * (bi + 1) / 2;
+  const int i0 = bi * BM, j0 = bj * BN;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NST; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], kDrainWarps);
+    }
+    *abort = 0;
+    *never_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  int last_round[NST];
+#pragma unroll
+  for (int q = 0; q < NST; ++q) last_round[q] = -1;
+
+  if (warp == kDrainWarps && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < k_blocks; ++kb) {
+      const int st = kb % NST;
+      const uint32_t round = kb / NST;
+      if (kb >= NST && !mbar_wait(&empty[st], (round - 1) & 1, abort)) {
+        record_device_error(err, DEV_TIMEOUT);
+        *abort = 1;
+        break;
+      }
+      uint8_t* sp = smem + st * STAGE_BYTES;
+      mbar_expect_tx(&full[st], STAGE_BYTES);
+      const int k = kb * BK;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        tma_load_2d(sp + q * A_BYTES, maps[q], &full[st], k, i0);
+        tma_load_2d(sp + 3 * A_BYTES + q * B_BYTES, maps[q], &full[st], k, j0);
+      }
+      last_round[st] = (int)round;
+    }
+  } else if (warp == kDrainWarps + 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kb = 0; kb < k_blocks; ++kb) {
+      const int st = kb % NST;
+      const uint32_t round = kb / NST;
+      const int buf = kb & 1;
+      const uint32_t use = kb >> 1;
+      if (!mbar_wait(&full[st], round & 1, abort) ||
+          (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1, abort))) {
+        record_device_error(err, DEV_TIMEOUT);
+        *abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint8_t* sp = smem + st * STAGE_BYTES;
+      const uint32_t d = tmem + buf * BN;
+#pragma unroll
+      for (int q = C::NP - 1; q >= 0; --q) {   // smallest products first (see the Gram)
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const int off = kk * 32;
+          const uint8_t* a = sp + kProdA[q] * A_BYTES + off;
+          const uint8_t* b = sp + 3 * A_BYTES + kProdB[q] * B_BYTES + off;
+          mma_bf16(d, smem_desc(a), smem_desc(b), idesc, (kk > 0 || q < C::NP - 1) ? 1u : 0u);
+        }
+      }
+      mma_commit(&empty[st]);
+      mma_commit(&accf[buf]);
+    }
+  } else if (warp < kDrainWarps) {
+    // ---------------- drain and FP64 subtraction
+    const int quarter = warp & 3, half = warp >> 2;
+    float sum[kDrainCols];
+#pragma unroll
+    for (int k = 0; k < kDrainCols; ++k) sum[k] = 0.f;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    bool done = true;
+    for (int kb = 0; kb < k_blocks; ++kb) {
+      const int buf = kb & 1;
+      const uint32_t use = kb >> 1;
+      const bool ok = mbar_wait(&accf[buf], use & 1, abort);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) {
+          record_device_error(err, DEV_TIMEOUT);
+          *abort = 1;
+        }
+        done = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int c4 = 0; c4 < kDrainCols / 16; ++c4) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + buf * BN + half * kDrainCols + c4 * 16, v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sum[c4 * 16 + k] += v[k];
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+    }
+    // This warp saw the last K block's accumulator, so every MMA (and every
+    // TMA copy they consumed) has completed and the stage memory is idle.
+    if (done && (bi > bj || half <= quarter)) {
+      float* W = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+#pragma unroll
+      for (int k = 0; k < kDrainCols; ++k) W[lane * 33 + k] = sum[k];
+      __syncwarp();
+      const int j = j0 + half * 32 + lane;
+      for (int rr = 0; rr < 32; ++rr) {
+        const int i = i0 + quarter * 32 + rr;
+        if (i < m && j <= i) A[(long)i * lda + j] -= (double)W[rr * 33 + lane];
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (*abort) {
+    if (warp == kDrainWarps && lane == 0)
+      for (int q = 0; q < NST; ++q)
+        if (last_round[q] >= 0) mbar_wait(&full[q], (uint32_t)last_round[q] & 1, never_abort);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+  }
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -403,6 +581,27 @@ static int launch_split(const uint16_t* zt, long k_pad, int n_features, float* G
   return QMLR_OK;
 }
 
+static int launch_syrk(const uint16_t* parts, long part_elems, int m, double* A, long lda, cudaStream_t s) {
+  using C = Cfg<3>;
+  const int T = (m + BM - 1) / BM;
+  QMLR_REQUIRE(part_elems >= (long)T * BM * kPanelK, "panel operand smaller than its padded rows");
+  CUtensorMap mp[3];
+  for (int q = 0; q < 3; ++q) {   // all T * 128 rows are in the buffer (zero beyond m)
+    int rc = make_map(&mp[q], parts + (size_t)q * part_elems, kPanelK, T * BM);
+    if (rc) return rc;
+  }
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       C::SMEM_BYTES));
+    attr = true;
+  }
+  syrk_tc_kernel<<<T * (T + 1) / 2, kThreads, C::SMEM_BYTES, s>>>(mp[0], mp[1], mp[2], m, A, lda,
+                                                                  device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
 }  // namespace tc
 
 int gram_split_tc(int n_split, const uint16_t* zt, long k_pad, int n_features, float* G, cudaStream_t s) {
@@ -412,6 +611,11 @@ int gram_split_tc(int n_split, const uint16_t* zt, long k_pad, int n_features, f
   }
   return n_split == 2 ? tc::launch_split<2>(zt, k_pad, n_features, G, s)
                       : tc::launch_split<3>(zt, k_pad, n_features, G, s);
+}
+
+int syrk_tc(const uint16_t* parts, long part_elems, int m, double* A, long lda, cudaStream_t s) {
+  if (m <= 0) return QMLR_OK;
+  return tc::launch_syrk(parts, part_elems, m, A, lda, s);
 }
 
 }  // namespace qmlr

@@ -12,9 +12,14 @@
 // exact FP64 normal equations.
 #include "common.cuh"
 
+#include <cuda_bf16.h>
+
 namespace qmlr {
 
 constexpr int NB = 64;
+
+// tensor-core trailing update (gram_tc.cu)
+int syrk_tc(const uint16_t* parts, long part_elems, int m, double* A, long lda, cudaStream_t s);
 
 // A = G + (lambda + shift) I in FP64, lower triangle (G symmetric fp32 [n][n]).
 __global__ void assemble_kernel(const float* __restrict__ G, int n, double diag,
@@ -97,20 +102,30 @@ trsm_panel_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
   }
 }
 
-// Trailing update of the lower block tiles: A[I][J] -= L[I][k] L[J][k]^T, I >= J > k.
+// Trailing update of the lower block tiles: A[I][J] -= L[I][k] L[J][k]^T, I >= J > k,
+// for the first `cblocks` trailing block columns J (all of them when cblocks >= T).
 __global__ void __launch_bounds__(256)
-syrk_update_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
+syrk_update_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n, int cblocks) {
   extern __shared__ double dsm[];
   double (*li)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm);
   double (*lj)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm + NB * (NB + 1));
   const int t0 = (k0 + nb) / NB;          // first trailing block
   const int T = (n + NB - 1) / NB - t0;   // trailing blocks
-  int t = blockIdx.x, bi = 0;
-  while (t > bi) {                        // lower-triangular (bi >= bj) enumeration
-    t -= bi + 1;
-    ++bi;
+  int t = blockIdx.x, bi = 0, bj = 0;
+  if (cblocks >= T) {
+    while (t > bi) {                      // lower-triangular (bi >= bj) enumeration, by rows
+      t -= bi + 1;
+      ++bi;
+    }
+    bj = t;
+  } else {
+    while (bj < cblocks && t >= T - bj) { // limited to cblocks columns, by columns
+      t -= T - bj;
+      ++bj;
+    }
+    if (bj >= cblocks) return;
+    bi = bj + t;
   }
-  const int bj = t;
   if (bi >= T) return;
   const int i0 = (t0 + bi) * NB, j0 = (t0 + bj) * NB;
   const int tid = threadIdx.x;
@@ -144,6 +159,28 @@ syrk_update_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
       if (j >= n || j > i) continue;
       L[(long)i * ldl + j] -= acc[u][v];
     }
+  }
+}
+
+// Panel operand of the tensor-core trailing update: rows [r0, r0 + m) and columns
+// [k0, k0 + 256) of the factor, split into three BF16 parts
+// S0 = bf16(x), S1 = bf16(x - S0), S2 = bf16(x - S0 - S1) ([3][m_pad][256],
+// K-major); rows m..m_pad-1 are zero.
+constexpr int kTcPanel = 256;
+
+__global__ void __launch_bounds__(256)
+panel_split_kernel(const double* __restrict__ L, long ldl, int r0, int k0, int m, int m_pad,
+                   __nv_bfloat16* __restrict__ parts) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)m_pad * kTcPanel;
+  if (idx >= total) return;
+  const int r = (int)(idx / kTcPanel), c = (int)(idx % kTcPanel);
+  double x = r < m ? L[(long)(r0 + r) * ldl + k0 + c] : 0.0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    parts[q * total + idx] = h;
+    x -= (double)__bfloat162float(h);
   }
 }
 
@@ -396,8 +433,59 @@ static int cholesky(double* L, long ldl, int n, cudaStream_t s, int* info) {
     trsm_panel_kernel<<<(rows + 63) / 64, 64, kPanelSmem, s>>>(L, ldl, k0, nb, n);
     QMLR_LAUNCH_CHECK();
     const int T = (rows + NB - 1) / NB;
-    syrk_update_kernel<<<T * (T + 1) / 2, 256, kPanelSmem, s>>>(L, ldl, k0, nb, n);
+    syrk_update_kernel<<<T * (T + 1) / 2, 256, kPanelSmem, s>>>(L, ldl, k0, nb, n, T);
     QMLR_LAUNCH_CHECK();
+  }
+  return QMLR_OK;
+}
+
+static size_t tc_parts_elems(int n) {
+  const long m_pad = ((long)std::max(n, 1) + 127) / 128 * 128;
+  return (size_t)3 * m_pad * kTcPanel;
+}
+
+// Mixed-precision factor (the preconditioner of the ridge solve): right-looking
+// with 256-column panels. Each panel is factorised in FP64 with the 64-block
+// kernels above, its trailing updates limited to the panel's own columns; the
+// update of the remaining matrix by the panel runs on the tensor cores from the
+// panel's 3-way BF16 split (products to ~2^-24 relative, FP32 sums per 64-deep
+// K block, subtracted from the FP64 matrix).
+static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts, cudaStream_t s, int* info) {
+  int* err = device_error_ptr();
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPanelSmem));
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPanelSmem));
+    attr = true;
+  }
+  for (int k0 = 0; k0 < n; k0 += kTcPanel) {
+    const int w = std::min(kTcPanel, n - k0);
+    for (int c0 = k0; c0 < k0 + w; c0 += NB) {
+      const int nb = std::min(NB, n - c0);
+      potrf_diag_kernel<<<1, 256, 0, s>>>(L, ldl, c0, nb, err, info);
+      QMLR_LAUNCH_CHECK();
+      const int rows = n - c0 - nb;
+      if (rows <= 0) break;
+      trsm_panel_kernel<<<(rows + 63) / 64, 64, kPanelSmem, s>>>(L, ldl, c0, nb, n);
+      QMLR_LAUNCH_CHECK();
+      const int cblocks = (k0 + w - (c0 + nb) + NB - 1) / NB;   // panel columns still to update
+      if (cblocks > 0) {
+        const int T = (rows + NB - 1) / NB;
+        const int tiles = cblocks * T - cblocks * (cblocks - 1) / 2;
+        syrk_update_kernel<<<tiles, 256, kPanelSmem, s>>>(L, ldl, c0, nb, n, cblocks);
+        QMLR_LAUNCH_CHECK();
+      }
+    }
+    const int r0 = k0 + w, m = n - r0;
+    if (m <= 0) break;
+    const int m_pad = (m + 127) / 128 * 128;
+    const long total = (long)m_pad * kTcPanel;
+    panel_split_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(L, ldl, r0, k0, m, m_pad, parts);
+    QMLR_LAUNCH_CHECK();
+    int rc = syrk_tc(reinterpret_cast<const uint16_t*>(parts), total, m, L + (long)r0 * ldl + r0, ldl, s);
+    if (rc) return rc;
   }
   return QMLR_OK;
 }
@@ -461,6 +549,7 @@ extern "C" int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features
          + parts * n * 8           // partial sums of Z^T t
          + std::max<int64_t>(n_rows, 1) * 8   // t = Z p
          + 6 * n * 8               // c, r, z, p, q, tmp
+         + (int64_t)tc_parts_elems((int)n) * 2   // split panel of the mixed-precision factor
          + 8 * 8 + 4096;           // scalars + alignment
 }
 
@@ -471,6 +560,31 @@ extern "C" int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_in
   QMLR_CUDA_TRY(cudaMallocAsync(&info, sizeof(int), s));
   QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
   int rc = cholesky(L, ldl, n, s, info);
+  int h = 0;
+  if (rc == QMLR_OK) {
+    QMLR_CUDA_TRY(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QMLR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  cudaFreeAsync(info, s);
+  if (host_info) *host_info = h;
+  return rc;
+}
+
+extern "C" int64_t qmlr_cholesky_mixed_workspace_bytes(int32_t n) {
+  if (n < 1) return 0;
+  return (int64_t)tc_parts_elems(n) * 2 + 256;
+}
+
+extern "C" int qmlr_cholesky_mixed(double* L, int64_t ldl, int32_t n, void* work, int64_t work_bytes,
+                                   int32_t* host_info, void* stream) {
+  QMLR_REQUIRE(L && n >= 1 && ldl >= n, "bad factor arguments");
+  QMLR_REQUIRE(work && work_bytes >= qmlr_cholesky_mixed_workspace_bytes(n), "workspace too small");
+  QMLR_REQUIRE((reinterpret_cast<uintptr_t>(work) & 255) == 0, "workspace must be 256-byte aligned");
+  cudaStream_t s = as_stream(stream);
+  int* info = nullptr;
+  QMLR_CUDA_TRY(cudaMallocAsync(&info, sizeof(int), s));
+  QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+  int rc = cholesky_mixed(L, ldl, n, static_cast<__nv_bfloat16*>(work), s, info);
   int h = 0;
   if (rc == QMLR_OK) {
     QMLR_CUDA_TRY(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -510,6 +624,8 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
                "workspace too small");
   QMLR_REQUIRE(opts->method == QMLR_SOLVE_PCG || opts->method == QMLR_SOLVE_REFINE,
                "unknown solve method %d", opts->method);
+  QMLR_REQUIRE(opts->factor == QMLR_FACTOR_FP64 || opts->factor == QMLR_FACTOR_MIXED,
+               "unknown factor kind %d", opts->factor);
   cudaStream_t s = as_stream(stream);
   const int n = n_features;
   SolveCtx c;
@@ -522,7 +638,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   c.s = s;
   c.parts = (int)std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
   char* p = static_cast<char*>(work);
-  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc, *vdinv, *vtri;
+  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc, *vdinv, *vtri, *vsplit;
   const int nblk = (n + NB - 1) / NB;
   carve(p, &vL, (size_t)n * n * 8);
   carve(p, &vdinv, (size_t)nblk * NB * NB * 8);
@@ -536,6 +652,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   carve(p, &vq, (size_t)n * 8);
   carve(p, &vtmp, (size_t)n * 8);
   carve(p, &vsc, 8 * 8);
+  carve(p, &vsplit, tc_parts_elems(n) * 2);
   c.L = static_cast<double*>(vL);
   c.part = static_cast<double*>(vpart);
   c.t = static_cast<double*>(vt);
@@ -584,7 +701,9 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
     assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(G, n, lambda + shift, c.L, c.ldl);
     QMLR_LAUNCH_CHECK();
     QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
-    int rc = cholesky(c.L, c.ldl, n, s, info);
+    int rc = opts->factor == QMLR_FACTOR_MIXED
+                 ? cholesky_mixed(c.L, c.ldl, n, static_cast<__nv_bfloat16*>(vsplit), s, info)
+                 : cholesky(c.L, c.ldl, n, s, info);
     if (rc) return rc;
     QMLR_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
     QMLR_CUDA_TRY(cudaStreamSynchronize(s));

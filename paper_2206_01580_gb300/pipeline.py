@@ -78,10 +78,12 @@ def feature_matrix(batch: Batch, spec: FeatureSpec, U, rep=None, perm=None, offs
 
 
 def solve(Z, y, lam: float, precision: int = qmlr.GRAM_BF16X6, method: int = qmlr.SOLVE_PCG,
-          max_iter: int = 50, tol: float = 1e-10, shift: float = -2.0 ** -14):
+          max_iter: int = 50, tol: float = 1e-10, shift: float = -2.0 ** -14,
+          factor: int = qmlr.FACTOR_MIXED):
     """alpha (float64) of (Z^T Z + lam I) alpha = Z^T y; returns (alpha, iterations, rel. residual)."""
     G = qmlr.gram(Z, precision)
-    return qmlr.gram_solve(G, Z, y, lam, method=method, max_iter=max_iter, tol=tol, shift=shift)
+    return qmlr.gram_solve(G, Z, y, lam, method=method, max_iter=max_iter, tol=tol, shift=shift,
+                           factor=factor)
 
 
 def train_energy(batch: Batch, energies, spec: FeatureSpec, lam: float, U=None,

@@ -49,13 +49,15 @@ class ServeStats(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("shift", C.c_double), ("iters_done", C.c_int32), ("rel_resid", C.c_double),
-                ("shift_used", C.c_double), ("factor_ms", C.c_float), ("refine_ms", C.c_float)]
+                ("shift_used", C.c_double), ("factor_ms", C.c_float), ("refine_ms", C.c_float),
+                ("factor", C.c_int32)]
 
 
 _lib = None
 P, I32, I64, D, VP = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_void_p
 GRAM_FP32, GRAM_BF16X3, GRAM_BF16X6 = 0, 1, 2
 SOLVE_PCG, SOLVE_REFINE = 0, 1
+FACTOR_FP64, FACTOR_MIXED = 0, 1
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -84,6 +86,8 @@ _SIGS = {
     "qmlr_zty_workspace_bytes": (C.c_int64, [I64, I32]),
     "qmlr_zty": (C.c_int, [P, I64, I32, I64, P, P, P, I64, VP]),
     "qmlr_cholesky": (C.c_int, [P, I64, I32, C.POINTER(C.c_int32), VP]),
+    "qmlr_cholesky_mixed_workspace_bytes": (C.c_int64, [I32]),
+    "qmlr_cholesky_mixed": (C.c_int, [P, I64, I32, P, I64, C.POINTER(C.c_int32), VP]),
     "qmlr_cholesky_solve": (C.c_int, [P, I64, I32, P, VP]),
     "qmlr_solve_workspace_bytes": (C.c_int64, [I64, I32]),
     "qmlr_gram_solve": (C.c_int, [P, P, I64, I32, I64, P, D, C.POINTER(SolveOpts), P, P, I64, VP]),
@@ -373,6 +377,17 @@ def cholesky(A):
     return L, info.value
 
 
+def cholesky_mixed(A):
+    """Mixed-precision lower factor (FP64 panels, tensor-core trailing updates)."""
+    L = _dev(A, torch.float64).clone()
+    n = L.shape[0]
+    wb = lib().qmlr_cholesky_mixed_workspace_bytes(n)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
+    info = C.c_int32(0)
+    _check(lib().qmlr_cholesky_mixed(_ptr(L), n, n, _ptr(work), wb, C.byref(info), _stream()))
+    return L, info.value
+
+
 def cholesky_solve(L, v):
     v = _dev(v, torch.float64).clone()
     n = L.shape[0]
@@ -381,9 +396,10 @@ def cholesky_solve(L, v):
 
 
 def gram_solve(G, Z, y, lam: float, method: int = SOLVE_PCG, max_iter: int = 50, tol: float = 1e-10,
-               shift: float = -2.0 ** -14, raise_on_notconv: bool = False):
+               shift: float = -2.0 ** -14, raise_on_notconv: bool = False, factor: int = FACTOR_MIXED):
     """alpha for (Z^T Z + lam I) alpha = Z^T y with a factor of G + (lam + shift) I
-    (shift < 0: relative to max diag G). Returns (alpha, iterations, relative residual)."""
+    (shift < 0: relative to max diag G; factor FACTOR_FP64 or FACTOR_MIXED).
+    Returns (alpha, iterations, relative residual)."""
     G = _dev(G, torch.float32)
     Z = _dev(Z, torch.float32)
     y = _dev(y, torch.float64)
@@ -391,7 +407,7 @@ def gram_solve(G, Z, y, lam: float, method: int = SOLVE_PCG, max_iter: int = 50,
     alpha = torch.empty(nf, device="cuda", dtype=torch.float64)
     wb = lib().qmlr_solve_workspace_bytes(n_rows, nf)
     work = torch.empty(wb, device="cuda", dtype=torch.uint8)
-    opts = SolveOpts(method, max_iter, tol, shift, 0, 0.0, 0.0, 0.0, 0.0)
+    opts = SolveOpts(method, max_iter, tol, shift, 0, 0.0, 0.0, 0.0, 0.0, factor)
     rc = lib().qmlr_gram_solve(_ptr(G), _ptr(Z), n_rows, nf, Z.stride(0), _ptr(y), float(lam),
                                C.byref(opts), _ptr(alpha), _ptr(work), wb, _stream())
     global last_solve

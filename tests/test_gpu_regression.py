@@ -103,6 +103,42 @@ def test_cholesky_matches_lapack(q, n):
     np.testing.assert_allclose(x, scipy.linalg.cho_solve((ref, True), v), rtol=1e-9)
 
 
+@pytest.mark.parametrize("n", [1, 200, 256, 300, 600, 1000, 1333])
+def test_mixed_cholesky_reconstructs_matrix(q, n):
+    """Mixed factor: panels of 256 columns in FP64, tensor-core trailing updates
+    from 3-way BF16 splits. L L^T reproduces A to ~1e-7 of max|A| (FP64
+    round-off while n <= 256, where no tensor-core update runs), and its
+    triangular solves match the FP64 factor's to the same relative order.
+    The bound comes from the tensor cores' truncating accumulator: per 64-deep
+    K block four large adds of ~2^-23 relative each (small split products are
+    added first), over the panels that touch an element."""
+    rng = np.random.default_rng(100 + n)
+    X = rng.normal(size=(n + 5, n))
+    A = X.T @ X + 0.1 * np.eye(n)
+    L, info = q.cholesky_mixed(A)
+    assert info == 0
+    assert q.device_status() == 0
+    L = L.cpu().numpy()
+    assert np.all(np.triu(L, 1) == np.triu(A, 1))     # strict upper triangle untouched
+    L = np.tril(L)
+    err = np.max(np.abs(L @ L.T - A)) / np.max(np.abs(A))
+    assert err <= (1e-13 if n <= 256 else 5e-7), err
+    v = rng.normal(size=n)
+    x = q.cholesky_solve(torch.as_tensor(L).cuda(), v).cpu().numpy()
+    ref = scipy.linalg.cho_solve((np.linalg.cholesky(A), True), v)
+    cond_bound = 1e-10 if n <= 256 else 1e-7 * np.linalg.cond(A)
+    assert np.max(np.abs(x - ref)) <= cond_bound * np.max(np.abs(ref))
+
+
+def test_mixed_cholesky_reports_indefinite_matrix(q):
+    A = np.eye(700)
+    A[400, 400] = -1.0          # met after two tensor-core trailing updates
+    _, info = q.cholesky_mixed(A)
+    assert info == 401
+    assert q.device_status() == 5
+    assert q.device_status() == 0
+
+
 def test_cholesky_reports_indefinite_matrix(q):
     A = np.eye(80)
     A[50, 50] = -1.0
@@ -112,19 +148,34 @@ def test_cholesky_reports_indefinite_matrix(q):
     assert q.device_status() == 0
 
 
+@pytest.mark.parametrize("factor", [0, 1])
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1, 2])
-def test_ridge_solve_matches_oracle(q, method, precision):
-    Z = _features(1500, 256, seed=9)
+def test_ridge_solve_matches_oracle(q, method, precision, factor):
+    Z = _features(1500, 640, seed=9)
     y = np.random.default_rng(10).normal(size=1500)
     lam = 1e-6
     alpha_ref, _ = o_reg.ridge_solve(Z.astype(np.float64), y, lam, refine=2)
     G = q.gram(Z, precision)
-    alpha, it, rel = q.gram_solve(G, Z, y, lam, method=method, max_iter=30, tol=1e-11)
+    alpha, it, rel = q.gram_solve(G, Z, y, lam, method=method, max_iter=30, tol=1e-11, factor=factor)
     assert rel <= 1e-11, (it, rel)
     alpha = alpha.cpu().numpy()
     pz, pr = Z.astype(np.float64) @ alpha, Z.astype(np.float64) @ alpha_ref
     assert np.max(np.abs(pz - pr)) <= 1e-6 * np.max(np.abs(pr))
+
+
+def test_mixed_factor_preconditions_as_well_as_fp64(q):
+    """On a Gram large enough for several tensor-core panel updates the mixed
+    factor needs at most two more PCG iterations than the FP64 one."""
+    Z = _features(3000, 1024, seed=13)
+    y = np.random.default_rng(14).normal(size=3000)
+    G = q.gram(Z, 2)
+    its = {}
+    for f in (q.FACTOR_FP64, q.FACTOR_MIXED):
+        alpha, it, rel = q.gram_solve(G, Z, y, 1e-6, max_iter=60, tol=1e-10, factor=f)
+        assert rel <= 1e-10
+        its[f] = it
+    assert its[q.FACTOR_MIXED] <= its[q.FACTOR_FP64] + 2, its
 
 
 def test_ridge_solve_underdetermined_with_shift(q):
@@ -136,7 +187,8 @@ def test_ridge_solve_underdetermined_with_shift(q):
     lam = 1e-6
     alpha_ref, _ = o_reg.ridge_solve(Z.astype(np.float64), y, lam, refine=2)
     G = q.gram(Z, 2)
-    alpha, it, rel = q.gram_solve(G, Z, y, lam, method=0, max_iter=200, tol=1e-10, shift=1e-4)
+    alpha, it, rel = q.gram_solve(G, Z, y, lam, method=0, max_iter=200, tol=1e-10, shift=1e-4,
+                                  factor=q.FACTOR_FP64)
     assert rel <= 1e-10, (it, rel)
     pz = Z.astype(np.float64) @ alpha.cpu().numpy()
     pr = Z.astype(np.float64) @ alpha_ref
