@@ -368,6 +368,20 @@ typedef struct qmlr_solve_opts {
   int32_t factor;      /* QMLR_FACTOR_FP64 or QMLR_FACTOR_MIXED */
 } qmlr_solve_opts;
 
+/*
+ * q = Z^T (Z p) + lambda p: the exact operator of the ridge solve below (the
+ * RFF section's normal-equation matrix applied to a vector without forming
+ * it). Z float [n_rows][ldz] (row-major), p and q double [n_features] (device).
+ * Arithmetic: FP32 products split exactly by FMA and summed in float pairs
+ * (two-sum) folded into FP64 every 128 terms, i.e. about twice FP32's
+ * precision (relative error ~1e-12 of the sum of |terms| on feature data);
+ * fixed summation order, so repeated calls agree bitwise. work: device scratch
+ * of qmlr_normal_apply_workspace_bytes bytes, 256-byte aligned. Asynchronous.
+ */
+int64_t qmlr_normal_apply_workspace_bytes(int64_t n_rows, int32_t n_features);
+int qmlr_normal_apply(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz, double lambda,
+                      const double* p, double* q, void* work, int64_t work_bytes, void* stream);
+
 /* Device workspace bytes of qmlr_gram_solve. */
 int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features);
 
@@ -375,7 +389,7 @@ int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features);
  * Solve (Z^T Z + lambda I) alpha = Z^T y (synchronous; returns once alpha is final).
  *   G      float [n_features]^2 symmetric Gram (any precision form of qmlr_gram)
  *   Z      float [n_rows][ldz] the stored feature rows (the exact operator is
- *          A v = Z^T (Z v) + lambda v, evaluated in FP64)
+ *          A v = Z^T (Z v) + lambda v, evaluated as in qmlr_normal_apply)
  *   y      double [n_rows] targets
  *   alpha  double [n_features] out
  * Steps: c = Z^T y; Cholesky factor of G + (lambda + shift) I (FP64 or mixed

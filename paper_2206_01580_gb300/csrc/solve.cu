@@ -236,8 +236,10 @@ __device__ __forceinline__ void block_matvec(const double* __restrict__ D, const
 
 constexpr int kTriCtas = 304;   // 2 CTAs per SM on 152 SMs
 
-// forward step k: y_k = Dinv_k r_k; r[i] -= L[i][k0:k0+nb] y_k for rows i >= k0 + nb
-// (warps grid-stride over rows, lanes over the 64 columns)
+// forward step k: y_k = Dinv_k r_k; r[i] -= L[i][k0:k0+nb] y_k for rows i >= k0 + nb.
+// Eight lanes share a row (lane j reads columns j, j+8, ..., j+56: 64 contiguous
+// bytes per load instruction and row) and a warp takes 8 rows per pass, so
+// every lane has 16 loads in flight; the 8 partial sums meet by shuffles.
 __global__ void __launch_bounds__(256)
 fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
                 int n, double* __restrict__ r, double* __restrict__ y) {
@@ -248,89 +250,182 @@ fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict
   block_matvec(Dinv + (long)(k0 / NB) * NB * NB, rk, xk, false);
   __syncthreads();
   if (blockIdx.x == 0 && tid < nb) y[k0 + tid] = xk[tid];
-  const int lane = tid & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  const double x0 = lane < nb ? xk[lane] : 0.0, x1 = lane + 32 < nb ? xk[lane + 32] : 0.0;
-  for (int row = k0 + nb + blockIdx.x * (blockDim.x >> 5) + (tid >> 5); row < n; row += warps) {
-    const double* Lr = L + (long)row * ldl + k0;
-    double sum = 0.0;
-    if (lane < nb) sum = Lr[lane] * x0;
-    if (lane + 32 < nb) sum = fma(Lr[lane + 32], x1, sum);
+  const int lane = tid & 31, sub = lane & 7, rg = lane >> 3;
+  double x[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) r[row] -= sum;
+  for (int m = 0; m < 8; ++m) x[m] = (8 * m + sub < nb) ? xk[8 * m + sub] : 0.0;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  const int base = k0 + nb;
+  for (int row0 = base + (blockIdx.x * (blockDim.x >> 5) + (tid >> 5)) * 8; row0 < n; row0 += warps * 8) {
+    double sum[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = row0 + 4 * h + rg;
+      sum[h] = 0.0;
+      if (row < n) {
+        const double* Lr = L + (long)row * ldl + k0 + sub;
+        double v[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = (8 * m + sub < nb) ? __ldg(Lr + 8 * m) : 0.0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) sum[h] = fma(v[m], x[m], sum[h]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) sum[h] += __shfl_xor_sync(0xffffffffu, sum[h], o);
+      const int row = row0 + 4 * h + rg;
+      if (sub == 0 && row < n) r[row] -= sum[h];
+    }
   }
 }
 
-// backward step k: x_k = Dinv_k^T y_k; y[c] -= sum_r L[k0+r][c] x_k[r] for columns c < k0
-// (threads grid-stride over columns)
+// backward step k: x_k = Dinv_k^T y_k; y[c] -= sum_r L[k0+r][c] x_k[r] for columns c < k0.
+// A CTA takes 64 columns; its four 64-thread groups take 16 of the block's rows
+// each (coalesced 512-byte row segments) and their partial sums are added in
+// a fixed order through shared memory.
 __global__ void __launch_bounds__(256)
 bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
                 double* __restrict__ y, double* __restrict__ x) {
-  __shared__ double yk[NB], xk[NB];
+  __shared__ double yk[NB], xk[NB], part[4][NB];
   const int tid = threadIdx.x;
   if (tid < NB) yk[tid] = tid < nb ? y[k0 + tid] : 0.0;
   __syncthreads();
   block_matvec(Dinv + (long)(k0 / NB) * NB * NB, yk, xk, true);
   __syncthreads();
   if (blockIdx.x == 0 && tid < nb) x[k0 + tid] = xk[tid];
-  for (int c = blockIdx.x * blockDim.x + tid; c < k0; c += gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int rr = 0;
-    for (; rr + 4 <= nb; rr += 4) {
-      s0 = fma(L[(long)(k0 + rr) * ldl + c], xk[rr], s0);
-      s1 = fma(L[(long)(k0 + rr + 1) * ldl + c], xk[rr + 1], s1);
-      s2 = fma(L[(long)(k0 + rr + 2) * ldl + c], xk[rr + 2], s2);
-      s3 = fma(L[(long)(k0 + rr + 3) * ldl + c], xk[rr + 3], s3);
+  const int cg = tid & 63, rg = tid >> 6;
+  for (int c0 = blockIdx.x * 64; c0 < k0; c0 += gridDim.x * 64) {
+    const int c = c0 + cg;
+    double v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int rr = rg * 16 + u;
+      v[u] = (rr < nb && c < k0) ? __ldg(L + (long)(k0 + rr) * ldl + c) : 0.0;
     }
-    for (; rr < nb; ++rr) s0 = fma(L[(long)(k0 + rr) * ldl + c], xk[rr], s0);
-    y[c] -= (s0 + s1) + (s2 + s3);
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) s = fma(v[u], xk[rg * 16 + u], s);
+    part[rg][cg] = s;
+    __syncthreads();
+    if (rg == 0 && c < k0) y[c] -= (part[0][cg] + part[1][cg]) + (part[2][cg] + part[3][cg]);
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// exact operator pieces: t = Z p (rows), q = Z^T t + lambda p (features), FP64 arithmetic
+// exact operator pieces: t = Z p (rows), q = Z^T t + lambda p (features).
+//
+// Z is FP32; p and t are FP64 vectors, carried as float pairs vh + vl with
+// vh = fl32(v), vl = fl32(v - vh). Each product z * vh is split exactly into
+// its rounded value and its error by one FMA (Dekker's product); the rounded
+// products are summed by Knuth's two-sum into a float pair (sum, compensation)
+// that also collects the product errors and z * vl (which is ~2^-24 of the
+// product), and every kFold terms the pair is folded into an FP64
+// accumulator. The sums are those of about twice FP32's precision (error of
+// order kFold^2 2^-48 of the sum of |terms| per fold at worst) at FP32
+// instruction throughput: in FP64 arithmetic the GB300's FP64 units, not HBM,
+// would bound these passes.
+constexpr int kFold = 128;
 
-__global__ void zmv_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz,
-                           const double* __restrict__ p, double* __restrict__ t) {
-  const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void dot2_step(float z, float vh, float vl, float& s, float& c) {
+  const float p = __fmul_rn(z, vh);
+  const float e = __fmaf_rn(z, vh, -p);
+  const float s1 = __fadd_rn(s, p);
+  const float bb = __fsub_rn(s1, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+  s = s1;
+  c = __fmaf_rn(z, vl, __fadd_rn(c, __fadd_rn(err, e)));
+}
+
+__device__ __forceinline__ double fold2(float s, float c) { return (double)s + (double)c; }
+
+// vh, vl <- the float pair of v
+__global__ void split_kernel(long n, const double* __restrict__ v, float* __restrict__ vh,
+                             float* __restrict__ vl) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = v[i];
+  const float h = __double2float_rn(x);
+  vh[i] = h;
+  vl[i] = __double2float_rn(x - (double)h);
+}
+
+// t = Z p: one warp per kZmvRows rows (lanes stride the features), so that each
+// load of the pair of p serves kZmvRows products; also writes t's float pair.
+constexpr int kZmvRows = 4;
+
+__global__ void __launch_bounds__(256)
+zmv_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz, const float* __restrict__ ph,
+           const float* __restrict__ pl, double* __restrict__ t, float* __restrict__ th,
+           float* __restrict__ tl) {
+  const long r0 = (((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kZmvRows;
   const int lane = threadIdx.x & 31;
-  if (r >= n_rows) return;
-  const float* zr = Z + r * ldz;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int f = lane;
-  for (; f + 96 < n_features; f += 128) {
-    s0 = fma((double)__ldg(zr + f), __ldg(p + f), s0);
-    s1 = fma((double)__ldg(zr + f + 32), __ldg(p + f + 32), s1);
-    s2 = fma((double)__ldg(zr + f + 64), __ldg(p + f + 64), s2);
-    s3 = fma((double)__ldg(zr + f + 96), __ldg(p + f + 96), s3);
-  }
-  for (; f < n_features; f += 32) s0 = fma((double)__ldg(zr + f), __ldg(p + f), s0);
-  double s = (s0 + s1) + (s2 + s3);
+  if (r0 >= n_rows) return;
+  const float* zr[kZmvRows];
+  float s[kZmvRows], c[kZmvRows];
+  double acc[kZmvRows];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) t[r] = s;
+  for (int k = 0; k < kZmvRows; ++k) {
+    zr[k] = Z + min(r0 + k, n_rows - 1) * ldz;   // rows past the end repeat the last (not stored)
+    s[k] = c[k] = 0.f;
+    acc[k] = 0.0;
+  }
+  for (int fb = 0; fb < n_features; fb += 32 * kFold) {
+    const int fe = min(n_features, fb + 32 * kFold);
+#pragma unroll 4
+    for (int f = fb + lane; f < fe; f += 32) {
+      const float h = __ldg(ph + f), l = __ldg(pl + f);
+#pragma unroll
+      for (int k = 0; k < kZmvRows; ++k) dot2_step(__ldg(zr[k] + f), h, l, s[k], c[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kZmvRows; ++k) {
+      acc[k] += fold2(s[k], c[k]);
+      s[k] = c[k] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kZmvRows; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  }
+  if (lane < kZmvRows) {
+    double v = acc[0];
+#pragma unroll
+    for (int k = 1; k < kZmvRows; ++k)
+      if (lane == k) v = acc[k];
+    const long r = r0 + lane;
+    if (r < n_rows) {
+      t[r] = v;
+      const float h = __double2float_rn(v);
+      th[r] = h;
+      tl[r] = __double2float_rn(v - (double)h);
+    }
+  }
 }
 
 constexpr int kZtRows = 2048;
 
-__global__ void ztmv_partial_kernel(const float* __restrict__ Z, long n_rows, int n_features,
-                                    long ldz, const double* __restrict__ t,
-                                    double* __restrict__ part) {
+// part[blk][f] = sum over the block's kZtRows rows r of Z[r][f] t[r] (one thread per feature)
+__global__ void __launch_bounds__(256)
+ztmv_partial_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz,
+                    const float* __restrict__ th, const float* __restrict__ tl,
+                    double* __restrict__ part) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   const long r0 = (long)blockIdx.y * kZtRows;
   const long r1 = min(n_rows, r0 + kZtRows);
   if (f >= n_features) return;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  long r = r0;
-  for (; r + 4 <= r1; r += 4) {
-    a0 = fma((double)__ldg(Z + r * ldz + f), __ldg(t + r), a0);
-    a1 = fma((double)__ldg(Z + (r + 1) * ldz + f), __ldg(t + r + 1), a1);
-    a2 = fma((double)__ldg(Z + (r + 2) * ldz + f), __ldg(t + r + 2), a2);
-    a3 = fma((double)__ldg(Z + (r + 3) * ldz + f), __ldg(t + r + 3), a3);
+  double acc = 0.0;
+  for (long rb = r0; rb < r1; rb += kFold) {
+    const long re = min(r1, rb + (long)kFold);
+    float s = 0.f, c = 0.f;
+#pragma unroll 8
+    for (long r = rb; r < re; ++r) dot2_step(__ldg(Z + r * ldz + f), __ldg(th + r), __ldg(tl + r), s, c);
+    acc += fold2(s, c);
   }
-  for (; r < r1; ++r) a0 = fma((double)__ldg(Z + r * ldz + f), __ldg(t + r), a0);
-  part[(long)blockIdx.y * n_features + f] = (a0 + a1) + (a2 + a3);
+  part[(long)blockIdx.y * n_features + f] = acc;
 }
 
 __global__ void ztmv_finish_kernel(const double* __restrict__ part, int n_parts, int n,
@@ -409,6 +504,8 @@ struct SolveCtx {
   double* part;  // [parts][n]
   int parts;
   double* t;     // [n_rows]
+  float *th, *tl;  // float pair of t (or of y) [n_rows]
+  float *ph, *pl;  // float pair of the operand [n]
   cudaStream_t s;
 };
 
@@ -497,7 +594,7 @@ static int chol_apply(const double* L, long ldl, const double* Dinv, int n, doub
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int nb = std::min(NB, n - k0);
     const int rows = std::max(n - k0 - nb, 0);
-    const int grid = std::min(std::max((rows + 7) / 8, 1), kTriCtas);
+    const int grid = std::min(std::max((rows + 63) / 64, 1), kTriCtas);   // 8 warps x 8 rows
     fwd_step_kernel<<<grid, 256, 0, s>>>(L, ldl, Dinv, k0, nb, n, v, tmp);
     QMLR_LAUNCH_CHECK();
   }
@@ -505,7 +602,7 @@ static int chol_apply(const double* L, long ldl, const double* Dinv, int n, doub
   const int last = ((n - 1) / NB) * NB;
   for (int k0 = last; k0 >= 0; k0 -= NB) {
     const int nb = std::min(NB, n - k0);
-    const int grid = std::min(std::max((k0 + 255) / 256, 1), kTriCtas);
+    const int grid = std::min(std::max((k0 + 63) / 64, 1), kTriCtas);
     bwd_step_kernel<<<grid, 256, 0, s>>>(L, ldl, Dinv, k0, nb, tmp, v);
     QMLR_LAUNCH_CHECK();
   }
@@ -519,12 +616,15 @@ static int diag_inverses(const double* L, long ldl, int n, double* Dinv, cudaStr
 }
 
 static int apply_exact(const SolveCtx& c, const double* p, double* q) {
-  const long threads = c.n_rows * 32;
+  const long threads = (c.n_rows + kZmvRows - 1) / kZmvRows * 32;
   if (c.n_rows > 0) {
-    zmv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, p, c.t);
+    split_kernel<<<(c.n + 255) / 256, 256, 0, c.s>>>(c.n, p, c.ph, c.pl);
+    QMLR_LAUNCH_CHECK();
+    zmv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.ph, c.pl,
+                                                                   c.t, c.th, c.tl);
     QMLR_LAUNCH_CHECK();
     dim3 grid((c.n + 255) / 256, c.parts);
-    ztmv_partial_kernel<<<grid, 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.t, c.part);
+    ztmv_partial_kernel<<<grid, 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.th, c.tl, c.part);
     QMLR_LAUNCH_CHECK();
   } else {
     QMLR_CUDA_TRY(cudaMemsetAsync(c.part, 0, sizeof(double) * c.n, c.s));
@@ -547,10 +647,11 @@ extern "C" int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features
          + nblk * NB * NB * 8      // inverses of the diagonal blocks
          + n * 8                   // triangular-solve scratch
          + parts * n * 8           // partial sums of Z^T t
-         + std::max<int64_t>(n_rows, 1) * 8   // t = Z p
+         + std::max<int64_t>(n_rows, 1) * 16  // t = Z p and its float pair
+         + n * 8                   // float pair of the operand
          + 6 * n * 8               // c, r, z, p, q, tmp
          + (int64_t)tc_parts_elems((int)n) * 2   // split panel of the mixed-precision factor
-         + 8 * 8 + 4096;           // scalars + alignment
+         + 8 * 8 + 8192;           // scalars + alignment
 }
 
 extern "C" int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_info, void* stream) {
@@ -612,6 +713,42 @@ static void carve(char*& p, void** out, size_t bytes) {
   p += (bytes + 255) & ~size_t(255);
 }
 
+extern "C" int64_t qmlr_normal_apply_workspace_bytes(int64_t n_rows, int32_t n_features) {
+  const int64_t n = n_features;
+  const int64_t parts = std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
+  return parts * n * 8 + std::max<int64_t>(n_rows, 1) * 16 + n * 8 + 4 * 256;
+}
+
+extern "C" int qmlr_normal_apply(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz, double lambda,
+                                 const double* p, double* q, void* work, int64_t work_bytes, void* stream) {
+  QMLR_REQUIRE(p && q, "NULL pointer argument");
+  QMLR_REQUIRE(n_features >= 1 && n_rows >= 0 && ldz >= n_features, "bad shapes");
+  QMLR_REQUIRE(n_rows == 0 || Z, "Z is NULL");
+  QMLR_REQUIRE(work && work_bytes >= qmlr_normal_apply_workspace_bytes(n_rows, n_features),
+               "workspace too small");
+  SolveCtx c{};
+  c.n = n_features;
+  c.n_rows = n_rows;
+  c.ldz = ldz;
+  c.Z = Z;
+  c.lambda = lambda;
+  c.s = as_stream(stream);
+  c.parts = (int)std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
+  char* w = static_cast<char*>(work);
+  void *vpart, *vt, *vth, *vph;
+  carve(w, &vpart, (size_t)c.parts * c.n * 8);
+  carve(w, &vt, (size_t)std::max<int64_t>(n_rows, 1) * 8);
+  carve(w, &vth, (size_t)std::max<int64_t>(n_rows, 1) * 8);
+  carve(w, &vph, (size_t)c.n * 8);
+  c.part = static_cast<double*>(vpart);
+  c.t = static_cast<double*>(vt);
+  c.th = static_cast<float*>(vth);
+  c.tl = c.th + std::max<int64_t>(n_rows, 1);
+  c.ph = static_cast<float*>(vph);
+  c.pl = c.ph + c.n;
+  return apply_exact(c, p, q);
+}
+
 extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, int32_t n_features,
                                int64_t ldz, const double* y, double lambda, qmlr_solve_opts* opts,
                                double* alpha, void* work, int64_t work_bytes, void* stream) {
@@ -638,7 +775,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   c.s = s;
   c.parts = (int)std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
   char* p = static_cast<char*>(work);
-  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc, *vdinv, *vtri, *vsplit;
+  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc, *vdinv, *vtri, *vsplit, *vth, *vph;
   const int nblk = (n + NB - 1) / NB;
   carve(p, &vL, (size_t)n * n * 8);
   carve(p, &vdinv, (size_t)nblk * NB * NB * 8);
@@ -653,9 +790,15 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   carve(p, &vtmp, (size_t)n * 8);
   carve(p, &vsc, 8 * 8);
   carve(p, &vsplit, tc_parts_elems(n) * 2);
+  carve(p, &vth, (size_t)std::max<int64_t>(n_rows, 1) * 8);
+  carve(p, &vph, (size_t)n * 8);
   c.L = static_cast<double*>(vL);
   c.part = static_cast<double*>(vpart);
   c.t = static_cast<double*>(vt);
+  c.th = static_cast<float*>(vth);
+  c.tl = c.th + std::max<int64_t>(n_rows, 1);
+  c.ph = static_cast<float*>(vph);
+  c.pl = c.ph + n;
   double *cv = static_cast<double*>(vc), *r = static_cast<double*>(vr), *z = static_cast<double*>(vz);
   double *pv = static_cast<double*>(vp), *q = static_cast<double*>(vq);
   double* sc = static_cast<double*>(vsc);
@@ -666,8 +809,10 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
 
   // right-hand side c = Z^T y
   if (n_rows > 0) {
+    split_kernel<<<(unsigned)((n_rows + 255) / 256), 256, 0, s>>>(n_rows, y, c.th, c.tl);
+    QMLR_LAUNCH_CHECK();
     dim3 grid(vb, c.parts);
-    ztmv_partial_kernel<<<grid, 256, 0, s>>>(Z, n_rows, n, ldz, y, c.part);
+    ztmv_partial_kernel<<<grid, 256, 0, s>>>(Z, n_rows, n, ldz, c.th, c.tl, c.part);
     QMLR_LAUNCH_CHECK();
     ztmv_finish_kernel<<<vb, 256, 0, s>>>(c.part, c.parts, n, cv, 0.0, cv);
     QMLR_LAUNCH_CHECK();

@@ -216,6 +216,79 @@ sorf_kernel(SorfArgs a) {
   }
 }
 
+// Segment sum Z[m] = sqrt(2/N_F) sum_I cos(W x_I + b) with b stack-minor
+// (b[i * n_stack + s]: a warp's loads of one index are contiguous). Thread =
+// stack; its running sums live in shared memory as a padded row [D + 4] read
+// and written as float4 (conflict-free), the atom's x is read as float4
+// broadcasts, and sqrt(2/N_F) is applied once when Z is written.
+template <int D>
+__global__ void __launch_bounds__(kStacksPerCta, 3)
+sorf_mol_kernel(SorfArgs a) {
+  constexpr int W = (D + 31) / 32, LD = D + 4;
+  extern __shared__ __align__(16) float smem[];
+  float* xs = smem;                                      // [D]
+  uint32_t* sg = reinterpret_cast<uint32_t*>(xs + D);    // [T*W][nt]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float* acc = reinterpret_cast<float*>(sg + a.T * W * nt);   // [nt][LD]
+  const int part = blockIdx.y;
+  const int s = part * kStacksPerCta + tid;
+  const bool active = s < a.n_stack;
+  const int m = blockIdx.x;
+  const int a0 = a.mol_ptr[m], a1 = a.mol_ptr[m + 1];
+  for (int k = 0; k < a.T * W; ++k)
+    sg[k * nt + tid] = active ? __ldg(a.sign_bits + ((long)s * a.T) * W + k) : 0u;
+  float4* row = reinterpret_cast<float4*>(acc + tid * LD);
+#pragma unroll
+  for (int q = 0; q < D / 4; ++q) row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* bs = a.b + (active ? s : 0);
+  for (int atom = a0; atom < a1; ++atom) {
+    __syncthreads();
+    for (int i = tid; i < D / 4; i += nt)
+      reinterpret_cast<float4*>(xs)[i] = __ldg(reinterpret_cast<const float4*>(a.x + (long)atom * D) + i);
+    __syncthreads();
+    float v[D];
+#pragma unroll
+    for (int q = 0; q < D / 4; ++q) {
+      const float4 x4 = reinterpret_cast<const float4*>(xs)[q];
+      v[4 * q] = x4.x;
+      v[4 * q + 1] = x4.y;
+      v[4 * q + 2] = x4.z;
+      v[4 * q + 3] = x4.w;
+    }
+    for (int t = 0; t < a.T; ++t) {
+      uint32_t w[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) w[q] = sg[(t * W + q) * nt + tid];
+      flip<D>(v, w);
+      fwht<D>(v);
+    }
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < D / 4; ++q) {
+        float4 r = row[q];
+        r.x += fast_cos(fmaf(v[4 * q], a.scale, __ldg(bs + (long)(4 * q) * a.n_stack)));
+        r.y += fast_cos(fmaf(v[4 * q + 1], a.scale, __ldg(bs + (long)(4 * q + 1) * a.n_stack)));
+        r.z += fast_cos(fmaf(v[4 * q + 2], a.scale, __ldg(bs + (long)(4 * q + 2) * a.n_stack)));
+        r.w += fast_cos(fmaf(v[4 * q + 3], a.scale, __ldg(bs + (long)(4 * q + 3) * a.n_stack)));
+        row[q] = r;
+      }
+    }
+  }
+  __syncthreads();
+  // Z[m][part*128*D + stack*D + i]: consecutive threads write consecutive features
+  float* o = static_cast<float*>(a.out) + (long)m * a.n_features + (long)part * kStacksPerCta * D;
+  const int nf = min(nt, a.n_stack - part * kStacksPerCta) * D;
+  for (int f = tid; f < nf; f += nt) o[f] = a.pref * acc[(f / D) * LD + f % D];
+}
+
+// bT[i * n_stack + s] = b[s * d + i]
+__global__ void transpose_phases_kernel(const float* __restrict__ b, int d, int n_stack, float* __restrict__ bT) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d * n_stack) return;
+  const int s = f / d, i = f % d;
+  bT[(long)i * n_stack + s] = b[f];
+}
+
 // ---------------------------------------------------------------------------
 // Force rows of the energy+force normal equations (RFF section: derivative
 // features dz/dr stacked under the energy rows). For molecule m, atom k, axis x:
@@ -282,19 +355,38 @@ force_rows_kernel(const float* __restrict__ tang, const int64_t* __restrict__ ja
 
 // ---------------------------------------------------------------------------
 // Energy (and gradient) with one CTA per (atom, stack part): atoms of one
-// molecule run in parallel. The atom's energy partial (FP64, reduced over the
-// CTA's stacks in a fixed order) goes to atom_e[part][atom]; molecule energies
-// are then summed over atoms and parts in order by segment_energy_kernel.
+// molecule run in parallel. The atom's energy partial (FP64) is reduced over
+// the CTA's stacks by warp shuffles and then over the warps in order, and goes
+// to atom_e[part][atom]; molecule energies are then summed over atoms and
+// parts in order by segment_energy_kernel. The gradient d-vectors of the
+// stacks are reduce-scattered within each warp by shuffles (after the five
+// halving steps lane l holds elements [l*D/32, (l+1)*D/32) summed over the
+// warp) and the warps' partial vectors are added in order.
+
+// One halving step of the warp reduce-scatter: lanes with the OFF bit set keep
+// the upper half of v[0:N) and send the lower half, the others the reverse.
+template <int D, int N, int OFF>
+__device__ __forceinline__ void reduce_scatter_step(float (&v)[D], int lane) {
+  const bool upper = (lane & OFF) != 0;
+#pragma unroll
+  for (int j = 0; j < N / 2; ++j) {
+    const float send = upper ? v[j] : v[j + N / 2];
+    const float keep = upper ? v[j + N / 2] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+  }
+}
+
 template <int D, bool GRAD>
 __global__ void __launch_bounds__(kStacksPerCta)
 sorf_atom_kernel(SorfArgs a, double* __restrict__ atom_e) {
   constexpr int W = (D + 31) / 32;
+  constexpr int NW = kStacksPerCta / 32;
   extern __shared__ __align__(16) float smem[];
   float* xs = smem;                                           // [D]
-  double* red = reinterpret_cast<double*>(smem + D + 4);      // [nt]
-  uint32_t* sg = reinterpret_cast<uint32_t*>(red + kStacksPerCta);   // [T*W][nt]
-  float* work = reinterpret_cast<float*>(sg + 4 * W * kStacksPerCta);  // [nt][D+1] (gradient)
-  const int tid = threadIdx.x, nt = blockDim.x;
+  double* red = reinterpret_cast<double*>(smem + D + 4);      // [NW]
+  uint32_t* sg = reinterpret_cast<uint32_t*>(red + NW);       // [T*W][nt]
+  float* work = reinterpret_cast<float*>(sg + 4 * W * kStacksPerCta);  // gradient partials
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int atom = blockIdx.x, part = blockIdx.y;
   const int s = part * kStacksPerCta + tid;
   const bool active = s < a.n_stack;
@@ -332,7 +424,10 @@ sorf_atom_kernel(SorfArgs a, double* __restrict__ atom_e) {
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = 0.f;
   }
-  red[tid] = (double)e;
+  double ed = (double)e;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ed += __shfl_xor_sync(0xffffffffu, ed, o);
+  if (lane == 0) red[warp] = ed;
   if (GRAD) {
     for (int t = a.T - 1; t >= 0; --t) {
       uint32_t w[W];
@@ -341,19 +436,36 @@ sorf_atom_kernel(SorfArgs a, double* __restrict__ atom_e) {
       fwht<D>(v);
       flip<D>(v, w);
     }
+    if constexpr (D >= 32) {
+      reduce_scatter_step<D, D, 16>(v, lane);
+      reduce_scatter_step<D, D / 2, 8>(v, lane);
+      reduce_scatter_step<D, D / 4, 4>(v, lane);
+      reduce_scatter_step<D, D / 8, 2>(v, lane);
+      reduce_scatter_step<D, D / 16, 1>(v, lane);
+      constexpr int PER = D / 32;
 #pragma unroll
-    for (int i = 0; i < D; ++i) work[tid * (D + 1) + i] = v[i];
+      for (int k = 0; k < PER; ++k) work[warp * D + lane * PER + k] = v[k];
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; ++i) work[tid * (D + 1) + i] = v[i];
+    }
   }
   __syncthreads();
   if (tid == 0) {
+    const int nw = (nt + 31) / 32;
     double sum = 0.0;
-    for (int k = 0; k < nt; ++k) sum += red[k];
+    for (int k = 0; k < nw; ++k) sum += red[k];
     atom_e[(long)part * a.n_atoms + atom] = sum * (double)a.pref;
   }
   if (GRAD) {
+    const int nw = (nt + 31) / 32;
     for (int i = tid; i < D; i += nt) {
       float sum = 0.f;
-      for (int k = 0; k < nt; ++k) sum += work[k * (D + 1) + i];
+      if constexpr (D >= 32) {
+        for (int k = 0; k < nw; ++k) sum += work[k * D + i];
+      } else {
+        for (int k = 0; k < nt; ++k) sum += work[k * (D + 1) + i];
+      }
       a.gx[((long)part * a.n_atoms + atom) * D + i] = sum;
     }
   }
@@ -374,8 +486,8 @@ template <int D, bool GRAD>
 static int launch_atoms(const SorfArgs& a, double* atom_e, int n_mol, double* E, cudaStream_t s) {
   const int nt = std::min(kStacksPerCta, ((a.n_stack + 31) / 32) * 32);
   constexpr int W = (D + 31) / 32;
-  const size_t smem = (size_t)(D + 4) * 4 + kStacksPerCta * 8 + (size_t)4 * W * kStacksPerCta * 4 +
-                      (GRAD ? (size_t)nt * (D + 1) * 4 : 0);
+  const size_t smem = (size_t)(D + 4) * 4 + (kStacksPerCta / 32) * 8 + (size_t)4 * W * kStacksPerCta * 4 +
+                      (GRAD ? (D >= 32 ? (size_t)(kStacksPerCta / 32) * D * 4 : (size_t)nt * (D + 1) * 4) : 0);
   static bool attr = false;
   if (!attr) {
     QMLR_CUDA_TRY(cudaFuncSetAttribute(sorf_atom_kernel<D, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -448,8 +560,52 @@ static size_t sorf_smem(int mode, int T, int nt) {
   return base + ((work + 15) & ~(size_t)15) + 16;
 }
 
+template <int D>
+static int launch_mol(const SorfArgs& a0, int n_mol, cudaStream_t s) {
+  constexpr int W = (D + 31) / 32;
+  QMLR_REQUIRE((reinterpret_cast<uintptr_t>(a0.x) & 15) == 0, "x must be 16-byte aligned");
+  const int nt = std::min(kStacksPerCta, ((a0.n_stack + 31) / 32) * 32);
+  const size_t smem = (size_t)D * 4 + (size_t)a0.T * W * nt * 4 + (size_t)nt * (D + 4) * 4;
+  QMLR_REQUIRE(smem <= 227 * 1024, "SORF shared memory request too large");
+  static bool attr = false;
+  if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(sorf_mol_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    attr = true;
+  }
+  // phases in stack-minor order for coalesced loads (stream-ordered scratch)
+  const int nf = a0.n_stack * D;
+  float* bT = nullptr;
+  QMLR_CUDA_TRY(cudaMallocAsync(&bT, sizeof(float) * nf, s));
+  transpose_phases_kernel<<<(nf + 255) / 256, 256, 0, s>>>(a0.b, D, a0.n_stack, bT);
+  int rc = QMLR_OK;
+  {
+    cudaError_t e = cudaGetLastError();
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("kernel launch failed: %s", cudaGetErrorString(e));
+      rc = QMLR_ECUDA;
+    }
+  }
+  if (rc == QMLR_OK) {
+    SorfArgs a = a0;
+    a.b = bT;
+    dim3 grid(n_mol, a.n_part);
+    sorf_mol_kernel<D><<<grid, nt, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    count_launch();
+    if (e != cudaSuccess) {
+      set_error("kernel launch failed: %s", cudaGetErrorString(e));
+      rc = QMLR_ECUDA;
+    }
+  }
+  cudaFreeAsync(bT, s);
+  return rc;
+}
+
 template <int D, int MODE>
 static int launch_mode(const SorfArgs& a, int n_mol, cudaStream_t s) {
+  if (MODE == M_PER_MOL) return launch_mol<D>(a, n_mol, s);
   const int nt = std::min(kStacksPerCta, ((a.n_stack + 31) / 32) * 32);
   const size_t smem = sorf_smem<D>(MODE, a.T, nt);
   QMLR_REQUIRE(smem <= 227 * 1024, "SORF shared memory request too large");

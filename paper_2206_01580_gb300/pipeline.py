@@ -78,7 +78,7 @@ def feature_matrix(batch: Batch, spec: FeatureSpec, U, rep=None, perm=None, offs
 
 
 def solve(Z, y, lam: float, precision: int = qmlr.GRAM_BF16X6, method: int = qmlr.SOLVE_PCG,
-          max_iter: int = 50, tol: float = 1e-10, shift: float = -2.0 ** -14,
+          max_iter: int = 50, tol: float = 1e-10, shift: float = -2.0 ** -16,
           factor: int = qmlr.FACTOR_MIXED):
     """alpha (float64) of (Z^T Z + lam I) alpha = Z^T y; returns (alpha, iterations, rel. residual)."""
     G = qmlr.gram(Z, precision)

@@ -89,6 +89,8 @@ _SIGS = {
     "qmlr_cholesky_mixed_workspace_bytes": (C.c_int64, [I32]),
     "qmlr_cholesky_mixed": (C.c_int, [P, I64, I32, P, I64, C.POINTER(C.c_int32), VP]),
     "qmlr_cholesky_solve": (C.c_int, [P, I64, I32, P, VP]),
+    "qmlr_normal_apply_workspace_bytes": (C.c_int64, [I64, I32]),
+    "qmlr_normal_apply": (C.c_int, [P, I64, I32, I64, D, P, P, P, I64, VP]),
     "qmlr_solve_workspace_bytes": (C.c_int64, [I64, I32]),
     "qmlr_gram_solve": (C.c_int, [P, P, I64, I32, I64, P, D, C.POINTER(SolveOpts), P, P, I64, VP]),
     "qmlr_pca_workspace_bytes": (C.c_int64, [I32, I32]),
@@ -395,8 +397,21 @@ def cholesky_solve(L, v):
     return v
 
 
+def normal_apply(Z, p, lam: float):
+    """q = Z^T (Z p) + lam p (float64), the solve's exact operator."""
+    Z = _dev(Z, torch.float32)
+    p = _dev(p, torch.float64)
+    n_rows, nf = Z.shape
+    q = torch.empty(nf, device="cuda", dtype=torch.float64)
+    wb = lib().qmlr_normal_apply_workspace_bytes(n_rows, nf)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
+    _check(lib().qmlr_normal_apply(_ptr(Z), n_rows, nf, Z.stride(0), float(lam), _ptr(p), _ptr(q),
+                                   _ptr(work), wb, _stream()))
+    return q
+
+
 def gram_solve(G, Z, y, lam: float, method: int = SOLVE_PCG, max_iter: int = 50, tol: float = 1e-10,
-               shift: float = -2.0 ** -14, raise_on_notconv: bool = False, factor: int = FACTOR_MIXED):
+               shift: float = -2.0 ** -16, raise_on_notconv: bool = False, factor: int = FACTOR_MIXED):
     """alpha for (Z^T Z + lam I) alpha = Z^T y with a factor of G + (lam + shift) I
     (shift < 0: relative to max diag G; factor FACTOR_FP64 or FACTOR_MIXED).
     Returns (alpha, iterations, relative residual)."""
