@@ -330,9 +330,10 @@ int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_info, void* s
  * ridge solve below). Right-looking in 256-column panels: each panel is
  * factorised in FP64; the update of the remaining lower triangle by a panel
  * runs on the tensor cores from the panel's 3-way BF16 split (products to
- * ~2^-24 relative, FP32 sums over each 64-deep K block, subtracted from the
- * FP64 matrix), so L L^T matches A to ~1e-7 of max|A| rather than to FP64
- * round-off. work: device scratch of qmlr_cholesky_mixed_workspace_bytes(n)
+ * ~2^-24 relative, FP32 sums over each 64-deep K block, subtracted in FP32
+ * arithmetic from the not yet factorised matrix, which is held as float pairs
+ * hi + lo in the same storage), so L L^T matches A to ~1e-7 of max|A| rather
+ * than to FP64 round-off. work: device scratch of qmlr_cholesky_mixed_workspace_bytes(n)
  * bytes, 256-byte aligned. Synchronous.
  */
 int64_t qmlr_cholesky_mixed_workspace_bytes(int32_t n);

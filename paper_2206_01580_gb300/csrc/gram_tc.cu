@@ -352,6 +352,18 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
   }
 }
 
+// (hi + lo) - w for a float pair: Knuth's two-sum of hi and -w, its error
+// folded into lo, and the pair renormalised by a second two-sum.
+__device__ __forceinline__ float2 pair_sub(float2 a, float w) {
+  const float s = __fsub_rn(a.x, w);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(-w, bb));
+  const float lo = __fadd_rn(a.y, e);
+  const float h = __fadd_rn(s, lo);
+  const float b2 = __fsub_rn(h, s);
+  return make_float2(h, __fadd_rn(__fsub_rn(s, __fsub_rn(h, b2)), __fsub_rn(lo, b2)));
+}
+
 // ---------------------------------------------------------------------------
 // Trailing update of the mixed-precision Cholesky factor on the tensor cores:
 //   A[i][j] -= sum_k P[i][k] P[j][k],  i >= j,  P = the factored 256-column
@@ -359,8 +371,8 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
 // [3][m][256] (K-major). Each CTA takes one 128 x 128 lower tile, runs the six
 // split products per 64-deep K block into TMEM, promotes every K block into
 // FP32 register sums (four blocks: K = 256), and subtracts the result from the
-// FP64 trailing matrix. The epilogue transposes each drain warp's 32 x 32 block
-// through its own slice of the (then idle) stage memory so that the FP64
+// trailing matrix, held as float pairs (hi, lo) in FP32 arithmetic. The epilogue transposes each drain warp's 32 x 32 block
+// through its own slice of the (then idle) stage memory so that the
 // read-modify-write runs along rows.
 constexpr int kPanelK = 256;
 
@@ -506,10 +518,22 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__
 #pragma unroll
       for (int k = 0; k < kDrainCols; ++k) W[lane * 33 + k] = sum[k];
       __syncwarp();
+      // 16 rows at a time: all loads in flight before the first store
+      float2* P = reinterpret_cast<float2*>(A);
       const int j = j0 + half * 32 + lane;
-      for (int rr = 0; rr < 32; ++rr) {
-        const int i = i0 + quarter * 32 + rr;
-        if (i < m && j <= i) A[(long)i * lda + j] -= (double)W[rr * 33 + lane];
+#pragma unroll
+      for (int r0 = 0; r0 < 32; r0 += 16) {
+        float2 old[16];
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const int i = i0 + quarter * 32 + r0 + rr;
+          old[rr] = (i < m && j <= i) ? P[(long)i * lda + j] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const int i = i0 + quarter * 32 + r0 + rr;
+          if (i < m && j <= i) P[(long)i * lda + j] = pair_sub(old[rr], W[(r0 + rr) * 33 + lane]);
+        }
       }
     }
   }

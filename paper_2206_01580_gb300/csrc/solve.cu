@@ -32,33 +32,102 @@ __global__ void assemble_kernel(const float* __restrict__ G, int n, double diag,
   L[(long)i * ldl + j] = (j <= i) ? v : 0.0;
 }
 
-// Unblocked Cholesky of the nb x nb diagonal block at (k0, k0), in shared memory.
+// 1/sqrt(d) in FP64 from an FP32 seed and one Newton-Raphson step for the
+// reciprocal square root, y <- y (3 - d y^2) / 2, which squares the seed's
+// relative error (~2^-22 -> ~2^-43). Outside the FP32 range of the seed it
+// falls back to the division.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  const double y = (double)rsqrtf((float)d);
+  return y * fma(-0.5 * d, y * y, 1.5);
+}
+
+// The mixed-precision factor keeps the not yet factorised trailing matrix as
+// float pairs (hi, lo) with value hi + lo (about 48 significant bits) in the
+// 8 bytes of each FP64 element, so that the tensor-core updates subtract in
+// FP32 arithmetic; a 256-column panel is converted to FP64 just before it is
+// factorised.
+__device__ __forceinline__ float2 to_pair(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// A = G + (lambda + shift) I as float pairs in the lower triangle (FP64 zeros above).
+__global__ void assemble_pairs_kernel(const float* __restrict__ G, int n, double diag, double* __restrict__ L,
+                                      long ldl) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  double* e = L + (long)i * ldl + j;
+  if (j < i) *reinterpret_cast<float2*>(e) = make_float2(G[idx], 0.f);
+  else if (j == i) *reinterpret_cast<float2*>(e) = to_pair((double)G[idx] + diag);
+  else *e = 0.0;
+}
+
+// FP64 -> float pairs in place over the lower triangle.
+__global__ void to_pairs_kernel(double* __restrict__ L, long ldl, int n) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  if (j > i) return;
+  double* e = L + (long)i * ldl + j;
+  *reinterpret_cast<float2*>(e) = to_pair(*e);
+}
+
+// float pairs -> FP64 in place: columns [c0, c0 + w), rows i >= j.
+__global__ void pairs_to_fp64_kernel(double* __restrict__ L, long ldl, int c0, int w, int n) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long rows = n - c0;
+  if (idx >= rows * w) return;
+  const int i = c0 + (int)(idx / w), j = c0 + (int)(idx % w);
+  if (j > i) return;
+  double* e = L + (long)i * ldl + j;
+  const float2 pr = *reinterpret_cast<const float2*>(e);
+  *e = (double)pr.x + (double)pr.y;
+}
+
+// Unblocked Cholesky of the nb x nb diagonal block at (k0, k0) in shared memory
+// (rows past nb are identity rows). Step j: one thread forms the pivot's
+// 1/sqrt, the column below it is scaled, and the active triangle j < l <= i is
+// updated by all threads from a table of its (i, l) pairs ordered by column
+// from the right, so that step j's work is the table's first (63-j)(64-j)/2
+// entries (no idle index arithmetic, no lanes outside the triangle).
 __global__ void __launch_bounds__(256)
 potrf_diag_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, int* info) {
   __shared__ double a[NB][NB + 1];
+  __shared__ uint16_t tri[NB * (NB - 1) / 2];
+  __shared__ double ys;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
-    const int i = idx / nb, j = idx % nb;
-    a[i][j] = (j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : 0.0;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx / NB, j = idx % NB;
+    a[i][j] = (i < nb && j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : (i == j ? 1.0 : 0.0);
+  }
+  if (tid >= 1 && tid < NB) {   // column l = tid: entries (i, l), i = l..63, after columns > l
+    const int l = tid, off = (NB - 1 - l) * (NB - l) / 2;
+    for (int i = l; i < NB; ++i) tri[off + i - l] = (uint16_t)((i << 8) | l);
   }
   __syncthreads();
-  for (int j = 0; j < nb; ++j) {
+  for (int j = 0; j < NB; ++j) {
     if (tid == 0) {
       double d = a[j][j];
       if (!(d > 0.0)) {
-        record_device_error(err, DEV_NOT_SPD);
-        if (info && *info == 0) *info = k0 + j + 1;
-        d = 1e-300;
+        if (j < nb) {
+          record_device_error(err, DEV_NOT_SPD);
+          if (info && *info == 0) *info = k0 + j + 1;
+        }
+        d = 1.0;
       }
-      a[j][j] = sqrt(d);
+      const double y = rsqrt_newton(d);
+      a[j][j] = d * y;
+      ys = y;
     }
     __syncthreads();
-    const double piv = a[j][j];
-    for (int i = j + 1 + tid; i < nb; i += blockDim.x) a[i][j] /= piv;
+    if (tid > j && tid < NB) a[tid][j] *= ys;
     __syncthreads();
-    for (int idx = tid; idx < (nb - j - 1) * (nb - j - 1); idx += blockDim.x) {
-      const int i = j + 1 + idx / (nb - j - 1), l = j + 1 + idx % (nb - j - 1);
-      if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+    const int cnt = (NB - 1 - j) * (NB - j) / 2;
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      const int pr = tri[e], i = pr >> 8, l = pr & 255;
+      a[i][l] = fma(-a[i][j], a[l][j], a[i][l]);
     }
     __syncthreads();
   }
@@ -68,39 +137,52 @@ potrf_diag_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, in
   }
 }
 
-// Panel: rows r in [k0+nb, n): L[r][k0:k0+nb] = A[r][k0:k0+nb] * L_kk^{-T}. One thread per row.
-__global__ void __launch_bounds__(64)
-trsm_panel_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n) {
-  extern __shared__ double dsm[];
-  double (*lkk)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm);
-  double (*x)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm + NB * (NB + 1));
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
-    const int i = idx / nb, j = idx % nb;
-    lkk[i][j] = (j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : 0.0;
+// Panel: rows r in [k0+nb, n): L[r][k0:k0+nb] = A[r][k0:k0+nb] * L_kk^{-T}. Four threads
+// share a row (thread q owns columns l = q mod 4) in shared memory: after the owner forms
+// x_j = a_j / L_jj it is shuffled to the row's other threads and removed from the later
+// equations (x_l -= x_j L_lj), so every warp keeps the FP64 units of its SM quarter busy
+// and a row's dependency chain is short. With lp set, the solved rows are also written
+// as float pairs (lp[r - k0 - nb][0:64]) for the update of the panel's later columns.
+constexpr int kTrsmRows = 64;
+
+__global__ void __launch_bounds__(256)
+trsm_panel_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n, float2* __restrict__ lp) {
+  extern __shared__ double tsm[];
+  double (*lkk)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(tsm);
+  double (*X)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(tsm + NB * (NB + 1));
+  double* rdg = tsm + 2 * NB * (NB + 1);
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx / NB, j = idx % NB;
+    lkk[i][j] = (i < nb && j <= i) ? L[(long)(k0 + i) * ldl + k0 + j] : (i == j ? 1.0 : 0.0);
   }
-  const int r0 = k0 + nb + blockIdx.x * 64;
-  for (int idx = tid; idx < 64 * nb; idx += blockDim.x) {
-    const int rr = idx / nb, j = idx % nb;
-    const int r = r0 + rr;
-    x[rr][j] = (r < n) ? L[(long)r * ldl + k0 + j] : 0.0;
+  const int rbase = k0 + nb + blockIdx.x * kTrsmRows;
+  for (int idx = tid; idx < kTrsmRows * NB; idx += blockDim.x) {
+    const int rr = idx / NB, j = idx % NB, r = rbase + rr;
+    X[rr][j] = (r < n && j < nb) ? L[(long)r * ldl + k0 + j] : 0.0;
   }
   __syncthreads();
-  const int r = r0 + tid;
-  if (r < n) {
-    for (int j = 0; j < nb; ++j) {
-      double v = x[tid][j];
-      for (int l = 0; l < j; ++l) v -= x[tid][l] * lkk[j][l];
-      x[tid][j] = v / lkk[j][j];
+  if (tid < NB) rdg[tid] = 1.0 / lkk[tid][tid];
+  __syncthreads();
+  const int row = tid >> 2, q = tid & 3;
+  for (int j = 0; j < NB; ++j) {
+    double xj = 0.0;
+    if (q == (j & 3)) {
+      xj = X[row][j] * rdg[j];
+      X[row][j] = xj;
     }
+    xj = __shfl_sync(0xffffffffu, xj, (lane & ~3) | (j & 3));
+    for (int l = j + 1 + ((q - j - 1) & 3); l < NB; l += 4) X[row][l] = fma(-xj, lkk[l][j], X[row][l]);
   }
   __syncthreads();
-  for (int idx = tid; idx < 64 * nb; idx += blockDim.x) {
-    const int rr = idx / nb, j = idx % nb;
-    const int rw = r0 + rr;
-    if (rw < n) L[(long)rw * ldl + k0 + j] = x[rr][j];
+  for (int idx = tid; idx < kTrsmRows * NB; idx += blockDim.x) {
+    const int rr = idx / NB, j = idx % NB, r = rbase + rr;
+    if (r < n && j < nb) L[(long)r * ldl + k0 + j] = X[rr][j];
+    if (lp && r < n) lp[(long)(r - k0 - nb) * NB + j] = j < nb ? to_pair(X[rr][j]) : make_float2(0.f, 0.f);
   }
 }
+
+constexpr size_t kTrsmSmem = (2 * NB * (NB + 1) + NB) * sizeof(double);
 
 // Trailing update of the lower block tiles: A[I][J] -= L[I][k] L[J][k]^T, I >= J > k,
 // for the first `cblocks` trailing block columns J (all of them when cblocks >= T).
@@ -162,8 +244,106 @@ syrk_update_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n, int 
   }
 }
 
+// Update of a panel's later columns inside the mixed-precision factor, in
+// double-float FP32 arithmetic: A[I][J] -= L[I][k] L[J][k]^T (I >= J, first
+// `cblocks` block columns), with L given as float pairs lp (rows from k0 + nb,
+// 64 columns) and A held as float pairs. Each product of pairs is formed by
+// Dekker's FMA product of the high parts plus the two cross terms, and summed
+// with Knuth's two-sum into a (sum, compensation) pair: about 44 significant
+// bits, at FP32 instruction rates instead of the GB300's FP64 rate.
+__device__ __forceinline__ void df_fma(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -p);
+  const float x = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  const float s1 = __fadd_rn(s, p);
+  const float bb = __fsub_rn(s1, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+  s = s1;
+  c = __fadd_rn(c, __fadd_rn(err, __fadd_rn(e, x)));
+}
+
+// (hi + lo) - (s + c) for float pairs, renormalised.
+__device__ __forceinline__ float2 pair_sub2(float2 a, float s, float c) {
+  const float t = __fsub_rn(a.x, s);
+  const float bb = __fsub_rn(t, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, bb)), __fsub_rn(-s, bb));
+  const float lo = __fadd_rn(__fsub_rn(a.y, c), e);
+  const float h = __fadd_rn(t, lo);
+  const float b2 = __fsub_rn(h, t);
+  return make_float2(h, __fadd_rn(__fsub_rn(t, __fsub_rn(h, b2)), __fsub_rn(lo, b2)));
+}
+
+__global__ void __launch_bounds__(256)
+syrk_pairs_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n, int cblocks,
+                  const float2* __restrict__ lp) {
+  extern __shared__ float fsm[];
+  float (*ih)[NB + 1] = reinterpret_cast<float (*)[NB + 1]>(fsm);
+  float (*il)[NB + 1] = reinterpret_cast<float (*)[NB + 1]>(fsm + NB * (NB + 1));
+  float (*jh)[NB + 1] = reinterpret_cast<float (*)[NB + 1]>(fsm + 2 * NB * (NB + 1));
+  float (*jl)[NB + 1] = reinterpret_cast<float (*)[NB + 1]>(fsm + 3 * NB * (NB + 1));
+  const int t0 = (k0 + nb) / NB;
+  const int T = (n + NB - 1) / NB - t0;
+  int t = blockIdx.x, bi = 0, bj = 0;
+  while (bj < cblocks && t >= T - bj) {
+    t -= T - bj;
+    ++bj;
+  }
+  if (bj >= cblocks) return;
+  bi = bj + t;
+  if (bi >= T) return;
+  const int m = n - k0 - nb;   // rows of lp
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int rr = idx / NB, c = idx % NB;
+    const int ri = bi * NB + rr, rj = bj * NB + rr;
+    const float2 a = ri < m ? lp[(long)ri * NB + c] : make_float2(0.f, 0.f);
+    const float2 b = rj < m ? lp[(long)rj * NB + c] : make_float2(0.f, 0.f);
+    ih[rr][c] = a.x;
+    il[rr][c] = a.y;
+    jh[rr][c] = b.x;
+    jl[rr][c] = b.y;
+  }
+  __syncthreads();
+  const int tr = tid / 16, tc = tid % 16;
+  float sa[4][4], ca[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sa[u][v] = ca[u][v] = 0.f;
+  for (int c = 0; c < nb; ++c) {
+    float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ah[u] = ih[tr + 16 * u][c];
+      al[u] = il[tr + 16 * u][c];
+      bh[u] = jh[tc + 16 * u][c];
+      bl[u] = jl[tc + 16 * u][c];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) df_fma(sa[u][v], ca[u][v], ah[u], al[u], bh[v], bl[v]);
+  }
+  float2* P = reinterpret_cast<float2*>(L);
+  const int i0 = (t0 + bi) * NB, j0 = (t0 + bj) * NB;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tr + 16 * u;
+    if (i >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + tc + 16 * v;
+      if (j > i) continue;
+      float2* e = P + (long)i * ldl + j;
+      *e = pair_sub2(*e, sa[u][v], ca[u][v]);
+    }
+  }
+}
+
+constexpr size_t kPairsSmem = 4 * NB * (NB + 1) * sizeof(float);
+
 // Panel operand of the tensor-core trailing update: rows [r0, r0 + m) and columns
-// [k0, k0 + 256) of the factor, split into three BF16 parts
+// [k0, k0 + 256) of the factor, rounded to FP32 and split into three BF16 parts
 // S0 = bf16(x), S1 = bf16(x - S0), S2 = bf16(x - S0 - S1) ([3][m_pad][256],
 // K-major); rows m..m_pad-1 are zero.
 constexpr int kTcPanel = 256;
@@ -175,12 +355,13 @@ panel_split_kernel(const double* __restrict__ L, long ldl, int r0, int k0, int m
   const long total = (long)m_pad * kTcPanel;
   if (idx >= total) return;
   const int r = (int)(idx / kTcPanel), c = (int)(idx % kTcPanel);
-  double x = r < m ? L[(long)(r0 + r) * ldl + k0 + c] : 0.0;
+  // rounded to FP32 first (24 bits), which the three BF16 parts then hold exactly
+  float x = r < m ? __double2float_rn(L[(long)(r0 + r) * ldl + k0 + c]) : 0.f;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const __nv_bfloat16 h = __double2bfloat16(x);
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
     parts[q * total + idx] = h;
-    x -= (double)__bfloat162float(h);
+    x = __fsub_rn(x, __bfloat162float(h));
   }
 }
 
@@ -515,10 +696,10 @@ static int cholesky(double* L, long ldl, int n, cudaStream_t s, int* info) {
   int* err = device_error_ptr();
   static bool attr = false;
   if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kPanelSmem));
     QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kPanelSmem));
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTrsmSmem));
     attr = true;
   }
   for (int k0 = 0; k0 < n; k0 += NB) {
@@ -527,7 +708,7 @@ static int cholesky(double* L, long ldl, int n, cudaStream_t s, int* info) {
     QMLR_LAUNCH_CHECK();
     const int rows = n - k0 - nb;
     if (rows <= 0) break;
-    trsm_panel_kernel<<<(rows + 63) / 64, 64, kPanelSmem, s>>>(L, ldl, k0, nb, n);
+    trsm_panel_kernel<<<(rows + kTrsmRows - 1) / kTrsmRows, 256, kTrsmSmem, s>>>(L, ldl, k0, nb, n, nullptr);
     QMLR_LAUNCH_CHECK();
     const int T = (rows + NB - 1) / NB;
     syrk_update_kernel<<<T * (T + 1) / 2, 256, kPanelSmem, s>>>(L, ldl, k0, nb, n, T);
@@ -542,36 +723,44 @@ static size_t tc_parts_elems(int n) {
 }
 
 // Mixed-precision factor (the preconditioner of the ridge solve): right-looking
-// with 256-column panels. Each panel is factorised in FP64 with the 64-block
-// kernels above, its trailing updates limited to the panel's own columns; the
-// update of the remaining matrix by the panel runs on the tensor cores from the
-// panel's 3-way BF16 split (products to ~2^-24 relative, FP32 sums per 64-deep
-// K block, subtracted from the FP64 matrix).
+// with 256-column panels. On entry the lower triangle holds float pairs. A
+// panel's 64-column blocks are converted to FP64 in turn, factorised (diagonal
+// block, triangular solve of the rows below), and applied to the panel's later
+// columns in double-float arithmetic; the update of the remaining matrix by
+// the whole panel runs on the tensor cores from the panel's 3-way BF16 split
+// (products to ~2^-24 relative, FP32 sums per 64-deep K block, subtracted from
+// the float pairs).
 static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts, cudaStream_t s, int* info) {
   int* err = device_error_ptr();
   static bool attr = false;
   if (!attr) {
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPairsSmem));
     QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kPanelSmem));
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kPanelSmem));
+                                       (int)kTrsmSmem));
     attr = true;
   }
+  // the solved 64-column block rows as float pairs, in the (then idle) split buffer
+  float2* lp = reinterpret_cast<float2*>(parts);
   for (int k0 = 0; k0 < n; k0 += kTcPanel) {
     const int w = std::min(kTcPanel, n - k0);
     for (int c0 = k0; c0 < k0 + w; c0 += NB) {
       const int nb = std::min(NB, n - c0);
+      const long conv = (long)(n - c0) * nb;
+      pairs_to_fp64_kernel<<<(unsigned)((conv + 255) / 256), 256, 0, s>>>(L, ldl, c0, nb, n);
+      QMLR_LAUNCH_CHECK();
       potrf_diag_kernel<<<1, 256, 0, s>>>(L, ldl, c0, nb, err, info);
       QMLR_LAUNCH_CHECK();
       const int rows = n - c0 - nb;
       if (rows <= 0) break;
-      trsm_panel_kernel<<<(rows + 63) / 64, 64, kPanelSmem, s>>>(L, ldl, c0, nb, n);
-      QMLR_LAUNCH_CHECK();
       const int cblocks = (k0 + w - (c0 + nb) + NB - 1) / NB;   // panel columns still to update
+      trsm_panel_kernel<<<(rows + kTrsmRows - 1) / kTrsmRows, 256, kTrsmSmem, s>>>(
+          L, ldl, c0, nb, n, cblocks > 0 ? lp : nullptr);
+      QMLR_LAUNCH_CHECK();
       if (cblocks > 0) {
         const int T = (rows + NB - 1) / NB;
         const int tiles = cblocks * T - cblocks * (cblocks - 1) / 2;
-        syrk_update_kernel<<<tiles, 256, kPanelSmem, s>>>(L, ldl, c0, nb, n, cblocks);
+        syrk_pairs_kernel<<<tiles, 256, kPairsSmem, s>>>(L, ldl, c0, nb, n, cblocks, lp);
         QMLR_LAUNCH_CHECK();
       }
     }
@@ -685,6 +874,9 @@ extern "C" int qmlr_cholesky_mixed(double* L, int64_t ldl, int32_t n, void* work
   int* info = nullptr;
   QMLR_CUDA_TRY(cudaMallocAsync(&info, sizeof(int), s));
   QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+  const long nn = (long)n * n;
+  to_pairs_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(L, ldl, n);
+  QMLR_LAUNCH_CHECK();
   int rc = cholesky_mixed(L, ldl, n, static_cast<__nv_bfloat16*>(work), s, info);
   int h = 0;
   if (rc == QMLR_OK) {
@@ -843,7 +1035,10 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   } ev_guard{ev};
   QMLR_CUDA_TRY(cudaEventRecord(ev[0], s));
   for (int attempt = 0;; ++attempt) {
-    assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(G, n, lambda + shift, c.L, c.ldl);
+    if (opts->factor == QMLR_FACTOR_MIXED)
+      assemble_pairs_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(G, n, lambda + shift, c.L, c.ldl);
+    else
+      assemble_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(G, n, lambda + shift, c.L, c.ldl);
     QMLR_LAUNCH_CHECK();
     QMLR_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
     int rc = opts->factor == QMLR_FACTOR_MIXED
