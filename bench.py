@@ -17,6 +17,7 @@ not sharded across GPUs here); rank 0 prints the line with max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -251,6 +252,23 @@ def ef_training_phase(pcg_iters, pcg_tol, factor):
     return st
 
 
+def measured_traffic(kind):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel's source changed since the capture."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[kind]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if digest != rec["sha256"]:
+        return None
+    return rec
+
+
 def build_workload(scale):
     from paper_2206_01580_gb300 import synth
     t = time.perf_counter()
@@ -329,7 +347,14 @@ def run_ours(args, rank, world):
         ev[2].record(stream)
         Z = qmlr.sorf(x, b.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
         ev[3].record(stream)
-        G = qmlr.gram(Z, precision)
+        if precision == qmlr.GRAM_BF16X6:
+            zt = qmlr.gram_operand(Z, 3)
+            ev[7].record(stream)
+            G = qmlr.gram(Z, precision, operand=zt)
+            del zt
+        else:
+            ev[7].record(stream)
+            G = qmlr.gram(Z, precision)
         ev[4].record(stream)
         alpha, it, rel = qmlr.gram_solve(G, Z, yv, w.lam, method=qmlr.SOLVE_PCG,
                                          max_iter=args.pcg_iters, tol=args.pcg_tol, factor=factor)
@@ -341,7 +366,8 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             so = qmlr.last_solve
             timing.append({"fchl19": ev[0].elapsed_time(ev[1]), "project": ev[1].elapsed_time(ev[2]),
-                           "sorf_Z": ev[2].elapsed_time(ev[3]), "gram": ev[3].elapsed_time(ev[4]),
+                           "sorf_Z": ev[2].elapsed_time(ev[3]), "gram_operand": ev[3].elapsed_time(ev[7]),
+                           "gram": ev[7].elapsed_time(ev[4]),
                            "solve": ev[4].elapsed_time(ev[5]), "factor": so.factor_ms,
                            "refine": so.refine_ms, "predict_ef": ev[5].elapsed_time(ev[6]),
                            "total": ev[0].elapsed_time(ev[6]), "pcg_iters": it, "rel_resid": rel})
@@ -422,6 +448,10 @@ def run_ours(args, rank, world):
         return
 
     # ---------------- roofline of the dominant kernel
+    # Candidates are the single kernels the step times on its own stream: the
+    # tensor-core Gram (split kernel) and the SORF segment sum. The Cholesky
+    # factor, the PCG and the prediction are sequences of kernels; their shares
+    # are in the committed launch list.
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -429,25 +459,33 @@ def run_ours(args, rank, world):
         pass
     nf = w.n_features
     rows = n_mol
-    chol_flops = nf ** 3 / 3.0
-    gram_flops = 3.0 * rows * nf * nf          # three bf16 products, symmetric half x 2 flop/MAC
-    fp64_peak = 1250.0                          # GFLOP/s nominal (FP64 units x clock, GB300)
-    stages = {k: st[k] for k in ("fchl19", "project", "sorf_Z", "gram", "factor", "refine", "predict_ef")}
-    dom = max(stages, key=stages.get)
-    if dom == "factor":
-        ach = chol_flops / (st["factor"] * 1e-3) / 1e12
-        roof = {"kernel": "fp64 blocked Cholesky (trailing update dominant)", "bound": "alu",
-                "achieved": ach, "peak": fp64_peak / 1e3, "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e3),
-                "traffic": None, "peak_source": "nominal FP64 rate of the profiling recipe (1.25 TFLOP/s)"}
-    elif dom == "gram":
-        pk = peaks.get("bf16_tflops_sustained", 1707.8)
-        ach = gram_flops / (st["gram"] * 1e-3) / 1e12
-        roof = {"kernel": "gram_bf16x3 (tcgen05)", "bound": "tensor", "achieved": ach, "peak": pk,
-                "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None}
+    bf16_sust = peaks.get("bf16_tflops_sustained", 1707.8)
+    fp32_add_peak = 36.9   # T FP32 adds/s, measured (profiles/gb300_unit_rates.md)
+    n_stack = nf // w.d
+    sorf_ops_atom = n_stack * w.n_transform * w.d * int(math.log2(w.d)) + 6 * nf
+    cands = {
+        "gram": {"kernel": "tc::gram_split_kernel<3> (3-way BF16 split, tcgen05)", "bound": "tensor",
+                 "achieved": rows * nf * nf / (st["gram"] * 1e-3) / 1e12, "peak": bf16_sust / 6.0,
+                 "unit": "TFLOP/s",
+                 "work": f"N_rows*N_F^2 = {rows * nf * nf:.3e} flop (symmetric half, 2 flop/MAC)",
+                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained / 6 (six BF16 products per "
+                                "FP32-accurate product)"},
+        "sorf_Z": {"kernel": "qmlr::sorf_mol_kernel<128> (SORF + segment sum into Z)", "bound": "alu",
+                   "achieved": sorf_ops_atom * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": fp32_add_peak,
+                   "unit": "TFLOP/s",
+                   "work": f"{sorf_ops_atom} FP32 ops/atom (n_stack*T*d*log2 d butterflies + 6*N_F "
+                           "for phase, cos, sum)",
+                   "peak_source": "measured FP32 add rate (unit-rate probe)"},
+    }
+    for c in cands.values():
+        c["frac"] = c["achieved"] / c["peak"]
+        c["traffic"] = None
+    dom = max(cands, key=lambda k: st[k])
+    roof = dict(cands[dom])
+    tr = measured_traffic(dom)
+    if tr is not None:
+        roof["traffic"] = tr["bytes_per_launch"]
+        roof["traffic_source"] = tr["summary"]
     line = {
         "metric": METRIC, "value": ms * 1e3 / n_atoms, "unit": "us/atom", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
@@ -465,6 +503,7 @@ def run_ours(args, rank, world):
         "pcg": {"iters": st["pcg_iters"], "rel_resid": st["rel_resid"]},
         "train_mae_eV": mae,
         "roofline": roof,
+        "kernel_rooflines": cands,
         "plain_fp32": plain,
         "clocks": clocks,
         "gpu_launches": launches,
