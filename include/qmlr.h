@@ -192,7 +192,11 @@ int qmlr_group_by_element_noalloc(const int32_t* elem, int32_t n_atoms, int32_t 
                                   int32_t* perm, int32_t* elem_offsets, void* stream);
 
 /*
- * x[i][:] = rep[i][:rep_dim] * U[elem(i)]   (float32 arithmetic, float32 accumulation)
+ * x[i][:] = rep[i][:rep_dim] * U[elem(i)]   (SORF section: projection onto the element's
+ * principal directions). Runs on the tensor cores with 3-way BF16 splits of
+ * both operands and FP32 accumulation (products to ~2^-24 relative, the
+ * accuracy of an FP32 GEMM); the split basis is made per call in
+ * stream-ordered scratch (cudaMallocAsync).
  *   rep  float [n_atoms][rep_ld]
  *   perm, elem_offsets  from qmlr_group_by_element
  *   U    float [n_el][rep_dim][d]   (U_e with the d basis vectors as columns)
@@ -207,7 +211,8 @@ int qmlr_project(const float* rep, int32_t rep_ld, int32_t rep_dim, const int32_
  * Transposed projection (chain rule through the projection):
  *   grad_rep[i][:rep_dim] = U[elem(i)] * sum_p gx[p][i][:]
  * gx holds n_part partial gradients [n_part][n_atoms][d] (summed in a fixed
- * order). Columns rep_dim..rep_ld-1 of grad_rep are written as zeros.
+ * order). Columns rep_dim..rep_ld-1 of grad_rep are written as zeros. Same
+ * tensor-core arithmetic as qmlr_project.
  */
 int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* perm,
                    const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el, const float* U,

@@ -89,15 +89,16 @@ int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords,
     return rc;
   if ((rc = qmlr_group_by_element(elem, n_atoms, n_el, w.perm, w.offs, w.gwork, w.gwork_bytes, stream)))
     return rc;
-  if ((rc = qmlr_project(w.rep, m->rep_ld, m->rep_dim, w.perm, w.offs, n_atoms, n_el, m->U, m->d, w.x, stream)))
+  if ((rc = proj_tc_launch(w.rep, m->rep_ld, m->rep_dim, 1, 0, m->Ufwd, m->d, w.perm, w.offs, n_atoms, n_el, w.x,
+                           m->d, m->d, s)))
     return rc;
   QMLR_REQUIRE(n_mol <= w.cap_mols, "batch of %d molecules exceeds the reserved capacity %d", n_mol, w.cap_mols);
   if ((rc = sorf_energy_grad_model(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->bT, m->n_features,
                                    m->sigma, m->alphaT, w.atom_e, energies, forces ? w.gx : nullptr, s)))
     return rc;
   if (!forces) return QMLR_OK;
-  if ((rc = qmlr_project_t(w.gx, m->n_part, w.perm, w.offs, n_atoms, n_el, m->U, m->d, m->rep_dim, w.grep,
-                           m->rep_ld, stream)))
+  if ((rc = proj_tc_launch(w.gx, m->d, m->d, m->n_part, (long)n_atoms * m->d, m->Utrn, m->rep_dim, w.perm, w.offs,
+                           n_atoms, n_el, w.grep, m->rep_ld, m->rep_ld, s)))
     return rc;
   if ((rc = qmlr_jac_offsets(mol_ptr, n_mol, w.pair_ptr, nullptr, stream))) return rc;
   // forces F = -dE/dr: scale -1 in the ordered reduction
@@ -156,10 +157,23 @@ extern "C" int qmlr_model_create(const qmlr_fchl19_params* p, int32_t max_mol_at
     e = cudaMemcpy(m->bT, t1.data(), (size_t)n_features * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->alphaT, t2.data(), (size_t)n_features * 4, cudaMemcpyHostToDevice);
   }
+  const size_t bf = proj_tc_basis_bytes(p->n_el, m->rep_dim, d), bt = proj_tc_basis_bytes(p->n_el, d, m->rep_dim);
+  if (e == cudaSuccess) e = cudaMalloc(&m->Ufwd, bf);
+  if (e == cudaSuccess) e = cudaMalloc(&m->Utrn, bt);
   if (e != cudaSuccess) {
     set_error("model allocation/copy failed: %s", cudaGetErrorString(e));
     qmlr_model_destroy(m);
     return e == cudaErrorMemoryAllocation ? QMLR_ENOMEM : QMLR_ECUDA;
+  }
+  rc = proj_tc_split_basis(m->U, p->n_el, m->rep_dim, d, (long)m->rep_dim * d, d, false, m->Ufwd, 0);
+  if (rc == QMLR_OK) rc = proj_tc_split_basis(m->U, p->n_el, d, m->rep_dim, (long)m->rep_dim * d, d, true, m->Utrn, 0);
+  if (rc == QMLR_OK && cudaStreamSynchronize(0) != cudaSuccess) {
+    set_error("splitting the model basis failed");
+    rc = QMLR_ECUDA;
+  }
+  if (rc) {
+    qmlr_model_destroy(m);
+    return rc;
   }
   *out = m;
   return QMLR_OK;
@@ -174,6 +188,8 @@ extern "C" int qmlr_model_destroy(qmlr_model* m) {
   cudaFree(m->alpha);
   cudaFree(m->bT);
   cudaFree(m->alphaT);
+  cudaFree(m->Ufwd);
+  cudaFree(m->Utrn);
   delete m;
   return QMLR_OK;
 }

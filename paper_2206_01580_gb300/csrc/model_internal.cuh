@@ -33,6 +33,14 @@ int sorf_energy_grad_model(const float* x, int d, const int32_t* mol_ptr, int n_
                            const uint32_t* sign_bits, int T, const float* bT, int n_features, double sigma,
                            const float* alphaT, double* atom_e, double* E, float* gx, cudaStream_t s);
 
+// Tensor-core grouped projection (project_tc.cu).
+size_t proj_tc_basis_bytes(int n_el, int K, int N);
+int proj_tc_split_basis(const float* U, int n_el, int K, int N, long es, int ldu, bool trans, uint16_t* out,
+                        cudaStream_t s);
+int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_stride, const uint16_t* basis, int N,
+                   const int32_t* perm, const int32_t* elem_offsets, int n_atoms, int n_el, float* C, int ldc,
+                   int zero_pad_to, cudaStream_t s);
+
 // Energies and forces of a CSR batch with the given workspace (no allocation).
 int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
                   const int32_t* mol_ptr, int n_mol, int n_atoms, double* energies, float* forces,
@@ -51,5 +59,7 @@ struct qmlr_model {
   float* alpha = nullptr;      // [N_F]
   float* bT = nullptr;         // [d][n_stack] stack-minor copy of b
   float* alphaT = nullptr;     // [d][n_stack] stack-minor copy of alpha
+  uint16_t* Ufwd = nullptr;    // U split for the tensor-core projection (bf16 [n_el][3][N_pad][K_pad])
+  uint16_t* Utrn = nullptr;    // U split for the transposed projection
   qmlr::PredictWorkspace ws;   // workspace of qmlr_predict_ef
 };

@@ -3,9 +3,9 @@
 // SORF section of the paper: each element has its own basis U_e (leading
 // left singular vectors of that element's representations); the projection
 // is one matrix product per element. Atoms are first grouped by element with
-// a stable device counting sort (count / scan / scatter), then a grouped
-// FP32 GEMM runs over 64-atom tiles that each hold one element, so that U_e
-// is streamed once per tile. Arithmetic and accumulation are FP32.
+// a stable device counting sort (count / scan / scatter), then a grouped GEMM
+// runs on the tensor cores over 128-atom tiles that each hold one element
+// (project_tc.cu).
 #include "common.cuh"
 
 #include <mutex>
@@ -97,114 +97,13 @@ __global__ void group_scatter_kernel(const int32_t* __restrict__ elem, int n_ato
 }
 
 // ---------------------------------------------------------------------------
-// Grouped GEMM: for each element e, rows perm[off[e] .. off[e+1]) :
-//   C[row][n] = sum_k A_sum[row][k] * B_e[k][n]
-// A_sum = sum over n_part slices of A (slice stride a_part_stride).
-// B_e[k][n] = B[e*b_elem_stride + k*ldb + n]          (B_T = false)
-//           = B[e*b_elem_stride + n*ldb + k]          (B_T = true)
-constexpr int TM = 64, TN = 128, TK = 16;
-
-template <bool B_T>
-__global__ void __launch_bounds__(256)
-grouped_gemm_kernel(const float* __restrict__ A, int lda, int K, int n_part, long a_part_stride,
-                    const float* __restrict__ B, int ldb, long b_elem_stride, int N,
-                    const int32_t* __restrict__ perm, const int32_t* __restrict__ elem_offsets,
-                    int n_el, float* __restrict__ C, int ldc, int zero_pad_to) {
-  __shared__ __align__(16) float As[TK][TM + 4];
-  __shared__ __align__(16) float Bs[TK][TN + 4];
-  __shared__ int rows[TM];
-
-  // map blockIdx.x to (element, tile)
-  int e = -1, tile = blockIdx.x, start = 0, count = 0;
-  for (int k = 0; k < n_el; ++k) {
-    const int s = elem_offsets[k], cnt = elem_offsets[k + 1] - s;
-    const int nt = (cnt + TM - 1) / TM;
-    if (tile < nt) {
-      e = k;
-      start = s + tile * TM;
-      count = min(TM, cnt - tile * TM);
-      break;
-    }
-    tile -= nt;
-  }
-  if (e < 0) return;
-  const int n0 = blockIdx.y * TN;
-  const int tid = threadIdx.x;
-  if (tid < TM) rows[tid] = tid < count ? perm[start + tid] : -1;
-  __syncthreads();
-
-  const float* Be = B + (long)e * b_elem_stride;
-  const int tr = tid / 16, tc = tid % 16;   // 16 x 16 threads, 4 rows x 8 cols each
-  float acc[4][8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-
-  for (int k0 = 0; k0 < K; k0 += TK) {
-    // A tile: TM x TK, thread loads 4 elements (row = tid/4, k = (tid%4)*4 .. +3)
-    {
-      const int r = tid / 4, kk = (tid % 4) * 4;
-      const int row = rows[r];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float v = 0.f;
-        const int k = k0 + kk + q;
-        if (row >= 0 && k < K) {
-          const float* ap = A + (long)row * lda + k;
-          for (int p = 0; p < n_part; ++p) v += __ldg(ap + p * a_part_stride);
-        }
-        As[kk + q][r] = v;
-      }
-    }
-    // B tile: TK x TN
-    if (!B_T) {
-      // thread loads 8 elements: k = tid/16, n = (tid%16)*8
-      const int k = k0 + tid / 16, nb = (tid % 16) * 8;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int n = n0 + nb + q;
-        Bs[tid / 16][nb + q] = (k < K && n < N) ? __ldg(Be + (long)k * ldb + n) : 0.f;
-      }
-    } else {
-      // k fastest: thread loads 8 elements: n = tid/2, k = (tid%2)*8
-      const int nl = tid / 2, kb = (tid % 2) * 8;
-      const int n = n0 + nl;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + kb + q;
-        Bs[kb + q][nl] = (k < K && n < N) ? __ldg(Be + (long)n * ldb + k) : 0.f;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < TK; ++k) {
-      float a[4], b[8];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][tr * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = Bs[k][tc * 8 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = tr * 4 + i;
-    if (r >= count) continue;
-    const int row = rows[r];
-    float* cp = C + (long)row * ldc;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int n = n0 + tc * 8 + j;
-      if (n < N) cp[n] = acc[i][j];
-      else if (n < zero_pad_to) cp[n] = 0.f;
-    }
-  }
-}
+// The grouped projection itself runs on the tensor cores (project_tc.cu).
+size_t proj_tc_basis_bytes(int n_el, int K, int N);
+int proj_tc_split_basis(const float* U, int n_el, int K, int N, long es, int ldu, bool trans, uint16_t* out,
+                        cudaStream_t s);
+int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_stride, const uint16_t* basis, int N,
+                   const int32_t* perm, const int32_t* elem_offsets, int n_atoms, int n_el, float* C, int ldc,
+                   int zero_pad_to, cudaStream_t s);
 
 }  // namespace qmlr
 
@@ -251,11 +150,15 @@ extern "C" int qmlr_project(const float* rep, int32_t rep_ld, int32_t rep_dim, c
   QMLR_REQUIRE(n_atoms >= 0, "n_atoms must be >= 0");
   if (n_atoms == 0) return QMLR_OK;
   QMLR_REQUIRE(rep && perm && elem_offsets && U && x, "NULL pointer argument");
-  dim3 grid((n_atoms + TM - 1) / TM + n_el, (d + TN - 1) / TN);
-  grouped_gemm_kernel<false><<<grid, 256, 0, as_stream(stream)>>>(
-      rep, rep_ld, rep_dim, 1, 0, U, d, (long)rep_dim * d, d, perm, elem_offsets, n_el, x, d, d);
-  QMLR_LAUNCH_CHECK();
-  return QMLR_OK;
+  // the basis is split per call into stream-ordered scratch; a model holds its split basis
+  cudaStream_t s = as_stream(stream);
+  uint16_t* basis = nullptr;
+  QMLR_CUDA_TRY(cudaMallocAsync(&basis, proj_tc_basis_bytes(n_el, rep_dim, d), s));
+  int rc = proj_tc_split_basis(U, n_el, rep_dim, d, (long)rep_dim * d, d, false, basis, s);
+  if (rc == QMLR_OK)
+    rc = proj_tc_launch(rep, rep_ld, rep_dim, 1, 0, basis, d, perm, elem_offsets, n_atoms, n_el, x, d, d, s);
+  cudaFreeAsync(basis, s);
+  return rc;
 }
 
 extern "C" int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* perm,
@@ -268,12 +171,15 @@ extern "C" int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* pe
   QMLR_REQUIRE(n_part >= 1, "n_part must be >= 1");
   if (n_atoms == 0) return QMLR_OK;
   QMLR_REQUIRE(gx && perm && elem_offsets && U && grad_rep, "NULL pointer argument");
-  dim3 grid((n_atoms + TM - 1) / TM + n_el, (rep_ld + TN - 1) / TN);
-  grouped_gemm_kernel<true><<<grid, 256, 0, as_stream(stream)>>>(
-      gx, d, d, n_part, (long)n_atoms * d, U, d, (long)rep_dim * d, rep_dim, perm, elem_offsets,
-      n_el, grad_rep, rep_ld, rep_ld);
-  QMLR_LAUNCH_CHECK();
-  return QMLR_OK;
+  cudaStream_t s = as_stream(stream);
+  uint16_t* basis = nullptr;
+  QMLR_CUDA_TRY(cudaMallocAsync(&basis, proj_tc_basis_bytes(n_el, d, rep_dim), s));
+  int rc = proj_tc_split_basis(U, n_el, d, rep_dim, (long)rep_dim * d, d, true, basis, s);
+  if (rc == QMLR_OK)
+    rc = proj_tc_launch(gx, d, d, n_part, (long)n_atoms * d, basis, rep_dim, perm, elem_offsets, n_atoms, n_el,
+                        grad_rep, rep_ld, rep_ld, s);
+  cudaFreeAsync(basis, s);
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
