@@ -406,9 +406,11 @@ __device__ __forceinline__ void block_matvec(const double* __restrict__ D, const
   const int o = tid >> 2, part = tid & 3;
   double acc = 0.0;
   if (o < NB) {
+    double a4[4] = {0.0, 0.0, 0.0, 0.0};   // four independent chains: FP64 latency is long
 #pragma unroll
     for (int l = part * 16; l < part * 16 + 16; ++l)
-      acc = fma(transposed ? D[l * NB + o] : D[o * NB + l], vk[l], acc);
+      a4[l & 3] = fma(transposed ? D[l * NB + o] : D[o * NB + l], vk[l], a4[l & 3]);
+    acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -421,12 +423,14 @@ constexpr int kTriCtas = 304;   // 2 CTAs per SM on 152 SMs
 // Eight lanes share a row (lane j reads columns j, j+8, ..., j+56: 64 contiguous
 // bytes per load instruction and row) and a warp takes 8 rows per pass, so
 // every lane has 16 loads in flight; the 8 partial sums meet by shuffles.
-__global__ void __launch_bounds__(256)
-fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
-                int n, double* __restrict__ r, double* __restrict__ y) {
+// (r and y are read through L2 (ld.cg): inside a persistent sweep, rows written
+// by other CTAs in the previous block step must not come from a stale L1 line.)
+__device__ __forceinline__ void fwd_step_body(const double* __restrict__ L, long ldl,
+                                              const double* __restrict__ Dinv, int k0, int nb, int n,
+                                              double* __restrict__ r, double* __restrict__ y) {
   __shared__ double rk[NB], xk[NB];
   const int tid = threadIdx.x;
-  if (tid < NB) rk[tid] = tid < nb ? r[k0 + tid] : 0.0;
+  if (tid < NB) rk[tid] = tid < nb ? __ldcg(r + k0 + tid) : 0.0;
   __syncthreads();
   block_matvec(Dinv + (long)(k0 / NB) * NB * NB, rk, xk, false);
   __syncthreads();
@@ -457,21 +461,27 @@ fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1) sum[h] += __shfl_xor_sync(0xffffffffu, sum[h], o);
       const int row = row0 + 4 * h + rg;
-      if (sub == 0 && row < n) r[row] -= sum[h];
+      if (sub == 0 && row < n) r[row] = __ldcg(r + row) - sum[h];
     }
   }
+}
+
+__global__ void __launch_bounds__(256)
+fwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
+                int n, double* __restrict__ r, double* __restrict__ y) {
+  fwd_step_body(L, ldl, Dinv, k0, nb, n, r, y);
 }
 
 // backward step k: x_k = Dinv_k^T y_k; y[c] -= sum_r L[k0+r][c] x_k[r] for columns c < k0.
 // A CTA takes 64 columns; its four 64-thread groups take 16 of the block's rows
 // each (coalesced 512-byte row segments) and their partial sums are added in
 // a fixed order through shared memory.
-__global__ void __launch_bounds__(256)
-bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
-                double* __restrict__ y, double* __restrict__ x) {
+__device__ __forceinline__ void bwd_step_body(const double* __restrict__ L, long ldl,
+                                              const double* __restrict__ Dinv, int k0, int nb,
+                                              double* __restrict__ y, double* __restrict__ x) {
   __shared__ double yk[NB], xk[NB], part[4][NB];
   const int tid = threadIdx.x;
-  if (tid < NB) yk[tid] = tid < nb ? y[k0 + tid] : 0.0;
+  if (tid < NB) yk[tid] = tid < nb ? __ldcg(y + k0 + tid) : 0.0;
   __syncthreads();
   block_matvec(Dinv + (long)(k0 / NB) * NB * NB, yk, xk, true);
   __syncthreads();
@@ -490,10 +500,204 @@ bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict
     for (int u = 0; u < 16; ++u) s = fma(v[u], xk[rg * 16 + u], s);
     part[rg][cg] = s;
     __syncthreads();
-    if (rg == 0 && c < k0) y[c] -= (part[0][cg] + part[1][cg]) + (part[2][cg] + part[3][cg]);
+    if (rg == 0 && c < k0) y[c] = __ldcg(y + c) - ((part[0][cg] + part[1][cg]) + (part[2][cg] + part[3][cg]));
     __syncthreads();
   }
 }
+
+__global__ void __launch_bounds__(256)
+bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int k0, int nb,
+                double* __restrict__ y, double* __restrict__ x) {
+  bwd_step_body(L, ldl, Dinv, k0, nb, y, x);
+}
+
+// Dataflow sweeps: one cooperative launch per substitution. 64-row block b is
+// owned by CTA b mod gridDim.x, and owners take their blocks in order. The
+// owner of block b accumulates L_bj x_j over the earlier blocks j as soon as
+// x_j has been published (its flag set), then forms x_b = Dinv_b (r_b - sum)
+// and publishes it (data, fence, flag). Blocks are published in order, so a
+// warp that has seen flag j knows x_0..x_j are final. Only the product with
+// the previous block and the diagonal solve lie on the critical path of a
+// step. Every wait is bounded: on expiry the kernel records a device error and
+// the CTA leaves the sweep. (The backward sweep is the same on L^T, blocks in
+// decreasing order.) All CTAs are co-resident (cooperative launch), so an owner
+// never waits on a CTA that is not running.
+constexpr long long kFlowSpin = 1LL << 23;   // ~2-4 s of polling (one L2 read per poll)
+
+// Warp-level wait until flag[j] is set (lane 0 polls); false on timeout.
+__device__ __forceinline__ bool wait_flag(const unsigned* flags, int j, int* err) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    long long it = 0;
+    while (*reinterpret_cast<const volatile unsigned*>(flags + j) == 0u) {
+      if (++it > kFlowSpin) {
+        record_device_error(err, DEV_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void publish(unsigned* flags, int b) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(flags + b, 1u);
+}
+
+// x = D v (D one 64 x 64 block, transposed or not) with D's 16 values of this
+// thread already in registers (thread: output o = tid >> 2, inputs part*16..+15).
+__device__ __forceinline__ void block_matvec_reg(const double (&dv)[16], const double* vk, double* xk) {
+  const int tid = threadIdx.x;
+  const int o = tid >> 2, part = tid & 3;
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a4[q & 3] = fma(dv[q], vk[part * 16 + q], a4[q & 3]);
+  double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (part == 0) xk[o] = acc;
+}
+
+__device__ __forceinline__ void load_dinv(const double* D, bool transposed, double (&dv)[16]) {
+  const int tid = threadIdx.x;
+  const int o = tid >> 2, part = tid & 3;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int l = part * 16 + q;
+    dv[q] = __ldg(transposed ? D + l * NB + o : D + o * NB + l);
+  }
+}
+
+// forward: L y = r (r read-only here); warp w takes rows 8w..8w+7 of the block,
+// 4 lanes per row, each lane 16 of the 64 columns of a block product. The L
+// tile of the next block product and the block's Dinv are loaded before the
+// wait, so that a step's critical path is the flag, x_{b-1} and the arithmetic.
+__global__ void __launch_bounds__(256)
+fwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int n,
+                const double* __restrict__ r, double* __restrict__ y, unsigned* flags, int* err) {
+  __shared__ double rb[NB], xb[NB];
+  __shared__ int fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int o = warp * 8 + (lane >> 2), part = lane & 3;
+  const int nblk = (n + NB - 1) / NB;
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int r0 = b * NB, nb = min(NB, n - r0);
+    double dv[16];
+    load_dinv(Dinv + (long)b * NB * NB, false, dv);
+    double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    const double* Lr = L + (long)(r0 + min(o, nb - 1)) * ldl + part * 16;
+    double lv[16];
+    if (b > 0) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) lv[q] = __ldg(Lr + q);
+    }
+    int ready = -1;
+    for (int j = 0; j < b; ++j) {
+      if (j > ready) {
+        if (!wait_flag(flags, j, err)) {
+          fail = 1;
+          break;
+        }
+        ready = j;
+      }
+      const double* xj = y + (long)j * NB + part * 16;
+      double xv[16], ln[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) xv[q] = __ldcg(xj + q);
+      if (j + 1 < b) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ln[q] = __ldg(Lr + (long)(j + 1) * NB + q);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) lv[q] = ln[q];
+    }
+    double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    __syncthreads();
+    if (fail) return;
+    if (part == 0) rb[o] = o < nb ? __ldcg(r + r0 + o) - acc : 0.0;
+    __syncthreads();
+    block_matvec_reg(dv, rb, xb);
+    __syncthreads();
+    if (tid < nb) y[r0 + tid] = xb[tid];
+    publish(flags, b);
+  }
+}
+
+// backward: L^T x = y; block b needs x_j for j > b: x_b = Dinv_b^T (y_b - sum_j L_jb^T x_j).
+// Thread (c = tid & 63, g = tid >> 6) sums 16 of block j's rows for column c; the
+// next L tile and Dinv_b^T are prefetched as in the forward sweep.
+__global__ void __launch_bounds__(256)
+bwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int n,
+                const double* __restrict__ yv, double* __restrict__ x, unsigned* flags, int* err) {
+  __shared__ double yb[NB], xb[NB], part[4][NB];
+  __shared__ int fail;
+  const int tid = threadIdx.x;
+  const int c = tid & 63, g = tid >> 6;
+  const int nblk = (n + NB - 1) / NB;
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int b = nblk - 1 - blockIdx.x; b >= 0; b -= gridDim.x) {
+    const int r0 = b * NB, nb = min(NB, n - r0);
+    double dv[16];
+    load_dinv(Dinv + (long)b * NB * NB, true, dv);
+    double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool colok = c < nb;
+    auto ltile = [&](int j, double (&t)[16]) {
+      const int j0 = j * NB, jn = min(NB, n - j0);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int rr = g * 16 + q;
+        t[q] = (rr < jn && colok) ? __ldg(L + (long)(j0 + rr) * ldl + r0 + c) : 0.0;
+      }
+    };
+    double lv[16];
+    if (b < nblk - 1) ltile(nblk - 1, lv);
+    int ready = nblk;
+    for (int j = nblk - 1; j > b; --j) {
+      if (j < ready) {
+        if (!wait_flag(flags, j, err)) {
+          fail = 1;
+          break;
+        }
+        ready = j;
+      }
+      const int j0 = j * NB, jn = min(NB, n - j0);
+      double xv[16], ln[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int rr = g * 16 + q;
+        xv[q] = rr < jn ? __ldcg(x + j0 + rr) : 0.0;
+      }
+      if (j - 1 > b) ltile(j - 1, ln);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) lv[q] = ln[q];
+    }
+    part[g][c] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+    __syncthreads();
+    if (fail) return;
+    if (tid < NB) yb[tid] = tid < nb ? __ldcg(yv + r0 + tid) - ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) : 0.0;
+    __syncthreads();
+    block_matvec_reg(dv, yb, xb);
+    __syncthreads();
+    if (tid < nb) x[r0 + tid] = xb[tid];
+    publish(flags, b);
+  }
+}
+
+constexpr int kMaxFlowBlocks = 4096;   // n <= 262144
+static __device__ unsigned g_flow_flags[2 * kMaxFlowBlocks];
+
 
 // ---------------------------------------------------------------------------
 // exact operator pieces: t = Z p (rows), q = Z^T t + lambda p (features).
@@ -560,6 +764,68 @@ zmv_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz, c
       const float h = __ldg(ph + f), l = __ldg(pl + f);
 #pragma unroll
       for (int k = 0; k < kZmvRows; ++k) dot2_step(__ldg(zr[k] + f), h, l, s[k], c[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kZmvRows; ++k) {
+      acc[k] += fold2(s[k], c[k]);
+      s[k] = c[k] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kZmvRows; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  }
+  if (lane < kZmvRows) {
+    double v = acc[0];
+#pragma unroll
+    for (int k = 1; k < kZmvRows; ++k)
+      if (lane == k) v = acc[k];
+    const long r = r0 + lane;
+    if (r < n_rows) {
+      t[r] = v;
+      const float h = __double2float_rn(v);
+      th[r] = h;
+      tl[r] = __double2float_rn(v - (double)h);
+    }
+  }
+}
+
+// The same with 16-byte loads (Z rows, ldz and the pair arrays 16-byte aligned,
+// n_features a multiple of 4): a warp reads 512 contiguous bytes per row and
+// instruction, and each float4 of the operand's pair serves kZmvRows rows.
+__global__ void __launch_bounds__(256)
+zmv4_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz, const float* __restrict__ ph,
+            const float* __restrict__ pl, double* __restrict__ t, float* __restrict__ th,
+            float* __restrict__ tl) {
+  const long r0 = (((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kZmvRows;
+  const int lane = threadIdx.x & 31;
+  if (r0 >= n_rows) return;
+  const float4* zr[kZmvRows];
+  float s[kZmvRows], c[kZmvRows];
+  double acc[kZmvRows];
+#pragma unroll
+  for (int k = 0; k < kZmvRows; ++k) {
+    zr[k] = reinterpret_cast<const float4*>(Z + min(r0 + k, n_rows - 1) * ldz);
+    s[k] = c[k] = 0.f;
+    acc[k] = 0.0;
+  }
+  const float4* h4 = reinterpret_cast<const float4*>(ph);
+  const float4* l4 = reinterpret_cast<const float4*>(pl);
+  const int n4 = n_features / 4;
+  for (int fb = 0; fb < n4; fb += 32 * (kFold / 4)) {
+    const int fe = min(n4, fb + 32 * (kFold / 4));
+#pragma unroll 2
+    for (int f = fb + lane; f < fe; f += 32) {
+      const float4 h = __ldg(h4 + f), l = __ldg(l4 + f);
+#pragma unroll
+      for (int k = 0; k < kZmvRows; ++k) {
+        const float4 z = __ldg(zr[k] + f);
+        dot2_step(z.x, h.x, l.x, s[k], c[k]);
+        dot2_step(z.y, h.y, l.y, s[k], c[k]);
+        dot2_step(z.z, h.z, l.z, s[k], c[k]);
+        dot2_step(z.w, h.w, l.w, s[k], c[k]);
+      }
     }
 #pragma unroll
     for (int k = 0; k < kZmvRows; ++k) {
@@ -776,9 +1042,63 @@ static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts, cuda
   return QMLR_OK;
 }
 
-// v <- (L L^T)^{-1} v; tmp is an n-vector of scratch.
+// Grid of the dataflow sweeps (all CTAs co-resident) and their flag words on
+// the current device; 0 when cooperative launch is not available.
+static int flow_grid() {
+  static int grid[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (grid[dev] == 0) {
+    int coop = 0, pf = 0, pb = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, fwd_flow_kernel, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, bwd_flow_kernel, 256, 0);
+    const int per_sm = std::min(std::min(pf, pb), 2);
+    grid[dev] = (coop && per_sm > 0) ? per_sm * sm_count() : -1;
+  }
+  return grid[dev] > 0 ? grid[dev] : 0;
+}
+
+static unsigned* flow_flags() {
+  static unsigned* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_flow_flags) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<unsigned*>(p);
+  }
+  return addr[dev];
+}
+
+// v <- (L L^T)^{-1} v; tmp is an n-vector of scratch. One dataflow launch per
+// sweep where cooperative launch is available (calls on one device are then
+// serialised by the caller: they share the flag words), else one launch per
+// block step.
 static int chol_apply(const double* L, long ldl, const double* Dinv, int n, double* v, double* tmp,
                       cudaStream_t s) {
+  const int nblk = (n + NB - 1) / NB;
+  const int grid = nblk <= kMaxFlowBlocks ? std::min(flow_grid(), nblk) : 0;
+  unsigned* flags = grid ? flow_flags() : nullptr;
+  if (grid && flags) {
+    int* err = device_error_ptr();
+    QMLR_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * (size_t)kMaxFlowBlocks * sizeof(unsigned), s));
+    unsigned* f1 = flags;
+    unsigned* f2 = flags + kMaxFlowBlocks;
+    {
+      void* args[] = {(void*)&L, (void*)&ldl, (void*)&Dinv, (void*)&n, (void*)&v, (void*)&tmp, (void*)&f1,
+                      (void*)&err};
+      QMLR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fwd_flow_kernel, grid, 256, args, 0, s));
+      count_launch();
+    }
+    {
+      void* args[] = {(void*)&L, (void*)&ldl, (void*)&Dinv, (void*)&n, (void*)&tmp, (void*)&v, (void*)&f2,
+                      (void*)&err};
+      QMLR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bwd_flow_kernel, grid, 256, args, 0, s));
+      count_launch();
+    }
+    return QMLR_OK;
+  }
   // forward: L tmp = v (v is consumed as the running residual)
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int nb = std::min(NB, n - k0);
@@ -809,8 +1129,14 @@ static int apply_exact(const SolveCtx& c, const double* p, double* q) {
   if (c.n_rows > 0) {
     split_kernel<<<(c.n + 255) / 256, 256, 0, c.s>>>(c.n, p, c.ph, c.pl);
     QMLR_LAUNCH_CHECK();
-    zmv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.ph, c.pl,
-                                                                   c.t, c.th, c.tl);
+    const bool vec = (c.n % 4 == 0) && (c.ldz % 4 == 0) && ((reinterpret_cast<uintptr_t>(c.Z) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(c.ph) & 15) == 0) && ((reinterpret_cast<uintptr_t>(c.pl) & 15) == 0);
+    if (vec)
+      zmv4_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.ph, c.pl,
+                                                                      c.t, c.th, c.tl);
+    else
+      zmv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.ph, c.pl,
+                                                                     c.t, c.th, c.tl);
     QMLR_LAUNCH_CHECK();
     dim3 grid((c.n + 255) / 256, c.parts);
     ztmv_partial_kernel<<<grid, 256, 0, c.s>>>(c.Z, c.n_rows, c.n, c.ldz, c.th, c.tl, c.part);
