@@ -33,6 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "µs/atom E+F predict, train s at 16k feats, p50/p99 latency vs plain FP32 form"
+# Gram form of the training step: 1 = 2-way BF16 split (three tensor-core
+# products), 2 = 3-way split (six products); set by --gram-split.
+GRAM_FORM = 1
 
 
 def parse():
@@ -50,6 +53,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
+    ap.add_argument("--gram-split", type=int, default=2, choices=[2, 3],
+                    help="BF16 split of the tensor-core Gram: 2 (three products) or 3 (six products)")
     ap.add_argument("--factor", default="mixed", choices=["mixed", "fp64"],
                     help="preconditioner factor: tensor-core trailing updates (mixed) or FP64 throughout")
     return ap.parse_args()
@@ -227,9 +232,10 @@ def ef_training_phase(pcg_iters, pcg_tol, factor):
         ev[0].record(s)
         rows = pipeline.energy_force_rows(tr, spec, U)
         ev[1].record(s)
-        G = qmlr.gram(rows, qmlr.GRAM_BF16X6)
+        G = qmlr.gram(rows, GRAM_FORM)
         ev[2].record(s)
-        alpha, it, rel = qmlr.gram_solve(G, rows, y, w.lam, max_iter=pcg_iters, tol=pcg_tol, factor=factor)
+        alpha, it, rel = qmlr.gram_solve(G, rows, y, w.lam, max_iter=pcg_iters, tol=pcg_tol, factor=factor,
+                                         shift=pipeline.DEFAULT_SHIFT[GRAM_FORM])
         ev[3].record(s)
         torch.cuda.synchronize()
         so = qmlr.last_solve
@@ -252,12 +258,15 @@ def ef_training_phase(pcg_iters, pcg_tol, factor):
     return st
 
 
-def measured_traffic(kind):
+def measured_traffic(kind, kernel):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when the kernel's source changed since the capture."""
+    summary, or None when it was taken for another kernel or the kernel's
+    source changed since the capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[kind]
     except (OSError, ValueError, KeyError):
+        return None
+    if not kernel.startswith(rec["kernel"]):
         return None
     src = os.path.join(ROOT, rec["source"])
     try:
@@ -338,7 +347,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     factor = qmlr.FACTOR_MIXED if args.factor == "mixed" else qmlr.FACTOR_FP64
 
-    def step(b: pipeline.Batch, yv, precision=qmlr.GRAM_BF16X6, timing=None):
+    def step(b: pipeline.Batch, yv, precision=GRAM_FORM, timing=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
         ev[0].record(stream)
         rep, perm, offs = pipeline.representations(b, spec)
@@ -347,8 +356,8 @@ def run_ours(args, rank, world):
         ev[2].record(stream)
         Z = qmlr.sorf(x, b.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
         ev[3].record(stream)
-        if precision == qmlr.GRAM_BF16X6:
-            zt = qmlr.gram_operand(Z, 3)
+        if precision in (qmlr.GRAM_BF16X3, qmlr.GRAM_BF16X6):
+            zt = qmlr.gram_operand(Z, 2 if precision == qmlr.GRAM_BF16X3 else 3)
             ev[7].record(stream)
             G = qmlr.gram(Z, precision, operand=zt)
             del zt
@@ -357,7 +366,9 @@ def run_ours(args, rank, world):
             G = qmlr.gram(Z, precision)
         ev[4].record(stream)
         alpha, it, rel = qmlr.gram_solve(G, Z, yv, w.lam, method=qmlr.SOLVE_PCG,
-                                         max_iter=args.pcg_iters, tol=args.pcg_tol, factor=factor)
+                                         max_iter=args.pcg_iters if precision != qmlr.GRAM_FP32 else 4 * args.pcg_iters,
+                                         tol=args.pcg_tol, factor=factor,
+                                         shift=pipeline.DEFAULT_SHIFT[precision])
         ev[5].record(stream)
         model.set_alpha_device(alpha)
         E, F = model.predict(b.coords, b.elem, b.mol_ptr)
@@ -460,16 +471,19 @@ def run_ours(args, rank, world):
     nf = w.n_features
     rows = n_mol
     bf16_sust = peaks.get("bf16_tflops_sustained", 1707.8)
+    n_split = 2 if GRAM_FORM == 1 else 3
+    n_prod = 3 if n_split == 2 else 6
     fp32_add_peak = 36.9   # T FP32 adds/s, measured (profiles/gb300_unit_rates.md)
     n_stack = nf // w.d
     sorf_ops_atom = n_stack * w.n_transform * w.d * int(math.log2(w.d)) + 6 * nf
     cands = {
-        "gram": {"kernel": "tc::gram_split_kernel<3> (3-way BF16 split, tcgen05)", "bound": "tensor",
-                 "achieved": rows * nf * nf / (st["gram"] * 1e-3) / 1e12, "peak": bf16_sust / 6.0,
+        "gram": {"kernel": f"tc::gram_split_kernel<{n_split}> ({n_split}-way BF16 split, tcgen05)",
+                 "bound": "tensor",
+                 "achieved": rows * nf * nf / (st["gram"] * 1e-3) / 1e12, "peak": bf16_sust / n_prod,
                  "unit": "TFLOP/s",
                  "work": f"N_rows*N_F^2 = {rows * nf * nf:.3e} flop (symmetric half, 2 flop/MAC)",
-                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained / 6 (six BF16 products per "
-                                "FP32-accurate product)"},
+                 "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained / {n_prod} ({n_prod} BF16 "
+                                "products per split product)"},
         "sorf_Z": {"kernel": "qmlr::sorf_mol_kernel<128> (SORF + segment sum into Z)", "bound": "alu",
                    "achieved": sorf_ops_atom * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": fp32_add_peak,
                    "unit": "TFLOP/s",
@@ -482,17 +496,18 @@ def run_ours(args, rank, world):
         c["traffic"] = None
     dom = max(cands, key=lambda k: st[k])
     roof = dict(cands[dom])
-    tr = measured_traffic(dom)
+    tr = measured_traffic(dom, roof["kernel"])
     if tr is not None:
         roof["traffic"] = tr["bytes_per_launch"]
         roof["traffic_source"] = tr["summary"]
     line = {
         "metric": METRIC, "value": ms * 1e3 / n_atoms, "unit": "us/atom", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 features, bf16x6 gram, f64 solve", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": f"f32 features, bf16 {n_split}-way split gram, f64 solve", "data": "synthetic",
         "config": {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
                    "n_molecules": n_mol, "n_atoms": n_atoms, "n_features": nf, "d": w.d,
-                   "n_transform": w.n_transform, "gram": "3-way bf16 split, 6 tcgen05 products, per-K-block FP32 Kahan promotion",
+                   "n_transform": w.n_transform, "gram": f"{n_split}-way bf16 split, {n_prod} tcgen05 products, per-K-block FP32 Kahan promotion "
+                           "(preconditioner input)",
                    "solve": ("mixed-precision cholesky (fp64 panels, tcgen05 trailing updates)"
                              if args.factor == "mixed" else "fp64 cholesky") + " + pcg (exact fp64 operator)",
                    "parallelism": "replicas" if world > 1 else "single",
@@ -532,7 +547,9 @@ def run_ours(args, rank, world):
 
 
 def main():
+    global GRAM_FORM
     args = parse()
+    GRAM_FORM = 1 if args.gram_split == 2 else 2
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -77,17 +77,28 @@ def feature_matrix(batch: Batch, spec: FeatureSpec, U, rep=None, perm=None, offs
     return qmlr.sorf(x, batch.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
 
 
-def solve(Z, y, lam: float, precision: int = qmlr.GRAM_BF16X6, method: int = qmlr.SOLVE_PCG,
-          max_iter: int = 50, tol: float = 1e-10, shift: float = -2.0 ** -16,
+# Relative diagonal shift of the preconditioner factor for each Gram form: the
+# smallest power of two at which the mixed-precision factor of the QM9-shaped
+# Gram (100 000 x 16384) stays positive definite (a smaller one fails a pivot
+# and the solve refactorises with a tenfold shift).
+DEFAULT_SHIFT = {qmlr.GRAM_BF16X3: -2.0 ** -15, qmlr.GRAM_BF16X6: -2.0 ** -16, qmlr.GRAM_FP32: -2.0 ** -13}
+
+
+def solve(Z, y, lam: float, precision: int = qmlr.GRAM_BF16X3, method: int = qmlr.SOLVE_PCG,
+          max_iter: int = 50, tol: float = 1e-10, shift: float | None = None,
           factor: int = qmlr.FACTOR_MIXED):
-    """alpha (float64) of (Z^T Z + lam I) alpha = Z^T y; returns (alpha, iterations, rel. residual)."""
+    """alpha (float64) of (Z^T Z + lam I) alpha = Z^T y; returns (alpha, iterations, rel. residual).
+    The Gram (2-way BF16 split by default) only builds the preconditioner; the
+    converged alpha is fixed by the exact operator."""
+    if shift is None:
+        shift = DEFAULT_SHIFT[precision]
     G = qmlr.gram(Z, precision)
     return qmlr.gram_solve(G, Z, y, lam, method=method, max_iter=max_iter, tol=tol, shift=shift,
                            factor=factor)
 
 
 def train_energy(batch: Batch, energies, spec: FeatureSpec, lam: float, U=None,
-                 precision: int = qmlr.GRAM_BF16X6, **solve_kw):
+                 precision: int = qmlr.GRAM_BF16X3, **solve_kw):
     """Energy-only training: returns (alpha, U, iterations, relative residual)."""
     rep, perm, offs = representations(batch, spec)
     if U is None:
@@ -118,7 +129,7 @@ def energy_force_rows(batch: Batch, spec: FeatureSpec, U):
 
 
 def train_energy_force(batch: Batch, energies, forces, spec: FeatureSpec, lam: float, U=None,
-                       precision: int = qmlr.GRAM_BF16X6, **solve_kw):
+                       precision: int = qmlr.GRAM_BF16X3, **solve_kw):
     """Energy + force training: returns (alpha, U, iterations, relative residual)."""
     if U is None:
         rep, perm, offs = representations(batch, spec)
