@@ -466,6 +466,22 @@ int qmlr_predict_ef(qmlr_model* m, const float* coords, const int32_t* elem,
                     const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms, double* energies,
                     float* forces, void* stream);
 
+/*
+ * qmlr_predict_ef in two calls, for overlapping the part that does not depend
+ * on the weights with other work (e.g. the solve that produces them):
+ * qmlr_predict_features computes the representations, element grouping and
+ * projections of the batch into the model's workspace;
+ * qmlr_predict_ef_from_features then forms energies (and forces) from them with
+ * the model's current weights. The second call must get the same batch, on a
+ * stream ordered after the first, with no other prediction through the same
+ * model in between. Same results as qmlr_predict_ef (bitwise).
+ */
+int qmlr_predict_features(qmlr_model* m, const float* coords, const int32_t* elem,
+                          const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms, void* stream);
+int qmlr_predict_ef_from_features(qmlr_model* m, const float* coords, const int32_t* elem,
+                                  const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+                                  double* energies, float* forces, void* stream);
+
 /* ------------------------------------------------------------------------
  * Continuous-batching server for energy + force prediction (the timings
  * section's observation that single configurations leave the GPU idle and

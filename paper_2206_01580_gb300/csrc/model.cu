@@ -78,20 +78,34 @@ int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords,
                w.cap_atoms);
   QMLR_REQUIRE(energies || n_mol == 0, "energies is NULL");
   if (n_mol == 0) return QMLR_OK;
-  void* stream = s;
   int rc;
-  const int n_el = m->p.n_el;
   if (n_atoms == 0) {
     QMLR_CUDA_TRY(cudaMemsetAsync(energies, 0, sizeof(double) * n_mol, s));
     return QMLR_OK;
   }
+  if ((rc = predict_features_ws(m, w, coords, elem, mol_ptr, n_mol, n_atoms, s))) return rc;
+  return predict_from_features_ws(m, w, coords, elem, mol_ptr, n_mol, n_atoms, energies, forces, s);
+}
+
+int predict_features_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
+                        const int32_t* mol_ptr, int n_mol, int n_atoms, cudaStream_t s) {
+  void* stream = s;
+  int rc;
+  const int n_el = m->p.n_el;
   if ((rc = qmlr_fchl19(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.rep, m->rep_ld, stream)))
     return rc;
   if ((rc = qmlr_group_by_element(elem, n_atoms, n_el, w.perm, w.offs, w.gwork, w.gwork_bytes, stream)))
     return rc;
-  if ((rc = proj_tc_launch(w.rep, m->rep_ld, m->rep_dim, 1, 0, m->Ufwd, m->d, w.perm, w.offs, n_atoms, n_el, w.x,
-                           m->d, m->d, s)))
-    return rc;
+  return proj_tc_launch(w.rep, m->rep_ld, m->rep_dim, 1, 0, m->Ufwd, m->d, w.perm, w.offs, n_atoms, n_el, w.x,
+                        m->d, m->d, s);
+}
+
+int predict_from_features_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
+                             const int32_t* mol_ptr, int n_mol, int n_atoms, double* energies, float* forces,
+                             cudaStream_t s) {
+  void* stream = s;
+  int rc;
+  const int n_el = m->p.n_el;
   QMLR_REQUIRE(n_mol <= w.cap_mols, "batch of %d molecules exceeds the reserved capacity %d", n_mol, w.cap_mols);
   if ((rc = sorf_energy_grad_model(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->bT, m->n_features,
                                    m->sigma, m->alphaT, w.atom_e, energies, forces ? w.gx : nullptr, s)))
@@ -236,4 +250,31 @@ extern "C" int qmlr_predict_ef(qmlr_model* m, const float* coords, const int32_t
                                double* energies, float* forces, void* stream) {
   QMLR_REQUIRE(m, "model is NULL");
   return predict_ef_ws(m, m->ws, coords, elem, mol_ptr, n_mol, n_atoms, energies, forces, as_stream(stream));
+}
+
+static int check_batch(const qmlr_model* m, int n_mol, int n_atoms) {
+  QMLR_REQUIRE(n_atoms >= 1 && n_mol >= 1, "the split prediction needs a non-empty batch");
+  QMLR_REQUIRE(n_atoms <= m->ws.cap_atoms,
+               "batch of %d atoms exceeds the reserved capacity %d (call qmlr_model_reserve)", n_atoms,
+               m->ws.cap_atoms);
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_predict_features(qmlr_model* m, const float* coords, const int32_t* elem,
+                                     const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms, void* stream) {
+  QMLR_REQUIRE(m, "model is NULL");
+  int rc = check_batch(m, n_mol, n_atoms);
+  if (rc) return rc;
+  return predict_features_ws(m, m->ws, coords, elem, mol_ptr, n_mol, n_atoms, as_stream(stream));
+}
+
+extern "C" int qmlr_predict_ef_from_features(qmlr_model* m, const float* coords, const int32_t* elem,
+                                             const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+                                             double* energies, float* forces, void* stream) {
+  QMLR_REQUIRE(m, "model is NULL");
+  QMLR_REQUIRE(energies, "energies is NULL");
+  int rc = check_batch(m, n_mol, n_atoms);
+  if (rc) return rc;
+  return predict_from_features_ws(m, m->ws, coords, elem, mol_ptr, n_mol, n_atoms, energies, forces,
+                                  as_stream(stream));
 }

@@ -41,6 +41,15 @@ int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_strid
                    const int32_t* perm, const int32_t* elem_offsets, int n_atoms, int n_el, float* C, int ldc,
                    int zero_pad_to, cudaStream_t s);
 
+// The two halves of predict_ef_ws: the representation, element grouping and
+// projection (independent of the weights), then the SORF energies/gradients,
+// the transposed projection and the VJP from those features.
+int predict_features_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
+                        const int32_t* mol_ptr, int n_mol, int n_atoms, cudaStream_t s);
+int predict_from_features_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
+                             const int32_t* mol_ptr, int n_mol, int n_atoms, double* energies, float* forces,
+                             cudaStream_t s);
+
 // Energies and forces of a CSR batch with the given workspace (no allocation).
 int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
                   const int32_t* mol_ptr, int n_mol, int n_atoms, double* energies, float* forces,

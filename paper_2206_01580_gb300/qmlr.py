@@ -102,6 +102,8 @@ _SIGS = {
     "qmlr_model_set_alpha_device": (C.c_int, [VP, P, VP]),
     "qmlr_model_reserve": (C.c_int, [VP, I32]),
     "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
+    "qmlr_predict_features": (C.c_int, [VP, P, P, P, I32, I32, VP]),
+    "qmlr_predict_ef_from_features": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
     "qmlr_serve_create": (C.c_int, [VP, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]),
     "qmlr_serve_submit": (C.c_int, [VP, P, P, I32, C.POINTER(C.c_uint64)]),
     "qmlr_serve_poll": (C.c_int, [VP, C.c_uint64, P, P, I64]),
@@ -504,6 +506,29 @@ class Model:
             E, F = out
         _check(lib().qmlr_predict_ef(self.handle, _ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol, n_atoms,
                                      _ptr(E), _ptr(F), _stream()))
+        return E, F
+
+    def predict_features(self, coords, elem, mol_ptr):
+        """First half of predict (representations, grouping, projection) on the
+        current stream; independent of the weights."""
+        coords = _dev(coords, torch.float32)
+        elem = _dev(elem, torch.int32)
+        mol_ptr = _dev(mol_ptr, torch.int32)
+        n_atoms, n_mol = coords.shape[0], mol_ptr.shape[0] - 1
+        self.reserve(n_atoms)
+        _check(lib().qmlr_predict_features(self.handle, _ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol, n_atoms,
+                                           _stream()))
+
+    def predict_from_features(self, coords, elem, mol_ptr, forces: bool = True):
+        """Second half of predict for the batch given to predict_features."""
+        coords = _dev(coords, torch.float32)
+        elem = _dev(elem, torch.int32)
+        mol_ptr = _dev(mol_ptr, torch.int32)
+        n_atoms, n_mol = coords.shape[0], mol_ptr.shape[0] - 1
+        E = torch.empty(n_mol, device="cuda", dtype=torch.float64)
+        F = torch.empty((n_atoms, 3), device="cuda", dtype=torch.float32) if forces else None
+        _check(lib().qmlr_predict_ef_from_features(self.handle, _ptr(coords), _ptr(elem), _ptr(mol_ptr), n_mol,
+                                                   n_atoms, _ptr(E), _ptr(F), _stream()))
         return E, F
 
     def close(self):

@@ -136,3 +136,28 @@ def test_energy_training_matches_oracle_mae(q):
     mae_g = np.mean(np.abs(o_model.energies_forces(test_mols.coords, test_mols.elem, test_mols.mol_ptr, om,
                                                    forces=False) - E_test))
     assert abs(mae_g - mae_o) <= 0.01 * mae_o, (mae_g, mae_o)
+
+
+def test_split_prediction_matches_one_call():
+    """qmlr_predict_features + qmlr_predict_ef_from_features give the results
+    of qmlr_predict_ef bitwise, also with the first half on another stream."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_01580_gb300 import qmlr
+    from paper_2206_01580_gb300.params import from_table
+    mols = synth.serving_molecules(synth.rng_for(4, 33), 30, lo=5, hi=60)
+    rng = np.random.default_rng(3)
+    p = from_table("EF", n2=24, n3=22)
+    U = (rng.normal(size=(5, 780, 64)) * 0.05).astype(np.float32)
+    signs, b = synth.sorf_draw(rng, 1024, 64, 3)
+    alpha = (rng.normal(size=1024) * 0.02).astype(np.float32)
+    model = qmlr.Model(p, 60, U, signs, 3, b.astype(np.float32), 2.0, alpha)
+    E1, F1 = model.predict(mols.coords, mols.elem, mols.mol_ptr)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        model.predict_features(mols.coords, mols.elem, mols.mol_ptr)
+    torch.cuda.current_stream().wait_stream(side)
+    E2, F2 = model.predict_from_features(mols.coords, mols.elem, mols.mol_ptr)
+    torch.cuda.synchronize()
+    assert torch.equal(E1, E2) and torch.equal(F1, F2)
+    model.close()
