@@ -282,7 +282,8 @@ constexpr int kPanelK = 256;
 
 __global__ void __launch_bounds__(kThreads, 1)
 syrk_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
-               const __grid_constant__ CUtensorMap map2, int m, double* __restrict__ A, long lda, int* err) {
+               const __grid_constant__ CUtensorMap map2, int m, double* __restrict__ A, long lda, int part,
+               int* err) {
   using C = Cfg<3>;
   constexpr int BN = C::BN, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES, NST = C::STAGES_N;
   constexpr int k_blocks = kPanelK / BK;
@@ -298,12 +299,30 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__
   volatile int* never_abort = abort + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // lower-triangle tile (bi >= bj) of this CTA
-  const int t = blockIdx.x;
-  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while (bi * (bi + 1) / 2 > t) --bi;
-  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-  const int bj = t - bi * (bi + 1) / 2;
+  // lower-triangle tile (bi >= bj) of this CTA: part 0 = all tiles, part 1 =
+  // the first two tile columns (the next panel's columns), part 2 = the rest
+  const int T = (m + BM - 1) / BM;
+  int bi, bj;
+  if (part == 1) {
+    const int t = blockIdx.x;
+    if (t < T) {
+      bi = t;
+      bj = 0;
+    } else {
+      bi = 1 + (t - T);
+      bj = 1;
+    }
+  } else {
+    const int t = blockIdx.x;
+    bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (bi * (bi + 1) / 2 > t) --bi;
+    while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    bj = t - bi * (bi + 1) / 2;
+    if (part == 2) {
+      bi += 2;
+      bj += 2;
+    }
+  }
   const int i0 = bi * BM, j0 = bj * BN;
 
   if (threadIdx.x == 0) {
@@ -481,7 +500,8 @@ static int launch_split(const uint16_t* zt, long k_pad, int n_features, float* G
   return QMLR_OK;
 }
 
-static int launch_syrk(const uint16_t* parts, long part_elems, int m, double* A, long lda, cudaStream_t s) {
+static int launch_syrk(const uint16_t* parts, long part_elems, int m, double* A, long lda, int part,
+                       cudaStream_t s) {
   using C = Cfg<3>;
   const int T = (m + BM - 1) / BM;
   QMLR_REQUIRE(part_elems >= (long)T * BM * kPanelK, "panel operand smaller than its padded rows");
@@ -496,8 +516,12 @@ static int launch_syrk(const uint16_t* parts, long part_elems, int m, double* A,
                                        C::SMEM_BYTES));
     attr = true;
   }
-  syrk_tc_kernel<<<T * (T + 1) / 2, kThreads, C::SMEM_BYTES, s>>>(mp[0], mp[1], mp[2], m, A, lda,
-                                                                  device_error_ptr());
+  int tiles = T * (T + 1) / 2;
+  if (part == 1) tiles = T >= 2 ? 2 * T - 1 : T;
+  if (part == 2) tiles = T > 2 ? (T - 2) * (T - 1) / 2 : 0;
+  if (tiles == 0) return QMLR_OK;
+  syrk_tc_kernel<<<tiles, kThreads, C::SMEM_BYTES, s>>>(mp[0], mp[1], mp[2], m, A, lda, part,
+                                                        device_error_ptr());
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }
@@ -513,9 +537,9 @@ int gram_split_tc(int n_split, const uint16_t* zt, long k_pad, int n_features, f
                       : tc::launch_split<3>(zt, k_pad, n_features, G, s);
 }
 
-int syrk_tc(const uint16_t* parts, long part_elems, int m, double* A, long lda, cudaStream_t s) {
+int syrk_tc(const uint16_t* parts, long part_elems, int m, double* A, long lda, int part, cudaStream_t s) {
   if (m <= 0) return QMLR_OK;
-  return tc::launch_syrk(parts, part_elems, m, A, lda, s);
+  return tc::launch_syrk(parts, part_elems, m, A, lda, part, s);
 }
 
 }  // namespace qmlr

@@ -19,7 +19,8 @@ namespace qmlr {
 constexpr int NB = 64;
 
 // tensor-core trailing update (gram_tc.cu)
-int syrk_tc(const uint16_t* parts, long part_elems, int m, double* A, long lda, cudaStream_t s);
+// part 0: all lower tiles; 1: the first two 128-wide tile columns; 2: the others
+int syrk_tc(const uint16_t* parts, long part_elems, int m, double* A, long lda, int part, cudaStream_t s);
 
 // A = G + (lambda + shift) I in FP64, lower triangle (G symmetric fp32 [n][n]).
 __global__ void assemble_kernel(const float* __restrict__ G, int n, double diag,
@@ -988,6 +989,28 @@ static size_t tc_parts_elems(int n) {
   return (size_t)3 * m_pad * kTcPanel;
 }
 
+// Side stream (highest priority) and events of the mixed factor's lookahead, per device.
+struct Lookahead {
+  cudaStream_t panel = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+static int lookahead(Lookahead** out) {
+  static Lookahead la[64];
+  int dev = 0;
+  QMLR_CUDA_TRY(cudaGetDevice(&dev));
+  QMLR_REQUIRE(dev >= 0 && dev < 64, "device index out of range");
+  Lookahead& l = la[dev];
+  if (!l.panel) {
+    int lo = 0, hi = 0;
+    QMLR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    QMLR_CUDA_TRY(cudaStreamCreateWithPriority(&l.panel, cudaStreamNonBlocking, hi));
+    for (int k = 0; k < 4; ++k) QMLR_CUDA_TRY(cudaEventCreateWithFlags(&l.ev[k], cudaEventDisableTiming));
+  }
+  *out = &l;
+  return QMLR_OK;
+}
+
 // Mixed-precision factor (the preconditioner of the ridge solve): right-looking
 // with 256-column panels. On entry the lower triangle holds float pairs. A
 // panel's 64-column blocks are converted to FP64 in turn, factorised (diagonal
@@ -995,8 +1018,11 @@ static size_t tc_parts_elems(int n) {
 // columns in double-float arithmetic; the update of the remaining matrix by
 // the whole panel runs on the tensor cores from the panel's 3-way BF16 split
 // (products to ~2^-24 relative, FP32 sums per 64-deep K block, subtracted from
-// the float pairs).
-static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts, cudaStream_t s, int* info) {
+// the float pairs). Lookahead: the tensor-core update is issued in two parts,
+// first the next panel's columns, then the rest; the next panel's FP64 work
+// runs on a high-priority side stream beside the second part (the two touch
+// disjoint columns). Two split buffers alternate between panels.
+static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts2, cudaStream_t s, int* info) {
   int* err = device_error_ptr();
   static bool attr = false;
   if (!attr) {
@@ -1006,27 +1032,36 @@ static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts, cuda
                                        (int)kTrsmSmem));
     attr = true;
   }
-  // the solved 64-column block rows as float pairs, in the (then idle) split buffer
-  float2* lp = reinterpret_cast<float2*>(parts);
+  Lookahead* la = nullptr;
+  int rc = lookahead(&la);
+  if (rc) return rc;
+  cudaStream_t p = la->panel;
+  cudaEvent_t ev_start = la->ev[0], ev_split = la->ev[1], ev_next = la->ev[2], ev_end = la->ev[3];
+  const size_t half = tc_parts_elems(n);
+  QMLR_CUDA_TRY(cudaEventRecord(ev_start, s));
+  QMLR_CUDA_TRY(cudaStreamWaitEvent(p, ev_start, 0));
   for (int k0 = 0; k0 < n; k0 += kTcPanel) {
     const int w = std::min(kTcPanel, n - k0);
+    __nv_bfloat16* parts = parts2 + ((k0 / kTcPanel) & 1) * half;
+    // the solved 64-column block rows as float pairs, in the (then idle) split buffer
+    float2* lp = reinterpret_cast<float2*>(parts);
     for (int c0 = k0; c0 < k0 + w; c0 += NB) {
       const int nb = std::min(NB, n - c0);
       const long conv = (long)(n - c0) * nb;
-      pairs_to_fp64_kernel<<<(unsigned)((conv + 255) / 256), 256, 0, s>>>(L, ldl, c0, nb, n);
+      pairs_to_fp64_kernel<<<(unsigned)((conv + 255) / 256), 256, 0, p>>>(L, ldl, c0, nb, n);
       QMLR_LAUNCH_CHECK();
-      potrf_diag_kernel<<<1, 256, 0, s>>>(L, ldl, c0, nb, err, info);
+      potrf_diag_kernel<<<1, 256, 0, p>>>(L, ldl, c0, nb, err, info);
       QMLR_LAUNCH_CHECK();
       const int rows = n - c0 - nb;
       if (rows <= 0) break;
       const int cblocks = (k0 + w - (c0 + nb) + NB - 1) / NB;   // panel columns still to update
-      trsm_panel_kernel<<<(rows + kTrsmRows - 1) / kTrsmRows, 256, kTrsmSmem, s>>>(
+      trsm_panel_kernel<<<(rows + kTrsmRows - 1) / kTrsmRows, 256, kTrsmSmem, p>>>(
           L, ldl, c0, nb, n, cblocks > 0 ? lp : nullptr);
       QMLR_LAUNCH_CHECK();
       if (cblocks > 0) {
         const int T = (rows + NB - 1) / NB;
         const int tiles = cblocks * T - cblocks * (cblocks - 1) / 2;
-        syrk_pairs_kernel<<<tiles, 256, kPairsSmem, s>>>(L, ldl, c0, nb, n, cblocks, lp);
+        syrk_pairs_kernel<<<tiles, 256, kPairsSmem, p>>>(L, ldl, c0, nb, n, cblocks, lp);
         QMLR_LAUNCH_CHECK();
       }
     }
@@ -1034,13 +1069,22 @@ static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts, cuda
     if (m <= 0) break;
     const int m_pad = (m + 127) / 128 * 128;
     const long total = (long)m_pad * kTcPanel;
-    panel_split_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(L, ldl, r0, k0, m, m_pad, parts);
+    panel_split_kernel<<<(unsigned)((total + 255) / 256), 256, 0, p>>>(L, ldl, r0, k0, m, m_pad, parts);
     QMLR_LAUNCH_CHECK();
-    int rc = syrk_tc(reinterpret_cast<const uint16_t*>(parts), total, m, L + (long)r0 * ldl + r0, ldl, s);
-    if (rc) return rc;
+    QMLR_CUDA_TRY(cudaEventRecord(ev_split, p));
+    QMLR_CUDA_TRY(cudaStreamWaitEvent(s, ev_split, 0));
+    double* A = L + (long)r0 * ldl + r0;
+    const uint16_t* pu = reinterpret_cast<const uint16_t*>(parts);
+    if ((rc = syrk_tc(pu, total, m, A, ldl, 1, s))) return rc;   // the next panel's columns
+    QMLR_CUDA_TRY(cudaEventRecord(ev_next, s));
+    QMLR_CUDA_TRY(cudaStreamWaitEvent(p, ev_next, 0));
+    if ((rc = syrk_tc(pu, total, m, A, ldl, 2, s))) return rc;   // the rest, beside the next panel
   }
+  QMLR_CUDA_TRY(cudaEventRecord(ev_end, p));
+  QMLR_CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
   return QMLR_OK;
 }
+
 
 // Grid of the dataflow sweeps (all CTAs co-resident) and their flag words on
 // the current device; 0 when cooperative launch is not available.
@@ -1165,7 +1209,7 @@ extern "C" int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features
          + std::max<int64_t>(n_rows, 1) * 16  // t = Z p and its float pair
          + n * 8                   // float pair of the operand
          + 6 * n * 8               // c, r, z, p, q, tmp
-         + (int64_t)tc_parts_elems((int)n) * 2   // split panel of the mixed-precision factor
+         + (int64_t)tc_parts_elems((int)n) * 4   // two split panels of the mixed-precision factor
          + 8 * 8 + 8192;           // scalars + alignment
 }
 
@@ -1188,7 +1232,7 @@ extern "C" int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_in
 
 extern "C" int64_t qmlr_cholesky_mixed_workspace_bytes(int32_t n) {
   if (n < 1) return 0;
-  return (int64_t)tc_parts_elems(n) * 2 + 256;
+  return (int64_t)tc_parts_elems(n) * 4 + 256;
 }
 
 extern "C" int qmlr_cholesky_mixed(double* L, int64_t ldl, int32_t n, void* work, int64_t work_bytes,
@@ -1307,7 +1351,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   carve(p, &vq, (size_t)n * 8);
   carve(p, &vtmp, (size_t)n * 8);
   carve(p, &vsc, 8 * 8);
-  carve(p, &vsplit, tc_parts_elems(n) * 2);
+  carve(p, &vsplit, tc_parts_elems(n) * 4);
   carve(p, &vth, (size_t)std::max<int64_t>(n_rows, 1) * 8);
   carve(p, &vph, (size_t)n * 8);
   c.L = static_cast<double*>(vL);
