@@ -152,11 +152,13 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
   } else if (warp == kDrainWarps + 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    int pa[C::NP], pb[C::NP];
+    // descriptors of stage 0's split parts; a stage adds STAGE_BYTES >> 4 and a
+    // 16-element K step adds 32 >> 4 = 2 to the start-address field
+    uint64_t da[S], db[S];
 #pragma unroll
-    for (int q = 0; q < C::NP; ++q) {
-      pa[q] = kProdA[q];
-      pb[q] = kProdB[q];
+    for (int q = 0; q < S; ++q) {
+      da[q] = smem_desc(smem + q * A_BYTES);
+      db[q] = smem_desc(smem + S * A_BYTES + q * B_BYTES);
     }
     for (int kb = 0; kb < k_blocks; ++kb) {
       const int st = kb % NST;
@@ -170,20 +172,20 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint8_t* sp = smem + st * STAGE_BYTES;
+      const uint64_t so = (uint64_t)(st * (STAGE_BYTES >> 4));
       const uint32_t d = tmem + buf * BN;
       // smallest split products first, S0'S0 last: every accumulator add
       // truncates relative to the running sum, so the many small terms are
       // added while that sum is still small (4 of the 4 * NP adds are large).
 #pragma unroll
       for (int q = C::NP - 1; q >= 0; --q) {
+        // (a-part, b-part) of product q: (0,0) (0,1) (1,0) (0,2) (2,0) (1,1), as compile-time indices
+        const int qa = q == 2 ? 1 : (q == 4 ? 2 : (q == 5 ? 1 : 0));
+        const int qb = q == 1 ? 1 : (q == 3 ? 2 : (q == 5 ? 1 : 0));
+        const uint64_t a0 = da[qa] + so, b0 = db[qb] + so;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const int off = kk * 32;   // 16 bf16 along K inside the 128-byte swizzled row
-          const uint8_t* a = sp + pa[q] * A_BYTES + off;
-          const uint8_t* b = sp + S * A_BYTES + pb[q] * B_BYTES + off;
-          mma_bf16(d, smem_desc(a), smem_desc(b), idesc, (kk > 0 || q < C::NP - 1) ? 1u : 0u);
-        }
+        for (int kk = 0; kk < BK / 16; ++kk)
+          mma_bf16(d, a0 + 2 * kk, b0 + 2 * kk, idesc, (kk > 0 || q < C::NP - 1) ? 1u : 0u);
       }
       mma_commit(&empty[st]);   // frees the smem stage once these MMAs have read it
       mma_commit(&accf[buf]);   // accumulator of this K block is ready
