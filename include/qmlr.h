@@ -483,6 +483,24 @@ int qmlr_predict_ef_from_features(qmlr_model* m, const float* coords, const int3
                                   double* energies, float* forces, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Diagnostics: throughput of single functional units on the current device
+ * (the denominators of the ALU-bound kernels' rooflines). Each rate is
+ * operations per second of one kind, issued independently by 8 CTAs of 256
+ * threads per SM (CUDA events, 5 launches after a warm-up); synchronous.
+ * ------------------------------------------------------------------------ */
+enum {
+  QMLR_RATE_DFMA = 0,    /* FP64 fused multiply-adds */
+  QMLR_RATE_FFMA = 1,    /* FP32 fused multiply-adds */
+  QMLR_RATE_FADD = 2,    /* FP32 adds */
+  QMLR_RATE_FADD_X2 = 3, /* FP32 element adds issued as packed add.rn.f32x2 */
+  QMLR_RATE_EXP = 4,     /* __expf */
+  QMLR_RATE_SIN = 5,     /* __sinf */
+  QMLR_RATE_SHFL = 6,    /* 32-bit warp shuffles (per lane) */
+  QMLR_RATE_COUNT = 7
+};
+int qmlr_unit_rates(double* host_rates, int32_t n_rates, void* stream);
+
+/* ------------------------------------------------------------------------
  * Continuous-batching server for energy + force prediction (the timings
  * section's observation that single configurations leave the GPU idle and
  * batching cuts the cost per configuration). Host-side runtime in the library.

@@ -102,6 +102,7 @@ _SIGS = {
     "qmlr_model_set_alpha_device": (C.c_int, [VP, P, VP]),
     "qmlr_model_reserve": (C.c_int, [VP, I32]),
     "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
+    "qmlr_unit_rates": (C.c_int, [P, I32, VP]),
     "qmlr_predict_features": (C.c_int, [VP, P, P, P, I32, I32, VP]),
     "qmlr_predict_ef_from_features": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
     "qmlr_serve_create": (C.c_int, [VP, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]),
@@ -436,6 +437,16 @@ def gram_solve(G, Z, y, lam: float, method: int = SOLVE_PCG, max_iter: int = 50,
 
 
 last_solve = None
+
+
+UNIT_RATES = ("dfma", "ffma", "fadd", "fadd_x2", "expf", "sinf", "shfl")
+
+
+def unit_rates() -> dict:
+    """Measured per-unit throughput of the current GPU (operations per second)."""
+    out = (C.c_double * len(UNIT_RATES))()
+    _check(lib().qmlr_unit_rates(out, len(UNIT_RATES), _stream()))
+    return dict(zip(UNIT_RATES, list(out)))
 
 
 def launch_count() -> int:

@@ -211,3 +211,15 @@ def test_ridge_solve_underdetermined_with_shift(q):
     pz = Z.astype(np.float64) @ alpha.cpu().numpy()
     pr = Z.astype(np.float64) @ alpha_ref
     assert np.max(np.abs(pz - pr)) <= 1e-6 * np.max(np.abs(pr))
+
+
+def test_unit_rates_are_plausible(q):
+    """The diagnostic unit-rate probe: FP32 FMA and add rates within a factor of
+    SMs x 128 lanes x clock, FP64 far below FP32, all rates positive."""
+    r = q.unit_rates()
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2.2e9
+    assert all(v > 0 and math.isfinite(v) for v in r.values())
+    assert 0.2 * nominal < r["ffma"] < 1.2 * nominal
+    assert 0.2 * nominal < r["fadd"] < 1.2 * nominal
+    assert r["dfma"] < r["ffma"]
