@@ -282,6 +282,202 @@ proj_tc_kernel(const __grid_constant__ CUtensorMap bmap, Args a) {
   }
 }
 
+// Short-K form (K_pad <= 128, the transposed projection g_rho = U_e g_x): the
+// CTA splits its 128 gathered rows once into shared memory (two K blocks stay
+// resident) and walks all output column tiles, streaming the basis tiles through
+// a 2-stage TMA ring; two TMEM accumulators alternate between column tiles so
+// that the drain of one overlaps the products of the next.
+constexpr int RK = 2;                                         // resident K blocks
+constexpr int R_A_BYTES = RK * 3 * A_BYTES;                   // 96 KB
+constexpr int R_STAGE = 3 * B_BYTES;                          // 48 KB per K block of a column tile
+constexpr int R_NST = 2;
+constexpr int R_SMEM_BYTES = R_A_BYTES + R_NST * R_STAGE + 1024 + 1024;
+
+__global__ void __launch_bounds__(kThreads, 1)
+proj_tc_resident_kernel(const __grid_constant__ CUtensorMap bmap, Args a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* As = smem;                                          // [RK][3][A_BYTES]
+  uint8_t* Bs = smem + R_A_BYTES;                              // [R_NST][3][B_BYTES]
+  uint64_t* full = reinterpret_cast<uint64_t*>(Bs + R_NST * R_STAGE);
+  uint64_t* empty = full + R_NST;
+  uint64_t* accf = empty + R_NST;      // [2]
+  uint64_t* acce = accf + 2;           // [2]
+  uint64_t* aready = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(aready + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* never_abort = abort + 1;
+  int* rows = const_cast<int*>(reinterpret_cast<volatile int*>(never_abort + 1));   // [BM]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  int e = -1, tile = blockIdx.x, start = 0, count = 0;
+  for (int k = 0; k < a.n_el; ++k) {
+    const int s0 = a.elem_offsets[k], cnt = a.elem_offsets[k + 1] - s0;
+    const int nt = (cnt + BM - 1) / BM;
+    if (tile < nt) {
+      e = k;
+      start = s0 + tile * BM;
+      count = min(BM, cnt - tile * BM);
+      break;
+    }
+    tile -= nt;
+  }
+  if (e < 0) return;   // whole CTA, before any barrier or allocation
+  const int k_blocks = a.K_pad / BK;                           // 1 or 2 (host guarantees <= RK)
+  const int n_tiles = (max(a.N, a.zero_pad_to) + BN - 1) / BN;
+  const int steps = n_tiles * k_blocks;
+
+  if (tid < BM) rows[tid] = tid < count ? a.perm[start + tid] : -1;
+  if (tid == 0) {
+    for (int q = 0; q < R_NST; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], kProd);
+    }
+    mbar_init(aready, 32 * kProd);
+    *abort = 0;
+    *never_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  int last_round[R_NST];
+#pragma unroll
+  for (int q = 0; q < R_NST; ++q) last_round[q] = -1;
+
+  if (warp < kProd) {
+    // ---------------- producers: the rows' K blocks, split once
+    const int r = tid & (BM - 1), h = tid >> 7;
+    const int row = rows[r];
+    const bool vec = ((a.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.A) & 15) == 0) &&
+                     ((a.a_part_stride & 3) == 0);
+    for (int kb = 0; kb < k_blocks; ++kb) {
+      float cur[32];
+      load_row32(a, row, kb * BK + h * 32, vec, cur);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float v8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v8[j] = cur[8 * c + j];
+        store_split_chunk(As + kb * 3 * A_BYTES, r, h * 4 + c, v8);
+      }
+    }
+    fence_proxy_async_smem();
+    mbar_arrive(aready);
+    // ---------------- drain: one column tile per accumulator use
+    const int quarter = warp & 3, half = warp >> 2;
+    const int rr = quarter * 32 + lane;
+    const int orow = rows[rr];
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    for (int nt = 0; nt < n_tiles; ++nt) {
+      const int buf = nt & 1;
+      const uint32_t use = nt >> 1;
+      const bool ok = mbar_wait(&accf[buf], use & 1, abort);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) {
+          record_device_error(a.err, DEV_TIMEOUT);
+          *abort = 1;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int n0 = nt * BN;
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        float v[16];
+        const int col = half * 64 + c4 * 16;
+        tmem_ld16(tmem + lane_base + buf * BN + col, v);
+        if (orow >= 0) {
+          float* dst = a.C + (long)orow * a.ldc + n0 + col;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + col + j;
+            if (n < a.N) dst[j] = v[j];
+            else if (n < a.zero_pad_to) dst[j] = 0.f;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+    }
+  } else if (warp == kProd && lane == 0) {
+    // ---------------- TMA: basis tiles (column tile nt, K block kb) through the ring
+    for (int i = 0; i < steps; ++i) {
+      const int nt = i / k_blocks, kb = i % k_blocks;
+      const int st = i % R_NST;
+      const uint32_t round = i / R_NST;
+      if (i >= R_NST && !mbar_wait(&empty[st], (round - 1) & 1, abort)) {
+        record_device_error(a.err, DEV_TIMEOUT);
+        *abort = 1;
+        break;
+      }
+      uint8_t* sp = Bs + st * R_STAGE;
+      mbar_expect_tx(&full[st], R_STAGE);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        tma_load_2d(sp + q * B_BYTES, &bmap, &full[st], kb * BK, (e * 3 + q) * a.N_pad + nt * BN);
+      last_round[st] = (int)round;
+    }
+  } else if (warp == kProd + 1 && lane == 0) {
+    // ---------------- MMA
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    bool ok = mbar_wait(aready, 0, abort);
+    for (int i = 0; i < steps && ok; ++i) {
+      const int nt = i / k_blocks, kb = i % k_blocks;
+      const int st = i % R_NST;
+      const uint32_t round = i / R_NST;
+      const int buf = nt & 1;
+      const uint32_t use = nt >> 1;
+      if (!mbar_wait(&full[st], round & 1, abort) ||
+          (kb == 0 && use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1, abort))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint8_t* ap = As + kb * 3 * A_BYTES;
+      const uint8_t* bp = Bs + st * R_STAGE;
+      const uint32_t d = tmem + buf * BN;
+#pragma unroll
+      for (int q = 5; q >= 0; --q) {   // smallest split products first
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk)
+          mma_bf16(d, smem_desc(ap + kPA[q] * A_BYTES + kk * 32), smem_desc(bp + kPB[q] * B_BYTES + kk * 32), idesc,
+                   (kb > 0 || q < 5 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[st]);
+      if (kb == k_blocks - 1) mma_commit(&accf[buf]);
+    }
+    if (!ok) {
+      record_device_error(a.err, DEV_TIMEOUT);
+      *abort = 1;
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (*abort) {
+    if (warp == kProd && lane == 0)
+      for (int q = 0; q < R_NST; ++q)
+        if (last_round[q] >= 0) mbar_wait(&full[q], (uint32_t)last_round[q] & 1, never_abort);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+  }
+}
+
 // out[(e*3 + q)*N_pad + n][k] = part q of B_e[k][n] (zero outside K x N), with
 // B_e[k][n] = U[e*es + k*ldu + n] (trans = 0) or U[e*es + n*ldu + k] (trans = 1).
 __global__ void split_basis_kernel(const float* __restrict__ U, int n_el, int K, int N, long es, int ldu,
@@ -344,7 +540,20 @@ int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_strid
   }
   Args a{A, lda, K, n_part, a_part_stride, N, np, kp, perm, elem_offsets, n_el, C, ldc, zero_pad_to,
          device_error_ptr()};
-  dim3 grid((n_atoms + BM - 1) / BM + n_el, (std::max(N, zero_pad_to) + BN - 1) / BN);
+  const int n_tiles = (std::max(N, zero_pad_to) + BN - 1) / BN;
+  if (kp <= RK * BK && n_tiles > 1) {
+    // short K, several column tiles: the CTA keeps its split rows and walks the tiles
+    static bool attr_r = false;
+    if (!attr_r) {
+      QMLR_CUDA_TRY(cudaFuncSetAttribute(proj_tc_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         R_SMEM_BYTES));
+      attr_r = true;
+    }
+    proj_tc_resident_kernel<<<(n_atoms + BM - 1) / BM + n_el, kThreads, R_SMEM_BYTES, s>>>(map, a);
+    QMLR_LAUNCH_CHECK();
+    return QMLR_OK;
+  }
+  dim3 grid((n_atoms + BM - 1) / BM + n_el, n_tiles);
   proj_tc_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map, a);
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
