@@ -396,6 +396,7 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
 // VJP: one CTA per molecule, warps over centre atoms.
 
 struct VjpWarp {
+  float4* stage;  // [64] one chunk of pair contributions (atom index bits, gradient)
   float4* nb_u;   // [mxp]
   float4* nb_2b;  // [mxp]
   float* g;       // [rp]   gradient row of the centre
@@ -404,11 +405,12 @@ struct VjpWarp {
   int* nb_idx;    // [mxp]
 };
 __host__ __device__ __forceinline__ size_t vjp_warp_bytes(int mxp, int rp) {
-  return (size_t)mxp * (16 + 16 + 12 + 4 + 4) + (size_t)rp * 4;
+  return 64 * 16 + (size_t)mxp * (16 + 16 + 12 + 4 + 4) + (size_t)rp * 4;
 }
 __device__ __forceinline__ VjpWarp carve_vjp(char* base, int mxp, int rp) {
   VjpWarp s;
-  s.nb_u = reinterpret_cast<float4*>(base);
+  s.stage = reinterpret_cast<float4*>(base);
+  s.nb_u = s.stage + 64;
   s.nb_2b = s.nb_u + mxp;
   s.g = reinterpret_cast<float*>(s.nb_2b + mxp);
   s.facc = s.g + rp;
@@ -460,8 +462,19 @@ __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts&
   }
   __syncwarp();
 
-  // three-body: lanes over flat neighbour pairs, each lane loops over its radial bins
+  // three-body: lanes over flat neighbour pairs, each lane loops over its radial bins.
+  // The pairs' contributions reach the atoms' accumulators in pair order (j side,
+  // then k side). Molecules of up to 32 atoms keep atom a's accumulator in lane
+  // a's registers, and each lane pulls its atom's entries from the staged chunk;
+  // larger ones broadcast each pair by shuffles to lane 0.
   const int n_pairs = n * (n - 1) / 2;
+  const bool regs = M <= 32;
+  float fa0 = 0.f, fa1 = 0.f, fa2 = 0.f;
+  if (regs && lane < M) {
+    fa0 = s.facc[3 * lane + 0];
+    fa1 = s.facc[3 * lane + 1];
+    fa2 = s.facc[3 * lane + 2];
+  }
   for (int q0 = 0; q0 < n_pairs; q0 += 32) {
     const int q = q0 + lane;
     float gj0 = 0.f, gj1 = 0.f, gj2 = 0.f, gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
@@ -535,8 +548,23 @@ __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts&
         gk2 = dE_db * uk.z + dE_dc * uz;
       }
     }
-    // scatter the j- and k-side gradients in a fixed lane order
     const int cnt = min(32, n_pairs - q0);
+    if (regs) {
+      s.stage[2 * lane] = make_float4(__int_as_float(jl), gj0, gj1, gj2);
+      s.stage[2 * lane + 1] = make_float4(__int_as_float(kl), gk0, gk1, gk2);
+      __syncwarp();
+      for (int e = 0; e < 2 * cnt; ++e) {
+        const float4 v = s.stage[e];
+        if (__float_as_int(v.x) == lane) {
+          fa0 += v.y;
+          fa1 += v.z;
+          fa2 += v.w;
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+    // scatter the j- and k-side gradients in a fixed lane order
     for (int t = 0; t < cnt; ++t) {
       const int jt = __shfl_sync(0xffffffffu, jl, t);
       const int kt = __shfl_sync(0xffffffffu, kl, t);
@@ -554,6 +582,14 @@ __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts&
         s.facc[3 * kt + 1] += v4;
         s.facc[3 * kt + 2] += v5;
       }
+    }
+    __syncwarp();
+  }
+  if (regs) {
+    if (lane < M) {
+      s.facc[3 * lane + 0] = fa0;
+      s.facc[3 * lane + 1] = fa1;
+      s.facc[3 * lane + 2] = fa2;
     }
     __syncwarp();
   }
