@@ -513,7 +513,8 @@ def run_ours(args, rank, world):
     n_stack = nf // w.d
     sorf_ops_atom = n_stack * w.n_transform * w.d * int(math.log2(w.d)) + 6 * nf
     cands = {
-        "gram": {"kernel": f"tc::gram_split_kernel<{n_split}> ({n_split}-way BF16 split, tcgen05)",
+        "gram": {"kernel": f"tc::gram_persist_kernel<{n_split}> ({n_split}-way BF16 split, tcgen05, "
+                           "one CTA per SM, wave-aligned loads)",
                  "bound": "tensor",
                  "achieved": rows * nf * nf / (st["gram"] * 1e-3) / 1e12, "peak": bf16_sust / n_prod,
                  "unit": "TFLOP/s",

@@ -258,6 +258,256 @@ gram_split_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constan
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent Gram: one CTA per SM walks the tiles of the grouped order in
+// waves (tile w * gridDim.x + blockIdx.x), and the TMA producers of all CTAs
+// meet at the start of every wave (a counter each producer increments once it
+// has issued its wave's loads; bounded wait). The tiles of a wave then stream
+// their shared operand panels through the same K range at the same time, so
+// fewer of their K-block slices have left L2 before the last tile of the wave
+// reads them. Barrier phases and the two TMEM accumulators continue across a
+// CTA's tiles; the drain warps write a tile's G block while the MMA thread
+// already fills the other accumulator with the next tile's first K block.
+constexpr long long kWaveSpin = 1LL << 22;
+
+__device__ __forceinline__ void gram_tile_of(int t, int tiles_i, int tiles_j, int& bi, int& bj) {
+  bi = 0;
+  bj = 0;
+  for (int r0 = 0; r0 < tiles_i; r0 += kGroupRows) {
+    const int r1 = min(r0 + kGroupRows, tiles_i);
+    int cnt = 0;
+    for (int c = r0; c < tiles_j; ++c) cnt += min(r1, c + 1) - r0;
+    if (t >= cnt) {
+      t -= cnt;
+      continue;
+    }
+    for (int c = r0; c < tiles_j; ++c) {
+      const int h = min(r1, c + 1) - r0;
+      if (t < h) {
+        bi = r0 + t;
+        bj = c;
+        return;
+      }
+      t -= h;
+    }
+    return;
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+gram_persist_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+                    const __grid_constant__ CUtensorMap map2, int n_features, int k_blocks, int tiles_j,
+                    int n_tiles, unsigned* wave_ctr, float* __restrict__ G, int* err) {
+  using C = Cfg<S>;
+  constexpr int BN = C::BN, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES, NST = C::STAGES_N;
+  const CUtensorMap* maps[3] = {&map0, &map1, &map2};
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES);
+  uint64_t* empty = full + NST;
+  uint64_t* accf = empty + NST;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* never_abort = abort + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_i = n_features / BM;
+  const int gsz = gridDim.x;
+  const int waves = (n_tiles + gsz - 1) / gsz;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NST; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], kDrainWarps);
+    }
+    *abort = 0;
+    *never_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  int last_round[NST];
+#pragma unroll
+  for (int q = 0; q < NST; ++q) last_round[q] = -1;
+
+  if (warp == kDrainWarps && lane == 0) {
+    // ---------------- TMA producer
+    int kg = 0;
+    for (int w = 0; w < waves && !*abort; ++w) {
+      if (w > 0) {   // every CTA has issued the loads of wave w - 1
+        long long it = 0;
+        const unsigned target = (unsigned)(w * gsz);
+        while (*reinterpret_cast<volatile unsigned*>(wave_ctr) < target) {
+          if (++it > kWaveSpin) break;
+          __nanosleep(64);
+        }
+        if (*reinterpret_cast<volatile unsigned*>(wave_ctr) < target) {
+          record_device_error(err, DEV_TIMEOUT);
+          *abort = 1;
+          break;
+        }
+      }
+      const int t = w * gsz + blockIdx.x;
+      if (t < n_tiles) {
+        int bi, bj;
+        gram_tile_of(t, tiles_i, tiles_j, bi, bj);
+        const int i0 = bi * BM, j0 = bj * BN;
+        bool ok = true;
+        for (int kb = 0; kb < k_blocks; ++kb, ++kg) {
+          const int st = kg % NST;
+          const uint32_t round = (uint32_t)(kg / NST);
+          if (kg >= NST && !mbar_wait(&empty[st], (round - 1) & 1, abort)) {
+            record_device_error(err, DEV_TIMEOUT);
+            *abort = 1;
+            ok = false;
+            break;
+          }
+          uint8_t* sp = smem + st * STAGE_BYTES;
+          mbar_expect_tx(&full[st], STAGE_BYTES);
+          const int k = kb * BK;
+#pragma unroll
+          for (int q = 0; q < S; ++q) {
+            tma_load_2d(sp + q * A_BYTES, maps[q], &full[st], k, i0);
+            tma_load_2d(sp + S * A_BYTES + q * B_BYTES, maps[q], &full[st], k, j0);
+          }
+          last_round[st] = (int)round;
+        }
+        if (!ok) break;
+      }
+      __threadfence();
+      atomicAdd(wave_ctr, 1u);
+    }
+  } else if (warp == kDrainWarps + 1 && lane == 0) {
+    // ---------------- MMA issuer: products smallest first, one fresh accumulator per K block
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    uint64_t da[S], db[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      da[q] = smem_desc(smem + q * A_BYTES);
+      db[q] = smem_desc(smem + S * A_BYTES + q * B_BYTES);
+    }
+    int kg = 0;
+    bool ok = true;
+    for (int w = 0; w < waves && ok; ++w) {
+      if (w * gsz + blockIdx.x >= n_tiles) continue;
+      for (int kb = 0; kb < k_blocks; ++kb, ++kg) {
+        const int st = kg % NST;
+        const uint32_t round = (uint32_t)(kg / NST);
+        const int buf = kg & 1;
+        const uint32_t use = (uint32_t)(kg >> 1);
+        if (!mbar_wait(&full[st], round & 1, abort) ||
+            (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1, abort))) {
+          record_device_error(err, DEV_TIMEOUT);
+          *abort = 1;
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint64_t so = (uint64_t)(st * (STAGE_BYTES >> 4));
+        const uint32_t d = tmem + buf * BN;
+#pragma unroll
+        for (int q = C::NP - 1; q >= 0; --q) {
+          const int qa = q == 2 ? 1 : (q == 4 ? 2 : (q == 5 ? 1 : 0));
+          const int qb = q == 1 ? 1 : (q == 3 ? 2 : (q == 5 ? 1 : 0));
+          const uint64_t a0 = da[qa] + so, b0 = db[qb] + so;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(d, a0 + 2 * kk, b0 + 2 * kk, idesc, (kk > 0 || q < C::NP - 1) ? 1u : 0u);
+        }
+        mma_commit(&empty[st]);
+        mma_commit(&accf[buf]);
+      }
+    }
+  } else if (warp < kDrainWarps) {
+    // ---------------- drain: per tile, FP32 Kahan sums of the K blocks, then the G block
+    const int quarter = warp & 3, half = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    int kg = 0;
+    bool ok = true;
+    for (int w = 0; w < waves && ok; ++w) {
+      const int t = w * gsz + blockIdx.x;
+      if (t >= n_tiles) continue;
+      float sum[kDrainCols], cmp[kDrainCols];
+#pragma unroll
+      for (int k = 0; k < kDrainCols; ++k) {
+        sum[k] = 0.f;
+        cmp[k] = 0.f;
+      }
+      for (int kb = 0; kb < k_blocks; ++kb, ++kg) {
+        const int buf = kg & 1;
+        const uint32_t use = (uint32_t)(kg >> 1);
+        const bool got = mbar_wait(&accf[buf], use & 1, abort);
+        if (__any_sync(0xffffffffu, !got)) {
+          if (lane == 0) {
+            record_device_error(err, DEV_TIMEOUT);
+            *abort = 1;
+          }
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int c4 = 0; c4 < kDrainCols / 16; ++c4) {
+          float v[16];
+          tmem_ld16(tmem + lane_base + buf * BN + half * kDrainCols + c4 * 16, v);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int e = c4 * 16 + k;
+            const float y = v[k] - cmp[e];
+            const float tt = sum[e] + y;
+            cmp[e] = (tt - sum[e]) - y;
+            sum[e] = tt;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[buf]);
+      }
+      if (!ok) break;
+      int bi, bj;
+      gram_tile_of(t, tiles_i, tiles_j, bi, bj);
+      const int i0 = bi * BM, j0 = bj * BN;
+      const int row = i0 + quarter * 32 + lane;
+      if (row < n_features) {
+#pragma unroll
+        for (int k = 0; k < kDrainCols; ++k) {
+          const int col = j0 + half * kDrainCols + k;
+          if (col >= row && col < n_features) {
+            G[(long)row * n_features + col] = sum[k];
+            G[(long)col * n_features + row] = sum[k];
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (*abort) {
+    if (warp == kDrainWarps && lane == 0)
+      for (int q = 0; q < NST; ++q)
+        if (last_round[q] >= 0) mbar_wait(&full[q], (uint32_t)last_round[q] & 1, never_abort);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+  }
+}
+
 // (hi + lo) - w for a float pair: Knuth's two-sum of hi and -w, its error
 // folded into lo, and the pair renormalised by a second two-sum.
 __device__ __forceinline__ float2 pair_sub(float2 a, float w) {
@@ -490,6 +740,40 @@ static int launch_split(const uint16_t* zt, long k_pad, int n_features, float* G
   const int tiles_j = (n_features + C::BN - 1) / C::BN;
   int n_tiles = 0;
   for (int bi = 0; bi < tiles_i; ++bi) n_tiles += tiles_j - (bi * BM) / C::BN;
+  const int sms = sm_count();
+  int coop = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (coop && n_tiles >= 4 * sms) {
+    // persistent form: one CTA per SM, producers meet at every wave
+    static bool attr_p = false;
+    if (!attr_p) {
+      QMLR_CUDA_TRY(cudaFuncSetAttribute(gram_persist_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         C::SMEM_BYTES));
+      attr_p = true;
+    }
+    int per_sm = 0;
+    QMLR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_persist_kernel<S>, kThreads,
+                                                                C::SMEM_BYTES));
+    if (per_sm >= 1) {
+      // a counter of this launch's own (stream-ordered), so that Gram launches
+      // on different streams never share one
+      void* ctr = nullptr;
+      QMLR_CUDA_TRY(cudaMallocAsync(&ctr, sizeof(unsigned), s));
+      QMLR_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
+      unsigned* wave_ctr = static_cast<unsigned*>(ctr);
+      int kbl = (int)(k_pad / BK);
+      int* err = device_error_ptr();
+      void* args[] = {(void*)&m[0], (void*)&m[1], (void*)&m[2], (void*)&n_features, (void*)&kbl,
+                      (void*)&tiles_j, (void*)&n_tiles, (void*)&wave_ctr, (void*)&G, (void*)&err};
+      const cudaError_t le = cudaLaunchCooperativeKernel((const void*)gram_persist_kernel<S>, sms, kThreads,
+                                                         args, C::SMEM_BYTES, s);
+      QMLR_CUDA_TRY(cudaFreeAsync(ctr, s));
+      QMLR_CUDA_TRY(le);
+      count_launch();
+      return QMLR_OK;
+    }
+  }
   static bool attr = false;
   if (!attr) {
     QMLR_CUDA_TRY(cudaFuncSetAttribute(gram_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

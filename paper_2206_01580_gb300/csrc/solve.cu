@@ -515,37 +515,78 @@ bwd_step_kernel(const double* __restrict__ L, long ldl, const double* __restrict
 // Dataflow sweeps: one cooperative launch per substitution. 64-row block b is
 // owned by CTA b mod gridDim.x, and owners take their blocks in order. The
 // owner of block b accumulates L_bj x_j over the earlier blocks j as soon as
-// x_j has been published (its flag set), then forms x_b = Dinv_b (r_b - sum)
-// and publishes it (data, fence, flag). Blocks are published in order, so a
-// warp that has seen flag j knows x_0..x_j are final. Only the product with
-// the previous block and the diagonal solve lie on the critical path of a
-// step. Every wait is bounded: on expiry the kernel records a device error and
-// the CTA leaves the sweep. (The backward sweep is the same on L^T, blocks in
-// decreasing order.) All CTAs are co-resident (cooperative launch), so an owner
-// never waits on a CTA that is not running.
-constexpr long long kFlowSpin = 1LL << 23;   // ~2-4 s of polling (one L2 read per poll)
+// x_j has been written, then forms x_b = Dinv_b (r_b - sum) and writes it.
+// The vector the readers poll is preset (stream-ordered, before the launch)
+// to the all-ones bit pattern, a NaN that the sweep's arithmetic on finite
+// data never produces, so every 8-byte entry says itself whether it has been
+// written: a reader polls the very values it needs (read through L2) until
+// none is unset, and the writer needs no fence and no flag. (An 8-byte store
+// is seen whole or not at all.) Only the product with the previous block and
+// the diagonal solve lie on the critical path of a step. Every wait is
+// bounded: on expiry (as also when the data hold that NaN pattern) the kernel
+// records a device error and the CTA leaves the sweep. The backward sweep is
+// the same on L^T, blocks in decreasing order. All CTAs are co-resident
+// (cooperative launch), so an owner never waits on a CTA that is not running.
+//
+// Two arithmetic forms. FP64 (DF = false): L, Dinv and the polled entries are
+// FP64. Double-float (DF = true, the preconditioner inside the solve): L and
+// Dinv hold float pairs (hi, lo) in their 8-byte slots, x_j is published as a
+// float pair in a separate vector (the FP64 output is written beside it), and
+// every product is a pair product summed with two-sum (about 44 significant
+// bits, far below the preconditioner's own error) at FP32 rates: on the
+// GB300's FP64 units alone a 64 x 64 block product takes ~1.2 us on one SM,
+// and a step's critical path holds two of them.
+constexpr long long kFlowSpin = 1LL << 22;   // ~1-4 s of polling (one L2 read per poll)
+constexpr unsigned char kUnsetByte = 0xFF;   // every byte of an unwritten entry
 
-// Warp-level wait until flag[j] is set (lane 0 polls); false on timeout.
-__device__ __forceinline__ bool wait_flag(const unsigned* flags, int j, int* err) {
-  int ok = 1;
-  if ((threadIdx.x & 31) == 0) {
-    long long it = 0;
-    while (*reinterpret_cast<const volatile unsigned*>(flags + j) == 0u) {
-      if (++it > kFlowSpin) {
-        record_device_error(err, DEV_TIMEOUT);
-        ok = 0;
-        break;
-      }
-    }
-    __threadfence();
-  }
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+__device__ __forceinline__ bool entry_set(double v) { return __double_as_longlong(v) != -1LL; }
+
+// a float pair in the 8 bytes of a double (hi in the low word, as a float2 stores it)
+__device__ __forceinline__ float2 unpack_pair(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+}
+__device__ __forceinline__ double pack_pair(float2 p) {
+  return __longlong_as_double(
+      (long long)(((unsigned long long)__float_as_uint(p.y) << 32) | (unsigned long long)__float_as_uint(p.x)));
+}
+// (a.x + a.y) + (b.x + b.y), renormalised (two-sum of the high parts)
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  const float lo = __fadd_rn(__fadd_rn(a.y, b.y), e);
+  const float h = __fadd_rn(s, lo);
+  return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 shfl_xor_pair(float2 a, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+}
+// four (sum, compensation) accumulators -> one renormalised pair
+__device__ __forceinline__ float2 fold4(const float (&s4)[4], const float (&c4)[4]) {
+  return pair_add(pair_add(make_float2(s4[0], c4[0]), make_float2(s4[1], c4[1])),
+                  pair_add(make_float2(s4[2], c4[2]), make_float2(s4[3], c4[3])));
 }
 
-__device__ __forceinline__ void publish(unsigned* flags, int b) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicExch(flags + b, 1u);
+// Warp-level: loads this lane's entries p[0..cnt) (cnt <= 16, 0 beyond) of
+// a block that other CTAs write, polling until all of the warp's are set;
+// false (after recording the error) on timeout.
+__device__ __forceinline__ bool load_written(const double* p, int cnt, double (&v)[16], int* err) {
+  long long it = 0;
+  for (;;) {
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      v[q] = q < cnt ? __ldcg(p + q) : 0.0;
+      ok = ok && (q >= cnt || entry_set(v[q]));
+    }
+    if (__all_sync(0xffffffffu, ok)) return true;
+    if (++it > kFlowSpin) {
+      if ((threadIdx.x & 31) == 0) record_device_error(err, DEV_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
 }
 
 // x = D v (D one 64 x 64 block, transposed or not) with D's 16 values of this
@@ -562,6 +603,22 @@ __device__ __forceinline__ void block_matvec_reg(const double (&dv)[16], const d
   if (part == 0) xk[o] = acc;
 }
 
+// The same with D and v as packed float pairs; xk[o] gets the packed pair.
+__device__ __forceinline__ void block_matvec_pairs(const double (&dv)[16], const double* vk, double* xk) {
+  const int tid = threadIdx.x;
+  const int o = tid >> 2, part = tid & 3;
+  float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const float2 d = unpack_pair(dv[q]), v = unpack_pair(vk[part * 16 + q]);
+    df_fma(s4[q & 3], c4[q & 3], d.x, d.y, v.x, v.y);
+  }
+  float2 a = fold4(s4, c4);
+  a = pair_add(a, shfl_xor_pair(a, 1));
+  a = pair_add(a, shfl_xor_pair(a, 2));
+  if (part == 0) xk[o] = pack_pair(a);
+}
+
 __device__ __forceinline__ void load_dinv(const double* D, bool transposed, double (&dv)[16]) {
   const int tid = threadIdx.x;
   const int o = tid >> 2, part = tid & 3;
@@ -572,13 +629,16 @@ __device__ __forceinline__ void load_dinv(const double* D, bool transposed, doub
   }
 }
 
-// forward: L y = r (r read-only here); warp w takes rows 8w..8w+7 of the block,
-// 4 lanes per row, each lane 16 of the 64 columns of a block product. The L
-// tile of the next block product and the block's Dinv are loaded before the
-// wait, so that a step's critical path is the flag, x_{b-1} and the arithmetic.
+// forward: L y = r (r read-only here); readers poll yp (y itself in the FP64
+// form, the pair vector in the double-float form), preset to the unset
+// pattern. Warp w takes rows 8w..8w+7 of the block, 4 lanes per row, each lane
+// 16 of the 64 columns of a block product. The L tile of the next block
+// product, the block's Dinv and its r entries are loaded before the wait, so
+// that a step's critical path is x_{b-1} and the arithmetic.
+template <bool DF>
 __global__ void __launch_bounds__(256)
 fwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int n,
-                const double* __restrict__ r, double* __restrict__ y, unsigned* flags, int* err) {
+                const double* __restrict__ r, double* __restrict__ y, double* yp, int* err) {
   __shared__ double rb[NB], xb[NB];
   __shared__ int fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -590,55 +650,79 @@ fwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict
     const int r0 = b * NB, nb = min(NB, n - r0);
     double dv[16];
     load_dinv(Dinv + (long)b * NB * NB, false, dv);
+    const double rv = (part == 0 && o < nb) ? __ldcg(r + r0 + o) : 0.0;
+    float2 rp = make_float2(0.f, 0.f);
+    if constexpr (DF) rp = to_pair(rv);
     double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
     const double* Lr = L + (long)(r0 + min(o, nb - 1)) * ldl + part * 16;
     double lv[16];
     if (b > 0) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) lv[q] = __ldg(Lr + q);
     }
-    int ready = -1;
     for (int j = 0; j < b; ++j) {
-      if (j > ready) {
-        if (!wait_flag(flags, j, err)) {
-          fail = 1;
-          break;
-        }
-        ready = j;
-      }
-      const double* xj = y + (long)j * NB + part * 16;
       double xv[16], ln[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) xv[q] = __ldcg(xj + q);
       if (j + 1 < b) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) ln[q] = __ldg(Lr + (long)(j + 1) * NB + q);
       }
+      if (!load_written(yp + (long)j * NB + part * 16, 16, xv, err)) {
+        fail = 1;
+        break;
+      }
+      if constexpr (DF) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
+        for (int q = 0; q < 16; ++q) {
+          const float2 l = unpack_pair(lv[q]), x = unpack_pair(xv[q]);
+          df_fma(s4[q & 3], c4[q & 3], l.x, l.y, x.x, x.y);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
+      }
 #pragma unroll
       for (int q = 0; q < 16; ++q) lv[q] = ln[q];
     }
-    double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    __syncthreads();
-    if (fail) return;
-    if (part == 0) rb[o] = o < nb ? __ldcg(r + r0 + o) - acc : 0.0;
-    __syncthreads();
-    block_matvec_reg(dv, rb, xb);
-    __syncthreads();
-    if (tid < nb) y[r0 + tid] = xb[tid];
-    publish(flags, b);
+    if constexpr (DF) {
+      float2 a = fold4(s4, c4);
+      a = pair_add(a, shfl_xor_pair(a, 1));
+      a = pair_add(a, shfl_xor_pair(a, 2));
+      __syncthreads();
+      if (fail) return;
+      if (part == 0) rb[o] = o < nb ? pack_pair(pair_sub2(rp, a.x, a.y)) : 0.0;
+      __syncthreads();
+      block_matvec_pairs(dv, rb, xb);
+      __syncthreads();
+      if (tid < nb) {
+        const double pk = xb[tid];
+        yp[r0 + tid] = pk;
+        const float2 x = unpack_pair(pk);
+        y[r0 + tid] = (double)x.x + (double)x.y;
+      }
+    } else {
+      double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      __syncthreads();
+      if (fail) return;
+      if (part == 0) rb[o] = o < nb ? rv - acc : 0.0;
+      __syncthreads();
+      block_matvec_reg(dv, rb, xb);
+      __syncthreads();
+      if (tid < nb) y[r0 + tid] = xb[tid];
+    }
   }
 }
 
-// backward: L^T x = y; block b needs x_j for j > b: x_b = Dinv_b^T (y_b - sum_j L_jb^T x_j).
-// Thread (c = tid & 63, g = tid >> 6) sums 16 of block j's rows for column c; the
-// next L tile and Dinv_b^T are prefetched as in the forward sweep.
+// backward: L^T x = y; block b needs x_j for j > b: x_b = Dinv_b^T (y_b - sum_j
+// L_jb^T x_j); readers poll xp (x itself, or the pair vector). Thread
+// (c = tid & 63, g = tid >> 6) sums 16 of block j's rows for column c; the next
+// L tile, Dinv_b^T and y_b are loaded before the wait as in the forward sweep.
+template <bool DF>
 __global__ void __launch_bounds__(256)
 bwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int n,
-                const double* __restrict__ yv, double* __restrict__ x, unsigned* flags, int* err) {
+                const double* __restrict__ yv, double* __restrict__ x, double* xp, int* err) {
   __shared__ double yb[NB], xb[NB], part[4][NB];
   __shared__ int fail;
   const int tid = threadIdx.x;
@@ -650,7 +734,11 @@ bwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict
     const int r0 = b * NB, nb = min(NB, n - r0);
     double dv[16];
     load_dinv(Dinv + (long)b * NB * NB, true, dv);
+    const double yr = tid < nb ? __ldcg(yv + r0 + tid) : 0.0;
+    float2 yrp = make_float2(0.f, 0.f);
+    if constexpr (DF) yrp = to_pair(yr);
     double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
     const bool colok = c < nb;
     auto ltile = [&](int j, double (&t)[16]) {
       const int j0 = j * NB, jn = min(NB, n - j0);
@@ -662,43 +750,65 @@ bwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict
     };
     double lv[16];
     if (b < nblk - 1) ltile(nblk - 1, lv);
-    int ready = nblk;
     for (int j = nblk - 1; j > b; --j) {
-      if (j < ready) {
-        if (!wait_flag(flags, j, err)) {
-          fail = 1;
-          break;
-        }
-        ready = j;
-      }
       const int j0 = j * NB, jn = min(NB, n - j0);
       double xv[16], ln[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int rr = g * 16 + q;
-        xv[q] = rr < jn ? __ldcg(x + j0 + rr) : 0.0;
-      }
       if (j - 1 > b) ltile(j - 1, ln);
+      if (!load_written(xp + j0 + g * 16, max(0, min(16, jn - g * 16)), xv, err)) {
+        fail = 1;
+        break;
+      }
+      if constexpr (DF) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
+        for (int q = 0; q < 16; ++q) {
+          const float2 l = unpack_pair(lv[q]), xx = unpack_pair(xv[q]);
+          df_fma(s4[q & 3], c4[q & 3], l.x, l.y, xx.x, xx.y);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
+      }
 #pragma unroll
       for (int q = 0; q < 16; ++q) lv[q] = ln[q];
     }
-    part[g][c] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-    __syncthreads();
-    if (fail) return;
-    if (tid < NB) yb[tid] = tid < nb ? __ldcg(yv + r0 + tid) - ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) : 0.0;
-    __syncthreads();
-    block_matvec_reg(dv, yb, xb);
-    __syncthreads();
-    if (tid < nb) x[r0 + tid] = xb[tid];
-    publish(flags, b);
+    if constexpr (DF) {
+      part[g][c] = pack_pair(fold4(s4, c4));
+      __syncthreads();
+      if (fail) return;
+      if (tid < NB) {
+        const float2 sm = pair_add(pair_add(unpack_pair(part[0][tid]), unpack_pair(part[1][tid])),
+                                   pair_add(unpack_pair(part[2][tid]), unpack_pair(part[3][tid])));
+        yb[tid] = tid < nb ? pack_pair(pair_sub2(yrp, sm.x, sm.y)) : 0.0;
+      }
+      __syncthreads();
+      block_matvec_pairs(dv, yb, xb);
+      __syncthreads();
+      if (tid < nb) {
+        const double pk = xb[tid];
+        xp[r0 + tid] = pk;
+        const float2 xx = unpack_pair(pk);
+        x[r0 + tid] = (double)xx.x + (double)xx.y;
+      }
+    } else {
+      part[g][c] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+      __syncthreads();
+      if (fail) return;
+      if (tid < NB) yb[tid] = tid < nb ? yr - ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) : 0.0;
+      __syncthreads();
+      block_matvec_reg(dv, yb, xb);
+      __syncthreads();
+      if (tid < nb) x[r0 + tid] = xb[tid];
+    }
   }
 }
 
-constexpr int kMaxFlowBlocks = 4096;   // n <= 262144
-static __device__ unsigned g_flow_flags[2 * kMaxFlowBlocks];
+// FP64 -> float pairs in place over count entries (the diagonal-block inverses)
+__global__ void to_pairs_flat_kernel(double* __restrict__ v, long count) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < count) *reinterpret_cast<float2*>(v + idx) = to_pair(v[idx]);
+}
 
+constexpr int kMaxFlowBlocks = 4096;   // n <= 262144
 
 // ---------------------------------------------------------------------------
 // exact operator pieces: t = Z p (rows), q = Z^T t + lambda p (features).
@@ -1086,8 +1196,8 @@ static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts2, cud
 }
 
 
-// Grid of the dataflow sweeps (all CTAs co-resident) and their flag words on
-// the current device; 0 when cooperative launch is not available.
+// Grid of the dataflow sweeps (all CTAs co-resident) on the current device;
+// 0 when cooperative launch is not available.
 static int flow_grid() {
   static int grid[64] = {0};
   int dev = 0;
@@ -1095,50 +1205,53 @@ static int flow_grid() {
   if (grid[dev] == 0) {
     int coop = 0, pf = 0, pb = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, fwd_flow_kernel, 256, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, bwd_flow_kernel, 256, 0);
-    const int per_sm = std::min(std::min(pf, pb), 2);
+    int pf2 = 0, pb2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, fwd_flow_kernel<false>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, bwd_flow_kernel<false>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf2, fwd_flow_kernel<true>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb2, bwd_flow_kernel<true>, 256, 0);
+    const int per_sm = std::min(std::min(std::min(pf, pb), std::min(pf2, pb2)), 2);
     grid[dev] = (coop && per_sm > 0) ? per_sm * sm_count() : -1;
   }
   return grid[dev] > 0 ? grid[dev] : 0;
 }
 
-static unsigned* flow_flags() {
-  static unsigned* addr[64] = {nullptr};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_flow_flags) != cudaSuccess) return nullptr;
-    addr[dev] = static_cast<unsigned*>(p);
-  }
-  return addr[dev];
+// Whether the dataflow sweeps run for an n x n factor on the current device.
+static bool flow_available(int n) {
+  const int nblk = (n + NB - 1) / NB;
+  return nblk <= kMaxFlowBlocks && flow_grid() > 0;
 }
 
 // v <- (L L^T)^{-1} v; tmp is an n-vector of scratch. One dataflow launch per
-// sweep where cooperative launch is available (calls on one device are then
-// serialised by the caller: they share the flag words), else one launch per
-// block step.
+// sweep where cooperative launch is available (the polled vector preset to
+// the unset pattern first), else one launch per block step. pairs == nullptr:
+// L and Dinv are FP64. Otherwise they hold float pairs (double-float sweeps,
+// which need flow_available(n)) and pairs is an n-vector for the published
+// pairs.
 static int chol_apply(const double* L, long ldl, const double* Dinv, int n, double* v, double* tmp,
-                      cudaStream_t s) {
+                      cudaStream_t s, double* pairs = nullptr) {
   const int nblk = (n + NB - 1) / NB;
   const int grid = nblk <= kMaxFlowBlocks ? std::min(flow_grid(), nblk) : 0;
-  unsigned* flags = grid ? flow_flags() : nullptr;
-  if (grid && flags) {
+  QMLR_REQUIRE(grid || !pairs, "double-float sweeps need a cooperative launch");
+  if (grid) {
     int* err = device_error_ptr();
-    QMLR_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * (size_t)kMaxFlowBlocks * sizeof(unsigned), s));
-    unsigned* f1 = flags;
-    unsigned* f2 = flags + kMaxFlowBlocks;
+    const bool df = pairs != nullptr;
+    const void* fk = df ? (const void*)fwd_flow_kernel<true> : (const void*)fwd_flow_kernel<false>;
+    const void* bk = df ? (const void*)bwd_flow_kernel<true> : (const void*)bwd_flow_kernel<false>;
+    double* fpoll = df ? pairs : tmp;
+    double* bpoll = df ? pairs : v;
+    QMLR_CUDA_TRY(cudaMemsetAsync(fpoll, kUnsetByte, (size_t)n * sizeof(double), s));
     {
-      void* args[] = {(void*)&L, (void*)&ldl, (void*)&Dinv, (void*)&n, (void*)&v, (void*)&tmp, (void*)&f1,
+      void* args[] = {(void*)&L, (void*)&ldl, (void*)&Dinv, (void*)&n, (void*)&v, (void*)&tmp, (void*)&fpoll,
                       (void*)&err};
-      QMLR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fwd_flow_kernel, grid, 256, args, 0, s));
+      QMLR_CUDA_TRY(cudaLaunchCooperativeKernel(fk, grid, 256, args, 0, s));
       count_launch();
     }
+    QMLR_CUDA_TRY(cudaMemsetAsync(bpoll, kUnsetByte, (size_t)n * sizeof(double), s));
     {
-      void* args[] = {(void*)&L, (void*)&ldl, (void*)&Dinv, (void*)&n, (void*)&tmp, (void*)&v, (void*)&f2,
+      void* args[] = {(void*)&L, (void*)&ldl, (void*)&Dinv, (void*)&n, (void*)&tmp, (void*)&v, (void*)&bpoll,
                       (void*)&err};
-      QMLR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bwd_flow_kernel, grid, 256, args, 0, s));
+      QMLR_CUDA_TRY(cudaLaunchCooperativeKernel(bk, grid, 256, args, 0, s));
       count_launch();
     }
     return QMLR_OK;
@@ -1208,7 +1321,7 @@ extern "C" int64_t qmlr_solve_workspace_bytes(int64_t n_rows, int32_t n_features
          + parts * n * 8           // partial sums of Z^T t
          + std::max<int64_t>(n_rows, 1) * 16  // t = Z p and its float pair
          + n * 8                   // float pair of the operand
-         + 6 * n * 8               // c, r, z, p, q, tmp
+         + 7 * n * 8               // c, r, z, p, q, tmp, published float pairs of the sweeps
          + (int64_t)tc_parts_elems((int)n) * 4   // two split panels of the mixed-precision factor
          + 8 * 8 + 8192;           // scalars + alignment
 }
@@ -1337,7 +1450,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   c.s = s;
   c.parts = (int)std::max<int64_t>((n_rows + kZtRows - 1) / kZtRows, 1);
   char* p = static_cast<char*>(work);
-  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc, *vdinv, *vtri, *vsplit, *vth, *vph;
+  void *vL, *vpart, *vt, *vc, *vr, *vz, *vp, *vq, *vtmp, *vsc, *vdinv, *vtri, *vsplit, *vth, *vph, *vpub;
   const int nblk = (n + NB - 1) / NB;
   carve(p, &vL, (size_t)n * n * 8);
   carve(p, &vdinv, (size_t)nblk * NB * NB * 8);
@@ -1354,6 +1467,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   carve(p, &vsplit, tc_parts_elems(n) * 4);
   carve(p, &vth, (size_t)std::max<int64_t>(n_rows, 1) * 8);
   carve(p, &vph, (size_t)n * 8);
+  carve(p, &vpub, (size_t)n * 8);
   c.L = static_cast<double*>(vL);
   c.part = static_cast<double*>(vpart);
   c.t = static_cast<double*>(vt);
@@ -1432,11 +1546,22 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
     int rc0 = diag_inverses(c.L, c.ldl, n, Dinv, s);
     if (rc0) return rc0;
   }
+  // The preconditioner's sweeps in double-float: L (lower triangle) and the
+  // diagonal-block inverses become float pairs in place.
+  double* pub = nullptr;
+  if (flow_available(n)) {
+    pub = static_cast<double*>(vpub);
+    to_pairs_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(c.L, c.ldl, n);
+    QMLR_LAUNCH_CHECK();
+    const long nd = (long)nblk * NB * NB;
+    to_pairs_flat_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(Dinv, nd);
+    QMLR_LAUNCH_CHECK();
+  }
   QMLR_CUDA_TRY(cudaEventRecord(ev[1], s));
   int rc = QMLR_OK;
   // alpha = M^{-1} c
   QMLR_CUDA_TRY(cudaMemcpyAsync(alpha, cv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  if ((rc = chol_apply(c.L, c.ldl, Dinv, n, alpha, tri, s))) return rc;
+  if ((rc = chol_apply(c.L, c.ldl, Dinv, n, alpha, tri, s, pub))) return rc;
   dot_kernel<<<1, 1024, 0, s>>>(cv, cv, n, sc + 5);
   QMLR_LAUNCH_CHECK();
   // r = c - A alpha
@@ -1459,7 +1584,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
     // alpha += M^{-1} r ; r = c - A alpha
     for (; it < opts->max_iter && rel > opts->tol; ++it) {
       QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s))) return rc;
+      if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s, pub))) return rc;
       add_kernel<<<vb, 256, 0, s>>>(n, z, alpha);
       QMLR_LAUNCH_CHECK();
       if ((rc = apply_exact(c, alpha, q))) return rc;
@@ -1470,7 +1595,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
   } else {
     // preconditioned conjugate gradients on the exact operator
     QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s))) return rc;
+    if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s, pub))) return rc;
     QMLR_CUDA_TRY(cudaMemcpyAsync(pv, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     dot_kernel<<<1, 1024, 0, s>>>(r, z, n, sc + 0);
     QMLR_LAUNCH_CHECK();
@@ -1490,7 +1615,7 @@ extern "C" int qmlr_gram_solve(const float* G, const float* Z, int64_t n_rows, i
         break;
       }
       QMLR_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s))) return rc;
+      if ((rc = chol_apply(c.L, c.ldl, Dinv, n, z, tri, s, pub))) return rc;
       dot_kernel<<<1, 1024, 0, s>>>(r, z, n, sc + 1);
       QMLR_LAUNCH_CHECK();
       pupdate_kernel<<<vb, 256, 0, s>>>(n, sc + 1, sc + 0, z, pv);

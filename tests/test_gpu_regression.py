@@ -68,6 +68,45 @@ def test_gram_matches_fp64(q, n_rows, nf, precision):
     assert np.array_equal(G, G.T)
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+def test_persistent_gram_matches_fp64(q, precision):
+    """Enough tiles (37 x 38 / 2 = 703 >= 4 per SM) for the persistent,
+    wave-aligned tensor-core Gram; a ragged K (600 rows, not a multiple of 64)."""
+    Z = _features(600, 4736, seed=17)
+    Zd = torch.as_tensor(Z, dtype=torch.float64)
+    ref = (Zd.T @ Zd).numpy()
+    G = q.gram(Z, precision).cpu().numpy()
+    assert q.device_status() == 0
+    err = np.max(np.abs(G - ref)) / np.max(np.abs(ref))
+    assert err <= GRAM_TOL[precision], err
+    assert np.array_equal(G, G.T)
+
+
+def test_gram_at_full_size_on_sampled_entries(q):
+    """The 2-way tensor-core Gram at the training size (100,000 molecules x
+    16,384 features, the launch the training step makes): 256 sampled entries,
+    every tile row and column touched, against FP64 dot products of the
+    sampled columns."""
+    n_rows, nf = 100_000, 16_384
+    g = torch.Generator(device="cuda").manual_seed(23)
+    Z = (torch.rand(n_rows, nf, device="cuda", generator=g) - 0.5) * 0.1
+    G = q.gram(Z, q.GRAM_BF16X3)
+    assert q.device_status() == 0
+    rng = np.random.default_rng(24)
+    ii = np.concatenate([np.arange(0, nf, 128), np.arange(127, nf, 128)])[:256]
+    jj = rng.integers(0, nf, size=ii.size)
+    jj[:128] = ii[:128]   # diagonal entries
+    cols = np.unique(np.concatenate([ii, jj]))
+    Zc = Z[:, torch.as_tensor(cols, device="cuda")].double().cpu().numpy()
+    pos = {c: k for k, c in enumerate(cols)}
+    ref = np.array([Zc[:, pos[i]] @ Zc[:, pos[j]] for i, j in zip(ii, jj)])
+    got = G[torch.as_tensor(ii, device="cuda"), torch.as_tensor(jj, device="cuda")].double().cpu().numpy()
+    scale = np.max(np.abs(np.diag(Zc.T @ Zc)))
+    assert np.max(np.abs(got - ref)) <= GRAM_TOL[1] * scale
+    sym = G[torch.as_tensor(jj, device="cuda"), torch.as_tensor(ii, device="cuda")].double().cpu().numpy()
+    assert np.array_equal(got, sym)
+
+
 def test_tensor_core_gram_is_unbiased_on_long_sums(q):
     """Tensor-core accumulator adds truncate; the kernel promotes every 64-row K
     block into FP32 Kahan sums, so the diagonal (sums of 6000 positive terms)
