@@ -568,27 +568,6 @@ __device__ __forceinline__ float2 fold4(const float (&s4)[4], const float (&c4)[
                   pair_add(make_float2(s4[2], c4[2]), make_float2(s4[3], c4[3])));
 }
 
-// Warp-level: loads this lane's entries p[0..cnt) (cnt <= 16, 0 beyond) of
-// a block that other CTAs write, polling until all of the warp's are set;
-// false (after recording the error) on timeout.
-__device__ __forceinline__ bool load_written(const double* p, int cnt, double (&v)[16], int* err) {
-  long long it = 0;
-  for (;;) {
-    bool ok = true;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      v[q] = q < cnt ? __ldcg(p + q) : 0.0;
-      ok = ok && (q >= cnt || entry_set(v[q]));
-    }
-    if (__all_sync(0xffffffffu, ok)) return true;
-    if (++it > kFlowSpin) {
-      if ((threadIdx.x & 31) == 0) record_device_error(err, DEV_TIMEOUT);
-      return false;
-    }
-    __nanosleep(32);
-  }
-}
-
 // x = D v (D one 64 x 64 block, transposed or not) with D's 16 values of this
 // thread already in registers (thread: output o = tid >> 2, inputs part*16..+15).
 __device__ __forceinline__ void block_matvec_reg(const double (&dv)[16], const double* vk, double* xk) {
@@ -629,12 +608,80 @@ __device__ __forceinline__ void load_dinv(const double* D, bool transposed, doub
   }
 }
 
+// Accumulator of a sweep's block products: FP64, or a double-float
+// (sum, compensation) pair fed with packed float-pair operands.
+template <bool DF>
+struct FlowAcc;
+template <>
+struct FlowAcc<false> {
+  double v = 0.0;
+  __device__ __forceinline__ void mac(double l, double x) { v = fma(l, x, v); }
+  __device__ __forceinline__ void add(const FlowAcc& o) { v += o.v; }
+  __device__ __forceinline__ FlowAcc xor_lane(int m) const {
+    FlowAcc a;
+    a.v = __shfl_xor_sync(0xffffffffu, v, m);
+    return a;
+  }
+};
+template <>
+struct FlowAcc<true> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void mac(double l, double x) {
+    const float2 a = unpack_pair(l), b = unpack_pair(x);
+    df_fma(s, c, a.x, a.y, b.x, b.y);
+  }
+  __device__ __forceinline__ void add(const FlowAcc& o) {
+    const float2 p = pair_add(make_float2(s, c), make_float2(o.s, o.c));
+    s = p.x;
+    c = p.y;
+  }
+  __device__ __forceinline__ FlowAcc xor_lane(int m) const {
+    FlowAcc a;
+    a.s = __shfl_xor_sync(0xffffffffu, s, m);
+    a.c = __shfl_xor_sync(0xffffffffu, c, m);
+    return a;
+  }
+};
+
+// rhs - acc as the value the diagonal solve reads: FP64, or a packed pair
+// (rp: the right-hand side's pair, split before the wait)
+template <bool DF>
+__device__ __forceinline__ double rhs_minus(double rv, float2 rp, const FlowAcc<DF>& a);
+template <>
+__device__ __forceinline__ double rhs_minus<false>(double rv, float2, const FlowAcc<false>& a) {
+  return rv - a.v;
+}
+template <>
+__device__ __forceinline__ double rhs_minus<true>(double, float2 rp, const FlowAcc<true>& a) {
+  return pack_pair(pair_sub2(rp, a.s, a.c));
+}
+
+// Warp-uniform: true once every lane's polled entries are set (re-reading
+// them with reload() between polls); false after recording a timeout.
+template <typename Ok, typename Reload>
+__device__ __forceinline__ bool poll_until_set(Ok ok, Reload reload, int* err) {
+  long long it = 0;
+  while (!__all_sync(0xffffffffu, ok())) {
+    if (++it > kFlowSpin) {
+      if ((threadIdx.x & 31) == 0) record_device_error(err, DEV_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+    reload();
+  }
+  return true;
+}
+
 // forward: L y = r (r read-only here); readers poll yp (y itself in the FP64
 // form, the pair vector in the double-float form), preset to the unset
-// pattern. Warp w takes rows 8w..8w+7 of the block, 4 lanes per row, each lane
-// 16 of the 64 columns of a block product. The L tile of the next block
-// product, the block's Dinv and its r entries are loaded before the wait, so
-// that a step's critical path is x_{b-1} and the arithmetic.
+// pattern. Warp w takes rows 8w..8w+7 of the block; lane l takes columns l
+// and l + 32 of every tile (each load instruction reads 256 contiguous bytes
+// of one row), and the warp's 8 row sums meet at the end in a shuffle
+// reduce-scatter (lane l then holds row 4 b4 + 2 b3 + b2 of its warp, b_k =
+// bit k of l). L tiles and x entries are loaded three tiles deep (registers),
+// x speculatively: an entry still unset when its tile is used is polled
+// again. Dinv_b and r_b are loaded before the walk, so that a step's critical
+// path is x_{b-1} and the arithmetic.
 template <bool DF>
 __global__ void __launch_bounds__(256)
 fwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int n,
@@ -642,7 +689,7 @@ fwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict
   __shared__ double rb[NB], xb[NB];
   __shared__ int fail;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int o = warp * 8 + (lane >> 2), part = lane & 3;
+  const int rs = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
   const int nblk = (n + NB - 1) / NB;
   if (tid == 0) fail = 0;
   __syncthreads();
@@ -650,82 +697,122 @@ fwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict
     const int r0 = b * NB, nb = min(NB, n - r0);
     double dv[16];
     load_dinv(Dinv + (long)b * NB * NB, false, dv);
-    const double rv = (part == 0 && o < nb) ? __ldcg(r + r0 + o) : 0.0;
+    const int myrow = 8 * warp + rs;
+    const double rv = ((lane & 3) == 0 && myrow < nb) ? __ldcg(r + r0 + myrow) : 0.0;
     float2 rp = make_float2(0.f, 0.f);
     if constexpr (DF) rp = to_pair(rv);
-    double a4[4] = {0.0, 0.0, 0.0, 0.0};
-    float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
-    const double* Lr = L + (long)(r0 + min(o, nb - 1)) * ldl + part * 16;
-    double lv[16];
+    FlowAcc<DF> acc[8];
+    auto load_tile = [&](int j, double (&t)[16]) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const double* p = L + (long)min(r0 + 8 * warp + i, n - 1) * ldl + (long)j * NB + lane;
+        t[2 * i] = __ldg(p);
+        t[2 * i + 1] = __ldg(p + 32);
+      }
+    };
+    auto load_x = [&](int j, double (&xx)[2]) {
+      xx[0] = __ldcg(yp + (long)j * NB + lane);
+      xx[1] = __ldcg(yp + (long)j * NB + lane + 32);
+    };
+    auto consume = [&](int j, const double (&t)[16], double (&xx)[2]) -> bool {
+      if (!poll_until_set([&] { return entry_set(xx[0]) && entry_set(xx[1]); }, [&] { load_x(j, xx); }, err))
+        return false;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        acc[i].mac(t[2 * i], xx[0]);
+        acc[i].mac(t[2 * i + 1], xx[1]);
+      }
+      return true;
+    };
+    double T0[16], T1[16], T2[16], X0[2], X1[2], X2[2];
+    bool ok = true;
     if (b > 0) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) lv[q] = __ldg(Lr + q);
+      load_tile(0, T0);
+      load_x(0, X0);
     }
-    for (int j = 0; j < b; ++j) {
-      double xv[16], ln[16];
-      if (j + 1 < b) {
+    if (b > 1) {
+      load_tile(1, T1);
+      load_x(1, X1);
+    }
+    for (int j = 0; j < b; j += 3) {
+      if (j + 2 < b) {
+        load_tile(j + 2, T2);
+        load_x(j + 2, X2);
+      }
+      if (!(ok = consume(j, T0, X0)) || j + 1 >= b) break;
+      if (j + 3 < b) {
+        load_tile(j + 3, T0);
+        load_x(j + 3, X0);
+      }
+      if (!(ok = consume(j + 1, T1, X1)) || j + 2 >= b) break;
+      if (j + 4 < b) {
+        load_tile(j + 4, T1);
+        load_x(j + 4, X1);
+      }
+      if (!(ok = consume(j + 2, T2, X2))) break;
+    }
+    if (!ok) fail = 1;
+    // reduce-scatter of the 8 row sums over the warp's lanes
+    {
+      const bool h = lane & 16;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) ln[q] = __ldg(Lr + (long)(j + 1) * NB + q);
+      for (int k = 0; k < 4; ++k) {
+        FlowAcc<DF> keep = h ? acc[k + 4] : acc[k];
+        keep.add((h ? acc[k] : acc[k + 4]).xor_lane(16));
+        acc[k] = keep;
       }
-      if (!load_written(yp + (long)j * NB + part * 16, 16, xv, err)) {
-        fail = 1;
-        break;
+    }
+    {
+      const bool h = lane & 8;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        FlowAcc<DF> keep = h ? acc[k + 2] : acc[k];
+        keep.add((h ? acc[k] : acc[k + 2]).xor_lane(8));
+        acc[k] = keep;
       }
+    }
+    {
+      const bool h = lane & 4;
+      FlowAcc<DF> keep = h ? acc[1] : acc[0];
+      keep.add((h ? acc[0] : acc[1]).xor_lane(4));
+      acc[0] = keep;
+    }
+    acc[0].add(acc[0].xor_lane(2));
+    acc[0].add(acc[0].xor_lane(1));
+    __syncthreads();
+    if (fail) return;
+    if ((lane & 3) == 0) rb[myrow] = myrow < nb ? rhs_minus<DF>(rv, rp, acc[0]) : 0.0;
+    __syncthreads();
+    if constexpr (DF) block_matvec_pairs(dv, rb, xb);
+    else block_matvec_reg(dv, rb, xb);
+    __syncthreads();
+    if (tid < nb) {
+      const double v = xb[tid];
       if constexpr (DF) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float2 l = unpack_pair(lv[q]), x = unpack_pair(xv[q]);
-          df_fma(s4[q & 3], c4[q & 3], l.x, l.y, x.x, x.y);
-        }
+        yp[r0 + tid] = v;
+        const float2 xx = unpack_pair(v);
+        y[r0 + tid] = (double)xx.x + (double)xx.y;
       } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
+        y[r0 + tid] = v;
       }
-#pragma unroll
-      for (int q = 0; q < 16; ++q) lv[q] = ln[q];
-    }
-    if constexpr (DF) {
-      float2 a = fold4(s4, c4);
-      a = pair_add(a, shfl_xor_pair(a, 1));
-      a = pair_add(a, shfl_xor_pair(a, 2));
-      __syncthreads();
-      if (fail) return;
-      if (part == 0) rb[o] = o < nb ? pack_pair(pair_sub2(rp, a.x, a.y)) : 0.0;
-      __syncthreads();
-      block_matvec_pairs(dv, rb, xb);
-      __syncthreads();
-      if (tid < nb) {
-        const double pk = xb[tid];
-        yp[r0 + tid] = pk;
-        const float2 x = unpack_pair(pk);
-        y[r0 + tid] = (double)x.x + (double)x.y;
-      }
-    } else {
-      double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      __syncthreads();
-      if (fail) return;
-      if (part == 0) rb[o] = o < nb ? rv - acc : 0.0;
-      __syncthreads();
-      block_matvec_reg(dv, rb, xb);
-      __syncthreads();
-      if (tid < nb) y[r0 + tid] = xb[tid];
     }
   }
 }
 
 // backward: L^T x = y; block b needs x_j for j > b: x_b = Dinv_b^T (y_b - sum_j
 // L_jb^T x_j); readers poll xp (x itself, or the pair vector). Thread
-// (c = tid & 63, g = tid >> 6) sums 16 of block j's rows for column c; the next
-// L tile, Dinv_b^T and y_b are loaded before the wait as in the forward sweep.
+// (c = tid & 63, g = tid >> 6) sums 16 of block j's rows for column c (each
+// load instruction reads 256 contiguous bytes of one row); lane l loads entry
+// g*16 + (l & 15) of x_j and the warp shares them by shuffles. L tiles and x
+// entries are loaded three tiles deep, x speculatively, as in the forward
+// sweep.
 template <bool DF>
 __global__ void __launch_bounds__(256)
 bwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict__ Dinv, int n,
                 const double* __restrict__ yv, double* __restrict__ x, double* xp, int* err) {
   __shared__ double yb[NB], xb[NB], part[4][NB];
   __shared__ int fail;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int c = tid & 63, g = tid >> 6;
   const int nblk = (n + NB - 1) / NB;
   if (tid == 0) fail = 0;
@@ -737,10 +824,10 @@ bwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict
     const double yr = tid < nb ? __ldcg(yv + r0 + tid) : 0.0;
     float2 yrp = make_float2(0.f, 0.f);
     if constexpr (DF) yrp = to_pair(yr);
-    double a4[4] = {0.0, 0.0, 0.0, 0.0};
-    float s4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
+    FlowAcc<DF> a4[4];
     const bool colok = c < nb;
-    auto ltile = [&](int j, double (&t)[16]) {
+    const int xi = g * 16 + (lane & 15);   // entry of x_j this lane loads
+    auto load_tile = [&](int j, double (&t)[16]) {
       const int j0 = j * NB, jn = min(NB, n - j0);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
@@ -748,56 +835,78 @@ bwd_flow_kernel(const double* __restrict__ L, long ldl, const double* __restrict
         t[q] = (rr < jn && colok) ? __ldg(L + (long)(j0 + rr) * ldl + r0 + c) : 0.0;
       }
     };
-    double lv[16];
-    if (b < nblk - 1) ltile(nblk - 1, lv);
-    for (int j = nblk - 1; j > b; --j) {
+    auto load_x = [&](int j, double& xr) {
       const int j0 = j * NB, jn = min(NB, n - j0);
-      double xv[16], ln[16];
-      if (j - 1 > b) ltile(j - 1, ln);
-      if (!load_written(xp + j0 + g * 16, max(0, min(16, jn - g * 16)), xv, err)) {
-        fail = 1;
-        break;
-      }
-      if constexpr (DF) {
+      xr = xi < jn ? __ldcg(xp + j0 + xi) : 0.0;
+    };
+    auto consume = [&](int j, const double (&t)[16], double& xr) -> bool {
+      const int jn = min(NB, n - j * NB);
+      if (!poll_until_set([&] { return xi >= jn || entry_set(xr); }, [&] { load_x(j, xr); }, err)) return false;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float2 l = unpack_pair(lv[q]), xx = unpack_pair(xv[q]);
-          df_fma(s4[q & 3], c4[q & 3], l.x, l.y, xx.x, xx.y);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) a4[q & 3] = fma(lv[q], xv[q], a4[q & 3]);
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q) lv[q] = ln[q];
+      for (int q = 0; q < 16; ++q) a4[q & 3].mac(t[q], __shfl_sync(0xffffffffu, xr, q));
+      return true;
+    };
+    double T0[16], T1[16], T2[16], X0 = 0.0, X1 = 0.0, X2 = 0.0;
+    bool ok = true;
+    const int j_hi = nblk - 1;   // tiles j = j_hi, j_hi - 1, ..., b + 1
+    const int cnt = j_hi - b;
+    if (cnt > 0) {
+      load_tile(j_hi, T0);
+      load_x(j_hi, X0);
     }
-    if constexpr (DF) {
-      part[g][c] = pack_pair(fold4(s4, c4));
-      __syncthreads();
-      if (fail) return;
-      if (tid < NB) {
+    if (cnt > 1) {
+      load_tile(j_hi - 1, T1);
+      load_x(j_hi - 1, X1);
+    }
+    for (int k = 0; k < cnt; k += 3) {
+      if (k + 2 < cnt) {
+        load_tile(j_hi - k - 2, T2);
+        load_x(j_hi - k - 2, X2);
+      }
+      if (!(ok = consume(j_hi - k, T0, X0)) || k + 1 >= cnt) break;
+      if (k + 3 < cnt) {
+        load_tile(j_hi - k - 3, T0);
+        load_x(j_hi - k - 3, X0);
+      }
+      if (!(ok = consume(j_hi - k - 1, T1, X1)) || k + 2 >= cnt) break;
+      if (k + 4 < cnt) {
+        load_tile(j_hi - k - 4, T1);
+        load_x(j_hi - k - 4, X1);
+      }
+      if (!(ok = consume(j_hi - k - 2, T2, X2))) break;
+    }
+    if (!ok) fail = 1;
+    FlowAcc<DF> sum = a4[0];
+    sum.add(a4[1]);
+    FlowAcc<DF> s23 = a4[2];
+    s23.add(a4[3]);
+    sum.add(s23);
+    if constexpr (DF) part[g][c] = pack_pair(make_float2(sum.s, sum.c));
+    else part[g][c] = sum.v;
+    __syncthreads();
+    if (fail) return;
+    if (tid < NB) {
+      if constexpr (DF) {
         const float2 sm = pair_add(pair_add(unpack_pair(part[0][tid]), unpack_pair(part[1][tid])),
                                    pair_add(unpack_pair(part[2][tid]), unpack_pair(part[3][tid])));
         yb[tid] = tid < nb ? pack_pair(pair_sub2(yrp, sm.x, sm.y)) : 0.0;
+      } else {
+        yb[tid] = tid < nb ? yr - ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) : 0.0;
       }
-      __syncthreads();
-      block_matvec_pairs(dv, yb, xb);
-      __syncthreads();
-      if (tid < nb) {
-        const double pk = xb[tid];
-        xp[r0 + tid] = pk;
-        const float2 xx = unpack_pair(pk);
+    }
+    __syncthreads();
+    if constexpr (DF) block_matvec_pairs(dv, yb, xb);
+    else block_matvec_reg(dv, yb, xb);
+    __syncthreads();
+    if (tid < nb) {
+      const double v = xb[tid];
+      if constexpr (DF) {
+        xp[r0 + tid] = v;
+        const float2 xx = unpack_pair(v);
         x[r0 + tid] = (double)xx.x + (double)xx.y;
+      } else {
+        x[r0 + tid] = v;
       }
-    } else {
-      part[g][c] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-      __syncthreads();
-      if (fail) return;
-      if (tid < NB) yb[tid] = tid < nb ? yr - ((part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid])) : 0.0;
-      __syncthreads();
-      block_matvec_reg(dv, yb, xb);
-      __syncthreads();
-      if (tid < nb) x[r0 + tid] = xb[tid];
     }
   }
 }
