@@ -75,18 +75,6 @@ __global__ void to_pairs_kernel(double* __restrict__ L, long ldl, int n) {
   *reinterpret_cast<float2*>(e) = to_pair(*e);
 }
 
-// float pairs -> FP64 in place: columns [c0, c0 + w), rows i >= j.
-__global__ void pairs_to_fp64_kernel(double* __restrict__ L, long ldl, int c0, int w, int n) {
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long rows = n - c0;
-  if (idx >= rows * w) return;
-  const int i = c0 + (int)(idx / w), j = c0 + (int)(idx % w);
-  if (j > i) return;
-  double* e = L + (long)i * ldl + j;
-  const float2 pr = *reinterpret_cast<const float2*>(e);
-  *e = (double)pr.x + (double)pr.y;
-}
-
 // Unblocked Cholesky of the nb x nb diagonal block at (k0, k0) in shared memory
 // (rows past nb are identity rows). Step j: one thread forms the pivot's
 // 1/sqrt, the column below it is scaled, and the active triangle j < l <= i is
@@ -263,6 +251,16 @@ __device__ __forceinline__ void df_fma(float& s, float& c, float ah, float al, f
   c = __fadd_rn(c, __fadd_rn(err, __fadd_rn(e, x)));
 }
 
+// (a.x + a.y) + (b.x + b.y), renormalised (two-sum of the high parts)
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  const float lo = __fadd_rn(__fadd_rn(a.y, b.y), e);
+  const float h = __fadd_rn(s, lo);
+  return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
+}
+
 // (hi + lo) - (s + c) for float pairs, renormalised.
 __device__ __forceinline__ float2 pair_sub2(float2 a, float s, float c) {
   const float t = __fsub_rn(a.x, s);
@@ -342,6 +340,190 @@ syrk_pairs_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n, int c
 }
 
 constexpr size_t kPairsSmem = 4 * NB * (NB + 1) * sizeof(float);
+
+// ---------------------------------------------------------------------------
+// Diagonal block and panel solve of the mixed-precision factor in double-float
+// arithmetic. The block column still holds the float pairs of the trailing
+// matrix; these kernels read them directly, compute with pair products
+// (Dekker's product of the high parts plus the cross terms, two-sum
+// accumulation: about 44 significant bits) at FP32 rates, and write the FP64
+// factor entries (and, for the panel, the pairs the later updates read). In
+// FP64 these two steps ran on the GB300's FP64 units, which bounded the
+// factor's panel stream.
+
+// x * y for float pairs, renormalised
+__device__ __forceinline__ float2 pair_mul(float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, e));
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+__device__ __forceinline__ double pair_value(float2 p) { return (double)p.x + (double)p.y; }
+
+// 1/sqrt(d) of a positive float pair without FP64 instructions: an FP32 seed
+// y0 (relative error ~2^-23) and one Newton-Raphson step y0 (1 + (1 - d y0^2)/2),
+// with d y0^2 formed as a pair product (1 - d y0^2 is then exact to ~2^-46), so
+// the result carries ~2^-44 relative error. (On the GB300 each FP64 instruction
+// holds the SM quarter's FP64 pipe for tens of cycles; the pivot is on the
+// factor's critical path.)
+__device__ __forceinline__ float2 pair_rsqrt(float2 d) {
+  const float y0 = rsqrtf(d.x);
+  const float p = __fmul_rn(y0, y0);
+  const float2 u = pair_mul(d, make_float2(p, __fmaf_rn(y0, y0, -p)));
+  const float e = __fsub_rn(__fsub_rn(1.f, u.x), u.y);
+  const float corr = __fmul_rn(__fmul_rn(y0, e), 0.5f);
+  const float h = __fadd_rn(y0, corr);
+  return make_float2(h, __fsub_rn(corr, __fsub_rn(h, y0)));
+}
+
+// Factor of the diagonal block (float pairs on entry). Row i of the block stays
+// in the registers of threads 4i..4i+3 (thread q holds columns 4k + q). Step j:
+// the holder of the pivot forms 1/L_jj = 1/sqrt(d) (pair_rsqrt) and L_jj;
+// the column below is scaled by 1/L_jj and published in shared memory; every row
+// i > j then subtracts L_ij L_lj from its columns j < l <= i (blocks of four
+// columns already done are skipped warp-uniformly). Two barriers per step.
+// Writes L_kk in FP64 to L, and its pairs and the pivots' reciprocals (pairs)
+// to dpairs ([64][64] then [64]) for the panel solve.
+__global__ void __launch_bounds__(256, 1)
+potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, int* info,
+                     float2* __restrict__ dpairs) {
+  __shared__ float2 colj[NB];
+  __shared__ float2 ys[NB];
+  const int tid = threadIdx.x;
+  const int row = tid >> 2, q = tid & 3;
+  float2 x[NB / 4];
+#pragma unroll
+  for (int k = 0; k < NB / 4; ++k) {
+    const int c = 4 * k + q;
+    x[k] = (row < nb && c <= row) ? *reinterpret_cast<const float2*>(L + (long)(k0 + row) * ldl + k0 + c)
+                                  : make_float2(c == row ? 1.f : 0.f, 0.f);
+  }
+  for (int j = 0; j < NB; ++j) {
+    const int m = j >> 2, jq = j & 3;
+    if (row == j && q == jq) {   // pivot
+      float2 dp = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < NB / 4; ++k)
+        if (k == m) dp = x[k];
+      float2 d = pair_add(dp, make_float2(0.f, 0.f));
+      if (!(d.x > 0.f)) {
+        if (j < nb) {
+          record_device_error(err, DEV_NOT_SPD);
+          if (info && *info == 0) *info = k0 + j + 1;
+        }
+        d = make_float2(1.f, 0.f);
+      }
+      const float2 y = pair_rsqrt(d);
+      const float2 ljj = pair_mul(d, y);
+#pragma unroll
+      for (int k = 0; k < NB / 4; ++k)
+        if (k == m) x[k] = ljj;
+      ys[j] = y;
+    }
+    __syncthreads();
+    if (row > j && q == jq) {   // column j below the pivot
+      float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < NB / 4; ++k)
+        if (k == m) v = x[k];
+      v = pair_mul(v, ys[j]);
+#pragma unroll
+      for (int k = 0; k < NB / 4; ++k)
+        if (k == m) x[k] = v;
+      colj[row] = v;
+    }
+    __syncthreads();
+    if (row > j) {
+      const float2 a = colj[row];
+#pragma unroll
+      for (int k = 0; k < NB / 4; ++k) {
+        if (4 * k + 3 <= j) continue;   // uniform: columns 4k..4k+3 all done
+        const int l = 4 * k + q;
+        if (l > j && l <= row) {
+          const float2 b = colj[l];
+          df_fma(x[k].x, x[k].y, -a.x, -a.y, b.x, b.y);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NB / 4; ++k) {
+    const int c = 4 * k + q;
+    const float2 v = c <= row ? pair_add(x[k], make_float2(0.f, 0.f)) : make_float2(0.f, 0.f);
+    dpairs[row * NB + c] = v;
+    if (row < nb && c <= row) L[(long)(k0 + row) * ldl + k0 + c] = pair_value(v);
+  }
+  __syncthreads();
+  if (tid < NB) dpairs[NB * NB + tid] = ys[tid];
+}
+
+// Panel solve as trsm_panel_kernel, on the float pairs of rows [k0+nb, n) of the
+// block column, with L_kk and 1/L_jj as pairs from potrf_diag_df_kernel. A row's
+// 64 values stay in the registers of its four threads (thread q holds columns
+// 4k + q); at step j the owner of column j forms x_j, the row's threads get it
+// by a shuffle and update their columns l > j (blocks of four columns already
+// solved are skipped warp-uniformly). Writes the FP64 entries to L and, with lp
+// set, the pairs (lp[r - k0 - nb][0:64]).
+__global__ void __launch_bounds__(256, 2)
+trsm_panel_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n,
+                     const float2* __restrict__ dpairs, float2* __restrict__ lp) {
+  extern __shared__ float2 psm[];
+  float2 (*lkk)[NB + 1] = reinterpret_cast<float2 (*)[NB + 1]>(psm);
+  float2* rdg = psm + NB * (NB + 1);
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) lkk[idx / NB][idx % NB] = dpairs[idx];
+  if (tid < NB) rdg[tid] = dpairs[NB * NB + tid];
+  const int row = tid >> 2, q = tid & 3;
+  const int r = k0 + nb + blockIdx.x * kTrsmRows + row;
+  float2 x[NB / 4];
+#pragma unroll
+  for (int k = 0; k < NB / 4; ++k) {
+    const int c = 4 * k + q;
+    x[k] = (r < n && c < nb) ? *reinterpret_cast<const float2*>(L + (long)r * ldl + k0 + c) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int j = 0; j < NB; ++j) {
+    const int m = j >> 2, jq = j & 3;
+    float2 xj = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < NB / 4; ++k)
+      if (k == m) xj = x[k];
+    if (q == jq) {
+      xj = pair_mul(xj, rdg[j]);
+#pragma unroll
+      for (int k = 0; k < NB / 4; ++k)
+        if (k == m) x[k] = xj;
+    }
+    const int src = (lane & ~3) | jq;
+    xj.x = __shfl_sync(0xffffffffu, xj.x, src);
+    xj.y = __shfl_sync(0xffffffffu, xj.y, src);
+#pragma unroll
+    for (int k = 0; k < NB / 4; ++k) {
+      if (4 * k + 3 <= j) continue;   // uniform: columns 4k..4k+3 all solved
+      const int l = 4 * k + q;
+      if (l > j) {
+        const float2 v = lkk[l][j];
+        df_fma(x[k].x, x[k].y, -xj.x, -xj.y, v.x, v.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NB / 4; ++k) {
+    const int c = 4 * k + q;
+    if (r >= n) break;
+    const float2 v = pair_add(x[k], make_float2(0.f, 0.f));
+    if (c < nb) L[(long)r * ldl + k0 + c] = pair_value(v);
+    if (lp) lp[(long)(r - k0 - nb) * NB + c] = c < nb ? v : make_float2(0.f, 0.f);
+  }
+}
+
+constexpr size_t kTrsmDfSmem = (NB * (NB + 1) + NB) * sizeof(float2);
+
+// pairs of L_kk and of the pivots' reciprocals, per device (the factor's
+// panel work runs on one stream per device)
+static __device__ float2 g_diag_pairs[NB * NB + NB];
 
 // Panel operand of the tensor-core trailing update: rows [r0, r0 + m) and columns
 // [k0, k0 + 256) of the factor, rounded to FP32 and split into three BF16 parts
@@ -549,15 +731,6 @@ __device__ __forceinline__ float2 unpack_pair(double v) {
 __device__ __forceinline__ double pack_pair(float2 p) {
   return __longlong_as_double(
       (long long)(((unsigned long long)__float_as_uint(p.y) << 32) | (unsigned long long)__float_as_uint(p.x)));
-}
-// (a.x + a.y) + (b.x + b.y), renormalised (two-sum of the high parts)
-__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float bb = __fsub_rn(s, a.x);
-  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
-  const float lo = __fadd_rn(__fadd_rn(a.y, b.y), e);
-  const float h = __fadd_rn(s, lo);
-  return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
 }
 __device__ __forceinline__ float2 shfl_xor_pair(float2 a, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
@@ -1249,12 +1422,16 @@ static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts2, cud
                                        (int)kPairsSmem));
     QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kTrsmSmem));
+    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTrsmDfSmem));
     attr = true;
   }
   Lookahead* la = nullptr;
   int rc = lookahead(&la);
   if (rc) return rc;
   cudaStream_t p = la->panel;
+  float2* dpairs = nullptr;
+  QMLR_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void**>(&dpairs), g_diag_pairs));
   cudaEvent_t ev_start = la->ev[0], ev_split = la->ev[1], ev_next = la->ev[2], ev_end = la->ev[3];
   const size_t half = tc_parts_elems(n);
   QMLR_CUDA_TRY(cudaEventRecord(ev_start, s));
@@ -1266,16 +1443,13 @@ static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts2, cud
     float2* lp = reinterpret_cast<float2*>(parts);
     for (int c0 = k0; c0 < k0 + w; c0 += NB) {
       const int nb = std::min(NB, n - c0);
-      const long conv = (long)(n - c0) * nb;
-      pairs_to_fp64_kernel<<<(unsigned)((conv + 255) / 256), 256, 0, p>>>(L, ldl, c0, nb, n);
-      QMLR_LAUNCH_CHECK();
-      potrf_diag_kernel<<<1, 256, 0, p>>>(L, ldl, c0, nb, err, info);
+      potrf_diag_df_kernel<<<1, 256, 0, p>>>(L, ldl, c0, nb, err, info, dpairs);
       QMLR_LAUNCH_CHECK();
       const int rows = n - c0 - nb;
       if (rows <= 0) break;
       const int cblocks = (k0 + w - (c0 + nb) + NB - 1) / NB;   // panel columns still to update
-      trsm_panel_kernel<<<(rows + kTrsmRows - 1) / kTrsmRows, 256, kTrsmSmem, p>>>(
-          L, ldl, c0, nb, n, cblocks > 0 ? lp : nullptr);
+      trsm_panel_df_kernel<<<(rows + kTrsmRows - 1) / kTrsmRows, 256, kTrsmDfSmem, p>>>(
+          L, ldl, c0, nb, n, dpairs, cblocks > 0 ? lp : nullptr);
       QMLR_LAUNCH_CHECK();
       if (cblocks > 0) {
         const int T = (rows + NB - 1) / NB;
