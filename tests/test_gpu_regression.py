@@ -221,6 +221,23 @@ def test_ridge_solve_matches_oracle(q, method, precision, factor):
     assert np.max(np.abs(pz - pr)) <= 1e-6 * np.max(np.abs(pr))
 
 
+@pytest.mark.parametrize("factor", [0, 1])
+def test_ridge_solve_ragged_feature_count(q, factor):
+    """N_F = 300: four 64-row blocks and a 44-row tail in the factor and in the
+    preconditioner's double-float dataflow sweeps (plain FP32 Gram, which takes
+    any feature count), against the FP64 oracle."""
+    Z = _features(1000, 300, seed=31)
+    y = np.random.default_rng(32).normal(size=1000)
+    lam = 1e-6
+    alpha_ref, _ = o_reg.ridge_solve(Z.astype(np.float64), y, lam, refine=2)
+    G = q.gram(Z, q.GRAM_FP32)
+    alpha, it, rel = q.gram_solve(G, Z, y, lam, max_iter=40, tol=1e-11, factor=factor)
+    assert rel <= 1e-11, (it, rel)
+    pz = Z.astype(np.float64) @ alpha.cpu().numpy()
+    pr = Z.astype(np.float64) @ alpha_ref
+    assert np.max(np.abs(pz - pr)) <= 1e-6 * np.max(np.abs(pr))
+
+
 def test_mixed_factor_preconditions_as_well_as_fp64(q):
     """On a Gram large enough for several tensor-core panel updates the mixed
     factor needs at most two more PCG iterations than the FP64 one."""
