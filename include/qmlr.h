@@ -311,7 +311,11 @@ int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_features, int64_
  *   QMLR_GRAM_FP32:   reads Z [n_rows][ldz] (zt may be NULL)
  *   QMLR_GRAM_BF16X3: reads zt with n_split = 2; QMLR_GRAM_BF16X6: n_split = 3
  *                     (Z may be NULL); n_features % 128 == 0.
- * Deterministic: every element is summed in a fixed order.
+ * Deterministic: every element is summed in a fixed order. Split forms with
+ * at least 4 x (SM count) tiles of 128 x 128 run as one cooperative launch of
+ * one CTA per SM (same per-tile arithmetic, bitwise the same G); that launch
+ * takes a 4-byte counter from the stream-ordered allocator and frees it
+ * stream-ordered.
  */
 int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
               const uint16_t* zt, int64_t k_pad, float* G, void* stream);
@@ -333,7 +337,9 @@ int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_info, void* s
  * Mixed-precision factor A ~= L L^T (same layout and info as qmlr_cholesky),
  * meant as the preconditioner of an iteration on the exact operator (the
  * ridge solve below). Right-looking in 256-column panels: each panel is
- * factorised in FP64; the update of the remaining lower triangle by a panel
+ * factorised in double-float FP32 arithmetic (pair products and two-sums,
+ * ~2^-44 relative; the entries are stored in FP64); the update of the
+ * remaining lower triangle by a panel
  * runs on the tensor cores from the panel's 3-way BF16 split (products to
  * ~2^-24 relative, FP32 sums over each 64-deep K block, subtracted in FP32
  * arithmetic from the not yet factorised matrix, which is held as float pairs
@@ -346,7 +352,8 @@ int qmlr_cholesky_mixed(double* L, int64_t ldl, int32_t n, void* work, int64_t w
                         int32_t* host_info, void* stream);
 
 /* v <- (L L^T)^{-1} v with a factor from qmlr_cholesky or qmlr_cholesky_mixed
-   (forward, then backward substitution). */
+   (forward, then backward substitution, in FP64). Non-finite entries whose bit
+   pattern is all ones make the dataflow sweeps time out (device error 4). */
 int qmlr_cholesky_solve(const double* L, int64_t ldl, int32_t n, double* v, void* stream);
 
 enum {
