@@ -250,6 +250,23 @@ int qmlr_sorf(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, 
               double sigma, const float* alpha, int32_t mode, void* out, void* stream);
 
 /*
+ * Dense random Fourier features (RFF section: z(x) = sqrt(2/N_F) cos(W x + b)
+ * with W = G / sigma, G standard normal), the feature map SORF replaces; the
+ * reference side of the paper's SORF-versus-RFF comparison.
+ *   x     float [n_atoms][d], d = 1..256
+ *   G     float [N_F][d]  the standard-normal draw (1/sigma is applied inside)
+ *   b     float [N_F]     phases
+ *   mode  QMLR_SORF_PER_ATOM: out float [n_atoms][N_F];
+ *         QMLR_SORF_PER_MOL:  out float [n_mol][N_F], Z_m = sum_{I in m} z_I
+ *         (atoms in order; an empty molecule gives a zero row)
+ * FP32 arithmetic (dot products with a fixed summation order, cosf);
+ * deterministic. Asynchronous.
+ */
+int qmlr_rff(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+             const float* G, const float* b, int32_t n_features, double sigma, int32_t mode,
+             float* out, void* stream);
+
+/*
  * Force rows of the energy+force normal equations (RFF section: the
  * derivative features dz/dr stacked under Z): for molecule m, atom k, axis x
  *   rows[row0 + 3*(mol_ptr[m] + k) + x][f] = -dZ_m/dr_{k,x}[f]

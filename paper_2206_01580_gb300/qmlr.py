@@ -79,6 +79,7 @@ _SIGS = {
     "qmlr_project": (C.c_int, [P, I32, I32, P, P, I32, I32, P, I32, P, VP]),
     "qmlr_project_t": (C.c_int, [P, I32, P, P, I32, I32, P, I32, I32, P, I32, VP]),
     "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
+    "qmlr_rff": (C.c_int, [P, I32, P, I32, I32, P, P, I32, D, I32, P, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, VP]),
     "qmlr_gram_operand": (C.c_int, [P, I64, I32, I64, I32, P, I64, VP]),
@@ -305,6 +306,22 @@ def sorf(x, mol_ptr, sign_bits, T: int, b, sigma: float, mode: int, alpha=None, 
     al = None if alpha is None else _dev(alpha, torch.float32)
     _check(lib().qmlr_sorf(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(sign_bits), T, _ptr(b),
                            nf, float(sigma), _ptr(al), mode, _ptr(out), _stream()))
+    return out
+
+
+def rff(x, mol_ptr, G, b, sigma: float, mode: int):
+    """Dense RFF features z = sqrt(2/N_F) cos(G x / sigma + b), per atom or summed per molecule."""
+    x = _dev(x, torch.float32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    G = _dev(G, torch.float32)
+    b = _dev(b, torch.float32)
+    n_atoms, d = x.shape
+    n_mol = mol_ptr.shape[0] - 1
+    nf = b.shape[0]
+    rows = n_atoms if mode == SORF_PER_ATOM else n_mol
+    out = torch.empty((rows, nf), device="cuda", dtype=torch.float32)
+    _check(lib().qmlr_rff(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(G), _ptr(b), nf, float(sigma),
+                          mode, _ptr(out), _stream()))
     return out
 
 

@@ -178,6 +178,41 @@ def test_sorf_per_atom_and_per_molecule_match_oracle(q, d, nf, T):
     assert np.all(Z[sizes == 0] == 0)
 
 
+RFF_CASES = [(16, 64), (64, 512), (128, 1000), (128, 4096), (200, 300), (256, 129)]
+
+
+@pytest.mark.parametrize("d,nf", RFF_CASES)
+def test_rff_per_atom_and_per_molecule_match_oracle(q, d, nf):
+    """Dense RFF (W = G / sigma) against the FP64 oracle, including feature
+    counts that end in a partial 128-feature tile and d that is not a power of
+    two. Bound from the FP32 arithmetic: the dot product's rounding
+    (d 2^-24 sum_k |G_fk x_k|, divided by sigma), one rounding of the scale and
+    phase add (2^-24 |u|), cosf (a few ulp); the molecule sums add their own
+    FP32 rounding."""
+    rng = np.random.default_rng(41 + d)
+    sizes = rng.integers(1, 12, size=9)
+    sizes[2] = 0
+    mol_ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    x = (rng.normal(size=(int(mol_ptr[-1]), d)) * 0.5).astype(np.float32)
+    G, b = synth.rff_draw(rng, nf, d)
+    G, b = G.astype(np.float32), b.astype(np.float32)
+    sigma = 1.7
+    xd, Gd, bd = x.astype(np.float64), G.astype(np.float64), b.astype(np.float64)
+    ref = o_sorf.features(xd, o_sorf.rff_matrix(Gd, sigma), bd)
+    pref = math.sqrt(2 / nf)
+    u = xd @ Gd.T / sigma + bd
+    bound = pref * (d * 2.0 ** -24 * (np.abs(xd) @ np.abs(Gd).T) / sigma + 2.0 ** -23 * np.abs(u) + 1e-6)
+    z = q.rff(x, mol_ptr, G, b, sigma, q.SORF_PER_ATOM).cpu().numpy()
+    assert np.all(np.abs(z - ref) <= bound)
+    Z = q.rff(x, mol_ptr, G, b, sigma, q.SORF_PER_MOL).cpu().numpy()
+    Zref = o_reg.segment_sum(ref, mol_ptr)
+    Zbound = o_reg.segment_sum(bound, mol_ptr) + pref * 2.0 ** -22 * sizes[:, None] ** 2
+    assert np.all(np.abs(Z - Zref) <= Zbound)
+    assert np.all(Z[sizes == 0] == 0)
+    # deterministic
+    assert np.array_equal(Z, q.rff(x, mol_ptr, G, b, sigma, q.SORF_PER_MOL).cpu().numpy())
+
+
 @pytest.mark.parametrize("d,nf,T", SORF_CASES)
 def test_sorf_energy_and_gradient_match_oracle(q, d, nf, T):
     x, mol_ptr, signs, b = _sorf_inputs(d, nf, T, seed=4)
