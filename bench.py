@@ -57,6 +57,9 @@ def parse():
                     help="BF16 split of the tensor-core Gram: 2 (three products) or 3 (six products)")
     ap.add_argument("--factor", default="mixed", choices=["mixed", "fp64"],
                     help="preconditioner factor: tensor-core trailing updates (mixed) or FP64 throughout")
+    ap.add_argument("--feature-sweep", action="store_true",
+                    help="instead of the step: time the SORF segment sum over N_transform and N_F, and "
+                         "the dense RFF map beside it, on the workload's projected features")
     return ap.parse_args()
 
 
@@ -586,6 +589,70 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_feature_sweep(args):
+    """SORF -> Z for N_transform in {1, 2, 3} and N_F in {8192, 16384, 32768}, and the
+    dense RFF map (W = G / sigma) at N_F in {8192, 16384}, on the projected features of
+    the QM9-shaped workload (setup untimed; each point: one warm-up call, then the
+    median of three CUDA-event-timed calls). Prints one JSON line."""
+    import torch
+    from paper_2206_01580_gb300 import pipeline, qmlr, synth
+    from paper_2206_01580_gb300.params import from_table
+
+    torch.cuda.set_device(0)
+    w, _ = build_workload(args.scale)
+    mols = w.mols
+    p = from_table(w.params_column, n2=w.n2, n3=w.n3)
+    spec = pipeline.spec_from(p, w.d, w.signs, w.b, w.sigma)
+    batch = pipeline.Batch.from_host(mols.coords, mols.elem, mols.mol_ptr)
+    rep, perm, offs = pipeline.representations(batch, spec)
+    U = pipeline.fit_pca(rep, perm, offs, spec)
+    x = qmlr.project(rep, p.rep_dim, perm, offs, p.n_el, U)
+    del rep
+    n_atoms, d = mols.n_atoms, w.d
+    props = torch.cuda.get_device_properties(0)
+    alu_peak = props.multi_processor_count * 128 * 2070e6 / 1e12   # FP32 lanes x max SM clock, T op/s
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            del out
+        return statistics.median(ts)
+
+    rng = np.random.default_rng(220601580 + 41)
+    sorf_pts, rff_pts = [], []
+    for nf in (8192, 16384, 32768):
+        for T in (1, 2, 3):
+            signs, b = synth.sorf_draw(rng, nf, d, T)
+            bits = qmlr.pack_signs(signs)
+            bt = torch.as_tensor(b.astype(np.float32)).cuda()
+            ms = timed(lambda: qmlr.sorf(x, batch.mol_ptr, bits, T, bt, w.sigma, qmlr.SORF_PER_MOL))
+            ops = (nf // d) * T * d * int(math.log2(d)) + 6 * nf
+            sorf_pts.append({"n_features": nf, "n_transform": T, "ms": ms, "us_per_atom": ms * 1e3 / n_atoms,
+                             "t_op_s": ops * n_atoms / (ms * 1e-3) / 1e12,
+                             "alu_frac": ops * n_atoms / (ms * 1e-3) / 1e12 / alu_peak})
+    for nf in (8192, 16384):
+        G, b = synth.rff_draw(rng, nf, d)
+        Gt = torch.as_tensor(G.astype(np.float32)).cuda()
+        bt = torch.as_tensor(b.astype(np.float32)).cuda()
+        ms = timed(lambda: qmlr.rff(x, batch.mol_ptr, Gt, bt, w.sigma, qmlr.SORF_PER_MOL))
+        flop = 2 * nf * d
+        rff_pts.append({"n_features": nf, "ms": ms, "us_per_atom": ms * 1e3 / n_atoms,
+                        "tflop_s": flop * n_atoms / (ms * 1e-3) / 1e12,
+                        "fma_frac": flop * n_atoms / (ms * 1e-3) / 1e12 / (2 * alu_peak)})
+    print(json.dumps({"feature_sweep": {
+        "workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
+        "n_atoms": n_atoms, "n_molecules": mols.n_mol, "d": d, "sigma": w.sigma,
+        "alu_peak_t_op_s": alu_peak, "sorf_Z": sorf_pts, "rff_Z": rff_pts}}), flush=True)
+
+
 def main():
     global GRAM_FORM
     args = parse()
@@ -594,6 +661,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.feature_sweep:
+        if rank == 0:
+            run_feature_sweep(args)
     else:
         run_ours(args, rank, world)
 
