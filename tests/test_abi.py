@@ -56,3 +56,20 @@ def test_host_side_validation_without_gpu(lib):
     # SORF: d not supported
     assert L.qmlr_sorf(None, 48, None, 1, 1, None, 3, None, 96, 1.0, None, 0, None, None) == qmlr.EINVAL
     assert qmlr.sorf_parts(16384, 128) == 1 and qmlr.sorf_parts(32768, 128) == 2
+
+
+def test_rff_validation_without_gpu(lib):
+    """qmlr_rff rejects bad modes, feature widths and sigma before any launch."""
+    from paper_2206_01580_gb300 import qmlr
+    L = qmlr.lib()
+    # energy mode is not offered by the dense map
+    assert L.qmlr_rff(None, 64, None, 1, 1, None, None, 128, 1.0, qmlr.SORF_ENERGY, None, None) == qmlr.EINVAL
+    assert b"mode" in L.qmlr_last_error()
+    # d above the shared-memory slice of G
+    assert L.qmlr_rff(None, 300, None, 1, 1, None, None, 128, 1.0, qmlr.SORF_PER_MOL, None, None) == qmlr.EINVAL
+    assert b"d must be" in L.qmlr_last_error()
+    # sigma must be positive
+    assert L.qmlr_rff(None, 64, None, 1, 1, None, None, 128, 0.0, qmlr.SORF_PER_MOL, None, None) == qmlr.EINVAL
+    # NULL buffers
+    assert L.qmlr_rff(None, 64, None, 1, 1, None, None, 128, 1.0, qmlr.SORF_PER_MOL, None, None) == qmlr.EINVAL
+    assert b"NULL" in L.qmlr_last_error()
