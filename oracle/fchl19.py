@@ -19,7 +19,7 @@ Follows the Representation section of the paper:
                 th = angle k-i-j at the centre atom i, n = 1
                 (three-body, radial, ATM and Fourier equations).
 
-Readings where the printed text is garbled or silent (listed in the design doc):
+Readings where the printed text is garbled or silent:
 * radial grids R_s = r_cut * k / n for k = 1..n (0 excluded: ln 0 undefined);
 * the ATM denominator is the product of the three triangle sides;
 * the sine term subtracts sin(n(th + pi)) (the print repeats "cos");

@@ -11,7 +11,7 @@ recursion H_{2^n} = [[H_{2^{n-1}}, H_{2^{n-1}}], [H_{2^{n-1}}, -H_{2^{n-1}}]],
 H_1 = 1. For N_F > d the transform is repeated N_F/d times with independent
 diagonals and the outputs concatenated.
 
-Reading of the normalisation (listed in the design doc): each factor is the
+Reading of the normalisation: each factor is the
 orthogonal matrix H/sqrt(d) times D, so the product Q is orthogonal and the
 rows of one stack of W have norm sqrt(d)/sigma, which is the scalar that the
 SORF section substitutes for the chi-distributed S. Factor t uses D_{s,t}
