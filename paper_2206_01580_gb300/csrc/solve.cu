@@ -1268,9 +1268,9 @@ ztmv_partial_kernel(const float* __restrict__ Z, long n_rows, int n_features, lo
   part[(long)blockIdx.y * n_features + f] = acc;
 }
 
-__global__ void ztmv_finish_kernel(const double* __restrict__ part, int n_parts, int n,
-                                   const double* __restrict__ p, double lambda,
-                                   double* __restrict__ q) {
+// (p and q may be the same vector: each thread reads p[f] before it writes q[f])
+__global__ void ztmv_finish_kernel(const double* __restrict__ part, int n_parts, int n, const double* p,
+                                   double lambda, double* q) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= n) return;
   double acc = 0.0;
