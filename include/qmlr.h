@@ -463,6 +463,30 @@ int qmlr_pca_fit(const float* rep, int32_t rep_ld, int32_t rep_dim, const int32_
 typedef struct qmlr_model qmlr_model;
 
 /*
+ * Model file: the checkpoint of a trained model, in host memory only (no GPU
+ * needed). Holds the FCHL19 parameters, rep_dim, d, T, N_F, sigma, the lambda
+ * the weights were trained with, and the arrays
+ *   host_U         float  [n_el][rep_dim][d]
+ *   host_sign_bits uint32 [N_F/d][T][ceil(d/32)]  (bit set: D entry -1)
+ *   host_b         float  [N_F]
+ *   host_alpha     double [N_F]
+ * Little-endian, a fixed field-by-field header after the magic "QMLRMDL1" and a
+ * version word, then the arrays in that order, then the 64-bit FNV-1a of all
+ * preceding bytes. qmlr_model_file_info reads the scalars (so the caller can
+ * size the arrays); qmlr_model_file_read copies the arrays out. Both reject a
+ * file with a bad magic, an unknown version, sizes that disagree with its
+ * length, or a failed checksum (QMLR_EINVAL with a message). Synchronous.
+ */
+int qmlr_model_file_write(const char* path, const qmlr_fchl19_params* p, int32_t rep_dim, int32_t d,
+                          int32_t n_transform, int32_t n_features, double sigma, double lambda,
+                          const float* host_U, const uint32_t* host_sign_bits, const float* host_b,
+                          const double* host_alpha);
+int qmlr_model_file_info(const char* path, qmlr_fchl19_params* p, int32_t* rep_dim, int32_t* d,
+                         int32_t* n_transform, int32_t* n_features, double* sigma, double* lambda);
+int qmlr_model_file_read(const char* path, float* host_U, uint32_t* host_sign_bits, float* host_b,
+                         double* host_alpha);
+
+/*
  * Copies the model to the current device. Host arrays (read once):
  *   host_U         float [n_el][rep_dim][d]
  *   host_sign_bits uint32 [N_F/d][T][ceil(d/32)]

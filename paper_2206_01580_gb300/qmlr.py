@@ -79,6 +79,12 @@ _SIGS = {
     "qmlr_project": (C.c_int, [P, I32, I32, P, P, I32, I32, P, I32, P, VP]),
     "qmlr_project_t": (C.c_int, [P, I32, P, P, I32, I32, P, I32, I32, P, I32, VP]),
     "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
+    "qmlr_model_file_write": (C.c_int, [C.c_char_p, C.POINTER(_Params), I32, I32, I32, I32, D, D,
+                                        P, P, P, P]),
+    "qmlr_model_file_info": (C.c_int, [C.c_char_p, C.POINTER(_Params), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "qmlr_model_file_read": (C.c_int, [C.c_char_p, P, P, P, P]),
     "qmlr_rff": (C.c_int, [P, I32, P, I32, I32, P, P, I32, D, I32, P, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, VP]),
@@ -278,16 +284,65 @@ def project_t(gx, perm, offs, n_el: int, U, rep_dim: int, rep_ld: int | None = N
 # SORF
 
 
-def pack_signs(signs) -> torch.Tensor:
-    """Rademacher signs [n_stack, T, d] (+1/-1) -> bit words [n_stack, T, ceil(d/32)] (bit set = -1)."""
+def pack_signs_host(signs) -> np.ndarray:
+    """Rademacher signs [n_stack, T, d] (+1/-1) -> uint32 bit words [n_stack, T, ceil(d/32)] (bit set = -1)."""
     s = np.asarray(signs)
     n_stack, T, d = s.shape
     W = (d + 31) // 32
     neg = np.zeros((n_stack, T, W * 32), dtype=np.uint64)
     neg[:, :, :d] = (s < 0)
     weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
-    words = (neg.reshape(n_stack, T, W, 32) * weights).sum(axis=-1).astype(np.uint32)
-    return torch.as_tensor(words.view(np.int32)).cuda()
+    return (neg.reshape(n_stack, T, W, 32) * weights).sum(axis=-1).astype(np.uint32)
+
+
+def unpack_signs_host(words: np.ndarray, d: int) -> np.ndarray:
+    """Inverse of pack_signs_host: bit words [n_stack, T, W] -> int8 signs [n_stack, T, d]."""
+    w = np.asarray(words, dtype=np.uint32)
+    bits = (w[..., None] >> np.arange(32, dtype=np.uint32)) & 1
+    bits = bits.reshape(w.shape[0], w.shape[1], -1)[:, :, :d]
+    return np.where(bits == 1, -1, 1).astype(np.int8)
+
+
+def pack_signs(signs) -> torch.Tensor:
+    """Rademacher signs [n_stack, T, d] (+1/-1) -> bit words [n_stack, T, ceil(d/32)] (bit set = -1), on the device."""
+    return torch.as_tensor(pack_signs_host(signs).view(np.int32)).cuda()
+
+
+def save_model(path: str, p: FCHL19Params, U, signs, T: int, b, sigma: float, lam: float, alpha) -> None:
+    """Write a trained model to a checksummed model file (host only)."""
+    def host(a, dt):
+        a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)
+        return np.ascontiguousarray(a, dtype=dt)
+    U = host(U, np.float32)
+    bits = np.ascontiguousarray(pack_signs_host(signs))
+    b = host(b, np.float32)
+    alpha = host(alpha, np.float64)
+    n_el, rep_dim, d = U.shape
+    assert bits.shape[1] == T and b.shape[0] == alpha.shape[0] == bits.shape[0] * d
+    cp = c_params(p)
+    _check(lib().qmlr_model_file_write(str(path).encode(), C.byref(cp), rep_dim, d, T, b.shape[0],
+                                       float(sigma), float(lam), U.ctypes.data, bits.ctypes.data,
+                                       b.ctypes.data, alpha.ctypes.data))
+
+
+def load_model(path: str) -> dict:
+    """Read a model file: dict with params (FCHL19Params), U, signs (int8 +1/-1), T, b, sigma, lam, alpha."""
+    cp = _Params()
+    rep_dim, d, T, nf = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    sigma, lam = C.c_double(), C.c_double()
+    path_b = str(path).encode()
+    _check(lib().qmlr_model_file_info(path_b, C.byref(cp), C.byref(rep_dim), C.byref(d), C.byref(T),
+                                      C.byref(nf), C.byref(sigma), C.byref(lam)))
+    U = np.empty((cp.n_el, rep_dim.value, d.value), np.float32)
+    bits = np.empty((nf.value // d.value, T.value, (d.value + 31) // 32), np.uint32)
+    b = np.empty(nf.value, np.float32)
+    alpha = np.empty(nf.value, np.float64)
+    _check(lib().qmlr_model_file_read(path_b, U.ctypes.data, bits.ctypes.data, b.ctypes.data,
+                                      alpha.ctypes.data))
+    params = FCHL19Params(n_el=cp.n_el, n2=cp.n2, n3=cp.n3, nfourier=cp.nfourier, eta2=cp.eta2, eta3=cp.eta3,
+                          N2=cp.N2, N3=cp.N3, c3=cp.c3, zeta=cp.zeta, rcut=cp.rcut)
+    return {"params": params, "U": U, "signs": unpack_signs_host(bits, d.value), "T": T.value, "b": b,
+            "sigma": sigma.value, "lam": lam.value, "alpha": alpha}
 
 
 def sorf(x, mol_ptr, sign_bits, T: int, b, sigma: float, mode: int, alpha=None, n_features=None):
@@ -506,6 +561,12 @@ class Model:
                                        float(sigma), al.ctypes.data, C.byref(h)))
         self.handle = h
         self.capacity = 0
+
+    @classmethod
+    def from_file(cls, path: str, max_mol_atoms: int) -> "Model":
+        """A device model from a model file written by save_model."""
+        m = load_model(path)
+        return cls(m["params"], max_mol_atoms, m["U"], m["signs"], m["T"], m["b"], m["sigma"], m["alpha"])
 
     def set_alpha(self, alpha):
         al = np.ascontiguousarray(np.asarray(alpha.cpu() if isinstance(alpha, torch.Tensor) else alpha,
