@@ -19,6 +19,11 @@ Follows the Representation section of the paper:
                 th = angle k-i-j at the centre atom i, n = 1
                 (three-body, radial, ATM and Fourier equations).
 
+Periodic systems (the paper's MOF and water rows): ``representation_periodic``
+takes the environment of an atom over all lattice images within r_cut (its own
+images included), not the minimum image, so cells shorter than 2 r_cut are
+described correctly; ``environment_row`` is the per-centre form of the sums.
+
 Readings where the printed text is garbled or silent:
 * radial grids R_s = r_cut * k / n for k = 1..n (0 excluded: ln 0 undefined);
 * the ATM denominator is the product of the three triangle sides;
@@ -205,6 +210,86 @@ def representation_batch(coords: np.ndarray, elem: np.ndarray, mol_ptr: np.ndarr
             R = torch.as_tensor(np.asarray(coords[a:b], dtype=np.float64))
             out[a:b] = representation(R, elem[a:b], p).numpy()
     return out
+
+
+def lattice_translations(cell: np.ndarray, rcut: float) -> np.ndarray:
+    """Integer triples n (as float64 [K, 3]) with |n_a| <= ceil(rcut / h_a) + 1, h_a the
+    spacing of the lattice planes normal to the other two vectors: every image
+    within rcut of a point of the cell is among n . cell."""
+    A = np.asarray(cell, dtype=np.float64)
+    vol = abs(np.linalg.det(A))
+    nmax = []
+    for a in range(3):
+        b, c = A[(a + 1) % 3], A[(a + 2) % 3]
+        h = vol / np.linalg.norm(np.cross(b, c))
+        nmax.append(int(np.ceil(rcut / h)) + 1)
+    g = np.stack(np.meshgrid(*[np.arange(-m, m + 1) for m in nmax], indexing="ij"), axis=-1)
+    return g.reshape(-1, 3).astype(np.float64)
+
+
+def environment_row(v: torch.Tensor, el: np.ndarray, p: Params) -> torch.Tensor:
+    """rho of one centre atom from its environment: v [K, 3] the vectors from the
+    centre to the K neighbours (all within r_cut), el [K] their elements. The
+    same two-body and three-body sums as ``representation``, written for a
+    centre with given relative vectors. Returns [rep_dim] float64."""
+    assert p.nfourier == 1
+    el = np.asarray(el, dtype=np.int64)
+    out = torch.zeros(p.rep_dim, dtype=v.dtype)
+    K = v.shape[0]
+    if K == 0:
+        return out
+    r = torch.sqrt(torch.sum(v * v, dim=1))
+    g2 = two_body_terms(r, p)                                           # [K, n2]
+    col = el[:, None] * p.n2 + np.arange(p.n2)[None, :]
+    out = out.index_add(0, torch.as_tensor(col.reshape(-1)), g2.reshape(-1))
+    a, b = np.triu_indices(K, k=1)
+    if len(a):
+        vij, vik = v[a], v[b]
+        vjk = vik - vij
+        rij, rik = r[a], r[b]
+        rjk = torch.sqrt(torch.sum(vjk * vjk, dim=1))
+        cos_i = torch.sum(vij * vik, dim=1) / (rij * rik)
+        cos_j = torch.sum(-vij * vjk, dim=1) / (rij * rjk)
+        cos_k = torch.sum(vik * vjk, dim=1) / (rik * rjk)
+        g3 = three_body_terms(rij, rik, rjk, cos_i, cos_j, cos_k, p)     # [T, n3, 2]
+        pidx = np.array([pair_index(x, y, p.n_el) for x, y in zip(el[a], el[b])], dtype=np.int64)
+        base = p.n_el * p.n2 + pidx * (p.n3 * 2)
+        col3 = base[:, None, None] + (np.arange(p.n3)[None, :, None] * 2 + np.arange(2)[None, None, :])
+        out = out.index_add(0, torch.as_tensor(col3.reshape(-1)), g3.reshape(-1))
+    return out
+
+
+def representation_periodic(R: torch.Tensor, elem: np.ndarray, cell, p: Params) -> torch.Tensor:
+    """FCHL19 under periodic boundary conditions (the paper's periodic MOF and
+    water systems): the environment of atom i is every periodic image
+    R_j + n . cell (n integer, all atoms j including i's own images, not i
+    itself) within r_cut of R_i, and rho_i is the environment sum of
+    ``environment_row`` (two-body over the images, three-body over unordered
+    pairs of images, f_cut(r_jk) from the image positions). The vector to one
+    of i's own images is the lattice translation n . cell itself (a constant):
+    such an image moves with i, and two of them at opposite translations make
+    a collinear triplet whose terms are constant. R [N, 3] float64 tensor (may
+    require grad), cell [3, 3] lattice vectors as rows. Returns [N, rep_dim]."""
+    elem = np.asarray(elem, dtype=np.int64)
+    A = torch.as_tensor(np.asarray(cell, dtype=np.float64))
+    shifts = torch.as_tensor(lattice_translations(A.numpy(), p.rcut)) @ A   # [K, 3]
+    xn = R.detach().cpu().numpy()
+    sn = shifts.numpy()
+    n_at = R.shape[0]
+    rows = []
+    for i in range(n_at):
+        rel = xn[None, :, :] + sn[:, None, :] - xn[i][None, None, :]      # [K, N, 3]
+        keep = np.sqrt(np.sum(rel * rel, axis=-1)) < p.rcut
+        zero = np.abs(sn).sum(axis=1) == 0
+        keep[zero, i] = False
+        kk, jj = np.nonzero(keep)
+        own = jj == i
+        v_other = R[jj[~own]] + shifts[kk[~own]] - R[i]
+        v_own = shifts[kk[own]]
+        v = torch.cat([v_other, v_own], dim=0)
+        el = np.concatenate([elem[jj[~own]], elem[jj[own]]])
+        rows.append(environment_row(v, el, p))
+    return torch.stack(rows, dim=0)
 
 
 def with_sizes(p: Params, n2: int, n3: int) -> Params:
