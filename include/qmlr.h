@@ -78,6 +78,25 @@ typedef struct qmlr_fchl19_params {
   double rcut;       /* cutoff radius in Angstrom */
 } qmlr_fchl19_params;
 
+/*
+ * Periodic environments (for the paper's periodic MOF and water systems): for
+ * every atom i, the lattice images R_j + n . cell (n an integer triple; all
+ * atoms j, i's own images included, i itself excluded) with |R_j + n . cell -
+ * R_i| < rcut. Host code (cell list in fractional coordinates, any triclinic
+ * cell, rcut larger than the cell allowed). Synchronous.
+ *   host_coords  double [n_atoms][3] (need not lie inside the cell)
+ *   host_cell    double [3][3] lattice vectors as rows (non-singular)
+ *   host_env_ptr int64 [n_atoms+1] CSR offsets, written by ..._count
+ *   host_env_atom  int32 [env_ptr[n_atoms]]     j of each entry
+ *   host_env_shift int32 [env_ptr[n_atoms]][3]  n of each entry
+ * Entries of one atom are sorted by (j, n). qmlr_periodic_environment checks
+ * that host_env_ptr matches the coordinates it is given.
+ */
+int qmlr_periodic_environment_count(const double* host_coords, int32_t n_atoms, const double* host_cell,
+                                    double rcut, int64_t* host_env_ptr);
+int qmlr_periodic_environment(const double* host_coords, int32_t n_atoms, const double* host_cell, double rcut,
+                              const int64_t* host_env_ptr, int32_t* host_env_atom, int32_t* host_env_shift);
+
 /* rep_dim = n_el*n2 + n_el(n_el+1)/2 * n3 * 2 (780 for 5 elements, n2=24, n3=22). */
 int qmlr_fchl19_rep_dim(const qmlr_fchl19_params* p, int32_t* rep_dim);
 

@@ -85,6 +85,8 @@ _SIGS = {
                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "qmlr_model_file_read": (C.c_int, [C.c_char_p, P, P, P, P]),
+    "qmlr_periodic_environment_count": (C.c_int, [P, I32, P, D, P]),
+    "qmlr_periodic_environment": (C.c_int, [P, I32, P, D, P, P, P]),
     "qmlr_rff": (C.c_int, [P, I32, P, I32, I32, P, P, I32, D, I32, P, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, VP]),
@@ -306,6 +308,21 @@ def unpack_signs_host(words: np.ndarray, d: int) -> np.ndarray:
 def pack_signs(signs) -> torch.Tensor:
     """Rademacher signs [n_stack, T, d] (+1/-1) -> bit words [n_stack, T, ceil(d/32)] (bit set = -1), on the device."""
     return torch.as_tensor(pack_signs_host(signs).view(np.int32)).cuda()
+
+
+def periodic_environment(coords, cell, rcut: float):
+    """Lattice-image environments of a periodic system (host): (env_ptr int64 [N+1],
+    env_atom int32 [E], env_shift int32 [E, 3]) with entries sorted by (j, n) per atom."""
+    x = np.ascontiguousarray(np.asarray(coords, dtype=np.float64))
+    A = np.ascontiguousarray(np.asarray(cell, dtype=np.float64))
+    n = x.shape[0]
+    ptr = np.zeros(n + 1, np.int64)
+    _check(lib().qmlr_periodic_environment_count(x.ctypes.data, n, A.ctypes.data, float(rcut), ptr.ctypes.data))
+    atom = np.zeros(max(int(ptr[-1]), 1), np.int32)
+    shift = np.zeros((max(int(ptr[-1]), 1), 3), np.int32)
+    _check(lib().qmlr_periodic_environment(x.ctypes.data, n, A.ctypes.data, float(rcut), ptr.ctypes.data,
+                                           atom.ctypes.data, shift.ctypes.data))
+    return ptr, atom[:ptr[-1]], shift[:ptr[-1]]
 
 
 def save_model(path: str, p: FCHL19Params, U, signs, T: int, b, sigma: float, lam: float, alpha) -> None:
