@@ -347,9 +347,11 @@ constexpr size_t kPairsSmem = 4 * NB * (NB + 1) * sizeof(float);
 // matrix; these kernels read them directly, compute with pair products
 // (Dekker's product of the high parts plus the cross terms, two-sum
 // accumulation: about 44 significant bits) at FP32 rates, and write the FP64
-// factor entries (and, for the panel, the pairs the later updates read). In
-// FP64 these two steps ran on the GB300's FP64 units, which bounded the
-// factor's panel stream.
+// factor entries (and, for the panel, the pairs the later updates read).
+// Reading the pairs saves a conversion pass per block column; the two kernels
+// are latency-bound chains of 64 dependent steps, so what matters per step is
+// its instruction latency (an FP64 pivot chain made the diagonal factor take
+// 95 us per block, the FP32 one below 59 us).
 
 // x * y for float pairs, renormalised
 __device__ __forceinline__ float2 pair_mul(float2 x, float2 y) {
