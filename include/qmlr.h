@@ -191,10 +191,10 @@ int qmlr_group_by_element(const int32_t* elem, int32_t n_atoms, int32_t n_el, in
 /*
  * Element grouping that allocates nothing (the paper has no counterpart: this
  * is an integration convenience). Same result as qmlr_group_by_element, for
- * callers that cannot allocate device memory when they need it: work being
- * captured into a CUDA graph, a host framework that owns every device buffer
- * through its own pool, or a latency-bound service that must not wait on the
- * allocator. The counting sort's scratch is a fixed 256 KiB array inside the
+ * callers that cannot allocate device memory when they need it: a host
+ * framework that owns every device buffer through its own pool and hands out
+ * no raw allocations, or a latency-bound service that must not wait on the
+ * allocator in its request path. The counting sort's scratch is a fixed 256 KiB array inside the
  * library (one per device that loads it, kept until the process exits), so
  * n_atoms is limited to QMLR_GROUP_NOALLOC_MAX_ATOMS; larger inputs are
  * rejected with QMLR_EINVAL before any launch.
@@ -210,32 +210,38 @@ int qmlr_group_by_element(const int32_t* elem, int32_t n_atoms, int32_t n_el, in
 int qmlr_group_by_element_noalloc(const int32_t* elem, int32_t n_atoms, int32_t n_el,
                                   int32_t* perm, int32_t* elem_offsets, void* stream);
 
+/* Bytes of device workspace qmlr_project and qmlr_project_t need (the split basis). */
+int64_t qmlr_project_workspace_bytes(int32_t n_el, int32_t rep_dim, int32_t d);
+
 /*
  * x[i][:] = rep[i][:rep_dim] * U[elem(i)]   (SORF section: projection onto the element's
  * principal directions). Runs on the tensor cores with 3-way BF16 splits of
  * both operands and FP32 accumulation (products to ~2^-24 relative, the
- * accuracy of an FP32 GEMM); the split basis is made per call in
- * stream-ordered scratch (cudaMallocAsync).
+ * accuracy of an FP32 GEMM); the split basis is made on every call in the
+ * caller's workspace (no allocation).
  *   rep  float [n_atoms][rep_ld]
  *   perm, elem_offsets  from qmlr_group_by_element
  *   U    float [n_el][rep_dim][d]   (U_e with the d basis vectors as columns)
  *   x    float [n_atoms][d]
+ *   work device workspace of qmlr_project_workspace_bytes(n_el, rep_dim, d) bytes
+ *        (used until the call's work on `stream` has finished)
  * d is a power of two, 16..512.
  */
 int qmlr_project(const float* rep, int32_t rep_ld, int32_t rep_dim, const int32_t* perm,
                  const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el, const float* U,
-                 int32_t d, float* x, void* stream);
+                 int32_t d, float* x, void* work, int64_t work_bytes, void* stream);
 
 /*
  * Transposed projection (chain rule through the projection):
  *   grad_rep[i][:rep_dim] = U[elem(i)] * sum_p gx[p][i][:]
  * gx holds n_part partial gradients [n_part][n_atoms][d] (summed in a fixed
  * order). Columns rep_dim..rep_ld-1 of grad_rep are written as zeros. Same
- * tensor-core arithmetic as qmlr_project.
+ * tensor-core arithmetic and workspace as qmlr_project.
  */
 int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* perm,
                    const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el, const float* U,
-                   int32_t d, int32_t rep_dim, float* grad_rep, int32_t rep_ld, void* stream);
+                   int32_t d, int32_t rep_dim, float* grad_rep, int32_t rep_ld, void* work,
+                   int64_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * SORF feature map (SORF section; RFF feature-map equation; GPU
@@ -381,7 +387,10 @@ int qmlr_cholesky(double* L, int64_t ldl, int32_t n, int32_t* host_info, void* s
  * arithmetic from the not yet factorised matrix, which is held as float pairs
  * hi + lo in the same storage), so L L^T matches A to ~1e-7 of max|A| rather
  * than to FP64 round-off. work: device scratch of qmlr_cholesky_mixed_workspace_bytes(n)
- * bytes, 256-byte aligned. Synchronous.
+ * bytes, 256-byte aligned. Synchronous. The factor's side stream, events and
+ * diagonal-block buffer are one set per device, so calls on one device (from
+ * any host thread or stream, including qmlr_gram_solve with QMLR_FACTOR_MIXED)
+ * run one at a time: a call waits until the previous one has finished on the GPU.
  */
 int64_t qmlr_cholesky_mixed_workspace_bytes(int32_t n);
 int qmlr_cholesky_mixed(double* L, int64_t ldl, int32_t n, void* work, int64_t work_bytes,

@@ -2,15 +2,20 @@
 #include "common.cuh"
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace qmlr {
 
 static __device__ int g_device_error = 0;
 
 int* device_error_ptr() {
+  static std::mutex mu;
   static int* ptrs[64] = {nullptr};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
   if (!ptrs[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
@@ -29,6 +34,21 @@ void set_error(const char* fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(t_last_error, sizeof(t_last_error), fmt, ap);
   va_end(ap);
+}
+
+cudaError_t smem_attr_once(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> raised;   // (kernel, device) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(func, dev);
+  const auto it = raised.find(key);
+  if (it != raised.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) raised[key] = bytes;
+  return e;
 }
 
 int sm_count() {

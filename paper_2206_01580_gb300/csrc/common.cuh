@@ -82,4 +82,8 @@ int validate_params(const qmlr_fchl19_params* p);
 
 int sm_count();
 
+// Raises the dynamic shared-memory limit of a kernel to `bytes` on the current
+// device, once per (kernel, device) pair; safe to call from several host threads.
+cudaError_t smem_attr_once(const void* func, int bytes);
+
 }  // namespace qmlr

@@ -952,14 +952,8 @@ extern "C" int qmlr_fchl19(const float* coords, const int32_t* elem, const int32
   const int mxp = (mx + 3) & ~3;
   const size_t smem = kWarpsFwd * fwd_warp_bytes(mxp, rp);
   QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
-  static bool attr_set = false;
-  if (!attr_set) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_forward_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_forward_reg_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_kernel, 227 * 1024));
+  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_reg_kernel, 227 * 1024));
   const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
   if (p->n_el <= 5 && p->n2 <= 32 && p->n3 <= 32) {
     fchl19_forward_reg_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
@@ -990,12 +984,7 @@ extern "C" int qmlr_fchl19_vjp(const float* coords, const int32_t* elem, const i
   const int mxp = (mx + 3) & ~3;
   const size_t smem = (size_t)mxp * 16 + kWarpsVjp * vjp_warp_bytes(mxp, rp);
   QMLR_REQUIRE(smem <= 200 * 1024, "shared memory request too large");
-  static bool attr_set = false;
-  if (!attr_set) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_vjp_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_vjp_kernel, 200 * 1024));
   fchl19_vjp_kernel<<<n_mol, 32 * kWarpsVjp, smem, as_stream(stream)>>>(
       coords, elem, mol_ptr, n_mol, mx, mxp, rp, c, grad_rep, rep_ld, grad_coords, accumulate,
       device_error_ptr());
@@ -1036,12 +1025,7 @@ extern "C" int qmlr_fchl19_jac(const float* coords, const int32_t* elem, const i
   const int mxp = (mx + 3) & ~3;
   const size_t smem = kWarpsFwd * jac_warp_bytes(mxp, rp);
   QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
-  static bool attr_set = false;
-  if (!attr_set) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_jac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
-    attr_set = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_jac_kernel, 227 * 1024));
   const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
   fchl19_jac_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
       coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, jac_ptr, jac, rep_ld, row_elem,
@@ -1069,12 +1053,7 @@ extern "C" int qmlr_fchl19_vjp_atoms(const float* coords, const int32_t* elem, c
   const int mxp = (mx + 3) & ~3;
   const size_t smem = kWarpsFwd * ((size_t)mxp * 16 + vjp_warp_bytes(mxp, rp));
   QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
-  static bool attr_set = false;
-  if (!attr_set) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(fchl19_vjp_centre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
-    attr_set = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_vjp_centre_kernel, 227 * 1024));
   cudaStream_t st = as_stream(stream);
   fchl19_vjp_centre_kernel<<<(n_atoms + kWarpsFwd - 1) / kWarpsFwd, 32 * kWarpsFwd, smem, st>>>(
       coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, grad_rep, rep_ld, pair_ptr, contrib,

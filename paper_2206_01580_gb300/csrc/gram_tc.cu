@@ -746,12 +746,7 @@ static int launch_split(const uint16_t* zt, long k_pad, int n_features, float* G
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (coop && n_tiles >= 4 * sms) {
     // persistent form: one CTA per SM, producers meet at every wave
-    static bool attr_p = false;
-    if (!attr_p) {
-      QMLR_CUDA_TRY(cudaFuncSetAttribute(gram_persist_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         C::SMEM_BYTES));
-      attr_p = true;
-    }
+    QMLR_CUDA_TRY(smem_attr_once((const void*)gram_persist_kernel<S>, C::SMEM_BYTES));
     int per_sm = 0;
     QMLR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_persist_kernel<S>, kThreads,
                                                                 C::SMEM_BYTES));
@@ -774,12 +769,7 @@ static int launch_split(const uint16_t* zt, long k_pad, int n_features, float* G
       return QMLR_OK;
     }
   }
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(gram_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       C::SMEM_BYTES));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)gram_split_kernel<S>, C::SMEM_BYTES));
   gram_split_kernel<S><<<n_tiles, kThreads, C::SMEM_BYTES, s>>>(m[0], m[1], m[2], n_features, (int)(k_pad / BK),
                                                             tiles_j, G, device_error_ptr());
   QMLR_LAUNCH_CHECK();
@@ -796,12 +786,7 @@ static int launch_syrk(const uint16_t* parts, long part_elems, int m, double* A,
     int rc = make_map(&mp[q], parts + (size_t)q * part_elems, kPanelK, T * BM);
     if (rc) return rc;
   }
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       C::SMEM_BYTES));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)syrk_tc_kernel, C::SMEM_BYTES));
   int tiles = T * (T + 1) / 2;
   if (part == 1) tiles = T >= 2 ? 2 * T - 1 : T;
   if (part == 2) tiles = T > 2 ? (T - 2) * (T - 1) / 2 : 0;

@@ -89,9 +89,17 @@ struct Sizes {
   size_t u, bits, b, alpha;
 };
 
+// The sizes a model file may hold: exactly what qmlr_model_create accepts
+// (FCHL19 parameters in range, rep_dim equal to the one those parameters
+// define, d a power of two 16..128, 1..4 transforms, N_F a multiple of d), so
+// that a reader never sizes an array from a field the model would disagree with.
 bool sizes_of(const Header& h, Sizes* s) {
-  if (h.p.n_el < 1 || h.p.n_el > 8 || h.rep_dim < 1 || h.d < 1 || h.n_transform < 1 ||
-      h.n_features < 1 || h.n_features % h.d != 0)
+  if (h.p.n_el < 1 || h.p.n_el > 8 || h.p.n2 < 1 || h.p.n2 > 64 || h.p.n3 < 1 || h.p.n3 > 64 ||
+      h.p.nfourier != 1)
+    return false;
+  if (h.rep_dim != rep_dim_of(h.p)) return false;
+  if (!(h.d == 16 || h.d == 32 || h.d == 64 || h.d == 128) || h.n_transform < 1 || h.n_transform > 4 ||
+      h.n_features < h.d || h.n_features % h.d != 0)
     return false;
   const size_t words = ((size_t)h.d + 31) / 32;
   s->u = (size_t)h.p.n_el * h.rep_dim * h.d * sizeof(float);

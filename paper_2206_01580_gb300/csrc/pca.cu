@@ -313,13 +313,8 @@ extern "C" int qmlr_pca_fit(const float* rep, int32_t rep_ld, int32_t rep_dim, c
   double* B = T + (long)R * l;
   double* W = B + (long)l * l;
   double* lam = W + (long)l * l;
-  static bool attr = false;
   const size_t jsm = (size_t)(l + 1) * (l + 1) * 8;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((kMaxL + 1) * (kMaxL + 1) * 8)));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)jacobi_kernel, (int)((kMaxL + 1) * (kMaxL + 1) * 8)));
   for (int e = 0; e < n_el; ++e) {
     float* Ue = U + (long)e * rep_dim * d;
     const int n = std::min(offs[e + 1] - offs[e], max_per_element);

@@ -141,44 +141,57 @@ extern "C" int qmlr_group_by_element(const int32_t* elem, int32_t n_atoms, int32
   return QMLR_OK;
 }
 
+extern "C" int64_t qmlr_project_workspace_bytes(int32_t n_el, int32_t rep_dim, int32_t d) {
+  if (n_el < 1 || n_el > kMaxEl || rep_dim < 1 || d < 1) return 0;
+  // the split basis of either direction (the same element count) plus alignment slack
+  return (int64_t)std::max(proj_tc_basis_bytes(n_el, rep_dim, d), proj_tc_basis_bytes(n_el, d, rep_dim)) + 256;
+}
+
+static uint16_t* aligned_basis(void* work) {
+  return reinterpret_cast<uint16_t*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
+}
+
 extern "C" int qmlr_project(const float* rep, int32_t rep_ld, int32_t rep_dim, const int32_t* perm,
                             const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el,
-                            const float* U, int32_t d, float* x, void* stream) {
+                            const float* U, int32_t d, float* x, void* work, int64_t work_bytes,
+                            void* stream) {
   QMLR_REQUIRE(n_el >= 1 && n_el <= kMaxEl, "n_el must be in 1..8");
   QMLR_REQUIRE(is_pow2(d) && d >= 16 && d <= 512, "d must be a power of two in 16..512 (got %d)", d);
   QMLR_REQUIRE(rep_dim >= 1 && rep_ld >= rep_dim, "need 1 <= rep_dim <= rep_ld");
   QMLR_REQUIRE(n_atoms >= 0, "n_atoms must be >= 0");
   if (n_atoms == 0) return QMLR_OK;
   QMLR_REQUIRE(rep && perm && elem_offsets && U && x, "NULL pointer argument");
-  // the basis is split per call into stream-ordered scratch; a model holds its split basis
+  QMLR_REQUIRE(work && work_bytes >= qmlr_project_workspace_bytes(n_el, rep_dim, d),
+               "workspace too small (%lld < %lld bytes)", (long long)work_bytes,
+               (long long)qmlr_project_workspace_bytes(n_el, rep_dim, d));
+  // the basis is split into the caller's workspace on every call (a model keeps its split basis)
   cudaStream_t s = as_stream(stream);
-  uint16_t* basis = nullptr;
-  QMLR_CUDA_TRY(cudaMallocAsync(&basis, proj_tc_basis_bytes(n_el, rep_dim, d), s));
+  uint16_t* basis = aligned_basis(work);
   int rc = proj_tc_split_basis(U, n_el, rep_dim, d, (long)rep_dim * d, d, false, basis, s);
   if (rc == QMLR_OK)
     rc = proj_tc_launch(rep, rep_ld, rep_dim, 1, 0, basis, d, perm, elem_offsets, n_atoms, n_el, x, d, d, s);
-  cudaFreeAsync(basis, s);
   return rc;
 }
 
 extern "C" int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* perm,
                               const int32_t* elem_offsets, int32_t n_atoms, int32_t n_el,
                               const float* U, int32_t d, int32_t rep_dim, float* grad_rep,
-                              int32_t rep_ld, void* stream) {
+                              int32_t rep_ld, void* work, int64_t work_bytes, void* stream) {
   QMLR_REQUIRE(n_el >= 1 && n_el <= kMaxEl, "n_el must be in 1..8");
   QMLR_REQUIRE(is_pow2(d) && d >= 16 && d <= 512, "d must be a power of two in 16..512 (got %d)", d);
   QMLR_REQUIRE(rep_dim >= 1 && rep_ld >= rep_dim, "need 1 <= rep_dim <= rep_ld");
   QMLR_REQUIRE(n_part >= 1, "n_part must be >= 1");
   if (n_atoms == 0) return QMLR_OK;
   QMLR_REQUIRE(gx && perm && elem_offsets && U && grad_rep, "NULL pointer argument");
+  QMLR_REQUIRE(work && work_bytes >= qmlr_project_workspace_bytes(n_el, rep_dim, d),
+               "workspace too small (%lld < %lld bytes)", (long long)work_bytes,
+               (long long)qmlr_project_workspace_bytes(n_el, rep_dim, d));
   cudaStream_t s = as_stream(stream);
-  uint16_t* basis = nullptr;
-  QMLR_CUDA_TRY(cudaMallocAsync(&basis, proj_tc_basis_bytes(n_el, d, rep_dim), s));
+  uint16_t* basis = aligned_basis(work);
   int rc = proj_tc_split_basis(U, n_el, d, rep_dim, (long)rep_dim * d, d, true, basis, s);
   if (rc == QMLR_OK)
     rc = proj_tc_launch(gx, d, d, n_part, (long)n_atoms * d, basis, rep_dim, perm, elem_offsets, n_atoms, n_el,
                         grad_rep, rep_ld, rep_ld, s);
-  cudaFreeAsync(basis, s);
   return rc;
 }
 
@@ -186,9 +199,8 @@ extern "C" int qmlr_project_t(const float* gx, int32_t n_part, const int32_t* pe
 // Element grouping without any allocation (same kernels, fixed scratch).
 //
 // Some callers cannot allocate device memory at the moment they need the
-// grouping: a stream that is being captured into a CUDA graph, a host
-// framework that hands out all device memory from its own pool, or a
-// latency-critical service that must not block on the allocator. For them the
+// grouping: a host framework that hands out all device memory from its own
+// pool, or a latency-critical service that must not block on the allocator. For them the
 // counting sort's per-chunk counts and offsets live in a file-scope device
 // array sized for QMLR_GROUP_NOALLOC_MAX_ATOMS atoms; every device that loads
 // the library holds it (256 KiB) until the process exits.

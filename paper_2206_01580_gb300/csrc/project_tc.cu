@@ -533,22 +533,13 @@ int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_strid
   CUtensorMap map;
   int rc = tc::make_map(&map, basis, kp, (long)n_el * 3 * np);
   if (rc) return rc;
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(proj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)proj_tc_kernel, SMEM_BYTES));
   Args a{A, lda, K, n_part, a_part_stride, N, np, kp, perm, elem_offsets, n_el, C, ldc, zero_pad_to,
          device_error_ptr()};
   const int n_tiles = (std::max(N, zero_pad_to) + BN - 1) / BN;
   if (kp <= RK * BK && n_tiles > 1) {
     // short K, several column tiles: the CTA keeps its split rows and walks the tiles
-    static bool attr_r = false;
-    if (!attr_r) {
-      QMLR_CUDA_TRY(cudaFuncSetAttribute(proj_tc_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         R_SMEM_BYTES));
-      attr_r = true;
-    }
+    QMLR_CUDA_TRY(smem_attr_once((const void*)proj_tc_resident_kernel, R_SMEM_BYTES));
     proj_tc_resident_kernel<<<(n_atoms + BM - 1) / BM + n_el, kThreads, R_SMEM_BYTES, s>>>(map, a);
     QMLR_LAUNCH_CHECK();
     return QMLR_OK;

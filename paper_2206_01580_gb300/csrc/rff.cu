@@ -75,12 +75,7 @@ extern "C" int qmlr_rff(const float* x, int32_t d, const int32_t* mol_ptr, int32
   cudaStream_t s = as_stream(stream);
   if (n_mol == 0) return QMLR_OK;
   const size_t smem = ((size_t)d * (kRffTile + 1) + d) * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(rff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(((size_t)kRffMaxD * (kRffTile + 1) + kRffMaxD) * sizeof(float))));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)rff_kernel, (int)(((size_t)kRffMaxD * (kRffTile + 1) + kRffMaxD) * sizeof(float))));
   const int tiles = (n_features + kRffTile - 1) / kRffTile;
   // about four CTAs per SM over all feature tiles; each walks every chunks-th molecule
   const int chunks = std::max(1, std::min(n_mol, (4 * sm_count() + tiles - 1) / tiles));

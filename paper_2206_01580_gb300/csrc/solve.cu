@@ -14,6 +14,8 @@
 
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 namespace qmlr {
 
 constexpr int NB = 64;
@@ -1355,14 +1357,8 @@ constexpr size_t kPanelSmem = 2 * NB * (NB + 1) * sizeof(double);
 
 static int cholesky(double* L, long ldl, int n, cudaStream_t s, int* info) {
   int* err = device_error_ptr();
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kPanelSmem));
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kTrsmSmem));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)syrk_update_kernel, (int)kPanelSmem));
+  QMLR_CUDA_TRY(smem_attr_once((const void*)trsm_panel_kernel, (int)kTrsmSmem));
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int nb = std::min(NB, n - k0);
     potrf_diag_kernel<<<1, 256, 0, s>>>(L, ldl, k0, nb, err, info);
@@ -1416,18 +1412,33 @@ static int lookahead(Lookahead** out) {
 // first the next panel's columns, then the rest; the next panel's FP64 work
 // runs on a high-priority side stream beside the second part (the two touch
 // disjoint columns). Two split buffers alternate between panels.
+// The lookahead stream, its events and the diagonal-block pairs are one set per
+// device, so calls on one device run one at a time: the lock is held until the
+// call's work on the device has finished.
+static std::mutex& factor_mutex(int dev) {
+  static std::mutex mu[64];
+  return mu[dev];
+}
+
+static int cholesky_mixed_locked(double* L, long ldl, int n, __nv_bfloat16* parts2, cudaStream_t s, int* info);
+
 static int cholesky_mixed(double* L, long ldl, int n, __nv_bfloat16* parts2, cudaStream_t s, int* info) {
+  int dev = 0;
+  QMLR_CUDA_TRY(cudaGetDevice(&dev));
+  QMLR_REQUIRE(dev >= 0 && dev < 64, "device index out of range");
+  std::lock_guard<std::mutex> lock(factor_mutex(dev));
+  const int rc = cholesky_mixed_locked(L, ldl, n, parts2, s, info);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (rc) return rc;
+  QMLR_CUDA_TRY(e);
+  return QMLR_OK;
+}
+
+static int cholesky_mixed_locked(double* L, long ldl, int n, __nv_bfloat16* parts2, cudaStream_t s, int* info) {
   int* err = device_error_ptr();
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(syrk_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kPairsSmem));
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kTrsmSmem));
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kTrsmDfSmem));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)syrk_pairs_kernel, (int)kPairsSmem));
+  QMLR_CUDA_TRY(smem_attr_once((const void*)trsm_panel_kernel, (int)kTrsmSmem));
+  QMLR_CUDA_TRY(smem_attr_once((const void*)trsm_panel_df_kernel, (int)kTrsmDfSmem));
   Lookahead* la = nullptr;
   int rc = lookahead(&la);
   if (rc) return rc;

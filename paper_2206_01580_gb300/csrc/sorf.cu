@@ -488,12 +488,7 @@ static int launch_atoms(const SorfArgs& a, double* atom_e, int n_mol, double* E,
   constexpr int W = (D + 31) / 32;
   const size_t smem = (size_t)(D + 4) * 4 + (kStacksPerCta / 32) * 8 + (size_t)4 * W * kStacksPerCta * 4 +
                       (GRAD ? (D >= 32 ? (size_t)(kStacksPerCta / 32) * D * 4 : (size_t)nt * (D + 1) * 4) : 0);
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(sorf_atom_kernel<D, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)sorf_atom_kernel<D, GRAD>, 227 * 1024));
   if (a.n_atoms > 0) {
     dim3 grid(a.n_atoms, a.n_part);
     sorf_atom_kernel<D, GRAD><<<grid, nt, smem, s>>>(a, atom_e);
@@ -567,12 +562,7 @@ static int launch_mol(const SorfArgs& a0, int n_mol, cudaStream_t s) {
   const int nt = std::min(kStacksPerCta, ((a0.n_stack + 31) / 32) * 32);
   const size_t smem = (size_t)D * 4 + (size_t)a0.T * W * nt * 4 + (size_t)nt * (D + 4) * 4;
   QMLR_REQUIRE(smem <= 227 * 1024, "SORF shared memory request too large");
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(sorf_mol_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)sorf_mol_kernel<D>, 227 * 1024));
   // phases in stack-minor order for coalesced loads (stream-ordered scratch)
   const int nf = a0.n_stack * D;
   float* bT = nullptr;
@@ -609,12 +599,7 @@ static int launch_mode(const SorfArgs& a, int n_mol, cudaStream_t s) {
   const int nt = std::min(kStacksPerCta, ((a.n_stack + 31) / 32) * 32);
   const size_t smem = sorf_smem<D>(MODE, a.T, nt);
   QMLR_REQUIRE(smem <= 227 * 1024, "SORF shared memory request too large");
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(sorf_kernel<D, MODE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)sorf_kernel<D, MODE>, 227 * 1024));
   dim3 grid(n_mol, a.n_part);
   sorf_kernel<D, MODE><<<grid, nt, smem, s>>>(a);
   QMLR_LAUNCH_CHECK();
@@ -700,12 +685,7 @@ static int launch_force_rows(const float* tang, const int64_t* jac_ptr, const in
   const int nt = std::min(kStacksPerCta, ((n_stack + 31) / 32) * 32);
   const size_t smem = (size_t)T * W * nt * 4 + 16 * D * 4 + (size_t)D * (nt + 1) * 4;
   QMLR_REQUIRE(smem <= 227 * 1024, "force-row shared memory request too large");
-  static bool attr = false;
-  if (!attr) {
-    QMLR_CUDA_TRY(cudaFuncSetAttribute(force_rows_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
-    attr = true;
-  }
+  QMLR_CUDA_TRY(smem_attr_once((const void*)force_rows_kernel<D>, 227 * 1024));
   dim3 grid(n_mol, (n_stack + kStacksPerCta - 1) / kStacksPerCta);
   force_rows_kernel<D><<<grid, nt, smem, s>>>(tang, jac_ptr, mol_ptr, sin_t, sign_bits, T, n_stack,
                                               n_features, scale, rows, ld, row0);

@@ -76,8 +76,9 @@ _SIGS = {
     "qmlr_group_workspace_bytes": (C.c_int64, [I32]),
     "qmlr_group_by_element": (C.c_int, [P, I32, I32, P, P, P, I64, VP]),
     "qmlr_group_by_element_noalloc": (C.c_int, [P, I32, I32, P, P, VP]),
-    "qmlr_project": (C.c_int, [P, I32, I32, P, P, I32, I32, P, I32, P, VP]),
-    "qmlr_project_t": (C.c_int, [P, I32, P, P, I32, I32, P, I32, I32, P, I32, VP]),
+    "qmlr_project_workspace_bytes": (C.c_int64, [I32, I32, I32]),
+    "qmlr_project": (C.c_int, [P, I32, I32, P, P, I32, I32, P, I32, P, P, I64, VP]),
+    "qmlr_project_t": (C.c_int, [P, I32, P, P, I32, I32, P, I32, I32, P, I32, P, I64, VP]),
     "qmlr_sorf": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I32, P, VP]),
     "qmlr_model_file_write": (C.c_int, [C.c_char_p, C.POINTER(_Params), I32, I32, I32, I32, D, D,
                                         P, P, P, P]),
@@ -263,8 +264,10 @@ def project(rep, rep_dim: int, perm, offs, n_el: int, U, out=None):
     n = rep.shape[0]
     if out is None:
         out = torch.empty((n, d), device="cuda", dtype=torch.float32)
+    wb = lib().qmlr_project_workspace_bytes(n_el, rep_dim, d)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
     _check(lib().qmlr_project(_ptr(rep), rep.shape[1], rep_dim, _ptr(perm), _ptr(offs), n, n_el,
-                              _ptr(U), d, _ptr(out), _stream()))
+                              _ptr(U), d, _ptr(out), _ptr(work), wb, _stream()))
     return out
 
 
@@ -277,8 +280,10 @@ def project_t(gx, perm, offs, n_el: int, U, rep_dim: int, rep_ld: int | None = N
     rep_ld = rep_ld or rep_ld_of(rep_dim)
     if out is None:
         out = torch.empty((n, rep_ld), device="cuda", dtype=torch.float32)
+    wb = lib().qmlr_project_workspace_bytes(n_el, rep_dim, d)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
     _check(lib().qmlr_project_t(_ptr(gx), n_part, _ptr(perm), _ptr(offs), n, n_el, _ptr(U), d,
-                                rep_dim, _ptr(out), rep_ld, _stream()))
+                                rep_dim, _ptr(out), rep_ld, _ptr(work), wb, _stream()))
     return out
 
 

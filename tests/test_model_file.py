@@ -84,3 +84,41 @@ def test_model_file_rejects_inconsistent_sizes_on_write(q, tmp_path):
     assert rc == q.EINVAL
     assert b"bad model sizes" in L.qmlr_last_error()
     assert not (tmp_path / "x").exists()
+
+
+@pytest.mark.parametrize("rep_dim,d,T", [(700, 64, 3), (781, 64, 3), (780, 48, 3), (780, 64, 5), (780, 256, 3)])
+def test_model_file_write_rejects_what_a_model_cannot_hold(q, tmp_path, rep_dim, d, T):
+    """rep_dim must be the one the FCHL19 parameters define, d a power of two in
+    16..128 and T in 1..4 (what qmlr_model_create accepts)."""
+    import ctypes
+    p, U, signs, _, b, sigma, lam, alpha = _model(64, 512, 3)
+    cp = q.c_params(p)
+    L = q.lib()
+    big = np.zeros(5 * 781 * 256, np.float32)            # large enough for any size asked above
+    bits = np.zeros(512 * 5 * 8, np.uint32)
+    rc = L.qmlr_model_file_write(str(tmp_path / "x").encode(), ctypes.byref(cp), rep_dim, d, T, 512, 1.7, 1e-6,
+                                 big.ctypes.data, bits.ctypes.data, b.ctypes.data, alpha.ctypes.data)
+    assert rc == q.EINVAL
+    assert b"bad model sizes" in L.qmlr_last_error()
+    assert not (tmp_path / "x").exists()
+
+
+def _fnv1a64(data: bytes) -> int:
+    h = 14695981039346656037
+    for c in data:
+        h = ((h ^ c) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_model_file_read_rejects_a_rep_dim_the_params_do_not_define(q, tmp_path):
+    """A file whose checksum is valid but whose rep_dim disagrees with its FCHL19
+    parameters is refused before any array is sized from it."""
+    path, raw = _written(q, tmp_path)
+    off = 8 + 4 + 4 + 4 * 4 + 7 * 8                       # rep_dim field after the FCHL19 parameters
+    assert int.from_bytes(raw[off:off + 4], "little") == 780
+    bad = bytearray(raw[:-8])
+    bad[off:off + 4] = (700).to_bytes(4, "little")
+    bad += _fnv1a64(bytes(bad)).to_bytes(8, "little")
+    path.write_bytes(bytes(bad))
+    with pytest.raises(q.QMLRError, match="inconsistent sizes"):
+        q.load_model(path)

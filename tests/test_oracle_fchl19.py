@@ -204,3 +204,41 @@ def test_gradient_matches_central_differences():
             xm[k, a] -= h
             fd[k, a] = (np.sum(rep(xp, e, p) * g.numpy()) - np.sum(rep(xm, e, p) * g.numpy())) / (2 * h)
     np.testing.assert_allclose(grad.numpy(), fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
+
+
+# The three-body block layout (the representation's concatenation order, read
+# as row-major upper-triangular order over unordered element pairs a <= b),
+# written out by hand for five elements so that the pin does not depend on the
+# oracle's own pair_index.
+PAIR_TABLE_5 = {
+    (0, 0): 0, (0, 1): 1, (0, 2): 2, (0, 3): 3, (0, 4): 4,
+    (1, 1): 5, (1, 2): 6, (1, 3): 7, (1, 4): 8,
+    (2, 2): 9, (2, 3): 10, (2, 4): 11,
+    (3, 3): 12, (3, 4): 13,
+    (4, 4): 14,
+}
+
+
+def test_pair_index_is_the_upper_triangular_order():
+    seen = set()
+    for a in range(5):
+        for b in range(5):
+            want = PAIR_TABLE_5[(min(a, b), max(a, b))]
+            assert fchl19.pair_index(a, b, 5) == want, (a, b)
+            seen.add(want)
+    assert seen == set(range(15))          # a bijection onto 0..14
+
+
+@pytest.mark.parametrize("pair", sorted(PAIR_TABLE_5))
+def test_three_body_block_lands_at_its_table_offset(pair):
+    """A centre with exactly one triplet of neighbour elements (a, b): every
+    non-zero three-body entry of its row lies in the block the table names."""
+    p = P()
+    a, b = pair
+    x = [[0, 0, 0], [1.3, 0, 0], [0.4, 1.2, 0]]
+    out = rep(x, [C, a, b], p)[0]
+    off = p.n_el * p.n2 + PAIR_TABLE_5[pair] * p.n3 * 2
+    three = out[p.n_el * p.n2:]
+    nz = np.nonzero(three)[0] + p.n_el * p.n2
+    assert len(nz) > 0
+    assert nz.min() >= off and nz.max() < off + 2 * p.n3, (pair, nz.min(), nz.max(), off)

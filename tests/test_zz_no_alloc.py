@@ -1,9 +1,9 @@
 """The element grouping entry point that allocates nothing, called through the
 C ABI, gives the same permutation and offsets as the workspace version.
 
-Callers that cannot allocate device memory when they group atoms (work being
-captured into a CUDA graph, a framework that owns all device memory, a service
-that must not wait on the allocator) use qmlr_group_by_element_noalloc; it
+Callers that cannot allocate device memory when they group atoms (a framework
+that owns all device memory through its own pool, a service that must not wait
+on the allocator in its request path) use qmlr_group_by_element_noalloc; it
 keeps its scratch in a fixed array inside the library. This file is collected
 last so that a failure here does not hide the other tests' results.
 """
