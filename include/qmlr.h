@@ -55,7 +55,9 @@ int64_t qmlr_launch_count(void);
  * the current device. *host_code = 0 if no kernel recorded an error since the
  * last call; 1 = molecule larger than the launch's max_mol_atoms, 2 = element
  * index out of range, 3 = index out of range, 4 = bounded wait ran out,
- * 5 = matrix not positive definite. Returns QMLR_EDEVICE when *host_code != 0.
+ * 5 = matrix not positive definite, 6 = a SORF input whose phases would leave
+ * the range the feature kernels reduce exactly (see qmlr_sorf). Returns
+ * QMLR_EDEVICE when *host_code != 0.
  */
 int qmlr_device_status(void* stream, int32_t* host_code);
 
@@ -269,6 +271,14 @@ enum {
  * T is 1..4; d is a power of two, 16..128; N_F = n_features is a multiple of d.
  * In ENERGY mode with more than 128 stacks the per-part molecule sums are
  * added to out with FP64 atomics (out is zeroed first).
+ * Range: the cosines and sines reduce u = W x + b by 2 pi exactly while
+ * |u| < 2^17 pi (about 4.1e5). Since each stack of W is sqrt(d)/sigma times an
+ * orthogonal matrix, |u_i| <= (sqrt(d)/sigma) |x|_2 + |b_i|; an atom whose
+ * (sqrt(d)/sigma) |x|_2 exceeds 2^17 pi - 4 pi (or is not finite) is recorded
+ * as device error 6 (qmlr_device_status) and its features are not meaningful.
+ * The same check runs in qmlr_sorf_grad and the model's prediction.
+ * In PER_MOL mode the phases are copied once per call into stream-ordered
+ * scratch (N_F floats, stack index fastest) for coalesced loads.
  */
 int qmlr_sorf(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
               const uint32_t* sign_bits, int32_t T, const float* b, int32_t n_features,
@@ -557,6 +567,18 @@ int qmlr_predict_features(qmlr_model* m, const float* coords, const int32_t* ele
 int qmlr_predict_ef_from_features(qmlr_model* m, const float* coords, const int32_t* elem,
                                   const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
                                   double* energies, float* forces, void* stream);
+
+/*
+ * Chain rule of molecule energies through their forces, for automatic-
+ * differentiation wrappers: given F = -dE/dr from qmlr_predict_ef and an
+ * upstream gradient grad_E (double [n_mol]) of a loss L with respect to the
+ * energies, grad_coords[k][x] = dL/dr_{k,x} = -grad_E[mol(k)] F[k][x] (every
+ * atom belongs to exactly one molecule, so this is the whole product).
+ * forces and grad_coords float [n_atoms][3] (may be the same buffer).
+ * Asynchronous.
+ */
+int qmlr_energy_vjp(const float* forces, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+                    const double* grad_E, float* grad_coords, void* stream);
 
 /* ------------------------------------------------------------------------
  * Diagnostics: throughput of single functional units on the current device

@@ -30,6 +30,7 @@ enum DeviceError : int {
   DEV_BAD_INDEX = 3,
   DEV_TIMEOUT = 4,
   DEV_NOT_SPD = 5,
+  DEV_RANGE = 6,
 };
 
 __device__ __forceinline__ void record_device_error(int* err, int code) {

@@ -278,3 +278,29 @@ extern "C" int qmlr_predict_ef_from_features(qmlr_model* m, const float* coords,
   return predict_from_features_ws(m, m->ws, coords, elem, mol_ptr, n_mol, n_atoms, energies, forces,
                                   as_stream(stream));
 }
+
+// d(sum_m g[m] E_m) / d r_k = -g[mol(k)] F_k (each atom is in one molecule).
+__global__ void energy_vjp_kernel(const float* __restrict__ F, const int32_t* __restrict__ mol_ptr, int n_mol,
+                                  int n_atoms, const double* __restrict__ g, float* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n_atoms) return;
+  const int atom = t / 3;
+  int lo = 0, hi = n_mol;   // mol_ptr[lo] <= atom < mol_ptr[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (mol_ptr[mid] <= atom) lo = mid; else hi = mid;
+  }
+  out[t] = (float)(-g[lo] * (double)F[t]);
+}
+
+extern "C" int qmlr_energy_vjp(const float* forces, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+                               const double* grad_E, float* grad_coords, void* stream) {
+  QMLR_REQUIRE(n_mol >= 0 && n_atoms >= 0, "negative sizes");
+  if (n_atoms == 0) return QMLR_OK;
+  QMLR_REQUIRE(n_mol >= 1, "n_atoms > 0 but n_mol == 0");
+  QMLR_REQUIRE(forces && mol_ptr && grad_E && grad_coords, "NULL pointer argument");
+  energy_vjp_kernel<<<(3 * n_atoms + 255) / 256, 256, 0, as_stream(stream)>>>(forces, mol_ptr, n_mol, n_atoms,
+                                                                              grad_E, grad_coords);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}

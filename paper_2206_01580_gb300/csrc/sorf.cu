@@ -55,9 +55,9 @@ __device__ __forceinline__ void flip(float (&v)[D], const uint32_t* w) {
 
 // sin and cos of an FP32 argument: Cody-Waite reduction by 2*pi with a
 // two-part constant (2*pi = 6.28125 + 1.9353071795864769e-3; 6.28125 has an
-// 8-bit significand so k * 6.28125 is exact for |k| < 2^16), then the
-// hardware approximations on [-pi, pi] (absolute error ~2^-21). The feature
-// arguments here stay well inside |u| < 2^16.
+// 8-bit significand so k * 6.28125 is exact for |k| < 2^16, i.e. |u| < 2^17 pi),
+// then the hardware approximations on [-pi, pi] (absolute error ~2^-21). The
+// kernels check that bound per atom before they use it (check_range below).
 __device__ __forceinline__ void fast_sincos(float u, float* sn, float* cs) {
   const float k = rintf(u * 0.15915494309189535f);
   float r = fmaf(-k, 6.28125f, u);
@@ -78,6 +78,26 @@ __device__ __forceinline__ float fast_sin(float u) {
   return __sinf(r);
 }
 
+// |u_i| <= (sqrt(d)/sigma) |x|_2 + |b_i| (each stack of W is sqrt(d)/sigma times
+// an orthogonal matrix), so the reduction above is exact for the whole atom when
+// |x|_2^2 <= x2max = ((2^17 - 4) pi)^2 sigma^2 / d (4 pi of margin for b and rounding).
+inline float sorf_x2max(int d, double sigma) {
+  const double lim = (131072.0 - 4.0) * 3.14159265358979323846;
+  return (float)(lim * lim * sigma * sigma / d);
+}
+
+// One warp checks the staged x of an atom against x2max; a non-finite or
+// too-long x is recorded as DEV_RANGE.
+template <int D>
+__device__ __forceinline__ void check_range(const float* xs, float x2max, int lane, int* err) {
+  float q = 0.f;
+#pragma unroll
+  for (int i = lane; i < D; i += 32) q = fmaf(xs[i], xs[i], q);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if (lane == 0 && !(q <= x2max)) record_device_error(err, DEV_RANGE);
+}
+
 struct SorfArgs {
   const float* x;
   const int32_t* mol_ptr;
@@ -89,6 +109,8 @@ struct SorfArgs {
   int n_atoms, n_stack, T, n_features, n_part;
   float scale;  // (sqrt(d)/sigma) / d^{T/2}
   float pref;   // sqrt(2/N_F)
+  float x2max;  // largest |x|^2 of an atom whose phases the reduction handles exactly
+  int* err;     // device error word
   // layout of b and alpha: element (stack s, index i) at s*sstr + i*istr
   // (natural order: sstr = d, istr = 1; stack-minor: sstr = 1, istr = n_stack)
   long sstr = 0, istr = 1;
@@ -123,6 +145,7 @@ sorf_kernel(SorfArgs a) {
     __syncthreads();
     for (int i = tid; i < D; i += nt) xs[i] = __ldg(a.x + (long)atom * D + i);
     __syncthreads();
+    if (tid < 32 && part == 0) check_range<D>(xs, a.x2max, tid, a.err);
     float v[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = xs[i];
@@ -246,6 +269,7 @@ sorf_mol_kernel(SorfArgs a) {
     for (int i = tid; i < D / 4; i += nt)
       reinterpret_cast<float4*>(xs)[i] = __ldg(reinterpret_cast<const float4*>(a.x + (long)atom * D) + i);
     __syncthreads();
+    if (tid < 32 && part == 0) check_range<D>(xs, a.x2max, tid, a.err);
     float v[D];
 #pragma unroll
     for (int q = 0; q < D / 4; ++q) {
@@ -393,6 +417,7 @@ sorf_atom_kernel(SorfArgs a, double* __restrict__ atom_e) {
   for (int i = tid; i < D; i += nt) xs[i] = __ldg(a.x + (long)atom * D + i);
   for (int k = 0; k < a.T * W; ++k) sg[k * nt + tid] = active ? __ldg(a.sign_bits + (long)s * a.T * W + k) : 0u;
   __syncthreads();
+  if (tid < 32 && part == 0) check_range<D>(xs, a.x2max, tid, a.err);
   float v[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) v[i] = xs[i];
@@ -529,6 +554,8 @@ SorfArgs make_sorf_args(const float* x, int d, const int32_t* mol_ptr, int n_ato
   a.n_part = (a.n_stack + kStacksPerCta - 1) / kStacksPerCta;
   a.scale = (float)(sqrt((double)d) / sigma / pow((double)d, 0.5 * T));
   a.pref = (float)sqrt(2.0 / n_features);
+  a.x2max = sorf_x2max(d, sigma);
+  a.err = device_error_ptr();
   a.sstr = stack_minor ? 1 : d;
   a.istr = stack_minor ? a.n_stack : 1;
   return a;
@@ -645,6 +672,8 @@ static int sorf_dispatch(const float* x, int d, const int32_t* mol_ptr, int n_mo
   a.n_part = (a.n_stack + kStacksPerCta - 1) / kStacksPerCta;
   a.scale = (float)(sqrt((double)d) / sigma / pow((double)d, 0.5 * T));
   a.pref = (float)sqrt(2.0 / n_features);
+  a.x2max = sorf_x2max(d, sigma);
+  a.err = device_error_ptr();
   cudaStream_t s = as_stream(stream);
   if ((mode == M_ENERGY || mode == M_ENERGY_GRAD) && a.n_part > 1)
     QMLR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * n_mol, s));

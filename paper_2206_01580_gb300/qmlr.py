@@ -112,6 +112,7 @@ _SIGS = {
     "qmlr_model_set_alpha_device": (C.c_int, [VP, P, VP]),
     "qmlr_model_reserve": (C.c_int, [VP, I32]),
     "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
+    "qmlr_energy_vjp": (C.c_int, [P, P, I32, I32, P, P, VP]),
     "qmlr_unit_rates": (C.c_int, [P, I32, VP]),
     "qmlr_predict_features": (C.c_int, [VP, P, P, P, I32, I32, VP]),
     "qmlr_predict_ef_from_features": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
@@ -652,6 +653,52 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# autograd: energies with forces from the hand-written adjoint
+
+
+class FCHL19SORFEnergy(torch.autograd.Function):
+    """Molecule energies E [n_mol] (float64) of a device-resident Model as a
+    differentiable function of the coordinates [n_atoms, 3] (float32).
+
+    Forward runs the model's path (FCHL19 -> per-element projection -> SORF
+    with the weight dot product, atomic energies summed per molecule); when the
+    coordinates require a gradient it also runs the hand-written adjoint in the
+    same call (SORF backward -> transposed projection -> FCHL19 vector-Jacobian
+    product) and keeps F = -dE/dr. Backward maps an upstream gradient g [n_mol]
+    to dL/dr_k = -g[mol(k)] F_k (qmlr_energy_vjp): every atom belongs to one
+    molecule, so that is the whole chain rule. Double backward is not supported.
+
+        E = FCHL19SORFEnergy.apply(coords, model, elem, mol_ptr)
+    """
+
+    @staticmethod
+    def forward(ctx, coords, model, elem, mol_ptr):
+        elem = _dev(elem, torch.int32)
+        mol_ptr = _dev(mol_ptr, torch.int32)
+        need = ctx.needs_input_grad[0]
+        E, F = model.predict(coords.detach(), elem, mol_ptr, forces=need)
+        if need:
+            ctx.save_for_backward(F, mol_ptr)
+            ctx.coords_dtype = coords.dtype
+        return E
+
+    @staticmethod
+    @torch.autograd.function.once_differentiable
+    def backward(ctx, grad_E):
+        F, mol_ptr = ctx.saved_tensors
+        g = _dev(grad_E, torch.float64)
+        out = torch.empty_like(F)
+        _check(lib().qmlr_energy_vjp(_ptr(F), _ptr(mol_ptr), mol_ptr.shape[0] - 1, F.shape[0], _ptr(g),
+                                     _ptr(out), _stream()))
+        return out.to(ctx.coords_dtype), None, None, None
+
+
+def energy(coords, model: "Model", elem, mol_ptr):
+    """E [n_mol] through FCHL19SORFEnergy (differentiable in coords)."""
+    return FCHL19SORFEnergy.apply(coords, model, elem, mol_ptr)
 
 
 # ----------------------------------------------------------------------------
