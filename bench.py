@@ -33,9 +33,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "µs/atom E+F predict, train s at 16k feats, p50/p99 latency vs plain FP32 form"
-# Gram form of the training step: 1 = 2-way BF16 split (three tensor-core
-# products), 2 = 3-way split (six products); set by --gram-split.
-GRAM_FORM = 1
+# Gram form of the training step (the preconditioner input): a qmlr precision
+# (1 = 2-way BF16 split, three tensor-core products; 2 = 3-way split, six
+# products; 3 = one BF16 part; 4 = e4m3 with per-feature scales), the K blocks
+# summed in the tensor cores' accumulator between promotions (0 = the whole
+# K range) and the tile width; set by --gram-form / --gram-promote / --gram-tile.
+GRAM = {"precision": 1, "promote": 1, "tile": 128}
+GRAM_FORMS = {"x3": 1, "x6": 2, "x1": 3, "fp8": 4}
 
 
 def parse():
@@ -53,8 +57,18 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
-    ap.add_argument("--gram-split", type=int, default=2, choices=[2, 3],
-                    help="BF16 split of the tensor-core Gram: 2 (three products) or 3 (six products)")
+    ap.add_argument("--gram-form", default="x3", choices=sorted(GRAM_FORMS),
+                    help="tensor-core Gram: x3 (2-way BF16 split), x6 (3-way), x1 (one BF16 part), "
+                         "fp8 (e4m3, per-feature scales)")
+    ap.add_argument("--gram-promote", type=int, default=None,
+                    help="K blocks per tensor-core accumulation (0: whole K); default 1 for x3/x6, 0 otherwise")
+    ap.add_argument("--gram-tile", type=int, default=None, choices=[128, 256],
+                    help="tile width; default 128 for x3/x6, 256 otherwise")
+    ap.add_argument("--shift", type=float, default=None,
+                    help="relative diagonal shift of the preconditioner factor (default: the form's)")
+    ap.add_argument("--gram-sweep", action="store_true",
+                    help="instead of the step: train with each Gram form and shift on the workload and "
+                         "report Gram, factor and PCG times, iterations and training MAE")
     ap.add_argument("--factor", default="mixed", choices=["mixed", "fp64"],
                     help="preconditioner factor: tensor-core trailing updates (mixed) or FP64 throughout")
     ap.add_argument("--feature-sweep", action="store_true",
@@ -235,10 +249,10 @@ def ef_training_phase(pcg_iters, pcg_tol, factor):
         ev[0].record(s)
         rows = pipeline.energy_force_rows(tr, spec, U)
         ev[1].record(s)
-        G = qmlr.gram(rows, GRAM_FORM)
+        G = pipeline.gram(rows, GRAM["precision"], GRAM["promote"], GRAM["tile"])
         ev[2].record(s)
         alpha, it, rel = qmlr.gram_solve(G, rows, y, w.lam, max_iter=pcg_iters, tol=pcg_tol, factor=factor,
-                                         shift=pipeline.DEFAULT_SHIFT[GRAM_FORM])
+                                         shift=GRAM["shift"])
         ev[3].record(s)
         torch.cuda.synchronize()
         so = qmlr.last_solve
@@ -373,7 +387,8 @@ def run_ours(args, rank, world):
     # solve's kernels on the main stream are scheduled first whenever they wait
     side = torch.cuda.Stream(priority=0)
 
-    def step(b: pipeline.Batch, yv, precision=GRAM_FORM, timing=None):
+    def step(b: pipeline.Batch, yv, precision=None, timing=None):
+        precision = GRAM["precision"] if precision is None else precision
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
         sev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
@@ -383,14 +398,13 @@ def run_ours(args, rank, world):
         ev[2].record(stream)
         Z = qmlr.sorf(x, b.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
         ev[3].record(stream)
-        if precision in (qmlr.GRAM_BF16X3, qmlr.GRAM_BF16X6):
-            zt = qmlr.gram_operand(Z, 2 if precision == qmlr.GRAM_BF16X3 else 3)
-            ev[7].record(stream)
-            G = qmlr.gram(Z, precision, operand=zt)
-            del zt
+        zt = pipeline.gram_operand(Z, precision)
+        ev[7].record(stream)
+        if precision == GRAM["precision"]:
+            G = pipeline.gram(Z, precision, GRAM["promote"], GRAM["tile"], operand=zt)
         else:
-            ev[7].record(stream)
-            G = qmlr.gram(Z, precision)
+            G = pipeline.gram(Z, precision, operand=zt)
+        del zt
         ev[4].record(stream)
         # the prediction's weight-independent half (representations, grouping,
         # projection) runs on a second stream beside the solve
@@ -402,7 +416,8 @@ def run_ours(args, rank, world):
         alpha, it, rel = qmlr.gram_solve(G, Z, yv, w.lam, method=qmlr.SOLVE_PCG,
                                          max_iter=args.pcg_iters if precision != qmlr.GRAM_FP32 else 4 * args.pcg_iters,
                                          tol=args.pcg_tol, factor=factor,
-                                         shift=pipeline.DEFAULT_SHIFT[precision])
+                                         shift=GRAM["shift"] if precision == GRAM["precision"]
+                                         else pipeline.DEFAULT_SHIFT[precision])
         ev[5].record(stream)
         model.set_alpha_device(alpha)
         stream.wait_stream(side)
@@ -503,8 +518,7 @@ def run_ours(args, rank, world):
     nf = w.n_features
     rows = n_mol
     bf16_sust = peaks.get("bf16_tflops_sustained", 1707.8)
-    n_split = 2 if GRAM_FORM == 1 else 3
-    n_prod = 3 if n_split == 2 else 6
+    gdesc = gram_description()
     # ALU peak of the SORF kernels (adds dominate): SMs x 128 FP32 lanes x max SM clock
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sm_max_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -516,14 +530,16 @@ def run_ours(args, rank, world):
     n_stack = nf // w.d
     sorf_ops_atom = n_stack * w.n_transform * w.d * int(math.log2(w.d)) + 6 * nf
     cands = {
-        "gram": {"kernel": f"tc::gram_persist_kernel<{n_split}> ({n_split}-way BF16 split, tcgen05, "
-                           "one CTA per SM, wave-aligned loads)",
+        "gram": {"kernel": gdesc["kernel"],
                  "bound": "tensor",
-                 "achieved": rows * nf * nf / (st["gram"] * 1e-3) / 1e12, "peak": bf16_sust / n_prod,
+                 "achieved": rows * nf * nf / (st["gram"] * 1e-3) / 1e12,
+                 "peak": bf16_sust * gdesc["rate"] / gdesc["products"],
                  "unit": "TFLOP/s",
                  "work": f"N_rows*N_F^2 = {rows * nf * nf:.3e} flop (symmetric half, 2 flop/MAC)",
-                 "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained / {n_prod} ({n_prod} BF16 "
-                                "products per split product)"},
+                 "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained x {gdesc['rate']} / "
+                                f"{gdesc['products']} ({gdesc['products']} tensor-core products per Gram "
+                                f"product; {gdesc['rate']} x the BF16 rate for its operand type, the nominal "
+                                "dense ratio)"},
         "sorf_Z": {"kernel": "qmlr::sorf_mol_kernel<128> (SORF + segment sum into Z)", "bound": "alu",
                    "achieved": sorf_ops_atom * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": fp32_add_peak,
                    "unit": "TFLOP/s",
@@ -544,10 +560,11 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": us_per_atom(ms, n_atoms, world), "unit": "us/atom", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": f"f32 features, bf16 {n_split}-way split gram, f64 solve", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": f"f32 features, {gdesc['dtype']} gram, f64 solve",
+        "data": "synthetic",
         "config": {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
                    "n_molecules": n_mol, "n_atoms": n_atoms, "n_features": nf, "d": w.d,
-                   "n_transform": w.n_transform, "gram": f"{n_split}-way bf16 split, {n_prod} tcgen05 products, per-K-block FP32 Kahan promotion "
+                   "n_transform": w.n_transform, "gram": gdesc["text"] + f", shift {GRAM['shift']:.3g} x max G_ii "
                            "(preconditioner input)",
                    "solve": ("mixed-precision cholesky (fp64 panels, tcgen05 trailing updates)"
                              if args.factor == "mixed" else "fp64 cholesky") + " + pcg (exact fp64 operator)",
@@ -653,10 +670,100 @@ def run_feature_sweep(args):
         "alu_peak_t_op_s": alu_peak, "sorf_Z": sorf_pts, "rff_Z": rff_pts}}), flush=True)
 
 
+def run_gram_sweep(args):
+    """Training on the workload with each preconditioner Gram form and shift:
+    Gram (operand + product) time, factor and PCG times, iterations, final
+    residual and training MAE (|Z alpha - y|), all by CUDA events. Setup
+    (features, Z) untimed. Prints one JSON line."""
+    import torch
+    from paper_2206_01580_gb300 import pipeline, qmlr
+    from paper_2206_01580_gb300.params import from_table
+
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream(priority=-100))
+    w, _ = build_workload(args.scale)
+    mols = w.mols
+    p = from_table(w.params_column, n2=w.n2, n3=w.n3)
+    spec = pipeline.spec_from(p, w.d, w.signs, w.b, w.sigma)
+    batch = pipeline.Batch.from_host(mols.coords, mols.elem, mols.mol_ptr)
+    y = torch.as_tensor(w.energies).cuda()
+    rep, perm, offs = pipeline.representations(batch, spec)
+    U = pipeline.fit_pca(rep, perm, offs, spec)
+    Z = pipeline.feature_matrix(batch, spec, U, rep, perm, offs)
+    del rep, perm, offs
+    factor = qmlr.FACTOR_MIXED if args.factor == "mixed" else qmlr.FACTOR_FP64
+    s = torch.cuda.current_stream()
+    configs = [(1, 1, 128, -2.0 ** -15), (1, 1, 128, -2.0 ** -14),
+               (1, 4, 128, -2.0 ** -14), (1, 4, 128, -2.0 ** -13),
+               (1, 0, 256, -2.0 ** -13), (1, 0, 256, -2.0 ** -12), (1, 0, 256, -2.0 ** -11),
+               (3, 0, 256, -2.0 ** -12), (3, 0, 256, -2.0 ** -10), (3, 0, 256, -2.0 ** -8),
+               (3, 0, 128, -2.0 ** -10),
+               (4, 0, 256, -2.0 ** -8), (4, 0, 256, -2.0 ** -6), (4, 0, 256, -2.0 ** -4),
+               (0, 0, 0, -2.0 ** -13), (0, 0, 0, -2.0 ** -12), (0, 0, 0, -2.0 ** -10)]
+    pts = []
+    for prec, promote, tile, shift in configs:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for rep_i in range(2):            # the first pass warms up kernels and the allocator
+            ev[0].record(s)
+            zt = pipeline.gram_operand(Z, prec)
+            ev[1].record(s)
+            G = pipeline.gram(Z, prec, promote if prec else None, tile if prec else None, operand=zt)
+            ev[2].record(s)
+            del zt
+            try:
+                alpha, it, rel = qmlr.gram_solve(G, Z, y, w.lam, max_iter=args.pcg_iters, tol=args.pcg_tol,
+                                                 factor=factor, shift=shift)
+                ok = True
+            except qmlr.QMLRError as e:
+                ok, it, rel, alpha = False, -1, float("nan"), None
+                err = str(e)
+            ev[3].record(s)
+            torch.cuda.synchronize()
+            del G
+        so = qmlr.last_solve
+        pt = {"precision": prec, "promote": promote, "tile": tile, "shift": shift,
+              "operand_ms": ev[0].elapsed_time(ev[1]), "gram_ms": ev[1].elapsed_time(ev[2]),
+              "solve_ms": ev[2].elapsed_time(ev[3]), "train_tail_ms": ev[0].elapsed_time(ev[3]),
+              "pcg_iters": it, "rel_resid": rel}
+        if ok:
+            pt.update({"factor_ms": so.factor_ms, "refine_ms": so.refine_ms, "shift_used": so.shift_used,
+                       "train_mae_eV": float(torch.mean(torch.abs(Z.double() @ alpha - y)).item())})
+        else:
+            pt["error"] = err
+        pts.append(pt)
+        print(json.dumps(pt), flush=True)
+    print(json.dumps({"gram_sweep": {
+        "workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
+        "n_rows": mols.n_mol, "n_features": w.n_features, "pcg_max_iter": args.pcg_iters, "pcg_tol": args.pcg_tol,
+        "points": pts}}), flush=True)
+
+
+def gram_description():
+    """Kernel name, tensor-core products per Gram product, rate relative to BF16
+    and a text description of the training step's Gram form."""
+    prec, promote, tile = GRAM["precision"], GRAM["promote"], GRAM["tile"]
+    S = {1: 2, 2: 3, 3: 1, 4: 1}[prec]
+    f8 = prec == 4
+    kahan = prec in (1, 2) and tile == 128
+    acc = "whole K in TMEM" if promote == 0 else f"{promote} K block(s) per TMEM accumulation"
+    sums = "FP32 Kahan register sums" if kahan else "FP32 register sums"
+    kind = "e4m3 (per-feature scales)" if f8 else (f"{S}-way bf16 split" if S > 1 else "one-part bf16")
+    products = {1: 3, 2: 6, 3: 1, 4: 1}[prec]
+    return {"kernel": f"tc::gram_persist_kernel<{S}, {str(f8).lower()}, {tile}, {str(kahan).lower()}> "
+                      f"({kind}, tcgen05, 128x{tile} tiles, one CTA per SM, wave-aligned loads)",
+            "products": products, "rate": 2 if f8 else 1,
+            "dtype": "e4m3" if f8 else (f"bf16 {S}-way split" if S > 1 else "bf16"),
+            "text": f"{kind}, {products} tcgen05 product(s), {acc}, {sums}, 128x{tile} tiles"}
+
+
 def main():
-    global GRAM_FORM
     args = parse()
-    GRAM_FORM = 1 if args.gram_split == 2 else 2
+    prec = GRAM_FORMS[args.gram_form]
+    from paper_2206_01580_gb300 import pipeline
+    p0, t0 = pipeline.DEFAULT_TC[prec]
+    GRAM.update({"precision": prec, "promote": p0 if args.gram_promote is None else args.gram_promote,
+                 "tile": t0 if args.gram_tile is None else args.gram_tile,
+                 "shift": pipeline.DEFAULT_SHIFT[prec] if args.shift is None else -abs(args.shift)})
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -664,6 +771,9 @@ def main():
     elif args.feature_sweep:
         if rank == 0:
             run_feature_sweep(args)
+    elif args.gram_sweep:
+        if rank == 0:
+            run_gram_sweep(args)
     else:
         run_ours(args, rank, world)
 

@@ -344,13 +344,16 @@ int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_
 enum {
   QMLR_GRAM_FP32 = 0,   /* plain FP32 SIMT product (comparison form, no compensation) */
   QMLR_GRAM_BF16X3 = 1, /* tensor cores, 2-way BF16 split S0+S1: S0'S0 + S0'S1 + S1'S0 (~2^-16 rel.) */
-  QMLR_GRAM_BF16X6 = 2  /* tensor cores, 3-way BF16 split: the six products of order <= 2 (~2^-24 rel.) */
+  QMLR_GRAM_BF16X6 = 2, /* tensor cores, 3-way BF16 split: the six products of order <= 2 (~2^-24 rel.) */
+  QMLR_GRAM_BF16X1 = 3, /* tensor cores, one BF16 part: S0'S0 (Z rounded to 8 significant bits) */
+  QMLR_GRAM_FP8X1 = 4   /* tensor cores (kind::f8f6f4), one e4m3 part with per-feature power-of-two
+                           scales: Q'Q / (s_i s_j), Q = e4m3(Z s) (4 significant bits) */
 };
 
 /*
  * Split-precision Gram operand, transposed (feature-major, rows contiguous):
  *   S0 = bf16(Z), S1 = bf16(Z - S0), S2 = bf16(Z - S0 - S1)   (round to nearest even)
- *   zt[q][f][r] = S_q[r][f] for q < n_split (2 or 3); bf16 bit patterns,
+ *   zt[q][f][r] = S_q[r][f] for q < n_split (1, 2 or 3); bf16 bit patterns,
  *   [n_split][n_features][k_pad]; k_pad >= n_rows, k_pad % 64 == 0; rows
  *   n_rows..k_pad-1 are written as zeros.
  *   Z float [n_rows][ldz]
@@ -359,10 +362,24 @@ int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_features, int64_
                       int32_t n_split, uint16_t* zt, int64_t k_pad, void* stream);
 
 /*
+ * The e4m3 Gram operand (QMLR_GRAM_FP8X1), transposed like the split operand:
+ *   inv_scale float [n_features]: 1/s_f with s_f = 2^floor(log2(448 / max_r |Z[r][f]|))
+ *                                 (s_f = 1 for an all-zero feature)
+ *   zt uint8 [n_features][k_pad]: e4m3 bit patterns of s_f Z[r][f], rounded to
+ *                                 nearest even, saturated at 448; rows n_rows..k_pad-1 zero
+ *   k_pad >= n_rows, k_pad % 128 == 0. Deterministic. Asynchronous.
+ */
+int qmlr_gram_operand_fp8(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz, uint8_t* zt,
+                          int64_t k_pad, float* inv_scale, void* stream);
+
+/*
  * G = Z^T Z as a full symmetric float [n_features][n_features] matrix.
  *   QMLR_GRAM_FP32:   reads Z [n_rows][ldz] (zt may be NULL)
  *   QMLR_GRAM_BF16X3: reads zt with n_split = 2; QMLR_GRAM_BF16X6: n_split = 3
  *                     (Z may be NULL); n_features % 128 == 0.
+ *   QMLR_GRAM_BF16X1: reads zt with n_split = 1; the qmlr_gram_tc defaults
+ *                     (256-wide tiles, the whole K range in the accumulator);
+ *                     n_features % 256 == 0.
  * Deterministic: every element is summed in a fixed order. Split forms with
  * at least 4 x (SM count) tiles of 128 x 128 run as one cooperative launch of
  * one CTA per SM (same per-tile arithmetic, bitwise the same G); that launch
@@ -371,6 +388,31 @@ int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_features, int64_
  */
 int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
               const uint16_t* zt, int64_t k_pad, float* G, void* stream);
+
+/*
+ * The tensor-core Gram with its tiling and accumulation chosen by the caller
+ * (the forms that only build a preconditioner can trade accuracy for time).
+ *   precision  QMLR_GRAM_BF16X1 / BF16X3 / BF16X6 (zt from qmlr_gram_operand with
+ *              n_split 1 / 2 / 3, k_pad % 64 == 0) or QMLR_GRAM_FP8X1 (zt and
+ *              inv_scale from qmlr_gram_operand_fp8, k_pad % 128 == 0)
+ *   promote    K blocks (128-byte lines of K: 64 bf16 or 128 e4m3 values) summed
+ *              in the tensor cores' FP32 accumulator before that sum is added
+ *              into FP32 register sums; 1 = every block (the accumulator's
+ *              truncating adds then span one block), 0 = the whole K range
+ *   tile_n     columns per 128-row tile: 128 or 256 (0: 256 for BF16X1 and FP8X1,
+ *              128 otherwise); n_features must be a multiple of it
+ * Register sums are Kahan sums for BF16X3/BF16X6 with 128-wide tiles, plain
+ * FP32 sums otherwise; BF16X6 supports 128-wide tiles only. One cooperative
+ * launch of one CTA per SM (fewer for small matrices); a 4-byte counter comes
+ * from the stream-ordered allocator. Deterministic. Asynchronous.
+ */
+typedef struct qmlr_gram_opts {
+  int32_t precision;
+  int32_t promote;
+  int32_t tile_n;
+} qmlr_gram_opts;
+int qmlr_gram_tc(const qmlr_gram_opts* opts, const void* zt, int64_t k_pad, int32_t n_features,
+                 const float* inv_scale, float* G, void* stream);
 
 /* c = Z^T y in FP64 (y double [n_rows], c double [n_features]); fixed-order sums. */
 int64_t qmlr_zty_workspace_bytes(int64_t n_rows, int32_t n_features);

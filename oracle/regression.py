@@ -10,6 +10,13 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   magnitude is positive; columns beyond the numerical rank are zero.
 * Feature matrix (atomic energy partition, RFF section): the row of molecule
   m is Z_m = sum over the atoms I of m of z(rho_I).
+* Reduced-precision Gram operands (the preconditioner inputs of the solve):
+  ``round_to_format`` rounds to a binary floating-point format given by its
+  fraction bits, smallest normal exponent and largest finite value (round to
+  nearest, ties to even, saturating): bfloat16 is (7, -126, (2 - 2^-7) 2^127),
+  e4m3 is (3, -6, 448). ``quantized_gram`` is the exact product Q^T Q of the
+  rounded operand, for one bfloat16 part or for e4m3 with a power-of-two
+  scale per feature (s_f = 2^floor(log2(448 / max |Z[:, f]|))).
 * Normal equations (RFF section): (Z^T Z + lambda I) alpha = Z^T y, with
   energy and force rows stacked vertically for energy+force training. Solved
   here by a dense float64 Cholesky factorisation (the matrix is symmetric
@@ -101,3 +108,46 @@ def ridge_solve(Z: np.ndarray, y: np.ndarray, lam: float, refine: int = 1):
     """Solve the regularised normal equations for rows Z [n_rows, N_F] and targets y."""
     A, c = normal_equations(Z, y, lam)
     return cholesky_solve(A, c, refine)
+
+
+BF16_FORMAT = (7, -126, (2.0 - 2.0 ** -7) * 2.0 ** 127)
+E4M3_FORMAT = (3, -6, 448.0)
+
+
+def round_to_format(x, fmt) -> np.ndarray:
+    """Nearest value (ties to even) of the format (fraction bits, smallest normal
+    exponent, largest finite value); magnitudes above the largest finite value
+    become it (saturation). Below the smallest normal the spacing stays
+    2^(emin - fraction bits) (subnormals)."""
+    mant, emin, vmax = fmt
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(np.where(a > 0, a, 1.0))      # a = m 2^ex, m in [0.5, 1)
+    e = np.maximum(ex - 1, emin)                   # exponent of the binade (or of the subnormals)
+    quantum = np.ldexp(1.0, e - mant)
+    q = np.minimum(np.round(a / quantum) * quantum, vmax)   # np.round: ties to even
+    return np.copysign(q, x)
+
+
+def fp8_feature_scales(Z) -> np.ndarray:
+    """s_f = 2^floor(log2(448 / max_r |Z[r, f]|)), 1 for an all-zero feature."""
+    amax = np.max(np.abs(np.asarray(Z, dtype=np.float64)), axis=0)
+    s = np.ones_like(amax)
+    nz = amax > 0
+    _, ex = np.frexp(448.0 / amax[nz])
+    s[nz] = np.ldexp(1.0, ex - 1)
+    return s
+
+
+def quantized_gram(Z, form: str) -> np.ndarray:
+    """Q^T Q in float64 for the operand rounded to 'bf16' or to 'e4m3' with
+    per-feature scales (then divided by s_i s_j)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    if form == "bf16":
+        Q = round_to_format(Z, BF16_FORMAT)
+        return Q.T @ Q
+    if form == "e4m3":
+        s = fp8_feature_scales(Z)
+        Q = round_to_format(Z * s[None, :], E4M3_FORMAT)
+        return (Q.T @ Q) / np.outer(s, s)
+    raise ValueError(form)

@@ -15,6 +15,7 @@
 // contiguous: the K-major layout the tensor-core kernel reads with TMA).
 #include "common.cuh"
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 namespace qmlr {
 
@@ -47,6 +48,60 @@ __global__ void gram_operand_kernel(const float* __restrict__ Z, long n_rows, in
         st[q * part + (long)f * k_pad + r] = h;
         v -= __bfloat162float(h);
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// e4m3 operand with per-feature power-of-two scales: s_f = 2^floor(log2(448 /
+// max_r |Z[r][f]|)) (1 for an all-zero feature), Q[f][r] = e4m3(s_f Z[r][f])
+// rounded to nearest even and saturated at 448, inv_scale[f] = 1 / s_f. Since
+// G = Z^T Z and each feature has its own scale, the tensor-core products of Q
+// give G_ij = (Q^T Q)_ij / (s_i s_j) exactly up to the rounding of Q.
+
+// |Z| column maxima as float bits (non-negative floats order like their bits).
+__global__ void column_absmax_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz,
+                                     unsigned* __restrict__ amax) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_features) return;
+  const long r0 = (long)blockIdx.y * 1024, r1 = min(n_rows, r0 + 1024);
+  float m = 0.f;
+  for (long r = r0; r < r1; ++r) m = fmaxf(m, fabsf(__ldg(Z + r * ldz + f)));
+  if (m > 0.f) atomicMax(amax + f, __float_as_uint(m));
+}
+
+__global__ void fp8_scales_kernel(int n_features, float* __restrict__ inv_scale) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_features) return;
+  const float m = __uint_as_float(reinterpret_cast<unsigned*>(inv_scale)[f]);
+  float inv = 1.0f;
+  if (m > 0.f && isfinite(m)) {
+    int e;
+    frexpf(448.0f / m, &e);            // 448/m = mant * 2^e, mant in [0.5, 1)
+    inv = ldexpf(1.0f, 1 - e);         // 1 / s with s = 2^(e-1) <= 448/m
+  }
+  inv_scale[f] = inv;
+}
+
+__global__ void gram_operand_fp8_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz,
+                                        const float* __restrict__ inv_scale, uint8_t* __restrict__ q8,
+                                        long k_pad) {
+  __shared__ float tile[kTT][kTT + 1];
+  const long r0 = (long)blockIdx.x * kTT;
+  const int f0 = blockIdx.y * kTT;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int j = ty; j < kTT; j += 8) {
+    const long r = r0 + j;
+    const int f = f0 + tx;
+    tile[j][tx] = (r < n_rows && f < n_features) ? __ldg(Z + r * ldz + f) : 0.f;
+  }
+  __syncthreads();
+  for (int j = ty; j < kTT; j += 8) {
+    const int f = f0 + j;
+    const long r = r0 + tx;
+    if (f < n_features && r < k_pad) {
+      const float v = tile[tx][j] / __ldg(inv_scale + f);   // times s_f (a power of two: exact)
+      q8[(long)f * k_pad + r] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
     }
   }
 }
@@ -144,6 +199,8 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int n_parts, i
 }
 
 int gram_split_tc(int n_split, const uint16_t* zt, long k_pad, int n_features, float* G, cudaStream_t s);
+int gram_tc_form(int form, int tile_n, int promote, const void* zt, long k_pad, int n_features,
+                 const float* inv_scale, float* G, cudaStream_t s);
 
 }  // namespace qmlr
 
@@ -152,7 +209,7 @@ using namespace qmlr;
 extern "C" int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
                                  int32_t n_split, uint16_t* zt, int64_t k_pad, void* stream) {
   QMLR_REQUIRE(n_rows >= 0 && n_features >= 1 && ldz >= n_features, "bad Z shape");
-  QMLR_REQUIRE(n_split == 2 || n_split == 3, "n_split must be 2 or 3 (got %d)", n_split);
+  QMLR_REQUIRE(n_split >= 1 && n_split <= 3, "n_split must be 1, 2 or 3 (got %d)", n_split);
   QMLR_REQUIRE(k_pad >= n_rows && k_pad % 64 == 0, "k_pad must be >= n_rows and a multiple of 64");
   QMLR_REQUIRE(zt && (n_rows == 0 || Z), "NULL pointer argument");
   if (k_pad == 0) return QMLR_OK;
@@ -161,6 +218,51 @@ extern "C" int qmlr_gram_operand(const float* Z, int64_t n_rows, int32_t n_featu
       Z, n_rows, n_features, ldz, n_split, reinterpret_cast<__nv_bfloat16*>(zt), k_pad);
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
+}
+
+extern "C" int qmlr_gram_operand_fp8(const float* Z, int64_t n_rows, int32_t n_features, int64_t ldz,
+                                     uint8_t* zt, int64_t k_pad, float* inv_scale, void* stream) {
+  QMLR_REQUIRE(n_rows >= 0 && n_features >= 1 && ldz >= n_features, "bad Z shape");
+  QMLR_REQUIRE(k_pad >= n_rows && k_pad % 128 == 0, "k_pad must be >= n_rows and a multiple of 128");
+  QMLR_REQUIRE(zt && inv_scale && (n_rows == 0 || Z), "NULL pointer argument");
+  cudaStream_t s = as_stream(stream);
+  QMLR_CUDA_TRY(cudaMemsetAsync(inv_scale, 0, sizeof(float) * n_features, s));
+  if (n_rows > 0) {
+    dim3 g1((n_features + 255) / 256, (unsigned)((n_rows + 1023) / 1024));
+    column_absmax_kernel<<<g1, 256, 0, s>>>(Z, n_rows, n_features, ldz, reinterpret_cast<unsigned*>(inv_scale));
+    QMLR_LAUNCH_CHECK();
+  }
+  fp8_scales_kernel<<<(n_features + 255) / 256, 256, 0, s>>>(n_features, inv_scale);
+  QMLR_LAUNCH_CHECK();
+  if (k_pad == 0) return QMLR_OK;
+  dim3 grid((unsigned)((k_pad + kTT - 1) / kTT), (n_features + kTT - 1) / kTT);
+  gram_operand_fp8_kernel<<<grid, dim3(32, 8), 0, s>>>(Z, n_rows, n_features, ldz, inv_scale, zt, k_pad);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_gram_tc(const qmlr_gram_opts* o, const void* zt, int64_t k_pad, int32_t n_features,
+                            const float* inv_scale, float* G, void* stream) {
+  QMLR_REQUIRE(o && zt && G, "NULL pointer argument");
+  QMLR_REQUIRE(n_features >= 128 && n_features % 128 == 0,
+               "tensor-core Gram needs n_features a positive multiple of 128 (got %d)", n_features);
+  const int tile = o->tile_n == 0 ? (o->precision == QMLR_GRAM_BF16X1 || o->precision == QMLR_GRAM_FP8X1 ? 256 : 128)
+                                  : o->tile_n;
+  QMLR_REQUIRE(tile == 128 || tile == 256, "tile_n must be 0, 128 or 256 (got %d)", o->tile_n);
+  QMLR_REQUIRE(n_features % tile == 0, "n_features (%d) must be a multiple of the tile width %d", n_features, tile);
+  QMLR_REQUIRE(o->promote >= 0, "promote must be >= 0");
+  int form = 0;
+  long kq = 64;
+  switch (o->precision) {
+    case QMLR_GRAM_BF16X1: form = 1; break;
+    case QMLR_GRAM_BF16X3: form = 2; break;
+    case QMLR_GRAM_BF16X6: form = 3; break;
+    case QMLR_GRAM_FP8X1: form = 4; kq = 128; break;
+    default: set_error("precision %d is not a tensor-core Gram form", o->precision); return QMLR_EINVAL;
+  }
+  QMLR_REQUIRE(k_pad >= 0 && k_pad % kq == 0, "k_pad must be a multiple of %ld for this form", kq);
+  QMLR_REQUIRE(form != 4 || inv_scale, "inv_scale is NULL");
+  return gram_tc_form(form, tile, o->promote, zt, k_pad, n_features, inv_scale, G, as_stream(stream));
 }
 
 extern "C" int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int32_t n_features,
@@ -179,6 +281,11 @@ extern "C" int qmlr_gram(int32_t precision, const float* Z, int64_t n_rows, int3
     QMLR_REQUIRE(k_pad % 64 == 0 && k_pad >= 0, "k_pad must be a multiple of 64");
     QMLR_REQUIRE(n_features % 128 == 0, "tensor-core Gram needs n_features %% 128 == 0 (got %d)", n_features);
     return gram_split_tc(precision == QMLR_GRAM_BF16X3 ? 2 : 3, zt, k_pad, n_features, G, s);
+  }
+  if (precision == QMLR_GRAM_BF16X1) {
+    QMLR_REQUIRE(zt, "operand is NULL");
+    qmlr_gram_opts o{QMLR_GRAM_BF16X1, 0, 0};
+    return qmlr_gram_tc(&o, zt, k_pad, n_features, nullptr, G, stream);
   }
   set_error("unknown Gram precision %d", precision);
   return QMLR_EINVAL;

@@ -88,6 +88,19 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// Instruction descriptor, kind::f8f6f4: D f32, A/B e4m3 (format code 0), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
@@ -126,19 +139,23 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map over a K-major bf16 operand [rows][k_pad] (k contiguous), box 64 x box_rows,
-// 128-byte swizzle (the layout smem_desc describes).
-inline int make_map(CUtensorMap* map, const void* base, long k_pad, long rows, int box_rows = 128) {
+// 2D map over a K-major operand [rows][k_pad] (k contiguous) of bf16 (elem_bytes 2) or
+// 8-bit (elem_bytes 1) elements: the box is one 128-byte line of K (64 or 128
+// elements) x box_rows rows, 128-byte swizzle (the layout smem_desc describes).
+inline int make_map(CUtensorMap* map, const void* base, long k_pad, long rows, int box_rows = 128,
+                    int elem_bytes = 2) {
   auto fn = encode_fn();
   QMLR_REQUIRE(fn, "cuTensorMapEncodeTiled is not available");
   QMLR_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, "operand not 16-byte aligned");
+  QMLR_REQUIRE(elem_bytes == 1 || elem_bytes == 2, "element size must be 1 or 2 bytes");
   cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
-  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)k_pad * elem_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   QMLR_REQUIRE(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return QMLR_OK;
 }

@@ -81,18 +81,45 @@ def feature_matrix(batch: Batch, spec: FeatureSpec, U, rep=None, perm=None, offs
 # smallest power of two at which the mixed-precision factor of the QM9-shaped
 # Gram (100 000 x 16384) stays positive definite (a smaller one fails a pivot
 # and the solve refactorises with a tenfold shift).
-DEFAULT_SHIFT = {qmlr.GRAM_BF16X3: -2.0 ** -15, qmlr.GRAM_BF16X6: -2.0 ** -16, qmlr.GRAM_FP32: -2.0 ** -13}
+DEFAULT_SHIFT = {qmlr.GRAM_BF16X3: -2.0 ** -15, qmlr.GRAM_BF16X6: -2.0 ** -16, qmlr.GRAM_FP32: -2.0 ** -13,
+                 qmlr.GRAM_BF16X1: -2.0 ** -10, qmlr.GRAM_FP8X1: -2.0 ** -6}
+
+# Accumulation and tile width of each tensor-core form by default: the accurate
+# split forms promote every K block into Kahan sums on 128-wide tiles; the
+# one-part forms keep the whole K range in the accumulator on 256-wide tiles.
+DEFAULT_TC = {qmlr.GRAM_BF16X3: (1, 128), qmlr.GRAM_BF16X6: (1, 128), qmlr.GRAM_BF16X1: (0, 256),
+              qmlr.GRAM_FP8X1: (0, 256)}
+
+
+def gram_operand(Z, precision: int):
+    """The tensor-core operand of a Gram form (None for the plain FP32 form)."""
+    if precision == qmlr.GRAM_FP32:
+        return None
+    if precision == qmlr.GRAM_FP8X1:
+        return qmlr.gram_operand_fp8(Z)
+    return qmlr.gram_operand(Z, qmlr.GRAM_SPLITS[precision])
+
+
+def gram(Z, precision: int, promote: int | None = None, tile: int | None = None, operand=None):
+    """G = Z^T Z in the given form (tensor-core forms: promote / tile default to DEFAULT_TC)."""
+    if precision == qmlr.GRAM_FP32:
+        return qmlr.gram(Z, precision)
+    p0, t0 = DEFAULT_TC[precision]
+    if operand is None:
+        operand = gram_operand(Z, precision)
+    return qmlr.gram_tc(Z, precision, promote=p0 if promote is None else promote,
+                        tile_n=t0 if tile is None else tile, operand=operand)
 
 
 def solve(Z, y, lam: float, precision: int = qmlr.GRAM_BF16X3, method: int = qmlr.SOLVE_PCG,
           max_iter: int = 50, tol: float = 1e-10, shift: float | None = None,
-          factor: int = qmlr.FACTOR_MIXED):
+          factor: int = qmlr.FACTOR_MIXED, promote: int | None = None, tile: int | None = None):
     """alpha (float64) of (Z^T Z + lam I) alpha = Z^T y; returns (alpha, iterations, rel. residual).
     The Gram (2-way BF16 split by default) only builds the preconditioner; the
     converged alpha is fixed by the exact operator."""
     if shift is None:
         shift = DEFAULT_SHIFT[precision]
-    G = qmlr.gram(Z, precision)
+    G = gram(Z, precision, promote, tile)
     return qmlr.gram_solve(G, Z, y, lam, method=method, max_iter=max_iter, tol=tol, shift=shift,
                            factor=factor)
 

@@ -46,6 +46,10 @@ class ServeStats(C.Structure):
                 ("throughput_rps", C.c_double), ("us_per_atom", C.c_double), ("mean_batch_atoms", C.c_double)]
 
 
+class GramOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("promote", C.c_int32), ("tile_n", C.c_int32)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("shift", C.c_double), ("iters_done", C.c_int32), ("rel_resid", C.c_double),
@@ -55,7 +59,8 @@ class SolveOpts(C.Structure):
 
 _lib = None
 P, I32, I64, D, VP = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_void_p
-GRAM_FP32, GRAM_BF16X3, GRAM_BF16X6 = 0, 1, 2
+GRAM_FP32, GRAM_BF16X3, GRAM_BF16X6, GRAM_BF16X1, GRAM_FP8X1 = 0, 1, 2, 3, 4
+GRAM_SPLITS = {GRAM_BF16X1: 1, GRAM_BF16X3: 2, GRAM_BF16X6: 3}
 SOLVE_PCG, SOLVE_REFINE = 0, 1
 FACTOR_FP64, FACTOR_MIXED = 0, 1
 
@@ -93,6 +98,8 @@ _SIGS = {
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, VP]),
     "qmlr_gram_operand": (C.c_int, [P, I64, I32, I64, I32, P, I64, VP]),
     "qmlr_gram": (C.c_int, [I32, P, I64, I32, I64, P, I64, P, VP]),
+    "qmlr_gram_operand_fp8": (C.c_int, [P, I64, I32, I64, P, I64, P, VP]),
+    "qmlr_gram_tc": (C.c_int, [C.POINTER(GramOpts), P, I64, I32, P, P, VP]),
     "qmlr_zty_workspace_bytes": (C.c_int64, [I64, I32]),
     "qmlr_zty": (C.c_int, [P, I64, I32, I64, P, P, P, I64, VP]),
     "qmlr_cholesky": (C.c_int, [P, I64, I32, C.POINTER(C.c_int32), VP]),
@@ -443,17 +450,48 @@ def gram_operand(Z, n_split: int = 2):
     return zt
 
 
+def gram_operand_fp8(Z):
+    """e4m3 operand [N_F, k_pad] (uint8) and per-feature inverse scales [N_F] (float32)."""
+    Z = _dev(Z, torch.float32)
+    n_rows, nf = Z.shape
+    kp = max(128, (n_rows + 127) // 128 * 128)
+    zt = torch.empty((nf, kp), device="cuda", dtype=torch.uint8)
+    inv = torch.empty(nf, device="cuda", dtype=torch.float32)
+    _check(lib().qmlr_gram_operand_fp8(_ptr(Z), n_rows, nf, Z.stride(0), _ptr(zt), kp, _ptr(inv), _stream()))
+    return zt, inv
+
+
 def gram(Z, precision: int = GRAM_BF16X6, operand=None):
     """G = Z^T Z (float32, full symmetric)."""
     Z = _dev(Z, torch.float32)
     n_rows, nf = Z.shape
     G = torch.empty((nf, nf), device="cuda", dtype=torch.float32)
-    if precision in (GRAM_BF16X3, GRAM_BF16X6):
-        zt = operand if operand is not None else gram_operand(Z, 2 if precision == GRAM_BF16X3 else 3)
+    if precision == GRAM_FP8X1:
+        return gram_tc(Z, precision, operand=operand)
+    if precision in GRAM_SPLITS:
+        zt = operand if operand is not None else gram_operand(Z, GRAM_SPLITS[precision])
         _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), _ptr(zt), zt.shape[2],
                                _ptr(G), _stream()))
     else:
         _check(lib().qmlr_gram(precision, _ptr(Z), n_rows, nf, Z.stride(0), None, 0, _ptr(G), _stream()))
+    return G
+
+
+def gram_tc(Z, precision: int, promote: int = 0, tile_n: int = 0, operand=None):
+    """G = Z^T Z on the tensor cores with explicit accumulation (promote) and tile
+    width (tile_n); operand: the split operand, or (zt, inv_scale) for FP8X1."""
+    Z = _dev(Z, torch.float32)
+    n_rows, nf = Z.shape
+    G = torch.empty((nf, nf), device="cuda", dtype=torch.float32)
+    inv = None
+    if precision == GRAM_FP8X1:
+        zt, inv = operand if operand is not None else gram_operand_fp8(Z)
+        kp = zt.shape[1]
+    else:
+        zt = operand if operand is not None else gram_operand(Z, GRAM_SPLITS[precision])
+        kp = zt.shape[2]
+    o = GramOpts(precision, promote, tile_n)
+    _check(lib().qmlr_gram_tc(C.byref(o), _ptr(zt), kp, nf, _ptr(inv), _ptr(G), _stream()))
     return G
 
 

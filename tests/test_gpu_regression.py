@@ -40,7 +40,7 @@ def _features(n_rows, nf, seed=0):
     return Z
 
 
-@pytest.mark.parametrize("n_split", [2, 3])
+@pytest.mark.parametrize("n_split", [1, 2, 3])
 def test_gram_operand_is_bf16_split(q, n_split):
     Z = _features(100, 256)
     zt = q.gram_operand(Z, n_split).cpu()
@@ -54,6 +54,65 @@ def test_gram_operand_is_bf16_split(q, n_split):
 
 
 GRAM_TOL = {0: 4e-5, 1: 4e-5, 2: 1e-5}
+
+
+def test_fp8_operand_matches_oracle_rounding(q):
+    """e4m3 operand: per-feature power-of-two scales and round-to-nearest-even
+    values equal the oracle's definition bit for bit; K padding is zero."""
+    Z = _features(300, 256, seed=31)
+    Z[:, 5] = 0.0                                   # an all-zero feature keeps scale 1
+    Z[:, 7] *= 1e-3
+    zt, inv = q.gram_operand_fp8(Z)
+    assert zt.shape == (256, 384)
+    s = o_reg.fp8_feature_scales(Z.astype(np.float64))
+    assert np.array_equal(1.0 / inv.cpu().numpy().astype(np.float64), s)
+    got = zt.cpu().view(torch.float8_e4m3fn).float().numpy().astype(np.float64)
+    want = o_reg.round_to_format(Z.astype(np.float64) * s[None, :], o_reg.E4M3_FORMAT).T
+    assert np.array_equal(got[:, :300], want)
+    assert np.all(got[:, 300:] == 0)
+
+
+# (precision, promote, tile_n) of the configurable tensor-core Gram
+REDUCED_FORMS = [(3, 0, 256), (3, 0, 128), (3, 2, 256), (4, 0, 256), (4, 3, 128)]
+
+
+@pytest.mark.parametrize("n_rows,nf", [(1000, 256), (777, 512), (4096, 768)])
+@pytest.mark.parametrize("form", REDUCED_FORMS)
+def test_reduced_precision_gram_matches_quantized_oracle(q, n_rows, nf, form):
+    """One-part BF16 and e4m3 Grams equal Q^T Q of the oracle's rounded operand
+    up to the FP32 accumulation (bound: K 2^-23 of the largest diagonal entry,
+    the worst case of truncating adds)."""
+    precision, promote, tile = form
+    Z = _features(n_rows, nf, seed=n_rows + 3 * nf)
+    ref = o_reg.quantized_gram(Z.astype(np.float64), "bf16" if precision == 3 else "e4m3")
+    G = q.gram_tc(Z, precision, promote=promote, tile_n=tile).cpu().numpy()
+    assert q.device_status() == 0
+    scale = np.max(np.diag(ref))
+    err = np.max(np.abs(G - ref)) / scale
+    assert err <= n_rows * 2.0 ** -23, err
+    assert np.array_equal(G, G.T)
+
+
+@pytest.mark.parametrize("form", [(3, 0, 256), (4, 0, 256), (1, 0, 256), (1, 1, 128)])
+def test_reduced_precision_gram_several_waves(q, form):
+    """380 tiles of 128 x 256 (or 703 of 128 x 128): several waves of the
+    persistent launch; the 2-way split without per-block promotion against FP64."""
+    precision, promote, tile = form
+    Z = _features(600, 4864, seed=41)
+    G = q.gram_tc(Z, precision, promote=promote, tile_n=tile).cpu().numpy()
+    assert q.device_status() == 0
+    if precision == 1:
+        Zd = Z.astype(np.float64)
+        ref = Zd.T @ Zd
+        tol = GRAM_TOL[1] + 600 * 2.0 ** -23
+    else:
+        ref = o_reg.quantized_gram(Z.astype(np.float64), "bf16" if precision == 3 else "e4m3")
+        tol = 600 * 2.0 ** -23
+    err = np.max(np.abs(G - ref)) / np.max(np.diag(ref))
+    assert err <= tol, err
+    assert np.array_equal(G, G.T)
+    if form == (1, 1, 128):            # the default 2-way form: bitwise the qmlr_gram result
+        assert np.array_equal(G, q.gram(Z, q.GRAM_BF16X3).cpu().numpy())
 
 
 @pytest.mark.parametrize("n_rows,nf", [(64, 128), (1000, 256), (777, 384), (4096, 1024), (130, 512)])
