@@ -61,9 +61,9 @@ def parse():
                     help="tensor-core Gram: x3 (2-way BF16 split), x6 (3-way), x1 (one BF16 part), "
                          "fp8 (e4m3, per-feature scales)")
     ap.add_argument("--gram-promote", type=int, default=None,
-                    help="K blocks per tensor-core accumulation (0: whole K); default 1 for x3/x6, 0 otherwise")
+                    help="K blocks per tensor-core accumulation (0: whole K); default 1")
     ap.add_argument("--gram-tile", type=int, default=None, choices=[128, 256],
-                    help="tile width; default 128 for x3/x6, 256 otherwise")
+                    help="tile width; default 128 for x6, 256 otherwise")
     ap.add_argument("--shift", type=float, default=None,
                     help="relative diagonal shift of the preconditioner factor (default: the form's)")
     ap.add_argument("--gram-sweep", action="store_true",
@@ -693,13 +693,15 @@ def run_gram_sweep(args):
     del rep, perm, offs
     factor = qmlr.FACTOR_MIXED if args.factor == "mixed" else qmlr.FACTOR_FP64
     s = torch.cuda.current_stream()
-    configs = [(1, 1, 128, -2.0 ** -15), (1, 1, 128, -2.0 ** -14),
-               (1, 4, 128, -2.0 ** -14), (1, 4, 128, -2.0 ** -13),
-               (1, 0, 256, -2.0 ** -13), (1, 0, 256, -2.0 ** -12), (1, 0, 256, -2.0 ** -11),
-               (3, 0, 256, -2.0 ** -12), (3, 0, 256, -2.0 ** -10), (3, 0, 256, -2.0 ** -8),
-               (3, 0, 128, -2.0 ** -10),
-               (4, 0, 256, -2.0 ** -8), (4, 0, 256, -2.0 ** -6), (4, 0, 256, -2.0 ** -4),
-               (0, 0, 0, -2.0 ** -13), (0, 0, 0, -2.0 ** -12), (0, 0, 0, -2.0 ** -10)]
+    configs = [(1, 1, 128, -2.0 ** -15), (1, 2, 128, -2.0 ** -15), (1, 2, 128, -2.0 ** -14),
+               (1, 4, 128, -2.0 ** -14),
+               (1, 1, 256, -2.0 ** -15), (1, 1, 256, -2.0 ** -14), (1, 2, 256, -2.0 ** -14),
+               (1, 2, 256, -2.0 ** -13),
+               (3, 1, 256, -2.0 ** -12), (3, 1, 256, -2.0 ** -11), (3, 1, 256, -2.0 ** -10),
+               (3, 1, 256, -2.0 ** -9), (3, 1, 256, -2.0 ** -8), (3, 2, 256, -2.0 ** -10),
+               (4, 1, 256, -2.0 ** -8), (4, 1, 256, -2.0 ** -7), (4, 1, 256, -2.0 ** -6),
+               (4, 1, 256, -2.0 ** -5), (4, 1, 256, -2.0 ** -4),
+               (0, 0, 0, -2.0 ** -11), (0, 0, 0, -2.0 ** -10), (0, 0, 0, -2.0 ** -9), (0, 0, 0, -2.0 ** -8)]
     pts = []
     for prec, promote, tile, shift in configs:
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]

@@ -81,14 +81,24 @@ def feature_matrix(batch: Batch, spec: FeatureSpec, U, rep=None, perm=None, offs
 # smallest power of two at which the mixed-precision factor of the QM9-shaped
 # Gram (100 000 x 16384) stays positive definite (a smaller one fails a pivot
 # and the solve refactorises with a tenfold shift).
-DEFAULT_SHIFT = {qmlr.GRAM_BF16X3: -2.0 ** -15, qmlr.GRAM_BF16X6: -2.0 ** -16, qmlr.GRAM_FP32: -2.0 ** -13,
-                 qmlr.GRAM_BF16X1: -2.0 ** -10, qmlr.GRAM_FP8X1: -2.0 ** -6}
+# Measured on that Gram (PCG to 1e-8, 150 iterations at most): the 2-way split
+# at 2^-15 converges in 10 iterations; the one-part BF16 form needs 2^-12 (33
+# iterations), the e4m3 form 2^-8 (117 iterations); the plain FP32 SIMT form
+# fails its pivots below 2^-11 (36 iterations there, 53 at 2^-10).
+DEFAULT_SHIFT = {qmlr.GRAM_BF16X3: -2.0 ** -15, qmlr.GRAM_BF16X6: -2.0 ** -16, qmlr.GRAM_FP32: -2.0 ** -11,
+                 qmlr.GRAM_BF16X1: -2.0 ** -12, qmlr.GRAM_FP8X1: -2.0 ** -8}
 
-# Accumulation and tile width of each tensor-core form by default: the accurate
-# split forms promote every K block into Kahan sums on 128-wide tiles; the
-# one-part forms keep the whole K range in the accumulator on 256-wide tiles.
-DEFAULT_TC = {qmlr.GRAM_BF16X3: (1, 128), qmlr.GRAM_BF16X6: (1, 128), qmlr.GRAM_BF16X1: (0, 256),
-              qmlr.GRAM_FP8X1: (0, 256)}
+# Accumulation and tile width of each tensor-core form by default: every K
+# block's accumulator is promoted into FP32 register sums (the tensor cores'
+# accumulator adds truncate each product to the accumulator's exponent, so a
+# long accumulation in TMEM is strongly biased: keeping the whole K range of
+# the QM9-shaped Gram in TMEM made the factor indefinite until the shift was
+# near 10 % of max G_ii); 256-wide tiles with plain FP32 register sums, which
+# keep the drain off the critical path (the 2-way split: 51 ms instead of 95 ms
+# with Kahan sums on 128-wide tiles, same iteration count); the 3-way split
+# keeps Kahan sums on 128-wide tiles (its accuracy is the point of it).
+DEFAULT_TC = {qmlr.GRAM_BF16X3: (1, 256), qmlr.GRAM_BF16X6: (1, 128), qmlr.GRAM_BF16X1: (1, 256),
+              qmlr.GRAM_FP8X1: (1, 256)}
 
 
 def gram_operand(Z, precision: int):

@@ -141,15 +141,20 @@ def test_persistent_gram_matches_fp64(q, precision):
     assert np.array_equal(G, G.T)
 
 
-def test_gram_at_full_size_on_sampled_entries(q):
+@pytest.mark.parametrize("tc_form", [None, (1, 256)])
+def test_gram_at_full_size_on_sampled_entries(q, tc_form):
     """The 2-way tensor-core Gram at the training size (100,000 molecules x
-    16,384 features, the launch the training step makes): 256 sampled entries,
-    every tile row and column touched, against FP64 dot products of the
-    sampled columns."""
+    16,384 features): qmlr_gram's form (Kahan sums, 128-wide tiles) and the
+    training step's (every K block promoted into plain FP32 sums, 256-wide
+    tiles). 256 sampled entries, every tile row and column touched, against
+    FP64 dot products of the sampled columns."""
     n_rows, nf = 100_000, 16_384
     g = torch.Generator(device="cuda").manual_seed(23)
     Z = (torch.rand(n_rows, nf, device="cuda", generator=g) - 0.5) * 0.1
-    G = q.gram(Z, q.GRAM_BF16X3)
+    if tc_form is None:
+        G = q.gram(Z, q.GRAM_BF16X3)
+    else:
+        G = q.gram_tc(Z, q.GRAM_BF16X3, promote=tc_form[0], tile_n=tc_form[1])
     assert q.device_status() == 0
     rng = np.random.default_rng(24)
     ii = np.concatenate([np.arange(0, nf, 128), np.arange(127, nf, 128)])[:256]
