@@ -280,114 +280,224 @@ fchl19_forward_kernel(const float* __restrict__ coords, const int32_t* __restric
 // (two-body) and of every element pair (three-body, cos and sin), so the
 // accumulation is a warp-uniform switch on the element or pair index into
 // registers instead of a shared-memory read-modify-write; the row is written
-// straight from registers at the end. Same order of summation as the
-// shared-memory kernel (neighbours, then pairs in the same order).
-#define QMLR_CASE2(E) case E: a2[E] += v; break;
-#define QMLR_CASE3(P) case P: ac[P] += g * pr.x; as[P] += g * pr.y; break;
+// straight from registers at the end.
+//
+// Work layout: a CTA takes a contiguous range of kFwdRange atoms; thread 0
+// finds the molecules at its two ends (two binary searches per CTA instead of
+// one per atom), the CTA stages the positions of every molecule the range
+// touches once, and each warp takes every kWarpsFwd-th atom of the range. The
+// Gaussians of the radial grids are evaluated as 2^(-c t^2) with the
+// hardware base-2 exponential (the constants carry the log2(e) factor), one
+// special-function instruction per (neighbour or triplet, bin); the per-pair
+// geometry uses the hardware cosine for the third cutoff factor and base-2
+// log / exponential for the ATM power. Summation order per bin: neighbours,
+// then triplets, in the same order as the shared-memory kernel.
+constexpr int kFwdRange = 32;          // atoms per CTA
+constexpr float kLog2e = 1.4426950408889634f;
 
-__global__ void __launch_bounds__(32 * kWarpsFwd)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Per-warp shared memory of the register kernel: neighbour data and one chunk of triplets.
+struct RegWarp {
+  float4* nb_u;   // [mxp] unit vector i->j, r_ij
+  float4* nb_2b;  // [mxp] mu, log2(e)/(2 s^2), two-body prefactor, f_cut(r_ij)
+  float4* pairs;  // [32] w G^cos, w G^sin, xbar, pair index (bits)
+  int* nb_el;     // [mxp]
+};
+__host__ __device__ __forceinline__ size_t reg_warp_bytes(int mxp) { return (size_t)mxp * 36 + 512; }
+__host__ __device__ __forceinline__ int reg_stage_atoms(int mx) { return kFwdRange + 2 * (mx - 1); }
+
+#define QMLR_CASE2(E) case E: a2[E] = fmaf(wv, g, a2[E]); break;
+#define QMLR_CASE3(P) case P: ac[P] = fmaf(g, pr.x, ac[P]); as[P] = fmaf(g, pr.y, as[P]); break;
+
+__global__ void __launch_bounds__(32 * kWarpsFwd, 6)
 fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
-                          const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp, int rp,
+                          const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp,
                           Fchl19Consts c, float* __restrict__ rep, int rep_ld, int* err) {
   extern __shared__ __align__(16) char smem_raw[];
+  __shared__ int s_m0, s_m1, s_base, s_end;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int atom = blockIdx.x * kWarpsFwd + warp;
-  if (atom >= n_atoms) return;
-  FwdWarp s = carve_fwd(smem_raw + warp * fwd_warp_bytes(mxp, rp), mxp, rp);
-  const int m = find_molecule(mol_ptr, n_mol, atom);
-  const int a0 = __ldg(mol_ptr + m);
-  const int M = __ldg(mol_ptr + m + 1) - a0;
-  float* out = rep + (size_t)atom * rep_ld;
-  if (M > mx) {
-    if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
-    for (int k = lane; k < rep_ld; k += 32) out[k] = 0.0f;
-    return;
+  const int a_lo = blockIdx.x * kFwdRange;
+  const int a_hi = min(a_lo + kFwdRange, n_atoms) - 1;
+  if (threadIdx.x == 0) {
+    const int m0 = find_molecule(mol_ptr, n_mol, a_lo);
+    const int m1 = find_molecule(mol_ptr, n_mol, a_hi);
+    s_m0 = m0;
+    s_m1 = m1;
+    // every atom of a molecule of at most mx atoms that owns an atom of the
+    // range lies in [a_lo - (mx - 1), a_hi + mx): the staged window
+    s_base = max(__ldg(mol_ptr + m0), a_lo - (mx - 1));
+    s_end = min(__ldg(mol_ptr + m1 + 1), a_hi + mx);
   }
-  stage_molecule(coords, elem, a0, M, c.n_el, s.pos, lane, 32, err);
-  __syncwarp();
-  const int n = neighbour_list(s.pos, M, atom - a0, c, s.nb_u, s.nb_2b, s.nb_el, nullptr, lane);
+  __syncthreads();
+  const int m0 = s_m0, m1 = s_m1, base = s_base;
+  const int stage_n = s_end - base;   // <= kFwdRange + 2 (mx - 1)
+  float4* pos = reinterpret_cast<float4*>(smem_raw);
+  for (int j = threadIdx.x; j < stage_n; j += blockDim.x) {
+    int e = __ldg(elem + base + j);
+    if (e < 0 || e >= c.n_el) {
+      record_device_error(err, DEV_BAD_ELEMENT);
+      e = 0;
+    }
+    const float* q = coords + 3 * (size_t)(base + j);
+    pos[j] = make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), __int_as_float(e));
+  }
+  __syncthreads();
+  char* wbase = smem_raw + (size_t)reg_stage_atoms(mx) * 16 + warp * reg_warp_bytes(mxp);
+  RegWarp s;
+  s.nb_u = reinterpret_cast<float4*>(wbase);
+  s.nb_2b = s.nb_u + mxp;
+  s.pairs = s.nb_2b + mxp;
+  s.nb_el = reinterpret_cast<int*>(s.pairs + 32);
 
-  float a2[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  const bool has2 = lane < c.n2;
+  // per-lane radial constants (lane = bin)
+  const bool has2 = lane < c.n2, has3 = lane < c.n3;
   const float r2log = has2 ? c.rs2_log[lane] : 0.f, r2inv = has2 ? c.rs2_inv[lane] : 0.f;
-  for (int jn = 0; jn < n; ++jn) {
-    const float4 t = s.nb_2b[jn];
-    const float a = r2log - t.x;
-    const float v = t.z * r2inv * expf(-a * a * t.y);
-    switch (s.nb_el[jn]) { QMLR_CASE2(0) QMLR_CASE2(1) QMLR_CASE2(2) QMLR_CASE2(3) QMLR_CASE2(4) default: break; }
-  }
-
-  float ac[15], as[15];
-#pragma unroll
-  for (int q = 0; q < 15; ++q) {
-    ac[q] = 0.f;
-    as[q] = 0.f;
-  }
-  const bool has3 = lane < c.n3;
   const float r3 = has3 ? c.rs3[lane] : 0.f;
-  const int n_pairs = n * (n - 1) / 2;
-  for (int q0 = 0; q0 < n_pairs; q0 += 32) {
-    const int q = q0 + lane;
-    bool ok = false;
-    float wc = 0.f, ws = 0.f, xbar = 0.f;
-    int pidx = 0;
-    if (q < n_pairs) {
-      int jn, kn;
-      decode_pair(q, n, jn, kn);
-      const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
-      const float vx = uk.x * uk.w - uj.x * uj.w;
-      const float vy = uk.y * uk.w - uj.y * uj.w;
-      const float vz = uk.z * uk.w - uj.z * uj.w;
-      const float rjk2 = vx * vx + vy * vy + vz * vz;
-      if (rjk2 < c.rcut2) {
-        ok = true;
-        const float rjk = sqrtf(rjk2);
-        const float inv_rjk = 1.0f / rjk;
-        const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-        const float cx = uj.y * uk.z - uj.z * uk.y;
-        const float cy = uj.z * uk.x - uj.x * uk.z;
-        const float cz = uj.x * uk.y - uj.y * uk.x;
-        const float si = sqrtf(cx * cx + cy * cy + cz * cz);
-        const float cj = -(uj.x * vx + uj.y * vy + uj.z * vz) * inv_rjk;
-        const float ck = (uk.x * vx + uk.y * vy + uk.z * vz) * inv_rjk;
-        const float atm = (1.0f + 3.0f * ci * cj * ck) * expf(-c.N3 * logf(uj.w * uk.w * rjk));
-        const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * cutoff_f(rjk, c);
-        wc = w * c.ang2 * ci;
-        ws = w * c.ang2 * si;
-        xbar = 0.5f * (uj.w + uk.w);
-        pidx = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
-      }
+  const float neg_eta3 = -c.eta3 * kLog2e;
+  const int np = c.n_el * (c.n_el + 1) / 2;
+
+  for (int atom = a_lo + warp; atom <= a_hi; atom += kWarpsFwd) {
+    // molecule of this atom: mol_ptr[mi] <= atom < mol_ptr[mi + 1], mi in [m0, m1]
+    int lo = m0, hi = m1 + 1;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(mol_ptr + mid) <= atom) lo = mid; else hi = mid;
     }
-    const unsigned mask = __ballot_sync(0xffffffffu, ok);
-    if (ok) s.pairs[__popc(mask & ((1u << lane) - 1u))] = make_float4(wc, ws, xbar, __int_as_float(pidx));
+    const int a0 = __ldg(mol_ptr + lo), M = __ldg(mol_ptr + lo + 1) - a0;
+    float* out = rep + (size_t)atom * rep_ld;
+    if (M > mx) {
+      if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+      for (int k = lane; k < rep_ld; k += 32) out[k] = 0.0f;
+      continue;
+    }
+    const float4* mpos = pos + (a0 - base);
+    const float4 ri = mpos[atom - a0];
+    // neighbour list (ballot compaction, ascending j)
+    int n = 0;
+    for (int b0 = 0; b0 < M; b0 += 32) {
+      const int j = b0 + lane;
+      bool ok = false;
+      float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, wj = 0.f;
+      if (j < M && j != atom - a0) {
+        const float4 pj = mpos[j];
+        dx = pj.x - ri.x;
+        dy = pj.y - ri.y;
+        dz = pj.z - ri.z;
+        wj = pj.w;
+        r2 = dx * dx + dy * dy + dz * dz;
+        ok = r2 < c.rcut2;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int slot = n + __popc(mask & ((1u << lane) - 1u));
+        const float r = sqrtf(r2);
+        const float inv = 1.0f / r;
+        s.nb_u[slot] = make_float4(dx * inv, dy * inv, dz * inv, r);
+        s.nb_el[slot] = __float_as_int(wj);
+        const float fc = cutoff_f(r, c);
+        const float s2 = log1pf(c.eta2 * inv * inv);   // sigma^2 = ln(1 + eta2 / r^2)
+        s.nb_2b[slot] = make_float4(logf(r) - 0.5f * s2,                        // mu = ln(r / sqrt(1 + eta2/r^2))
+                                    kLog2e * 0.5f / s2,                        // log2(e) / (2 sigma^2)
+                                    fc * expf(-c.N2 * logf(r)) * c.inv_sqrt_2pi * rsqrtf(s2),
+                                    fc);
+      }
+      n += __popc(mask);
+    }
     __syncwarp();
-    const int cnt = __popc(mask);
-    for (int t = 0; t < cnt; ++t) {
-      const float4 pr = s.pairs[t];
-      const float d = pr.z - r3;
-      const float g = expf(-c.eta3 * d * d);
-      switch (__float_as_int(pr.w)) {
-        QMLR_CASE3(0) QMLR_CASE3(1) QMLR_CASE3(2) QMLR_CASE3(3) QMLR_CASE3(4) QMLR_CASE3(5) QMLR_CASE3(6)
-        QMLR_CASE3(7) QMLR_CASE3(8) QMLR_CASE3(9) QMLR_CASE3(10) QMLR_CASE3(11) QMLR_CASE3(12) QMLR_CASE3(13)
-        QMLR_CASE3(14) default: break;
-      }
+
+    // two-body: lanes over bins, neighbours in order
+    float a2[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int jn = 0; jn < n; ++jn) {
+      const float4 t = s.nb_2b[jn];
+      const float d = r2log - t.x;
+      const float g = ex2_approx(-(d * d) * t.y);
+      const float wv = t.z * r2inv;
+      switch (s.nb_el[jn]) { QMLR_CASE2(0) QMLR_CASE2(1) QMLR_CASE2(2) QMLR_CASE2(3) QMLR_CASE2(4) default: break; }
     }
+
+    // three-body: pair geometry lane-parallel over flat pairs (j < k), then lanes over bins
+    float ac[15], as[15];
+#pragma unroll
+    for (int q = 0; q < 15; ++q) {
+      ac[q] = 0.f;
+      as[q] = 0.f;
+    }
+    const int n_pairs = n * (n - 1) / 2;
+    for (int q0 = 0; q0 < n_pairs; q0 += 32) {
+      const int q = q0 + lane;
+      bool ok = false;
+      float wc = 0.f, ws = 0.f, xbar = 0.f;
+      int pidx = 0;
+      if (q < n_pairs) {
+        int jn, kn;
+        decode_pair(q, n, jn, kn);
+        const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+        const float vx = uk.x * uk.w - uj.x * uj.w;
+        const float vy = uk.y * uk.w - uj.y * uj.w;
+        const float vz = uk.z * uk.w - uj.z * uj.w;
+        const float rjk2 = vx * vx + vy * vy + vz * vz;
+        if (rjk2 < c.rcut2) {
+          ok = true;
+          const float inv_rjk = rsqrtf(rjk2);
+          const float rjk = rjk2 * inv_rjk;
+          const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+          const float cx = uj.y * uk.z - uj.z * uk.y;
+          const float cy = uj.z * uk.x - uj.x * uk.z;
+          const float cz = uj.x * uk.y - uj.y * uk.x;
+          const float si = sqrtf(cx * cx + cy * cy + cz * cz);
+          const float cj = -(uj.x * vx + uj.y * vy + uj.z * vz) * inv_rjk;
+          const float ck = (uk.x * vx + uk.y * vy + uk.z * vz) * inv_rjk;
+          // (r_ij r_ik r_jk)^-N3 = 2^(-N3 log2(r_ij r_ik r_jk))
+          const float atm = (1.0f + 3.0f * ci * cj * ck) * ex2_approx(-c.N3 * lg2_approx(uj.w * uk.w * rjk));
+          const float fcjk = 0.5f * (__cosf(rjk * c.pi_over_rcut) + 1.0f);
+          const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * fcjk;
+          wc = w * c.ang2 * ci;
+          ws = w * c.ang2 * si;
+          xbar = 0.5f * (uj.w + uk.w);
+          pidx = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
+        }
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) s.pairs[__popc(mask & ((1u << lane) - 1u))] = make_float4(wc, ws, xbar, __int_as_float(pidx));
+      __syncwarp();
+      const int cnt = __popc(mask);
+      for (int t = 0; t < cnt; ++t) {
+        const float4 pr = s.pairs[t];
+        const float d = pr.z - r3;
+        const float g = ex2_approx(d * (d * neg_eta3));
+        switch (__float_as_int(pr.w)) {
+          QMLR_CASE3(0) QMLR_CASE3(1) QMLR_CASE3(2) QMLR_CASE3(3) QMLR_CASE3(4) QMLR_CASE3(5) QMLR_CASE3(6)
+          QMLR_CASE3(7) QMLR_CASE3(8) QMLR_CASE3(9) QMLR_CASE3(10) QMLR_CASE3(11) QMLR_CASE3(12) QMLR_CASE3(13)
+          QMLR_CASE3(14) default: break;
+        }
+      }
+      __syncwarp();
+    }
+    // write the row from registers; padding columns zero
+    if (has2)
+#pragma unroll
+      for (int e = 0; e < 5; ++e)
+        if (e < c.n_el) out[e * c.n2 + lane] = a2[e];
+    if (has3)
+#pragma unroll
+      for (int q = 0; q < 15; ++q)
+        if (q < np) {
+          out[c.base3 + (q * c.n3 + lane) * 2] = ac[q];
+          out[c.base3 + (q * c.n3 + lane) * 2 + 1] = as[q];
+        }
+    for (int k = c.rep_dim + lane; k < rep_ld; k += 32) out[k] = 0.0f;
     __syncwarp();
   }
-  // write the row from registers; padding columns zero
-  if (has2)
-#pragma unroll
-    for (int e = 0; e < 5; ++e)
-      if (e < c.n_el) out[e * c.n2 + lane] = a2[e];
-  const int np = c.n_el * (c.n_el + 1) / 2;
-  if (has3)
-#pragma unroll
-    for (int q = 0; q < 15; ++q)
-      if (q < np) {
-        out[c.base3 + (q * c.n3 + lane) * 2] = ac[q];
-        out[c.base3 + (q * c.n3 + lane) * 2 + 1] = as[q];
-      }
-  for (int k = c.rep_dim + lane; k < rep_ld; k += 32) out[k] = 0.0f;
 }
 #undef QMLR_CASE2
 #undef QMLR_CASE3
@@ -421,12 +531,21 @@ __device__ __forceinline__ VjpWarp carve_vjp(char* base, int mxp, int rp) {
 
 // Adjoint of one centre: accumulates d(sum_b g_b rho_il,b)/d r_k into facc[3k..3k+2]
 // for every atom k of the molecule (the centre's own entry included). One warp.
+// Gaussians as 2^(-c t^2) with the hardware base-2 exponential.
+//
+// Three-body contributions are computed lane-parallel over flat neighbour
+// pairs (j < k, row-major), 32 at a time, and reach the atoms' accumulators in
+// a fixed order without atomics: the j-side values of a chunk share their row
+// index j along contiguous lanes, so a segmented scan over lanes (keyed by j)
+// sums each row's run and the run's last lane adds it; the k-side values of one
+// row name distinct atoms, so the rows of the chunk add theirs one row at a time.
 __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts& c, const float* __restrict__ grow,
                            VjpWarp& s, int lane) {
   for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grow + k);
   const int n = neighbour_list(pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
 
   float gi_x = 0.f, gi_y = 0.f, gi_z = 0.f;   // gradient on the centre (per-lane partials)
+  const float neg_eta3 = -c.eta3 * kLog2e;
 
   // two-body: lanes over neighbours (distinct atoms per lane)
   for (int jn = lane; jn < n; jn += 32) {
@@ -444,12 +563,15 @@ __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts&
     const float rN = expf(-c.N2 * logf(r));
     const float P = fc * rN;
     const float dP = rN * (dfc - c.N2 * fc * inv_r);
+    const float negc = -t.y * kLog2e;
+    const float pre = c.inv_sqrt_2pi / sd;
+    const float k1 = -ds / sd, k2 = dmu / s2, k3 = ds / (s2 * sd);
     const float* gb = s.g + s.nb_el[jn] * c.n2;
     float dEdr = 0.f;
     for (int k = 0; k < c.n2; ++k) {
       const float a = c.rs2_log[k] - t.x;
-      const float L = c.rs2_inv[k] * c.inv_sqrt_2pi / sd * expf(-a * a * t.y);
-      const float dlnL = -ds / sd + a * dmu / s2 + a * a * ds / (s2 * sd);
+      const float L = c.rs2_inv[k] * pre * ex2_approx(a * (a * negc));
+      const float dlnL = k1 + a * k2 + a * a * k3;
       dEdr += gb[k] * L * (dP + P * dlnL);
     }
     const int jl = s.nb_idx[jn];
@@ -462,28 +584,14 @@ __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts&
   }
   __syncwarp();
 
-  // three-body: lanes over flat neighbour pairs, each lane loops over its radial bins.
-  // The pairs' contributions reach the atoms' accumulators in pair order (j side,
-  // then k side). Molecules of up to 32 atoms keep atom a's accumulator in lane
-  // a's registers, and each lane pulls its atom's entries from the staged chunk;
-  // larger ones broadcast each pair by shuffles to lane 0.
+  // three-body
   const int n_pairs = n * (n - 1) / 2;
-  const bool regs = M <= 32;
-  float fa0 = 0.f, fa1 = 0.f, fa2 = 0.f;
-  if (regs && lane < M) {
-    fa0 = s.facc[3 * lane + 0];
-    fa1 = s.facc[3 * lane + 1];
-    fa2 = s.facc[3 * lane + 2];
-  }
   for (int q0 = 0; q0 < n_pairs; q0 += 32) {
     const int q = q0 + lane;
     float gj0 = 0.f, gj1 = 0.f, gj2 = 0.f, gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
-    int jl = 0, kl = 0;
+    int jn = n, kn = n;   // lanes past the last pair: key n (no atom)
     if (q < n_pairs) {
-      int jn, kn;
       decode_pair(q, n, jn, kn);
-      jl = s.nb_idx[jn];
-      kl = s.nb_idx[kn];
       const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
       const float a = uj.w, b = uk.w;
       const float vx = uk.x * b - uj.x * a, vy = uk.y * b - uj.y * a, vz = uk.z * b - uj.z * a;
@@ -522,7 +630,7 @@ __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts&
         float Sc = 0.f, Ss = 0.f, Sc1 = 0.f, Ss1 = 0.f;
         for (int k = 0; k < c.n3; ++k) {
           const float d = xbar - c.rs3[k];
-          const float rad = expf(-c.eta3 * d * d);
+          const float rad = ex2_approx(d * (d * neg_eta3));
           const float drad = -2.0f * c.eta3 * d * rad;
           const float g0 = gb[2 * k], g1 = gb[2 * k + 1];
           Sc += g0 * rad;
@@ -548,50 +656,39 @@ __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts&
         gk2 = dE_db * uk.z + dE_dc * uz;
       }
     }
-    const int cnt = min(32, n_pairs - q0);
-    if (regs) {
-      s.stage[2 * lane] = make_float4(__int_as_float(jl), gj0, gj1, gj2);
-      s.stage[2 * lane + 1] = make_float4(__int_as_float(kl), gk0, gk1, gk2);
-      __syncwarp();
-      for (int e = 0; e < 2 * cnt; ++e) {
-        const float4 v = s.stage[e];
-        if (__float_as_int(v.x) == lane) {
-          fa0 += v.y;
-          fa1 += v.z;
-          fa2 += v.w;
-        }
-      }
-      __syncwarp();
-      continue;
-    }
-    // scatter the j- and k-side gradients in a fixed lane order
-    for (int t = 0; t < cnt; ++t) {
-      const int jt = __shfl_sync(0xffffffffu, jl, t);
-      const int kt = __shfl_sync(0xffffffffu, kl, t);
-      const float v0 = __shfl_sync(0xffffffffu, gj0, t);
-      const float v1 = __shfl_sync(0xffffffffu, gj1, t);
-      const float v2 = __shfl_sync(0xffffffffu, gj2, t);
-      const float v3 = __shfl_sync(0xffffffffu, gk0, t);
-      const float v4 = __shfl_sync(0xffffffffu, gk1, t);
-      const float v5 = __shfl_sync(0xffffffffu, gk2, t);
-      if (lane == 0) {
-        s.facc[3 * jt + 0] += v0;
-        s.facc[3 * jt + 1] += v1;
-        s.facc[3 * jt + 2] += v2;
-        s.facc[3 * kt + 0] += v3;
-        s.facc[3 * kt + 1] += v4;
-        s.facc[3 * kt + 2] += v5;
+    // j side: segmented inclusive scan over lanes with equal jn (runs are contiguous)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float t0 = __shfl_up_sync(0xffffffffu, gj0, o);
+      const float t1 = __shfl_up_sync(0xffffffffu, gj1, o);
+      const float t2 = __shfl_up_sync(0xffffffffu, gj2, o);
+      const int kk = __shfl_up_sync(0xffffffffu, jn, o);
+      if (lane >= o && kk == jn) {
+        gj0 += t0;
+        gj1 += t1;
+        gj2 += t2;
       }
     }
-    __syncwarp();
-  }
-  if (regs) {
-    if (lane < M) {
-      s.facc[3 * lane + 0] = fa0;
-      s.facc[3 * lane + 1] = fa1;
-      s.facc[3 * lane + 2] = fa2;
+    const int next = __shfl_down_sync(0xffffffffu, jn, 1);
+    if (jn < n && (lane == 31 || next != jn)) {
+      const int jl = s.nb_idx[jn];
+      s.facc[3 * jl + 0] += gj0;
+      s.facc[3 * jl + 1] += gj1;
+      s.facc[3 * jl + 2] += gj2;
     }
     __syncwarp();
+    // k side: one row at a time (distinct atoms within a row)
+    const int r_first = __shfl_sync(0xffffffffu, jn, 0);
+    const int r_last = __reduce_max_sync(0xffffffffu, jn < n ? jn : -1);
+    for (int r = r_first; r <= r_last; ++r) {
+      if (jn == r) {
+        const int kl = s.nb_idx[kn];
+        s.facc[3 * kl + 0] += gk0;
+        s.facc[3 * kl + 1] += gk1;
+        s.facc[3 * kl + 2] += gk2;
+      }
+      __syncwarp();
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -952,13 +1049,15 @@ extern "C" int qmlr_fchl19(const float* coords, const int32_t* elem, const int32
   const int mxp = (mx + 3) & ~3;
   const size_t smem = kWarpsFwd * fwd_warp_bytes(mxp, rp);
   QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
-  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_kernel, 227 * 1024));
-  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_reg_kernel, 227 * 1024));
-  const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
   if (p->n_el <= 5 && p->n2 <= 32 && p->n3 <= 32) {
-    fchl19_forward_reg_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
-        coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, rep, rep_ld, device_error_ptr());
+    const size_t rsmem = (size_t)reg_stage_atoms(mx) * 16 + kWarpsFwd * reg_warp_bytes(mxp);
+    QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_reg_kernel, (int)rsmem));
+    const int rgrid = (n_atoms + kFwdRange - 1) / kFwdRange;
+    fchl19_forward_reg_kernel<<<rgrid, 32 * kWarpsFwd, rsmem, as_stream(stream)>>>(
+        coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, c, rep, rep_ld, device_error_ptr());
   } else {
+    QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_kernel, 227 * 1024));
+    const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
     fchl19_forward_kernel<<<grid, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
         coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, rp, c, rep, rep_ld, device_error_ptr());
   }
