@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-ef", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
     ap.add_argument("--gram-form", default="x3", choices=sorted(GRAM_FORMS),
@@ -134,6 +134,9 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # oracle (CPU) timing on a bounded sample: the reported CPU baseline
 
+ORACLE_SAMPLE = 20   # molecules of the workload per oracle step
+
+
 def oracle_step_times(w, n_mol_sample: int, threads: int):
     """Time the FP64 oracle's training + E+F prediction on a bounded sample of the
     workload and extrapolate to the full workload: features and prediction scale
@@ -171,13 +174,92 @@ def oracle_step_times(w, n_mol_sample: int, threads: int):
             "train_s": feat + gram + chol, "predict_us_per_atom": pred / full_atoms * 1e6}
 
 
+def oracle_per_atom_one_core(w, n_mol_sample: int):
+    """The oracle's per-atom parts (SORF features of the molecules, then energies
+    and forces) on one thread, us per atom of the sample."""
+    import torch
+    from oracle import fchl19 as o_fchl19
+    from oracle import model as o_model
+    from oracle import regression as o_reg
+    prev = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        mols = w.mols.subset(range(n_mol_sample))
+        p = o_fchl19.params(w.params_column, n2=w.n2, n3=w.n3)
+        reps = o_fchl19.representation_batch(mols.coords, mols.elem, mols.mol_ptr, p)
+        U = o_reg.pca_bases(reps, mols.elem, 5, w.d)
+        rng = np.random.default_rng(0)
+        m = o_model.sorf_model(p, U, w.signs, w.b, w.sigma, rng.normal(size=w.n_features))
+        t0 = time.perf_counter()
+        o_model.feature_matrix(mols.coords, mols.elem, mols.mol_ptr, m)
+        t1 = time.perf_counter()
+        o_model.energies_forces(mols.coords, mols.elem, mols.mol_ptr, m)
+        t2 = time.perf_counter()
+    finally:
+        torch.set_num_threads(prev)
+    n = mols.n_atoms
+    return {"cores": 1, "sample_molecules": n_mol_sample, "sample_atoms": n,
+            "features_us_per_atom": (t1 - t0) / n * 1e6, "predict_ef_us_per_atom": (t2 - t1) / n * 1e6}
+
+
+def oracle_parity_workload_full():
+    """The oracle on the whole parity workload (64 molecules x 9 atoms, N_F = 512):
+    training (features, normal equations, Cholesky + one refinement) and E+F
+    prediction, all host cores."""
+    from oracle import fchl19 as o_fchl19
+    from oracle import model as o_model
+    from oracle import regression as o_reg
+    from paper_2206_01580_gb300 import synth
+    w = synth.workload(0)
+    mols = w.mols
+    p = o_fchl19.params(w.params_column, n2=w.n2, n3=w.n3)
+    t0 = time.perf_counter()
+    reps = o_fchl19.representation_batch(mols.coords, mols.elem, mols.mol_ptr, p)
+    U = o_reg.pca_bases(reps, mols.elem, 5, w.d)
+    m = o_model.sorf_model(p, U, w.signs, w.b, w.sigma)
+    alpha, _ = o_model.train(mols.coords, mols.elem, mols.mol_ptr, w.energies, m, w.lam)
+    t1 = time.perf_counter()
+    m.alpha = alpha
+    o_model.energies_forces(mols.coords, mols.elem, mols.mol_ptr, m)
+    t2 = time.perf_counter()
+    return {"workload": "parity-64x9 (64 molecules x 9 atoms, N_F = 512), in full", "train_s": t1 - t0,
+            "predict_ef_us_per_atom": (t2 - t1) / mols.n_atoms * 1e6, "cores": os.cpu_count() or 1}
+
+
+def workload_config(args, w, world, gram_text, solve_text):
+    """The config object of the bench line (the same keys in both arms)."""
+    return {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
+            "n_molecules": w.mols.n_mol, "n_atoms": w.mols.n_atoms, "n_features": w.n_features, "d": w.d,
+            "n_transform": w.n_transform, "gram": gram_text, "solve": solve_text,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (rep 5.5 GB, Z 6.6 GB)",
+            "step": "one training (FCHL19 -> projection -> SORF -> Z -> Gram -> factor + PCG) plus E+F "
+                    "prediction of the same molecules; value = us per atom of that step"}
+
+
 # ----------------------------------------------------------------------------
 # serving: Poisson request streams through the continuous-batching server
 
+SIZE_BINS = ((5, 25), (26, 50), (51, 100), (101, 200))
+
+
+def latency_bins(lat_us, atoms):
+    """p50 / p99 latency (ms) and request count per molecule-size bin."""
+    out = []
+    for lo, hi in SIZE_BINS:
+        sel = (atoms >= lo) & (atoms <= hi)
+        if sel.any():
+            v = np.sort(lat_us[sel])
+            out.append({"atoms": f"{lo}-{hi}", "requests": int(sel.sum()),
+                        "p50_ms": float(v[int(0.50 * (len(v) - 1) + 0.5)]) / 1e3,
+                        "p99_ms": float(v[int(0.99 * (len(v) - 1) + 0.5)]) / 1e3})
+    return out
+
+
 def serving_phase(model_args, rates, seconds):
     """p50/p99 latency, throughput and us/atom of the server under Poisson
-    arrivals of 5-200-atom molecules, and of one request at a time."""
-    import queue
+    arrivals of 5-200-atom molecules, and of one request at a time; latencies
+    also per molecule-size bin."""
     from paper_2206_01580_gb300 import qmlr, synth
     p, U, signs, T, b, sigma, alpha = model_args
     pool = synth.serving_molecules(synth.rng_for(4), 2000)
@@ -190,10 +272,11 @@ def serving_phase(model_args, rates, seconds):
         arrivals = synth.poisson_arrivals(rng, rate, seconds)
         picks = rng.integers(0, pool.n_mol, size=len(arrivals))
         st = srv.replay(pool.coords, pool.elem, pool.mol_ptr, arrivals, picks)
+        lat, at = srv.latencies()
         return {"rate_rps": rate, "requests": len(arrivals), "rejected": st["rejected"],
                 "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
                 "throughput_rps": st["throughput_rps"], "us_per_atom": st["us_per_atom"],
-                "mean_batch_atoms": st["mean_batch_atoms"]}
+                "mean_batch_atoms": st["mean_batch_atoms"], "by_size": latency_bins(lat, at)}
 
     srv = qmlr.Server(model, n_lanes=2, max_batch_atoms=16384, max_batch_mols=4096, use_graphs=True)
     # warm-up: every batch-size bucket once outside capture and once captured
@@ -209,15 +292,17 @@ def serving_phase(model_args, rates, seconds):
     for i in range(20):
         t = one.submit(*mols[i])
         one.poll(t, len(mols[i][1]))
-    # one request at a time: each arrives after the previous result (closed loop, 300 requests)
+    # one request at a time: each arrives after the previous result (closed loop, 600 requests)
     one.reset_stats()
-    for i in range(300):
+    for i in range(600):
         c, e = mols[(7 * i) % len(mols)]
         t = one.submit(c, e)
         one.poll(t, len(e))
     st = one.stats()
+    lat, at = one.latencies()
     out["one_at_a_time"] = {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
-                            "throughput_rps": st["throughput_rps"], "us_per_atom": st["us_per_atom"]}
+                            "throughput_rps": st["throughput_rps"], "us_per_atom": st["us_per_atom"],
+                            "by_size": latency_bins(lat, at)}
     one.close()
     model.close()
     out["molecules"] = "5-200 atoms, log-uniform (mean %.1f)" % pool.sizes().mean()
@@ -228,13 +313,16 @@ def serving_phase(model_args, rates, seconds):
 # ----------------------------------------------------------------------------
 # energy + force training on the 3BPA-shaped workload
 
-def ef_training_phase(pcg_iters, pcg_tol, factor):
-    """Train on 500 conformations with energy and force rows (41 000 x 16384),
-    then predict 2000 held-out conformations; stage times by CUDA events."""
+def ef_training_phase(config, pcg_iters, pcg_tol, factor):
+    """Energy + force training on the MD17-shaped (config 2: 1000 conformations,
+    64 000 x 8192 rows) or 3BPA-shaped workload (config 3: 500 conformations,
+    41 000 x 16384 rows), then prediction of the held-out conformations (3BPA)
+    or of the training set (MD17, which has no test split); stage times by CUDA
+    events."""
     import torch
     from paper_2206_01580_gb300 import pipeline, qmlr, synth
     from paper_2206_01580_gb300.params import from_table
-    w = synth.workload(3)
+    w = synth.workload(config)
     p = from_table(w.params_column, n2=w.n2, n3=w.n3)
     spec = pipeline.spec_from(p, w.d, w.signs, w.b, w.sigma)
     tr = pipeline.Batch.from_host(w.mols.coords, w.mols.elem, w.mols.mol_ptr)
@@ -261,17 +349,26 @@ def ef_training_phase(pcg_iters, pcg_tol, factor):
         return alpha, {"rows_ms": ev[0].elapsed_time(ev[1]), "gram_ms": ev[1].elapsed_time(ev[2]),
                        "solve_ms": ev[2].elapsed_time(ev[3]), "factor_ms": so.factor_ms,
                        "refine_ms": so.refine_ms, "train_s": ev[0].elapsed_time(ev[3]) / 1e3,
-                       "pcg_iters": it, "rel_resid": rel, "n_rows": n_rows}
+                       "pcg_iters": it, "rel_resid": rel, "n_rows": n_rows, "n_features": w.n_features}
 
     once()                     # warm-up
     alpha, st = once()
-    model = qmlr.Model(p, 32, U, w.signs, w.n_transform, w.b, w.sigma, alpha.float().cpu().numpy())
-    E, F = model.predict(w.test.coords, w.test.elem, w.test.mol_ptr)
-    mae_e = float(np.mean(np.abs(E.cpu().numpy() - w.test_energies)))
-    mae_f = float(np.mean(np.abs(F.cpu().numpy() - w.test_forces)))
+    model = qmlr.Model(p, int(w.mols.sizes().max()), U, w.signs, w.n_transform, w.b, w.sigma,
+                       alpha.float().cpu().numpy())
+    if w.test is not None:
+        E, F = model.predict(w.test.coords, w.test.elem, w.test.mol_ptr)
+        mae_e = float(np.mean(np.abs(E.cpu().numpy() - w.test_energies)))
+        mae_f = float(np.mean(np.abs(F.cpu().numpy() - w.test_forces)))
+        split = "test"
+    else:
+        E, F = model.predict(w.mols.coords, w.mols.elem, w.mols.mol_ptr)
+        mae_e = float(np.mean(np.abs(E.cpu().numpy() - w.energies)))
+        mae_f = float(np.mean(np.abs(F.cpu().numpy() - w.forces)))
+        split = "train"
     model.close()
-    st.update({"workload": "3bpa-shaped-500 (500 train / 2000 test conformations, 27 atoms, N_F = 16384)",
-               "test_mae_E_eV": mae_e, "test_mae_F_eV_per_A": mae_f})
+    name = ("md17-shaped-1k (1000 conformations of a 21-atom C9H8O4-like molecule, N_F = 8192)" if config == 2
+            else "3bpa-shaped-500 (500 train / 2000 test conformations, 27 atoms, N_F = 16384)")
+    st.update({"workload": name, f"{split}_mae_E_eV": mae_e, f"{split}_mae_F_eV_per_A": mae_f})
     return st
 
 
@@ -321,30 +418,30 @@ def build_workload(scale):
 
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores: each step is a bounded sample
-    (6 molecules) of the same workload, extrapolated to the whole workload."""
+    (20 molecules) of the same workload, extrapolated to the whole workload."""
     if rank != 0:
         return
     w, _ = build_workload(args.scale)
     threads = os.cpu_count() or 1
     times = []
     for k in range(args.warmup + args.steps):
-        r = oracle_step_times(w, 6, threads)
+        r = oracle_step_times(w, ORACLE_SAMPLE, threads)
         if k >= args.warmup:
             times.append(r)
     total = statistics.mean(t["total_s"] for t in times)
     val = total / w.mols.n_atoms * 1e6
+    sample = (f"{ORACLE_SAMPLE} molecules per step ({times[0]['sample_atoms']} atoms); features, Gram rows and "
+              "prediction extrapolated linearly to the workload (values extrapolated, not a full run); "
+              "full N_F^3 Cholesky")
     line = {"metric": METRIC, "impl": "reference", "value": val, "unit": "us/atom",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
-                       "n_molecules": w.mols.n_mol, "n_atoms": w.mols.n_atoms, "n_features": w.n_features},
+            "config": workload_config(args, w, world, "fp64 dense Z^T Z (numpy)",
+                                      "fp64 dense Cholesky + one refinement step (numpy/scipy)"),
             "train_s": statistics.mean(t["train_s"] for t in times),
             "predict_us_per_atom": statistics.mean(t["predict_us_per_atom"] for t in times),
-            "cpu_baseline": {"value": val, "unit": "us/atom", "cores": threads, "kind": "oracle",
-                             "sample": f"6 molecules per step ({times[0]['sample_atoms']} atoms); features, "
-                                       "Gram rows and prediction extrapolated linearly to the workload; "
-                                       "full N_F^3 Cholesky"},
+            "cpu_baseline": {"value": val, "unit": "us/atom", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "us/atom", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -562,14 +659,10 @@ def run_ours(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": f"f32 features, {gdesc['dtype']} gram, f64 solve",
         "data": "synthetic",
-        "config": {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
-                   "n_molecules": n_mol, "n_atoms": n_atoms, "n_features": nf, "d": w.d,
-                   "n_transform": w.n_transform, "gram": gdesc["text"] + f", shift {GRAM['shift']:.3g} x max G_ii "
-                           "(preconditioner input)",
-                   "solve": ("mixed-precision cholesky (fp64 panels, tcgen05 trailing updates)"
-                             if args.factor == "mixed" else "fp64 cholesky") + " + pcg (exact fp64 operator)",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (rep 5.5 GB, Z 6.6 GB)"},
+        "config": workload_config(args, w, world, gdesc["text"] + f", shift {GRAM['shift']:.3g} x max G_ii "
+                                  "(preconditioner input)",
+                                  ("mixed-precision cholesky (double-float panels, tcgen05 trailing updates)"
+                                   if args.factor == "mixed" else "fp64 cholesky") + " + pcg (exact fp64 operator)"),
         "train_s": (st["total"] - st["predict_ef"]) / 1e3,
         # prediction cost: its feature half (timed on the side stream, beside the
         # solve) plus the weight-dependent half
@@ -587,20 +680,23 @@ def run_ours(args, rank, world):
         "workload_gen_s": gen_s,
     }
     if not args.no_ef and world == 1:
-        line["ef_training"] = ef_training_phase(args.pcg_iters, args.pcg_tol, factor)
+        line["ef_training"] = ef_training_phase(3, args.pcg_iters, args.pcg_tol, factor)
+        line["ef_training_md17"] = ef_training_phase(2, args.pcg_iters, args.pcg_tol, factor)
     if not args.no_serve and world == 1:
         alpha_host = alpha.float().cpu().numpy()
         line["serving"] = serving_phase((p, U, w.signs, w.n_transform, w.b, w.sigma, alpha_host),
-                                        (1000, 5000, 20000), args.serve_seconds)
+                                        (1000, 5000, 10000, 20000), args.serve_seconds)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
-        cb = oracle_step_times(w, 6, threads)
+        cb = oracle_step_times(w, ORACLE_SAMPLE, threads)
         line["cpu_baseline"] = {"value": cb["total_s"] / n_atoms * 1e6, "unit": "us/atom", "cores": threads,
                                 "kind": "oracle",
                                 "sample": f"{cb['sample_molecules']} molecules ({cb['sample_atoms']} atoms); "
                                           "features, Gram rows and prediction extrapolated linearly to the "
-                                          "workload; full N_F^3 Cholesky",
-                                "train_s": cb["train_s"], "predict_us_per_atom": cb["predict_us_per_atom"]}
+                                          "workload (values extrapolated, not a full run); full N_F^3 Cholesky",
+                                "train_s": cb["train_s"], "predict_us_per_atom": cb["predict_us_per_atom"],
+                                "one_core": oracle_per_atom_one_core(w, 4),
+                                "parity_workload_full": oracle_parity_workload_full()}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

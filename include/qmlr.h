@@ -693,6 +693,15 @@ int qmlr_serve_stats(qmlr_server* s, qmlr_serve_report* out);
 int qmlr_serve_reset_stats(qmlr_server* s);
 
 /*
+ * The latencies behind the statistics (submit -> result ready, microseconds,
+ * in completion order since the last reset) with the atom count of each
+ * request: copies min(count, capacity) pairs into host_latency_us (float) and
+ * host_atoms (int32), and sets *count to the number recorded. Thread-safe.
+ */
+int qmlr_serve_latencies(qmlr_server* s, float* host_latency_us, int32_t* host_atoms, int64_t capacity,
+                         int64_t* count);
+
+/*
  * Load driver: replays a request trace against the server from two host
  * threads (one submits molecule pick[i] of the pool at arrival_us[i]
  * microseconds after the start, spinning until then; one collects results in

@@ -316,8 +316,6 @@ struct RegWarp {
 __host__ __device__ __forceinline__ size_t reg_warp_bytes(int mxp) { return (size_t)mxp * 36 + 512; }
 __host__ __device__ __forceinline__ int reg_stage_atoms(int mx) { return kFwdRange + 2 * (mx - 1); }
 
-#define QMLR_CASE2(E) case E: a2[E] = fmaf(wv, g, a2[E]); break;
-#define QMLR_CASE3(P) case P: ac[P] = fmaf(g, pr.x, ac[P]); as[P] = fmaf(g, pr.y, as[P]); break;
 
 __global__ void __launch_bounds__(32 * kWarpsFwd, 6)
 fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
@@ -415,14 +413,22 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
     }
     __syncwarp();
 
-    // two-body: lanes over bins, neighbours in order
+    // two-body: lanes over bins; per block of 32 neighbours, element by element
+    // (a compile-time accumulator index), neighbours in order
     float a2[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int jn = 0; jn < n; ++jn) {
-      const float4 t = s.nb_2b[jn];
-      const float d = r2log - t.x;
-      const float g = ex2_approx(-(d * d) * t.y);
-      const float wv = t.z * r2inv;
-      switch (s.nb_el[jn]) { QMLR_CASE2(0) QMLR_CASE2(1) QMLR_CASE2(2) QMLR_CASE2(3) QMLR_CASE2(4) default: break; }
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      const int ej = j0 + lane < n ? s.nb_el[j0 + lane] : -1;
+#pragma unroll
+      for (int e = 0; e < 5; ++e) {
+        unsigned m = __ballot_sync(0xffffffffu, ej == e);
+        while (m) {
+          const int jn = j0 + __ffs(m) - 1;
+          m &= m - 1u;
+          const float4 t = s.nb_2b[jn];
+          const float d = r2log - t.x;
+          a2[e] = fmaf(t.z * r2inv, ex2_approx(-(d * d) * t.y), a2[e]);
+        }
+      }
     }
 
     // three-body: pair geometry lane-parallel over flat pairs (j < k), then lanes over bins
@@ -467,18 +473,34 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
           pidx = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
         }
       }
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) s.pairs[__popc(mask & ((1u << lane) - 1u))] = make_float4(wc, ws, xbar, __int_as_float(pidx));
+      // stage the chunk in lane order; then, pair type by pair type (a
+      // compile-time accumulator index), walk that type's triplets in lane order
+      s.pairs[lane] = make_float4(wc, ws, xbar, 0.f);
       __syncwarp();
-      const int cnt = __popc(mask);
-      for (int t = 0; t < cnt; ++t) {
-        const float4 pr = s.pairs[t];
-        const float d = pr.z - r3;
-        const float g = ex2_approx(d * (d * neg_eta3));
-        switch (__float_as_int(pr.w)) {
-          QMLR_CASE3(0) QMLR_CASE3(1) QMLR_CASE3(2) QMLR_CASE3(3) QMLR_CASE3(4) QMLR_CASE3(5) QMLR_CASE3(6)
-          QMLR_CASE3(7) QMLR_CASE3(8) QMLR_CASE3(9) QMLR_CASE3(10) QMLR_CASE3(11) QMLR_CASE3(12) QMLR_CASE3(13)
-          QMLR_CASE3(14) default: break;
+      const int key = ok ? pidx : 15;
+#pragma unroll
+      for (int b = 0; b < 15; ++b) {
+        unsigned m = __ballot_sync(0xffffffffu, key == b);
+        while (m) {
+          const int t0 = __ffs(m) - 1;
+          m &= m - 1u;
+          const float4 p0 = s.pairs[t0];
+          const float d0 = p0.z - r3;
+          const float g0 = ex2_approx(d0 * (d0 * neg_eta3));
+          if (m) {
+            const int t1 = __ffs(m) - 1;
+            m &= m - 1u;
+            const float4 p1 = s.pairs[t1];
+            const float d1 = p1.z - r3;
+            const float g1 = ex2_approx(d1 * (d1 * neg_eta3));
+            ac[b] = fmaf(g0, p0.x, ac[b]);
+            as[b] = fmaf(g0, p0.y, as[b]);
+            ac[b] = fmaf(g1, p1.x, ac[b]);
+            as[b] = fmaf(g1, p1.y, as[b]);
+          } else {
+            ac[b] = fmaf(g0, p0.x, ac[b]);
+            as[b] = fmaf(g0, p0.y, as[b]);
+          }
         }
       }
       __syncwarp();
@@ -499,9 +521,6 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
     __syncwarp();
   }
 }
-#undef QMLR_CASE2
-#undef QMLR_CASE3
-
 // ---------------------------------------------------------------------------
 // VJP: one CTA per molecule, warps over centre atoms.
 

@@ -93,6 +93,7 @@ struct qmlr_server {
   int pad_reserve = 2;   // molecules kept free in every batch for padding
   std::thread worker;
   std::vector<float> latencies_us;
+  std::vector<int32_t> latency_atoms;   // atoms of the request behind each latency
   int64_t completed = 0, rejected = 0, batches = 0, batch_atoms = 0;
   double atoms_done = 0, t_first = -1, t_last = 0;
   int fatal = QMLR_OK;
@@ -222,6 +223,7 @@ static void finish(qmlr_server* S, Lane& L) {
     r->state = 2;
     r->t_done = t;
     S->latencies_us.push_back((float)(t - r->t_submit));
+    S->latency_atoms.push_back(r->n_atoms);
     S->atoms_done += r->n_atoms;
     ++S->completed;
   }
@@ -427,10 +429,27 @@ extern "C" int qmlr_serve_stats(qmlr_server* S, qmlr_serve_report* out) {
   return QMLR_OK;
 }
 
+extern "C" int qmlr_serve_latencies(qmlr_server* S, float* host_latency_us, int32_t* host_atoms, int64_t capacity,
+                                    int64_t* count) {
+  QMLR_REQUIRE(S && count, "NULL pointer argument");
+  QMLR_REQUIRE(capacity >= 0, "capacity must be >= 0");
+  std::lock_guard<std::mutex> lk(S->mu);
+  const int64_t n = (int64_t)S->latencies_us.size();
+  *count = n;
+  const int64_t k = std::min(n, capacity);
+  if (k > 0) {
+    QMLR_REQUIRE(host_latency_us && host_atoms, "NULL output array");
+    std::copy(S->latencies_us.begin(), S->latencies_us.begin() + k, host_latency_us);
+    std::copy(S->latency_atoms.begin(), S->latency_atoms.begin() + k, host_atoms);
+  }
+  return QMLR_OK;
+}
+
 extern "C" int qmlr_serve_reset_stats(qmlr_server* S) {
   QMLR_REQUIRE(S, "server is NULL");
   std::lock_guard<std::mutex> lk(S->mu);
   S->latencies_us.clear();
+  S->latency_atoms.clear();
   S->completed = S->rejected = S->batches = S->batch_atoms = 0;
   S->atoms_done = 0;
   S->t_first = -1;

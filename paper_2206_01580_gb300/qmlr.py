@@ -128,6 +128,7 @@ _SIGS = {
     "qmlr_serve_poll": (C.c_int, [VP, C.c_uint64, P, P, I64]),
     "qmlr_serve_stats": (C.c_int, [VP, C.POINTER(ServeStats)]),
     "qmlr_serve_reset_stats": (C.c_int, [VP]),
+    "qmlr_serve_latencies": (C.c_int, [VP, P, P, I64, C.POINTER(C.c_int64)]),
     "qmlr_serve_destroy": (C.c_int, [VP]),
     "qmlr_serve_replay": (C.c_int, [VP, P, P, P, I32, P, P, I32, C.POINTER(C.c_int64), C.POINTER(ServeStats)]),
 }
@@ -822,6 +823,15 @@ class Server:
 
     def reset_stats(self):
         _check(lib().qmlr_serve_reset_stats(self.handle))
+
+    def latencies(self):
+        """(latency_us float32 [n], atoms int32 [n]) of the requests since the last reset."""
+        n = C.c_int64(0)
+        _check(lib().qmlr_serve_latencies(self.handle, None, None, 0, C.byref(n)))
+        lat = np.zeros(max(n.value, 1), np.float32)
+        at = np.zeros(max(n.value, 1), np.int32)
+        _check(lib().qmlr_serve_latencies(self.handle, lat.ctypes.data, at.ctypes.data, n.value, C.byref(n)))
+        return lat[:n.value], at[:n.value]
 
     def replay(self, coords, elem, mol_ptr, arrival_s, pick) -> dict:
         """Replay a request trace from native threads; returns the run's statistics."""
