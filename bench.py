@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-ef", action="store_true")
+    ap.add_argument("--no-periodic", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
@@ -66,6 +67,10 @@ def parse():
                     help="tile width; default 128 for x6, 256 otherwise")
     ap.add_argument("--shift", type=float, default=None,
                     help="relative diagonal shift of the preconditioner factor (default: the form's)")
+    ap.add_argument("--nf-sweep", action="store_true",
+                    help="instead of the step: train time and held-out MAE at N_F = 4096 ... 32768")
+    ap.add_argument("--rff-sweep", action="store_true",
+                    help="instead of the step: SORF vs dense RFF time and held-out MAE on MD17-shaped data")
     ap.add_argument("--gram-sweep", action="store_true",
                     help="instead of the step: train with each Gram form and shift on the workload and "
                          "report Gram, factor and PCG times, iterations and training MAE")
@@ -370,6 +375,69 @@ def ef_training_phase(config, pcg_iters, pcg_tol, factor):
             else "3bpa-shaped-500 (500 train / 2000 test conformations, 27 atoms, N_F = 16384)")
     st.update({"workload": name, f"{split}_mae_E_eV": mae_e, f"{split}_mae_F_eV_per_A": mae_f})
     return st
+
+
+def periodic_phase():
+    """E+F prediction of the periodic stand-ins for the paper's liquid water
+    (4000 waters, 12 000 atoms) and MOF (16 848 atoms) rows: random-weight model
+    (N_F = 16384, d = 128, T = 3, E+F parameters, per-system PCA basis); device
+    time (CUDA events, median of 5 after a warm-up) and the same with the
+    host->device copy of the coordinates and the device->host copy of E and F
+    inside the timed region; the host cell list (a per-geometry setup) timed apart."""
+    import torch
+    from paper_2206_01580_gb300 import pipeline, qmlr, synth
+    from paper_2206_01580_gb300.params import from_table
+    p = from_table("EF", n2=24, n3=22)
+    out = []
+    for name, gen in (("water-shaped (4000 rigid waters, 12 000 atoms, 1 g/cm^3, cubic cell)",
+                       lambda: synth.water_box(synth.rng_for(5, 10), 4000)),
+                      ("mof-shaped (16 848 atoms, framework density 0.075 atoms/A^3, orthorhombic cell)",
+                       lambda: synth.framework_crystal(synth.rng_for(5, 11), 16848))):
+        ps = gen()
+        rng = np.random.default_rng(12)
+        signs, b = synth.sorf_draw(rng, 16384, 128, 3)
+        alpha = torch.as_tensor(rng.normal(size=16384).astype(np.float32)).cuda()
+        spec = pipeline.spec_from(p, 128, signs, b.astype(np.float32), 2.0)
+        t0 = time.perf_counter()
+        system = qmlr.PeriodicSystem(ps.coords, ps.elem, ps.cell, p.rcut)
+        env_s = time.perf_counter() - t0
+        rep = qmlr.fchl19_periodic(system, p)
+        perm, offs = qmlr.group_by_element(system.elem, p.n_el)
+        U = qmlr.pca_fit(rep, p.rep_dim, perm, offs, p.n_el, 128)
+        del rep
+        host_x = torch.as_tensor(ps.coords.astype(np.float32)).pin_memory()
+        host_E = torch.empty(1, dtype=torch.float64).pin_memory()
+        host_F = torch.empty((ps.n_atoms, 3), dtype=torch.float32).pin_memory()
+
+        def run(e2e):
+            if e2e:
+                system.coords.copy_(host_x, non_blocking=True)
+            E, F = pipeline.predict_periodic(system, spec, U, alpha)
+            if e2e:
+                host_E.copy_(E, non_blocking=True)
+                host_F.copy_(F, non_blocking=True)
+
+        res = {}
+        for e2e in (False, True):
+            run(e2e)
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                run(e2e)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res["e2e_ms" if e2e else "device_ms"] = statistics.median(ts)
+        n_env = np.diff(system.env_ptr.cpu().numpy())
+        out.append({"workload": name, "n_atoms": ps.n_atoms, "env_mean": float(n_env.mean()),
+                    "env_max": int(n_env.max()), "cell_list_s": env_s,
+                    "device_ms": res["device_ms"], "device_us_per_atom": res["device_ms"] * 1e3 / ps.n_atoms,
+                    "e2e_ms": res["e2e_ms"], "e2e_us_per_atom": res["e2e_ms"] * 1e3 / ps.n_atoms})
+        del system, U
+        torch.cuda.empty_cache()
+    return out
 
 
 def max_over_ranks(x: float, dist, device: str) -> float:
@@ -682,6 +750,8 @@ def run_ours(args, rank, world):
     if not args.no_ef and world == 1:
         line["ef_training"] = ef_training_phase(3, args.pcg_iters, args.pcg_tol, factor)
         line["ef_training_md17"] = ef_training_phase(2, args.pcg_iters, args.pcg_tol, factor)
+    if not args.no_periodic and world == 1:
+        line["periodic"] = periodic_phase()
     if not args.no_serve and world == 1:
         alpha_host = alpha.float().cpu().numpy()
         line["serving"] = serving_phase((p, U, w.signs, w.n_transform, w.b, w.sigma, alpha_host),
@@ -836,6 +906,131 @@ def run_gram_sweep(args):
         "points": pts}}), flush=True)
 
 
+def run_nf_sweep(args):
+    """Training time and held-out MAE against the feature count: QM9-shaped
+    workload, the first 90 % of the molecules for training and the last 10 %
+    held out, N_F in {4096, 8192, 16384, 32768} (T = 3, d = 128); train time =
+    FCHL19 -> projection -> SORF -> Z -> Gram -> factor + PCG by CUDA events.
+    Prints one JSON line."""
+    import torch
+    from paper_2206_01580_gb300 import pipeline, qmlr, synth
+    from paper_2206_01580_gb300.params import from_table
+
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream(priority=-100))
+    w, _ = build_workload(args.scale)
+    n_tr = int(0.9 * w.mols.n_mol)
+    tr, te = w.mols.subset(range(n_tr)), w.mols.subset(range(n_tr, w.mols.n_mol))
+    y = torch.as_tensor(w.energies[:n_tr]).cuda()
+    y_te = w.energies[n_tr:]
+    p = from_table(w.params_column, n2=w.n2, n3=w.n3)
+    btr = pipeline.Batch.from_host(tr.coords, tr.elem, tr.mol_ptr)
+    factor = qmlr.FACTOR_MIXED if args.factor == "mixed" else qmlr.FACTOR_FP64
+    s = torch.cuda.current_stream()
+    pts = []
+    U = None
+    for nf in (4096, 8192, 16384, 32768):
+        signs, b = synth.sorf_draw(synth.rng_for(1, 60 + nf // 4096), nf, w.d, w.n_transform)
+        spec = pipeline.spec_from(p, w.d, signs, b, w.sigma)
+        if U is None:
+            rep, perm, offs = pipeline.representations(btr, spec)
+            U = pipeline.fit_pca(rep, perm, offs, spec)
+            del rep, perm, offs
+        for rep_i in range(2):           # the first pass warms up
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(s)
+            Z = pipeline.feature_matrix(btr, spec, U)
+            ev[1].record(s)
+            alpha, it, rel = pipeline.solve(Z, y, w.lam, GRAM["precision"], max_iter=args.pcg_iters,
+                                            tol=args.pcg_tol, shift=GRAM["shift"], factor=factor,
+                                            promote=GRAM["promote"], tile=GRAM["tile"])
+            ev[2].record(s)
+            torch.cuda.synchronize()
+            del Z
+        so = qmlr.last_solve
+        model = qmlr.Model(p, int(te.sizes().max()), U, signs, w.n_transform, b, w.sigma,
+                           alpha.float().cpu().numpy())
+        E, _ = model.predict(te.coords, te.elem, te.mol_ptr, forces=False)
+        mae = float(np.mean(np.abs(E.cpu().numpy() - y_te)))
+        model.close()
+        pt = {"n_features": nf, "features_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
+              "train_s": ev[0].elapsed_time(ev[2]) / 1e3, "factor_ms": so.factor_ms, "refine_ms": so.refine_ms,
+              "pcg_iters": it, "rel_resid": rel, "test_mae_eV": mae}
+        print(json.dumps(pt), flush=True)
+        pts.append(pt)
+        del alpha
+        torch.cuda.empty_cache()
+    print(json.dumps({"nf_sweep": {
+        "workload": f"qm9-shaped ({n_tr} training / {te.n_mol} held-out molecules)",
+        "gram": gram_description()["text"], "shift": GRAM["shift"], "points": pts}}), flush=True)
+
+
+def run_rff_sweep(args):
+    """SORF against dense RFF (W = G / sigma) at equal feature counts on the
+    MD17-shaped conformations (energies only: 800 for training, 200 held out):
+    feature-map time and held-out MAE for N_F in {512, ..., 8192}. Prints one
+    JSON line."""
+    import torch
+    from paper_2206_01580_gb300 import pipeline, qmlr, synth
+    from paper_2206_01580_gb300.params import from_table
+
+    torch.cuda.set_device(0)
+    w = synth.workload(2)
+    tr, te = w.mols.subset(range(800)), w.mols.subset(range(800, 1000))
+    y = torch.as_tensor(w.energies[:800]).cuda()
+    y_te = torch.as_tensor(w.energies[800:]).cuda()
+    p = from_table(w.params_column, n2=w.n2, n3=w.n3)
+    spec0 = pipeline.spec_from(p, w.d, w.signs, w.b, w.sigma)
+    btr = pipeline.Batch.from_host(tr.coords, tr.elem, tr.mol_ptr)
+    bte = pipeline.Batch.from_host(te.coords, te.elem, te.mol_ptr)
+    rep, perm, offs = pipeline.representations(btr, spec0)
+    U = pipeline.fit_pca(rep, perm, offs, spec0)
+    x_tr = qmlr.project(rep, p.rep_dim, perm, offs, p.n_el, U)
+    rep, perm, offs = pipeline.representations(bte, spec0)
+    x_te = qmlr.project(rep, p.rep_dim, perm, offs, p.n_el, U)
+    del rep
+    factor = qmlr.FACTOR_MIXED if args.factor == "mixed" else qmlr.FACTOR_FP64
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def fit_mae(Z_tr, Z_te):
+        alpha, it, rel = pipeline.solve(Z_tr, y, w.lam, GRAM["precision"], max_iter=args.pcg_iters,
+                                        tol=args.pcg_tol, shift=GRAM["shift"], factor=factor,
+                                        promote=GRAM["promote"], tile=GRAM["tile"])
+        E = Z_te.double() @ alpha
+        return float(torch.mean(torch.abs(E - y_te)).item()), it, rel
+
+    pts = []
+    for nf in (512, 1024, 2048, 4096, 8192):
+        rng = synth.rng_for(2, 70 + nf // 512)
+        signs, b = synth.sorf_draw(rng, nf, w.d, w.n_transform)
+        bits = qmlr.pack_signs(signs)
+        bt = torch.as_tensor(b.astype(np.float32)).cuda()
+        Zs, ms_s = timed(lambda: qmlr.sorf(x_tr, btr.mol_ptr, bits, w.n_transform, bt, w.sigma, qmlr.SORF_PER_MOL))
+        Zs_te = qmlr.sorf(x_te, bte.mol_ptr, bits, w.n_transform, bt, w.sigma, qmlr.SORF_PER_MOL)
+        mae_s, it_s, _ = fit_mae(Zs, Zs_te)
+        G, b2 = synth.rff_draw(rng, nf, w.d)
+        Gt = torch.as_tensor(G.astype(np.float32)).cuda()
+        bt2 = torch.as_tensor(b2.astype(np.float32)).cuda()
+        Zr, ms_r = timed(lambda: qmlr.rff(x_tr, btr.mol_ptr, Gt, bt2, w.sigma, qmlr.SORF_PER_MOL))
+        Zr_te = qmlr.rff(x_te, bte.mol_ptr, Gt, bt2, w.sigma, qmlr.SORF_PER_MOL)
+        mae_r, it_r, _ = fit_mae(Zr, Zr_te)
+        pt = {"n_features": nf, "sorf_ms": ms_s, "rff_ms": ms_r, "sorf_test_mae_eV": mae_s,
+              "rff_test_mae_eV": mae_r, "sorf_pcg_iters": it_s, "rff_pcg_iters": it_r}
+        print(json.dumps(pt), flush=True)
+        pts.append(pt)
+    print(json.dumps({"rff_sweep": {
+        "workload": "md17-shaped (800 training / 200 held-out conformations, energies only)",
+        "sigma": w.sigma, "d": w.d, "n_transform": w.n_transform, "points": pts}}), flush=True)
+
+
 def gram_description():
     """Kernel name, tensor-core products per Gram product, rate relative to BF16
     and a text description of the training step's Gram form."""
@@ -872,6 +1067,12 @@ def main():
     elif args.gram_sweep:
         if rank == 0:
             run_gram_sweep(args)
+    elif args.nf_sweep:
+        if rank == 0:
+            run_nf_sweep(args)
+    elif args.rff_sweep:
+        if rank == 0:
+            run_rff_sweep(args)
     else:
         run_ours(args, rank, world)
 

@@ -99,6 +99,49 @@ int qmlr_periodic_environment_count(const double* host_coords, int32_t n_atoms, 
 int qmlr_periodic_environment(const double* host_coords, int32_t n_atoms, const double* host_cell, double rcut,
                               const int64_t* host_env_ptr, int32_t* host_env_atom, int32_t* host_env_shift);
 
+/*
+ * The environment entries grouped by the atom they name (host, synchronous):
+ * host_rev_ptr int64 [n_atoms+1], host_rev_entry int64 [env_ptr[n_atoms]]:
+ * the entries e with env_atom[e] == k are host_rev_entry[rev_ptr[k] .. rev_ptr[k+1]),
+ * ascending. Used by qmlr_fchl19_periodic_vjp to sum each atom's gradient in a
+ * fixed order.
+ */
+int qmlr_periodic_reverse(const int64_t* host_env_ptr, const int32_t* host_env_atom, int32_t n_atoms,
+                          int64_t* host_rev_ptr, int64_t* host_rev_entry);
+
+/*
+ * FCHL19 of a periodic system (the paper's periodic MOF and water systems): the
+ * row of atom i sums over its environment entries (j, n) (device copies of the
+ * qmlr_periodic_environment arrays) at R_j + n . cell, the displacement formed
+ * in FP64 and rounded to FP32. Entries at or beyond the cutoff in FP32 are
+ * skipped.
+ *   coords     float [n_atoms][3]    elem int32 [n_atoms]
+ *   host_cell  double [3][3] lattice vectors as rows (read on the call)
+ *   env_ptr    int64 [n_atoms+1], env_atom int32 [E], env_shift int32 [E][3]  (device)
+ *   max_env    upper bound on entries per atom (sizes shared memory; 0..2048,
+ *              the adjoint needs max_env of a few hundred at most); an atom with
+ *              more entries is recorded as device error 1 and its row set to zero
+ *   rep        float [n_atoms][rep_ld]
+ * Deterministic; asynchronous. n_el <= 5, n2, n3 <= 32.
+ */
+int qmlr_fchl19_periodic(const float* coords, const int32_t* elem, int32_t n_atoms, const double* host_cell,
+                         const int64_t* env_ptr, const int32_t* env_atom, const int32_t* env_shift,
+                         int32_t max_env, const qmlr_fchl19_params* p, float* rep, int32_t rep_ld, void* stream);
+
+/*
+ * Vector-Jacobian product of the periodic FCHL19 (forces of a periodic system):
+ *   grad_coords[k] (+)= scale * sum_i (d rho_i / d R_k)^T grad_rep[i]
+ * where an image R_j + n . cell moves with R_j. Same geometry arguments as
+ * qmlr_fchl19_periodic; rev_ptr, rev_entry (device) from qmlr_periodic_reverse;
+ * contrib: device scratch float [(E + n_atoms)][3]. Every atom's sum runs in a
+ * fixed order (deterministic); asynchronous.
+ */
+int qmlr_fchl19_periodic_vjp(const float* coords, const int32_t* elem, int32_t n_atoms, const double* host_cell,
+                             const int64_t* env_ptr, const int32_t* env_atom, const int32_t* env_shift,
+                             int32_t max_env, const qmlr_fchl19_params* p, const float* grad_rep, int32_t rep_ld,
+                             const int64_t* rev_ptr, const int64_t* rev_entry, float* contrib, float scale,
+                             float* grad_coords, int32_t accumulate, void* stream);
+
 /* rep_dim = n_el*n2 + n_el(n_el+1)/2 * n3 * 2 (780 for 5 elements, n2=24, n3=22). */
 int qmlr_fchl19_rep_dim(const qmlr_fchl19_params* p, int32_t* rep_dim);
 

@@ -121,3 +121,17 @@ def sorf_model(p: fchl19.Params, U: np.ndarray, signs: np.ndarray, b: np.ndarray
 
 def prefactor(n_features: int) -> float:
     return math.sqrt(2.0 / n_features)
+
+
+def periodic_energy_forces(coords: np.ndarray, elem: np.ndarray, cell: np.ndarray, m: Model):
+    """E = sum over the cell's atoms of alpha^T z(rho_I U_e(I)), rho from the
+    periodic FCHL19 (lattice images within r_cut), and F = -dE/dR [N, 3] by
+    reverse-mode differentiation of that definition."""
+    elem = np.asarray(elem)
+    R = torch.tensor(np.asarray(coords, dtype=np.float64), requires_grad=True)
+    rho = fchl19.representation_periodic(R, elem, cell, m.p)
+    U = torch.as_tensor(m.U)
+    x = torch.stack([rho[i] @ U[int(elem[i])] for i in range(R.shape[0])])
+    e = sorf.features(x, m.W, m.b).sum(dim=0) @ torch.as_tensor(m.alpha, dtype=torch.float64)
+    (g,) = torch.autograd.grad(e, R)
+    return float(e.detach()), -g.numpy()

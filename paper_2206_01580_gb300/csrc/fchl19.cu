@@ -149,10 +149,9 @@ __device__ int neighbour_list(const float4* pos, int M, int il, const Fchl19Cons
       nb_el[slot] = __float_as_int(wj);
       if (nb_idx) nb_idx[slot] = j;
       const float fc = cutoff_f(r, c);
-      const float q = 1.0f + c.eta2 * inv * inv;
-      const float s2 = logf(q);
+      const float s2 = log1pf(c.eta2 * inv * inv);   // sigma^2 = ln(1 + eta2 / r^2)
       const float s = sqrtf(s2);
-      nb_2b[slot] = make_float4(logf(r) - 0.5f * s2,                       // mu = ln(r / sqrt(q))
+      nb_2b[slot] = make_float4(logf(r) - 0.5f * s2,                       // mu = ln(r / sqrt(1 + eta2/r^2))
                                 0.5f / s2,                                  // 1 / (2 s^2)
                                 fc * expf(-c.N2 * logf(r)) * c.inv_sqrt_2pi / s,
                                 fc);
@@ -282,7 +281,9 @@ fchl19_forward_kernel(const float* __restrict__ coords, const int32_t* __restric
 // registers instead of a shared-memory read-modify-write; the row is written
 // straight from registers at the end.
 //
-// Work layout: a CTA takes a contiguous range of kFwdRange atoms; thread 0
+// Work layout: a CTA takes a contiguous range of `range` atoms (32 for large
+// batches, 4 - one atom per warp - for small ones, where the range would
+// otherwise leave most SMs idle and serialise the atoms of a molecule); thread 0
 // finds the molecules at its two ends (two binary searches per CTA instead of
 // one per atom), the CTA stages the positions of every molecule the range
 // touches once, and each warp takes every kWarpsFwd-th atom of the range. The
@@ -292,7 +293,7 @@ fchl19_forward_kernel(const float* __restrict__ coords, const int32_t* __restric
 // geometry uses the hardware cosine for the third cutoff factor and base-2
 // log / exponential for the ATM power. Summation order per bin: neighbours,
 // then triplets, in the same order as the shared-memory kernel.
-constexpr int kFwdRange = 32;          // atoms per CTA
+constexpr int kFwdRange = 32;          // atoms per CTA for large batches
 constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -314,18 +315,166 @@ struct RegWarp {
   int* nb_el;     // [mxp]
 };
 __host__ __device__ __forceinline__ size_t reg_warp_bytes(int mxp) { return (size_t)mxp * 36 + 512; }
-__host__ __device__ __forceinline__ int reg_stage_atoms(int mx) { return kFwdRange + 2 * (mx - 1); }
+__host__ __device__ __forceinline__ int reg_stage_atoms(int mx, int range) { return range + 2 * (mx - 1); }
 
+
+// Per-lane constants of the register forward (lane = radial bin).
+struct BinConsts {
+  bool has2, has3;
+  float r2log, r2inv, r3, neg_eta3;
+  int np;
+};
+__device__ __forceinline__ BinConsts bin_consts(const Fchl19Consts& c, int lane) {
+  BinConsts k;
+  k.has2 = lane < c.n2;
+  k.has3 = lane < c.n3;
+  k.r2log = k.has2 ? c.rs2_log[lane] : 0.f;
+  k.r2inv = k.has2 ? c.rs2_inv[lane] : 0.f;
+  k.r3 = k.has3 ? c.rs3[lane] : 0.f;
+  k.neg_eta3 = -c.eta3 * kLog2e;
+  k.np = c.n_el * (c.n_el + 1) / 2;
+  return k;
+}
+
+// One neighbour of the register forward at `slot`: displacement (dx, dy, dz)
+// from the centre, r2 = its squared length (0 < r2 < rcut^2), element e.
+__device__ __forceinline__ void store_neighbour(const RegWarp& s, int slot, float dx, float dy, float dz, float r2,
+                                                int e, const Fchl19Consts& c) {
+  const float r = sqrtf(r2);
+  const float inv = 1.0f / r;
+  s.nb_u[slot] = make_float4(dx * inv, dy * inv, dz * inv, r);
+  s.nb_el[slot] = e;
+  const float fc = cutoff_f(r, c);
+  const float s2 = log1pf(c.eta2 * inv * inv);   // sigma^2 = ln(1 + eta2 / r^2)
+  s.nb_2b[slot] = make_float4(logf(r) - 0.5f * s2,                        // mu = ln(r / sqrt(1 + eta2/r^2))
+                              kLog2e * 0.5f / s2,                        // log2(e) / (2 sigma^2)
+                              fc * expf(-c.N2 * logf(r)) * c.inv_sqrt_2pi * rsqrtf(s2),
+                              fc);
+}
+
+// The representation row of a centre from its n staged neighbours (one warp);
+// columns rep_dim..rep_ld-1 are written as zeros.
+__device__ __forceinline__ void fwd_row(const RegWarp& s, int n, const Fchl19Consts& c, const BinConsts& kb,
+                                        float* __restrict__ out, int rep_ld, int lane) {
+  const bool has2 = kb.has2, has3 = kb.has3;
+  const float r2log = kb.r2log, r2inv = kb.r2inv, r3 = kb.r3, neg_eta3 = kb.neg_eta3;
+  const int np = kb.np;
+  // two-body: lanes over bins; per block of 32 neighbours, element by element
+  // (a compile-time accumulator index), neighbours in order
+  float a2[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int ej = j0 + lane < n ? s.nb_el[j0 + lane] : -1;
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+      unsigned m = __ballot_sync(0xffffffffu, ej == e);
+      while (m) {
+        const int jn = j0 + __ffs(m) - 1;
+        m &= m - 1u;
+        const float4 t = s.nb_2b[jn];
+        const float d = r2log - t.x;
+        a2[e] = fmaf(t.z * r2inv, ex2_approx(-(d * d) * t.y), a2[e]);
+      }
+    }
+  }
+
+  // three-body: pair geometry lane-parallel over flat pairs (j < k), then lanes over bins
+  float ac[15], as[15];
+#pragma unroll
+  for (int q = 0; q < 15; ++q) {
+    ac[q] = 0.f;
+    as[q] = 0.f;
+  }
+  const int n_pairs = n * (n - 1) / 2;
+  for (int q0 = 0; q0 < n_pairs; q0 += 32) {
+    const int q = q0 + lane;
+    bool ok = false;
+    float wc = 0.f, ws = 0.f, xbar = 0.f;
+    int pidx = 0;
+    if (q < n_pairs) {
+      int jn, kn;
+      decode_pair(q, n, jn, kn);
+      const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+      const float vx = uk.x * uk.w - uj.x * uj.w;
+      const float vy = uk.y * uk.w - uj.y * uj.w;
+      const float vz = uk.z * uk.w - uj.z * uj.w;
+      const float rjk2 = vx * vx + vy * vy + vz * vz;
+      if (rjk2 < c.rcut2) {
+        ok = true;
+        const float inv_rjk = rsqrtf(rjk2);
+        const float rjk = rjk2 * inv_rjk;
+        const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+        const float cx = uj.y * uk.z - uj.z * uk.y;
+        const float cy = uj.z * uk.x - uj.x * uk.z;
+        const float cz = uj.x * uk.y - uj.y * uk.x;
+        const float si = sqrtf(cx * cx + cy * cy + cz * cz);
+        const float cj = -(uj.x * vx + uj.y * vy + uj.z * vz) * inv_rjk;
+        const float ck = (uk.x * vx + uk.y * vy + uk.z * vz) * inv_rjk;
+        // (r_ij r_ik r_jk)^-N3 = 2^(-N3 log2(r_ij r_ik r_jk))
+        const float atm = (1.0f + 3.0f * ci * cj * ck) * ex2_approx(-c.N3 * lg2_approx(uj.w * uk.w * rjk));
+        const float fcjk = 0.5f * (__cosf(rjk * c.pi_over_rcut) + 1.0f);
+        const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * fcjk;
+        wc = w * c.ang2 * ci;
+        ws = w * c.ang2 * si;
+        xbar = 0.5f * (uj.w + uk.w);
+        pidx = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
+      }
+    }
+    // stage the chunk in lane order; then, pair type by pair type (a
+    // compile-time accumulator index), walk that type's triplets in lane order
+    s.pairs[lane] = make_float4(wc, ws, xbar, 0.f);
+    __syncwarp();
+    const int key = ok ? pidx : 15;
+#pragma unroll
+    for (int b = 0; b < 15; ++b) {
+      unsigned m = __ballot_sync(0xffffffffu, key == b);
+      while (m) {
+        const int t0 = __ffs(m) - 1;
+        m &= m - 1u;
+        const float4 p0 = s.pairs[t0];
+        const float d0 = p0.z - r3;
+        const float g0 = ex2_approx(d0 * (d0 * neg_eta3));
+        if (m) {
+          const int t1 = __ffs(m) - 1;
+          m &= m - 1u;
+          const float4 p1 = s.pairs[t1];
+          const float d1 = p1.z - r3;
+          const float g1 = ex2_approx(d1 * (d1 * neg_eta3));
+          ac[b] = fmaf(g0, p0.x, ac[b]);
+          as[b] = fmaf(g0, p0.y, as[b]);
+          ac[b] = fmaf(g1, p1.x, ac[b]);
+          as[b] = fmaf(g1, p1.y, as[b]);
+        } else {
+          ac[b] = fmaf(g0, p0.x, ac[b]);
+          as[b] = fmaf(g0, p0.y, as[b]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  // write the row from registers; padding columns zero
+  if (has2)
+#pragma unroll
+    for (int e = 0; e < 5; ++e)
+      if (e < c.n_el) out[e * c.n2 + lane] = a2[e];
+  if (has3)
+#pragma unroll
+    for (int q = 0; q < 15; ++q)
+      if (q < np) {
+        out[c.base3 + (q * c.n3 + lane) * 2] = ac[q];
+        out[c.base3 + (q * c.n3 + lane) * 2 + 1] = as[q];
+      }
+    for (int k = c.rep_dim + lane; k < rep_ld; k += 32) out[k] = 0.0f;
+}
 
 __global__ void __launch_bounds__(32 * kWarpsFwd, 6)
 fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
-                          const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp,
+                          const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp, int range,
                           Fchl19Consts c, float* __restrict__ rep, int rep_ld, int* err) {
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ int s_m0, s_m1, s_base, s_end;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int a_lo = blockIdx.x * kFwdRange;
-  const int a_hi = min(a_lo + kFwdRange, n_atoms) - 1;
+  const int a_lo = blockIdx.x * range;
+  const int a_hi = min(a_lo + range, n_atoms) - 1;
   if (threadIdx.x == 0) {
     const int m0 = find_molecule(mol_ptr, n_mol, a_lo);
     const int m1 = find_molecule(mol_ptr, n_mol, a_hi);
@@ -338,7 +487,7 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
   }
   __syncthreads();
   const int m0 = s_m0, m1 = s_m1, base = s_base;
-  const int stage_n = s_end - base;   // <= kFwdRange + 2 (mx - 1)
+  const int stage_n = s_end - base;   // <= range + 2 (mx - 1)
   float4* pos = reinterpret_cast<float4*>(smem_raw);
   for (int j = threadIdx.x; j < stage_n; j += blockDim.x) {
     int e = __ldg(elem + base + j);
@@ -350,19 +499,14 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
     pos[j] = make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), __int_as_float(e));
   }
   __syncthreads();
-  char* wbase = smem_raw + (size_t)reg_stage_atoms(mx) * 16 + warp * reg_warp_bytes(mxp);
+  char* wbase = smem_raw + (size_t)reg_stage_atoms(mx, range) * 16 + warp * reg_warp_bytes(mxp);
   RegWarp s;
   s.nb_u = reinterpret_cast<float4*>(wbase);
   s.nb_2b = s.nb_u + mxp;
   s.pairs = s.nb_2b + mxp;
   s.nb_el = reinterpret_cast<int*>(s.pairs + 32);
 
-  // per-lane radial constants (lane = bin)
-  const bool has2 = lane < c.n2, has3 = lane < c.n3;
-  const float r2log = has2 ? c.rs2_log[lane] : 0.f, r2inv = has2 ? c.rs2_inv[lane] : 0.f;
-  const float r3 = has3 ? c.rs3[lane] : 0.f;
-  const float neg_eta3 = -c.eta3 * kLog2e;
-  const int np = c.n_el * (c.n_el + 1) / 2;
+  const BinConsts kb = bin_consts(c, lane);   // per-lane radial constants (lane = bin)
 
   for (int atom = a_lo + warp; atom <= a_hi; atom += kWarpsFwd) {
     // molecule of this atom: mol_ptr[mi] <= atom < mol_ptr[mi + 1], mi in [m0, m1]
@@ -396,128 +540,12 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
         ok = r2 < c.rcut2;
       }
       const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) {
-        const int slot = n + __popc(mask & ((1u << lane) - 1u));
-        const float r = sqrtf(r2);
-        const float inv = 1.0f / r;
-        s.nb_u[slot] = make_float4(dx * inv, dy * inv, dz * inv, r);
-        s.nb_el[slot] = __float_as_int(wj);
-        const float fc = cutoff_f(r, c);
-        const float s2 = log1pf(c.eta2 * inv * inv);   // sigma^2 = ln(1 + eta2 / r^2)
-        s.nb_2b[slot] = make_float4(logf(r) - 0.5f * s2,                        // mu = ln(r / sqrt(1 + eta2/r^2))
-                                    kLog2e * 0.5f / s2,                        // log2(e) / (2 sigma^2)
-                                    fc * expf(-c.N2 * logf(r)) * c.inv_sqrt_2pi * rsqrtf(s2),
-                                    fc);
-      }
+      if (ok) store_neighbour(s, n + __popc(mask & ((1u << lane) - 1u)), dx, dy, dz, r2, __float_as_int(wj), c);
       n += __popc(mask);
     }
     __syncwarp();
 
-    // two-body: lanes over bins; per block of 32 neighbours, element by element
-    // (a compile-time accumulator index), neighbours in order
-    float a2[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int j0 = 0; j0 < n; j0 += 32) {
-      const int ej = j0 + lane < n ? s.nb_el[j0 + lane] : -1;
-#pragma unroll
-      for (int e = 0; e < 5; ++e) {
-        unsigned m = __ballot_sync(0xffffffffu, ej == e);
-        while (m) {
-          const int jn = j0 + __ffs(m) - 1;
-          m &= m - 1u;
-          const float4 t = s.nb_2b[jn];
-          const float d = r2log - t.x;
-          a2[e] = fmaf(t.z * r2inv, ex2_approx(-(d * d) * t.y), a2[e]);
-        }
-      }
-    }
-
-    // three-body: pair geometry lane-parallel over flat pairs (j < k), then lanes over bins
-    float ac[15], as[15];
-#pragma unroll
-    for (int q = 0; q < 15; ++q) {
-      ac[q] = 0.f;
-      as[q] = 0.f;
-    }
-    const int n_pairs = n * (n - 1) / 2;
-    for (int q0 = 0; q0 < n_pairs; q0 += 32) {
-      const int q = q0 + lane;
-      bool ok = false;
-      float wc = 0.f, ws = 0.f, xbar = 0.f;
-      int pidx = 0;
-      if (q < n_pairs) {
-        int jn, kn;
-        decode_pair(q, n, jn, kn);
-        const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
-        const float vx = uk.x * uk.w - uj.x * uj.w;
-        const float vy = uk.y * uk.w - uj.y * uj.w;
-        const float vz = uk.z * uk.w - uj.z * uj.w;
-        const float rjk2 = vx * vx + vy * vy + vz * vz;
-        if (rjk2 < c.rcut2) {
-          ok = true;
-          const float inv_rjk = rsqrtf(rjk2);
-          const float rjk = rjk2 * inv_rjk;
-          const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-          const float cx = uj.y * uk.z - uj.z * uk.y;
-          const float cy = uj.z * uk.x - uj.x * uk.z;
-          const float cz = uj.x * uk.y - uj.y * uk.x;
-          const float si = sqrtf(cx * cx + cy * cy + cz * cz);
-          const float cj = -(uj.x * vx + uj.y * vy + uj.z * vz) * inv_rjk;
-          const float ck = (uk.x * vx + uk.y * vy + uk.z * vz) * inv_rjk;
-          // (r_ij r_ik r_jk)^-N3 = 2^(-N3 log2(r_ij r_ik r_jk))
-          const float atm = (1.0f + 3.0f * ci * cj * ck) * ex2_approx(-c.N3 * lg2_approx(uj.w * uk.w * rjk));
-          const float fcjk = 0.5f * (__cosf(rjk * c.pi_over_rcut) + 1.0f);
-          const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * fcjk;
-          wc = w * c.ang2 * ci;
-          ws = w * c.ang2 * si;
-          xbar = 0.5f * (uj.w + uk.w);
-          pidx = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
-        }
-      }
-      // stage the chunk in lane order; then, pair type by pair type (a
-      // compile-time accumulator index), walk that type's triplets in lane order
-      s.pairs[lane] = make_float4(wc, ws, xbar, 0.f);
-      __syncwarp();
-      const int key = ok ? pidx : 15;
-#pragma unroll
-      for (int b = 0; b < 15; ++b) {
-        unsigned m = __ballot_sync(0xffffffffu, key == b);
-        while (m) {
-          const int t0 = __ffs(m) - 1;
-          m &= m - 1u;
-          const float4 p0 = s.pairs[t0];
-          const float d0 = p0.z - r3;
-          const float g0 = ex2_approx(d0 * (d0 * neg_eta3));
-          if (m) {
-            const int t1 = __ffs(m) - 1;
-            m &= m - 1u;
-            const float4 p1 = s.pairs[t1];
-            const float d1 = p1.z - r3;
-            const float g1 = ex2_approx(d1 * (d1 * neg_eta3));
-            ac[b] = fmaf(g0, p0.x, ac[b]);
-            as[b] = fmaf(g0, p0.y, as[b]);
-            ac[b] = fmaf(g1, p1.x, ac[b]);
-            as[b] = fmaf(g1, p1.y, as[b]);
-          } else {
-            ac[b] = fmaf(g0, p0.x, ac[b]);
-            as[b] = fmaf(g0, p0.y, as[b]);
-          }
-        }
-      }
-      __syncwarp();
-    }
-    // write the row from registers; padding columns zero
-    if (has2)
-#pragma unroll
-      for (int e = 0; e < 5; ++e)
-        if (e < c.n_el) out[e * c.n2 + lane] = a2[e];
-    if (has3)
-#pragma unroll
-      for (int q = 0; q < 15; ++q)
-        if (q < np) {
-          out[c.base3 + (q * c.n3 + lane) * 2] = ac[q];
-          out[c.base3 + (q * c.n3 + lane) * 2 + 1] = as[q];
-        }
-    for (int k = c.rep_dim + lane; k < rep_ld; k += 32) out[k] = 0.0f;
+    fwd_row(s, n, c, kb, out, rep_ld, lane);
     __syncwarp();
   }
 }
@@ -558,11 +586,20 @@ __device__ __forceinline__ VjpWarp carve_vjp(char* base, int mxp, int rp) {
 // index j along contiguous lanes, so a segmented scan over lanes (keyed by j)
 // sums each row's run and the run's last lane adds it; the k-side values of one
 // row name distinct atoms, so the rows of the chunk add theirs one row at a time.
+// The body of the adjoint for n staged neighbours (nb_u, nb_2b in the
+// neighbour_list format, nb_el, nb_idx naming each neighbour's accumulator) and
+// the centre's gradient row in s.g; the centre's own gradient goes to
+// accumulator il.
+__device__ void vjp_from_neighbours(int n, int il, const Fchl19Consts& c, VjpWarp& s, int lane);
+
 __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts& c, const float* __restrict__ grow,
                            VjpWarp& s, int lane) {
   for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grow + k);
   const int n = neighbour_list(pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
+  vjp_from_neighbours(n, il, c, s, lane);
+}
 
+__device__ void vjp_from_neighbours(int n, int il, const Fchl19Consts& c, VjpWarp& s, int lane) {
   float gi_x = 0.f, gi_y = 0.f, gi_z = 0.f;   // gradient on the centre (per-lane partials)
   const float neg_eta3 = -c.eta3 * kLog2e;
 
@@ -1026,6 +1063,162 @@ __global__ void vjp_reduce_kernel(const int32_t* __restrict__ mol_ptr, int n_mol
   grad[t] = accumulate ? grad[t] + scale * sum : scale * sum;
 }
 
+// ---------------------------------------------------------------------------
+// Periodic systems (the paper's periodic MOF and water rows): the environment of
+// centre i is its list of lattice images (j, n) within r_cut, from the host
+// cell list (qmlr_periodic_environment), at R_j + n . cell. A warp per centre
+// builds its neighbour list from that list (the displacement R_j + n . cell -
+// R_i formed in FP64, then rounded, so that the lattice shift does not cost
+// FP32 precision), then runs the molecular kernels' row or adjoint arithmetic.
+
+struct Cell9 {
+  double a[9];   // lattice vectors as rows
+};
+
+__device__ __forceinline__ bool periodic_entry(const float* __restrict__ coords, const int32_t* __restrict__ elem,
+                                               int n_atoms, const Cell9& cell, const int32_t* __restrict__ env_atom,
+                                               const int32_t* __restrict__ env_shift, long e, double xi, double yi,
+                                               double zi, int n_el, float rcut2, float& dx, float& dy, float& dz,
+                                               float& r2, int& el, int* err) {
+  const int j = __ldg(env_atom + e);
+  if (j < 0 || j >= n_atoms) {
+    record_device_error(err, DEV_BAD_INDEX);
+    return false;
+  }
+  const double n0 = __ldg(env_shift + 3 * e), n1 = __ldg(env_shift + 3 * e + 1), n2 = __ldg(env_shift + 3 * e + 2);
+  const double px = (double)__ldg(coords + 3 * (size_t)j) + n0 * cell.a[0] + n1 * cell.a[3] + n2 * cell.a[6];
+  const double py = (double)__ldg(coords + 3 * (size_t)j + 1) + n0 * cell.a[1] + n1 * cell.a[4] + n2 * cell.a[7];
+  const double pz = (double)__ldg(coords + 3 * (size_t)j + 2) + n0 * cell.a[2] + n1 * cell.a[5] + n2 * cell.a[8];
+  dx = (float)(px - xi);
+  dy = (float)(py - yi);
+  dz = (float)(pz - zi);
+  r2 = dx * dx + dy * dy + dz * dz;
+  el = __ldg(elem + j);
+  if (el < 0 || el >= n_el) {
+    record_device_error(err, DEV_BAD_ELEMENT);
+    el = 0;
+  }
+  return r2 < rcut2 && r2 > 0.f;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsFwd, 6)
+fchl19_periodic_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem, int n_atoms, Cell9 cell,
+                       const int64_t* __restrict__ env_ptr, const int32_t* __restrict__ env_atom,
+                       const int32_t* __restrict__ env_shift, int max_env, int envp, Fchl19Consts c,
+                       float* __restrict__ rep, int rep_ld, int* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarpsFwd + warp;
+  if (i >= n_atoms) return;
+  char* wbase = smem_raw + warp * reg_warp_bytes(envp);
+  RegWarp s;
+  s.nb_u = reinterpret_cast<float4*>(wbase);
+  s.nb_2b = s.nb_u + envp;
+  s.pairs = s.nb_2b + envp;
+  s.nb_el = reinterpret_cast<int*>(s.pairs + 32);
+  const BinConsts kb = bin_consts(c, lane);
+  float* out = rep + (size_t)i * rep_ld;
+  const long e0 = __ldg(env_ptr + i), e1 = __ldg(env_ptr + i + 1);
+  if (e1 - e0 > max_env || e1 < e0) {
+    if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+    for (int k = lane; k < rep_ld; k += 32) out[k] = 0.0f;
+    return;
+  }
+  const double xi = __ldg(coords + 3 * (size_t)i), yi = __ldg(coords + 3 * (size_t)i + 1),
+               zi = __ldg(coords + 3 * (size_t)i + 2);
+  int n = 0;
+  for (long b0 = e0; b0 < e1; b0 += 32) {
+    const long e = b0 + lane;
+    bool ok = false;
+    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+    int el = 0;
+    if (e < e1)
+      ok = periodic_entry(coords, elem, n_atoms, cell, env_atom, env_shift, e, xi, yi, zi, c.n_el, c.rcut2, dx, dy,
+                          dz, r2, el, err);
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) store_neighbour(s, n + __popc(mask & ((1u << lane) - 1u)), dx, dy, dz, r2, el, c);
+    n += __popc(mask);
+  }
+  __syncwarp();
+  fwd_row(s, n, c, kb, out, rep_ld, lane);
+}
+
+// Adjoint: warp per centre i; the contribution of every environment entry e
+// goes to contrib[e] (the gradient with respect to the image, which is the
+// gradient with respect to R_j), the centre's own to contrib[E + i]. Entries
+// beyond the cutoff in FP32 get zero.
+__global__ void __launch_bounds__(32 * kWarpsVjp)
+fchl19_periodic_vjp_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem, int n_atoms,
+                           Cell9 cell, const int64_t* __restrict__ env_ptr, const int32_t* __restrict__ env_atom,
+                           const int32_t* __restrict__ env_shift, int max_env, int envp, Fchl19Consts c,
+                           const float* __restrict__ grad_rep, int rep_ld, float* __restrict__ contrib,
+                           int* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarpsVjp + warp;
+  if (i >= n_atoms) return;
+  const int rp = (c.rep_dim + 3) & ~3;
+  VjpWarp s = carve_vjp(smem_raw + warp * vjp_warp_bytes(envp + 4, rp), envp + 4, rp);
+  const long E = __ldg(env_ptr + n_atoms);
+  const long e0 = __ldg(env_ptr + i), e1 = __ldg(env_ptr + i + 1);
+  const int ne = (int)(e1 - e0);
+  if (e1 - e0 > max_env || e1 < e0) {
+    if (lane == 0) record_device_error(err, DEV_MOL_TOO_LARGE);
+    if (e1 >= e0)
+      for (long k = 3 * e0 + lane; k < 3 * e1; k += 32) contrib[k] = 0.0f;
+    if (lane < 3) contrib[3 * (E + i) + lane] = 0.0f;
+    return;
+  }
+  for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grad_rep + (size_t)i * rep_ld + k);
+  for (int k = lane; k < 3 * (ne + 1); k += 32) s.facc[k] = 0.0f;
+  const double xi = __ldg(coords + 3 * (size_t)i), yi = __ldg(coords + 3 * (size_t)i + 1),
+               zi = __ldg(coords + 3 * (size_t)i + 2);
+  int n = 0;
+  for (long b0 = e0; b0 < e1; b0 += 32) {
+    const long e = b0 + lane;
+    bool ok = false;
+    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+    int el = 0;
+    if (e < e1)
+      ok = periodic_entry(coords, elem, n_atoms, cell, env_atom, env_shift, e, xi, yi, zi, c.n_el, c.rcut2, dx, dy,
+                          dz, r2, el, err);
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const int slot = n + __popc(mask & ((1u << lane) - 1u));
+      const float r = sqrtf(r2);
+      const float inv = 1.0f / r;
+      s.nb_u[slot] = make_float4(dx * inv, dy * inv, dz * inv, r);
+      s.nb_el[slot] = el;
+      s.nb_idx[slot] = (int)(e - e0);          // accumulator: the entry
+      const float fc = cutoff_f(r, c);
+      const float s2 = log1pf(c.eta2 * inv * inv);
+      s.nb_2b[slot] = make_float4(logf(r) - 0.5f * s2, 0.5f / s2,
+                                  fc * expf(-c.N2 * logf(r)) * c.inv_sqrt_2pi / sqrtf(s2), fc);
+    }
+    n += __popc(mask);
+  }
+  __syncwarp();
+  vjp_from_neighbours(n, ne, c, s, lane);       // the centre's accumulator after the entries'
+  __syncwarp();
+  for (int k = lane; k < 3 * ne; k += 32) contrib[3 * e0 + k] = s.facc[k];
+  if (lane < 3) contrib[3 * (E + i) + lane] = s.facc[3 * ne + lane];
+}
+
+// grad[k] (+)= scale * (contrib[E + k] + sum over the entries naming atom k, in
+// entry order); rev_ptr / rev_entry: the entries grouped by atom.
+__global__ void periodic_reduce_kernel(int n_atoms, const int64_t* __restrict__ env_ptr,
+                                       const int64_t* __restrict__ rev_ptr, const int64_t* __restrict__ rev_entry,
+                                       const float* __restrict__ contrib, float scale, int accumulate,
+                                       float* __restrict__ grad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n_atoms) return;
+  const int k = t / 3, x = t % 3;
+  const long E = env_ptr[n_atoms];
+  float sum = contrib[3 * (E + k) + x];
+  for (long q = rev_ptr[k]; q < rev_ptr[k + 1]; ++q) sum += contrib[3 * rev_entry[q] + x];
+  grad[t] = accumulate ? grad[t] + scale * sum : scale * sum;
+}
+
 static int rep_pad_of(int rep_dim) { return (rep_dim + 3) & ~3; }
 
 static int check_geometry(const float* coords, const int32_t* elem, const int32_t* mol_ptr,
@@ -1069,11 +1262,14 @@ extern "C" int qmlr_fchl19(const float* coords, const int32_t* elem, const int32
   const size_t smem = kWarpsFwd * fwd_warp_bytes(mxp, rp);
   QMLR_REQUIRE(smem <= 227 * 1024, "shared memory request too large");
   if (p->n_el <= 5 && p->n2 <= 32 && p->n3 <= 32) {
-    const size_t rsmem = (size_t)reg_stage_atoms(mx) * 16 + kWarpsFwd * reg_warp_bytes(mxp);
-    QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_reg_kernel, (int)rsmem));
-    const int rgrid = (n_atoms + kFwdRange - 1) / kFwdRange;
+    // 32-atom ranges once they still give every SM several CTAs, one atom per warp below that
+    const int range = n_atoms >= kFwdRange * 8 * sm_count() ? kFwdRange : kWarpsFwd;
+    const size_t rsmem = (size_t)reg_stage_atoms(mx, range) * 16 + kWarpsFwd * reg_warp_bytes(mxp);
+    QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_reg_kernel,
+                                 (int)((size_t)reg_stage_atoms(mx, kFwdRange) * 16 + kWarpsFwd * reg_warp_bytes(mxp))));
+    const int rgrid = (n_atoms + range - 1) / range;
     fchl19_forward_reg_kernel<<<rgrid, 32 * kWarpsFwd, rsmem, as_stream(stream)>>>(
-        coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, c, rep, rep_ld, device_error_ptr());
+        coords, elem, mol_ptr, n_mol, n_atoms, mx, mxp, range, c, rep, rep_ld, device_error_ptr());
   } else {
     QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_forward_kernel, 227 * 1024));
     const int grid = (n_atoms + kWarpsFwd - 1) / kWarpsFwd;
@@ -1179,6 +1375,78 @@ extern "C" int qmlr_fchl19_vjp_atoms(const float* coords, const int32_t* elem, c
   QMLR_LAUNCH_CHECK();
   vjp_reduce_kernel<<<(3 * n_atoms + 255) / 256, 256, 0, st>>>(mol_ptr, n_mol, n_atoms, pair_ptr, contrib, scale,
                                                               accumulate, grad_coords);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+static int periodic_setup(const qmlr_fchl19_params* p, const float* coords, const int32_t* elem, int32_t n_atoms,
+                          const double* host_cell, const int64_t* env_ptr, const int32_t* env_atom,
+                          const int32_t* env_shift, int32_t max_env, Cell9* cell) {
+  int rc = validate_params(p);
+  if (rc) return rc;
+  QMLR_REQUIRE(n_atoms >= 0, "n_atoms must be >= 0");
+  QMLR_REQUIRE(max_env >= 0 && max_env <= 2048, "max_env must be in 0..2048 (got %d)", max_env);
+  QMLR_REQUIRE(host_cell, "host_cell is NULL");
+  QMLR_REQUIRE(n_atoms == 0 || (coords && elem && env_ptr && (max_env == 0 || (env_atom && env_shift))),
+               "NULL pointer argument");
+  for (int k = 0; k < 9; ++k) {
+    QMLR_REQUIRE(std::isfinite(host_cell[k]), "cell entries must be finite");
+    cell->a[k] = host_cell[k];
+  }
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_fchl19_periodic(const float* coords, const int32_t* elem, int32_t n_atoms, const double* host_cell,
+                                    const int64_t* env_ptr, const int32_t* env_atom, const int32_t* env_shift,
+                                    int32_t max_env, const qmlr_fchl19_params* p, float* rep, int32_t rep_ld,
+                                    void* stream) {
+  Cell9 cell;
+  int rc = periodic_setup(p, coords, elem, n_atoms, host_cell, env_ptr, env_atom, env_shift, max_env, &cell);
+  if (rc) return rc;
+  const int rd = rep_dim_of(*p);
+  QMLR_REQUIRE(rep_ld >= rd, "rep_ld (%d) < rep_dim (%d)", rep_ld, rd);
+  QMLR_REQUIRE(p->n_el <= 5 && p->n2 <= 32 && p->n3 <= 32,
+               "the periodic kernels support n_el <= 5 and radial grids of at most 32 points");
+  if (n_atoms == 0) return QMLR_OK;
+  QMLR_REQUIRE(rep, "rep is NULL");
+  const Fchl19Consts c = make_consts(*p);
+  const int envp = (std::max(max_env, 1) + 3) & ~3;
+  const size_t smem = kWarpsFwd * reg_warp_bytes(envp);
+  QMLR_REQUIRE(smem <= 227 * 1024, "max_env too large for shared memory");
+  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_periodic_kernel, (int)smem));
+  fchl19_periodic_kernel<<<(n_atoms + kWarpsFwd - 1) / kWarpsFwd, 32 * kWarpsFwd, smem, as_stream(stream)>>>(
+      coords, elem, n_atoms, cell, env_ptr, env_atom, env_shift, max_env, envp, c, rep, rep_ld, device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_fchl19_periodic_vjp(const float* coords, const int32_t* elem, int32_t n_atoms,
+                                        const double* host_cell, const int64_t* env_ptr, const int32_t* env_atom,
+                                        const int32_t* env_shift, int32_t max_env, const qmlr_fchl19_params* p,
+                                        const float* grad_rep, int32_t rep_ld, const int64_t* rev_ptr,
+                                        const int64_t* rev_entry, float* contrib, float scale, float* grad_coords,
+                                        int32_t accumulate, void* stream) {
+  Cell9 cell;
+  int rc = periodic_setup(p, coords, elem, n_atoms, host_cell, env_ptr, env_atom, env_shift, max_env, &cell);
+  if (rc) return rc;
+  const int rd = rep_dim_of(*p);
+  QMLR_REQUIRE(rep_ld >= rd, "rep_ld (%d) < rep_dim (%d)", rep_ld, rd);
+  if (n_atoms == 0) return QMLR_OK;
+  QMLR_REQUIRE(grad_rep && rev_ptr && (max_env == 0 || rev_entry) && contrib && grad_coords,
+               "NULL pointer argument");
+  const Fchl19Consts c = make_consts(*p);
+  const int rp = rep_pad_of(rd);
+  const int envp = (std::max(max_env, 1) + 3) & ~3;
+  const size_t smem = kWarpsVjp * vjp_warp_bytes(envp + 4, rp);
+  QMLR_REQUIRE(smem <= 227 * 1024, "max_env too large for shared memory");
+  QMLR_CUDA_TRY(smem_attr_once((const void*)fchl19_periodic_vjp_kernel, (int)smem));
+  cudaStream_t st = as_stream(stream);
+  fchl19_periodic_vjp_kernel<<<(n_atoms + kWarpsVjp - 1) / kWarpsVjp, 32 * kWarpsVjp, smem, st>>>(
+      coords, elem, n_atoms, cell, env_ptr, env_atom, env_shift, max_env, envp, c, grad_rep, rep_ld, contrib,
+      device_error_ptr());
+  QMLR_LAUNCH_CHECK();
+  periodic_reduce_kernel<<<(3 * n_atoms + 255) / 256, 256, 0, st>>>(n_atoms, env_ptr, rev_ptr, rev_entry, contrib,
+                                                                    scale, accumulate, grad_coords);
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }

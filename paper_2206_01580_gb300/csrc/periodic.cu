@@ -165,3 +165,22 @@ extern "C" int qmlr_periodic_environment(const double* host_coords, int32_t n_at
 }
 
 }  // namespace qmlr
+
+extern "C" int qmlr_periodic_reverse(const int64_t* host_env_ptr, const int32_t* host_env_atom, int32_t n_atoms,
+                                     int64_t* host_rev_ptr, int64_t* host_rev_entry) {
+  QMLR_REQUIRE(n_atoms >= 0, "n_atoms must be >= 0");
+  QMLR_REQUIRE(host_env_ptr && host_rev_ptr, "NULL pointer argument");
+  const int64_t E = host_env_ptr[n_atoms];
+  QMLR_REQUIRE(E >= 0 && (E == 0 || (host_env_atom && host_rev_entry)), "NULL pointer argument");
+  std::vector<int64_t> cnt((size_t)n_atoms + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t j = host_env_atom[e];
+    QMLR_REQUIRE(j >= 0 && j < n_atoms, "env_atom[%lld] = %d out of range", (long long)e, j);
+    ++cnt[(size_t)j + 1];
+  }
+  host_rev_ptr[0] = 0;
+  for (int k = 0; k < n_atoms; ++k) host_rev_ptr[k + 1] = host_rev_ptr[k] + cnt[(size_t)k + 1];
+  std::vector<int64_t> pos(host_rev_ptr, host_rev_ptr + n_atoms);
+  for (int64_t e = 0; e < E; ++e) host_rev_entry[pos[(size_t)host_env_atom[e]]++] = e;
+  return QMLR_OK;
+}

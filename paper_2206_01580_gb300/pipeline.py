@@ -177,3 +177,24 @@ def train_energy_force(batch: Batch, energies, forces, spec: FeatureSpec, lam: f
                    torch.as_tensor(np.asarray(forces, dtype=np.float64)).reshape(-1)]).cuda()
     alpha, it, rel = solve(rows, y, lam, precision, **solve_kw)
     return alpha, U, it, rel
+
+
+def predict_periodic(system: "qmlr.PeriodicSystem", spec: FeatureSpec, U, alpha, forces: bool = True):
+    """Energy (float64 [1]) and forces F = -dE/dR [N, 3] of a periodic system with
+    the atomic energy partition over the cell's atoms: periodic FCHL19 ->
+    grouping -> projection -> SORF energies and gradient -> transposed
+    projection -> periodic FCHL19 adjoint (scale -1)."""
+    p = spec.p
+    rep = qmlr.fchl19_periodic(system, p)
+    perm, offs = qmlr.group_by_element(system.elem, p.n_el)
+    x = qmlr.project(rep, p.rep_dim, perm, offs, p.n_el, U)
+    del rep
+    mol_ptr = torch.tensor([0, system.n_atoms], dtype=torch.int32, device="cuda")
+    if not forces:
+        E = qmlr.sorf(x, mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_ENERGY, alpha=alpha)
+        return E, None
+    E, gx = qmlr.sorf_grad(x, mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, alpha)
+    grep = qmlr.project_t(gx, perm, offs, p.n_el, U, p.rep_dim)
+    del gx
+    F = qmlr.fchl19_periodic_vjp(system, p, grep, scale=-1.0)
+    return E, F

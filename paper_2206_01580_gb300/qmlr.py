@@ -93,6 +93,10 @@ _SIGS = {
     "qmlr_model_file_read": (C.c_int, [C.c_char_p, P, P, P, P]),
     "qmlr_periodic_environment_count": (C.c_int, [P, I32, P, D, P]),
     "qmlr_periodic_environment": (C.c_int, [P, I32, P, D, P, P, P]),
+    "qmlr_periodic_reverse": (C.c_int, [P, P, I32, P, P]),
+    "qmlr_fchl19_periodic": (C.c_int, [P, P, I32, P, P, P, P, I32, C.POINTER(_Params), P, I32, VP]),
+    "qmlr_fchl19_periodic_vjp": (C.c_int, [P, P, I32, P, P, P, P, I32, C.POINTER(_Params), P, I32, P, P, P,
+                                           C.c_float, P, I32, VP]),
     "qmlr_rff": (C.c_int, [P, I32, P, I32, I32, P, P, I32, D, I32, P, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, VP]),
@@ -337,6 +341,60 @@ def periodic_environment(coords, cell, rcut: float):
     _check(lib().qmlr_periodic_environment(x.ctypes.data, n, A.ctypes.data, float(rcut), ptr.ctypes.data,
                                            atom.ctypes.data, shift.ctypes.data))
     return ptr, atom[:ptr[-1]], shift[:ptr[-1]]
+
+
+class PeriodicSystem:
+    """A periodic system on the device: coordinates, elements, the cell and its
+    lattice-image environments (host cell list, uploaded once) with the entries
+    grouped by atom for the adjoint."""
+
+    def __init__(self, coords, elem, cell, rcut: float):
+        x = np.ascontiguousarray(np.asarray(coords, dtype=np.float32))
+        self.cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64))
+        self.n_atoms = x.shape[0]
+        env_ptr, env_atom, env_shift = periodic_environment(x.astype(np.float64), self.cell, rcut)
+        rev_ptr = np.zeros(self.n_atoms + 1, np.int64)
+        rev_entry = np.zeros(max(int(env_ptr[-1]), 1), np.int64)
+        ea = np.ascontiguousarray(env_atom.astype(np.int32))
+        _check(lib().qmlr_periodic_reverse(env_ptr.ctypes.data, ea.ctypes.data, self.n_atoms, rev_ptr.ctypes.data,
+                                           rev_entry.ctypes.data))
+        self.max_env = int(np.max(np.diff(env_ptr))) if self.n_atoms else 0
+        self.n_entries = int(env_ptr[-1])
+        self.coords = torch.as_tensor(x).cuda()
+        self.elem = _dev(elem, torch.int32)
+        self.env_ptr = torch.as_tensor(env_ptr).cuda()
+        self.env_atom = torch.as_tensor(np.ascontiguousarray(ea if len(ea) else np.zeros(1, np.int32))).cuda()
+        sh = env_shift.astype(np.int32) if len(env_shift) else np.zeros((1, 3), np.int32)
+        self.env_shift = torch.as_tensor(np.ascontiguousarray(sh)).cuda()
+        self.rev_ptr = torch.as_tensor(rev_ptr).cuda()
+        self.rev_entry = torch.as_tensor(rev_entry).cuda()
+
+
+def fchl19_periodic(system: "PeriodicSystem", p: FCHL19Params, rep_ld: int | None = None, coords=None):
+    """Rows [n_atoms, rep_ld] of a periodic system (coords: optional replacement positions)."""
+    rep_ld = rep_ld or rep_ld_of(p.rep_dim)
+    x = system.coords if coords is None else _dev(coords, torch.float32)
+    out = torch.empty((system.n_atoms, rep_ld), device="cuda", dtype=torch.float32)
+    cp = c_params(p)
+    _check(lib().qmlr_fchl19_periodic(_ptr(x), _ptr(system.elem), system.n_atoms, system.cell.ctypes.data,
+                                      _ptr(system.env_ptr), _ptr(system.env_atom), _ptr(system.env_shift),
+                                      system.max_env, C.byref(cp), _ptr(out), rep_ld, _stream()))
+    return out
+
+
+def fchl19_periodic_vjp(system: "PeriodicSystem", p: FCHL19Params, grad_rep, scale: float = 1.0, coords=None):
+    """scale * sum_i (d rho_i / d R)^T grad_rep[i] for a periodic system, [n_atoms, 3]."""
+    x = system.coords if coords is None else _dev(coords, torch.float32)
+    grad_rep = _dev(grad_rep, torch.float32)
+    contrib = torch.empty((system.n_entries + system.n_atoms, 3), device="cuda", dtype=torch.float32)
+    out = torch.empty((system.n_atoms, 3), device="cuda", dtype=torch.float32)
+    cp = c_params(p)
+    _check(lib().qmlr_fchl19_periodic_vjp(_ptr(x), _ptr(system.elem), system.n_atoms, system.cell.ctypes.data,
+                                          _ptr(system.env_ptr), _ptr(system.env_atom), _ptr(system.env_shift),
+                                          system.max_env, C.byref(cp), _ptr(grad_rep), grad_rep.shape[1],
+                                          _ptr(system.rev_ptr), _ptr(system.rev_entry), _ptr(contrib), scale,
+                                          _ptr(out), 0, _stream()))
+    return out
 
 
 def save_model(path: str, p: FCHL19Params, U, signs, T: int, b, sigma: float, lam: float, alpha) -> None:

@@ -347,6 +347,93 @@ def serving_molecules(rng, n_mol: int, lo: int = 5, hi: int = 200) -> MoleculeSe
     return grow_batch(rng, [random_composition(rng, int(m)) for m in sizes])
 
 
+# ----------------------------------------------------------------------------
+# periodic systems: stand-ins for the paper's liquid water and MOF crystal
+
+
+@dataclass
+class PeriodicSet:
+    coords: np.ndarray   # float64 [N, 3] (inside the cell)
+    elem: np.ndarray     # int32 [N]
+    cell: np.ndarray     # float64 [3, 3] lattice vectors as rows
+
+    @property
+    def n_atoms(self) -> int:
+        return len(self.elem)
+
+
+def _periodic_ok(tree_pts, pts, box, rmin):
+    """True where a point of pts keeps rmin from every point of tree_pts (orthorhombic box)."""
+    from scipy.spatial import cKDTree
+    if len(tree_pts) == 0:
+        return np.ones(len(pts), dtype=bool)
+    t = cKDTree(np.mod(tree_pts, box), boxsize=box)
+    d, _ = t.query(np.mod(pts, box), k=1)
+    return d >= rmin
+
+
+def water_box(rng, n_waters: int, density_g_cm3: float = 1.0) -> PeriodicSet:
+    """Liquid-water-shaped periodic box: n rigid waters (O-H 0.957 A, H-O-H
+    104.5 deg) in a cubic cell at the given density (29.9 A^3 per molecule at
+    1 g/cm^3); oxygens on a jittered cubic grid, random orientations, and the
+    waters with an atom closer than 1.2 A to another water's are re-oriented
+    until none is."""
+    from scipy.spatial import cKDTree
+    L = (n_waters * 18.015 / (6.02214076e23 * density_g_cm3) * 1e24) ** (1.0 / 3.0)
+    k = int(math.ceil(n_waters ** (1.0 / 3.0)))
+    a = L / k
+    grid = np.stack(np.meshgrid(*[np.arange(k)] * 3, indexing="ij"), axis=-1).reshape(-1, 3)[:n_waters]
+    oxy = (grid + 0.5) * a + rng.uniform(-0.25, 0.25, size=(n_waters, 3))
+    box = np.array([L, L, L])
+    ang = math.radians(104.5)
+
+    def orient(m):
+        u = rng.normal(size=(m, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        v = rng.normal(size=(m, 3))
+        v -= u * np.sum(u * v, axis=1, keepdims=True)
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return 0.957 * u, 0.957 * (math.cos(ang) * u + math.sin(ang) * v)
+
+    h1, h2 = orient(n_waters)
+    for _ in range(100):
+        pts = np.concatenate([oxy, oxy + h1, oxy + h2])            # [3n, 3]: O block, H1 block, H2 block
+        pairs = cKDTree(np.mod(pts, box), boxsize=box).query_pairs(1.2, output_type="ndarray")
+        mol = np.tile(np.arange(n_waters), 3)
+        bad = pairs[mol[pairs[:, 0]] != mol[pairs[:, 1]]] if len(pairs) else pairs
+        if len(bad) == 0:
+            break
+        redo = np.unique(mol[bad[:, 1]])
+        h1[redo], h2[redo] = orient(len(redo))
+    atoms = np.stack([oxy, oxy + h1, oxy + h2], axis=1).reshape(-1, 3)
+    elem = np.tile(np.array([O, H, H], dtype=np.int32), n_waters)
+    return PeriodicSet(np.mod(atoms, box), elem, np.diag(box))
+
+
+def framework_crystal(rng, n_atoms: int, density: float = 0.075, rmin: float = 1.05,
+                      fractions=(0.35, 0.45, 0.08, 0.12, 0.0)) -> PeriodicSet:
+    """MOF-shaped periodic crystal: n atoms (H/C/N/O/F fractions) at a framework's
+    number density (atoms per A^3) in an orthorhombic cell with edges in ratio
+    1 : 1.1 : 1.2, positions by random sequential insertion keeping rmin."""
+    vol = n_atoms / density
+    a = (vol / (1.0 * 1.1 * 1.2)) ** (1.0 / 3.0)
+    box = np.array([a, 1.1 * a, 1.2 * a])
+    from scipy.spatial import cKDTree
+    pts = np.zeros((0, 3))
+    while len(pts) < n_atoms:
+        cand = rng.uniform(0.0, 1.0, size=(n_atoms - len(pts) + 16, 3)) * box
+        cand = cand[_periodic_ok(pts, cand, box, rmin)]
+        # candidates must also keep rmin from each other: of a close pair the later one goes
+        if len(cand) > 1:
+            pairs = cKDTree(cand, boxsize=box).query_pairs(rmin, output_type="ndarray")
+            drop = np.zeros(len(cand), dtype=bool)
+            drop[pairs[:, 1] if len(pairs) else []] = True
+            cand = cand[~drop]
+        pts = np.concatenate([pts, cand[: n_atoms - len(pts)]])
+    elem = rng.choice(5, size=n_atoms, p=np.asarray(fractions) / np.sum(fractions)).astype(np.int32)
+    return PeriodicSet(pts[:n_atoms], elem, np.diag(box))
+
+
 def poisson_arrivals(rng, rate_per_s: float, duration_s: float) -> np.ndarray:
     """Arrival times (s) of a Poisson process."""
     t, out = 0.0, []

@@ -120,3 +120,27 @@ def test_periodic_forces_are_the_energy_gradient():
     assert rel(g.numpy(), fd) <= 1e-6
     # the energy of a crystal does not change when every atom moves together
     assert np.max(np.abs(g.numpy().sum(0))) <= 1e-9 * np.max(np.abs(g.numpy()))
+
+
+def test_periodic_energy_forces_are_minus_the_energy_gradient():
+    """The periodic energy + force oracle: forces equal central differences of
+    its energies (h = 1e-4 A) and sum to zero (translation invariance)."""
+    from oracle import model, regression, sorf
+    p = P("EF")
+    rng = np.random.default_rng(3)
+    reps = per(X3, E3, CELL, p)
+    U = regression.pca_bases(reps, np.asarray(E3), 5, 16)
+    signs = rng.choice([-1, 1], size=(4, 3, 16))
+    b = rng.uniform(0, 2 * math.pi, size=64)
+    m = model.Model(p, U, sorf.sorf_matrix(signs, 2.0), b, rng.normal(size=64))
+    E, F = model.periodic_energy_forces(X3, E3, CELL, m)
+    h = 1e-4
+    for k in range(3):
+        for a in range(3):
+            xp, xm = X3.copy(), X3.copy()
+            xp[k, a] += h
+            xm[k, a] -= h
+            fd = -(model.periodic_energy_forces(xp, E3, CELL, m)[0] -
+                   model.periodic_energy_forces(xm, E3, CELL, m)[0]) / (2 * h)
+            assert abs(fd - F[k, a]) <= 1e-6 * max(1.0, np.abs(F).max()), (k, a, fd, F[k, a])
+    assert np.max(np.abs(F.sum(axis=0))) <= 1e-9 * max(1.0, np.abs(F).max())
