@@ -826,10 +826,13 @@ def run_feature_sweep(args):
         Gt = torch.as_tensor(G.astype(np.float32)).cuda()
         bt = torch.as_tensor(b.astype(np.float32)).cuda()
         ms = timed(lambda: qmlr.rff(x, batch.mol_ptr, Gt, bt, w.sigma, qmlr.SORF_PER_MOL))
+        ms_tc = timed(lambda: qmlr.rff_tc(x, batch.mol_ptr, Gt, bt, w.sigma, qmlr.SORF_PER_MOL))
         flop = 2 * nf * d
-        rff_pts.append({"n_features": nf, "ms": ms, "us_per_atom": ms * 1e3 / n_atoms,
-                        "tflop_s": flop * n_atoms / (ms * 1e-3) / 1e12,
-                        "fma_frac": flop * n_atoms / (ms * 1e-3) / 1e12 / (2 * alu_peak)})
+        rff_pts.append({"n_features": nf, "simt_ms": ms, "simt_us_per_atom": ms * 1e3 / n_atoms,
+                        "simt_tflop_s": flop * n_atoms / (ms * 1e-3) / 1e12,
+                        "simt_fma_frac": flop * n_atoms / (ms * 1e-3) / 1e12 / (2 * alu_peak),
+                        "tc_ms": ms_tc, "tc_us_per_atom": ms_tc * 1e3 / n_atoms,
+                        "tc_tflop_s": flop * n_atoms / (ms_tc * 1e-3) / 1e12})
     print(json.dumps({"feature_sweep": {
         "workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
         "n_atoms": n_atoms, "n_molecules": mols.n_mol, "d": d, "sigma": w.sigma,
@@ -1022,8 +1025,12 @@ def run_rff_sweep(args):
         Zr, ms_r = timed(lambda: qmlr.rff(x_tr, btr.mol_ptr, Gt, bt2, w.sigma, qmlr.SORF_PER_MOL))
         Zr_te = qmlr.rff(x_te, bte.mol_ptr, Gt, bt2, w.sigma, qmlr.SORF_PER_MOL)
         mae_r, it_r, _ = fit_mae(Zr, Zr_te)
-        pt = {"n_features": nf, "sorf_ms": ms_s, "rff_ms": ms_r, "sorf_test_mae_eV": mae_s,
-              "rff_test_mae_eV": mae_r, "sorf_pcg_iters": it_s, "rff_pcg_iters": it_r}
+        Zt, ms_t = timed(lambda: qmlr.rff_tc(x_tr, btr.mol_ptr, Gt, bt2, w.sigma, qmlr.SORF_PER_MOL))
+        Zt_te = qmlr.rff_tc(x_te, bte.mol_ptr, Gt, bt2, w.sigma, qmlr.SORF_PER_MOL)
+        mae_t, _, _ = fit_mae(Zt, Zt_te)
+        pt = {"n_features": nf, "sorf_ms": ms_s, "rff_simt_ms": ms_r, "rff_tc_ms": ms_t,
+              "sorf_test_mae_eV": mae_s, "rff_test_mae_eV": mae_r, "rff_tc_test_mae_eV": mae_t,
+              "sorf_pcg_iters": it_s, "rff_pcg_iters": it_r}
         print(json.dumps(pt), flush=True)
         pts.append(pt)
     print(json.dumps({"rff_sweep": {

@@ -345,6 +345,22 @@ int qmlr_rff(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, i
              float* out, void* stream);
 
 /*
+ * The same dense random Fourier features on the tensor cores: u = x (G/sigma)^T
+ * as a tcgen05 GEMM on 3-way BF16 splits of both operands (FP32 accumulation:
+ * products to ~2^-24, the accuracy of an FP32 GEMM), in chunks of up to 65 536
+ * atoms, then cos(u + b) (cosf) and, in PER_MOL mode, the per-molecule sums of
+ * each chunk's atoms in order (a molecule split across chunks adds its parts
+ * in chunk order). Arguments as qmlr_rff; d = 1..512; work: device scratch of
+ * qmlr_rff_tc_workspace_bytes(n_atoms, d, n_features, mode) bytes (the split
+ * (G/sigma), the row order and, in PER_MOL mode, one chunk of u). Deterministic;
+ * asynchronous.
+ */
+int64_t qmlr_rff_tc_workspace_bytes(int32_t n_atoms, int32_t d, int32_t n_features, int32_t mode);
+int qmlr_rff_tc(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+                const float* G, const float* b, int32_t n_features, double sigma, int32_t mode, float* out,
+                void* work, int64_t work_bytes, void* stream);
+
+/*
  * Force rows of the energy+force normal equations (RFF section: the
  * derivative features dz/dr stacked under Z): for molecule m, atom k, axis x
  *   rows[row0 + 3*(mol_ptr[m] + k) + x][f] = -dZ_m/dr_{k,x}[f]
@@ -624,6 +640,18 @@ int qmlr_model_destroy(qmlr_model* m);
 int qmlr_model_set_alpha(qmlr_model* m, const float* host_alpha);
 /* Replace alpha from a device FP64 vector [N_F] (e.g. the output of qmlr_gram_solve); asynchronous. */
 int qmlr_model_set_alpha_device(qmlr_model* m, const double* alpha, void* stream);
+
+/*
+ * Diagnostics: with timing enabled the model records CUDA events around the
+ * kernels of each prediction on the caller's stream; qmlr_model_timings waits
+ * for the last prediction and writes up to five times in ms: [0] FCHL19
+ * forward, [1] element grouping + projection, [2] SORF energies and gradient,
+ * [3] transposed projection, [4] FCHL19 adjoint with its ordered reduction
+ * (entries 3 and 4 only when forces were requested). Not for use while a
+ * prediction is being captured into a CUDA graph.
+ */
+int qmlr_model_set_timing(qmlr_model* m, int32_t enable);
+int qmlr_model_timings(qmlr_model* m, float* host_ms, int32_t n);
 
 /* Allocates (or grows) the model's prediction workspace for batches of up to max_atoms atoms. */
 int qmlr_model_reserve(qmlr_model* m, int32_t max_atoms);

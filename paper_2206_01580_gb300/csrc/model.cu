@@ -92,12 +92,16 @@ int predict_features_ws(const qmlr_model* m, PredictWorkspace& w, const float* c
   void* stream = s;
   int rc;
   const int n_el = m->p.n_el;
+  if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[0], s));
   if ((rc = qmlr_fchl19(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.rep, m->rep_ld, stream)))
     return rc;
+  if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[1], s));
   if ((rc = qmlr_group_by_element(elem, n_atoms, n_el, w.perm, w.offs, w.gwork, w.gwork_bytes, stream)))
     return rc;
-  return proj_tc_launch(w.rep, m->rep_ld, m->rep_dim, 1, 0, m->Ufwd, m->d, w.perm, w.offs, n_atoms, n_el, w.x,
-                        m->d, m->d, s);
+  rc = proj_tc_launch(w.rep, m->rep_ld, m->rep_dim, 1, 0, m->Ufwd, m->d, w.perm, w.offs, n_atoms, n_el, w.x,
+                      m->d, m->d, s);
+  if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[2], s));
+  return rc;
 }
 
 int predict_from_features_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
@@ -107,17 +111,22 @@ int predict_from_features_ws(const qmlr_model* m, PredictWorkspace& w, const flo
   int rc;
   const int n_el = m->p.n_el;
   QMLR_REQUIRE(n_mol <= w.cap_mols, "batch of %d molecules exceeds the reserved capacity %d", n_mol, w.cap_mols);
+  if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[3], s));
   if ((rc = sorf_energy_grad_model(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->bT, m->n_features,
                                    m->sigma, m->alphaT, w.atom_e, energies, forces ? w.gx : nullptr, s)))
     return rc;
+  if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[4], s));
   if (!forces) return QMLR_OK;
   if ((rc = proj_tc_launch(w.gx, m->d, m->d, m->n_part, (long)n_atoms * m->d, m->Utrn, m->rep_dim, w.perm, w.offs,
                            n_atoms, n_el, w.grep, m->rep_ld, m->rep_ld, s)))
     return rc;
+  if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[5], s));
   if ((rc = qmlr_jac_offsets(mol_ptr, n_mol, w.pair_ptr, nullptr, stream))) return rc;
   // forces F = -dE/dr: scale -1 in the ordered reduction
-  return qmlr_fchl19_vjp_atoms(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.grep,
-                               m->rep_ld, w.pair_ptr, w.contrib, -1.0f, forces, 0, stream);
+  rc = qmlr_fchl19_vjp_atoms(coords, elem, mol_ptr, n_mol, n_atoms, m->max_mol_atoms, &m->p, w.grep,
+                             m->rep_ld, w.pair_ptr, w.contrib, -1.0f, forces, 0, stream);
+  if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[6], s));
+  return rc;
 }
 
 }  // namespace qmlr
@@ -204,6 +213,8 @@ extern "C" int qmlr_model_destroy(qmlr_model* m) {
   cudaFree(m->alphaT);
   cudaFree(m->Ufwd);
   cudaFree(m->Utrn);
+  for (int k = 0; k < 8; ++k)
+    if (m->tev[k]) cudaEventDestroy(m->tev[k]);
   delete m;
   return QMLR_OK;
 }
@@ -302,5 +313,24 @@ extern "C" int qmlr_energy_vjp(const float* forces, const int32_t* mol_ptr, int3
   energy_vjp_kernel<<<(3 * n_atoms + 255) / 256, 256, 0, as_stream(stream)>>>(forces, mol_ptr, n_mol, n_atoms,
                                                                               grad_E, grad_coords);
   QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_model_set_timing(qmlr_model* m, int32_t enable) {
+  QMLR_REQUIRE(m, "model is NULL");
+  if (enable && !m->tev[0])
+    for (int k = 0; k < 8; ++k) QMLR_CUDA_TRY(cudaEventCreate(&m->tev[k]));
+  m->timing = enable != 0;
+  return QMLR_OK;
+}
+
+extern "C" int qmlr_model_timings(qmlr_model* m, float* host_ms, int32_t n) {
+  QMLR_REQUIRE(m && host_ms && n >= 0, "bad arguments");
+  QMLR_REQUIRE(m->tev[0], "timing was never enabled on this model");
+  const int pairs[5][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}};
+  for (int k = 0; k < std::min(n, 5); ++k) {
+    QMLR_CUDA_TRY(cudaEventSynchronize(m->tev[pairs[k][1]]));
+    QMLR_CUDA_TRY(cudaEventElapsedTime(&host_ms[k], m->tev[pairs[k][0]], m->tev[pairs[k][1]]));
+  }
   return QMLR_OK;
 }

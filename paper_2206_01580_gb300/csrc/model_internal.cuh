@@ -36,7 +36,7 @@ int sorf_energy_grad_model(const float* x, int d, const int32_t* mol_ptr, int n_
 // Tensor-core grouped projection (project_tc.cu).
 size_t proj_tc_basis_bytes(int n_el, int K, int N);
 int proj_tc_split_basis(const float* U, int n_el, int K, int N, long es, int ldu, bool trans, uint16_t* out,
-                        cudaStream_t s);
+                        cudaStream_t s, float scale = 1.0f);
 int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_stride, const uint16_t* basis, int N,
                    const int32_t* perm, const int32_t* elem_offsets, int n_atoms, int n_el, float* C, int ldc,
                    int zero_pad_to, cudaStream_t s);
@@ -71,4 +71,6 @@ struct qmlr_model {
   uint16_t* Ufwd = nullptr;    // U split for the tensor-core projection (bf16 [n_el][3][N_pad][K_pad])
   uint16_t* Utrn = nullptr;    // U split for the transposed projection
   qmlr::PredictWorkspace ws;   // workspace of qmlr_predict_ef
+  bool timing = false;         // record events around the prediction's kernels (diagnostics)
+  cudaEvent_t tev[8] = {};     // FCHL19 | grouping + projection | SORF | projection^T | adjoint
 };

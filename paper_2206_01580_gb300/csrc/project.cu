@@ -100,7 +100,7 @@ __global__ void group_scatter_kernel(const int32_t* __restrict__ elem, int n_ato
 // The grouped projection itself runs on the tensor cores (project_tc.cu).
 size_t proj_tc_basis_bytes(int n_el, int K, int N);
 int proj_tc_split_basis(const float* U, int n_el, int K, int N, long es, int ldu, bool trans, uint16_t* out,
-                        cudaStream_t s);
+                        cudaStream_t s, float scale = 1.0f);
 int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_stride, const uint16_t* basis, int N,
                    const int32_t* perm, const int32_t* elem_offsets, int n_atoms, int n_el, float* C, int ldc,
                    int zero_pad_to, cudaStream_t s);

@@ -481,7 +481,7 @@ proj_tc_resident_kernel(const __grid_constant__ CUtensorMap bmap, Args a) {
 // out[(e*3 + q)*N_pad + n][k] = part q of B_e[k][n] (zero outside K x N), with
 // B_e[k][n] = U[e*es + k*ldu + n] (trans = 0) or U[e*es + n*ldu + k] (trans = 1).
 __global__ void split_basis_kernel(const float* __restrict__ U, int n_el, int K, int N, long es, int ldu,
-                                   int trans, int K_pad, int N_pad, __nv_bfloat16* __restrict__ out) {
+                                   int trans, float scale, int K_pad, int N_pad, __nv_bfloat16* __restrict__ out) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long total = (long)n_el * N_pad * K_pad;
   if (idx >= total) return;
@@ -489,7 +489,7 @@ __global__ void split_basis_kernel(const float* __restrict__ U, int n_el, int K,
   const int n = (int)((idx / K_pad) % N_pad);
   const int e = (int)(idx / ((long)K_pad * N_pad));
   float v = 0.f;
-  if (k < K && n < N) v = trans ? U[e * es + (long)n * ldu + k] : U[e * es + (long)k * ldu + n];
+  if (k < K && n < N) v = scale * (trans ? U[e * es + (long)n * ldu + k] : U[e * es + (long)k * ldu + n]);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -513,12 +513,12 @@ size_t proj_tc_basis_bytes(int n_el, int K, int N) {
 }
 
 int proj_tc_split_basis(const float* U, int n_el, int K, int N, long es, int ldu, bool trans, uint16_t* out,
-                        cudaStream_t s) {
+                        cudaStream_t s, float scale) {
   int kp, np;
   proj_tc_dims(K, N, &kp, &np);
   const long total = (long)n_el * np * kp;
   tcp::split_basis_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-      U, n_el, K, N, es, ldu, trans ? 1 : 0, kp, np, reinterpret_cast<__nv_bfloat16*>(out));
+      U, n_el, K, N, es, ldu, trans ? 1 : 0, scale, kp, np, reinterpret_cast<__nv_bfloat16*>(out));
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }

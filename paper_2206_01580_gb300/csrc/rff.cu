@@ -61,7 +61,134 @@ rff_kernel(const float* __restrict__ x, int d, const int32_t* __restrict__ mol_p
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form: u = x (G / sigma)^T is a dense contraction (K = d), run by
+// the projection's tcgen05 grouped GEMM (3-way BF16 splits of both operands,
+// FP32 accumulation in TMEM, one "element" and the identity row order) into a
+// chunk of u rows; an epilogue then applies cos(u + b) and, per molecule, sums
+// the chunk's atoms in order.
+
+constexpr int kRffChunk = 65536;   // atoms per GEMM chunk (per-molecule mode)
+
+__global__ void iota_kernel(int32_t* __restrict__ v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i;
+}
+
+__global__ void offsets_kernel(int32_t* __restrict__ offs, int n) {
+  offs[0] = 0;
+  offs[1] = n;
+}
+
+// out[a][f] = pref * cos(u[a][f] + b[f]) in place
+__global__ void rff_cos_kernel(float* __restrict__ u, long n_atoms, int n_features, const float* __restrict__ b,
+                               float pref) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_atoms * n_features) return;
+  const int f = (int)(idx % n_features);
+  u[idx] = pref * cosf(u[idx] + __ldg(b + f));
+}
+
+// Z[m][f] (+)= pref * sum over the atoms a of molecule m in [c0, c1), in order,
+// of cos(u[a - c0][f] + b[f]); molecules from the first one that ends after c0.
+__global__ void rff_mol_epilogue_kernel(const float* __restrict__ u, int n_features, const float* __restrict__ b,
+                                        const int32_t* __restrict__ mol_ptr, int n_mol, int c0, int c1, float pref,
+                                        float* __restrict__ Z) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ int s_m0;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n_mol;   // first m with mol_ptr[m + 1] > c0
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(mol_ptr + mid + 1) > c0) hi = mid; else lo = mid + 1;
+    }
+    s_m0 = lo;
+  }
+  __syncthreads();
+  if (f >= n_features) return;
+  const float bf = __ldg(b + f);
+  for (int m = s_m0 + blockIdx.y; m < n_mol; m += gridDim.y) {
+    const int m_lo = __ldg(mol_ptr + m), m_hi = __ldg(mol_ptr + m + 1);
+    if (m_lo >= c1) break;
+    const int a0 = max(m_lo, c0), a1 = min(m_hi, c1);
+    if (a0 >= a1) continue;
+    float sum = 0.f;
+    for (int a = a0; a < a1; ++a) sum += cosf(u[(long)(a - c0) * n_features + f] + bf);
+    Z[(long)m * n_features + f] += pref * sum;
+  }
+}
+
 }  // namespace
+
+size_t proj_tc_basis_bytes(int n_el, int K, int N);
+int proj_tc_split_basis(const float* U, int n_el, int K, int N, long es, int ldu, bool trans, uint16_t* out,
+                        cudaStream_t s, float scale);
+int proj_tc_launch(const float* A, int lda, int K, int n_part, long a_part_stride, const uint16_t* basis, int N,
+                   const int32_t* perm, const int32_t* elem_offsets, int n_atoms, int n_el, float* C, int ldc,
+                   int zero_pad_to, cudaStream_t s);
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+extern "C" int64_t qmlr_rff_tc_workspace_bytes(int32_t n_atoms, int32_t d, int32_t n_features, int32_t mode) {
+  if (n_atoms < 0 || d < 1 || n_features < 1) return 0;
+  const int chunk = std::min(std::max(n_atoms, 1), kRffChunk);
+  size_t b = align256(proj_tc_basis_bytes(1, d, n_features)) + align256((size_t)chunk * 4) + 256;
+  if (mode == QMLR_SORF_PER_MOL) b += align256((size_t)chunk * n_features * 4);
+  return (int64_t)b + 256;
+}
+
+extern "C" int qmlr_rff_tc(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
+                           const float* G, const float* b, int32_t n_features, double sigma, int32_t mode,
+                           float* out, void* work, int64_t work_bytes, void* stream) {
+  QMLR_REQUIRE(mode == QMLR_SORF_PER_ATOM || mode == QMLR_SORF_PER_MOL,
+               "qmlr_rff_tc supports the per-atom and per-molecule modes (got %d)", mode);
+  QMLR_REQUIRE(d >= 1 && d <= 512, "d must be in 1..512 (got %d)", d);
+  QMLR_REQUIRE(n_features >= 1 && n_mol >= 0 && n_atoms >= 0, "bad sizes");
+  QMLR_REQUIRE(sigma > 0, "sigma must be positive");
+  QMLR_REQUIRE(mol_ptr && G && b && out && (n_atoms == 0 || x), "NULL pointer argument");
+  QMLR_REQUIRE(work && work_bytes >= qmlr_rff_tc_workspace_bytes(n_atoms, d, n_features, mode),
+               "workspace too small (%lld < %lld bytes)", (long long)work_bytes,
+               (long long)qmlr_rff_tc_workspace_bytes(n_atoms, d, n_features, mode));
+  cudaStream_t s = as_stream(stream);
+  const float pref = (float)std::sqrt(2.0 / n_features);
+  if (mode == QMLR_SORF_PER_MOL) QMLR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)n_mol * n_features, s));
+  if (n_atoms == 0 || n_mol == 0) return QMLR_OK;
+  const int chunk = std::min(n_atoms, kRffChunk);
+  char* w = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
+  uint16_t* basis = reinterpret_cast<uint16_t*>(w);
+  w += align256(proj_tc_basis_bytes(1, d, n_features));
+  int32_t* perm = reinterpret_cast<int32_t*>(w);
+  w += align256((size_t)chunk * 4);
+  int32_t* offs = reinterpret_cast<int32_t*>(w);
+  w += 256;
+  float* u = reinterpret_cast<float*>(w);
+  int rc = proj_tc_split_basis(G, 1, d, n_features, 0, d, true, basis, s, (float)(1.0 / sigma));
+  if (rc) return rc;
+  iota_kernel<<<(chunk + 255) / 256, 256, 0, s>>>(perm, chunk);
+  QMLR_LAUNCH_CHECK();
+  for (int c0 = 0; c0 < n_atoms; c0 += chunk) {
+    const int nc = std::min(chunk, n_atoms - c0);
+    offsets_kernel<<<1, 1, 0, s>>>(offs, nc);   // stream order keeps the previous chunk's value until it is used
+    QMLR_LAUNCH_CHECK();
+    if (mode == QMLR_SORF_PER_ATOM) {
+      float* uo = out + (size_t)c0 * n_features;
+      rc = proj_tc_launch(x + (size_t)c0 * d, d, d, 1, 0, basis, n_features, perm, offs, nc, 1, uo, n_features,
+                          n_features, s);
+      if (rc) return rc;
+      const long tot = (long)nc * n_features;
+      rff_cos_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(uo, nc, n_features, b, pref);
+      QMLR_LAUNCH_CHECK();
+    } else {
+      rc = proj_tc_launch(x + (size_t)c0 * d, d, d, 1, 0, basis, n_features, perm, offs, nc, 1, u, n_features,
+                          n_features, s);
+      if (rc) return rc;
+      dim3 grid((n_features + 255) / 256, std::min(nc + 1, 4096));
+      rff_mol_epilogue_kernel<<<grid, 256, 0, s>>>(u, n_features, b, mol_ptr, n_mol, c0, c0 + nc, pref, out);
+      QMLR_LAUNCH_CHECK();
+    }
+  }
+  return QMLR_OK;
+}
 
 extern "C" int qmlr_rff(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol, int32_t n_atoms,
                         const float* G, const float* b, int32_t n_features, double sigma, int32_t mode,

@@ -98,6 +98,8 @@ _SIGS = {
     "qmlr_fchl19_periodic_vjp": (C.c_int, [P, P, I32, P, P, P, P, I32, C.POINTER(_Params), P, I32, P, P, P,
                                            C.c_float, P, I32, VP]),
     "qmlr_rff": (C.c_int, [P, I32, P, I32, I32, P, P, I32, D, I32, P, VP]),
+    "qmlr_rff_tc_workspace_bytes": (C.c_int64, [I32, I32, I32, I32]),
+    "qmlr_rff_tc": (C.c_int, [P, I32, P, I32, I32, P, P, I32, D, I32, P, P, I64, VP]),
     "qmlr_sorf_parts": (C.c_int32, [I32, I32]),
     "qmlr_sorf_grad": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, VP]),
     "qmlr_gram_operand": (C.c_int, [P, I64, I32, I64, I32, P, I64, VP]),
@@ -122,6 +124,8 @@ _SIGS = {
     "qmlr_model_set_alpha": (C.c_int, [VP, P]),
     "qmlr_model_set_alpha_device": (C.c_int, [VP, P, VP]),
     "qmlr_model_reserve": (C.c_int, [VP, I32]),
+    "qmlr_model_set_timing": (C.c_int, [VP, I32]),
+    "qmlr_model_timings": (C.c_int, [VP, P, I32]),
     "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
     "qmlr_energy_vjp": (C.c_int, [P, P, I32, I32, P, P, VP]),
     "qmlr_unit_rates": (C.c_int, [P, I32, VP]),
@@ -469,6 +473,24 @@ def rff(x, mol_ptr, G, b, sigma: float, mode: int):
     return out
 
 
+def rff_tc(x, mol_ptr, G, b, sigma: float, mode: int):
+    """Dense RFF features on the tensor cores (same result form as rff)."""
+    x = _dev(x, torch.float32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    G = _dev(G, torch.float32)
+    b = _dev(b, torch.float32)
+    n_atoms, d = x.shape
+    n_mol = mol_ptr.shape[0] - 1
+    nf = b.shape[0]
+    rows = n_atoms if mode == SORF_PER_ATOM else n_mol
+    out = torch.empty((rows, nf), device="cuda", dtype=torch.float32)
+    wb = lib().qmlr_rff_tc_workspace_bytes(n_atoms, d, nf, mode)
+    work = torch.empty(wb, device="cuda", dtype=torch.uint8)
+    _check(lib().qmlr_rff_tc(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(G), _ptr(b), nf, float(sigma), mode,
+                             _ptr(out), _ptr(work), wb, _stream()))
+    return out
+
+
 def sorf_parts(n_features: int, d: int) -> int:
     return lib().qmlr_sorf_parts(n_features, d)
 
@@ -695,6 +717,18 @@ class Model:
 
     def set_alpha_device(self, alpha64: torch.Tensor):
         _check(lib().qmlr_model_set_alpha_device(self.handle, _ptr(alpha64), _stream()))
+
+    TIMINGS = ("fchl19", "group_project", "sorf_energy_grad", "project_t", "fchl19_vjp")
+
+    def set_timing(self, enable: bool = True):
+        """Record CUDA events around the prediction's kernels (diagnostics)."""
+        _check(lib().qmlr_model_set_timing(self.handle, int(enable)))
+
+    def timings(self) -> dict:
+        """ms of the last prediction's kernels (waits for them)."""
+        out = (C.c_float * 5)()
+        _check(lib().qmlr_model_timings(self.handle, out, 5))
+        return dict(zip(self.TIMINGS, list(out)))
 
     def reserve(self, n_atoms: int):
         if n_atoms > self.capacity:

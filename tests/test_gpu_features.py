@@ -235,3 +235,35 @@ def test_sorf_energy_and_gradient_match_oracle(q, d, nf, T):
     assert np.all(np.abs(E2 - Eref) <= 1e-4 * np.maximum(sizes, 1))
     scale = np.max(np.abs(gref.numpy()))
     assert np.max(np.abs(gx - gref.numpy())) <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("d,nf,n_mol", [(16, 64, 9), (64, 512, 9), (128, 1000, 9), (128, 4096, 9),
+                                        (200, 300, 9), (256, 129, 9), (16, 64, 10001)])
+def test_rff_tensor_core_matches_oracle(q, d, nf, n_mol):
+    """Dense RFF on the tensor cores (split-BF16 GEMM, FP32 accumulation)
+    against the FP64 oracle; the last case has 70 000 atoms, so the GEMM runs
+    in two chunks and molecules straddle the chunk boundary. Bound: four times
+    the FP32 dot-product bound of the SIMT form (the split products and the
+    accumulator's adds), plus the phase add and cosf."""
+    rng = np.random.default_rng(43 + d + n_mol)
+    sizes = rng.integers(1, 12, size=n_mol) if n_mol < 100 else np.full(n_mol, 7)
+    sizes[2] = 0
+    mol_ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    x = (rng.normal(size=(int(mol_ptr[-1]), d)) * 0.5).astype(np.float32)
+    G, b = synth.rff_draw(rng, nf, d)
+    G, b = G.astype(np.float32), b.astype(np.float32)
+    sigma = 1.7
+    xd, Gd, bd = x.astype(np.float64), G.astype(np.float64), b.astype(np.float64)
+    ref = o_sorf.features(xd, o_sorf.rff_matrix(Gd, sigma), bd)
+    pref = math.sqrt(2 / nf)
+    u = xd @ Gd.T / sigma + bd
+    bound = pref * (4 * d * 2.0 ** -24 * (np.abs(xd) @ np.abs(Gd).T) / sigma + 2.0 ** -23 * np.abs(u) + 1e-6)
+    z = q.rff_tc(x, mol_ptr, G, b, sigma, q.SORF_PER_ATOM).cpu().numpy()
+    assert q.device_status() == 0
+    assert np.all(np.abs(z - ref) <= bound), np.max(np.abs(z - ref) / bound)
+    Z = q.rff_tc(x, mol_ptr, G, b, sigma, q.SORF_PER_MOL).cpu().numpy()
+    Zref = o_reg.segment_sum(ref, mol_ptr)
+    Zbound = o_reg.segment_sum(bound, mol_ptr) + pref * 2.0 ** -22 * (sizes[:, None] + 1) ** 2
+    assert np.all(np.abs(Z - Zref) <= Zbound), np.max(np.abs(Z - Zref) / Zbound)
+    assert np.all(Z[sizes == 0] == 0)
+    assert np.array_equal(Z, q.rff_tc(x, mol_ptr, G, b, sigma, q.SORF_PER_MOL).cpu().numpy())
