@@ -231,6 +231,28 @@ def oracle_parity_workload_full():
             "predict_ef_us_per_atom": (t2 - t1) / mols.n_atoms * 1e6, "cores": os.cpu_count() or 1}
 
 
+def fchl19_exps_per_atom(w, frac: float = 0.02) -> float:
+    """Radial-grid exponentials per atom of FCHL19 on the workload: n2 per
+    neighbour within r_cut and n3 per pair of neighbours whose distance is also
+    within r_cut (counted on the first `frac` of the molecules)."""
+    mols = w.mols
+    rc = 6.0
+    n_mol = max(1, int(frac * mols.n_mol))
+    tot = 0
+    n_at = 0
+    for k in range(n_mol):
+        a, b = int(mols.mol_ptr[k]), int(mols.mol_ptr[k + 1])
+        x = mols.coords[a:b]
+        d = np.sqrt(((x[:, None, :] - x[None, :, :]) ** 2).sum(-1))
+        inside = d < rc
+        np.fill_diagonal(inside, False)
+        for i in range(b - a):
+            nb = np.nonzero(inside[i])[0]
+            tot += len(nb) * w.n2 + int(np.triu(inside[np.ix_(nb, nb)], 1).sum()) * w.n3
+        n_at += b - a
+    return tot / max(n_at, 1)
+
+
 def workload_config(args, w, world, gram_text, solve_text):
     """The config object of the bench line (the same keys in both arms)."""
     return {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
@@ -542,6 +564,7 @@ def run_ours(args, rank, world):
     model = qmlr.Model(p, batch.max_atoms, U, w.signs, w.n_transform, w.b, w.sigma,
                        np.zeros(w.n_features, np.float32))
     model.reserve(n_atoms)
+    model.set_timing(True)          # CUDA events around the prediction's kernels (read per timed step)
     del rep, perm, offs
     torch.cuda.synchronize()
 
@@ -591,7 +614,10 @@ def run_ours(args, rank, world):
         if timing is not None:
             torch.cuda.synchronize()
             so = qmlr.last_solve
-            timing.append({"fchl19": ev[0].elapsed_time(ev[1]), "project": ev[1].elapsed_time(ev[2]),
+            mt = model.timings()
+            timing.append({"sorf_atom": mt["sorf_energy_grad"], "fchl19_vjp": mt["fchl19_vjp"],
+                           "project_t": mt["project_t"],
+                           "fchl19": ev[0].elapsed_time(ev[1]), "project": ev[1].elapsed_time(ev[2]),
                            "sorf_Z": ev[2].elapsed_time(ev[3]), "gram_operand": ev[3].elapsed_time(ev[7]),
                            "gram": ev[7].elapsed_time(ev[4]),
                            "solve": ev[4].elapsed_time(ev[5]), "factor": so.factor_ms,
@@ -694,6 +720,13 @@ def run_ours(args, rank, world):
         fadd_measured = None
     n_stack = nf // w.d
     sorf_ops_atom = n_stack * w.n_transform * w.d * int(math.log2(w.d)) + 6 * nf
+    butterflies = n_stack * w.n_transform * w.d * int(math.log2(w.d))
+    sorf_atom_ops = 2 * butterflies + 4 * nf
+    try:
+        exp_rate = qmlr.unit_rates()["expf"] / 1e12
+    except Exception:   # diagnostics only
+        exp_rate = None
+    exps_atom = fchl19_exps_per_atom(w)
     cands = {
         "gram": {"kernel": gdesc["kernel"],
                  "bound": "tensor",
@@ -712,11 +745,39 @@ def run_ours(args, rank, world):
                            "for phase, cos, sum)",
                    "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
                                   f"(measured FP32 add rate {fadd_measured} T/s, qmlr_unit_rates)"},
+        "sorf_atom": {"kernel": "qmlr::sorf_atom_kernel<128, 1> (SORF energies + gradient, prediction)",
+                      "bound": "alu",
+                      "achieved": sorf_atom_ops * n_atoms / (st["sorf_atom"] * 1e-3) / 1e12, "peak": fp32_add_peak,
+                      "unit": "TFLOP/s",
+                      "work": f"{sorf_atom_ops} FP32 ops/atom (forward and transposed butterflies "
+                              f"2*n_stack*T*d*log2 d = {2 * butterflies}, plus 4*N_F for phase, energy and gradient "
+                              "scaling; sign flips and sin/cos not counted)",
+                      "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz",
+                      "timing": "CUDA events of the model's prediction in every timed step"},
+        "fchl19_fwd": {"kernel": "qmlr::fchl19_forward_reg_kernel (FCHL19 forward, training pass)",
+                       "bound": "alu",
+                       "achieved": exps_atom * n_atoms / (st["fchl19"] * 1e-3) / 1e12,
+                       "peak": exp_rate, "unit": "T exp/s",
+                       "work": f"{exps_atom:.0f} radial-grid exponentials per atom (n*n2 two-body + in-cutoff "
+                               "triplets*n3, counted on a 2 % sample of the workload)",
+                       "peak_source": "measured __expf rate (MUFU), qmlr_unit_rates"},
+        "fchl19_vjp": {"kernel": "qmlr::fchl19_vjp_centre_kernel + vjp_reduce_kernel (FCHL19 adjoint, prediction)",
+                       "bound": "alu",
+                       "achieved": exps_atom * n_atoms / (st["fchl19_vjp"] * 1e-3) / 1e12,
+                       "peak": exp_rate, "unit": "T exp/s",
+                       "work": f"{exps_atom:.0f} radial-grid exponentials per atom (as the forward; the "
+                               "derivative arithmetic not counted)",
+                       "peak_source": "measured __expf rate (MUFU), qmlr_unit_rates",
+                       "timing": "CUDA events of the model's prediction in every timed step"},
     }
     for c in cands.values():
-        c["frac"] = c["achieved"] / c["peak"]
+        c["frac"] = c["achieved"] / c["peak"] if c["peak"] else None
         c["traffic"] = None
-    dom = max(cands, key=lambda k: st[k])
+    stage_of = {"gram": "gram", "sorf_Z": "sorf_Z", "sorf_atom": "sorf_atom", "fchl19_fwd": "fchl19",
+                "fchl19_vjp": "fchl19_vjp"}
+    for k, c in cands.items():
+        c["ms"] = st[stage_of[k]]
+    dom = max(cands, key=lambda k: st[stage_of[k]])
     roof = dict(cands[dom])
     tr = measured_traffic(dom, roof["kernel"])
     if tr is not None:
