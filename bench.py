@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-ef", action="store_true")
     ap.add_argument("--no-periodic", action="store_true")
+    ap.add_argument("--sorf-kernel", default="tc", choices=["tc", "fwht"],
+                    help="SORF energies + gradients of the prediction: both Hadamard chains as tensor-core "
+                         "FP16 products (tc) or the in-register fast Walsh-Hadamard kernel (fwht)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--pcg-iters", type=int, default=30)
     ap.add_argument("--pcg-tol", type=float, default=1e-8)
@@ -258,6 +261,9 @@ def workload_config(args, w, world, gram_text, solve_text):
     return {"workload": "qm9-shaped-100k" if args.scale == 1.0 else f"qm9-shaped x{args.scale}",
             "n_molecules": w.mols.n_mol, "n_atoms": w.mols.n_atoms, "n_features": w.n_features, "d": w.d,
             "n_transform": w.n_transform, "gram": gram_text, "solve": solve_text,
+            "sorf_prediction": ("both Hadamard chains as tcgen05 FP16 products (exact FP16 chain tables, "
+                                "two-part operands)" if args.sorf_kernel == "tc"
+                                else "in-register fast Walsh-Hadamard transform (FP32)"),
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "inputs larger than L2 (rep 5.5 GB, Z 6.6 GB)",
             "step": "one training (FCHL19 -> projection -> SORF -> Z -> Gram -> factor + PCG) plus E+F "
@@ -565,6 +571,9 @@ def run_ours(args, rank, world):
                        np.zeros(w.n_features, np.float32))
     model.reserve(n_atoms)
     model.set_timing(True)          # CUDA events around the prediction's kernels (read per timed step)
+    if args.sorf_kernel == "fwht" and model.sorf_tc:
+        model.set_sorf_tc(False)
+    sorf_tc = model.sorf_tc
     del rep, perm, offs
     torch.cuda.synchronize()
 
@@ -745,15 +754,34 @@ def run_ours(args, rank, world):
                            "for phase, cos, sum)",
                    "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
                                   f"(measured FP32 add rate {fadd_measured} T/s, qmlr_unit_rates)"},
-        "sorf_atom": {"kernel": "qmlr::sorf_atom_kernel<128, 1> (SORF energies + gradient, prediction)",
-                      "bound": "alu",
-                      "achieved": sorf_atom_ops * n_atoms / (st["sorf_atom"] * 1e-3) / 1e12, "peak": fp32_add_peak,
-                      "unit": "TFLOP/s",
-                      "work": f"{sorf_atom_ops} FP32 ops/atom (forward and transposed butterflies "
-                              f"2*n_stack*T*d*log2 d = {2 * butterflies}, plus 4*N_F for phase, energy and gradient "
-                              "scaling; sign flips and sin/cos not counted)",
-                      "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz",
-                      "timing": "CUDA events of the model's prediction in every timed step"},
+        "sorf_atom": ({"kernel": "qmlr::stc::sorf_tc_kernel (SORF energies + gradient, both Hadamard chains "
+                                 "as tcgen05 FP16 products, prediction)",
+                       "bound": "tensor",
+                       "achieved": 4 * w.d * nf * n_atoms / (st["sorf_atom"] * 1e-3) / 1e12,
+                       "peak": bf16_sust / 2,
+                       "unit": "TFLOP/s",
+                       "work": f"2 directions x 2*d*N_F = {4 * w.d * nf} flop/atom (dense chain products "
+                               "x M_s^T and y M_s)",
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained / 2 (two FP16 products per "
+                                      "dense product: two-part operands, exact FP16 chain tables; FP16 at the "
+                                      "BF16 rate)",
+                       "mufu": {"achieved": 2 * nf * n_atoms / (st["sorf_atom"] * 1e-3) / 1e12,
+                                "peak": exp_rate, "unit": "T op/s",
+                                "work": "sin and cos per feature (2*N_F per atom)",
+                                "peak_source": "measured __expf rate (MUFU), qmlr_unit_rates"},
+                       "timing": "CUDA events of the model's prediction in every timed step (x split, "
+                                 "tensor-core kernel, molecule sums)"}
+                      if sorf_tc else
+                      {"kernel": "qmlr::sorf_atom_kernel<128, 1> (SORF energies + gradient, prediction)",
+                       "bound": "alu",
+                       "achieved": sorf_atom_ops * n_atoms / (st["sorf_atom"] * 1e-3) / 1e12,
+                       "peak": fp32_add_peak,
+                       "unit": "TFLOP/s",
+                       "work": f"{sorf_atom_ops} FP32 ops/atom (forward and transposed butterflies "
+                               f"2*n_stack*T*d*log2 d = {2 * butterflies}, plus 4*N_F for phase, energy and "
+                               "gradient scaling; sign flips and sin/cos not counted)",
+                       "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz",
+                       "timing": "CUDA events of the model's prediction in every timed step"}),
         "fchl19_fwd": {"kernel": "qmlr::fchl19_forward_reg_kernel (FCHL19 forward, training pass)",
                        "bound": "alu",
                        "achieved": exps_atom * n_atoms / (st["fchl19"] * 1e-3) / 1e12,

@@ -395,6 +395,44 @@ int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_
                    int32_t n_features, double sigma, const float* alpha, double* atom_energy,
                    double* energies, float* gx, void* stream);
 
+/*
+ * The same energies and gradients with both Hadamard chains on the tensor
+ * cores (SORF section: u_s = c M_s x + b_s with M_s = H D_T ... H D_1 and
+ * c = (sqrt(d)/sigma) / d^{T/2}; gradient -sqrt(2/N_F) c sum_s M_s^T
+ * (alpha_s * sin u_s)). For d = 128 and T <= 3 the entries of M_s are integers
+ * of magnitude <= d^{T/2} (<= 1448), exact in FP16, so M_s is stored as FP16
+ * tables and both directions are tcgen05 products (kind::f16, FP32
+ * accumulation): x is split per atom into two FP16 parts after a power-of-two
+ * row scale (2^-22 relative per element), the backward operand
+ * alpha * sin(u) likewise with one power-of-two scale for all features; the
+ * backward accumulator is promoted into FP32 sums every 8 half stacks.
+ * Phases use the same reduction and range check as qmlr_sorf (device error 6).
+ *
+ *   qmlr_sorf_tc_table_bytes(N_F)   bytes of the chain tables (4 N_F d bytes)
+ *   qmlr_sorf_tc_tables             fills them from the packed signs (device
+ *                                   tables, 16-byte aligned; caller-owned;
+ *                                   build once per set of signs)
+ *   qmlr_sorf_tc_workspace_bytes(n) bytes of the per-call workspace
+ *                                   (~516 B per atom; 256-byte aligned)
+ *   qmlr_sorf_grad_tc               atom_energy double [n_atoms] (one part),
+ *                                   energies double [n_mol], gx float
+ *                                   [n_atoms][128] (one part: pass n_part = 1
+ *                                   to qmlr_project_t); x, b, alpha, gx 16-byte
+ *                                   aligned; gx is required.
+ * Errors: QMLR_EINVAL for d != 128, T > 3, N_F not a multiple of 128, NULL or
+ * misaligned pointers, a workspace below the required size. Asynchronous on
+ * `stream`; deterministic; allocates nothing; a persistent kernel of one CTA
+ * per SM whose waits are bounded (device error 4, a timeout, on expiry).
+ */
+int64_t qmlr_sorf_tc_table_bytes(int32_t n_features);
+int64_t qmlr_sorf_tc_workspace_bytes(int32_t n_atoms);
+int qmlr_sorf_tc_tables(const uint32_t* sign_bits, int32_t d, int32_t T, int32_t n_features,
+                        void* tables, void* stream);
+int qmlr_sorf_grad_tc(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
+                      int32_t n_atoms, const void* tables, int32_t T, const float* b,
+                      int32_t n_features, double sigma, const float* alpha, double* atom_energy,
+                      double* energies, float* gx, void* work, int64_t work_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * Regularised normal equations (RFF section: (Z^T Z + lambda I) alpha = Z^T E,
  * energy and force rows stacked for energy+force training; the paper solves
@@ -650,6 +688,16 @@ int qmlr_model_set_alpha_device(qmlr_model* m, const double* alpha, void* stream
  * (entries 3 and 4 only when forces were requested). Not for use while a
  * prediction is being captured into a CUDA graph.
  */
+/*
+ * Which kernel computes the SORF energies and gradients of qmlr_predict_ef
+ * with forces: the tensor-core chains (qmlr_sorf_grad_tc; the default when
+ * the model has d = 128 and T <= 3, tables built at model creation) or the
+ * FWHT kernel of qmlr_sorf_grad (enable = 0). Enabling it on a model without
+ * tables returns QMLR_EINVAL. Energy-only predictions use the FWHT kernel.
+ */
+int qmlr_model_set_sorf_tc(qmlr_model* m, int32_t enable);
+int32_t qmlr_model_sorf_tc(const qmlr_model* m);
+
 int qmlr_model_set_timing(qmlr_model* m, int32_t enable);
 int qmlr_model_timings(qmlr_model* m, float* host_ms, int32_t n);
 

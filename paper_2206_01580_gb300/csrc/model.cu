@@ -33,6 +33,9 @@ void PredictWorkspace::release() {
   cudaFree(perm);
   cudaFree(offs);
   cudaFree(gwork);
+  cudaFree(sorf_work);
+  sorf_work = nullptr;
+  sorf_work_bytes = 0;
   rep = x = gx = grep = nullptr;
   perm = offs = nullptr;
   gwork = nullptr;
@@ -54,6 +57,10 @@ int PredictWorkspace::reserve(const qmlr_model* m, int max_atoms) {
   if (e == cudaSuccess) e = cudaMalloc(&atom_e, (size_t)m->n_part * n * 8);
   if (e == cudaSuccess) e = cudaMalloc(&pair_ptr, (n + 4096 + 1) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&contrib, n * (size_t)m->max_mol_atoms * 3 * 4);
+  if (e == cudaSuccess && m->sorf_tables) {
+    sorf_work_bytes = sorf_tc_work_bytes((int)n);
+    e = cudaMalloc(&sorf_work, sorf_work_bytes);
+  }
   if (e != cudaSuccess) {
     release();
     set_error("workspace allocation failed: %s", cudaGetErrorString(e));
@@ -66,7 +73,7 @@ int PredictWorkspace::reserve(const qmlr_model* m, int max_atoms) {
 
 size_t PredictWorkspace::bytes_per_atom(const qmlr_model* m) {
   return (size_t)m->rep_ld * 8 + (size_t)m->d * 4 * (1 + m->n_part) + 4 + 64 + 8 * m->n_part + 8 +
-         (size_t)m->max_mol_atoms * 12;
+         (size_t)m->max_mol_atoms * 12 + (m->sorf_tables ? (size_t)m->d * 4 + 4 : 0);
 }
 
 int predict_ef_ws(const qmlr_model* m, PredictWorkspace& w, const float* coords, const int32_t* elem,
@@ -112,12 +119,22 @@ int predict_from_features_ws(const qmlr_model* m, PredictWorkspace& w, const flo
   const int n_el = m->p.n_el;
   QMLR_REQUIRE(n_mol <= w.cap_mols, "batch of %d molecules exceeds the reserved capacity %d", n_mol, w.cap_mols);
   if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[3], s));
-  if ((rc = sorf_energy_grad_model(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->bT, m->n_features,
-                                   m->sigma, m->alphaT, w.atom_e, energies, forces ? w.gx : nullptr, s)))
+  // gradient partials: one per 128-stack part of the FWHT kernel, one of the tensor-core kernel
+  int g_parts = m->n_part;
+  if (forces && m->sorf_tc) {
+    if ((rc = sorf_tc_energy_grad(w.x, n_atoms, m->sorf_tables, m->T, m->b, m->alpha, m->n_features, m->sigma,
+                                  w.atom_e, w.gx, w.sorf_work, w.sorf_work_bytes, s)))
+      return rc;
+    if ((rc = sorf_segment_energy(w.atom_e, 1, n_atoms, mol_ptr, n_mol, energies, s))) return rc;
+    g_parts = 1;
+  } else if ((rc = sorf_energy_grad_model(w.x, m->d, mol_ptr, n_mol, n_atoms, m->signs, m->T, m->bT,
+                                          m->n_features, m->sigma, m->alphaT, w.atom_e, energies,
+                                          forces ? w.gx : nullptr, s))) {
     return rc;
+  }
   if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[4], s));
   if (!forces) return QMLR_OK;
-  if ((rc = proj_tc_launch(w.gx, m->d, m->d, m->n_part, (long)n_atoms * m->d, m->Utrn, m->rep_dim, w.perm, w.offs,
+  if ((rc = proj_tc_launch(w.gx, m->d, m->d, g_parts, (long)n_atoms * m->d, m->Utrn, m->rep_dim, w.perm, w.offs,
                            n_atoms, n_el, w.grep, m->rep_ld, m->rep_ld, s)))
     return rc;
   if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[5], s));
@@ -188,7 +205,17 @@ extern "C" int qmlr_model_create(const qmlr_fchl19_params* p, int32_t max_mol_at
     qmlr_model_destroy(m);
     return e == cudaErrorMemoryAllocation ? QMLR_ENOMEM : QMLR_ECUDA;
   }
-  rc = proj_tc_split_basis(m->U, p->n_el, m->rep_dim, d, (long)m->rep_dim * d, d, false, m->Ufwd, 0);
+  if (e == cudaSuccess && sorf_tc_supported(d, T, n_features)) {
+    e = cudaMalloc(&m->sorf_tables, sorf_tc_table_bytes(n_features));
+    m->sorf_tc = e == cudaSuccess;
+  }
+  if (e != cudaSuccess) {
+    set_error("model allocation failed: %s", cudaGetErrorString(e));
+    qmlr_model_destroy(m);
+    return e == cudaErrorMemoryAllocation ? QMLR_ENOMEM : QMLR_ECUDA;
+  }
+  rc = m->sorf_tables ? sorf_tc_tables(m->signs, T, n_features, m->sorf_tables, 0) : QMLR_OK;
+  if (rc == QMLR_OK) rc = proj_tc_split_basis(m->U, p->n_el, m->rep_dim, d, (long)m->rep_dim * d, d, false, m->Ufwd, 0);
   if (rc == QMLR_OK) rc = proj_tc_split_basis(m->U, p->n_el, d, m->rep_dim, (long)m->rep_dim * d, d, true, m->Utrn, 0);
   if (rc == QMLR_OK && cudaStreamSynchronize(0) != cudaSuccess) {
     set_error("splitting the model basis failed");
@@ -213,6 +240,7 @@ extern "C" int qmlr_model_destroy(qmlr_model* m) {
   cudaFree(m->alphaT);
   cudaFree(m->Ufwd);
   cudaFree(m->Utrn);
+  cudaFree(m->sorf_tables);
   for (int k = 0; k < 8; ++k)
     if (m->tev[k]) cudaEventDestroy(m->tev[k]);
   delete m;
@@ -315,6 +343,16 @@ extern "C" int qmlr_energy_vjp(const float* forces, const int32_t* mol_ptr, int3
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }
+
+extern "C" int qmlr_model_set_sorf_tc(qmlr_model* m, int32_t enable) {
+  QMLR_REQUIRE(m, "model is NULL");
+  QMLR_REQUIRE(!enable || m->sorf_tables,
+               "the tensor-core SORF kernel needs d = 128 and T <= 3 (this model: d = %d, T = %d)", m->d, m->T);
+  m->sorf_tc = enable != 0;
+  return QMLR_OK;
+}
+
+extern "C" int32_t qmlr_model_sorf_tc(const qmlr_model* m) { return m && m->sorf_tc ? 1 : 0; }
 
 extern "C" int qmlr_model_set_timing(qmlr_model* m, int32_t enable) {
   QMLR_REQUIRE(m, "model is NULL");

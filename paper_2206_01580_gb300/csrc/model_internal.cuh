@@ -22,6 +22,8 @@ struct PredictWorkspace {
   int64_t* pair_ptr = nullptr;// [cap_mols + 1] offsets of the per-centre force contributions
   float* contrib = nullptr;   // [cap * max_mol_atoms * 3]
   int cap_mols = 0;
+  void* sorf_work = nullptr;  // tensor-core SORF: FP16 parts of x and row scales
+  size_t sorf_work_bytes = 0;
 
   int reserve(const qmlr_model* m, int max_atoms);
   void release();
@@ -32,6 +34,19 @@ struct PredictWorkspace {
 int sorf_energy_grad_model(const float* x, int d, const int32_t* mol_ptr, int n_mol, int n_atoms,
                            const uint32_t* sign_bits, int T, const float* bT, int n_features, double sigma,
                            const float* alphaT, double* atom_e, double* E, float* gx, cudaStream_t s);
+
+// Tensor-core SORF energies and gradients (sorf_tc.cu): chain tables
+// [2][N_F][128] FP16, per-call workspace of FP16 parts of x and row scales.
+size_t sorf_tc_table_bytes(int n_features);
+size_t sorf_tc_work_bytes(int n_atoms);
+bool sorf_tc_supported(int d, int T, int n_features);
+int sorf_tc_tables(const uint32_t* sign_bits, int T, int n_features, void* tables, cudaStream_t s);
+int sorf_tc_energy_grad(const float* x, int n_atoms, const void* tables, int T, const float* b,
+                        const float* alpha, int n_features, double sigma, double* atom_e, float* gx, void* work,
+                        size_t work_bytes, cudaStream_t s);
+// E[m] = sum over the molecule's atoms and the n_part partials (sorf.cu).
+int sorf_segment_energy(const double* atom_e, int n_part, int n_atoms, const int32_t* mol_ptr, int n_mol,
+                        double* E, cudaStream_t s);
 
 // Tensor-core grouped projection (project_tc.cu).
 size_t proj_tc_basis_bytes(int n_el, int K, int N);
@@ -71,6 +86,8 @@ struct qmlr_model {
   uint16_t* Ufwd = nullptr;    // U split for the tensor-core projection (bf16 [n_el][3][N_pad][K_pad])
   uint16_t* Utrn = nullptr;    // U split for the transposed projection
   qmlr::PredictWorkspace ws;   // workspace of qmlr_predict_ef
+  void* sorf_tables = nullptr;  // chain tables of the tensor-core SORF (d = 128, T <= 3)
+  bool sorf_tc = false;        // energies + gradients on the tensor cores (else the FWHT kernel)
   bool timing = false;         // record events around the prediction's kernels (diagnostics)
   cudaEvent_t tev[8] = {};     // FCHL19 | grouping + projection | SORF | projection^T | adjoint
 };

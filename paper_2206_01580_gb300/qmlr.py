@@ -126,6 +126,12 @@ _SIGS = {
     "qmlr_model_reserve": (C.c_int, [VP, I32]),
     "qmlr_model_set_timing": (C.c_int, [VP, I32]),
     "qmlr_model_timings": (C.c_int, [VP, P, I32]),
+    "qmlr_model_set_sorf_tc": (C.c_int, [VP, I32]),
+    "qmlr_model_sorf_tc": (I32, [VP]),
+    "qmlr_sorf_tc_table_bytes": (I64, [I32]),
+    "qmlr_sorf_tc_workspace_bytes": (I64, [I32]),
+    "qmlr_sorf_tc_tables": (C.c_int, [P, I32, I32, I32, P, VP]),
+    "qmlr_sorf_grad_tc": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, P, I64, VP]),
     "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
     "qmlr_energy_vjp": (C.c_int, [P, P, I32, I32, P, P, VP]),
     "qmlr_unit_rates": (C.c_int, [P, I32, VP]),
@@ -513,6 +519,35 @@ def sorf_grad(x, mol_ptr, sign_bits, T: int, b, sigma: float, alpha):
     return E, gx
 
 
+def sorf_tc_tables(sign_bits, T: int, n_features: int, d: int = 128):
+    """FP16 chain tables of the tensor-core SORF ([2, N_F, 128] as int16 bits)."""
+    nbytes = lib().qmlr_sorf_tc_table_bytes(n_features)
+    tables = torch.empty((nbytes // 2,), device="cuda", dtype=torch.int16)
+    _check(lib().qmlr_sorf_tc_tables(_ptr(sign_bits), d, T, n_features, _ptr(tables), _stream()))
+    return tables
+
+
+def sorf_grad_tc(x, mol_ptr, tables, T: int, b, sigma: float, alpha):
+    """Energies [n_mol] and gradients [1, n_atoms, d] from the tensor-core chains."""
+    x = _dev(x, torch.float32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    b = _dev(b, torch.float32)
+    alpha = _dev(alpha, torch.float32)
+    n_atoms, d = x.shape
+    n_mol = mol_ptr.shape[0] - 1
+    nf = b.shape[0]
+    E = torch.empty((n_mol,), device="cuda", dtype=torch.float64)
+    gx = torch.empty((1, n_atoms, d), device="cuda", dtype=torch.float32)
+    atom_e = torch.empty((max(n_atoms, 1),), device="cuda", dtype=torch.float64)
+    wb = lib().qmlr_sorf_tc_workspace_bytes(n_atoms)
+    work = torch.empty((wb + 256,), device="cuda", dtype=torch.uint8)
+    off = (-work.data_ptr()) % 256
+    _check(lib().qmlr_sorf_grad_tc(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(tables), T, _ptr(b), nf,
+                                   float(sigma), _ptr(alpha), _ptr(atom_e), _ptr(E), _ptr(gx),
+                                   work.data_ptr() + off, wb, _stream()))
+    return E, gx
+
+
 # ----------------------------------------------------------------------------
 # normal equations
 
@@ -719,6 +754,14 @@ class Model:
         _check(lib().qmlr_model_set_alpha_device(self.handle, _ptr(alpha64), _stream()))
 
     TIMINGS = ("fchl19", "group_project", "sorf_energy_grad", "project_t", "fchl19_vjp")
+
+    def set_sorf_tc(self, enable: bool = True):
+        """SORF energies + gradients of E+F predictions on the tensor cores (else the FWHT kernel)."""
+        _check(lib().qmlr_model_set_sorf_tc(self.handle, int(enable)))
+
+    @property
+    def sorf_tc(self) -> bool:
+        return bool(lib().qmlr_model_sorf_tc(self.handle))
 
     def set_timing(self, enable: bool = True):
         """Record CUDA events around the prediction's kernels (diagnostics)."""

@@ -237,6 +237,68 @@ def test_sorf_energy_and_gradient_match_oracle(q, d, nf, T):
     assert np.max(np.abs(gx - gref.numpy())) <= 1e-4 * scale
 
 
+SORF_TC_CASES = [(128, 1, 10), (384, 3, 60), (1024, 2, 60), (16384, 3, 60), (32768, 2, 10), (512, 3, 2000)]
+
+
+@pytest.mark.parametrize("nf,T,n_mol", SORF_TC_CASES)
+def test_sorf_tensor_core_energy_and_gradient_match_oracle(q, nf, T, n_mol):
+    """Both Hadamard chains on the tensor cores (FP16 chain tables, two-part
+    FP16 operands, FP32 accumulation) against the FP64 oracle: the same bounds
+    as the FWHT kernel. Cases span one to 150+ tiles of 128 atoms (several
+    tiles per CTA in the last), a ragged last tile, an empty molecule, odd stack
+    counts (backward promotion every 2 half stacks), atoms whose x spans six
+    orders of magnitude, a zero row, and weights spanning four."""
+    d = 128
+    x, mol_ptr, signs, b = _sorf_inputs(d, nf, T, n_mol=n_mol, seed=6 + nf)
+    rng = np.random.default_rng(7 + nf)
+    x *= (10.0 ** rng.uniform(-3, 3, size=(x.shape[0], 1))).astype(np.float32)
+    x[min(5, x.shape[0] - 1)] = 0.0
+    x = np.ascontiguousarray(x)
+    sigma = 1.3 * float(np.sqrt(np.mean(np.sum(x.astype(np.float64) ** 2, axis=1))))
+    alpha = (rng.normal(size=nf) * 0.05 * 10.0 ** rng.uniform(-2, 2, size=nf)).astype(np.float32)
+    W = o_sorf.sorf_matrix(signs, sigma)
+    xt = torch.tensor(x.astype(np.float64), requires_grad=True)
+    zt = o_sorf.features(xt, W, b.astype(np.float64))
+    e_atom = zt @ torch.as_tensor(alpha.astype(np.float64))
+    (gref,) = torch.autograd.grad(e_atom.sum(), xt)
+    gref = gref.numpy()
+    sizes = np.diff(mol_ptr)
+    Eref = np.array([e_atom[mol_ptr[k]:mol_ptr[k + 1]].sum().item() for k in range(len(sizes))])
+    bits = q.pack_signs(signs)
+    tables = q.sorf_tc_tables(bits, T, nf)
+    E, gx = q.sorf_grad_tc(x, mol_ptr, tables, T, b, sigma, alpha)
+    E, gx = E.cpu().numpy(), gx.cpu().numpy()[0]
+    # per atom: phase error <= 2^-18 of its bound (sqrt(d)/sigma)|x| plus 2^-20
+    # (sin/cos), weighted by sqrt(2/N_F) sum |alpha|; summed over the molecule
+    a1 = math.sqrt(2 / nf) * float(np.sum(np.abs(alpha.astype(np.float64))))
+    xn = np.linalg.norm(x.astype(np.float64), axis=1)
+    tol_a = a1 * (2.0 ** -18 * math.sqrt(d) / sigma * xn + 2.0 ** -20)
+    tol = np.array([tol_a[mol_ptr[k]:mol_ptr[k + 1]].sum() for k in range(len(sizes))])
+    assert np.all(np.abs(E - Eref) <= tol)
+    assert np.max(np.abs(gx - gref)) <= 1e-4 * np.max(np.abs(gref))
+    # deterministic
+    E2, gx2 = q.sorf_grad_tc(x, mol_ptr, tables, T, b, sigma, alpha)
+    assert np.array_equal(E, E2.cpu().numpy()) and np.array_equal(gx, gx2.cpu().numpy()[0])
+    assert q.device_status() == 0
+
+
+def test_sorf_tensor_core_tables_are_the_integer_chain(q):
+    """The FP16 tables hold M_s = H D_T ... H D_1 exactly (unnormalised
+    Hadamard, integer entries), forward [s][i][j] and backward [s][j][i]."""
+    nf, d, T = 384, 128, 3
+    rng = np.random.default_rng(11)
+    signs, _ = synth.sorf_draw(rng, nf, d, T)
+    tables = q.sorf_tc_tables(q.pack_signs(signs), T, nf).view(torch.float16).float().cpu().numpy()
+    mf = tables[:nf * d].reshape(nf // d, d, d)
+    mb = tables[nf * d:].reshape(nf // d, d, d)
+    W = o_sorf.sorf_matrix(signs, 1.0)            # (sqrt(d)) d^{-T/2} M_s stacked
+    M = W * d ** (T / 2) / math.sqrt(d)
+    assert np.array_equal(mf.reshape(nf, d), np.round(M))
+    assert np.allclose(M, np.round(M), atol=1e-9)
+    assert np.array_equal(mb, np.transpose(mf, (0, 2, 1)))
+    assert np.max(np.abs(mf)) <= d ** (T / 2)
+
+
 @pytest.mark.parametrize("d,nf,n_mol", [(16, 64, 9), (64, 512, 9), (128, 1000, 9), (128, 4096, 9),
                                         (200, 300, 9), (256, 129, 9), (16, 64, 10001)])
 def test_rff_tensor_core_matches_oracle(q, d, nf, n_mol):
