@@ -573,6 +573,7 @@ def run_ours(args, rank, world):
     model.set_timing(True)          # CUDA events around the prediction's kernels (read per timed step)
     if args.sorf_kernel == "fwht" and model.sorf_tc:
         model.set_sorf_tc(False)
+    pipeline.SORF_TC = args.sorf_kernel == "tc"
     sorf_tc = model.sorf_tc
     del rep, perm, offs
     torch.cuda.synchronize()
@@ -593,7 +594,7 @@ def run_ours(args, rank, world):
         ev[1].record(stream)
         x = qmlr.project(rep, p.rep_dim, perm, offs, p.n_el, U)
         ev[2].record(stream)
-        Z = qmlr.sorf(x, b.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
+        Z = pipeline.segment_features(x, b.mol_ptr, spec)
         ev[3].record(stream)
         zt = pipeline.gram_operand(Z, precision)
         ev[7].record(stream)
@@ -747,13 +748,25 @@ def run_ours(args, rank, world):
                                 f"{gdesc['products']} ({gdesc['products']} tensor-core products per Gram "
                                 f"product; {gdesc['rate']} x the BF16 rate for its operand type, the nominal "
                                 "dense ratio)"},
-        "sorf_Z": {"kernel": "qmlr::sorf_mol_kernel<128> (SORF + segment sum into Z)", "bound": "alu",
-                   "achieved": sorf_ops_atom * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": fp32_add_peak,
-                   "unit": "TFLOP/s",
-                   "work": f"{sorf_ops_atom} FP32 ops/atom (n_stack*T*d*log2 d butterflies + 6*N_F "
-                           "for phase, cos, sum)",
-                   "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
-                                  f"(measured FP32 add rate {fadd_measured} T/s, qmlr_unit_rates)"},
+        "sorf_Z": ({"kernel": "qmlr::stc::sorf_z_tc_kernel (SORF forward chains as tcgen05 FP16 products, cos, "
+                               "ordered molecule sums into Z)",
+                    "bound": "tensor",
+                    "achieved": 2 * w.d * nf * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": bf16_sust / 2,
+                    "unit": "TFLOP/s",
+                    "work": f"2*d*N_F = {2 * w.d * nf} flop/atom (dense chain product x M_s^T)",
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained / 2 (two FP16 products per dense "
+                                   "product; FP16 at the BF16 rate)",
+                    "mufu": {"achieved": nf * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": exp_rate,
+                             "unit": "T op/s", "work": "cos per feature (N_F per atom)",
+                             "peak_source": "measured __expf rate (MUFU), qmlr_unit_rates"}}
+                   if sorf_tc else
+                   {"kernel": "qmlr::sorf_mol_kernel<128> (SORF + segment sum into Z)", "bound": "alu",
+                    "achieved": sorf_ops_atom * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": fp32_add_peak,
+                    "unit": "TFLOP/s",
+                    "work": f"{sorf_ops_atom} FP32 ops/atom (n_stack*T*d*log2 d butterflies + 6*N_F "
+                            "for phase, cos, sum)",
+                    "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
+                                   f"(measured FP32 add rate {fadd_measured} T/s, qmlr_unit_rates)"}),
         "sorf_atom": ({"kernel": "qmlr::stc::sorf_tc_kernel (SORF energies + gradient, both Hadamard chains "
                                  "as tcgen05 FP16 products, prediction)",
                        "bound": "tensor",

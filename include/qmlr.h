@@ -412,8 +412,8 @@ int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_
  *   qmlr_sorf_tc_tables             fills them from the packed signs (device
  *                                   tables, 16-byte aligned; caller-owned;
  *                                   build once per set of signs)
- *   qmlr_sorf_tc_workspace_bytes(n) bytes of the per-call workspace
- *                                   (~516 B per atom; 256-byte aligned)
+ *   qmlr_sorf_tc_workspace_bytes(n, N_F) bytes of the per-call workspace
+ *                                   (~516 B per atom + 4 N_F; 256-byte aligned)
  *   qmlr_sorf_grad_tc               atom_energy double [n_atoms] (one part),
  *                                   energies double [n_mol], gx float
  *                                   [n_atoms][128] (one part: pass n_part = 1
@@ -425,13 +425,35 @@ int qmlr_sorf_grad(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_
  * per SM whose waits are bounded (device error 4, a timeout, on expiry).
  */
 int64_t qmlr_sorf_tc_table_bytes(int32_t n_features);
-int64_t qmlr_sorf_tc_workspace_bytes(int32_t n_atoms);
+int64_t qmlr_sorf_tc_workspace_bytes(int32_t n_atoms, int32_t n_features);
 int qmlr_sorf_tc_tables(const uint32_t* sign_bits, int32_t d, int32_t T, int32_t n_features,
                         void* tables, void* stream);
 int qmlr_sorf_grad_tc(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
                       int32_t n_atoms, const void* tables, int32_t T, const float* b,
                       int32_t n_features, double sigma, const float* alpha, double* atom_energy,
                       double* energies, float* gx, void* work, int64_t work_bytes, void* stream);
+
+/*
+ * Energy rows Z_m = sqrt(2/N_F) sum_{I in m} cos(u(x_I)) (SORF section; the
+ * rows of the normal equations) with the forward chains on the tensor cores:
+ * the same FP16 tables, operand split, phases and range check as
+ * qmlr_sorf_grad_tc, cos of the phases, and each molecule's atoms added in
+ * atom order in FP32 (the order of qmlr_sorf's PER_MOL mode), so Z_m does not
+ * depend on the batch the molecule is in. Each CTA of the persistent kernel
+ * owns a contiguous range of whole molecules; a molecule of any size is
+ * carried across 128-atom tiles.
+ *   Z     float [n_mol] rows of stride ldz >= N_F (16-byte aligned), every
+ *         row written (an empty molecule gives a zero row)
+ *   work  qmlr_sorf_tc_segment_workspace_bytes(n_atoms, N_F) bytes, 256-byte
+ *         aligned (FP16 parts of x, row scales, carried rows)
+ * Same argument rules and errors as qmlr_sorf_grad_tc. Asynchronous on
+ * `stream`; allocates nothing.
+ */
+int64_t qmlr_sorf_tc_segment_workspace_bytes(int32_t n_atoms, int32_t n_features);
+int qmlr_sorf_segment_sum_tc(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
+                             int32_t n_atoms, const void* tables, int32_t T, const float* b,
+                             int32_t n_features, double sigma, float* Z, int64_t ldz, void* work,
+                             int64_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * Regularised normal equations (RFF section: (Z^T Z + lambda I) alpha = Z^T E,

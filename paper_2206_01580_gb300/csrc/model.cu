@@ -58,7 +58,7 @@ int PredictWorkspace::reserve(const qmlr_model* m, int max_atoms) {
   if (e == cudaSuccess) e = cudaMalloc(&pair_ptr, (n + 4096 + 1) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&contrib, n * (size_t)m->max_mol_atoms * 3 * 4);
   if (e == cudaSuccess && m->sorf_tables) {
-    sorf_work_bytes = sorf_tc_work_bytes((int)n);
+    sorf_work_bytes = sorf_tc_work_bytes((int)n, m->n_features);
     e = cudaMalloc(&sorf_work, sorf_work_bytes);
   }
   if (e != cudaSuccess) {

@@ -38,7 +38,7 @@ int sorf_energy_grad_model(const float* x, int d, const int32_t* mol_ptr, int n_
 // Tensor-core SORF energies and gradients (sorf_tc.cu): chain tables
 // [2][N_F][128] FP16, per-call workspace of FP16 parts of x and row scales.
 size_t sorf_tc_table_bytes(int n_features);
-size_t sorf_tc_work_bytes(int n_atoms);
+size_t sorf_tc_work_bytes(int n_atoms, int n_features);
 bool sorf_tc_supported(int d, int T, int n_features);
 int sorf_tc_tables(const uint32_t* sign_bits, int T, int n_features, void* tables, cudaStream_t s);
 int sorf_tc_energy_grad(const float* x, int n_atoms, const void* tables, int T, const float* b,

@@ -280,6 +280,7 @@ force_rows_kernel(const float* __restrict__ tang, const int64_t* __restrict__ ja
   for (int k = 0; k < T * W; ++k) sg[k * nt + tid] = active ? __ldg(sign_bits + (long)sidx * T * W + k) : 0u;
   for (int kx = 0; kx < 3 * M; ++kx) {
     const int kl = kx / 3, x = kx % 3;
+    __syncthreads();   // every thread has written out the previous row's columns of acc
     for (int i = 0; i < D; ++i) acc[i * (nt + 1) + tid] = 0.f;
     for (int c0 = 0; c0 < M; c0 += CH) {
       const int cn = min(CH, M - c0);

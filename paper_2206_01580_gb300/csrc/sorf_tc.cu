@@ -22,11 +22,12 @@
 // error small).
 //
 // Kernel layout: persistent, one CTA per SM, tiles of 128 atoms (one TMEM lane
-// per atom). A unit is half a stack (64 features). Warp 8 issues TMA (the
+// per atom). A unit is half a stack (64 features). Warp 16 issues TMA (the
 // tile's two X parts once, then per unit the forward tile of M_s, the backward
-// tile of M_s^T and the unit's 64 phases and weights), warp 9 issues the MMAs
-// (forward of unit n, then backward of unit n - 2), warps 0-7 run the epilogue:
-// each reads 32 columns of the unit's accumulator for its atom, forms the
+// tile of M_s^T and the unit's 64 phases and weights), warp 17 issues the MMAs
+// (forward of unit n, then backward of unit n - 1), warps 0-15 run the
+// epilogue (four per SM sub-partition, to hide the latency of the sin/cos
+// chains): each reads 16 columns of the unit's accumulator for its atom, forms the
 // phases, sin and cos, the energy partial and the two FP16 parts of Y, and
 // writes them 128-byte swizzled for the backward MMA. Every wait is bounded:
 // on expiry the CTA records DEV_TIMEOUT, stops, waits (bounded) for its own
@@ -45,12 +46,15 @@ using namespace tc;
 constexpr int D = 128;        // projected dimension = features per stack
 constexpr int TM = 128;       // atoms per tile
 constexpr int UN = 64;        // features per unit (half a stack)
-constexpr int NS = 5;         // ring of 16 KB operand tiles (forward and backward, in MMA order)
+constexpr int NS = 7;         // ring of 16 KB operand tiles (forward and backward, in MMA order)
 constexpr int NDB = 4;        // forward accumulators (64 TMEM columns each)
-constexpr int NYS = 2;        // Y slots
+constexpr int NYS = 1;        // Y slots
 constexpr int NBA = 8;        // phase / weight slots
-constexpr int LA = 2;         // the backward of unit n is issued after the forward of unit n + LA
-constexpr int kEpiWarps = 8;
+constexpr int LA = 1;         // the backward of unit n is issued after the forward of unit n + LA
+constexpr int kEpiWarps = 16;   // four per SM sub-partition
+constexpr int CQ = kEpiWarps / 4;   // column groups (warps sharing a TMEM lane quarter)
+constexpr int CW = 64 / CQ;         // accumulator columns of a unit per epilogue thread
+constexpr int GW = 128 / CQ;        // gradient dimensions per epilogue thread
 constexpr int kThreads = 32 * (kEpiWarps + 2);
 
 constexpr int X_BYTES = 2 * TM * D * 2;     // two FP16 parts x two 64-wide K blocks
@@ -61,22 +65,24 @@ constexpr int OFF_X = 0;
 constexpr int OFF_B = OFF_X + X_BYTES;
 constexpr int OFF_Y = OFF_B + NS * TILE_BYTES;
 constexpr int OFF_BA = OFF_Y + NYS * Y_BYTES;
-constexpr int OFF_RED = OFF_BA + NBA * BA_FLOATS * 4;    // double [2 tile parities][TM]
-constexpr int OFF_BAR = OFF_RED + 2 * TM * 8;
+constexpr int OFF_RED = OFF_BA + NBA * BA_FLOATS * 4;    // double [2 tile parities][CQ - 1][TM]
+constexpr int OFF_BAR = OFF_RED + 2 * (CQ - 1) * TM * 8;
 constexpr int N_BARS = 2 + 2 * NS + 2 * NBA + 2 * NDB + 2 * NYS + 2 * 2 + 2 * 4 + 1;
 constexpr int SMEM_BYTES = OFF_BAR + N_BARS * 8 + 64 + 1024;
 constexpr int TMEM_COLS = 512;   // NDB x 64 forward + 2 x 128 backward
 
 static_assert(NDB * UN + 2 * D <= TMEM_COLS, "TMEM budget");
+static_assert((CW == 16 || CW == 32) && GW % 32 == 0, "epilogue TMEM loads: 16 or 32 unit columns, gradient in 32s");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared-memory budget");
 
 struct Args {
   const float* kx;       // [n_pad] 2^-k of each atom's row scale
   const float* b;        // [N_F] phases, natural order (stack-major)
-  const float* alpha;    // [N_F] weights, natural order
+  const float* alpha;    // [N_F] weights times S, natural order
+  const float* ys;       // [2]: S, a power of two with max |alpha| S in [2^14, 2^15), and 1/S
   double* atom_e;        // [n_atoms]
   float* gx;             // [n_atoms][D]
-  int n_atoms, n_pad, n_tiles, n_stack, period;
+  int n_atoms, n_pad, n_tiles, n_stack, period_log2;   // backward promotion every 2^period_log2 units
   float cscale;          // (sqrt(d)/sigma) / d^{T/2}
   float pref;            // sqrt(2/N_F)
   int* err;
@@ -105,6 +111,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
+
+__device__ __forceinline__ void tmem_ldn(uint32_t taddr, float (&v)[16]) { tmem_ld16(taddr, v); }
+__device__ __forceinline__ void tmem_ldn(uint32_t taddr, float (&v)[32]) { tmem_ld32(taddr, v); }
 
 // kind::f16 instruction descriptor with FP16 A and B (format code 0), FP32 D, K-major.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
@@ -135,15 +144,14 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
   uint64_t* yempty = yfull + NYS;
   uint64_t* gfull = yempty + NYS;
   uint64_t* gempty = gfull + 2;
-  uint64_t* efull = gempty + 2;     // [2 parities][4 quarters]: upper-half energy partials written
+  uint64_t* efull = gempty + 2;     // [2 parities][4 quarters]: energy partials of column groups 1.. written
   uint64_t* mdone = efull + 8;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* never_abort = abort + 1;
-  float* s_wmax = reinterpret_cast<float*>(tmem_slot + 4);   // [kEpiWarps + 2]: max |alpha| per warp
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int U = 2 * a.n_stack, P = a.period;
+  const int U = 2 * a.n_stack, PL = a.period_log2, P = 1 << PL, PM = P - 1;
 
   if (threadIdx.x == 0) {
     mbar_init(xfull, 1);
@@ -168,23 +176,11 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
       mbar_init(&gfull[q], 1);
       mbar_init(&gempty[q], kEpiWarps);
     }
-    for (int q = 0; q < 8; ++q) mbar_init(&efull[q], 1);
+    for (int q = 0; q < 8; ++q) mbar_init(&efull[q], CQ - 1);
     mbar_init(mdone, 1);
     *abort = 0;
     *never_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // S = 2^(15 - e) with max |alpha| = m 2^e, m in [0.5, 1): max |alpha| S in [2^14, 2^15)
-  {
-    float m = 0.f;
-    const float4* a4 = reinterpret_cast<const float4*>(a.alpha);
-    for (int i = threadIdx.x; i < a.n_stack * D / 4; i += blockDim.x) {
-      const float4 v = __ldg(a4 + i);
-      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) s_wmax[warp] = m;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -195,11 +191,7 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
-  float amax = 0.f;
-  for (int w = 0; w < kEpiWarps + 2; ++w) amax = fmaxf(amax, s_wmax[w]);
-  int ex = 0;
-  frexpf(amax, &ex);
-  const float S = (amax > 0.f && amax < 1e30f) ? ldexpf(1.f, min(max(15 - ex, -100), 100)) : 1.f;
+  const float S = __ldg(a.ys), inv_s = __ldg(a.ys + 1);
 
   int last_x = -1, last_b[NS], last_ba[NBA];
 #pragma unroll
@@ -209,9 +201,12 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
 
   if (warp == kEpiWarps && lane == 0) {
     // ------------------------------------------------------------ TMA producer
-    long q = 0, n = 0;
+    int q = 0, n = 0;
     int k = 0;
     bool ok = true;
+    // every CTA walks the stacks in the same order: an atom's energy and gradient
+    // sums then do not depend on the CTA (or batch) that computes it
+    const int s0 = 0;
     for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++k, n += U) {
       if (k > 0 && !mbar_wait(xempty, (k - 1) & 1, abort)) {
         ok = false;
@@ -226,8 +221,10 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
       last_x = k;
       for (int j = 0; ok && j < U + LA; ++j) {
         if (j < U) {
-          const long un = n + j;
-          const int s = j >> 1, h = j & 1;
+          const int un = n + j;
+          int s = (j >> 1) + s0;
+          if (s >= a.n_stack) s -= a.n_stack;
+          const int h = j & 1;
           const int bs = (int)(un % NBA);
           if (un >= NBA && !mbar_wait(&baempty[bs], (uint32_t)((un / NBA) - 1) & 1, abort)) {
             ok = false;
@@ -249,7 +246,9 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
           ++q;
         }
         if (j >= LA) {
-          const int jm = j - LA, s = jm >> 1, h = jm & 1;
+          const int jm = j - LA, h = jm & 1;
+          int s = (jm >> 1) + s0;
+          if (s >= a.n_stack) s -= a.n_stack;
           const int st = (int)(q % NS);
           if (q >= NS && !mbar_wait(&bempty[st], (uint32_t)((q / NS) - 1) & 1, abort)) {
             ok = false;
@@ -269,7 +268,7 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
   } else if (warp == kEpiWarps + 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     constexpr uint32_t idf = idesc_f16(TM, UN), idb = idesc_f16(TM, D);
-    long q = 0, n = 0;
+    int q = 0, n = 0;
     int k = 0;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++k, n += U) {
@@ -279,8 +278,8 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
       }
       for (int j = 0; ok && j < U + LA; ++j) {
         if (j < U) {
-          const long un = n + j;
-          const int st = (int)(q % NS), db = (int)(un % NDB);
+          const int un = n + j;
+          const int st = q % NS, db = un % NDB;
           if (!mbar_wait(&bfull[st], (uint32_t)(q / NS) & 1, abort) ||
               (un >= NDB && !mbar_wait(&dempty[db], (uint32_t)((un / NDB) - 1) & 1, abort))) {
             ok = false;
@@ -303,11 +302,11 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
           ++q;
         }
         if (j >= LA) {
-          const long um = n + j - LA;
-          const int st = (int)(q % NS), ys = (int)(um % NYS);
-          const long gp = um / P;
-          const int gb = (int)(gp & 1);
-          const bool first = (um % P) == 0;
+          const int um = n + j - LA;
+          const int st = q % NS, ys = um % NYS;
+          const int gp = um >> PL;
+          const int gb = gp & 1;
+          const bool first = (um & PM) == 0;
           if (!mbar_wait(&bfull[st], (uint32_t)(q / NS) & 1, abort) ||
               !mbar_wait(&yfull[ys], (uint32_t)(um / NYS) & 1, abort) ||
               (first && gp >= 2 && !mbar_wait(&gempty[gb], (uint32_t)((gp / 2) - 1) & 1, abort))) {
@@ -326,7 +325,7 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
             }
           mma_commit(&bempty[st]);
           mma_commit(&yempty[ys]);
-          if ((um % P) == P - 1) mma_commit(&gfull[gb]);
+          if ((um & PM) == PM) mma_commit(&gfull[gb]);
           ++q;
         }
       }
@@ -340,12 +339,14 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
     mbar_wait(mdone, 0, never_abort);
   } else if (warp < kEpiWarps) {
     // ------------------------------------------------------------ epilogue
-    const int quarter = warp & 3, qh = warp >> 2;
+    // warp = (column group cg, lane quarter): TMEM lanes 32*quarter.., unit
+    // columns cg*CW.., gradient dimensions cg*GW..
+    const int quarter = warp & 3, cg = warp >> 2;
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    const float gscale = -a.pref * a.cscale / S;
-    float g[64];
-    long n = 0;
+    const float gscale = -a.pref * a.cscale * inv_s;
+    float g[GW];
+    int n = 0;
     int k = 0;
     bool ok = true;
     auto fail = [&]() {
@@ -356,8 +357,8 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
       ok = false;
     };
     // add the backward accumulator of period gp into the register sums
-    auto promote = [&](long gp) {
-      const int gb = (int)(gp & 1);
+    auto promote = [&](int gp) {
+      const int gb = gp & 1;
       const bool w = mbar_wait(&gfull[gb], (uint32_t)(gp / 2) & 1, abort);
       if (__any_sync(0xffffffffu, !w)) {
         fail();
@@ -365,9 +366,9 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) {
+      for (int c2 = 0; c2 < GW / 32; ++c2) {
         float t[32];
-        tmem_ld32(tmem + lane_base + NDB * UN + gb * D + qh * 64 + c2 * 32, t);
+        tmem_ld32(tmem + lane_base + NDB * UN + gb * D + cg * GW + c2 * 32, t);
 #pragma unroll
         for (int i = 0; i < 32; ++i) g[c2 * 32 + i] += t[i];
       }
@@ -380,24 +381,24 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
       const bool valid = atom < a.n_atoms;
       const float cs = a.cscale * __ldg(a.kx + atom);   // atom < n_pad always
 #pragma unroll
-      for (int i = 0; i < 64; ++i) g[i] = 0.f;
+      for (int i = 0; i < GW; ++i) g[i] = 0.f;
       double e_tile = 0.0;
       float e_f = 0.f;
       for (int j = 0; j < U; ++j) {
-        const long un = n + j;
-        if (j >= P && (j % P) == 1) {
-          promote(un / P - 1);
+        const int un = n + j;
+        if (j >= P && (j & PM) == 1) {
+          promote((un >> PL) - 1);
           if (!ok) break;
         }
-        const int db = (int)(un % NDB), bs = (int)(un % NBA), ys = (int)(un % NYS);
+        const int db = un % NDB, bs = un % NBA, ys = un % NYS;
         bool w = mbar_wait(&dfull[db], (uint32_t)(un / NDB) & 1, abort);
         if (__any_sync(0xffffffffu, !w)) {
           fail();
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        float v[32];
-        tmem_ld32(tmem + lane_base + db * UN + qh * 32, v);
+        float v[CW];
+        tmem_ldn(tmem + lane_base + db * UN + cg * CW, v);
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) mbar_arrive(&dempty[db]);
@@ -406,10 +407,10 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
           fail();
           break;
         }
-        const float4* b4 = reinterpret_cast<const float4*>(sba + bs * BA_FLOATS + qh * 32);
-        const float4* a4 = reinterpret_cast<const float4*>(sba + bs * BA_FLOATS + UN + qh * 32);
+        const float4* b4 = reinterpret_cast<const float4*>(sba + bs * BA_FLOATS + cg * CW);
+        const float4* a4 = reinterpret_cast<const float4*>(sba + bs * BA_FLOATS + UN + cg * CW);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < CW / 4; ++c) {
           const float4 bb = b4[c], aa = a4[c];
           const float bv[4] = {bb.x, bb.y, bb.z, bb.w}, av[4] = {aa.x, aa.y, aa.z, aa.w};
 #pragma unroll
@@ -417,7 +418,7 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
             float sn, cn;
             fast_sincos(fmaf(v[4 * c + e], cs, bv[e]), &sn, &cn);
             e_f = fmaf(av[e], cn, e_f);
-            v[4 * c + e] = (av[e] * S) * sn;
+            v[4 * c + e] = av[e] * sn;
           }
         }
         __syncwarp();
@@ -429,10 +430,10 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
             break;
           }
         }
-        // Y parts: row `row`, K offset qh*32 of the unit, 128-byte swizzle
+        // Y parts: row `row`, K offset cg*CW of the unit, 128-byte swizzle
         uint8_t* yrow = sy + ys * Y_BYTES + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
+        for (int cc = 0; cc < CW / 8; ++cc) {
           uint32_t hw[4], lw[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
@@ -443,32 +444,32 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
             hw[t] = h2_bits(hi);
             lw[t] = h2_bits(lo);
           }
-          const int chunk = ((qh * 4 + cc) ^ (row & 7)) * 16;
+          const int chunk = ((cg * (CW / 8) + cc) ^ (row & 7)) * 16;
           *reinterpret_cast<uint4*>(yrow + chunk) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           *reinterpret_cast<uint4*>(yrow + Y_BYTES / 2 + chunk) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&yfull[ys]);
-        if ((j % P) == P - 1) {
+        if ((j & PM) == PM) {
           e_tile += (double)e_f;
           e_f = 0.f;
         }
       }
       if (!ok) break;
-      promote((n + U - 1) / P);
+      promote((n + U - 1) >> PL);
       if (!ok) break;
       if (valid) {
-        float4* o = reinterpret_cast<float4*>(a.gx + (long)atom * D + qh * 64);
+        float4* o = reinterpret_cast<float4*>(a.gx + (long)atom * D + cg * GW);
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
+        for (int c = 0; c < GW / 4; ++c)
           o[c] = make_float4(g[4 * c] * gscale, g[4 * c + 1] * gscale, g[4 * c + 2] * gscale, g[4 * c + 3] * gscale);
       }
-      // energy: lower-half warp adds the upper half's partial (written to red) in a fixed order
-      double* rb = red + (k & 1) * TM;
+      // energy: column group 0 adds the other groups' partials (written to red) in order
+      double* rb = red + (k & 1) * (CQ - 1) * TM;
       uint64_t* eb = &efull[(k & 1) * 4 + quarter];
-      if (qh == 1) {
-        rb[row] = e_tile;
+      if (cg > 0) {
+        rb[(cg - 1) * TM + row] = e_tile;
         __syncwarp();
         if (lane == 0) mbar_arrive(eb);
       } else {
@@ -477,7 +478,10 @@ sorf_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__
           fail();
           break;
         }
-        if (valid) a.atom_e[atom] = (e_tile + rb[row]) * (double)a.pref;
+        double e = e_tile;
+#pragma unroll
+        for (int c = 0; c < CQ - 1; ++c) e += rb[c * TM + row];
+        if (valid) a.atom_e[atom] = e * (double)a.pref * (double)inv_s;
       }
     }
   }
@@ -534,6 +538,34 @@ __global__ void split_x_kernel(const float* __restrict__ x, int n_atoms, int n_p
   if (lane == 0) kx[atom] = ldexpf(1.f, -k);
 }
 
+// S = 2^(15 - e) for max |alpha| = m 2^e, m in [0.5, 1) (so max |alpha| S lies in
+// [2^14, 2^15), the range of the backward operand's FP16 parts), 1/S, and
+// alpha_sc = alpha S (exact: a power-of-two scale). One CTA.
+__global__ void __launch_bounds__(1024) alpha_scale_kernel(const float* __restrict__ alpha, int n,
+                                                           float* __restrict__ ys, float* __restrict__ alpha_sc) {
+  __shared__ float wmax[32];
+  __shared__ float s_sc;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(alpha[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, wmax[w]);
+    int ex = 0;
+    frexpf(mm, &ex);
+    const int k = (mm > 0.f && mm < 1e30f) ? min(max(15 - ex, -100), 100) : 0;
+    s_sc = ldexpf(1.f, k);
+    ys[0] = s_sc;
+    ys[1] = ldexpf(1.f, -k);
+  }
+  __syncthreads();
+  const float sc = s_sc;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) alpha_sc[i] = alpha[i] * sc;
+}
+
 // Forward and backward operand tables of the chains (exact integers in FP16):
 // mf[s][i][j] = (M_s)_{ij} (rows = features, K = dims) and mb[s][j][i] = (M_s)_{ij}
 // (rows = dims, K = features). One thread per (stack, column j): the chain of
@@ -560,15 +592,403 @@ __global__ void __launch_bounds__(D) chain_tables_kernel(const uint32_t* __restr
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Segment sums Z_m = sqrt(2/N_F) sum_{I in m} cos(u(x_I)) on the tensor cores:
+// the energy rows of the normal equations (SORF and RFF sections). Forward
+// chains only (two FP16 products per unit, as above); the epilogue writes
+// cos(c D + b) of its 16 columns to a padded shared-memory tile, and reader
+// threads (one feature column and one molecule slot each) add each molecule's
+// rows in atom order. Each CTA owns a contiguous range of whole molecules
+// (split at molecule starts, balanced by atom count) and walks it in tiles of
+// 128 atoms from the range's first atom; a molecule that crosses a tile
+// boundary is carried to the next tile through a per-CTA row in global memory,
+// always by the same thread. Every row of Z is written exactly once (empty
+// molecules as zeros); the order of every sum is fixed: deterministic.
+namespace zc {
+constexpr int NSZ = 5;               // ring of forward operand tiles
+constexpr int NBZ = 8;               // phase slots (64 floats each)
+constexpr int CLD = UN + 4;          // padded row of the cos tile (floats)
+constexpr int C_BYTES = TM * CLD * 4;
+constexpr int OFF_X = 0;
+constexpr int OFF_B = OFF_X + X_BYTES;
+constexpr int OFF_C = OFF_B + NSZ * TILE_BYTES;
+constexpr int OFF_BZ = OFF_C + 2 * C_BYTES;
+constexpr int OFF_BAR = OFF_BZ + NBZ * UN * 4;
+constexpr int N_BARS = 2 + 2 * NSZ + 2 * NBZ + 2 * NDB + 2 * 2 + 1;
+constexpr int SMEM_BYTES = OFF_BAR + N_BARS * 8 + 64 + 1024;
+constexpr int TMEM_COLS = 256;
+constexpr int kSlots = kEpiWarps * 32 / UN;   // molecule slots of the reader threads
+static_assert(SMEM_BYTES <= 227 * 1024, "shared-memory budget");
+static_assert(NDB * UN <= TMEM_COLS, "TMEM budget");
+static_assert(kSlots >= 2, "reader slots");
+}  // namespace zc
+
+struct ZArgs {
+  const float* kx;          // [n_pad] row scales of the FP16 parts
+  const float* b;           // [N_F] phases
+  const int32_t* mol_ptr;   // [n_mol + 1]
+  float* Z;                 // [n_mol][ldz]
+  long ldz;
+  float* carry;             // [gridDim.x][N_F] raw sums of molecules crossing a tile boundary
+  int n_atoms, n_mol, n_pad, n_stack;
+  float cscale, pref;
+  int* err;
+};
+
+// first m in [0, n] with p[m] >= v (p non-decreasing)
+__device__ __forceinline__ int lower_bound_i(const int32_t* p, int n, long v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(p + mid) < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+// first m in [0, n] with p[m] > v
+__device__ __forceinline__ int upper_bound_i(const int32_t* p, int n, long v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(p + mid) <= v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Rows [a0, a1) of one tile and the molecules [mf, mf + nm) that own them; sin:
+// the first molecule started in an earlier tile, sout: the last one continues.
+struct ZTile {
+  int a0, a1, mf, nm;
+  bool sin, sout;
+};
+
+__device__ __forceinline__ ZTile z_tile(const int32_t* mol_ptr, int n_mol, int A0, int A1, int M0, int M1, int k,
+                                        int n_tiles) {
+  ZTile t;
+  t.a0 = A0 + k * TM;
+  t.a1 = min(t.a0 + TM, A1);
+  const bool last = k == n_tiles - 1;
+  int mf;
+  if (k == 0) {
+    mf = M0;
+    t.sin = false;
+  } else {
+    const int mc = upper_bound_i(mol_ptr, n_mol + 1, t.a0) - 1;   // the molecule holding atom a0
+    t.sin = __ldg(mol_ptr + mc) < t.a0;
+    mf = t.sin ? mc : lower_bound_i(mol_ptr, n_mol + 1, t.a0);
+  }
+  const int me = last ? M1 : lower_bound_i(mol_ptr, n_mol + 1, t.a1);
+  t.mf = mf;
+  t.nm = me - mf;
+  t.sout = !last && t.nm > 0 && __ldg(mol_ptr + me) > t.a1;
+  return t;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__ CUtensorMap mapf, ZArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sx = smem + zc::OFF_X;
+  uint8_t* sb = smem + zc::OFF_B;
+  float* sc = reinterpret_cast<float*>(smem + zc::OFF_C);
+  float* sbz = reinterpret_cast<float*>(smem + zc::OFF_BZ);
+  uint64_t* xfull = reinterpret_cast<uint64_t*>(smem + zc::OFF_BAR);
+  uint64_t* xempty = xfull + 1;
+  uint64_t* bfull = xempty + 1;
+  uint64_t* bempty = bfull + zc::NSZ;
+  uint64_t* bzfull = bempty + zc::NSZ;
+  uint64_t* bzempty = bzfull + zc::NBZ;
+  uint64_t* dfull = bzempty + zc::NBZ;
+  uint64_t* dempty = dfull + NDB;
+  uint64_t* cfull = dempty + NDB;
+  uint64_t* cempty = cfull + 2;
+  uint64_t* mdone = cempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* never_abort = abort + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int U = 2 * a.n_stack, NF = a.n_stack * D;
+  // this CTA's molecules [M0, M1) and atoms [A0, A1)
+  const int M0 = blockIdx.x == 0 ? 0 : lower_bound_i(a.mol_ptr, a.n_mol + 1, (long)blockIdx.x * a.n_atoms / gridDim.x);
+  const int M1 = blockIdx.x == gridDim.x - 1
+                     ? a.n_mol
+                     : lower_bound_i(a.mol_ptr, a.n_mol + 1, (long)(blockIdx.x + 1) * a.n_atoms / gridDim.x);
+  const int A0 = __ldg(a.mol_ptr + M0), A1 = __ldg(a.mol_ptr + M1);
+  const int n_tiles = (A1 - A0 + TM - 1) / TM;
+  const int s0 = (int)(((long)blockIdx.x * a.n_stack) / gridDim.x);
+
+  if (threadIdx.x == 0) {
+    mbar_init(xfull, 1);
+    mbar_init(xempty, 1);
+    for (int q = 0; q < zc::NSZ; ++q) {
+      mbar_init(&bfull[q], 1);
+      mbar_init(&bempty[q], 1);
+    }
+    for (int q = 0; q < zc::NBZ; ++q) {
+      mbar_init(&bzfull[q], 1);
+      mbar_init(&bzempty[q], kEpiWarps);
+    }
+    for (int q = 0; q < NDB; ++q) {
+      mbar_init(&dfull[q], 1);
+      mbar_init(&dempty[q], kEpiWarps);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&cfull[q], kEpiWarps);
+      mbar_init(&cempty[q], kEpiWarps);
+    }
+    mbar_init(mdone, 1);
+    *abort = 0;
+    *never_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(zc::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  int last_x = -1, last_b[zc::NSZ], last_bz[zc::NBZ];
+#pragma unroll
+  for (int q = 0; q < zc::NSZ; ++q) last_b[q] = -1;
+#pragma unroll
+  for (int q = 0; q < zc::NBZ; ++q) last_bz[q] = -1;
+
+  if (warp == kEpiWarps && lane == 0) {
+    // ------------------------------------------------------------ TMA producer
+    int q = 0, n = 0;
+    bool ok = true;
+    for (int k = 0; ok && k < n_tiles; ++k, n += U) {
+      if (k > 0 && !mbar_wait(xempty, (k - 1) & 1, abort)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(xfull, X_BYTES);
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb)
+          tma_load_2d(sx + p * (X_BYTES / 2) + kb * (X_BYTES / 4), &mapx, xfull, kb * 64, p * a.n_pad + A0 + k * TM);
+      last_x = k;
+      for (int j = 0; j < U; ++j) {
+        const int un = n + j;
+        int s = (j >> 1) + s0;
+        if (s >= a.n_stack) s -= a.n_stack;
+        const int h = j & 1;
+        const int bs = un % zc::NBZ;
+        if (un >= zc::NBZ && !mbar_wait(&bzempty[bs], (uint32_t)((un / zc::NBZ) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&bzfull[bs], UN * 4);
+        bulk_load(sbz + bs * UN, a.b + (long)s * D + h * UN, UN * 4, &bzfull[bs]);
+        last_bz[bs] = un / zc::NBZ;
+        const int st = q % zc::NSZ;
+        if (q >= zc::NSZ && !mbar_wait(&bempty[st], (uint32_t)((q / zc::NSZ) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&bfull[st], TILE_BYTES);
+        tma_load_2d(sb + st * TILE_BYTES, &mapf, &bfull[st], 0, s * D + h * UN);
+        tma_load_2d(sb + st * TILE_BYTES + TILE_BYTES / 2, &mapf, &bfull[st], 64, s * D + h * UN);
+        last_b[st] = q / zc::NSZ;
+        ++q;
+      }
+    }
+    if (!ok) {
+      record_device_error(a.err, DEV_TIMEOUT);
+      *abort = 1;
+    }
+  } else if (warp == kEpiWarps + 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    constexpr uint32_t idf = idesc_f16(TM, UN);
+    int q = 0, n = 0;
+    bool ok = true;
+    for (int k = 0; ok && k < n_tiles; ++k, n += U) {
+      if (!mbar_wait(xfull, k & 1, abort)) {
+        ok = false;
+        break;
+      }
+      for (int j = 0; j < U; ++j) {
+        const int un = n + j;
+        const int st = q % zc::NSZ, db = un % NDB;
+        if (!mbar_wait(&bfull[st], (uint32_t)(q / zc::NSZ) & 1, abort) ||
+            (un >= NDB && !mbar_wait(&dempty[db], (uint32_t)((un / NDB) - 1) & 1, abort))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t d = tmem + db * UN;
+#pragma unroll
+        for (int p = 1; p >= 0; --p)
+#pragma unroll
+          for (int kk = 0; kk < D / 16; ++kk) {
+            const uint64_t da = smem_desc(sx + p * (X_BYTES / 2) + (kk >> 2) * (X_BYTES / 4)) + 2 * (kk & 3);
+            const uint64_t dbd = smem_desc(sb + st * TILE_BYTES + (kk >> 2) * (TILE_BYTES / 2)) + 2 * (kk & 3);
+            mma_bf16(d, da, dbd, idf, (p == 1 && kk == 0) ? 0u : 1u);
+          }
+        mma_commit(&bempty[st]);
+        mma_commit(&dfull[db]);
+        if (j == U - 1) mma_commit(xempty);
+        ++q;
+      }
+    }
+    if (!ok) {
+      record_device_error(a.err, DEV_TIMEOUT);
+      *abort = 1;
+    }
+    mma_commit(mdone);
+    mbar_wait(mdone, 0, never_abort);
+  } else if (warp < kEpiWarps) {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    // reader role: feature column f of a unit, molecule slot
+    const int t = warp * 32 + lane, f = t % UN, slot = t / UN;
+    float* carry = a.carry + (long)blockIdx.x * NF;
+    bool ok = true;
+    auto fail = [&]() {
+      if (lane == 0) {
+        record_device_error(a.err, DEV_TIMEOUT);
+        *abort = 1;
+      }
+      ok = false;
+    };
+    if (n_tiles == 0) {
+      // molecules without atoms only: zero rows
+      for (int m = M0; m < M1; ++m)
+        for (int i = t; i < NF; i += kEpiWarps * 32) a.Z[(long)m * a.ldz + i] = 0.f;
+    }
+    // sum0 plus one molecule's rows [r0, r1) of column f of the cos tile, in row
+    // order (a molecule carried across tiles is summed exactly as if in one)
+    auto col_sum = [&](const float* cbuf, int r0, int r1, float sum0) {
+      float sum = sum0;
+      for (int r = r0; r < r1; ++r) sum += cbuf[r * zc::CLD + f];
+      return sum;
+    };
+    // the reader pass for unit un (local index j of a tile with info tt)
+    auto read_unit = [&](int un, int j, const ZTile& tt) {
+      const int cb = un & 1;
+      const bool w = mbar_wait(&cfull[cb], (uint32_t)(un >> 1) & 1, abort);
+      if (__any_sync(0xffffffffu, !w)) {
+        fail();
+        return;
+      }
+      const float* cbuf = sc + cb * (zc::C_BYTES / 4);
+      int s = (j >> 1) + s0;
+      if (s >= a.n_stack) s -= a.n_stack;
+      const int fi = s * D + (j & 1) * UN + f;
+      const int n_own = tt.nm - (tt.sout && tt.nm > 1 ? 1 : 0);   // molecules ending in this tile
+      if (slot == 0) {
+        // first molecule (carried in or not), then the one carried out
+        const int m = tt.mf;
+        const int r0 = max(__ldg(a.mol_ptr + m), tt.a0) - tt.a0, r1 = min(__ldg(a.mol_ptr + m + 1), tt.a1) - tt.a0;
+        const float sum = col_sum(cbuf, r0, r1, tt.sin ? carry[fi] : 0.f);
+        if (tt.nm == 1 && tt.sout) carry[fi] = sum;
+        else a.Z[(long)m * a.ldz + fi] = a.pref * sum;
+        if (tt.sout && tt.nm > 1) {
+          const int ml = tt.mf + tt.nm - 1;
+          carry[fi] = col_sum(cbuf, __ldg(a.mol_ptr + ml) - tt.a0, tt.a1 - tt.a0, 0.f);
+        }
+      } else {
+        for (int i = slot; i < n_own; i += zc::kSlots - 1) {
+          const int m = tt.mf + i;
+          const int r0 = __ldg(a.mol_ptr + m) - tt.a0, r1 = __ldg(a.mol_ptr + m + 1) - tt.a0;
+          a.Z[(long)m * a.ldz + fi] = a.pref * col_sum(cbuf, r0, r1, 0.f);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cempty[cb]);
+    };
+    int n = 0;
+    ZTile prev{};
+    for (int k = 0; ok && k < n_tiles; ++k, n += U) {
+      const ZTile tt = z_tile(a.mol_ptr, a.n_mol, A0, A1, M0, M1, k, n_tiles);
+      const float cs = a.cscale * __ldg(a.kx + tt.a0 + row);   // a0 + row < n_pad
+      for (int j = 0; j < U; ++j) {
+        const int un = n + j;
+        const int db = un % NDB, bs = un % zc::NBZ, cb = un & 1;
+        bool w = mbar_wait(&dfull[db], (uint32_t)(un / NDB) & 1, abort);
+        if (__any_sync(0xffffffffu, !w)) {
+          fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        float v[CW];
+        tmem_ldn(tmem + lane_base + db * UN + cg * CW, v);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&dempty[db]);
+        w = mbar_wait(&bzfull[bs], (uint32_t)(un / zc::NBZ) & 1, abort);
+        if (__any_sync(0xffffffffu, !w)) {
+          fail();
+          break;
+        }
+        const float4* b4 = reinterpret_cast<const float4*>(sbz + bs * UN + cg * CW);
+#pragma unroll
+        for (int c = 0; c < CW / 4; ++c) {
+          const float4 bb = b4[c];
+          v[4 * c] = fast_cos(fmaf(v[4 * c], cs, bb.x));
+          v[4 * c + 1] = fast_cos(fmaf(v[4 * c + 1], cs, bb.y));
+          v[4 * c + 2] = fast_cos(fmaf(v[4 * c + 2], cs, bb.z));
+          v[4 * c + 3] = fast_cos(fmaf(v[4 * c + 3], cs, bb.w));
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bzempty[bs]);
+        if (un >= 2) {
+          w = mbar_wait(&cempty[cb], (uint32_t)((un >> 1) - 1) & 1, abort);
+          if (__any_sync(0xffffffffu, !w)) {
+            fail();
+            break;
+          }
+        }
+        float4* crow = reinterpret_cast<float4*>(sc + cb * (zc::C_BYTES / 4) + row * zc::CLD + cg * CW);
+#pragma unroll
+        for (int c = 0; c < CW / 4; ++c) crow[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&cfull[cb]);
+        if (un > 0) {
+          read_unit(un - 1, j > 0 ? j - 1 : U - 1, j > 0 ? tt : prev);
+          if (!ok) break;
+        }
+      }
+      prev = tt;
+    }
+    if (ok && n_tiles > 0) read_unit(n - 1, U - 1, prev);
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (*abort && warp == kEpiWarps && lane == 0) {
+    if (last_x >= 0) mbar_wait(xfull, (uint32_t)last_x & 1, never_abort);
+    for (int q = 0; q < zc::NSZ; ++q)
+      if (last_b[q] >= 0) mbar_wait(&bfull[q], (uint32_t)last_b[q] & 1, never_abort);
+    for (int q = 0; q < zc::NBZ; ++q)
+      if (last_bz[q] >= 0) mbar_wait(&bzfull[q], (uint32_t)last_bz[q] & 1, never_abort);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(zc::TMEM_COLS));
+  }
+}
+
 }  // namespace stc
 
 size_t sorf_tc_table_bytes(int n_features) { return (size_t)2 * n_features * stc::D * sizeof(__half); }
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-size_t sorf_tc_work_bytes(int n_atoms) {
+size_t sorf_tc_work_bytes(int n_atoms, int n_features) {
   const size_t n_pad = (size_t)((std::max(n_atoms, 1) + stc::TM - 1) / stc::TM) * stc::TM;
-  return align256(2 * n_pad * stc::D * sizeof(__half)) + align256(n_pad * sizeof(float));
+  return align256(2 * n_pad * stc::D * sizeof(__half)) + align256(n_pad * sizeof(float)) + 256 +
+         align256((size_t)std::max(n_features, 1) * sizeof(float));
 }
 
 bool sorf_tc_supported(int d, int T, int n_features) {
@@ -595,8 +1015,8 @@ int sorf_tc_energy_grad(const float* x, int n_atoms, const void* tables, int T, 
   QMLR_REQUIRE(n_atoms >= 0, "negative sizes");
   if (n_atoms == 0) return QMLR_OK;
   QMLR_REQUIRE(x && tables && b && alpha && atom_e && gx && work, "NULL pointer argument");
-  QMLR_REQUIRE(work_bytes >= sorf_tc_work_bytes(n_atoms), "SORF workspace too small (%zu < %zu bytes)",
-               work_bytes, sorf_tc_work_bytes(n_atoms));
+  QMLR_REQUIRE(work_bytes >= sorf_tc_work_bytes(n_atoms, n_features), "SORF workspace too small (%zu < %zu bytes)",
+               work_bytes, sorf_tc_work_bytes(n_atoms, n_features));
   QMLR_REQUIRE((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(b) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(alpha) & 15) == 0 && (reinterpret_cast<uintptr_t>(gx) & 15) == 0 &&
                    (reinterpret_cast<uintptr_t>(tables) & 15) == 0 && (reinterpret_cast<uintptr_t>(work) & 255) == 0,
@@ -605,7 +1025,11 @@ int sorf_tc_energy_grad(const float* x, int n_atoms, const void* tables, int T, 
   const int n_tiles = (n_atoms + TM - 1) / TM, n_pad = n_tiles * TM;
   __half* xh = static_cast<__half*>(work);
   float* kx = reinterpret_cast<float*>(static_cast<uint8_t*>(work) + align256((size_t)2 * n_pad * D * sizeof(__half)));
+  float* ys = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(kx) + align256((size_t)n_pad * sizeof(float)));
+  float* alpha_sc = ys + 64;
   int* err = device_error_ptr();
+  alpha_scale_kernel<<<1, 1024, 0, s>>>(alpha, n_features, ys, alpha_sc);
+  QMLR_LAUNCH_CHECK();
   split_x_kernel<<<(n_pad + 7) / 8, 256, 0, s>>>(x, n_atoms, n_pad, sorf_x2max(D, sigma), xh, kx, err);
   QMLR_LAUNCH_CHECK();
   const __half* mf = static_cast<const __half*>(tables);
@@ -618,7 +1042,8 @@ int sorf_tc_energy_grad(const float* x, int n_atoms, const void* tables, int T, 
   Args a;
   a.kx = kx;
   a.b = b;
-  a.alpha = alpha;
+  a.alpha = alpha_sc;
+  a.ys = ys;
   a.atom_e = atom_e;
   a.gx = gx;
   a.n_atoms = n_atoms;
@@ -626,13 +1051,77 @@ int sorf_tc_energy_grad(const float* x, int n_atoms, const void* tables, int T, 
   a.n_tiles = n_tiles;
   a.n_stack = n_stack;
   const int U = 2 * n_stack;
-  a.period = U % 8 == 0 ? 8 : (U % 4 == 0 ? 4 : 2);
+  a.period_log2 = U % 8 == 0 ? 3 : (U % 4 == 0 ? 2 : 1);
   a.cscale = (float)(sqrt((double)D) / sigma / pow((double)D, 0.5 * T));
   a.pref = (float)sqrt(2.0 / n_features);
   a.err = err;
   QMLR_CUDA_TRY(smem_attr_once((const void*)sorf_tc_kernel, SMEM_BYTES));
   const int grid = std::min(n_tiles, sm_count());
   sorf_tc_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(mx, mapf, mapb, a);
+  QMLR_LAUNCH_CHECK();
+  return QMLR_OK;
+}
+
+// Z rows [n_mol][ldz] of the SORF segment sums for tables built by
+// sorf_tc_tables; work holds sorf_tc_z_work_bytes.
+constexpr int kZMaxCtas = 256;
+
+static size_t z_pad(int n_atoms) { return ((size_t)(std::max(n_atoms, 0) + stc::TM - 1) / stc::TM + 1) * stc::TM; }
+
+size_t sorf_tc_z_work_bytes(int n_atoms, int n_features) {
+  const size_t n_pad = z_pad(n_atoms);
+  return align256(2 * n_pad * stc::D * sizeof(__half)) + align256(n_pad * sizeof(float)) +
+         align256((size_t)kZMaxCtas * std::max(n_features, 1) * sizeof(float));
+}
+
+int sorf_tc_segment_sum(const float* x, int n_atoms, const int32_t* mol_ptr, int n_mol, const void* tables, int T,
+                        const float* b, int n_features, double sigma, float* Z, long ldz, void* work,
+                        size_t work_bytes, cudaStream_t s) {
+  using namespace stc;
+  QMLR_REQUIRE(n_atoms >= 0 && n_mol >= 0, "negative sizes");
+  QMLR_REQUIRE(ldz >= n_features, "ldz must be >= n_features");
+  if (n_mol == 0) return QMLR_OK;
+  QMLR_REQUIRE(mol_ptr && Z, "NULL pointer argument");
+  if (n_atoms == 0) {
+    QMLR_CUDA_TRY(cudaMemset2DAsync(Z, (size_t)ldz * sizeof(float), 0, (size_t)n_features * sizeof(float),
+                                    (size_t)n_mol, s));
+    return QMLR_OK;
+  }
+  QMLR_REQUIRE(x && tables && b && work, "NULL pointer argument");
+  QMLR_REQUIRE(work_bytes >= sorf_tc_z_work_bytes(n_atoms, n_features), "SORF workspace too small (%zu < %zu bytes)",
+               work_bytes, sorf_tc_z_work_bytes(n_atoms, n_features));
+  QMLR_REQUIRE((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(b) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(tables) & 15) == 0 && (reinterpret_cast<uintptr_t>(work) & 255) == 0,
+               "x, b, tables must be 16-byte and work 256-byte aligned");
+  const int n_stack = n_features / D;
+  const int n_pad = (int)z_pad(n_atoms);
+  __half* xh = static_cast<__half*>(work);
+  float* kx = reinterpret_cast<float*>(static_cast<uint8_t*>(work) + align256((size_t)2 * n_pad * D * sizeof(__half)));
+  float* carry = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(kx) + align256((size_t)n_pad * sizeof(float)));
+  int* err = device_error_ptr();
+  split_x_kernel<<<(n_pad + 7) / 8, 256, 0, s>>>(x, n_atoms, n_pad, sorf_x2max(D, sigma), xh, kx, err);
+  QMLR_LAUNCH_CHECK();
+  CUtensorMap mx, mapf;
+  int rc;
+  if ((rc = make_map(&mx, xh, D, 2L * n_pad, TM))) return rc;
+  if ((rc = make_map(&mapf, tables, D, (long)n_stack * D, UN))) return rc;
+  ZArgs a;
+  a.kx = kx;
+  a.b = b;
+  a.mol_ptr = mol_ptr;
+  a.Z = Z;
+  a.ldz = ldz;
+  a.carry = carry;
+  a.n_atoms = n_atoms;
+  a.n_mol = n_mol;
+  a.n_pad = n_pad;
+  a.n_stack = n_stack;
+  a.cscale = (float)(sqrt((double)D) / sigma / pow((double)D, 0.5 * T));
+  a.pref = (float)sqrt(2.0 / n_features);
+  a.err = err;
+  QMLR_CUDA_TRY(smem_attr_once((const void*)sorf_z_tc_kernel, zc::SMEM_BYTES));
+  const int grid = std::max(1, std::min(std::min(sm_count(), kZMaxCtas), (n_atoms + 255) / 256));
+  sorf_z_tc_kernel<<<grid, kThreads, zc::SMEM_BYTES, s>>>(mx, mapf, a);
   QMLR_LAUNCH_CHECK();
   return QMLR_OK;
 }
@@ -645,8 +1134,8 @@ extern "C" int64_t qmlr_sorf_tc_table_bytes(int32_t n_features) {
   return n_features > 0 ? (int64_t)sorf_tc_table_bytes(n_features) : 0;
 }
 
-extern "C" int64_t qmlr_sorf_tc_workspace_bytes(int32_t n_atoms) {
-  return n_atoms >= 0 ? (int64_t)sorf_tc_work_bytes(n_atoms) : 0;
+extern "C" int64_t qmlr_sorf_tc_workspace_bytes(int32_t n_atoms, int32_t n_features) {
+  return n_atoms >= 0 && n_features > 0 ? (int64_t)sorf_tc_work_bytes(n_atoms, n_features) : 0;
 }
 
 extern "C" int qmlr_sorf_tc_tables(const uint32_t* sign_bits, int32_t d, int32_t T, int32_t n_features,
@@ -675,4 +1164,21 @@ extern "C" int qmlr_sorf_grad_tc(const float* x, int32_t d, const int32_t* mol_p
                                (size_t)work_bytes, s);
   if (rc) return rc;
   return sorf_segment_energy(atom_energy, 1, n_atoms, mol_ptr, n_mol, energies, s);
+}
+
+extern "C" int64_t qmlr_sorf_tc_segment_workspace_bytes(int32_t n_atoms, int32_t n_features) {
+  return n_atoms >= 0 && n_features > 0 ? (int64_t)sorf_tc_z_work_bytes(n_atoms, n_features) : 0;
+}
+
+extern "C" int qmlr_sorf_segment_sum_tc(const float* x, int32_t d, const int32_t* mol_ptr, int32_t n_mol,
+                                        int32_t n_atoms, const void* tables, int32_t T, const float* b,
+                                        int32_t n_features, double sigma, float* Z, int64_t ldz, void* work,
+                                        int64_t work_bytes, void* stream) {
+  QMLR_REQUIRE(sorf_tc_supported(d, T, n_features),
+               "tensor-core SORF needs d = 128, T in 1..3 and n_features a multiple of 128 (got %d, %d, %d)", d,
+               T, n_features);
+  QMLR_REQUIRE(sigma > 0, "sigma must be > 0");
+  QMLR_REQUIRE(work_bytes >= 0, "negative sizes");
+  return sorf_tc_segment_sum(x, n_atoms, mol_ptr, n_mol, tables, T, b, n_features, sigma, Z, ldz, work,
+                             (size_t)work_bytes, as_stream(stream));
 }

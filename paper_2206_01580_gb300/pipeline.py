@@ -40,6 +40,11 @@ class Batch:
                      int(np.diff(mol_ptr).max()) if len(mol_ptr) > 1 else 1)
 
 
+# SORF energy rows on the tensor cores (d = 128, T <= 3) or with the in-register
+# fast Walsh-Hadamard kernel
+SORF_TC = True
+
+
 @dataclass
 class FeatureSpec:
     p: FCHL19Params
@@ -48,10 +53,28 @@ class FeatureSpec:
     sign_bits: torch.Tensor   # packed Rademacher signs
     b: torch.Tensor           # float32 [N_F]
     sigma: float
+    tc_tables: torch.Tensor = None   # FP16 chain tables of the tensor-core SORF (built on first use)
 
     @property
     def n_features(self) -> int:
         return self.b.shape[0]
+
+    @property
+    def sorf_tc(self) -> bool:
+        return SORF_TC and self.d == 128 and self.T <= 3 and self.n_features % 128 == 0
+
+
+def segment_features(x, mol_ptr, spec: FeatureSpec, out=None):
+    """Z [n_mol, N_F]: sqrt(2/N_F) sum over each molecule's atoms of cos(W x + b)."""
+    if spec.sorf_tc:
+        if spec.tc_tables is None:
+            spec.tc_tables = qmlr.sorf_tc_tables(spec.sign_bits, spec.T, spec.n_features)
+        return qmlr.sorf_segment_sum_tc(x, mol_ptr, spec.tc_tables, spec.T, spec.b, spec.sigma, out=out)
+    Z = qmlr.sorf(x, mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
+    if out is not None:
+        out.copy_(Z)
+        return out
+    return Z
 
 
 def spec_from(p: FCHL19Params, d: int, signs, b, sigma: float) -> FeatureSpec:
@@ -74,7 +97,7 @@ def feature_matrix(batch: Batch, spec: FeatureSpec, U, rep=None, perm=None, offs
     if rep is None:
         rep, perm, offs = representations(batch, spec)
     x = qmlr.project(rep, spec.p.rep_dim, perm, offs, spec.p.n_el, U)
-    return qmlr.sorf(x, batch.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
+    return segment_features(x, batch.mol_ptr, spec)
 
 
 # Relative diagonal shift of the preconditioner factor for each Gram form: the
@@ -153,7 +176,7 @@ def energy_force_rows(batch: Batch, spec: FeatureSpec, U):
     x = qmlr.project(rep, spec.p.rep_dim, perm, offs, spec.p.n_el, U)
     n_mol, n_atoms = batch.n_mol, batch.n_atoms
     rows = torch.empty((n_mol + 3 * n_atoms, spec.n_features), device="cuda", dtype=torch.float32)
-    rows[:n_mol] = qmlr.sorf(x, batch.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_PER_MOL)
+    segment_features(x, batch.mol_ptr, spec, out=rows[:n_mol])
     sin_t = qmlr.sorf(x, batch.mol_ptr, spec.sign_bits, spec.T, spec.b, spec.sigma, qmlr.SORF_SIN_T)
     del rep, x
     jac_ptr, jac, row_elem = qmlr.fchl19_jacobian(batch.coords, batch.elem, batch.mol_ptr, batch.max_atoms, spec.p)

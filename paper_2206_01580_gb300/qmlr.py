@@ -129,9 +129,11 @@ _SIGS = {
     "qmlr_model_set_sorf_tc": (C.c_int, [VP, I32]),
     "qmlr_model_sorf_tc": (I32, [VP]),
     "qmlr_sorf_tc_table_bytes": (I64, [I32]),
-    "qmlr_sorf_tc_workspace_bytes": (I64, [I32]),
+    "qmlr_sorf_tc_workspace_bytes": (I64, [I32, I32]),
     "qmlr_sorf_tc_tables": (C.c_int, [P, I32, I32, I32, P, VP]),
     "qmlr_sorf_grad_tc": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, P, P, P, P, I64, VP]),
+    "qmlr_sorf_tc_segment_workspace_bytes": (I64, [I32, I32]),
+    "qmlr_sorf_segment_sum_tc": (C.c_int, [P, I32, P, I32, I32, P, I32, P, I32, D, P, I64, P, I64, VP]),
     "qmlr_predict_ef": (C.c_int, [VP, P, P, P, I32, I32, P, P, VP]),
     "qmlr_energy_vjp": (C.c_int, [P, P, I32, I32, P, P, VP]),
     "qmlr_unit_rates": (C.c_int, [P, I32, VP]),
@@ -539,13 +541,34 @@ def sorf_grad_tc(x, mol_ptr, tables, T: int, b, sigma: float, alpha):
     E = torch.empty((n_mol,), device="cuda", dtype=torch.float64)
     gx = torch.empty((1, n_atoms, d), device="cuda", dtype=torch.float32)
     atom_e = torch.empty((max(n_atoms, 1),), device="cuda", dtype=torch.float64)
-    wb = lib().qmlr_sorf_tc_workspace_bytes(n_atoms)
+    wb = lib().qmlr_sorf_tc_workspace_bytes(n_atoms, nf)
     work = torch.empty((wb + 256,), device="cuda", dtype=torch.uint8)
     off = (-work.data_ptr()) % 256
     _check(lib().qmlr_sorf_grad_tc(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(tables), T, _ptr(b), nf,
                                    float(sigma), _ptr(alpha), _ptr(atom_e), _ptr(E), _ptr(gx),
                                    work.data_ptr() + off, wb, _stream()))
     return E, gx
+
+
+def sorf_segment_sum_tc(x, mol_ptr, tables, T: int, b, sigma: float, out=None):
+    """Energy rows Z [n_mol, N_F] (float32) from the tensor-core chains; out may be
+    a row block of a larger float32 matrix (row stride >= N_F, unit column stride)."""
+    x = _dev(x, torch.float32)
+    mol_ptr = _dev(mol_ptr, torch.int32)
+    b = _dev(b, torch.float32)
+    n_atoms, d = x.shape
+    n_mol = mol_ptr.shape[0] - 1
+    nf = b.shape[0]
+    if out is None:
+        out = torch.empty((n_mol, nf), device="cuda", dtype=torch.float32)
+    assert out.dtype == torch.float32 and out.stride(1) == 1 and out.shape == (n_mol, nf)
+    wb = lib().qmlr_sorf_tc_segment_workspace_bytes(n_atoms, nf)
+    work = torch.empty((wb + 256,), device="cuda", dtype=torch.uint8)
+    off = (-work.data_ptr()) % 256
+    _check(lib().qmlr_sorf_segment_sum_tc(_ptr(x), d, _ptr(mol_ptr), n_mol, n_atoms, _ptr(tables), T, _ptr(b),
+                                          nf, float(sigma), _ptr(out), out.stride(0), work.data_ptr() + off, wb,
+                                          _stream()))
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -282,6 +282,51 @@ def test_sorf_tensor_core_energy_and_gradient_match_oracle(q, nf, T, n_mol):
     assert q.device_status() == 0
 
 
+def _ragged_molecules(rng, n_mol, big=()):
+    sizes = rng.integers(1, 30, size=n_mol)
+    for i, n in big:
+        sizes[i] = n
+    sizes[[0, n_mol // 2, n_mol - 1]] = 0          # empty first, middle and last molecules
+    return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+
+
+@pytest.mark.parametrize("nf,T,n_mol,big", [(128, 1, 9, ()), (1024, 3, 40, ((5, 300),)),
+                                            (16384, 3, 30, ((3, 129), (7, 200))), (384, 2, 3000, ((11, 700),))])
+def test_sorf_tensor_core_segment_sums_match_oracle(q, nf, T, n_mol, big):
+    """Z on the tensor cores against the FP64 oracle's segment sums: molecules
+    of 1-29 atoms, empty molecules (first, middle, last), molecules spanning
+    two to six 128-atom tiles, up to 150+ CTAs; Z written into a row block of
+    a wider matrix; every row of a molecule identical to the row the same
+    molecule gets in another batch (the sum order does not depend on tiling)."""
+    d = 128
+    rng = np.random.default_rng(17 + nf + n_mol)
+    mol_ptr = _ragged_molecules(rng, n_mol, big)
+    n_atoms = int(mol_ptr[-1])
+    x = (rng.normal(size=(n_atoms, d)) * 0.5).astype(np.float32)
+    signs, b = synth.sorf_draw(rng, nf, d, T)
+    b = b.astype(np.float32)
+    sigma = 1.7
+    W = o_sorf.sorf_matrix(signs, sigma)
+    ref = o_sorf.features(x.astype(np.float64), W, b.astype(np.float64))
+    Zref = o_reg.segment_sum(ref, mol_ptr)
+    sizes = np.diff(mol_ptr)
+    bits = q.pack_signs(signs)
+    tables = q.sorf_tc_tables(bits, T, nf)
+    big_out = torch.full((n_mol, nf + 32), float("nan"), device="cuda")
+    q.sorf_segment_sum_tc(x, mol_ptr, tables, T, b, sigma, out=big_out[:, :nf])
+    Z = big_out[:, :nf].cpu().numpy()
+    assert torch.isnan(big_out[:, nf:]).all()
+    pref = math.sqrt(2 / nf)
+    assert np.all(np.max(np.abs(Z - Zref), axis=1) <= 2e-5 * pref * np.maximum(sizes, 1))
+    assert np.all(Z[sizes == 0] == 0)
+    # the same molecules in a different batch (shifted start, other neighbours)
+    lo = n_mol // 3
+    sub_ptr = (mol_ptr[lo:] - mol_ptr[lo]).astype(np.int32)
+    Zs = q.sorf_segment_sum_tc(x[mol_ptr[lo]:], sub_ptr, tables, T, b, sigma).cpu().numpy()
+    assert np.array_equal(Zs, Z[lo:])
+    assert q.device_status() == 0
+
+
 def test_sorf_tensor_core_tables_are_the_integer_chain(q):
     """The FP16 tables hold M_s = H D_T ... H D_1 exactly (unnormalised
     Hadamard, integer entries), forward [s][i][j] and backward [s][j][i]."""
