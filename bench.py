@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-ef", action="store_true")
     ap.add_argument("--no-periodic", action="store_true")
+    ap.add_argument("--z-kernel", default="fwht", choices=["tc", "fwht"],
+                    help="SORF segment sums Z of training: the in-register fast Walsh-Hadamard kernel (fwht) or "
+                         "the forward chains as tensor-core FP16 products (tc)")
     ap.add_argument("--sorf-kernel", default="tc", choices=["tc", "fwht"],
                     help="SORF energies + gradients of the prediction: both Hadamard chains as tensor-core "
                          "FP16 products (tc) or the in-register fast Walsh-Hadamard kernel (fwht)")
@@ -264,6 +267,9 @@ def workload_config(args, w, world, gram_text, solve_text):
             "sorf_prediction": ("both Hadamard chains as tcgen05 FP16 products (exact FP16 chain tables, "
                                 "two-part operands)" if args.sorf_kernel == "tc"
                                 else "in-register fast Walsh-Hadamard transform (FP32)"),
+            "sorf_training": ("forward chains as tcgen05 FP16 products, ordered molecule sums"
+                              if getattr(args, "z_kernel", "fwht") == "tc"
+                              else "in-register fast Walsh-Hadamard transform (FP32), ordered molecule sums"),
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "inputs larger than L2 (rep 5.5 GB, Z 6.6 GB)",
             "step": "one training (FCHL19 -> projection -> SORF -> Z -> Gram -> factor + PCG) plus E+F "
@@ -573,7 +579,7 @@ def run_ours(args, rank, world):
     model.set_timing(True)          # CUDA events around the prediction's kernels (read per timed step)
     if args.sorf_kernel == "fwht" and model.sorf_tc:
         model.set_sorf_tc(False)
-    pipeline.SORF_TC = args.sorf_kernel == "tc"
+    pipeline.SORF_TC = args.z_kernel == "tc"
     sorf_tc = model.sorf_tc
     del rep, perm, offs
     torch.cuda.synchronize()
@@ -759,7 +765,7 @@ def run_ours(args, rank, world):
                     "mufu": {"achieved": nf * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": exp_rate,
                              "unit": "T op/s", "work": "cos per feature (N_F per atom)",
                              "peak_source": "measured __expf rate (MUFU), qmlr_unit_rates"}}
-                   if sorf_tc else
+                   if pipeline.SORF_TC else
                    {"kernel": "qmlr::sorf_mol_kernel<128> (SORF + segment sum into Z)", "bound": "alu",
                     "achieved": sorf_ops_atom * n_atoms / (st["sorf_Z"] * 1e-3) / 1e12, "peak": fp32_add_peak,
                     "unit": "TFLOP/s",

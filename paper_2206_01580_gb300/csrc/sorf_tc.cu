@@ -776,7 +776,7 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
         for (int kb = 0; kb < 2; ++kb)
           tma_load_2d(sx + p * (X_BYTES / 2) + kb * (X_BYTES / 4), &mapx, xfull, kb * 64, p * a.n_pad + A0 + k * TM);
       last_x = k;
-      for (int j = 0; j < U; ++j) {
+      for (int j = 0; ok && j < U; ++j) {
         const int un = n + j;
         int s = (j >> 1) + s0;
         if (s >= a.n_stack) s -= a.n_stack;
@@ -789,14 +789,14 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
         mbar_expect_tx(&bzfull[bs], UN * 4);
         bulk_load(sbz + bs * UN, a.b + (long)s * D + h * UN, UN * 4, &bzfull[bs]);
         last_bz[bs] = un / zc::NBZ;
+        // the stack's chain tile, one 64-wide K block (all 128 features) per ring slot
         const int st = q % zc::NSZ;
         if (q >= zc::NSZ && !mbar_wait(&bempty[st], (uint32_t)((q / zc::NSZ) - 1) & 1, abort)) {
           ok = false;
           break;
         }
         mbar_expect_tx(&bfull[st], TILE_BYTES);
-        tma_load_2d(sb + st * TILE_BYTES, &mapf, &bfull[st], 0, s * D + h * UN);
-        tma_load_2d(sb + st * TILE_BYTES + TILE_BYTES / 2, &mapf, &bfull[st], 64, s * D + h * UN);
+        tma_load_2d(sb + st * TILE_BYTES, &mapf, &bfull[st], h * 64, s * D);
         last_b[st] = q / zc::NSZ;
         ++q;
       }
@@ -807,7 +807,7 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
     }
   } else if (warp == kEpiWarps + 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    constexpr uint32_t idf = idesc_f16(TM, UN);
+    constexpr uint32_t idf2 = idesc_f16(TM, 2 * UN);
     int q = 0, n = 0;
     bool ok = true;
     for (int k = 0; ok && k < n_tiles; ++k, n += U) {
@@ -815,11 +815,14 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
         ok = false;
         break;
       }
-      for (int j = 0; j < U; ++j) {
+      // one N = 128 product per stack (two units: adjacent accumulators)
+      for (int j = 0; j < U; j += 2) {
         const int un = n + j;
-        const int st = q % zc::NSZ, db = un % NDB;
-        if (!mbar_wait(&bfull[st], (uint32_t)(q / zc::NSZ) & 1, abort) ||
-            (un >= NDB && !mbar_wait(&dempty[db], (uint32_t)((un / NDB) - 1) & 1, abort))) {
+        const int st0 = q % zc::NSZ, st1 = (q + 1) % zc::NSZ, db = un % NDB;
+        if (!mbar_wait(&bfull[st0], (uint32_t)(q / zc::NSZ) & 1, abort) ||
+            !mbar_wait(&bfull[st1], (uint32_t)((q + 1) / zc::NSZ) & 1, abort) ||
+            (un >= NDB && !mbar_wait(&dempty[db], (uint32_t)((un / NDB) - 1) & 1, abort)) ||
+            (un + 1 >= NDB && !mbar_wait(&dempty[db + 1], (uint32_t)(((un + 1) / NDB) - 1) & 1, abort))) {
           ok = false;
           break;
         }
@@ -830,13 +833,15 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
 #pragma unroll
           for (int kk = 0; kk < D / 16; ++kk) {
             const uint64_t da = smem_desc(sx + p * (X_BYTES / 2) + (kk >> 2) * (X_BYTES / 4)) + 2 * (kk & 3);
-            const uint64_t dbd = smem_desc(sb + st * TILE_BYTES + (kk >> 2) * (TILE_BYTES / 2)) + 2 * (kk & 3);
-            mma_bf16(d, da, dbd, idf, (p == 1 && kk == 0) ? 0u : 1u);
+            const uint64_t dbd = smem_desc(sb + ((kk >> 2) ? st1 : st0) * TILE_BYTES) + 2 * (kk & 3);
+            mma_bf16(d, da, dbd, idf2, (p == 1 && kk == 0) ? 0u : 1u);
           }
-        mma_commit(&bempty[st]);
+        mma_commit(&bempty[st0]);
+        mma_commit(&bempty[st1]);
         mma_commit(&dfull[db]);
-        if (j == U - 1) mma_commit(xempty);
-        ++q;
+        mma_commit(&dfull[db + 1]);
+        if (j == U - 2) mma_commit(xempty);
+        q += 2;
       }
     }
     if (!ok) {
@@ -873,8 +878,54 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
       for (int r = r0; r < r1; ++r) sum += cbuf[r * zc::CLD + f];
       return sum;
     };
-    // the reader pass for unit un (local index j of a tile with info tt)
-    auto read_unit = [&](int un, int j, const ZTile& tt) {
+    // this thread's molecules of a tile (row bounds cached per tile): slot 0 the
+    // first molecule (carried in or not) and the one carried out; slots 1.. the
+    // molecules that start and end in the tile, in turn (more than two: bounds
+    // loaded when read)
+    struct ZSlot {
+      int m[2], r0[2], r1[2], cnt;
+      bool more;
+    };
+    auto slot_of = [&](const ZTile& tt) {
+      ZSlot z;
+      z.cnt = 0;
+      z.more = false;
+      if (slot == 0) {
+        z.m[0] = tt.mf;
+        z.r0[0] = max(__ldg(a.mol_ptr + tt.mf), tt.a0) - tt.a0;
+        z.r1[0] = min(__ldg(a.mol_ptr + tt.mf + 1), tt.a1) - tt.a0;
+        z.cnt = 1;
+        if (tt.sout && tt.nm > 1) {
+          z.m[1] = tt.mf + tt.nm - 1;
+          z.r0[1] = __ldg(a.mol_ptr + z.m[1]) - tt.a0;
+          z.r1[1] = tt.a1 - tt.a0;
+          z.cnt = 2;
+        }
+      } else {
+        const int n_own = tt.nm - (tt.sout && tt.nm > 1 ? 1 : 0);   // molecules ending in this tile
+        for (int i = slot; i < n_own; i += zc::kSlots - 1) {
+          if (z.cnt == 2) {
+            z.more = true;
+            break;
+          }
+          const int m = tt.mf + i;
+          z.m[z.cnt] = m;
+          z.r0[z.cnt] = __ldg(a.mol_ptr + m) - tt.a0;
+          z.r1[z.cnt] = __ldg(a.mol_ptr + m + 1) - tt.a0;
+          ++z.cnt;
+        }
+      }
+      return z;
+    };
+    // feature index of a tile's unit j for this reader thread
+    auto feat_of = [&](int j) {
+      int st = (j >> 1) + s0;
+      if (st >= a.n_stack) st -= a.n_stack;
+      return st * D + (j & 1) * UN + f;
+    };
+    // the reader pass for unit un (local index j of a tile with info tt);
+    // cin: the carried sum of the first molecule (prefetched), if tt.sin
+    auto read_unit = [&](int un, int j, const ZTile& tt, const ZSlot& z, float cin) {
       const int cb = un & 1;
       const bool w = mbar_wait(&cfull[cb], (uint32_t)(un >> 1) & 1, abort);
       if (__any_sync(0xffffffffu, !w)) {
@@ -882,26 +933,21 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
         return;
       }
       const float* cbuf = sc + cb * (zc::C_BYTES / 4);
-      int s = (j >> 1) + s0;
-      if (s >= a.n_stack) s -= a.n_stack;
-      const int fi = s * D + (j & 1) * UN + f;
-      const int n_own = tt.nm - (tt.sout && tt.nm > 1 ? 1 : 0);   // molecules ending in this tile
+      const int fi = feat_of(j);
       if (slot == 0) {
-        // first molecule (carried in or not), then the one carried out
-        const int m = tt.mf;
-        const int r0 = max(__ldg(a.mol_ptr + m), tt.a0) - tt.a0, r1 = min(__ldg(a.mol_ptr + m + 1), tt.a1) - tt.a0;
-        const float sum = col_sum(cbuf, r0, r1, tt.sin ? carry[fi] : 0.f);
+        const float sum = col_sum(cbuf, z.r0[0], z.r1[0], tt.sin ? cin : 0.f);
         if (tt.nm == 1 && tt.sout) carry[fi] = sum;
-        else a.Z[(long)m * a.ldz + fi] = a.pref * sum;
-        if (tt.sout && tt.nm > 1) {
-          const int ml = tt.mf + tt.nm - 1;
-          carry[fi] = col_sum(cbuf, __ldg(a.mol_ptr + ml) - tt.a0, tt.a1 - tt.a0, 0.f);
-        }
+        else a.Z[(long)z.m[0] * a.ldz + fi] = a.pref * sum;
+        if (z.cnt == 2) carry[fi] = col_sum(cbuf, z.r0[1], z.r1[1], 0.f);
       } else {
-        for (int i = slot; i < n_own; i += zc::kSlots - 1) {
-          const int m = tt.mf + i;
-          const int r0 = __ldg(a.mol_ptr + m) - tt.a0, r1 = __ldg(a.mol_ptr + m + 1) - tt.a0;
-          a.Z[(long)m * a.ldz + fi] = a.pref * col_sum(cbuf, r0, r1, 0.f);
+        for (int c = 0; c < z.cnt; ++c) a.Z[(long)z.m[c] * a.ldz + fi] = a.pref * col_sum(cbuf, z.r0[c], z.r1[c], 0.f);
+        if (z.more) {
+          const int n_own = tt.nm - (tt.sout && tt.nm > 1 ? 1 : 0);
+          for (int i = slot + 2 * (zc::kSlots - 1); i < n_own; i += zc::kSlots - 1) {
+            const int m = tt.mf + i;
+            const int r0 = __ldg(a.mol_ptr + m) - tt.a0, r1 = __ldg(a.mol_ptr + m + 1) - tt.a0;
+            a.Z[(long)m * a.ldz + fi] = a.pref * col_sum(cbuf, r0, r1, 0.f);
+          }
         }
       }
       __syncwarp();
@@ -909,11 +955,16 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
     };
     int n = 0;
     ZTile prev{};
+    ZSlot zprev{};
     for (int k = 0; ok && k < n_tiles; ++k, n += U) {
       const ZTile tt = z_tile(a.mol_ptr, a.n_mol, A0, A1, M0, M1, k, n_tiles);
+      const ZSlot zs = slot_of(tt);
       const float cs = a.cscale * __ldg(a.kx + tt.a0 + row);   // a0 + row < n_pad
       for (int j = 0; j < U; ++j) {
         const int un = n + j;
+        // the carried sum the reader of unit un - 1 needs, loaded ahead of the writer work
+        const ZTile& tr = j > 0 ? tt : prev;
+        const float cin = (un > 0 && slot == 0 && tr.sin) ? carry[feat_of(j > 0 ? j - 1 : U - 1)] : 0.f;
         const int db = un % NDB, bs = un % zc::NBZ, cb = un & 1;
         bool w = mbar_wait(&dfull[db], (uint32_t)(un / NDB) & 1, abort);
         if (__any_sync(0xffffffffu, !w)) {
@@ -955,13 +1006,14 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
         __syncwarp();
         if (lane == 0) mbar_arrive(&cfull[cb]);
         if (un > 0) {
-          read_unit(un - 1, j > 0 ? j - 1 : U - 1, j > 0 ? tt : prev);
+          read_unit(un - 1, j > 0 ? j - 1 : U - 1, tr, j > 0 ? zs : zprev, cin);
           if (!ok) break;
         }
       }
       prev = tt;
+      zprev = zs;
     }
-    if (ok && n_tiles > 0) read_unit(n - 1, U - 1, prev);
+    if (ok && n_tiles > 0) read_unit(n - 1, U - 1, prev, zprev, slot == 0 && prev.sin ? carry[feat_of(U - 1)] : 0.f);
   }
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1104,7 +1156,7 @@ int sorf_tc_segment_sum(const float* x, int n_atoms, const int32_t* mol_ptr, int
   CUtensorMap mx, mapf;
   int rc;
   if ((rc = make_map(&mx, xh, D, 2L * n_pad, TM))) return rc;
-  if ((rc = make_map(&mapf, tables, D, (long)n_stack * D, UN))) return rc;
+  if ((rc = make_map(&mapf, tables, D, (long)n_stack * D, TM))) return rc;
   ZArgs a;
   a.kx = kx;
   a.b = b;

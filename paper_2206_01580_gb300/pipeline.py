@@ -40,9 +40,12 @@ class Batch:
                      int(np.diff(mol_ptr).max()) if len(mol_ptr) > 1 else 1)
 
 
-# SORF energy rows on the tensor cores (d = 128, T <= 3) or with the in-register
-# fast Walsh-Hadamard kernel
-SORF_TC = True
+# SORF energy rows Z on the tensor cores (qmlr_sorf_segment_sum_tc; d = 128,
+# T <= 3) instead of the in-register fast Walsh-Hadamard kernel (qmlr_sorf,
+# PER_MOL). Off by default: on the QM9-shaped workload both take 38 ms, the
+# tensor-core form bound by its epilogue (cos and the ordered molecule sums),
+# not by the products.
+SORF_TC = False
 
 
 @dataclass
