@@ -714,8 +714,12 @@ int qmlr_model_set_alpha_device(qmlr_model* m, const double* alpha, void* stream
  * Which kernel computes the SORF energies and gradients of qmlr_predict_ef
  * with forces: the tensor-core chains (qmlr_sorf_grad_tc; the default when
  * the model has d = 128 and T <= 3, tables built at model creation) or the
- * FWHT kernel of qmlr_sorf_grad (enable = 0). Enabling it on a model without
- * tables returns QMLR_EINVAL. Energy-only predictions use the FWHT kernel.
+ * FWHT kernel of qmlr_sorf_grad (enable = 0). Batches below 8192 atoms and
+ * energy-only predictions always use the FWHT kernel (the tensor-core form
+ * takes a fixed ~0.4 ms per 128-atom tile at N_F = 16384). Results are
+ * bitwise independent of the batch a molecule is in within each form; the
+ * two forms agree to the parity bounds. Enabling it on a model without tables
+ * returns QMLR_EINVAL.
  */
 int qmlr_model_set_sorf_tc(qmlr_model* m, int32_t enable);
 int32_t qmlr_model_sorf_tc(const qmlr_model* m);

@@ -18,6 +18,9 @@
 
 namespace qmlr {
 
+// smallest batch (atoms) whose SORF energies + gradients run on the tensor cores
+constexpr int kSorfTcMinAtoms = 8192;
+
 void PredictWorkspace::release() {
   cudaFree(atom_e);
   cudaFree(pair_ptr);
@@ -121,7 +124,9 @@ int predict_from_features_ws(const qmlr_model* m, PredictWorkspace& w, const flo
   if (m->timing) QMLR_CUDA_TRY(cudaEventRecord(m->tev[3], s));
   // gradient partials: one per 128-stack part of the FWHT kernel, one of the tensor-core kernel
   int g_parts = m->n_part;
-  if (forces && m->sorf_tc) {
+  // the tensor-core form walks a 128-atom tile's 2 N_F/128 half stacks in one CTA
+  // (~0.4 ms at N_F = 16384): small batches are faster on the FWHT kernel
+  if (forces && m->sorf_tc && n_atoms >= kSorfTcMinAtoms) {
     if ((rc = sorf_tc_energy_grad(w.x, n_atoms, m->sorf_tables, m->T, m->b, m->alpha, m->n_features, m->sigma,
                                   w.atom_e, w.gx, w.sorf_work, w.sorf_work_bytes, s)))
       return rc;

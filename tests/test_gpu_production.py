@@ -81,6 +81,48 @@ def test_predict_ef_production_config_5_to_200_atoms(q):
     assert np.abs(F_ref[big]).max() > 1.0
 
 
+def test_predict_ef_tensor_core_sorf_on_a_large_batch(q):
+    """Batches of >= 8192 atoms take the tensor-core SORF energies + gradients:
+    twelve shuffled copies of the 5-200-atom set (~9.6 k atoms) against the
+    oracle (same bounds), against the FWHT kernel of the same model, and every
+    copy of a molecule bitwise equal to the others (the result does not depend
+    on the molecule's place in the batch)."""
+    base = sizes_5_to_200()
+    nb = base.sizes()
+    po = o_fchl19.params("EF", n2=24, n3=22)
+    reps = o_fchl19.representation_batch(base.coords, base.elem, base.mol_ptr, po)
+    U = o_reg.pca_bases(reps, base.elem, 5, D).astype(np.float32)
+    rng = np.random.default_rng(6)
+    signs, b = synth.sorf_draw(rng, NF, D, T)
+    b = b.astype(np.float32)
+    alpha = rng.normal(size=NF).astype(np.float32)
+    om = o_model.sorf_model(po, U.astype(np.float64), signs, b.astype(np.float64), SIGMA, alpha.astype(np.float64))
+    E_ref, F_ref = o_model.energies_forces(base.coords, base.elem, base.mol_ptr, om)
+    order = np.random.default_rng(7).permutation(np.tile(np.arange(base.n_mol), 12))
+    mols = synth.concat([base.molecule(int(i)) for i in order])
+    assert mols.n_atoms >= 8192
+    m = q.Model(gpu_params("EF"), int(nb.max()), U, signs, T, b, SIGMA, alpha)
+    assert m.sorf_tc
+    E, F = (t.cpu().numpy() for t in m.predict(mols.coords, mols.elem, mols.mol_ptr))
+    m.set_sorf_tc(False)
+    E2, F2 = (t.cpu().numpy() for t in m.predict(mols.coords, mols.elem, mols.mol_ptr))
+    assert q.device_status() == 0
+    m.close()
+    ptr = mols.mol_ptr
+    first = {}
+    for k, i in enumerate(order):
+        a, e = int(ptr[k]), int(ptr[k + 1])
+        ra, re_ = int(base.mol_ptr[i]), int(base.mol_ptr[i + 1])
+        assert abs(E[k] - E_ref[i]) <= 1e-4 * nb[i]
+        assert np.max(np.abs(F[a:e] - F_ref[ra:re_])) <= 1e-3
+        assert abs(E[k] - E2[k]) <= 1e-4 * nb[i] and np.max(np.abs(F[a:e] - F2[a:e])) <= 1e-3
+        if i in first:
+            k0, a0, e0 = first[i]
+            assert E[k] == E[k0] and np.array_equal(F[a:e], F[a0:e0])
+        else:
+            first[i] = (k, a, e)
+
+
 def test_force_rows_production_config_3bpa_shaped(q):
     from paper_2206_01580_gb300 import pipeline
     w = synth.workload(3, scale=0.004)                  # two 27-atom conformations
