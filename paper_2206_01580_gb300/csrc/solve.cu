@@ -384,16 +384,17 @@ __device__ __forceinline__ float2 pair_rsqrt(float2 d) {
 
 // Factor of the diagonal block (float pairs on entry). Row i of the block stays
 // in the registers of threads 4i..4i+3 (thread q holds columns 4k + q). Step j:
-// the holder of the pivot forms 1/L_jj = 1/sqrt(d) (pair_rsqrt) and L_jj;
-// the column below is scaled by 1/L_jj and published in shared memory; every row
-// i > j then subtracts L_ij L_lj from its columns j < l <= i (blocks of four
-// columns already done are skipped warp-uniformly). Two barriers per step.
-// Writes L_kk in FP64 to L, and its pairs and the pivots' reciprocals (pairs)
-// to dpairs ([64][64] then [64]) for the panel solve.
+// the holder of the pivot forms 1/L_jj = 1/sqrt(d) (pair_rsqrt) and L_jj while
+// the holders of column j publish it unscaled in shared memory; after one
+// barrier every row i > j scales its own entry and subtracts L_ij L_lj from its
+// columns j < l <= i (blocks of four columns already done are skipped; the 64
+// steps are unrolled, so every register index is static). Writes L_kk in FP64
+// to L, and its pairs and the pivots' reciprocals (pairs) to dpairs ([64][64]
+// then [64]) for the panel solve.
 __global__ void __launch_bounds__(256, 1)
 potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, int* info,
                      float2* __restrict__ dpairs) {
-  __shared__ float2 colj[NB];
+  __shared__ float2 craw[2][NB];   // column j before scaling, by step parity
   __shared__ float2 ys[NB];
   const int tid = threadIdx.x;
   const int row = tid >> 2, q = tid & 3;
@@ -404,50 +405,43 @@ potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err,
     x[k] = (row < nb && c <= row) ? *reinterpret_cast<const float2*>(L + (long)(k0 + row) * ldl + k0 + c)
                                   : make_float2(c == row ? 1.f : 0.f, 0.f);
   }
+  // Step j, one barrier: the holders of column j publish it unscaled and the
+  // pivot's holder forms y = 1/L_jj; after the barrier every row i > j takes
+  // L_ij = a_ij y and t = L_ij y, and subtracts t a_lj (= L_ij L_lj) from its
+  // columns j < l <= i.
+#pragma unroll
   for (int j = 0; j < NB; ++j) {
     const int m = j >> 2, jq = j & 3;
-    if (row == j && q == jq) {   // pivot
-      float2 dp = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < NB / 4; ++k)
-        if (k == m) dp = x[k];
-      float2 d = pair_add(dp, make_float2(0.f, 0.f));
-      if (!(d.x > 0.f)) {
-        if (j < nb) {
-          record_device_error(err, DEV_NOT_SPD);
-          if (info && *info == 0) *info = k0 + j + 1;
+    if (q == jq && row >= j) {
+      if (row == j) {   // pivot
+        float2 d = pair_add(x[m], make_float2(0.f, 0.f));
+        if (!(d.x > 0.f)) {
+          if (j < nb) {
+            record_device_error(err, DEV_NOT_SPD);
+            if (info && *info == 0) *info = k0 + j + 1;
+          }
+          d = make_float2(1.f, 0.f);
         }
-        d = make_float2(1.f, 0.f);
+        const float2 y = pair_rsqrt(d);
+        x[m] = pair_mul(d, y);
+        ys[j] = y;
+      } else {
+        craw[j & 1][row] = x[m];
       }
-      const float2 y = pair_rsqrt(d);
-      const float2 ljj = pair_mul(d, y);
-#pragma unroll
-      for (int k = 0; k < NB / 4; ++k)
-        if (k == m) x[k] = ljj;
-      ys[j] = y;
-    }
-    __syncthreads();
-    if (row > j && q == jq) {   // column j below the pivot
-      float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < NB / 4; ++k)
-        if (k == m) v = x[k];
-      v = pair_mul(v, ys[j]);
-#pragma unroll
-      for (int k = 0; k < NB / 4; ++k)
-        if (k == m) x[k] = v;
-      colj[row] = v;
     }
     __syncthreads();
     if (row > j) {
-      const float2 a = colj[row];
+      const float2 y = ys[j];
+      const float2 lij = pair_mul(craw[j & 1][row], y);
+      const float2 t = pair_mul(lij, y);
+      if (q == jq) x[m] = lij;
 #pragma unroll
       for (int k = 0; k < NB / 4; ++k) {
-        if (4 * k + 3 <= j) continue;   // uniform: columns 4k..4k+3 all done
+        if (4 * k + 3 <= j) continue;   // columns 4k..4k+3 all done
         const int l = 4 * k + q;
         if (l > j && l <= row) {
-          const float2 b = colj[l];
-          df_fma(x[k].x, x[k].y, -a.x, -a.y, b.x, b.y);
+          const float2 b = craw[j & 1][l];
+          df_fma(x[k].x, x[k].y, -t.x, -t.y, b.x, b.y);
         }
       }
     }
@@ -465,48 +459,50 @@ potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err,
 
 // Panel solve as trsm_panel_kernel, on the float pairs of rows [k0+nb, n) of the
 // block column, with L_kk and 1/L_jj as pairs from potrf_diag_df_kernel. A row's
-// 64 values stay in the registers of its four threads (thread q holds columns
-// 4k + q); at step j the owner of column j forms x_j, the row's threads get it
-// by a shuffle and update their columns l > j (blocks of four columns already
-// solved are skipped warp-uniformly). Writes the FP64 entries to L and, with lp
-// set, the pairs (lp[r - k0 - nb][0:64]).
+// 64 values stay in the registers of its eight threads (thread q holds columns
+// 8k + q); at step j the owner of column j forms x_j, the row's threads get it
+// by a shuffle and update their columns l > j (the 64 steps are unrolled, so
+// register indices and the skipped column blocks are static). 32 rows per CTA.
+// Writes the FP64 entries to L and, with lp set, the pairs
+// (lp[r - k0 - nb][0:64]).
+constexpr int kTrsmDfTpr = 8;                       // threads per row
+constexpr int kTrsmDfRows = 256 / kTrsmDfTpr;       // rows per CTA
+constexpr int kTrsmDfCols = NB / kTrsmDfTpr;        // columns per thread
+
 __global__ void __launch_bounds__(256, 2)
 trsm_panel_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n,
                      const float2* __restrict__ dpairs, float2* __restrict__ lp) {
+  constexpr int TPR = kTrsmDfTpr, NC = kTrsmDfCols;
   extern __shared__ float2 psm[];
   float2 (*lkk)[NB + 1] = reinterpret_cast<float2 (*)[NB + 1]>(psm);
   float2* rdg = psm + NB * (NB + 1);
   const int tid = threadIdx.x, lane = tid & 31;
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) lkk[idx / NB][idx % NB] = dpairs[idx];
   if (tid < NB) rdg[tid] = dpairs[NB * NB + tid];
-  const int row = tid >> 2, q = tid & 3;
-  const int r = k0 + nb + blockIdx.x * kTrsmRows + row;
-  float2 x[NB / 4];
+  const int row = tid / TPR, q = tid % TPR;
+  const int r = k0 + nb + blockIdx.x * kTrsmDfRows + row;
+  float2 x[NC];
 #pragma unroll
-  for (int k = 0; k < NB / 4; ++k) {
-    const int c = 4 * k + q;
+  for (int k = 0; k < NC; ++k) {
+    const int c = TPR * k + q;
     x[k] = (r < n && c < nb) ? *reinterpret_cast<const float2*>(L + (long)r * ldl + k0 + c) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int j = 0; j < NB; ++j) {
-    const int m = j >> 2, jq = j & 3;
-    float2 xj = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < NB / 4; ++k)
-      if (k == m) xj = x[k];
+  for (int j = 0; j < NB; ++j) {
+    const int m = j / TPR, jq = j % TPR;
+    float2 xj = x[m];
     if (q == jq) {
       xj = pair_mul(xj, rdg[j]);
-#pragma unroll
-      for (int k = 0; k < NB / 4; ++k)
-        if (k == m) x[k] = xj;
+      x[m] = xj;
     }
-    const int src = (lane & ~3) | jq;
+    const int src = (lane & ~(TPR - 1)) | jq;
     xj.x = __shfl_sync(0xffffffffu, xj.x, src);
     xj.y = __shfl_sync(0xffffffffu, xj.y, src);
 #pragma unroll
-    for (int k = 0; k < NB / 4; ++k) {
-      if (4 * k + 3 <= j) continue;   // uniform: columns 4k..4k+3 all solved
-      const int l = 4 * k + q;
+    for (int k = 0; k < NC; ++k) {
+      if (TPR * k + TPR - 1 <= j) continue;   // columns TPR k .. TPR k + TPR - 1 all solved
+      const int l = TPR * k + q;
       if (l > j) {
         const float2 v = lkk[l][j];
         df_fma(x[k].x, x[k].y, -xj.x, -xj.y, v.x, v.y);
@@ -514,8 +510,8 @@ trsm_panel_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int n,
     }
   }
 #pragma unroll
-  for (int k = 0; k < NB / 4; ++k) {
-    const int c = 4 * k + q;
+  for (int k = 0; k < NC; ++k) {
+    const int c = TPR * k + q;
     if (r >= n) break;
     const float2 v = pair_add(x[k], make_float2(0.f, 0.f));
     if (c < nb) L[(long)r * ldl + k0 + c] = pair_value(v);
@@ -1461,7 +1457,7 @@ static int cholesky_mixed_locked(double* L, long ldl, int n, __nv_bfloat16* part
       const int rows = n - c0 - nb;
       if (rows <= 0) break;
       const int cblocks = (k0 + w - (c0 + nb) + NB - 1) / NB;   // panel columns still to update
-      trsm_panel_df_kernel<<<(rows + kTrsmRows - 1) / kTrsmRows, 256, kTrsmDfSmem, p>>>(
+      trsm_panel_df_kernel<<<(rows + kTrsmDfRows - 1) / kTrsmDfRows, 256, kTrsmDfSmem, p>>>(
           L, ldl, c0, nb, n, dpairs, cblocks > 0 ? lp : nullptr);
       QMLR_LAUNCH_CHECK();
       if (cblocks > 0) {
