@@ -387,8 +387,8 @@ __device__ __forceinline__ float2 pair_rsqrt(float2 d) {
 // the holder of the pivot forms 1/L_jj = 1/sqrt(d) (pair_rsqrt) and L_jj while
 // the holders of column j publish it unscaled in shared memory; after one
 // barrier every row i > j scales its own entry and subtracts L_ij L_lj from its
-// columns j < l <= i (blocks of four columns already done are skipped; the 64
-// steps are unrolled, so every register index is static). Writes L_kk in FP64
+// columns j < l <= i (blocks of four columns already done are skipped
+// warp-uniformly). Writes L_kk in FP64
 // to L, and its pairs and the pivots' reciprocals (pairs) to dpairs ([64][64]
 // then [64]) for the panel solve.
 __global__ void __launch_bounds__(256, 1)
@@ -408,13 +408,17 @@ potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err,
   // Step j, one barrier: the holders of column j publish it unscaled and the
   // pivot's holder forms y = 1/L_jj; after the barrier every row i > j takes
   // L_ij = a_ij y and t = L_ij y, and subtracts t a_lj (= L_ij L_lj) from its
-  // columns j < l <= i.
-#pragma unroll
+  // columns j < l <= i. (Not unrolled: one CTA runs this, and the unrolled
+  // body outgrows the instruction cache.)
   for (int j = 0; j < NB; ++j) {
     const int m = j >> 2, jq = j & 3;
     if (q == jq && row >= j) {
+      float2 xm = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < NB / 4; ++k)
+        if (k == m) xm = x[k];
       if (row == j) {   // pivot
-        float2 d = pair_add(x[m], make_float2(0.f, 0.f));
+        float2 d = pair_add(xm, make_float2(0.f, 0.f));
         if (!(d.x > 0.f)) {
           if (j < nb) {
             record_device_error(err, DEV_NOT_SPD);
@@ -423,10 +427,13 @@ potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err,
           d = make_float2(1.f, 0.f);
         }
         const float2 y = pair_rsqrt(d);
-        x[m] = pair_mul(d, y);
+        const float2 ljj = pair_mul(d, y);
+#pragma unroll
+        for (int k = 0; k < NB / 4; ++k)
+          if (k == m) x[k] = ljj;
         ys[j] = y;
       } else {
-        craw[j & 1][row] = x[m];
+        craw[j & 1][row] = xm;
       }
     }
     __syncthreads();
@@ -434,7 +441,11 @@ potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err,
       const float2 y = ys[j];
       const float2 lij = pair_mul(craw[j & 1][row], y);
       const float2 t = pair_mul(lij, y);
-      if (q == jq) x[m] = lij;
+      if (q == jq) {
+#pragma unroll
+        for (int k = 0; k < NB / 4; ++k)
+          if (k == m) x[k] = lij;
+      }
 #pragma unroll
       for (int k = 0; k < NB / 4; ++k) {
         if (4 * k + 3 <= j) continue;   // columns 4k..4k+3 all done
@@ -1268,49 +1279,11 @@ ztmv_partial_kernel(const float* __restrict__ Z, long n_rows, int n_features, lo
   part[(long)blockIdx.y * n_features + f] = acc;
 }
 
-// The same partial sums with four consecutive features per thread (16-byte
-// loads of Z: the memory-bound pass reads each row segment as float4);
-// requires n_features and ldz multiples of 4 and a 16-byte aligned Z. Each
-// feature's terms are added in the same order as in ztmv_partial_kernel.
-__global__ void ztmv4_partial_kernel(const float* __restrict__ Z, long n_rows, int n_features, long ldz,
-                     const float* __restrict__ th, const float* __restrict__ tl, double* __restrict__ part) {
-  const int f4 = blockIdx.x * blockDim.x + threadIdx.x;
-  const long r0 = (long)blockIdx.y * kZtRows;
-  const long r1 = min(n_rows, r0 + kZtRows);
-  if (4 * f4 >= n_features) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const float4* Z4 = reinterpret_cast<const float4*>(Z);
-  const long ld4 = ldz / 4;
-  for (long rb = r0; rb < r1; rb += kFold) {
-    const long re = min(r1, rb + (long)kFold);
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (long r = rb; r < re; ++r) {
-      const float4 z = __ldg(Z4 + r * ld4 + f4);
-      const float h = __ldg(th + r), l = __ldg(tl + r);
-      dot2_step(z.x, h, l, s[0], c[0]);
-      dot2_step(z.y, h, l, s[1], c[1]);
-      dot2_step(z.z, h, l, s[2], c[2]);
-      dot2_step(z.w, h, l, s[3], c[3]);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] += fold2(s[k], c[k]);
-  }
-  double* o = part + (long)blockIdx.y * n_features + 4 * f4;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) o[k] = acc[k];
-}
-
-// Z^T t partial sums ([parts][n]) with the 16-byte form when the layout allows it.
+// Z^T t partial sums ([parts][n]).
 static void ztmv_launch(const float* Z, long n_rows, int n, long ldz, const float* th, const float* tl,
                         double* part, int parts, cudaStream_t s) {
-  if (n % 4 == 0 && ldz % 4 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0) {
-    dim3 grid((n / 4 + 255) / 256, parts);
-    ztmv4_partial_kernel<<<grid, 256, 0, s>>>(Z, n_rows, n, ldz, th, tl, part);
-  } else {
-    dim3 grid((n + 255) / 256, parts);
-    ztmv_partial_kernel<<<grid, 256, 0, s>>>(Z, n_rows, n, ldz, th, tl, part);
-  }
+  dim3 grid((n + 255) / 256, parts);
+  ztmv_partial_kernel<<<grid, 256, 0, s>>>(Z, n_rows, n, ldz, th, tl, part);
 }
 
 // (p and q may be the same vector: each thread reads p[f] before it writes q[f])
