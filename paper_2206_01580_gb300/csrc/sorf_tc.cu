@@ -621,7 +621,7 @@ constexpr int TMEM_COLS = 256;
 constexpr int kSlots = kEpiWarps * 32 / UN;   // molecule slots of the reader threads
 static_assert(SMEM_BYTES <= 227 * 1024, "shared-memory budget");
 static_assert(NDB * UN <= TMEM_COLS, "TMEM budget");
-static_assert(kSlots >= 2, "reader slots");
+static_assert(kSlots >= 3, "reader slots");
 }  // namespace zc
 
 struct ZArgs {
@@ -879,9 +879,9 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
       return sum;
     };
     // this thread's molecules of a tile (row bounds cached per tile): slot 0 the
-    // first molecule (carried in or not) and the one carried out; slots 1.. the
-    // molecules that start and end in the tile, in turn (more than two: bounds
-    // loaded when read)
+    // first molecule (carried in or not), the last slot the one carried out,
+    // the slots between the molecules that start and end in the tile, in turn
+    // (more than two: bounds loaded when read)
     struct ZSlot {
       int m[2], r0[2], r1[2], cnt;
       bool more;
@@ -895,15 +895,16 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
         z.r0[0] = max(__ldg(a.mol_ptr + tt.mf), tt.a0) - tt.a0;
         z.r1[0] = min(__ldg(a.mol_ptr + tt.mf + 1), tt.a1) - tt.a0;
         z.cnt = 1;
+      } else if (slot == zc::kSlots - 1) {
         if (tt.sout && tt.nm > 1) {
-          z.m[1] = tt.mf + tt.nm - 1;
-          z.r0[1] = __ldg(a.mol_ptr + z.m[1]) - tt.a0;
-          z.r1[1] = tt.a1 - tt.a0;
-          z.cnt = 2;
+          z.m[0] = tt.mf + tt.nm - 1;
+          z.r0[0] = __ldg(a.mol_ptr + z.m[0]) - tt.a0;
+          z.r1[0] = tt.a1 - tt.a0;
+          z.cnt = 1;
         }
       } else {
         const int n_own = tt.nm - (tt.sout && tt.nm > 1 ? 1 : 0);   // molecules ending in this tile
-        for (int i = slot; i < n_own; i += zc::kSlots - 1) {
+        for (int i = slot; i < n_own; i += zc::kSlots - 2) {
           if (z.cnt == 2) {
             z.more = true;
             break;
@@ -938,12 +939,15 @@ sorf_z_tc_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant
         const float sum = col_sum(cbuf, z.r0[0], z.r1[0], tt.sin ? cin : 0.f);
         if (tt.nm == 1 && tt.sout) carry[fi] = sum;
         else a.Z[(long)z.m[0] * a.ldz + fi] = a.pref * sum;
-        if (z.cnt == 2) carry[fi] = col_sum(cbuf, z.r0[1], z.r1[1], 0.f);
+      } else if (slot == zc::kSlots - 1) {
+        // the molecule carried out: read back by slot 0 of this feature one tile
+        // later (the mbarrier phases in between order the accesses)
+        if (z.cnt == 1) carry[fi] = col_sum(cbuf, z.r0[0], z.r1[0], 0.f);
       } else {
         for (int c = 0; c < z.cnt; ++c) a.Z[(long)z.m[c] * a.ldz + fi] = a.pref * col_sum(cbuf, z.r0[c], z.r1[c], 0.f);
         if (z.more) {
           const int n_own = tt.nm - (tt.sout && tt.nm > 1 ? 1 : 0);
-          for (int i = slot + 2 * (zc::kSlots - 1); i < n_own; i += zc::kSlots - 1) {
+          for (int i = slot + 2 * (zc::kSlots - 2); i < n_own; i += zc::kSlots - 2) {
             const int m = tt.mf + i;
             const int r0 = __ldg(a.mol_ptr + m) - tt.a0, r1 = __ldg(a.mol_ptr + m + 1) - tt.a0;
             a.Z[(long)m * a.ldz + fi] = a.pref * col_sum(cbuf, r0, r1, 0.f);
