@@ -197,6 +197,7 @@ proj_tc_kernel(const __grid_constant__ CUtensorMap bmap, Args a) {
     }
     // ---------------- drain: rows quarter*32.., columns half*64..
     const int quarter = warp & 3, half = warp >> 2;
+    const bool vec_out = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0);
     const bool done = ok && mbar_wait(accf, 0, abort);
     if (__any_sync(0xffffffffu, !done)) {
       if (lane == 0) {
@@ -216,11 +217,19 @@ proj_tc_kernel(const __grid_constant__ CUtensorMap bmap, Args a) {
         tmem_ld16(tmem + lane_base + BN + col, v1);
         if (orow >= 0) {
           float* dst = a.C + (long)orow * a.ldc + n0 + col;
+          if (vec_out && n0 + col + 16 <= a.N) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + col + j;
-            if (n < a.N) dst[j] = v0[j] + v1[j];
-            else if (n < a.zero_pad_to) dst[j] = 0.f;
+            for (int j = 0; j < 4; ++j)
+              d4[j] = make_float4(v0[4 * j] + v1[4 * j], v0[4 * j + 1] + v1[4 * j + 1], v0[4 * j + 2] + v1[4 * j + 2],
+                                  v0[4 * j + 3] + v1[4 * j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = n0 + col + j;
+              if (n < a.N) dst[j] = v0[j] + v1[j];
+              else if (n < a.zero_pad_to) dst[j] = 0.f;
+            }
           }
         }
       }
@@ -377,6 +386,7 @@ proj_tc_resident_kernel(const __grid_constant__ CUtensorMap bmap, Args a) {
     mbar_arrive(aready);
     // ---------------- drain: one column tile per accumulator use
     const int quarter = warp & 3, half = warp >> 2;
+    const bool vec_out = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0);
     const int rr = quarter * 32 + lane;
     const int orow = rows[rr];
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
@@ -400,11 +410,19 @@ proj_tc_resident_kernel(const __grid_constant__ CUtensorMap bmap, Args a) {
         tmem_ld16(tmem + lane_base + buf * BN + col, v);
         if (orow >= 0) {
           float* dst = a.C + (long)orow * a.ldc + n0 + col;
+          if (vec_out && n0 + col + 16 <= a.N) {
+            // whole chunk inside the output: four 16-byte stores (a scalar store
+            // per element made one L2 write request per element)
+            float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + col + j;
-            if (n < a.N) dst[j] = v[j];
-            else if (n < a.zero_pad_to) dst[j] = 0.f;
+            for (int j = 0; j < 4; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = n0 + col + j;
+              if (n < a.N) dst[j] = v[j];
+              else if (n < a.zero_pad_to) dst[j] = 0.f;
+            }
           }
         }
       }
