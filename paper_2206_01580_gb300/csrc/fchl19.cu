@@ -24,7 +24,7 @@ constexpr int kWarpsVjp = 4;
 
 struct Fchl19Consts {
   int n_el, n2, n3, rep_dim, base3;
-  float rcut, rcut2, pi_over_rcut;
+  float rcut, rcut2, pi_over_rcut, inv_rcut;
   float eta2, eta3, N2, N3;
   float w3;          // c3 * sqrt(eta3/pi)
   float ang2;        // 2 exp(-zeta^2/2): G^cos = ang2 cos(th), G^sin = ang2 sin(th) for n = 1
@@ -42,6 +42,7 @@ static Fchl19Consts make_consts(const qmlr_fchl19_params& p) {
   c.rcut = (float)p.rcut;
   c.rcut2 = (float)(p.rcut * p.rcut);
   c.pi_over_rcut = (float)(M_PI / p.rcut);
+  c.inv_rcut = (float)(1.0 / p.rcut);
   c.eta2 = (float)p.eta2;
   c.eta3 = (float)p.eta3;
   c.N2 = (float)p.N2;
@@ -306,15 +307,39 @@ __device__ __forceinline__ float lg2_approx(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
-// Per-warp shared memory of the register kernel: neighbour data and one chunk of triplets.
+// Per-warp shared memory of the register kernel: neighbour data and one block
+// of triplets, sorted by element-pair type.
+constexpr int kPairBlock = 256;   // neighbour pairs staged per walk (8 rounds of 32 lanes)
 struct RegWarp {
   float4* nb_u;   // [mxp] unit vector i->j, r_ij
   float4* nb_2b;  // [mxp] mu, log2(e)/(2 s^2), two-body prefactor, f_cut(r_ij)
-  float4* pairs;  // [32] w G^cos, w G^sin, xbar, pair index (bits)
+  float4* pairs;  // [kPairBlock] w G^cos, w G^sin, xbar, 0 (the block's triplets, by type)
+  int* run;       // [16] first entry of each type's run in `pairs` (entry 15: end of type 14)
   int* nb_el;     // [mxp]
 };
-__host__ __device__ __forceinline__ size_t reg_warp_bytes(int mxp) { return (size_t)mxp * 36 + 512; }
+__host__ __device__ __forceinline__ size_t reg_warp_bytes(int mxp) {
+  return (size_t)mxp * 36 + (size_t)kPairBlock * 16 + 64;
+}
+__device__ __forceinline__ RegWarp carve_reg(char* base, int mxp) {
+  RegWarp s;
+  s.nb_u = reinterpret_cast<float4*>(base);
+  s.nb_2b = s.nb_u + mxp;
+  s.pairs = s.nb_2b + mxp;
+  s.run = reinterpret_cast<int*>(s.pairs + kPairBlock);
+  s.nb_el = s.run + 16;
+  return s;
+}
 __host__ __device__ __forceinline__ int reg_stage_atoms(int mx, int range) { return range + 2 * (mx - 1); }
 
 
@@ -340,16 +365,35 @@ __device__ __forceinline__ BinConsts bin_consts(const Fchl19Consts& c, int lane)
 // from the centre, r2 = its squared length (0 < r2 < rcut^2), element e.
 __device__ __forceinline__ void store_neighbour(const RegWarp& s, int slot, float dx, float dy, float dz, float r2,
                                                 int e, const Fchl19Consts& c) {
-  const float r = sqrtf(r2);
-  const float inv = 1.0f / r;
+  const float inv = rsqrt_approx(r2);
+  const float r = r2 * inv;
   s.nb_u[slot] = make_float4(dx * inv, dy * inv, dz * inv, r);
   s.nb_el[slot] = e;
-  const float fc = cutoff_f(r, c);
+  const float fc = 0.5f * (cospif(r * c.inv_rcut) + 1.0f);   // r < rcut
   const float s2 = log1pf(c.eta2 * inv * inv);   // sigma^2 = ln(1 + eta2 / r^2)
-  s.nb_2b[slot] = make_float4(logf(r) - 0.5f * s2,                        // mu = ln(r / sqrt(1 + eta2/r^2))
-                              kLog2e * 0.5f / s2,                        // log2(e) / (2 sigma^2)
-                              fc * expf(-c.N2 * logf(r)) * c.inv_sqrt_2pi * rsqrtf(s2),
+  const float lr = logf(r);
+  s.nb_2b[slot] = make_float4(lr - 0.5f * s2,                              // mu = ln(r / sqrt(1 + eta2/r^2))
+                              kLog2e * 0.5f / s2,                          // log2(e) / (2 sigma^2)
+                              fc * ex2_approx(-c.N2 * kLog2e * lr) * c.inv_sqrt_2pi * rsqrtf(s2),
                               fc);
+}
+
+// Flat index q over the pairs (j < k) of n items, row-major: the row from an
+// approximate square root, then one correction step each way.
+__device__ __forceinline__ void decode_pair_fast(int q, int n, int& j, int& k) {
+  const float t = (float)(2 * n - 1);
+  float sq;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(fmaf(t, t, -8.0f * (float)q)));
+  int jj = max(0, min((int)((t - sq) * 0.5f), n - 2));
+  if (jj * (2 * n - jj - 1) / 2 > q) --jj;
+  else if ((jj + 1) * (2 * n - jj - 2) / 2 <= q) ++jj;
+  j = jj;
+  k = q - jj * (2 * n - jj - 1) / 2 + jj + 1;
+}
+
+// Lanes whose 4-bit type equals t, from the ballots b0..b3 of the types' bits.
+__device__ __forceinline__ unsigned type_lanes(int t, unsigned b0, unsigned b1, unsigned b2, unsigned b3) {
+  return ((t & 1) ? b0 : ~b0) & ((t & 2) ? b1 : ~b1) & ((t & 4) ? b2 : ~b2) & ((t & 8) ? b3 : ~b3);
 }
 
 // The representation row of a centre from its n staged neighbours (one warp);
@@ -377,96 +421,136 @@ __device__ __forceinline__ void fwd_row(const RegWarp& s, int n, const Fchl19Con
     }
   }
 
-  // three-body: pair geometry lane-parallel over flat pairs (j < k), then lanes over bins
-  float ac[15], as[15];
+  if (has2)   // two-body columns (written before the three-body sums take the registers)
 #pragma unroll
-  for (int q = 0; q < 15; ++q) {
-    ac[q] = 0.f;
-    as[q] = 0.f;
-  }
+    for (int e = 0; e < 5; ++e)
+      if (e < c.n_el) out[e * c.n2 + lane] = a2[e];
+
+  // three-body, per block of up to kPairBlock neighbour pairs (j < k, row-major):
+  //  1. lanes over pairs: each pair's element-pair type (15: no term, r_jk >= r_cut),
+  //     4 bits per round in `keys`, and the count of each type (lane t counts type t);
+  //  2. lanes over pairs: the pair geometry, written to its type's run in pair
+  //     order (rank among the round's lanes of the same type from four bit ballots);
+  //  3. lanes over bins: type by type (a compile-time accumulator index), the
+  //     run in pair order, two triplets per step.
+  // Every type's triplets are summed in pair order within a block; a block's
+  // sums are added to the earlier blocks' in the row (one block in most rows).
+  const unsigned lt_mask = (1u << lane) - 1u;
   const int n_pairs = n * (n - 1) / 2;
-  for (int q0 = 0; q0 < n_pairs; q0 += 32) {
-    const int q = q0 + lane;
-    bool ok = false;
-    float wc = 0.f, ws = 0.f, xbar = 0.f;
-    int pidx = 0;
-    if (q < n_pairs) {
-      int jn, kn;
-      decode_pair(q, n, jn, kn);
-      const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
-      const float vx = uk.x * uk.w - uj.x * uj.w;
-      const float vy = uk.y * uk.w - uj.y * uj.w;
-      const float vz = uk.z * uk.w - uj.z * uj.w;
-      const float rjk2 = vx * vx + vy * vy + vz * vz;
-      if (rjk2 < c.rcut2) {
-        ok = true;
+  for (int p0 = 0; p0 == 0 || p0 < n_pairs; p0 += kPairBlock) {   // one (empty) block when n_pairs = 0
+    const int p1 = min(p0 + kPairBlock, n_pairs);
+    unsigned keys = 0u;
+    int cnt = 0;
+    for (int r = 0, q0 = p0; q0 < p1; ++r, q0 += 32) {
+      const int q = q0 + lane;
+      int key = 15;
+      if (q < p1) {
+        int jn, kn;
+        decode_pair_fast(q, n, jn, kn);
+        const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+        const float vx = uk.x * uk.w - uj.x * uj.w;
+        const float vy = uk.y * uk.w - uj.y * uj.w;
+        const float vz = uk.z * uk.w - uj.z * uj.w;
+        if (vx * vx + vy * vy + vz * vz < c.rcut2) key = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
+      }
+      keys |= (unsigned)key << (4 * r);
+      const unsigned b0 = __ballot_sync(0xffffffffu, key & 1), b1 = __ballot_sync(0xffffffffu, key & 2);
+      const unsigned b2 = __ballot_sync(0xffffffffu, key & 4), b3 = __ballot_sync(0xffffffffu, key & 8);
+      cnt += __popc(type_lanes(lane, b0, b1, b2, b3));
+    }
+    // exclusive scan of the counts over lanes 0..15: each type's first entry
+    if (lane >= 16) cnt = 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int run = incl - cnt;
+    if (lane < 16) s.run[lane] = run;
+    for (int r = 0, q0 = p0; q0 < p1; ++r, q0 += 32) {
+      const int q = q0 + lane;
+      const int key = (int)((keys >> (4 * r)) & 15u);
+      const unsigned b0 = __ballot_sync(0xffffffffu, key & 1), b1 = __ballot_sync(0xffffffffu, key & 2);
+      const unsigned b2 = __ballot_sync(0xffffffffu, key & 4), b3 = __ballot_sync(0xffffffffu, key & 8);
+      const int slot = __shfl_sync(0xffffffffu, run, key) + __popc(type_lanes(key, b0, b1, b2, b3) & lt_mask);
+      run += __popc(type_lanes(lane, b0, b1, b2, b3));
+      if (key < 15) {   // q < p1 and r_jk < r_cut
+        int jn, kn;
+        decode_pair_fast(q, n, jn, kn);
+        const float4 uj = s.nb_u[jn], uk = s.nb_u[kn];
+        const float vx = uk.x * uk.w - uj.x * uj.w;
+        const float vy = uk.y * uk.w - uj.y * uj.w;
+        const float vz = uk.z * uk.w - uj.z * uj.w;
+        const float rjk2 = vx * vx + vy * vy + vz * vz;
         const float inv_rjk = rsqrtf(rjk2);
         const float rjk = rjk2 * inv_rjk;
         const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
         const float cx = uj.y * uk.z - uj.z * uk.y;
         const float cy = uj.z * uk.x - uj.x * uk.z;
         const float cz = uj.x * uk.y - uj.y * uk.x;
-        const float si = sqrtf(cx * cx + cy * cy + cz * cz);
+        const float s2i = cx * cx + cy * cy + cz * cz;
+        const float si = s2i > 0.0f ? s2i * rsqrt_approx(s2i) : 0.0f;
         const float cj = -(uj.x * vx + uj.y * vy + uj.z * vz) * inv_rjk;
         const float ck = (uk.x * vx + uk.y * vy + uk.z * vz) * inv_rjk;
         // (r_ij r_ik r_jk)^-N3 = 2^(-N3 log2(r_ij r_ik r_jk))
         const float atm = (1.0f + 3.0f * ci * cj * ck) * ex2_approx(-c.N3 * lg2_approx(uj.w * uk.w * rjk));
         const float fcjk = 0.5f * (__cosf(rjk * c.pi_over_rcut) + 1.0f);
         const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * fcjk;
-        wc = w * c.ang2 * ci;
-        ws = w * c.ang2 * si;
-        xbar = 0.5f * (uj.w + uk.w);
-        pidx = pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el);
+        s.pairs[slot] = make_float4(w * c.ang2 * ci, w * c.ang2 * si, 0.5f * (uj.w + uk.w), 0.f);
       }
     }
-    // stage the chunk in lane order; then, pair type by pair type (a
-    // compile-time accumulator index), walk that type's triplets in lane order
-    s.pairs[lane] = make_float4(wc, ws, xbar, 0.f);
     __syncwarp();
-    const int key = ok ? pidx : 15;
-#pragma unroll
+    // one copy of the walk for all types (the sums are two scalars per type, so
+    // nothing needs a compile-time index; a small body stays in the instruction cache)
+    int lo = s.run[0];
+#pragma unroll 1
     for (int b = 0; b < 15; ++b) {
-      unsigned m = __ballot_sync(0xffffffffu, key == b);
-      while (m) {
-        const int t0 = __ffs(m) - 1;
-        m &= m - 1u;
-        const float4 p0 = s.pairs[t0];
-        const float d0 = p0.z - r3;
-        const float g0 = ex2_approx(d0 * (d0 * neg_eta3));
-        if (m) {
-          const int t1 = __ffs(m) - 1;
-          m &= m - 1u;
-          const float4 p1 = s.pairs[t1];
-          const float d1 = p1.z - r3;
-          const float g1 = ex2_approx(d1 * (d1 * neg_eta3));
-          ac[b] = fmaf(g0, p0.x, ac[b]);
-          as[b] = fmaf(g0, p0.y, as[b]);
-          ac[b] = fmaf(g1, p1.x, ac[b]);
-          as[b] = fmaf(g1, p1.y, as[b]);
-        } else {
-          ac[b] = fmaf(g0, p0.x, ac[b]);
-          as[b] = fmaf(g0, p0.y, as[b]);
+      const int hi = s.run[b + 1];
+      int t = lo;
+      lo = hi;
+      float ac = 0.f, as = 0.f;
+      for (; t + 3 < hi; t += 4) {   // four triplets' Gaussians in flight, summed in order
+        float g[4];
+        float4 e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          e[u] = s.pairs[t + u];
+          const float d = e[u].z - r3;
+          g[u] = ex2_approx(d * (d * neg_eta3));
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ac = fmaf(g[u], e[u].x, ac);
+          as = fmaf(g[u], e[u].y, as);
+        }
+      }
+      for (; t < hi; ++t) {
+        const float4 e0 = s.pairs[t];
+        const float d0 = e0.z - r3;
+        const float g0 = ex2_approx(d0 * (d0 * neg_eta3));
+        ac = fmaf(g0, e0.x, ac);
+        as = fmaf(g0, e0.y, as);
+      }
+      if (has3 && b < np) {   // the type's two columns at this lane's bin
+        float* o = out + c.base3 + (b * c.n3 + lane) * 2;
+        if (p0 > 0) {
+          ac += o[0];
+          as += o[1];
+        }
+        o[0] = ac;
+        o[1] = as;
       }
     }
     __syncwarp();
   }
-  // write the row from registers; padding columns zero
-  if (has2)
-#pragma unroll
-    for (int e = 0; e < 5; ++e)
-      if (e < c.n_el) out[e * c.n2 + lane] = a2[e];
-  if (has3)
-#pragma unroll
-    for (int q = 0; q < 15; ++q)
-      if (q < np) {
-        out[c.base3 + (q * c.n3 + lane) * 2] = ac[q];
-        out[c.base3 + (q * c.n3 + lane) * 2 + 1] = as[q];
-      }
-    for (int k = c.rep_dim + lane; k < rep_ld; k += 32) out[k] = 0.0f;
+  for (int k = c.rep_dim + lane; k < rep_ld; k += 32) out[k] = 0.0f;   // padding columns
 }
 
-__global__ void __launch_bounds__(32 * kWarpsFwd, 6)
+#ifndef QMLR_FWD_MIN_BLOCKS
+#define QMLR_FWD_MIN_BLOCKS 8   // resident CTAs per SM the register budget is sized for (64 registers)
+#endif
+__global__ void __launch_bounds__(32 * kWarpsFwd, QMLR_FWD_MIN_BLOCKS)
 fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __restrict__ elem,
                           const int32_t* __restrict__ mol_ptr, int n_mol, int n_atoms, int mx, int mxp, int range,
                           Fchl19Consts c, float* __restrict__ rep, int rep_ld, int* err) {
@@ -499,12 +583,7 @@ fchl19_forward_reg_kernel(const float* __restrict__ coords, const int32_t* __res
     pos[j] = make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), __int_as_float(e));
   }
   __syncthreads();
-  char* wbase = smem_raw + (size_t)reg_stage_atoms(mx, range) * 16 + warp * reg_warp_bytes(mxp);
-  RegWarp s;
-  s.nb_u = reinterpret_cast<float4*>(wbase);
-  s.nb_2b = s.nb_u + mxp;
-  s.pairs = s.nb_2b + mxp;
-  s.nb_el = reinterpret_cast<int*>(s.pairs + 32);
+  const RegWarp s = carve_reg(smem_raw + (size_t)reg_stage_atoms(mx, range) * 16 + warp * reg_warp_bytes(mxp), mxp);
 
   const BinConsts kb = bin_consts(c, lane);   // per-lane radial constants (lane = bin)
 
@@ -603,33 +682,39 @@ __device__ void vjp_from_neighbours(int n, int il, const Fchl19Consts& c, VjpWar
   float gi_x = 0.f, gi_y = 0.f, gi_z = 0.f;   // gradient on the centre (per-lane partials)
   const float neg_eta3 = -c.eta3 * kLog2e;
 
-  // two-body: lanes over neighbours (distinct atoms per lane)
+  // two-body: lanes over neighbours (distinct atoms per lane); reciprocals
+  // and the cutoff's sine from the hardware approximations (a few ulp)
   for (int jn = lane; jn < n; jn += 32) {
     const float4 u = s.nb_u[jn];
     const float r = u.w;
     const float4 t = s.nb_2b[jn];   // mu, 1/(2s^2), fc r^-N2/(s sqrt(2pi)), fc
-    const float inv_r = 1.0f / r;
-    const float s2 = 0.5f / t.y;
-    const float sd = sqrtf(s2);
-    const float rr_eta = r * r + c.eta2;
-    const float ds = -c.eta2 / (sd * r * rr_eta);            // d sigma / dr
-    const float dmu = inv_r + c.eta2 / (r * rr_eta);          // d mu / dr
+    const float inv_r = rcp_approx(r);
+    const float inv_s2 = 2.0f * t.y;                           // 1 / sigma^2
+    const float inv_sd = inv_s2 * rsqrt_approx(inv_s2);        // 1 / sigma
+    const float inv_rr = rcp_approx(fmaf(r, r, c.eta2));       // 1 / (r^2 + eta2)
+    const float ds = -c.eta2 * inv_sd * inv_r * inv_rr;        // d sigma / dr
+    const float dmu = inv_r + c.eta2 * inv_r * inv_rr;         // d mu / dr
     const float fc = t.w;
-    const float dfc = cutoff_df(r, c);
-    const float rN = expf(-c.N2 * logf(r));
+    const float dfc = -0.5f * c.pi_over_rcut * __sinf(r * c.pi_over_rcut);
+    const float rN = ex2_approx(-c.N2 * lg2_approx(r));
     const float P = fc * rN;
     const float dP = rN * (dfc - c.N2 * fc * inv_r);
     const float negc = -t.y * kLog2e;
-    const float pre = c.inv_sqrt_2pi / sd;
-    const float k1 = -ds / sd, k2 = dmu / s2, k3 = ds / (s2 * sd);
+    const float pre = c.inv_sqrt_2pi * inv_sd;
+    const float k1 = -ds * inv_sd, k2 = dmu * inv_s2, k3 = ds * inv_s2 * inv_sd;
     const float* gb = s.g + s.nb_el[jn] * c.n2;
-    float dEdr = 0.f;
+    // dE/dr = sum_k g_k L_k (dP + P dlnL_k), dlnL_k = k1 + a_k k2 + a_k^2 k3, with
+    // L_k = pre e_k: the sums of g_k e_k a_k^p (p = 0, 1, 2) over the bins, then combined
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
     for (int k = 0; k < c.n2; ++k) {
       const float a = c.rs2_log[k] - t.x;
-      const float L = c.rs2_inv[k] * pre * ex2_approx(a * (a * negc));
-      const float dlnL = k1 + a * k2 + a * a * k3;
-      dEdr += gb[k] * L * (dP + P * dlnL);
+      const float ge = gb[k] * (c.rs2_inv[k] * ex2_approx(a * (a * negc)));
+      const float gea = ge * a;
+      S0 += ge;
+      S1 += gea;
+      S2 = fmaf(gea, a, S2);
     }
+    const float dEdr = pre * (dP * S0 + P * (k1 * S0 + k2 * S1 + k3 * S2));
     const int jl = s.nb_idx[jn];
     s.facc[3 * jl + 0] += dEdr * u.x;
     s.facc[3 * jl + 1] += dEdr * u.y;
@@ -653,47 +738,62 @@ __device__ void vjp_from_neighbours(int n, int il, const Fchl19Consts& c, VjpWar
       const float vx = uk.x * b - uj.x * a, vy = uk.y * b - uj.y * a, vz = uk.z * b - uj.z * a;
       const float c2 = vx * vx + vy * vy + vz * vz;
       if (c2 < c.rcut2) {
-        const float cc = sqrtf(c2);
-        const float inv_c = 1.0f / cc;
+        // reciprocals, square roots, the ATM power and the cutoffs from the
+        // hardware approximations (a few ulp; the gradient's tolerance is 1e-4)
+        const float inv_c = rsqrt_approx(c2);
+        const float cc = c2 * inv_c;
+        const float inv_a = rcp_approx(a), inv_b = rcp_approx(b);
         const float ux = vx * inv_c, uy = vy * inv_c, uz = vz * inv_c;   // unit j -> k
         const float ci = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
         const float crx = uj.y * uk.z - uj.z * uk.y;
         const float cry = uj.z * uk.x - uj.x * uk.z;
         const float crz = uj.x * uk.y - uj.y * uk.x;
-        const float si = sqrtf(crx * crx + cry * cry + crz * crz);
+        const float s2i = crx * crx + cry * cry + crz * crz;
+        const float si = s2i > 0.0f ? s2i * rsqrt_approx(s2i) : 0.0f;
         const float cj = -(uj.x * ux + uj.y * uy + uj.z * uz);
         const float ck = (uk.x * ux + uk.y * uy + uk.z * uz);
         // cosines as functions of the sides a = r_ij, b = r_ik, cc = r_jk
-        const float dci_da = (a - b * ci) / (a * b), dci_db = (b - a * ci) / (a * b), dci_dc = -cc / (a * b);
-        const float dcj_da = (a - cc * cj) / (a * cc), dcj_dc = (cc - a * cj) / (a * cc), dcj_db = -b / (a * cc);
-        const float dck_db = (b - cc * ck) / (b * cc), dck_dc = (cc - b * ck) / (b * cc), dck_da = -a / (b * cc);
+        const float iab = inv_a * inv_b, iac = inv_a * inv_c, ibc = inv_b * inv_c;
+        const float dci_da = (a - b * ci) * iab, dci_db = (b - a * ci) * iab, dci_dc = -cc * iab;
+        const float dcj_da = (a - cc * cj) * iac, dcj_dc = (cc - a * cj) * iac, dcj_db = -b * iac;
+        const float dck_db = (b - cc * ck) * ibc, dck_dc = (cc - b * ck) * ibc, dck_da = -a * ibc;
         const float Q = 1.0f + 3.0f * ci * cj * ck;
         const float dQ_da = 3.0f * (dci_da * cj * ck + ci * dcj_da * ck + ci * cj * dck_da);
         const float dQ_db = 3.0f * (dci_db * cj * ck + ci * dcj_db * ck + ci * cj * dck_db);
         const float dQ_dc = 3.0f * (dci_dc * cj * ck + ci * dcj_dc * ck + ci * cj * dck_dc);
-        const float R3 = expf(-c.N3 * logf(a * b * cc));
-        const float fa = s.nb_2b[jn].w, fb = s.nb_2b[kn].w, fcc = cutoff_f(cc, c);
-        const float dfa = cutoff_df(a, c), dfb = cutoff_df(b, c), dfcc = cutoff_df(cc, c);
+        const float R3 = ex2_approx(-c.N3 * lg2_approx(a * b * cc));   // (r_ij r_ik r_jk)^-N3
+        const float fa = s.nb_2b[jn].w, fb = s.nb_2b[kn].w;
+        float sin_c, cos_c;
+        __sincosf(cc * c.pi_over_rcut, &sin_c, &cos_c);
+        const float hp = -0.5f * c.pi_over_rcut;
+        const float fcc = 0.5f * (cos_c + 1.0f), dfcc = hp * sin_c;
+        const float dfa = hp * __sinf(a * c.pi_over_rcut), dfb = hp * __sinf(b * c.pi_over_rcut);
         const float F3 = fa * fb * fcc;
-        const float W = c.w3 * Q * R3 * F3;
-        const float dW_da = c.w3 * R3 * (dQ_da * F3 - Q * F3 * c.N3 / a + Q * dfa * fb * fcc);
-        const float dW_db = c.w3 * R3 * (dQ_db * F3 - Q * F3 * c.N3 / b + Q * fa * dfb * fcc);
-        const float dW_dc = c.w3 * R3 * (dQ_dc * F3 - Q * F3 * c.N3 / cc + Q * fa * fb * dfcc);
+        const float WR = c.w3 * R3;
+        const float W = WR * Q * F3;
+        const float QFN = Q * F3 * c.N3;
+        const float dW_da = WR * (dQ_da * F3 - QFN * inv_a + Q * dfa * fb * fcc);
+        const float dW_db = WR * (dQ_db * F3 - QFN * inv_b + Q * fa * dfb * fcc);
+        const float dW_dc = WR * (dQ_dc * F3 - QFN * inv_c + Q * fa * fb * dfcc);
         const float Ac = c.ang2 * ci, As = c.ang2 * si;
-        const float dsi_dci = si > 1e-7f ? -ci / si : 0.0f;   // collinear guard
+        const float dsi_dci = si > 1e-7f ? -ci * rcp_approx(si) : 0.0f;   // collinear guard
         const float xbar = 0.5f * (a + b);
         const float* gb = s.g + c.base3 + pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el) * c.n3 * 2;
+        // S = sum_k g_k rad_k and S1 = sum_k g_k (xbar - R_k) rad_k; d rad_k / d xbar
+        // = -2 eta3 (xbar - R_k) rad_k, the factor applied once below
         float Sc = 0.f, Ss = 0.f, Sc1 = 0.f, Ss1 = 0.f;
         for (int k = 0; k < c.n3; ++k) {
           const float d = xbar - c.rs3[k];
           const float rad = ex2_approx(d * (d * neg_eta3));
-          const float drad = -2.0f * c.eta3 * d * rad;
+          const float td = d * rad;
           const float g0 = gb[2 * k], g1 = gb[2 * k + 1];
-          Sc += g0 * rad;
-          Ss += g1 * rad;
-          Sc1 += g0 * drad;
-          Ss1 += g1 * drad;
+          Sc = fmaf(g0, rad, Sc);
+          Ss = fmaf(g1, rad, Ss);
+          Sc1 = fmaf(g0, td, Sc1);
+          Ss1 = fmaf(g1, td, Ss1);
         }
+        Sc1 *= -2.0f * c.eta3;
+        Ss1 *= -2.0f * c.eta3;
         const float AS = Ac * Sc + As * Ss;
         const float AS1 = Ac * Sc1 + As * Ss1;
         const float dA = c.ang2 * (Sc + dsi_dci * Ss);   // d(A.S)/d cos(th_i) at fixed S
@@ -854,6 +954,7 @@ fchl19_jac_kernel(const float* __restrict__ coords, const int32_t* __restrict__ 
   for (int k = lane; k < 3 * rp; k += 32) s.cblk[k] = 0.f;
   __syncwarp();
   const int n = neighbour_list(s.pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
+  const float neg_eta3 = -c.eta3 * kLog2e;
 
   int next_nb = 0;
   for (int kl = 0; kl < M; ++kl) {
@@ -870,23 +971,26 @@ fchl19_jac_kernel(const float* __restrict__ coords, const int32_t* __restrict__ 
     const float A = uA.w;
     // two-body term of the pair (I, k): d G / d r_k = G'(A) uA
     {
+      // reciprocals, the power and the cutoff's sine from the hardware approximations
       const float4 t = s.nb_2b[kn];
-      const float inv_r = 1.0f / A;
-      const float s2 = 0.5f / t.y;
-      const float sd = sqrtf(s2);
-      const float rr_eta = A * A + c.eta2;
-      const float ds = -c.eta2 / (sd * A * rr_eta);
-      const float dmu = inv_r + c.eta2 / (A * rr_eta);
+      const float inv_r = rcp_approx(A);
+      const float inv_s2 = 2.0f * t.y;                           // 1 / sigma^2
+      const float inv_sd = inv_s2 * rsqrt_approx(inv_s2);        // 1 / sigma
+      const float inv_rr = rcp_approx(fmaf(A, A, c.eta2));       // 1 / (r^2 + eta2)
+      const float ds = -c.eta2 * inv_sd * inv_r * inv_rr;        // d sigma / dr
+      const float dmu = inv_r + c.eta2 * inv_r * inv_rr;         // d mu / dr
       const float fc = t.w;
-      const float dfc = cutoff_df(A, c);
-      const float rN = expf(-c.N2 * logf(A));
+      const float dfc = -0.5f * c.pi_over_rcut * __sinf(A * c.pi_over_rcut);
+      const float rN = ex2_approx(-c.N2 * lg2_approx(A));
       const float P = fc * rN;
       const float dP = rN * (dfc - c.N2 * fc * inv_r);
+      const float pre = c.inv_sqrt_2pi * inv_sd, negc = -t.y * kLog2e;
+      const float k1 = -ds * inv_sd, k2 = dmu * inv_s2, k3 = ds * inv_s2 * inv_sd;
       const int b0 = s.nb_el[kn] * c.n2;
       for (int q = lane; q < c.n2; q += 32) {
         const float a = c.rs2_log[q] - t.x;
-        const float L = c.rs2_inv[q] * c.inv_sqrt_2pi / sd * expf(-a * a * t.y);
-        const float dlnL = -ds / sd + a * dmu / s2 + a * a * ds / (s2 * sd);
+        const float L = c.rs2_inv[q] * pre * ex2_approx(a * (a * negc));
+        const float dlnL = k1 + a * k2 + a * a * k3;
         const float g = L * (dP + P * dlnL);
         s.blk[0 * rp + b0 + q] += g * uA.x;
         s.blk[1 * rp + b0 + q] += g * uA.y;
@@ -906,33 +1010,44 @@ fchl19_jac_kernel(const float* __restrict__ coords, const int32_t* __restrict__ 
         const float C2 = vx * vx + vy * vy + vz * vz;
         if (C2 < c.rcut2) {
           ok = true;
-          const float C = sqrtf(C2);
-          const float icc = 1.0f / C;
+          // reciprocals, square roots, the ATM power and the cutoffs from the
+          // hardware approximations (a few ulp)
+          const float icc = rsqrt_approx(C2);
+          const float C = C2 * icc;
           const float ux = vx * icc, uy = vy * icc, uz = vz * icc;   // unit k -> j
           const float ci = uA.x * uB.x + uA.y * uB.y + uA.z * uB.z;
           const float crx = uA.y * uB.z - uA.z * uB.y;
           const float cry = uA.z * uB.x - uA.x * uB.z;
           const float crz = uA.x * uB.y - uA.y * uB.x;
-          const float si = sqrtf(crx * crx + cry * cry + crz * crz);
+          const float s2i = crx * crx + cry * cry + crz * crz;
+          const float si = s2i > 0.0f ? s2i * rsqrt_approx(s2i) : 0.0f;
           const float ck = -(uA.x * ux + uA.y * uy + uA.z * uz);   // angle at k (first neighbour)
           const float cj = (uB.x * ux + uB.y * uy + uB.z * uz);    // angle at j (second neighbour)
           // sides: a = A (I-k), b = B (I-j), cc = C (k-j); "first" = k, "second" = j
           const float a = A, b = B, cc = C;
-          const float dci_da = (a - b * ci) / (a * b), dci_dc = -cc / (a * b);
-          const float dcf_da = (a - cc * ck) / (a * cc), dcf_dc = (cc - a * ck) / (a * cc);
-          const float dcs_da = -a / (b * cc), dcs_dc = (cc - b * cj) / (b * cc);
+          const float ia = rcp_approx(a), ib = rcp_approx(b);
+          const float iab = ia * ib, iac = ia * icc, ibc = ib * icc;
+          const float dci_da = (a - b * ci) * iab, dci_dc = -cc * iab;
+          const float dcf_da = (a - cc * ck) * iac, dcf_dc = (cc - a * ck) * iac;
+          const float dcs_da = -a * ibc, dcs_dc = (cc - b * cj) * ibc;
           const float Q = 1.0f + 3.0f * ci * ck * cj;
           const float dQ_da = 3.0f * (dci_da * ck * cj + ci * dcf_da * cj + ci * ck * dcs_da);
           const float dQ_dc = 3.0f * (dci_dc * ck * cj + ci * dcf_dc * cj + ci * ck * dcs_dc);
-          const float R3 = expf(-c.N3 * logf(a * b * cc));
-          const float fa = s.nb_2b[kn].w, fb = s.nb_2b[jn].w, fcc = cutoff_f(cc, c);
-          const float dfa = cutoff_df(a, c), dfcc = cutoff_df(cc, c);
+          const float R3 = ex2_approx(-c.N3 * lg2_approx(a * b * cc));
+          const float fa = s.nb_2b[kn].w, fb = s.nb_2b[jn].w;
+          float sin_c, cos_c;
+          __sincosf(cc * c.pi_over_rcut, &sin_c, &cos_c);
+          const float hp = -0.5f * c.pi_over_rcut;
+          const float fcc = 0.5f * (cos_c + 1.0f), dfcc = hp * sin_c;
+          const float dfa = hp * __sinf(a * c.pi_over_rcut);
           const float F3 = fa * fb * fcc;
-          const float W = c.w3 * Q * R3 * F3;
-          const float dW_da = c.w3 * R3 * (dQ_da * F3 - Q * F3 * c.N3 / a + Q * dfa * fb * fcc);
-          const float dW_dc = c.w3 * R3 * (dQ_dc * F3 - Q * F3 * c.N3 / cc + Q * fa * fb * dfcc);
+          const float WR = c.w3 * R3;
+          const float W = WR * Q * F3;
+          const float QFN = Q * F3 * c.N3;
+          const float dW_da = WR * (dQ_da * F3 - QFN * ia + Q * dfa * fb * fcc);
+          const float dW_dc = WR * (dQ_dc * F3 - QFN * icc + Q * fa * fb * dfcc);
           const float Ac = c.ang2 * ci, As = c.ang2 * si;
-          const float dAc = c.ang2, dAs = si > 1e-7f ? -c.ang2 * ci / si : 0.0f;
+          const float dAc = c.ang2, dAs = si > 1e-7f ? -c.ang2 * ci * rcp_approx(si) : 0.0f;
           const int bin = c.base3 + pair_index(s.nb_el[kn], s.nb_el[jn], c.n_el) * c.n3 * 2;
           q0 = make_float4(dW_da * Ac + W * dAc * dci_da, dW_da * As + W * dAs * dci_da, 0.5f * W * Ac,
                            0.5f * W * As);
@@ -955,7 +1070,7 @@ fchl19_jac_kernel(const float* __restrict__ coords, const int32_t* __restrict__ 
         const int bin = __float_as_int(p1.w);
         for (int q = lane; q < c.n3; q += 32) {
           const float d = p1.z - c.rs3[q];
-          const float rad = expf(-c.eta3 * d * d);
+          const float rad = ex2_approx(d * (d * neg_eta3));
           const float drad = -2.0f * c.eta3 * d * rad;
           // d v / d r_k = dv/da * uA - dv/dc * uC   (C = |r_j - r_k|)
           const float da_c = rad * p0.x + drad * p0.z, da_s = rad * p0.y + drad * p0.w;
@@ -1110,12 +1225,7 @@ fchl19_periodic_kernel(const float* __restrict__ coords, const int32_t* __restri
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarpsFwd + warp;
   if (i >= n_atoms) return;
-  char* wbase = smem_raw + warp * reg_warp_bytes(envp);
-  RegWarp s;
-  s.nb_u = reinterpret_cast<float4*>(wbase);
-  s.nb_2b = s.nb_u + envp;
-  s.pairs = s.nb_2b + envp;
-  s.nb_el = reinterpret_cast<int*>(s.pairs + 32);
+  const RegWarp s = carve_reg(smem_raw + warp * reg_warp_bytes(envp), envp);
   const BinConsts kb = bin_consts(c, lane);
   float* out = rep + (size_t)i * rep_ld;
   const long e0 = __ldg(env_ptr + i), e1 = __ldg(env_ptr + i + 1);
