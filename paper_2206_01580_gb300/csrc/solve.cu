@@ -382,94 +382,97 @@ __device__ __forceinline__ float2 pair_rsqrt(float2 d) {
   return make_float2(h, __fsub_rn(corr, __fsub_rn(h, y0)));
 }
 
-// Factor of the diagonal block (float pairs on entry). Row i of the block stays
-// in the registers of threads 4i..4i+3 (thread q holds columns 4k + q). Step j:
-// the holder of the pivot forms 1/L_jj = 1/sqrt(d) (pair_rsqrt) and L_jj while
-// the holders of column j publish it unscaled in shared memory; after one
-// barrier every row i > j scales its own entry and subtracts L_ij L_lj from its
-// columns j < l <= i (blocks of four columns already done are skipped
-// warp-uniformly). Writes L_kk in FP64
-// to L, and its pairs and the pivots' reciprocals (pairs) to dpairs ([64][64]
-// then [64]) for the panel solve.
-__global__ void __launch_bounds__(256, 1)
-potrf_diag_df_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, int* info,
-                     float2* __restrict__ dpairs) {
-  __shared__ float2 craw[2][NB];   // column j before scaling, by step parity
-  __shared__ float2 ys[NB];
-  const int tid = threadIdx.x;
-  const int row = tid >> 2, q = tid & 3;
-  float2 x[NB / 4];
-#pragma unroll
-  for (int k = 0; k < NB / 4; ++k) {
-    const int c = 4 * k + q;
-    x[k] = (row < nb && c <= row) ? *reinterpret_cast<const float2*>(L + (long)(k0 + row) * ldl + k0 + c)
-                                  : make_float2(c == row ? 1.f : 0.f, 0.f);
+// Factor of the diagonal block (float pairs on entry), right-looking over the
+// block held in shared memory as float pairs, one barrier per step. Column j is
+// kept unscaled (a_ij) until the end: at step j every entry (i, l) of the
+// trailing triangle j < l <= i takes a_il -= a_ij a_lj / d_j (a pair product
+// with the pair 1/d_j, then a two-sum subtraction), the entries spread evenly
+// over the CTA's threads in a compact triangular enumeration (no idle
+// predicated work), and the thread holding entry (j+1, j+1) forms the next
+// pivot's 1/sqrt (pair_rsqrt) before the barrier. At the end L_ij = a_ij / sqrt(d_j).
+// The loop is small and not unrolled: one CTA runs it, on an SM whose
+// instruction cache holds none of it. Writes L_kk in FP64 to L, and its pairs
+// and the pivots' reciprocals (pairs) to dpairs ([64][64] then [64]).
+__device__ __forceinline__ void diag_pivot(float2 a, int j, int k0, int nb, int* err, int* info, float2* ys,
+                                           float2* yy) {
+  float2 d = pair_add(a, make_float2(0.f, 0.f));
+  if (!(d.x > 0.f)) {
+    if (j < nb) {
+      record_device_error(err, DEV_NOT_SPD);
+      if (info && *info == 0) *info = k0 + j + 1;
+    }
+    d = make_float2(1.f, 0.f);
   }
-  // Step j, one barrier: the holders of column j publish it unscaled and the
-  // pivot's holder forms y = 1/L_jj; after the barrier every row i > j takes
-  // L_ij = a_ij y and t = L_ij y, and subtracts t a_lj (= L_ij L_lj) from its
-  // columns j < l <= i. (Not unrolled: one CTA runs this, and the unrolled
-  // body outgrows the instruction cache.)
-  for (int j = 0; j < NB; ++j) {
-    const int m = j >> 2, jq = j & 3;
-    if (q == jq && row >= j) {
-      float2 xm = make_float2(0.f, 0.f);
+  const float2 y = pair_rsqrt(d);   // 1 / sqrt(d_j)
+  ys[j] = y;
+  yy[j] = pair_mul(y, y);           // 1 / d_j
+}
+
+constexpr int kDiagThreads = 1024;   // about one trailing entry per thread and step: latency, not work, bounds a step
+static_assert(2 * kDiagThreads >= NB * (NB - 1) / 2, "two trailing entries per thread cover the first step");
+
+__global__ void __launch_bounds__(kDiagThreads, 1)
+potrf_diag_blk_kernel(double* __restrict__ L, long ldl, int k0, int nb, int* err, int* info,
+                      float2* __restrict__ dpairs) {
+  __shared__ float2 A[NB][NB + 1];
+  __shared__ float2 ys[NB], yy[NB];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int r = idx / NB, c = idx % NB;
+    A[r][c] = (r < nb && c <= r) ? *reinterpret_cast<const float2*>(L + (long)(k0 + r) * ldl + k0 + c)
+                                 : make_float2(c == r ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  if (tid == 0) diag_pivot(A[0][0], 0, k0, nb, err, info, ys, yy);
+  __syncthreads();
+  // the triangle's row-major enumeration does not depend on the step: entry
+  // e = (ii, ll) of the trailing triangle at step j is (j + 1 + ii, j + 1 + ll),
+  // and thread tid holds e = tid + k kDiagThreads (k < 2: at most 2016 entries)
+  int tii[2], tll[2];
 #pragma unroll
-      for (int k = 0; k < NB / 4; ++k)
-        if (k == m) xm = x[k];
-      if (row == j) {   // pivot
-        float2 d = pair_add(xm, make_float2(0.f, 0.f));
-        if (!(d.x > 0.f)) {
-          if (j < nb) {
-            record_device_error(err, DEV_NOT_SPD);
-            if (info && *info == 0) *info = k0 + j + 1;
-          }
-          d = make_float2(1.f, 0.f);
-        }
-        const float2 y = pair_rsqrt(d);
-        const float2 ljj = pair_mul(d, y);
+  for (int k = 0; k < 2; ++k) {
+    const int e = tid + k * kDiagThreads;
+    float sq;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(8.0f * (float)e + 1.0f));
+    int ii = (int)((sq - 1.0f) * 0.5f);
+    if (ii * (ii + 1) / 2 > e) --ii;
+    else if ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+    tii[k] = ii;
+    tll[k] = e - ii * (ii + 1) / 2;
+  }
+#pragma unroll 1
+  for (int j = 0; j < NB - 1; ++j) {
+    const float2 w = yy[j];
+    const int m = NB - 1 - j;                 // trailing rows j+1 .. 63
+    const int count = m * (m + 1) / 2;        // entries (i, l), j < l <= i
 #pragma unroll
-        for (int k = 0; k < NB / 4; ++k)
-          if (k == m) x[k] = ljj;
-        ys[j] = y;
-      } else {
-        craw[j & 1][row] = xm;
+    for (int k = 0; k < 2; ++k) {
+      const int e = tid + k * kDiagThreads;
+      if (e < count) {
+        const int i = j + 1 + tii[k], l = j + 1 + tll[k];
+        const float2 t = pair_mul(A[l][j], w);   // a_lj / d_j
+        const float2 aij = A[i][j];
+        float2 a = A[i][l];
+        df_fma(a.x, a.y, -aij.x, -aij.y, t.x, t.y);
+        A[i][l] = a;
+        if (e == 0) diag_pivot(a, j + 1, k0, nb, err, info, ys, yy);   // entry (j+1, j+1)
       }
     }
     __syncthreads();
-    if (row > j) {
-      const float2 y = ys[j];
-      const float2 lij = pair_mul(craw[j & 1][row], y);
-      const float2 t = pair_mul(lij, y);
-      if (q == jq) {
-#pragma unroll
-        for (int k = 0; k < NB / 4; ++k)
-          if (k == m) x[k] = lij;
-      }
-#pragma unroll
-      for (int k = 0; k < NB / 4; ++k) {
-        if (4 * k + 3 <= j) continue;   // columns 4k..4k+3 all done
-        const int l = 4 * k + q;
-        if (l > j && l <= row) {
-          const float2 b = craw[j & 1][l];
-          df_fma(x[k].x, x[k].y, -t.x, -t.y, b.x, b.y);
-        }
-      }
-    }
   }
-#pragma unroll
-  for (int k = 0; k < NB / 4; ++k) {
-    const int c = 4 * k + q;
-    const float2 v = c <= row ? pair_add(x[k], make_float2(0.f, 0.f)) : make_float2(0.f, 0.f);
-    dpairs[row * NB + c] = v;
-    if (row < nb && c <= row) L[(long)(k0 + row) * ldl + k0 + c] = pair_value(v);
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int r = idx / NB, c = idx % NB;
+    float2 v = make_float2(0.f, 0.f);
+    if (c < r) v = pair_mul(A[r][c], ys[c]);                                          // a_rc / sqrt(d_c)
+    else if (c == r) v = pair_mul(pair_add(A[r][r], make_float2(0.f, 0.f)), ys[r]);   // sqrt(d_r)
+    dpairs[idx] = v;
+    if (r < nb && c <= r) L[(long)(k0 + r) * ldl + k0 + c] = pair_value(v);
   }
-  __syncthreads();
   if (tid < NB) dpairs[NB * NB + tid] = ys[tid];
 }
 
 // Panel solve as trsm_panel_kernel, on the float pairs of rows [k0+nb, n) of the
-// block column, with L_kk and 1/L_jj as pairs from potrf_diag_df_kernel. A row's
+// block column, with L_kk and 1/L_jj as pairs from potrf_diag_blk_kernel. A row's
 // 64 values stay in the registers of its eight threads (thread q holds columns
 // 8k + q); at step j the owner of column j forms x_j, the row's threads get it
 // by a shuffle and update their columns l > j (the 64 steps are unrolled, so
@@ -1470,7 +1473,7 @@ static int cholesky_mixed_locked(double* L, long ldl, int n, __nv_bfloat16* part
     float2* lp = reinterpret_cast<float2*>(parts);
     for (int c0 = k0; c0 < k0 + w; c0 += NB) {
       const int nb = std::min(NB, n - c0);
-      potrf_diag_df_kernel<<<1, 256, 0, p>>>(L, ldl, c0, nb, err, info, dpairs);
+      potrf_diag_blk_kernel<<<1, kDiagThreads, 0, p>>>(L, ldl, c0, nb, err, info, dpairs);
       QMLR_LAUNCH_CHECK();
       const int rows = n - c0 - nb;
       if (rows <= 0) break;
