@@ -82,6 +82,10 @@ def parse():
                          "report Gram, factor and PCG times, iterations and training MAE")
     ap.add_argument("--factor", default="mixed", choices=["mixed", "fp64"],
                     help="preconditioner factor: tensor-core trailing updates (mixed) or FP64 throughout")
+    ap.add_argument("--kernel-times", action="store_true",
+                    help="instead of the step: time the FCHL19 forward and adjoints on the workload and the "
+                         "mixed-precision factor of a random SPD matrix of order --factor-n")
+    ap.add_argument("--factor-n", type=int, default=16384)
     ap.add_argument("--feature-sweep", action="store_true",
                     help="instead of the step: time the SORF segment sum over N_transform and N_F, and "
                          "the dense RFF map beside it, on the workload's projected features")
@@ -880,6 +884,55 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_kernel_times(args):
+    """FCHL19 forward, per-molecule adjoint and per-centre adjoint on the QM9-shaped
+    workload (at --scale), and the mixed-precision factor of A = X^T X + I (X
+    Gaussian, order --factor-n); each: one warm-up call, then the median of three
+    CUDA-event-timed calls. Prints one JSON line (a fixed small command for
+    kernel counter captures)."""
+    import torch
+    from paper_2206_01580_gb300 import qmlr
+    from paper_2206_01580_gb300.params import from_table
+
+    torch.cuda.set_device(0)
+    w, _ = build_workload(args.scale)
+    mols = w.mols
+    p = from_table(w.params_column, n2=w.n2, n3=w.n3)
+    coords = torch.as_tensor(mols.coords, dtype=torch.float32).cuda()
+    elem = torch.as_tensor(mols.elem, dtype=torch.int32).cuda()
+    mp = torch.as_tensor(mols.mol_ptr, dtype=torch.int32).cuda()
+    mx = int(np.max(np.diff(mols.mol_ptr)))
+    rep = qmlr.fchl19(coords, elem, mp, mx, p)
+    g = torch.randn_like(rep)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {"workload": w.name, "n_atoms": int(mols.n_atoms),
+           "fchl19_fwd_ms": timed(lambda: qmlr.fchl19(coords, elem, mp, mx, p, out=rep)),
+           "fchl19_vjp_ms": timed(lambda: qmlr.fchl19_vjp(coords, elem, mp, mx, p, g)),
+           "fchl19_vjp_atoms_ms": timed(lambda: qmlr.fchl19_vjp_atoms(coords, elem, mp, mx, p, g))}
+    del rep, g
+    n = args.factor_n
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(n + 64, n, device="cuda", generator=gen)
+    A = (X.T @ X).double() + torch.eye(n, device="cuda", dtype=torch.float64)
+    del X
+    out.update({"factor_n": n, "factor_ms": timed(lambda: qmlr.cholesky_mixed(A))})
+    assert qmlr.device_status() == 0
+    print(json.dumps(out))
+
+
 def run_feature_sweep(args):
     """SORF -> Z for N_transform in {1, 2, 3} and N_F in {8192, 16384, 32768}, and the
     dense RFF map (W = G / sigma) at N_F in {8192, 16384}, on the projected features of
@@ -1176,6 +1229,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.kernel_times:
+        if rank == 0:
+            run_kernel_times(args)
     elif args.feature_sweep:
         if rank == 0:
             run_feature_sweep(args)

@@ -29,7 +29,8 @@ struct Fchl19Consts {
   float w3;          // c3 * sqrt(eta3/pi)
   float ang2;        // 2 exp(-zeta^2/2): G^cos = ang2 cos(th), G^sin = ang2 sin(th) for n = 1
   float inv_sqrt_2pi;
-  float rs2_log[kMaxGrid], rs2_inv[kMaxGrid], rs3[kMaxGrid];
+  float sq_eta3;      // sqrt(eta3 log2(e)): three-body Gaussians as 2^-(y - y_k)^2, y = xbar sq_eta3
+  float rs2_log[kMaxGrid], rs2_inv[kMaxGrid], rs3[kMaxGrid], ys3[kMaxGrid];
 };
 
 static Fchl19Consts make_consts(const qmlr_fchl19_params& p) {
@@ -55,7 +56,11 @@ static Fchl19Consts make_consts(const qmlr_fchl19_params& p) {
     c.rs2_log[k] = (float)log(R);
     c.rs2_inv[k] = (float)(1.0 / R);
   }
-  for (int k = 0; k < p.n3; ++k) c.rs3[k] = (float)(p.rcut * (k + 1) / p.n3);
+  c.sq_eta3 = (float)sqrt(p.eta3 / log(2.0));
+  for (int k = 0; k < p.n3; ++k) {
+    c.rs3[k] = (float)(p.rcut * (k + 1) / p.n3);
+    c.ys3[k] = (float)(p.rcut * (k + 1) / p.n3 * sqrt(p.eta3 / log(2.0)));
+  }
   return c;
 }
 
@@ -324,7 +329,7 @@ constexpr int kPairBlock = 256;   // neighbour pairs staged per walk (8 rounds o
 struct RegWarp {
   float4* nb_u;   // [mxp] unit vector i->j, r_ij
   float4* nb_2b;  // [mxp] mu, log2(e)/(2 s^2), two-body prefactor, f_cut(r_ij)
-  float4* pairs;  // [kPairBlock] w G^cos, w G^sin, xbar, 0 (the block's triplets, by type)
+  float4* pairs;  // [kPairBlock] w G^cos, w G^sin, xbar sqrt(eta3 log2 e), 0 (the block's triplets, by type)
   int* run;       // [16] first entry of each type's run in `pairs` (entry 15: end of type 14)
   int* nb_el;     // [mxp]
 };
@@ -346,7 +351,7 @@ __host__ __device__ __forceinline__ int reg_stage_atoms(int mx, int range) { ret
 // Per-lane constants of the register forward (lane = radial bin).
 struct BinConsts {
   bool has2, has3;
-  float r2log, r2inv, r3, neg_eta3;
+  float r2log, r2inv, y3;   // y3 = R_k sqrt(eta3 log2 e) of this lane's bin
   int np;
 };
 __device__ __forceinline__ BinConsts bin_consts(const Fchl19Consts& c, int lane) {
@@ -355,8 +360,7 @@ __device__ __forceinline__ BinConsts bin_consts(const Fchl19Consts& c, int lane)
   k.has3 = lane < c.n3;
   k.r2log = k.has2 ? c.rs2_log[lane] : 0.f;
   k.r2inv = k.has2 ? c.rs2_inv[lane] : 0.f;
-  k.r3 = k.has3 ? c.rs3[lane] : 0.f;
-  k.neg_eta3 = -c.eta3 * kLog2e;
+  k.y3 = k.has3 ? c.ys3[lane] : 0.f;
   k.np = c.n_el * (c.n_el + 1) / 2;
   return k;
 }
@@ -401,7 +405,7 @@ __device__ __forceinline__ unsigned type_lanes(int t, unsigned b0, unsigned b1, 
 __device__ __forceinline__ void fwd_row(const RegWarp& s, int n, const Fchl19Consts& c, const BinConsts& kb,
                                         float* __restrict__ out, int rep_ld, int lane) {
   const bool has2 = kb.has2, has3 = kb.has3;
-  const float r2log = kb.r2log, r2inv = kb.r2inv, r3 = kb.r3, neg_eta3 = kb.neg_eta3;
+  const float r2log = kb.r2log, r2inv = kb.r2inv, y3 = kb.y3;
   const int np = kb.np;
   // two-body: lanes over bins; per block of 32 neighbours, element by element
   // (a compile-time accumulator index), neighbours in order
@@ -497,7 +501,7 @@ __device__ __forceinline__ void fwd_row(const RegWarp& s, int n, const Fchl19Con
         const float atm = (1.0f + 3.0f * ci * cj * ck) * ex2_approx(-c.N3 * lg2_approx(uj.w * uk.w * rjk));
         const float fcjk = 0.5f * (__cosf(rjk * c.pi_over_rcut) + 1.0f);
         const float w = c.w3 * atm * s.nb_2b[jn].w * s.nb_2b[kn].w * fcjk;
-        s.pairs[slot] = make_float4(w * c.ang2 * ci, w * c.ang2 * si, 0.5f * (uj.w + uk.w), 0.f);
+        s.pairs[slot] = make_float4(w * c.ang2 * ci, w * c.ang2 * si, 0.5f * (uj.w + uk.w) * c.sq_eta3, 0.f);
       }
     }
     __syncwarp();
@@ -516,8 +520,8 @@ __device__ __forceinline__ void fwd_row(const RegWarp& s, int n, const Fchl19Con
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           e[u] = s.pairs[t + u];
-          const float d = e[u].z - r3;
-          g[u] = ex2_approx(d * (d * neg_eta3));
+          const float d = e[u].z - y3;
+          g[u] = ex2_approx(-(d * d));
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -527,8 +531,8 @@ __device__ __forceinline__ void fwd_row(const RegWarp& s, int n, const Fchl19Con
       }
       for (; t < hi; ++t) {
         const float4 e0 = s.pairs[t];
-        const float d0 = e0.z - r3;
-        const float g0 = ex2_approx(d0 * (d0 * neg_eta3));
+        const float d0 = e0.z - y3;
+        const float g0 = ex2_approx(-(d0 * d0));
         ac = fmaf(g0, e0.x, ac);
         as = fmaf(g0, e0.y, as);
       }
@@ -641,7 +645,19 @@ struct VjpWarp {
   int* nb_idx;    // [mxp]
 };
 __host__ __device__ __forceinline__ size_t vjp_warp_bytes(int mxp, int rp) {
-  return 64 * 16 + (size_t)mxp * (16 + 16 + 12 + 4 + 4) + (size_t)rp * 4;
+  return 64 * 16 + (size_t)mxp * (16 + 16 + 12 + 4 + 4) + (size_t)(rp + 4) * 4;
+}
+
+// The centre's gradient row in the warp's buffer, the three-body columns moved
+// up by one float when they start at an odd column so that each (cos, sin)
+// pair is one 8-byte load (grad3() points at them).
+__device__ __forceinline__ void load_grad_row(float* g, const float* __restrict__ grow, const Fchl19Consts& c,
+                                              int lane) {
+  const int sh = c.base3 & 1;
+  for (int k = lane; k < c.rep_dim; k += 32) g[k + (k >= c.base3 ? sh : 0)] = __ldg(grow + k);
+}
+__device__ __forceinline__ const float2* grad3(const float* g, const Fchl19Consts& c) {
+  return reinterpret_cast<const float2*>(g + c.base3 + (c.base3 & 1));
 }
 __device__ __forceinline__ VjpWarp carve_vjp(char* base, int mxp, int rp) {
   VjpWarp s;
@@ -649,7 +665,7 @@ __device__ __forceinline__ VjpWarp carve_vjp(char* base, int mxp, int rp) {
   s.nb_u = s.stage + 64;
   s.nb_2b = s.nb_u + mxp;
   s.g = reinterpret_cast<float*>(s.nb_2b + mxp);
-  s.facc = s.g + rp;
+  s.facc = s.g + rp + 4;
   s.nb_el = reinterpret_cast<int*>(s.facc + 3 * mxp);
   s.nb_idx = s.nb_el + mxp;
   return s;
@@ -673,14 +689,13 @@ __device__ void vjp_from_neighbours(int n, int il, const Fchl19Consts& c, VjpWar
 
 __device__ void vjp_centre(const float4* pos, int M, int il, const Fchl19Consts& c, const float* __restrict__ grow,
                            VjpWarp& s, int lane) {
-  for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grow + k);
+  load_grad_row(s.g, grow, c, lane);
   const int n = neighbour_list(pos, M, il, c, s.nb_u, s.nb_2b, s.nb_el, s.nb_idx, lane);
   vjp_from_neighbours(n, il, c, s, lane);
 }
 
 __device__ void vjp_from_neighbours(int n, int il, const Fchl19Consts& c, VjpWarp& s, int lane) {
   float gi_x = 0.f, gi_y = 0.f, gi_z = 0.f;   // gradient on the centre (per-lane partials)
-  const float neg_eta3 = -c.eta3 * kLog2e;
 
   // two-body: lanes over neighbours (distinct atoms per lane); reciprocals
   // and the cutoff's sine from the hardware approximations (a few ulp)
@@ -777,23 +792,25 @@ __device__ void vjp_from_neighbours(int n, int il, const Fchl19Consts& c, VjpWar
         const float dW_dc = WR * (dQ_dc * F3 - QFN * inv_c + Q * fa * fb * dfcc);
         const float Ac = c.ang2 * ci, As = c.ang2 * si;
         const float dsi_dci = si > 1e-7f ? -ci * rcp_approx(si) : 0.0f;   // collinear guard
-        const float xbar = 0.5f * (a + b);
-        const float* gb = s.g + c.base3 + pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el) * c.n3 * 2;
-        // S = sum_k g_k rad_k and S1 = sum_k g_k (xbar - R_k) rad_k; d rad_k / d xbar
-        // = -2 eta3 (xbar - R_k) rad_k, the factor applied once below
+        // radial Gaussians rad_k = 2^-(y - y_k)^2, y = xbar sqrt(eta3 log2 e);
+        // S = sum_k g_k rad_k and S1 = sum_k g_k (y - y_k) rad_k, with
+        // d rad_k / d xbar = -2 eta3 (xbar - R_k) rad_k = -2 eta3 / sqrt(eta3 log2 e) (y - y_k) rad_k
+        const float y = 0.5f * (a + b) * c.sq_eta3;
+        const float2* gb = grad3(s.g, c) + pair_index(s.nb_el[jn], s.nb_el[kn], c.n_el) * c.n3;
         float Sc = 0.f, Ss = 0.f, Sc1 = 0.f, Ss1 = 0.f;
         for (int k = 0; k < c.n3; ++k) {
-          const float d = xbar - c.rs3[k];
-          const float rad = ex2_approx(d * (d * neg_eta3));
+          const float d = y - c.ys3[k];
+          const float rad = ex2_approx(-(d * d));
           const float td = d * rad;
-          const float g0 = gb[2 * k], g1 = gb[2 * k + 1];
-          Sc = fmaf(g0, rad, Sc);
-          Ss = fmaf(g1, rad, Ss);
-          Sc1 = fmaf(g0, td, Sc1);
-          Ss1 = fmaf(g1, td, Ss1);
+          const float2 g = gb[k];
+          Sc = fmaf(g.x, rad, Sc);
+          Ss = fmaf(g.y, rad, Ss);
+          Sc1 = fmaf(g.x, td, Sc1);
+          Ss1 = fmaf(g.y, td, Ss1);
         }
-        Sc1 *= -2.0f * c.eta3;
-        Ss1 *= -2.0f * c.eta3;
+        const float kd = -2.0f * c.eta3 / c.sq_eta3;
+        Sc1 *= kd;
+        Ss1 *= kd;
         const float AS = Ac * Sc + As * Ss;
         const float AS1 = Ac * Sc1 + As * Ss1;
         const float dA = c.ang2 * (Sc + dsi_dci * Ss);   // d(A.S)/d cos(th_i) at fixed S
@@ -1279,7 +1296,7 @@ fchl19_periodic_vjp_kernel(const float* __restrict__ coords, const int32_t* __re
     if (lane < 3) contrib[3 * (E + i) + lane] = 0.0f;
     return;
   }
-  for (int k = lane; k < c.rep_dim; k += 32) s.g[k] = __ldg(grad_rep + (size_t)i * rep_ld + k);
+  load_grad_row(s.g, grad_rep + (size_t)i * rep_ld, c, lane);
   for (int k = lane; k < 3 * (ne + 1); k += 32) s.facc[k] = 0.0f;
   const double xi = __ldg(coords + 3 * (size_t)i), yi = __ldg(coords + 3 * (size_t)i + 1),
                zi = __ldg(coords + 3 * (size_t)i + 2);
