@@ -4,16 +4,19 @@
 // cutoff and r^-N2 decay; three-body terms = ATM weight x Gaussian radial in
 // (r_ij + r_ik)/2 x Fourier angular [cos, sin] x three cutoffs.
 //
-// Design (GB300): one warp per centre atom. The warp stages its molecule's
-// coordinates in shared memory, builds the neighbour list with a ballot /
-// popc compaction (no HBM neighbour list), and accumulates the 780-wide row
-// in a per-warp shared-memory accumulator in a fixed order (deterministic,
-// no atomics). Two-body: lanes over radial bins, loop over neighbours.
-// Three-body forward: pair geometry computed lane-parallel over neighbour
-// pairs, staged in a 32-entry shared buffer, then lanes over radial bins.
+// Design (GB300): one warp per centre atom. The warp builds its neighbour list
+// from staged coordinates with a ballot / popc compaction (no HBM neighbour
+// list); every sum has a fixed order (deterministic, no atomics).
+// Forward (fchl19_forward_reg_kernel, up to 5 elements and 32-point grids):
+// lane k owns radial bin k; two-body sums in registers element by element;
+// three-body pairs are counting-sorted by element-pair type per block of up to
+// 256 pairs (lane-parallel geometry), then each type's run is walked in pair
+// order and its two columns stored. Larger parameter sets take
+// fchl19_forward_kernel (shared-memory rows).
 // VJP: lanes over neighbour pairs, each lane loops over its pair's radial
-// bins (no per-pair warp reductions); forces are summed per molecule by one
-// CTA, per-warp buffers reduced in a fixed order.
+// bins (no per-pair warp reductions); the pair contributions reach the atoms'
+// accumulators in a fixed order (segmented scans over lanes), summed per atom
+// in a fixed order.
 #include "common.cuh"
 
 namespace qmlr {
@@ -325,7 +328,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 
 // Per-warp shared memory of the register kernel: neighbour data and one block
 // of triplets, sorted by element-pair type.
-constexpr int kPairBlock = 256;   // neighbour pairs staged per walk (8 rounds of 32 lanes)
+constexpr int kPairBlock = 256;   // neighbour pairs staged per walk (8 sweeps of 32 lanes)
 struct RegWarp {
   float4* nb_u;   // [mxp] unit vector i->j, r_ij
   float4* nb_2b;  // [mxp] mu, log2(e)/(2 s^2), two-body prefactor, f_cut(r_ij)
@@ -432,11 +435,12 @@ __device__ __forceinline__ void fwd_row(const RegWarp& s, int n, const Fchl19Con
 
   // three-body, per block of up to kPairBlock neighbour pairs (j < k, row-major):
   //  1. lanes over pairs: each pair's element-pair type (15: no term, r_jk >= r_cut),
-  //     4 bits per round in `keys`, and the count of each type (lane t counts type t);
+  //     4 bits per 32-lane sweep in `keys`, and the count of each type (lane t counts type t);
   //  2. lanes over pairs: the pair geometry, written to its type's run in pair
-  //     order (rank among the round's lanes of the same type from four bit ballots);
-  //  3. lanes over bins: type by type (a compile-time accumulator index), the
-  //     run in pair order, two triplets per step.
+  //     order (rank among the sweep's lanes of the same type from four bit ballots);
+  //  3. lanes over bins: type by type, the run in pair order with four
+  //     Gaussians in flight; each type's (cos, sin) sums are stored at the end
+  //     of its run.
   // Every type's triplets are summed in pair order within a block; a block's
   // sums are added to the earlier blocks' in the row (one block in most rows).
   const unsigned lt_mask = (1u << lane) - 1u;
